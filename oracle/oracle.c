@@ -1,0 +1,1029 @@
+/*
+ * FP64 CPU oracle for light transport among Gaussian surfels (adapted radiosity).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path links, loads or calls this
+ * file; it exists so that the CUDA library can be checked against a plain, slow,
+ * obviously correct restatement of the method. It shares no code, header, table or
+ * constant generator with the CUDA path.
+ *
+ * Every function follows the paper's notation and cites the passage it restates:
+ *   Eq. G            surfel parametrisation P_i(u,v), G_i(u,v)            (Sec. 3.1)
+ *   Eq. L_I          alpha-composited incident radiance                     (Sec. 3.1)
+ *   Sec. 3.2         real SH basis, ordering [Y00, Y1-1, Y10, Y11, ...], Ybar(w)=Y(-w)
+ *   Eq. sh-brdf      SH expansion of a reciprocal BRDF, c_lm = (-1)^m c_l0
+ *   Eq. brdf         diffuse + Phong mixture;  App. A  closed-form coefficients
+ *   Eq. primal (DI)  direct illumination, Sec. 5.2;  light = infinitesimal surfel (Sec. 5.3)
+ *   Eq. before-final-radiosity / final-radiosity (Sec. 5.3), solid-angle form App. B
+ *   Eq. final_dL_dE  adjoint (dual) transport (Sec. 6, App. C)
+ *   Eq. final-dl-dbrdf closed-form BRDF gradient (limit n -> infinity)
+ *
+ * Readings taken where the paper is silent (each is listed in the design notes):
+ *   - kappa_i is a Dirac at p_i, so alpha_i(p_i)/Lambda_i * int kappa = o_i, and the
+ *     hemisphere / shadow rays start at the surfel centre.
+ *   - SH in world coordinates; the paper's local-frame (-1)^m sign is the mirror
+ *     reflection R_i d = 2(n_i.d)n_i - d:  f_i(d) = c_i (x) Y(R_i d), d = -w_I.
+ *   - c_l (same for all m of band l): l=0: 4 k a^d + (1-k) a^s; l>=1: (1-k) a^s rho_l(s).
+ *   - alpha = o_j * exp(-(u^2+v^2)/2) with a 3-sigma cutoff (u^2+v^2 <= 9), or the
+ *     furnace-only disc model alpha = o_j for u^2+v^2 <= 1.
+ *   - hemisphere directions: Nd = n_a x n_b stratified cosine-weighted (Malley) samples
+ *     with SplitMix64 jitter; weight pi/Nd.  Hits with |n_j.(p_j-o)| <= eps_plane are
+ *     ignored (coplanar neighbours); hits are sorted by t and runs of near-equal t are
+ *     ordered by surfel index.
+ *   - B^(0) = S = E + D (direct term), B^(k) = S + K B^(k-1): "n bounces" = n
+ *     applications of K after the direct term.
+ *
+ * Layouts: B, S, D, Q, V are [N][nc][C] with C = 3*max(NL,1) and column c = light*3 +
+ * channel (one right-hand side per light; a scene without lights has one, emission only).
+ * E and dL/dE are [N][nc][3].  Everything is double precision.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+enum { OR_ALPHA_GAUSS = 0, OR_ALPHA_DISC = 1 };
+
+/* ------------------------------------------------------------------ small vectors */
+static inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static inline void cross3(const double *a, const double *b, double *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* ------------------------------------------------------------------ SH (Sec. 3.2) */
+/* Real orthonormal SH, index l*l + l + m, Condon-Shortley phase, evaluated with the
+ * associated-Legendre recurrence on P_l^m(z)/(1-z^2)^{m/2} and the azimuthal factors
+ * Re/Im (x + i y)^m = sin^m(theta) cos/sin(m phi).  Valid for any degree. */
+void or_sh_eval(int L, const double *dir, double *Y) {
+    double x = dir[0], y = dir[1], z = dir[2];
+    double Pt[32][32]; /* Pt[l][m] = P_l^m(z) / sin^m(theta) */
+    for (int m = 0; m <= L; ++m) {
+        double pmm = 1.0;
+        for (int q = 1; q <= m; ++q) pmm *= -(2.0 * q - 1.0); /* (-1)^m (2m-1)!! */
+        Pt[m][m] = pmm;
+        if (m + 1 <= L) Pt[m + 1][m] = z * (2.0 * m + 1.0) * pmm;
+        for (int l = m + 2; l <= L; ++l)
+            Pt[l][m] = ((2.0 * l - 1.0) * z * Pt[l - 1][m] - (l + m - 1.0) * Pt[l - 2][m]) / (double)(l - m);
+    }
+    double cm[32], sm[32];
+    cm[0] = 1.0;
+    sm[0] = 0.0;
+    for (int m = 1; m <= L; ++m) { /* (x + i y)^m */
+        cm[m] = cm[m - 1] * x - sm[m - 1] * y;
+        sm[m] = cm[m - 1] * y + sm[m - 1] * x;
+    }
+    for (int l = 0; l <= L; ++l) {
+        for (int m = 0; m <= l; ++m) {
+            double ratio = 1.0; /* (l-m)!/(l+m)! */
+            for (int q = l - m + 1; q <= l + m; ++q) ratio /= (double)q;
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * ratio);
+            if (m == 0) {
+                Y[l * l + l] = K * Pt[l][0];
+            } else {
+                Y[l * l + l + m] = sqrt(2.0) * K * Pt[l][m] * cm[m];
+                Y[l * l + l - m] = sqrt(2.0) * K * Pt[l][m] * sm[m];
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------ BRDF (Eq. brdf, App. A) */
+/* rho_l(s): the Phong lobe's Funk-Hecke factor for band l, App. A.  l=0 gives 1. */
+double or_phong_rho(int l, double s) {
+    if (l == 0) return 1.0;
+    double num = 1.0, den = 1.0;
+    if (l % 2 == 1) { /* (s+1)(s-1)...(s-l+2) / ((s+2)(s+4)...(s+l+1)) */
+        for (int q = 1; q >= -(l - 2); q -= 2) num *= (s + q);
+        for (int q = 2; q <= l + 1; q += 2) den *= (s + q);
+    } else { /* s(s-2)...(s-l+2) / ((s+3)(s+5)...(s+l+1)) */
+        for (int q = 0; q >= -(l - 2); q -= 2) num *= (s + q);
+        for (int q = 3; q <= l + 1; q += 2) den *= (s + q);
+    }
+    return num / den;
+}
+
+/* c_{l,ch} for one surfel: l=0: 4 k a^d + (1-k) a^s ; l>=1: (1-k) a^s rho_l(s). */
+static void brdf_coeffs(int L, double k, const double *ad, const double *as, double shin, double *c /*[L+1][3]*/) {
+    for (int l = 0; l <= L; ++l)
+        for (int ch = 0; ch < 3; ++ch)
+            c[l * 3 + ch] = (l == 0) ? 4.0 * k * ad[ch] + (1.0 - k) * as[ch] : (1.0 - k) * as[ch] * or_phong_rho(l, shin);
+}
+
+/* ------------------------------------------------------------------ scene state */
+typedef struct {
+    double lo[3], hi[3];
+    int left, right; /* children; leaves: left = -(first+1), right = count */
+} or_node;
+
+typedef struct {
+    int n, L, nc, alpha_model, use_bvh;
+    double *p, *tu, *tv, *nrm, *su, *sv, *o, *k, *ad, *as, *shin;
+    double *c; /* [n][L+1][3] */
+    double eps_plane;
+    /* BVH (median split) */
+    or_node *nodes;
+    int nnodes, *prim;
+    double *blo, *bhi;
+    /* transport */
+    int nd, nl, C;
+    uint64_t seed;
+    double *lp, *li;
+    long nrays;
+    long *ray_off; /* [nrays+1] */
+    int *hit_j;
+    double *hit_alpha, *hit_G, *hit_a, *hit_t;
+    double *Dgeo; /* [n][nc][C] direct term without the o_i c_i factor */
+    long *sh_off; /* [n*nl + 1] shadow-ray hit lists */
+    int *sh_j;
+    double *sh_alpha, *sh_G;
+    double *sh_pre; /* [n*nl] = Y-free prefactor I*cos/r^2 (0 if back-facing) */
+} or_scene;
+
+static double *dup_arr(const double *src, size_t cnt) {
+    double *d = (double *)malloc(sizeof(double) * (cnt ? cnt : 1));
+    if (src) memcpy(d, src, sizeof(double) * cnt);
+    return d;
+}
+
+/* -------------------------------------------------------------- BVH (oracle's own) */
+typedef struct {
+    int *idx;
+    double *cen;
+    int axis;
+} sort_ctx_t;
+static sort_ctx_t g_sort; /* qsort comparator context (build is single-threaded) */
+static int cmp_cen(const void *a, const void *b) {
+    double ca = g_sort.cen[*(const int *)a * 3 + g_sort.axis], cb = g_sort.cen[*(const int *)b * 3 + g_sort.axis];
+    if (ca < cb) return -1;
+    if (ca > cb) return 1;
+    return (*(const int *)a) - (*(const int *)b);
+}
+
+static int bvh_build_rec(or_scene *s, int first, int count, double *cen) {
+    int id = s->nnodes++;
+    or_node *nd = &s->nodes[id];
+    for (int a = 0; a < 3; ++a) {
+        nd->lo[a] = 1e300;
+        nd->hi[a] = -1e300;
+    }
+    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+    for (int q = first; q < first + count; ++q) {
+        int j = s->prim[q];
+        for (int a = 0; a < 3; ++a) {
+            if (s->blo[j * 3 + a] < nd->lo[a]) nd->lo[a] = s->blo[j * 3 + a];
+            if (s->bhi[j * 3 + a] > nd->hi[a]) nd->hi[a] = s->bhi[j * 3 + a];
+            if (cen[j * 3 + a] < clo[a]) clo[a] = cen[j * 3 + a];
+            if (cen[j * 3 + a] > chi[a]) chi[a] = cen[j * 3 + a];
+        }
+    }
+    if (count <= 4) {
+        nd->left = -(first + 1);
+        nd->right = count;
+        return id;
+    }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+        if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+    g_sort.cen = cen;
+    g_sort.axis = axis;
+    qsort(s->prim + first, (size_t)count, sizeof(int), cmp_cen);
+    int half = count / 2;
+    int l = bvh_build_rec(s, first, half, cen);
+    int r = bvh_build_rec(s, first + half, count - half, cen);
+    s->nodes[id].left = l;
+    s->nodes[id].right = r;
+    return id;
+}
+
+static void bvh_build(or_scene *s) {
+    int n = s->n;
+    s->blo = (double *)malloc(sizeof(double) * 3 * n);
+    s->bhi = (double *)malloc(sizeof(double) * 3 * n);
+    double *cen = (double *)malloc(sizeof(double) * 3 * n);
+    double rad = (s->alpha_model == OR_ALPHA_DISC) ? 1.0 : 3.0;
+    for (int j = 0; j < n; ++j)
+        for (int a = 0; a < 3; ++a) {
+            double e = rad * sqrt(pow(s->su[j] * s->tu[j * 3 + a], 2) + pow(s->sv[j] * s->tv[j * 3 + a], 2));
+            e = e * (1.0 + 1e-9) + 1e-12; /* conservative against rounding of the hit point */
+            s->blo[j * 3 + a] = s->p[j * 3 + a] - e;
+            s->bhi[j * 3 + a] = s->p[j * 3 + a] + e;
+            cen[j * 3 + a] = s->p[j * 3 + a];
+        }
+    s->prim = (int *)malloc(sizeof(int) * n);
+    for (int j = 0; j < n; ++j) s->prim[j] = j;
+    s->nodes = (or_node *)malloc(sizeof(or_node) * (2 * n + 1));
+    s->nnodes = 0;
+    if (n > 0) bvh_build_rec(s, 0, n, cen);
+    free(cen);
+}
+
+/* ------------------------------------------------------------- scene construction */
+or_scene *or_scene_new(int n, int L, const double *p, const double *tu, const double *tv, const double *sc,
+                       const double *o, const double *ad, const double *k, const double *as, const double *shin,
+                       int alpha_model, int use_bvh) {
+    if (L < 0 || L > 30 || n < 0) return NULL;
+    or_scene *s = (or_scene *)calloc(1, sizeof(or_scene));
+    s->n = n;
+    s->L = L;
+    s->nc = (L + 1) * (L + 1);
+    s->alpha_model = alpha_model;
+    s->use_bvh = use_bvh;
+    s->p = dup_arr(p, 3 * (size_t)n);
+    s->o = dup_arr(o, n);
+    s->k = dup_arr(k, n);
+    s->ad = dup_arr(ad, 3 * (size_t)n);
+    s->as = dup_arr(as, 3 * (size_t)n);
+    s->shin = dup_arr(shin, n);
+    s->tu = dup_arr(NULL, 3 * (size_t)n);
+    s->tv = dup_arr(NULL, 3 * (size_t)n);
+    s->nrm = dup_arr(NULL, 3 * (size_t)n);
+    s->su = dup_arr(NULL, n);
+    s->sv = dup_arr(NULL, n);
+    s->c = dup_arr(NULL, (size_t)n * (L + 1) * 3);
+    /* Eq. G: orthonormal tangent frame (Gram-Schmidt of the given directions), n = tu x tv */
+    for (int i = 0; i < n; ++i) {
+        double a[3] = {tu[i * 3], tu[i * 3 + 1], tu[i * 3 + 2]}, b[3] = {tv[i * 3], tv[i * 3 + 1], tv[i * 3 + 2]};
+        double la = sqrt(dot3(a, a));
+        for (int q = 0; q < 3; ++q) a[q] /= la;
+        double pr = dot3(a, b);
+        for (int q = 0; q < 3; ++q) b[q] -= pr * a[q];
+        double lb = sqrt(dot3(b, b));
+        for (int q = 0; q < 3; ++q) b[q] /= lb;
+        double nn[3];
+        cross3(a, b, nn);
+        memcpy(s->tu + i * 3, a, sizeof a);
+        memcpy(s->tv + i * 3, b, sizeof b);
+        memcpy(s->nrm + i * 3, nn, sizeof nn);
+        s->su[i] = sc[i * 2];
+        s->sv[i] = sc[i * 2 + 1];
+        brdf_coeffs(L, k[i], ad + i * 3, as + i * 3, shin[i], s->c + (size_t)i * (L + 1) * 3);
+    }
+    /* eps_plane = 1e-5 * diagonal of the bounding box of the surfel centres */
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (p[i * 3 + a] < lo[a]) lo[a] = p[i * 3 + a];
+            if (p[i * 3 + a] > hi[a]) hi[a] = p[i * 3 + a];
+        }
+    double diag = 0.0;
+    if (n > 0)
+        for (int a = 0; a < 3; ++a) diag += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+    s->eps_plane = 1e-5 * sqrt(diag);
+    if (use_bvh) bvh_build(s);
+    return s;
+}
+
+static void free_transport(or_scene *s) {
+    free(s->lp);
+    free(s->li);
+    free(s->ray_off);
+    free(s->hit_j);
+    free(s->hit_alpha);
+    free(s->hit_G);
+    free(s->hit_a);
+    free(s->hit_t);
+    free(s->Dgeo);
+    free(s->sh_off);
+    free(s->sh_j);
+    free(s->sh_alpha);
+    free(s->sh_G);
+    free(s->sh_pre);
+    s->lp = s->li = NULL;
+    s->ray_off = NULL;
+    s->hit_j = NULL;
+    s->hit_alpha = s->hit_G = s->hit_a = s->hit_t = s->Dgeo = NULL;
+    s->sh_off = NULL;
+    s->sh_j = NULL;
+    s->sh_alpha = s->sh_G = s->sh_pre = NULL;
+}
+
+void or_scene_free(or_scene *s) {
+    if (!s) return;
+    free_transport(s);
+    free(s->p);
+    free(s->tu);
+    free(s->tv);
+    free(s->nrm);
+    free(s->su);
+    free(s->sv);
+    free(s->o);
+    free(s->k);
+    free(s->ad);
+    free(s->as);
+    free(s->shin);
+    free(s->c);
+    free(s->nodes);
+    free(s->prim);
+    free(s->blo);
+    free(s->bhi);
+    free(s);
+}
+
+double or_eps_plane(const or_scene *s) { return s->eps_plane; }
+void or_frames(const or_scene *s, double *tu, double *tv, double *nrm) {
+    memcpy(tu, s->tu, sizeof(double) * 3 * s->n);
+    memcpy(tv, s->tv, sizeof(double) * 3 * s->n);
+    memcpy(nrm, s->nrm, sizeof(double) * 3 * s->n);
+}
+void or_brdf(const or_scene *s, double *c) { memcpy(c, s->c, sizeof(double) * (size_t)s->n * (s->L + 1) * 3); }
+
+/* ------------------------------------------------------ hemisphere directions */
+/* SplitMix64 output function (Steele, Lea, Flood 2014) applied to a counter. */
+uint64_t or_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* uniform in [0,1) with 24 random bits; key = ((seed*2^32 + i)*2^12 + r)*2 + dim */
+double or_jitter(uint64_t seed, uint64_t i, uint64_t r, uint64_t dim) {
+    uint64_t key = ((((seed << 32) + i) << 12) + r) * 2u + dim;
+    return (double)(or_splitmix64(key) >> 40) * (1.0 / 16777216.0);
+}
+
+int or_strata_a(int nd) { /* n_a = 2^floor(log2(nd)/2): largest power of two with n_a^2 <= nd */
+    int na = 1;
+    while ((2 * na) * (2 * na) <= nd) na *= 2;
+    return na;
+}
+
+/* Ray r of surfel i: stratified cosine-weighted direction over the front hemisphere
+ * Omega = {w_I . n_i < 0}, i.e. d . n_i > 0 (App. B).  Each ray carries weight pi/Nd. */
+void or_ray_dir(const or_scene *s, int i, int nd, uint64_t seed, int r, double *d) {
+    int na = or_strata_a(nd), nb = nd / na;
+    int a = r / nb, b = r % nb;
+    double u1 = (a + or_jitter(seed, (uint64_t)i, (uint64_t)r, 0)) / na;
+    double u2 = (b + or_jitter(seed, (uint64_t)i, (uint64_t)r, 1)) / nb;
+    double rr = sqrt(u1), ph = 2.0 * OR_PI * u2, cz = sqrt(1.0 - u1);
+    double cx = rr * cos(ph), cy = rr * sin(ph);
+    for (int q = 0; q < 3; ++q) d[q] = cx * s->tu[i * 3 + q] + cy * s->tv[i * 3 + q] + cz * s->nrm[i * 3 + q];
+}
+
+/* ------------------------------------------------------ ray / surfel intersection */
+typedef struct {
+    double t, alpha, G;
+    int j;
+} or_hit;
+
+typedef struct {
+    or_hit *h;
+    int cnt, cap;
+} hitvec;
+
+static void hv_push(hitvec *v, or_hit x) {
+    if (v->cnt == v->cap) {
+        v->cap = v->cap ? 2 * v->cap : 32;
+        v->h = (or_hit *)realloc(v->h, sizeof(or_hit) * v->cap);
+    }
+    v->h[v->cnt++] = x;
+}
+
+/* Eq. G: the ray o + t d meets the plane of surfel j at t = n_j.(p_j - o) / n_j.d; the
+ * hit's local coordinates are (u,v) = ((x-p_j).t^u_j / s^u_j, (x-p_j).t^v_j / s^v_j). */
+static void test_surfel(const or_scene *s, int self, const double *o, const double *d, double tmax, int j, hitvec *out) {
+    if (j == self) return; /* no self-reflection (Sec. 5.1) */
+    const double *nj = s->nrm + j * 3, *pj = s->p + j * 3;
+    double den = dot3(nj, d);
+    if (fabs(den) < 1e-12) return;
+    double w[3] = {pj[0] - o[0], pj[1] - o[1], pj[2] - o[2]};
+    double h = dot3(nj, w);
+    if (fabs(h) <= s->eps_plane) return;
+    double t = h / den;
+    if (!(t > 0.0) || !(t < tmax)) return;
+    double q[3] = {t * d[0] - w[0], t * d[1] - w[1], t * d[2] - w[2]}; /* x - p_j */
+    double u = dot3(q, s->tu + j * 3) / s->su[j];
+    double v = dot3(q, s->tv + j * 3) / s->sv[j];
+    double r2 = u * u + v * v;
+    double G;
+    if (s->alpha_model == OR_ALPHA_DISC) {
+        if (r2 > 1.0) return;
+        G = 1.0;
+    } else {
+        if (r2 > 9.0) return;
+        G = exp(-0.5 * r2);
+    }
+    or_hit x = {t, s->o[j] * G, G, j};
+    hv_push(out, x);
+}
+
+static int ray_box(const double *lo, const double *hi, const double *o, const double *d, double tmax) {
+    double t0 = 0.0, t1 = tmax;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (o[a] < lo[a] || o[a] > hi[a]) return 0;
+            continue;
+        }
+        double ta = (lo[a] - o[a]) / d[a], tb = (hi[a] - o[a]) / d[a];
+        if (ta > tb) {
+            double tt = ta;
+            ta = tb;
+            tb = tt;
+        }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+static int cmp_hit(const void *a, const void *b) {
+    const or_hit *x = (const or_hit *)a, *y = (const or_hit *)b;
+    if (x->t < y->t) return -1;
+    if (x->t > y->t) return 1;
+    return x->j - y->j;
+}
+static int cmp_hit_j(const void *a, const void *b) { return ((const or_hit *)a)->j - ((const or_hit *)b)->j; }
+
+/* All hits on the segment (0, tmax), in compositing order: ascending t ("ideally
+ * sorted", Eq. L_I); consecutive hits within 1e-6*max(1,t) form a run that is ordered
+ * by surfel index so that exactly coplanar surfels composite deterministically. */
+static void trace_all(const or_scene *s, int self, const double *o, const double *d, double tmax, hitvec *out) {
+    out->cnt = 0;
+    if (s->use_bvh && s->nnodes > 0) {
+        int stack[256], sp = 0;
+        stack[sp++] = 0;
+        while (sp) {
+            const or_node *nd = &s->nodes[stack[--sp]];
+            if (!ray_box(nd->lo, nd->hi, o, d, tmax)) continue;
+            if (nd->left < 0) {
+                int first = -nd->left - 1;
+                for (int q = 0; q < nd->right; ++q) test_surfel(s, self, o, d, tmax, s->prim[first + q], out);
+            } else {
+                stack[sp++] = nd->left;
+                stack[sp++] = nd->right;
+            }
+        }
+    } else {
+        for (int j = 0; j < s->n; ++j) test_surfel(s, self, o, d, tmax, j, out);
+    }
+    if (out->cnt > 1) {
+        qsort(out->h, (size_t)out->cnt, sizeof(or_hit), cmp_hit);
+        int k = 0;
+        while (k < out->cnt) {
+            int e = k;
+            while (e + 1 < out->cnt && out->h[e + 1].t - out->h[e].t <= 1e-6 * fmax(1.0, out->h[e].t)) ++e;
+            if (e > k) qsort(out->h + k, (size_t)(e - k + 1), sizeof(or_hit), cmp_hit_j);
+            k = e + 1;
+        }
+    }
+}
+
+/* Exposed for tests: sorted hits of one ray.  Returns the hit count (<= cap written). */
+int or_trace_ray(const or_scene *s, int self, const double *o, const double *d, double tmax, int cap, int *j,
+                 double *t, double *alpha, double *G) {
+    hitvec hv = {0};
+    trace_all(s, self, o, d, tmax, &hv);
+    for (int q = 0; q < hv.cnt && q < cap; ++q) {
+        j[q] = hv.h[q].j;
+        t[q] = hv.h[q].t;
+        alpha[q] = hv.h[q].alpha;
+        G[q] = hv.h[q].G;
+    }
+    int c = hv.cnt;
+    free(hv.h);
+    return c;
+}
+
+/* ------------------------------------------------------------------ transport */
+static inline int band_of(int kk) { /* SH index -> degree l */
+    int l = 0;
+    while ((l + 1) * (l + 1) <= kk) ++l;
+    return l;
+}
+
+static void reflect(const double *n, const double *d, double *r) { /* R d = 2 (n.d) n - d */
+    double nd = dot3(n, d);
+    for (int q = 0; q < 3; ++q) r[q] = 2.0 * nd * n[q] - d[q];
+}
+
+/* Traces every surfel's Nd hemisphere rays (App. B, Eq. L_I) and the N x NL shadow
+ * rays of the direct term (Sec. 5.2), and stores per-ray hit records in compositing
+ * order with their weights a_h = alpha_h * prod_{k<h} (1 - alpha_k). */
+int or_transport(or_scene *s, int nd, uint64_t seed, int nl, const double *lp, const double *li) {
+    free_transport(s);
+    int n = s->n, nc = s->nc, L = s->L;
+    s->nd = nd;
+    s->seed = seed;
+    s->nl = nl;
+    s->C = 3 * (nl > 0 ? nl : 1); /* one right-hand side per light; emission only: one */
+    int C = s->C;
+    s->lp = dup_arr(lp, 3 * (size_t)nl);
+    s->li = dup_arr(li, 3 * (size_t)nl);
+    s->nrays = (long)n * nd;
+    hitvec *per = (hitvec *)calloc((size_t)(s->nrays ? s->nrays : 1), sizeof(hitvec));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i) {
+        for (int r = 0; r < nd; ++r) {
+            double d[3];
+            or_ray_dir(s, i, nd, seed, r, d);
+            trace_all(s, i, s->p + i * 3, d, INFINITY, &per[(long)i * nd + r]);
+        }
+    }
+    s->ray_off = (long *)malloc(sizeof(long) * (s->nrays + 1));
+    s->ray_off[0] = 0;
+    for (long r = 0; r < s->nrays; ++r) s->ray_off[r + 1] = s->ray_off[r] + per[r].cnt;
+    long H = s->ray_off[s->nrays];
+    s->hit_j = (int *)malloc(sizeof(int) * (H ? H : 1));
+    s->hit_alpha = dup_arr(NULL, H);
+    s->hit_G = dup_arr(NULL, H);
+    s->hit_a = dup_arr(NULL, H);
+    s->hit_t = dup_arr(NULL, H);
+    for (long r = 0; r < s->nrays; ++r) {
+        double T = 1.0;
+        for (int q = 0; q < per[r].cnt; ++q) {
+            long e = s->ray_off[r] + q;
+            s->hit_j[e] = per[r].h[q].j;
+            s->hit_t[e] = per[r].h[q].t;
+            s->hit_alpha[e] = per[r].h[q].alpha;
+            s->hit_G[e] = per[r].h[q].G;
+            s->hit_a[e] = per[r].h[q].alpha * T;
+            T *= (1.0 - per[r].h[q].alpha);
+        }
+        free(per[r].h);
+    }
+    free(per);
+
+    /* Direct term (Sec. 5.2): lights are infinitesimal emissive surfels sampled at their
+     * centre, with the light's normal factor dropped (Sec. 5.3); Y^T E_light = I. */
+    s->Dgeo = dup_arr(NULL, (size_t)n * nc * C);
+    memset(s->Dgeo, 0, sizeof(double) * (size_t)n * nc * C);
+    s->sh_pre = dup_arr(NULL, (size_t)n * nl);
+    hitvec *sper = (hitvec *)calloc((size_t)n * nl + 1, sizeof(hitvec));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i) {
+        double Y[1024];
+        for (int lt = 0; lt < nl; ++lt) {
+            const double *pl = lp + lt * 3;
+            double l[3] = {pl[0] - s->p[i * 3], pl[1] - s->p[i * 3 + 1], pl[2] - s->p[i * 3 + 2]};
+            double r = sqrt(dot3(l, l));
+            double w[3] = {l[0] / r, l[1] / r, l[2] / r};
+            double cs = dot3(s->nrm + i * 3, w);
+            s->sh_pre[(long)i * nl + lt] = 0.0;
+            if (!(cs > 0.0)) continue; /* only the front hemisphere Omega receives */
+            hitvec *hv = &sper[(long)i * nl + lt];
+            trace_all(s, i, s->p + i * 3, w, r, hv);
+            double T = 1.0;
+            for (int q = 0; q < hv->cnt; ++q) T *= (1.0 - hv->h[q].alpha);
+            double pre = cs / (r * r);
+            s->sh_pre[(long)i * nl + lt] = pre;
+            double rw[3];
+            reflect(s->nrm + i * 3, w, rw);
+            or_sh_eval(L, rw, Y);
+            for (int kk = 0; kk < nc; ++kk)
+                for (int ch = 0; ch < 3; ++ch)
+                    s->Dgeo[((size_t)i * nc + kk) * C + lt * 3 + ch] = Y[kk] * li[lt * 3 + ch] * pre * T;
+        }
+    }
+    s->sh_off = (long *)malloc(sizeof(long) * ((size_t)n * nl + 1));
+    s->sh_off[0] = 0;
+    for (long q = 0; q < (long)n * nl; ++q) s->sh_off[q + 1] = s->sh_off[q] + sper[q].cnt;
+    long SH = s->sh_off[(long)n * nl];
+    s->sh_j = (int *)malloc(sizeof(int) * (SH ? SH : 1));
+    s->sh_alpha = dup_arr(NULL, SH);
+    s->sh_G = dup_arr(NULL, SH);
+    for (long q = 0; q < (long)n * nl; ++q) {
+        for (int e = 0; e < sper[q].cnt; ++e) {
+            s->sh_j[s->sh_off[q] + e] = sper[q].h[e].j;
+            s->sh_alpha[s->sh_off[q] + e] = sper[q].h[e].alpha;
+            s->sh_G[s->sh_off[q] + e] = sper[q].h[e].G;
+        }
+        free(sper[q].h);
+    }
+    free(sper);
+    return 0;
+}
+
+long or_num_hits(const or_scene *s) { return s->ray_off ? s->ray_off[s->nrays] : 0; }
+long or_num_shadow_hits(const or_scene *s) { return s->sh_off ? s->sh_off[(long)s->n * s->nl] : 0; }
+
+/* Copies per-ray hit records: offsets [nrays+1], j, alpha, G, a, t. */
+void or_get_hits(const or_scene *s, long *off, int *j, double *alpha, double *G, double *a, double *t) {
+    long H = or_num_hits(s);
+    memcpy(off, s->ray_off, sizeof(long) * (s->nrays + 1));
+    memcpy(j, s->hit_j, sizeof(int) * H);
+    memcpy(alpha, s->hit_alpha, sizeof(double) * H);
+    memcpy(G, s->hit_G, sizeof(double) * H);
+    memcpy(a, s->hit_a, sizeof(double) * H);
+    memcpy(t, s->hit_t, sizeof(double) * H);
+}
+
+/* D = o_i c_i (x) Dgeo  ([N][nc][C]) */
+void or_direct(const or_scene *s, double *D) {
+    int n = s->n, nc = s->nc, C = s->C, L = s->L;
+    for (int i = 0; i < n; ++i)
+        for (int kk = 0; kk < nc; ++kk)
+            for (int c = 0; c < C; ++c)
+                D[((size_t)i * nc + kk) * C + c] =
+                    s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * s->Dgeo[((size_t)i * nc + kk) * C + c];
+}
+
+/* Eq. final-radiosity with the hemisphere integral taken by the stored rays:
+ *   Q_i = sum_r (pi/Nd) Y(R_i d_r) sum_h a_rh Y(-d_r)^T B_{j_h}        (geometric gather)
+ *   (K B)_i = o_i c_i (x) Q_i.
+ * Bout may be NULL; Q (un-scaled gather) may be NULL. */
+void or_apply_K(const or_scene *s, const double *Bin, double *Bout, double *Q) {
+    int n = s->n, nc = s->nc, C = s->C, nd = s->nd, L = s->L;
+    double w = OR_PI / nd;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i) {
+        double Yo[1024], Yi[1024], x[4096], acc[16384];
+        memset(acc, 0, sizeof(double) * nc * C);
+        for (int r = 0; r < nd; ++r) {
+            double d[3], md[3], rd[3];
+            or_ray_dir(s, i, nd, s->seed, r, d);
+            for (int q = 0; q < 3; ++q) md[q] = -d[q];
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            long ray = (long)i * nd + r;
+            for (int c = 0; c < C; ++c) x[c] = 0.0;
+            for (long e = s->ray_off[ray]; e < s->ray_off[ray + 1]; ++e) {
+                const double *Bj = Bin + (size_t)s->hit_j[e] * nc * C;
+                for (int c = 0; c < C; ++c) {
+                    double sv = 0.0;
+                    for (int kk = 0; kk < nc; ++kk) sv += Yo[kk] * Bj[kk * C + c];
+                    x[c] += s->hit_a[e] * sv;
+                }
+            }
+            for (int kk = 0; kk < nc; ++kk)
+                for (int c = 0; c < C; ++c) acc[kk * C + c] += w * Yi[kk] * x[c];
+        }
+        for (int kk = 0; kk < nc; ++kk)
+            for (int c = 0; c < C; ++c) {
+                size_t idx = ((size_t)i * nc + kk) * C + c;
+                if (Q) Q[idx] = acc[kk * C + c];
+                if (Bout) Bout[idx] = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
+            }
+    }
+}
+
+/* Transpose of or_apply_K, written as the scatter it is (Eq. final_dL_dE: the same
+ * paths with the decay reversed):
+ *   y_r[c]          = o_i (pi/Nd) sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) Vin_i[k'][c]
+ *   Vout_{j_h}[k][c] += a_rh Y_k(-d_r) y_r[c]                                         */
+void or_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
+    int n = s->n, nc = s->nc, C = s->C, nd = s->nd, L = s->L;
+    double w = OR_PI / nd;
+    memset(Vout, 0, sizeof(double) * (size_t)n * nc * C);
+    double Yo[1024], Yi[1024], y[4096];
+    for (int i = 0; i < n; ++i) {
+        for (int r = 0; r < nd; ++r) {
+            double d[3], md[3], rd[3];
+            or_ray_dir(s, i, nd, s->seed, r, d);
+            for (int q = 0; q < 3; ++q) md[q] = -d[q];
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            for (int c = 0; c < C; ++c) {
+                double sv = 0.0;
+                for (int kk = 0; kk < nc; ++kk)
+                    sv += s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Yi[kk] * Vin[((size_t)i * nc + kk) * C + c];
+                y[c] = s->o[i] * w * sv;
+            }
+            long ray = (long)i * nd + r;
+            for (long e = s->ray_off[ray]; e < s->ray_off[ray + 1]; ++e) {
+                double *Vj = Vout + (size_t)s->hit_j[e] * nc * C;
+                for (int kk = 0; kk < nc; ++kk)
+                    for (int c = 0; c < C; ++c) Vj[kk * C + c] += s->hit_a[e] * Yo[kk] * y[c];
+            }
+        }
+    }
+}
+
+/* S = E (broadcast over lights) + D */
+static void make_S(const or_scene *s, const double *E, double *S) {
+    int n = s->n, nc = s->nc, C = s->C;
+    or_direct(s, S);
+    if (E)
+        for (int i = 0; i < n; ++i)
+            for (int kk = 0; kk < nc; ++kk)
+                for (int c = 0; c < C; ++c) S[((size_t)i * nc + kk) * C + c] += E[((size_t)i * nc + kk) * 3 + c % 3];
+}
+
+/* Hybrid-solver analogue (Sec. 7): direct term first, then nb bounces
+ *   B^(0) = S,  B^(k) = S + K B^(k-1).
+ * B receives B^(nb).  iters (optional) receives B^(0..nb), (nb+1) x [N][nc][C]. */
+void or_solve(const or_scene *s, const double *E, int nb, double *B, double *iters) {
+    size_t M = (size_t)s->n * s->nc * s->C;
+    double *S = dup_arr(NULL, M), *cur = dup_arr(NULL, M), *nxt = dup_arr(NULL, M);
+    make_S(s, E, S);
+    memcpy(cur, S, sizeof(double) * M);
+    if (iters) memcpy(iters, cur, sizeof(double) * M);
+    for (int b = 1; b <= nb; ++b) {
+        or_apply_K(s, cur, nxt, NULL);
+        for (size_t q = 0; q < M; ++q) nxt[q] += S[q];
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
+        if (iters) memcpy(iters + (size_t)b * M, cur, sizeof(double) * M);
+    }
+    memcpy(B, cur, sizeof(double) * M);
+    free(S);
+    free(cur);
+    free(nxt);
+}
+
+/* Exact gradient of L(B^(nb)) with g = dL/dB^(nb)  (Sec. 6 restated for the truncated
+ * series; Eq. final_dL_dE is its n -> infinity limit):
+ *   v^(0) = g, v^(a) = K^T v^(a-1),  u = sum_{a=0..nb} v^(a) = dL/dS
+ *   dL/dE_i[k][ch]    = sum_L u_i[k][L*3+ch]
+ *   P_i[l][ch]        = sum_{k in l} sum_L ( sum_{a<nb} v_i^(a) Q_i^(nb-1-a) + u_i Dgeo_i )
+ *   dL/dc_i[l][ch]    = o_i P_i[l][ch];   dL/da^d_i[ch] = 4 k_i dL/dc_i[0][ch]
+ *   dL/do_i           = sum_{l,ch} c_i[l][ch] P_i[l][ch]                  (receiver factor)
+ *                     + sum over hemisphere hits on i of T_h (g_h - R_h) G_h  (compositing)
+ *                     + sum over shadow hits on i of -q prod_{m!=h}(1-alpha_m) G_h.
+ * Outputs may be NULL.  dc: [N][L+1][3]. */
+void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, double *dE, double *dad, double *dop,
+                double *dc) {
+    int n = s->n, nc = s->nc, C = s->C, nd = s->nd, L = s->L, nl = s->nl;
+    size_t M = (size_t)n * nc * C;
+    double w = OR_PI / nd;
+    double *iters = dup_arr(NULL, M * (nb + 1));
+    double *Bn = dup_arr(NULL, M);
+    or_solve(s, E, nb, Bn, iters);
+    double *Q = dup_arr(NULL, M * (nb > 0 ? nb : 1)); /* Q^(b) = gather of B^(b), b < nb */
+    for (int b = 0; b < nb; ++b) or_apply_K(s, iters + (size_t)b * M, NULL, Q + (size_t)b * M);
+    double *v = dup_arr(NULL, M * (nb + 1));
+    memcpy(v, g, sizeof(double) * M);
+    for (int a = 1; a <= nb; ++a) or_apply_KT(s, v + (size_t)(a - 1) * M, v + (size_t)a * M);
+    double *u = dup_arr(NULL, M);
+    memset(u, 0, sizeof(double) * M);
+    for (int a = 0; a <= nb; ++a)
+        for (size_t q = 0; q < M; ++q) u[q] += v[(size_t)a * M + q];
+
+    if (dE)
+        for (int i = 0; i < n; ++i)
+            for (int kk = 0; kk < nc; ++kk)
+                for (int ch = 0; ch < 3; ++ch) {
+                    double acc = 0.0;
+                    for (int lt = 0; lt < C / 3; ++lt) acc += u[((size_t)i * nc + kk) * C + lt * 3 + ch];
+                    dE[((size_t)i * nc + kk) * 3 + ch] = acc;
+                }
+    double *P = dup_arr(NULL, (size_t)n * (L + 1) * 3);
+    memset(P, 0, sizeof(double) * (size_t)n * (L + 1) * 3);
+    for (int i = 0; i < n; ++i)
+        for (int kk = 0; kk < nc; ++kk)
+            for (int c = 0; c < C; ++c) {
+                size_t idx = ((size_t)i * nc + kk) * C + c;
+                double acc = u[idx] * s->Dgeo[idx];
+                for (int a = 0; a < nb; ++a) acc += v[(size_t)a * M + idx] * Q[(size_t)(nb - 1 - a) * M + idx];
+                P[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] += acc;
+            }
+    if (dc)
+        for (int i = 0; i < n; ++i)
+            for (int q = 0; q < (L + 1) * 3; ++q) dc[(size_t)i * (L + 1) * 3 + q] = s->o[i] * P[(size_t)i * (L + 1) * 3 + q];
+    if (dad)
+        for (int i = 0; i < n; ++i)
+            for (int ch = 0; ch < 3; ++ch) dad[i * 3 + ch] = 4.0 * s->k[i] * s->o[i] * P[((size_t)i * (L + 1)) * 3 + ch];
+    if (dop) {
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int q = 0; q < (L + 1) * 3; ++q) acc += s->c[(size_t)i * (L + 1) * 3 + q] * P[(size_t)i * (L + 1) * 3 + q];
+            dop[i] = acc;
+        }
+        /* hemisphere rays: backward through a_h = alpha_h prod_{k<h}(1 - alpha_k) */
+        double Yo[1024], Yi[1024];
+        double *y = dup_arr(NULL, (size_t)(nb > 0 ? nb : 1) * C);
+        for (int i = 0; i < n; ++i) {
+            for (int r = 0; r < nd; ++r) {
+                long ray = (long)i * nd + r;
+                long e0 = s->ray_off[ray], e1 = s->ray_off[ray + 1];
+                if (e1 == e0 || nb == 0) continue;
+                double d[3], md[3], rd[3];
+                or_ray_dir(s, i, nd, s->seed, r, d);
+                for (int q = 0; q < 3; ++q) md[q] = -d[q];
+                reflect(s->nrm + i * 3, d, rd);
+                or_sh_eval(L, md, Yo);
+                or_sh_eval(L, rd, Yi);
+                for (int a = 0; a < nb; ++a)
+                    for (int c = 0; c < C; ++c) {
+                        double sv = 0.0;
+                        for (int kk = 0; kk < nc; ++kk)
+                            sv += s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Yi[kk] *
+                                  v[(size_t)a * M + ((size_t)i * nc + kk) * C + c];
+                        y[a * C + c] = s->o[i] * w * sv;
+                    }
+                int H = (int)(e1 - e0);
+                double *gh = dup_arr(NULL, H), *Th = dup_arr(NULL, H);
+                double T = 1.0;
+                for (int h = 0; h < H; ++h) {
+                    long e = e0 + h;
+                    Th[h] = T;
+                    T *= (1.0 - s->hit_alpha[e]);
+                    double acc = 0.0;
+                    for (int a = 0; a < nb; ++a) {
+                        const double *Bb = iters + (size_t)(nb - 1 - a) * M + (size_t)s->hit_j[e] * nc * C;
+                        for (int c = 0; c < C; ++c) {
+                            double sv = 0.0;
+                            for (int kk = 0; kk < nc; ++kk) sv += Yo[kk] * Bb[kk * C + c];
+                            acc += y[a * C + c] * sv;
+                        }
+                    }
+                    gh[h] = acc;
+                }
+                double R = 0.0;
+                for (int h = H - 1; h >= 0; --h) {
+                    long e = e0 + h;
+                    double dalpha = Th[h] * (gh[h] - R);
+                    dop[s->hit_j[e]] += dalpha * s->hit_G[e];
+                    R = s->hit_alpha[e] * gh[h] + (1.0 - s->hit_alpha[e]) * R;
+                }
+                free(gh);
+                free(Th);
+            }
+        }
+        free(y);
+        /* shadow rays: backward through T = prod_m (1 - alpha_m) */
+        for (int i = 0; i < n; ++i) {
+            for (int lt = 0; lt < nl; ++lt) {
+                long q0 = s->sh_off[(long)i * nl + lt], q1 = s->sh_off[(long)i * nl + lt + 1];
+                double pre = s->sh_pre[(long)i * nl + lt];
+                if (q1 == q0 || pre == 0.0) continue;
+                const double *pl = s->lp + lt * 3;
+                double l[3] = {pl[0] - s->p[i * 3], pl[1] - s->p[i * 3 + 1], pl[2] - s->p[i * 3 + 2]};
+                double r = sqrt(dot3(l, l));
+                double wv[3] = {l[0] / r, l[1] / r, l[2] / r}, rw[3];
+                reflect(s->nrm + i * 3, wv, rw);
+                or_sh_eval(L, rw, Yi);
+                double qv = 0.0;
+                for (int kk = 0; kk < nc; ++kk)
+                    for (int ch = 0; ch < 3; ++ch)
+                        qv += u[((size_t)i * nc + kk) * C + lt * 3 + ch] * s->o[i] *
+                              s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + ch] * Yi[kk] * s->li[lt * 3 + ch] * pre;
+                for (long e = q0; e < q1; ++e) {
+                    double others = 1.0;
+                    for (long m = q0; m < q1; ++m)
+                        if (m != e) others *= (1.0 - s->sh_alpha[m]);
+                    dop[s->sh_j[e]] += -qv * others * s->sh_G[e];
+                }
+            }
+        }
+    }
+    free(P);
+    free(iters);
+    free(Bn);
+    free(Q);
+    free(v);
+    free(u);
+}
+
+/* The paper's closed-form BRDF gradient (Eq. final-dl-dbrdf), exact as n -> infinity:
+ *   dL/dc_i[l][ch] = sum_{k in l} sum_L u_i[k][c] (B_i - E_i)[k][c] / c_i[l][ch]
+ * with u = dL/dS of the same truncated solve and B = B^(nb).  Bands with c = 0 get 0. */
+void or_brdf_grad_closed_form(const or_scene *s, const double *E, int nb, const double *g, double *dc) {
+    int n = s->n, nc = s->nc, C = s->C, L = s->L;
+    size_t M = (size_t)n * nc * C;
+    double *B = dup_arr(NULL, M);
+    or_solve(s, E, nb, B, NULL);
+    double *v = dup_arr(NULL, M), *t = dup_arr(NULL, M), *u = dup_arr(NULL, M);
+    memcpy(v, g, sizeof(double) * M);
+    memcpy(u, g, sizeof(double) * M);
+    for (int a = 1; a <= nb; ++a) {
+        or_apply_KT(s, v, t);
+        memcpy(v, t, sizeof(double) * M);
+        for (size_t q = 0; q < M; ++q) u[q] += v[q];
+    }
+    memset(dc, 0, sizeof(double) * (size_t)n * (L + 1) * 3);
+    for (int i = 0; i < n; ++i)
+        for (int kk = 0; kk < nc; ++kk)
+            for (int c = 0; c < C; ++c) {
+                size_t idx = ((size_t)i * nc + kk) * C + c;
+                double cc = s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3];
+                double e = E ? E[((size_t)i * nc + kk) * 3 + c % 3] : 0.0;
+                if (cc != 0.0) dc[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] += u[idx] * (B[idx] - e) / cc;
+            }
+    free(B);
+    free(v);
+    free(t);
+    free(u);
+}
+
+/* Dense K for one column c: Kd[(i*nc+k')*(N*nc) + j*nc + k] (tiny scenes only). */
+void or_dense_K(const or_scene *s, int col, double *Kd) {
+    int n = s->n, nc = s->nc, nd = s->nd, L = s->L;
+    size_t Mm = (size_t)n * nc;
+    double w = OR_PI / nd;
+    memset(Kd, 0, sizeof(double) * Mm * Mm);
+    double Yo[1024], Yi[1024];
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < nd; ++r) {
+            double d[3], md[3], rd[3];
+            or_ray_dir(s, i, nd, s->seed, r, d);
+            for (int q = 0; q < 3; ++q) md[q] = -d[q];
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            long ray = (long)i * nd + r;
+            for (long e = s->ray_off[ray]; e < s->ray_off[ray + 1]; ++e) {
+                int j = s->hit_j[e];
+                for (int kp = 0; kp < nc; ++kp) {
+                    double f = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kp)) * 3 + col % 3] * w * Yi[kp] * s->hit_a[e];
+                    for (int kk = 0; kk < nc; ++kk) Kd[((size_t)i * nc + kp) * Mm + (size_t)j * nc + kk] += f * Yo[kk];
+                }
+            }
+        }
+}
+
+/* ------------------------------------------------ sampled checks for large scenes */
+/* Direct term D_i for the listed receivers only (no hemisphere rays traced).
+ * out: [m][nc][C]. */
+void or_sample_direct(const or_scene *s, int nl, const double *lp, const double *li, int m, const int *recv, double *out) {
+    int nc = s->nc, L = s->L, C = 3 * nl;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int q = 0; q < m; ++q) {
+        int i = recv[q];
+        double Y[1024];
+        hitvec hv = {0};
+        for (int kk = 0; kk < nc * C; ++kk) out[(size_t)q * nc * C + kk] = 0.0;
+        for (int lt = 0; lt < nl; ++lt) {
+            const double *pl = lp + lt * 3;
+            double l[3] = {pl[0] - s->p[i * 3], pl[1] - s->p[i * 3 + 1], pl[2] - s->p[i * 3 + 2]};
+            double r = sqrt(dot3(l, l));
+            double w[3] = {l[0] / r, l[1] / r, l[2] / r};
+            double cs = dot3(s->nrm + i * 3, w);
+            if (!(cs > 0.0)) continue;
+            trace_all(s, i, s->p + i * 3, w, r, &hv);
+            double T = 1.0;
+            for (int e = 0; e < hv.cnt; ++e) T *= (1.0 - hv.h[e].alpha);
+            double rw[3];
+            reflect(s->nrm + i * 3, w, rw);
+            or_sh_eval(L, rw, Y);
+            for (int kk = 0; kk < nc; ++kk)
+                for (int ch = 0; ch < 3; ++ch)
+                    out[((size_t)q * nc + kk) * C + lt * 3 + ch] =
+                        s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + ch] * Y[kk] * li[lt * 3 + ch] * cs / (r * r) * T;
+        }
+        free(hv.h);
+    }
+}
+
+/* First bounce B^(1)_i = S_i + (K S)_i for the listed receivers: traces only their
+ * hemisphere rays and the shadow rays of the surfels those rays hit.  E may be NULL.
+ * out: [m][nc][C]. */
+void or_sample_bounce1(const or_scene *s, int nd, uint64_t seed, int nl, const double *lp, const double *li,
+                       const double *E, int m, const int *recv, double *out) {
+    int nc = s->nc, L = s->L, C = 3 * nl;
+    double w = OR_PI / nd;
+    for (int q = 0; q < m; ++q) {
+        int i = recv[q];
+        double *acc = out + (size_t)q * nc * C;
+        /* S_i */
+        or_sample_direct(s, nl, lp, li, 1, &i, acc);
+        if (E)
+            for (int kk = 0; kk < nc; ++kk)
+                for (int c = 0; c < C; ++c) acc[kk * C + c] += E[((size_t)i * nc + kk) * 3 + c % 3];
+        double *Q = dup_arr(NULL, (size_t)nc * C);
+        memset(Q, 0, sizeof(double) * nc * C);
+        double *Sj = dup_arr(NULL, (size_t)nc * C);
+        double Yo[1024], Yi[1024], x[4096];
+        hitvec hv = {0};
+        for (int r = 0; r < nd; ++r) {
+            double d[3], md[3], rd[3];
+            or_ray_dir(s, i, nd, seed, r, d);
+            for (int qq = 0; qq < 3; ++qq) md[qq] = -d[qq];
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            trace_all(s, i, s->p + i * 3, d, INFINITY, &hv);
+            for (int c = 0; c < C; ++c) x[c] = 0.0;
+            double T = 1.0;
+            for (int h = 0; h < hv.cnt; ++h) {
+                int j = hv.h[h].j;
+                double a = hv.h[h].alpha * T;
+                T *= (1.0 - hv.h[h].alpha);
+                or_sample_direct(s, nl, lp, li, 1, &j, Sj);
+                if (E)
+                    for (int kk = 0; kk < nc; ++kk)
+                        for (int c = 0; c < C; ++c) Sj[kk * C + c] += E[((size_t)j * nc + kk) * 3 + c % 3];
+                for (int c = 0; c < C; ++c) {
+                    double sv = 0.0;
+                    for (int kk = 0; kk < nc; ++kk) sv += Yo[kk] * Sj[kk * C + c];
+                    x[c] += a * sv;
+                }
+            }
+            for (int kk = 0; kk < nc; ++kk)
+                for (int c = 0; c < C; ++c) Q[kk * C + c] += w * Yi[kk] * x[c];
+        }
+        for (int kk = 0; kk < nc; ++kk)
+            for (int c = 0; c < C; ++c)
+                acc[kk * C + c] += s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Q[kk * C + c];
+        free(hv.h);
+        free(Q);
+        free(Sj);
+    }
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

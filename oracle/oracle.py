@@ -1,0 +1,270 @@
+"""ctypes binding of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by bench.py's
+CPU-baseline / reference legs.  The product path never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ALPHA_GAUSS, ALPHA_DISC = 0, 1
+
+_dp = ct.POINTER(ct.c_double)
+_ip = ct.POINTER(ct.c_int)
+_lp = ct.POINTER(ct.c_long)
+
+
+def build(force=False):
+    """Compile oracle.c into liboracle.so (gcc, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ct.CDLL(_LIB)
+            L.or_scene_new.restype = ct.c_void_p
+            L.or_scene_new.argtypes = [ct.c_int, ct.c_int] + [_dp] * 9 + [ct.c_int, ct.c_int]
+            L.or_scene_free.argtypes = [ct.c_void_p]
+            L.or_sh_eval.argtypes = [ct.c_int, _dp, _dp]
+            L.or_phong_rho.restype = ct.c_double
+            L.or_phong_rho.argtypes = [ct.c_int, ct.c_double]
+            L.or_splitmix64.restype = ct.c_uint64
+            L.or_splitmix64.argtypes = [ct.c_uint64]
+            L.or_jitter.restype = ct.c_double
+            L.or_jitter.argtypes = [ct.c_uint64] * 4
+            L.or_strata_a.restype = ct.c_int
+            L.or_strata_a.argtypes = [ct.c_int]
+            L.or_eps_plane.restype = ct.c_double
+            L.or_eps_plane.argtypes = [ct.c_void_p]
+            L.or_frames.argtypes = [ct.c_void_p, _dp, _dp, _dp]
+            L.or_brdf.argtypes = [ct.c_void_p, _dp]
+            L.or_ray_dir.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_uint64, ct.c_int, _dp]
+            L.or_trace_ray.restype = ct.c_int
+            L.or_trace_ray.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, ct.c_double, ct.c_int, _ip, _dp, _dp, _dp]
+            L.or_transport.restype = ct.c_int
+            L.or_transport.argtypes = [ct.c_void_p, ct.c_int, ct.c_uint64, ct.c_int, _dp, _dp]
+            L.or_num_hits.restype = ct.c_long
+            L.or_num_hits.argtypes = [ct.c_void_p]
+            L.or_num_shadow_hits.restype = ct.c_long
+            L.or_num_shadow_hits.argtypes = [ct.c_void_p]
+            L.or_get_hits.argtypes = [ct.c_void_p, _lp, _ip, _dp, _dp, _dp, _dp]
+            L.or_direct.argtypes = [ct.c_void_p, _dp]
+            L.or_apply_K.argtypes = [ct.c_void_p, _dp, _dp, _dp]
+            L.or_apply_KT.argtypes = [ct.c_void_p, _dp, _dp]
+            L.or_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
+            L.or_adjoint.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp, _dp, _dp]
+            L.or_brdf_grad_closed_form.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
+            L.or_dense_K.argtypes = [ct.c_void_p, ct.c_int, _dp]
+            L.or_sample_direct.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, ct.c_int, _ip, _dp]
+            L.or_sample_bounce1.argtypes = [ct.c_void_p, ct.c_int, ct.c_uint64, ct.c_int, _dp, _dp, _dp,
+                                            ct.c_int, _ip, _dp]
+            L.or_num_threads.restype = ct.c_int
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    if a is None:
+        return ct.cast(None, _dp)
+    return a.ctypes.data_as(_dp)
+
+
+def sh_eval(L, d):
+    d = _d(d).reshape(3)
+    out = np.zeros((L + 1) ** 2)
+    lib().or_sh_eval(L, _ptr(d), _ptr(out))
+    return out
+
+
+def phong_rho(l, s):
+    return lib().or_phong_rho(int(l), float(s))
+
+
+def splitmix64(x):
+    return int(lib().or_splitmix64(ct.c_uint64(x)))
+
+
+def jitter(seed, i, r, dim):
+    return lib().or_jitter(seed, i, r, dim)
+
+
+def strata_a(nd):
+    return lib().or_strata_a(nd)
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+class Oracle:
+    """FP64 CPU implementation of the transport, adjoint and gradients of one scene."""
+
+    def __init__(self, sc, alpha_model=ALPHA_GAUSS, use_bvh=True):
+        L = lib()
+        self.sc = sc
+        self.n = int(sc["n"])
+        self.L = int(sc["L"])
+        self.nc = (self.L + 1) ** 2
+        self._keep = [_d(sc[k]) for k in ("p", "tu", "tv", "s", "o", "ad", "k", "as_", "shin")]
+        self.h = L.or_scene_new(self.n, self.L, *[_ptr(a) for a in self._keep], int(alpha_model), int(use_bvh))
+        if not self.h:
+            raise ValueError("oracle: invalid scene")
+        self.C = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().or_scene_free(self.h)
+                self.h = None
+        except Exception:  # pragma: no cover
+            pass
+
+    # geometry ------------------------------------------------------------
+    @property
+    def eps_plane(self):
+        return lib().or_eps_plane(self.h)
+
+    def frames(self):
+        tu, tv, nn = (np.zeros((self.n, 3)) for _ in range(3))
+        lib().or_frames(self.h, _ptr(tu), _ptr(tv), _ptr(nn))
+        return tu, tv, nn
+
+    def brdf(self):
+        c = np.zeros((self.n, self.L + 1, 3))
+        lib().or_brdf(self.h, _ptr(c))
+        return c
+
+    def ray_dir(self, i, nd, seed, r):
+        d = np.zeros(3)
+        lib().or_ray_dir(self.h, i, nd, seed, r, _ptr(d))
+        return d
+
+    def trace_ray(self, self_idx, o, d, tmax=np.inf, cap=4096):
+        j = np.zeros(cap, np.int32)
+        t, a, G = (np.zeros(cap) for _ in range(3))
+        o, d = _d(o).reshape(3), _d(d).reshape(3)
+        cnt = lib().or_trace_ray(self.h, self_idx, _ptr(o), _ptr(d), float(tmax), cap,
+                                 j.ctypes.data_as(_ip), _ptr(t), _ptr(a), _ptr(G))
+        cnt = min(cnt, cap)
+        return j[:cnt], t[:cnt], a[:cnt], G[:cnt]
+
+    # transport -----------------------------------------------------------
+    def transport(self, nd=None, seed=None, light_pos=None, light_I=None):
+        nd = self.sc["nd"] if nd is None else nd
+        seed = self.sc["seed"] if seed is None else seed
+        lp = _d(self.sc["light_pos"] if light_pos is None else light_pos).reshape(-1, 3)
+        li = _d(self.sc["light_I"] if light_I is None else light_I).reshape(-1, 3)
+        self.nd, self.seed, self.nl = int(nd), int(seed), lp.shape[0]
+        self.C = 3 * max(self.nl, 1)
+        self._lights = (lp, li)
+        lib().or_transport(self.h, self.nd, self.seed, self.nl, _ptr(lp), _ptr(li))
+        return self
+
+    def hits(self):
+        L = lib()
+        H = L.or_num_hits(self.h)
+        R = self.n * self.nd
+        off = np.zeros(R + 1, np.int64)
+        j = np.zeros(max(H, 1), np.int32)
+        al, G, a, t = (np.zeros(max(H, 1)) for _ in range(4))
+        L.or_get_hits(self.h, off.ctypes.data_as(_lp), j.ctypes.data_as(_ip), _ptr(al), _ptr(G), _ptr(a), _ptr(t))
+        return dict(off=off, j=j[:H], alpha=al[:H], G=G[:H], a=a[:H], t=t[:H])
+
+    def num_shadow_hits(self):
+        return lib().or_num_shadow_hits(self.h)
+
+    def _shape(self):
+        return (self.n, self.nc, self.C)
+
+    def direct(self):
+        D = np.zeros(self._shape())
+        lib().or_direct(self.h, _ptr(D))
+        return D
+
+    def apply_K(self, B):
+        B = _d(B).reshape(self._shape())
+        out, Q = np.zeros(self._shape()), np.zeros(self._shape())
+        lib().or_apply_K(self.h, _ptr(B), _ptr(out), _ptr(Q))
+        return out, Q
+
+    def apply_KT(self, V):
+        V = _d(V).reshape(self._shape())
+        out = np.zeros(self._shape())
+        lib().or_apply_KT(self.h, _ptr(V), _ptr(out))
+        return out
+
+    def solve(self, E=None, nb=None, iters=False):
+        nb = self.sc["nb"] if nb is None else nb
+        E = _d(E)
+        B = np.zeros(self._shape())
+        it = np.zeros((nb + 1,) + self._shape()) if iters else None
+        lib().or_solve(self.h, _ptr(E), int(nb), _ptr(B), _ptr(it))
+        return (B, it) if iters else B
+
+    def adjoint(self, g, E=None, nb=None):
+        nb = self.sc["nb"] if nb is None else nb
+        g = _d(g).reshape(self._shape())
+        E = _d(E)
+        dE = np.zeros((self.n, self.nc, 3))
+        dad = np.zeros((self.n, 3))
+        dop = np.zeros(self.n)
+        dc = np.zeros((self.n, self.L + 1, 3))
+        lib().or_adjoint(self.h, _ptr(E), int(nb), _ptr(g), _ptr(dE), _ptr(dad), _ptr(dop), _ptr(dc))
+        return dict(dE=dE, dad=dad, dop=dop, dc=dc)
+
+    def brdf_grad_closed_form(self, g, E=None, nb=None):
+        nb = self.sc["nb"] if nb is None else nb
+        dc = np.zeros((self.n, self.L + 1, 3))
+        lib().or_brdf_grad_closed_form(self.h, _ptr(_d(E)), int(nb), _ptr(_d(g).reshape(self._shape())), _ptr(dc))
+        return dc
+
+    def dense_K(self, col):
+        m = self.n * self.nc
+        K = np.zeros((m, m))
+        lib().or_dense_K(self.h, int(col), _ptr(K))
+        return K
+
+    def sample_direct(self, recv, light_pos=None, light_I=None):
+        lp = _d(self.sc["light_pos"] if light_pos is None else light_pos).reshape(-1, 3)
+        li = _d(self.sc["light_I"] if light_I is None else light_I).reshape(-1, 3)
+        recv = np.ascontiguousarray(recv, dtype=np.int32)
+        out = np.zeros((len(recv), self.nc, 3 * lp.shape[0]))
+        lib().or_sample_direct(self.h, lp.shape[0], _ptr(lp), _ptr(li), len(recv), recv.ctypes.data_as(_ip), _ptr(out))
+        return out
+
+    def sample_bounce1(self, recv, E=None, nd=None, seed=None, light_pos=None, light_I=None):
+        nd = self.sc["nd"] if nd is None else nd
+        seed = self.sc["seed"] if seed is None else seed
+        lp = _d(self.sc["light_pos"] if light_pos is None else light_pos).reshape(-1, 3)
+        li = _d(self.sc["light_I"] if light_I is None else light_I).reshape(-1, 3)
+        recv = np.ascontiguousarray(recv, dtype=np.int32)
+        out = np.zeros((len(recv), self.nc, 3 * lp.shape[0]))
+        lib().or_sample_bounce1(self.h, int(nd), int(seed), lp.shape[0], _ptr(lp), _ptr(li), _ptr(_d(E)),
+                                len(recv), recv.ctypes.data_as(_ip), _ptr(out))
+        return out
