@@ -1,0 +1,214 @@
+/*
+ * rgs.h — C ABI of the GB300 light-transport library for Gaussian surfels
+ * (adapted radiosity; "Differentiable Light Transport with Gaussian Surfels via
+ * Adapted Radiosity", arXiv 2509.18497).
+ *
+ * The library computes, on one GPU, the outgoing radiance of every surfel held as
+ * spherical-harmonic (SH) coefficients per RGB channel, under point lights, with
+ * global illumination, and the gradients of a loss with respect to the surfels'
+ * emission, diffuse albedo and opacity:
+ *
+ *   rgs_build_scene      surfel frames, BRDF coefficients, Morton order, BVH  (Eq. G, Eq. brdf, App. A)
+ *   rgs_trace_transport  hemisphere rays with alpha compositing (Eq. L_I, App. B) and the
+ *                        direct term from shadow rays (Sec. 5.2 direct-illumination equation)
+ *   rgs_solve            bounce iteration B <- S + K B (Eq. final-radiosity; Sec. 7 hybrid solver:
+ *                        direct term first, then a fixed number of bounces)
+ *   rgs_adjoint          transposed bounces and parameter gradients (Eq. final_dL_dE,
+ *                        Eq. final-dl-dbrdf, Eq. dl-dgeo-0 restricted to opacity)
+ *
+ * CONVENTIONS (all entry points)
+ *  - Every pointer documented "device" must point to memory of the current CUDA device;
+ *    "host" pointers to host memory.  Arrays are dense, row-major, float32 unless stated.
+ *  - The caller owns every array it passes in or receives results in; the library never
+ *    frees caller memory.  The library owns the opaque handles and their workspace.
+ *  - All GPU work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *    Entry points that report data to the host (hit counts, residual norms, status flags
+ *    raised on the device) synchronise `stream` before returning; this is stated per call.
+ *  - No C++ exception crosses this boundary.  Every call returns an rgs_status; the text
+ *    of the last error on the calling thread is available from rgs_last_error().
+ *  - Handles are not thread-safe: one handle is used by one host thread at a time.
+ *  - Indexing: surfels are numbered 0..N-1 in the caller's order everywhere in the ABI.
+ *    SH coefficients are ordered Y00, Y1-1, Y10, Y11, Y2-2, ... (index l*l + l + m), real,
+ *    orthonormal, with the Condon-Shortley phase (Y1-1 = -c y, Y10 = c z, Y11 = -c x).
+ *  - Right-hand sides ("columns"): C = 3 * max(NL, 1).  Column c = light * 3 + channel:
+ *    light `light` alone plus the emission E.  With no lights there is one condition
+ *    (emission only).
+ *  - Radiosity arrays B and dL/dB are [N][nc][C] with nc = (L+1)^2.
+ */
+#ifndef RGS_H
+#define RGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RGS_MAX_SH_DEGREE 3  /* L in [0, 3]: nc in {1, 4, 9, 16} */
+#define RGS_MAX_BOUNCES 64
+#define RGS_ABI_VERSION 1
+
+typedef enum rgs_status {
+    RGS_OK = 0,
+    RGS_ERR_ARG = 1,       /* invalid argument (NULL pointer, size out of range, bad enum) */
+    RGS_ERR_CUDA = 2,      /* a CUDA runtime call failed; see rgs_last_error() */
+    RGS_ERR_OOM = 3,       /* device allocation failed */
+    RGS_ERR_CAPACITY = 4,  /* a fixed-size buffer was too small (reported, never overrun) */
+    RGS_ERR_NONFINITE = 5, /* an input holds NaN or Inf (only when checking is enabled) */
+    RGS_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+    RGS_ERR_STATE = 7      /* call out of order (e.g. adjoint before solve) */
+} rgs_status;
+
+typedef enum rgs_alpha_model {
+    RGS_ALPHA_GAUSS = 0, /* alpha = o * exp(-(u^2+v^2)/2) for u^2+v^2 <= 9 (3-sigma cutoff) */
+    RGS_ALPHA_DISC = 1   /* alpha = o for u^2+v^2 <= 1, else 0 (closed-sphere furnace test) */
+} rgs_alpha_model;
+
+typedef enum rgs_precision {
+    RGS_FP32 = 0 /* plain FP32 SIMT bounces, one light per column tile */
+} rgs_precision;
+
+typedef struct rgs_scene rgs_scene;         /* opaque: surfels in Morton order + BVH */
+typedef struct rgs_transport rgs_transport; /* opaque: hit records, direct term, iterates */
+
+/* Surfel parameters, caller order, all device pointers (Sec. 3.1, Eq. G; Sec. 5.1, Eq. brdf):
+ *   p[N][3]   centre p_i                tu[N][3], tv[N][3]  tangent directions t^u, t^v
+ *   s[N][2]   scales (s^u, s^v) > 0     o[N]                opacity in [0, 1]
+ *   ad[N][3]  diffuse albedo a^d        k[N]                diffuse/specular blend k
+ *   as[N][3]  specular albedo a^s       shin[N]             Phong shininess s >= 0
+ * The normal is n = t^u x t^v after Gram-Schmidt orthonormalisation of (t^u, t^v). */
+typedef struct rgs_surfels {
+    int32_t n;         /* N >= 1 */
+    int32_t sh_degree; /* L in [0, RGS_MAX_SH_DEGREE] */
+    const float *p, *tu, *tv, *s, *o, *ad, *k, *as, *shin;
+} rgs_surfels;
+
+typedef struct rgs_build_opts {
+    int32_t alpha_model;  /* rgs_alpha_model */
+    int32_t check_finite; /* nonzero: reject NaN/Inf inputs with RGS_ERR_NONFINITE (synchronises) */
+} rgs_build_opts;
+
+/* Point lights (Sec. 5.1 "Lighting", Sec. 5.3): infinitesimal emitters sampled at their
+ * centre, isotropic, intensity I (RGB) so that the received radiance is I / r^2.
+ * Device pointers pos[NL][3], intensity[NL][3]; NL may be 0. */
+typedef struct rgs_lights {
+    int32_t n_lights;
+    const float *pos;
+    const float *intensity;
+} rgs_lights;
+
+typedef struct rgs_trace_opts {
+    int32_t nd;           /* hemisphere rays per surfel: multiple of 32 in [32, 4096] */
+    int32_t reserved0;
+    uint64_t seed;        /* jitter seed of the stratified directions */
+    int64_t hit_capacity; /* hit-record slots to reserve; 0 = automatic (grown on demand) */
+} rgs_trace_opts;
+
+typedef struct rgs_solve_stats {
+    int32_t n_bounces;
+    int32_t n_cols;
+    double residual_norm[RGS_MAX_BOUNCES]; /* FP64 ||B^(k) - B^(k-1)||_2 over all columns */
+    int64_t n_hits;          /* stored hemisphere hit records */
+    int64_t n_hit_slots;     /* reserved record slots actually used (with warp padding) */
+    int64_t n_full_rays;     /* rays whose hit buffer filled up (nearest hits kept) */
+} rgs_solve_stats;
+
+typedef struct rgs_transport_info {
+    int32_t n, sh_degree, nc, n_cols, nd, n_lights;
+    int64_t n_hits, n_hit_slots, n_full_rays;
+    int64_t device_bytes; /* device memory held by the transport handle */
+} rgs_transport_info;
+
+/* ---------------------------------------------------------------- entry points */
+
+/* Builds (or rebuilds in place) the scene: orthonormal frames and normals (Eq. G), the
+ * BRDF coefficients c_{i,l,ch} of the diffuse + Phong mixture (Eq. brdf; App. A: l = 0:
+ * 4 k a^d + (1-k) a^s, l >= 1: (1-k) a^s rho_l(s)), the Morton order of the centres and
+ * a BVH over the surfels' cutoff ellipses.
+ *   surfels : host struct of device pointers (read only during the call's GPU work).
+ *   opts    : host, may be NULL (Gaussian model, no finite check).
+ *   inout   : host; *inout == NULL creates a handle, otherwise the handle is rebuilt and
+ *             its buffers reused when large enough (no allocation in steady state).
+ * Asynchronous unless opts->check_finite is set.  Errors: RGS_ERR_ARG, RGS_ERR_OOM,
+ * RGS_ERR_CUDA, RGS_ERR_NONFINITE.  On error *inout keeps its previous value. */
+rgs_status rgs_build_scene(const rgs_surfels *surfels, const rgs_build_opts *opts, void *stream, rgs_scene **inout);
+
+/* Traces N * nd stratified cosine-weighted hemisphere rays from the surfel centres over
+ * their front hemispheres (App. B; weight pi/nd), alpha-composites the hits in depth order
+ * (Eq. L_I) and stores per-ray hit records (source surfel, compositing weight, Gaussian
+ * value); traces the N * NL shadow rays of the direct term (Sec. 5.2) and forms
+ * S = E + D (E added in rgs_solve).  Rays start at the surfel centre (kappa_i = Dirac),
+ * a surfel never hits itself (Sec. 5.1) nor planes within eps = 1e-5 * (bounding-box
+ * diagonal) of the ray origin; compositing stops once the transmittance drops below 1e-6.
+ *   scene  : built scene.  lights: host struct of device pointers (copied during the call).
+ *   opts   : host.  inout: as in rgs_build_scene.
+ * Synchronises `stream` (the record count decides the buffer size).  Errors: RGS_ERR_ARG,
+ * RGS_ERR_OOM, RGS_ERR_CUDA, RGS_ERR_CAPACITY (opts->hit_capacity too small). */
+rgs_status rgs_trace_transport(rgs_scene *scene, const rgs_lights *lights, const rgs_trace_opts *opts, void *stream,
+                               rgs_transport **inout);
+
+/* Runs B^(0) = S = E + D, B^(k) = S + K B^(k-1) for k = 1..n_bounces with
+ * (K B)_i = o_i c_i (x) sum_r (pi/nd) Y(R_i d_r) sum_h a_rh Y(-d_r)^T B_{j_h}
+ * (Eq. final-radiosity with the hemisphere integral taken by the traced rays;
+ * R_i d = 2 (n_i.d) n_i - d places the Phong lobe, Eq. sh-brdf) and keeps every
+ * iterate for rgs_adjoint.
+ *   E      : device [N][nc][3] emission coefficients, or NULL for zero emission.
+ *   B_out  : device [N][nc][C], receives B^(n_bounces).
+ *   stats  : host, may be NULL; if given, the stream is synchronised and the FP64
+ *            residual norms per bounce are written.
+ * Errors: RGS_ERR_ARG (n_bounces outside [0, RGS_MAX_BOUNCES], unknown precision),
+ * RGS_ERR_CUDA, RGS_ERR_OOM. */
+rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_t precision, float *B_out,
+                     rgs_solve_stats *stats, void *stream);
+
+/* Exact gradients of a loss L(B^(n)) for the last rgs_solve (the truncated series; the
+ * paper's Eq. final_dL_dE / final-dl-dbrdf are its n -> infinity limit):
+ *   v^(0) = dL/dB, v^(a) = K^T v^(a-1), u = sum_a v^(a) = dL/dS
+ *   dL/dE[i][k][ch]  = sum over lights of u                                 (device [N][nc][3])
+ *   dL/da^d[i][ch]   = 4 k_i o_i sum_{light} ( sum_a v^(a) Q^(n-1-a) + u Dgeo )_00  (device [N][3])
+ *   dL/do[i]         = receiver factor + backward through the compositing of every
+ *                      hemisphere and shadow ray that hits surfel i           (device [N])
+ * Each output may be NULL (not computed).  dL_dB: device [N][nc][C].
+ * Asynchronous.  Errors: RGS_ERR_STATE (no prior rgs_solve), RGS_ERR_ARG, RGS_ERR_CUDA. */
+rgs_status rgs_adjoint(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo, float *dL_dopacity,
+                       void *stream);
+
+/* Copies iterate B^(b) (0 <= b <= last n_bounces) of the last rgs_solve to the device
+ * array out [N][nc][C].  Asynchronous.  Errors: RGS_ERR_STATE, RGS_ERR_ARG, RGS_ERR_CUDA. */
+rgs_status rgs_get_iterate(rgs_transport *t, int32_t b, float *out, void *stream);
+
+/* Fills *info (host).  Synchronises nothing.  Errors: RGS_ERR_ARG. */
+rgs_status rgs_transport_info_get(const rgs_transport *t, rgs_transport_info *info);
+
+/* Release handles (NULL is accepted).  Synchronises the device. */
+void rgs_destroy_transport(rgs_transport *t);
+void rgs_destroy_scene(rgs_scene *s);
+
+/* ---------------------------------------------------------------- profiling
+ * Per-kernel timing for roofline reports.  While enabled, every kernel the library
+ * launches is bracketed by two CUDA events recorded on the stream it is launched on;
+ * rgs_profile_report synchronises those events and returns, per kernel name, the
+ * number of launches and their summed device time.  rgs_launch_count counts every
+ * kernel launched by the library since it was loaded (enabled or not). */
+typedef struct rgs_kernel_time {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} rgs_kernel_time;
+
+void rgs_profile_enable(int32_t on);
+void rgs_profile_reset(void);
+/* Writes up to max entries to out (host); returns the number of kernel names seen, or -1
+ * if an event could not be read (see rgs_last_error).  Synchronises on the events. */
+int32_t rgs_profile_report(rgs_kernel_time *out, int32_t max);
+int64_t rgs_launch_count(void);
+
+const char *rgs_status_string(rgs_status s);
+const char *rgs_last_error(void); /* thread-local message of the last failing call */
+int32_t rgs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RGS_H */

@@ -1,0 +1,85 @@
+"""Convenience layer over the C-ABI binding: upload a scene, run build -> trace -> solve
+-> adjoint, and a torch.autograd.Function differentiable in emission, diffuse albedo and
+opacity.  Every numerical step is a librgs.so kernel; this module only moves tensors.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import rgs
+
+SURFEL_KEYS = ("p", "tu", "tv", "s", "o", "ad", "k", "as_", "shin")
+
+
+def upload(sc, device="cuda"):
+    """numpy scene dict (scenes.py layout) -> dict of contiguous float32 CUDA tensors."""
+    out = {k: torch.as_tensor(np.ascontiguousarray(sc[k], dtype=np.float32), device=device) for k in SURFEL_KEYS}
+    out["light_pos"] = torch.as_tensor(np.ascontiguousarray(sc["light_pos"], np.float32).reshape(-1, 3), device=device)
+    out["light_I"] = torch.as_tensor(np.ascontiguousarray(sc["light_I"], np.float32).reshape(-1, 3), device=device)
+    out["E"] = None if sc.get("E") is None else torch.as_tensor(np.ascontiguousarray(sc["E"], np.float32), device=device)
+    for key in ("L", "nd", "nb", "seed", "n"):
+        out[key] = int(sc[key])
+    return out
+
+
+class Pipeline:
+    """Reusable handles for one scene shape: build, trace, solve and adjoint in sequence.
+    Handles (and their device workspaces) are reused across calls, so steady-state steps
+    allocate nothing inside the library."""
+
+    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS):
+        self.alpha_model = alpha_model
+        self.scene = None
+        self.transport = None
+
+    def build(self, d, stream=None):
+        self.scene = rgs.rgs_build_scene(*[d[k] for k in SURFEL_KEYS], sh_degree=d["L"],
+                                         alpha_model=self.alpha_model, stream=stream, scene=self.scene)
+        return self.scene
+
+    def trace(self, d, stream=None, hit_capacity=0):
+        self.transport = rgs.rgs_trace_transport(self.scene, d["light_pos"], d["light_I"], d["nd"], d["seed"],
+                                                 hit_capacity=hit_capacity, stream=stream,
+                                                 transport=self.transport)
+        return self.transport
+
+    def solve(self, E, nb, B_out=None, stats=False, stream=None):
+        return rgs.rgs_solve(self.transport, E, nb, B_out=B_out, stats=stats, stream=stream)
+
+    def adjoint(self, g, outs=(None, None, None), stream=None):
+        return rgs.rgs_adjoint(self.transport, g, *outs, stream=stream)
+
+    def step(self, d, g, B_out=None, grads=(None, None, None), stream=None):
+        """One full pass of the path: scene build, trace, n bounces, adjoint."""
+        self.build(d, stream)
+        self.trace(d, stream)
+        B, _ = self.solve(d["E"], d["nb"], B_out=B_out, stream=stream)
+        return B, self.adjoint(g, grads, stream=stream)
+
+
+class RadiositySolve(torch.autograd.Function):
+    """B = solve(E, a^d, o; geometry, lights) with gradients w.r.t. E, a^d and o.
+
+    forward rebuilds the scene from the given albedo/opacity, traces and runs n bounces;
+    backward runs rgs_adjoint (exact gradient of the truncated series)."""
+
+    @staticmethod
+    def forward(ctx, E, ad, o, geom, nb, alpha_model=rgs.RGS_ALPHA_GAUSS):
+        d = dict(geom)
+        d["ad"], d["o"] = ad.detach().contiguous(), o.detach().contiguous()
+        pipe = Pipeline(alpha_model)
+        pipe.build(d)
+        pipe.trace(d)
+        B, _ = pipe.solve(E.detach().contiguous() if E is not None else None, int(nb))
+        ctx.pipe = pipe
+        return B
+
+    @staticmethod
+    def backward(ctx, gB):
+        dE, dad, do = ctx.pipe.adjoint(gB.contiguous())
+        return dE, dad, do, None, None, None
+
+
+def radiosity(E, ad, o, geom, nb, alpha_model=rgs.RGS_ALPHA_GAUSS):
+    return RadiositySolve.apply(E, ad, o, geom, nb, alpha_model)

@@ -1,0 +1,370 @@
+// Internal definitions shared by the CUDA translation units of librgs (not part of the ABI).
+//
+// Data layout in HBM (all arrays in the library's internal Morton order of the surfels):
+//   P[j]  = (p.xyz, o)          N4[j] = (n.xyz, 0)
+//   FU[j] = (t^u.xyz, 1/s^u)    FV[j] = (t^v.xyz, 1/s^v)        64 B read per intersection test
+//   cl[j] = c_{j,l,ch} as [4][3] floats (bands beyond L are zero)
+//   uid[j] = caller index of internal surfel j (ray seeds and depth-tie order use it)
+//   radiosity-like arrays (S, B^(b), Q^(b), v^(a), u): [N][C][NC] float, SH index innermost
+//   hit records: warp-interleaved rows; ray r of warp w = r/32 stores hit h at
+//                warp_base[w] + h*32 + (r & 31): rec_ja = (source j, bits of a_rh), rec_g = G
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rgs.h"
+
+#define RGS_HMAX 128          // per-ray hit buffer; when full the nearest RGS_HMAX hits are kept
+#define RGS_T_EPS 1e-6f       // compositing stops once the transmittance is below this
+#define RGS_STACK 64          // BVH traversal stack depth (tree depth is bounded by 32 + log2 N)
+
+// ------------------------------------------------------------------ error flags
+enum {
+    FLAG_CAPACITY = 0,  // hit-record slots exhausted (warps that could not store)
+    FLAG_FULL_RAYS = 1, // rays whose RGS_HMAX buffer filled up
+    FLAG_STACK = 2,     // traversal stack overflow (the ray then misses the rest of the tree)
+    FLAG_NONFINITE = 3,
+    FLAG_COUNT = 8
+};
+
+// ------------------------------------------------------------------ BVH node
+// Internal node of a binary LBVH; stores both children's boxes. A child index c >= 0
+// is an internal node, c < 0 is the leaf (surfel) ~c.
+struct __align__(16) BvhNode {
+    float4 a; // l.lo.x l.lo.y l.lo.z l.hi.x
+    float4 b; // l.hi.y l.hi.z r.lo.x r.lo.y
+    float4 c; // r.lo.z r.hi.x r.hi.y r.hi.z
+    int4 d;   // left, right, 0, 0
+};
+
+struct SceneDev {
+    int n, L, alpha_model;
+    float cutoff2;
+    const float4 *P, *N4, *FU, *FV;
+    const float *cl; // [n][4][3]
+    const int *uid;
+    const BvhNode *nodes;
+    const float *eps_plane; // device scalar
+};
+
+struct RaysDev {
+    int nd, na, nbs; // rays per surfel, strata n_a x n_b
+    unsigned long long seed;
+    const int2 *rec_ja;
+    const float *rec_g;
+    const long long *warp_base;
+    const int *cnt;
+};
+
+// ------------------------------------------------------------------ small math
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 neg3(float3 a) { return make_float3(-a.x, -a.y, -a.z); }
+
+// mirror of d about the normal n: R d = 2 (n.d) n - d (places the Phong lobe, Eq. sh-brdf)
+__device__ __forceinline__ float3 reflect_n(float3 n, float3 d) {
+    float s = 2.f * dot3(n, d);
+    return make_float3(s * n.x - d.x, s * n.y - d.y, s * n.z - d.z);
+}
+
+// Real orthonormal SH up to degree 3, Condon-Shortley phase, index l*l + l + m,
+// as Cartesian polynomials of a unit vector.  Constants are the normalisations
+// K = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times sqrt(2) for m != 0, folded with
+// the polynomial's integer factors.
+template <int NC>
+__device__ __forceinline__ void sh_eval(float3 v, float *Y) {
+    const float x = v.x, y = v.y, z = v.z;
+    Y[0] = 0.28209479177387814f; // 1/(2 sqrt(pi))
+    if (NC > 1) {
+        const float c1 = 0.4886025119029199f; // sqrt(3/(4 pi))
+        Y[1] = -c1 * y;
+        Y[2] = c1 * z;
+        Y[3] = -c1 * x;
+    }
+    if (NC > 4) {
+        const float c21 = 1.0925484305920792f; // (1/2) sqrt(15/pi)
+        const float c20 = 0.31539156525252005f; // (1/4) sqrt(5/pi)
+        const float c22 = 0.5462742152960396f; // (1/4) sqrt(15/pi)
+        Y[4] = c21 * x * y;
+        Y[5] = -c21 * y * z;
+        Y[6] = c20 * (3.f * z * z - 1.f);
+        Y[7] = -c21 * x * z;
+        Y[8] = c22 * (x * x - y * y);
+    }
+    if (NC > 9) {
+        const float c33 = 0.5900435899266435f;  // (1/4) sqrt(35/(2 pi))
+        const float c32a = 2.890611442640554f;  // (1/2) sqrt(105/pi)
+        const float c31 = 0.4570457994644658f;  // (1/4) sqrt(21/(2 pi))
+        const float c30 = 0.3731763325901154f;  // (1/4) sqrt(7/pi)
+        const float c32b = 1.445305721320277f;  // (1/4) sqrt(105/pi)
+        const float zz5 = 5.f * z * z;
+        Y[9] = -c33 * y * (3.f * x * x - y * y);
+        Y[10] = c32a * x * y * z;
+        Y[11] = -c31 * y * (zz5 - 1.f);
+        Y[12] = c30 * z * (zz5 - 3.f);
+        Y[13] = -c31 * x * (zz5 - 1.f);
+        Y[14] = c32b * z * (x * x - y * y);
+        Y[15] = -c33 * x * (x * x - 3.f * y * y);
+    }
+}
+
+__host__ __device__ constexpr int band_of(int k) { return k == 0 ? 0 : (k < 4 ? 1 : (k < 9 ? 2 : 3)); }
+
+// ------------------------------------------------------------------ ray generation
+// SplitMix64 output function (Steele, Lea & Flood 2014) applied to a counter.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// 24-bit uniform in [0,1); key = ((seed*2^32 + i)*2^12 + r)*2 + dim (exact in float)
+__device__ __forceinline__ float jitter(unsigned long long seed, unsigned i, unsigned r, unsigned dim) {
+    unsigned long long key = ((((seed << 32) + (unsigned long long)i) << 12) + (unsigned long long)r) * 2ull + dim;
+    return (float)(unsigned)(splitmix64(key) >> 40) * (1.0f / 16777216.0f);
+}
+
+// Ray q of a surfel with caller index uid and frame (tu, tv, n): stratified cosine-weighted
+// direction on the front hemisphere (App. B, Omega = {w_I . n < 0}); weight pi/nd.
+__device__ __forceinline__ float3 ray_dir(unsigned long long seed, int uid, int q, int na, int nbs, float3 tu, float3 tv,
+                                          float3 n) {
+    int a = q / nbs, b = q - a * nbs;
+    float u1 = ((float)a + jitter(seed, (unsigned)uid, (unsigned)q, 0u)) / (float)na;
+    float u2 = ((float)b + jitter(seed, (unsigned)uid, (unsigned)q, 1u)) / (float)nbs;
+    float rr = sqrtf(u1), cz = sqrtf(fmaxf(0.f, 1.f - u1));
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    return (rr * cs) * tu + (rr * sn) * tv + cz * n;
+}
+
+// ------------------------------------------------------------------ intersection
+// Ray o + t d against the plane of surfel j (Eq. G). Returns true with t and G when the
+// hit is accepted: j != self, |n_j.(p_j - o)| > eps, 0 < t < tmax, inside the cutoff.
+__device__ __forceinline__ bool hit_surfel(const SceneDev &sc, int j, int self, float3 o, float3 d, float tmax,
+                                           float eps, float &t_out, float &g_out) {
+    if (j == self) return false;
+    const float4 Nj = __ldg(&sc.N4[j]);
+    const float den = Nj.x * d.x + Nj.y * d.y + Nj.z * d.z;
+    if (fabsf(den) < 1e-12f) return false;
+    const float4 Pj = __ldg(&sc.P[j]);
+    const float3 w = make_float3(Pj.x - o.x, Pj.y - o.y, Pj.z - o.z);
+    const float h = Nj.x * w.x + Nj.y * w.y + Nj.z * w.z;
+    if (fabsf(h) <= eps) return false;
+    const float t = h / den;
+    if (!(t > 0.f) || !(t < tmax)) return false;
+    const float3 q = make_float3(t * d.x - w.x, t * d.y - w.y, t * d.z - w.z); // x - p_j
+    const float4 U = __ldg(&sc.FU[j]);
+    const float4 V = __ldg(&sc.FV[j]);
+    const float u = (q.x * U.x + q.y * U.y + q.z * U.z) * U.w;
+    const float v = (q.x * V.x + q.y * V.y + q.z * V.z) * V.w;
+    const float r2 = u * u + v * v;
+    if (r2 > sc.cutoff2) return false;
+    t_out = t;
+    g_out = (sc.alpha_model == RGS_ALPHA_DISC) ? 1.f : expf(-0.5f * r2);
+    return true;
+}
+
+// slab test of the box [lo, hi] against the segment (0, tmax); NaNs from 0*inf are ignored
+__device__ __forceinline__ bool slab(float lox, float loy, float loz, float hix, float hiy, float hiz, float3 o,
+                                     float3 inv, float tmax) {
+    float tx0 = (lox - o.x) * inv.x, tx1 = (hix - o.x) * inv.x;
+    float ty0 = (loy - o.y) * inv.y, ty1 = (hiy - o.y) * inv.y;
+    float tz0 = (loz - o.z) * inv.z, tz1 = (hiz - o.z) * inv.z;
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmx = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    return tmin <= tmx;
+}
+
+// Visits every surfel whose box the segment (0, tmax) crosses and calls f(j).
+// Returns false if the stack overflowed (then part of the tree was skipped).
+template <class F>
+__device__ __forceinline__ bool bvh_traverse(const SceneDev &sc, float3 o, float3 d, float tmax, F &&f) {
+    if (sc.n == 1) {
+        f(0);
+        return true;
+    }
+    const float3 inv = make_float3(1.f / d.x, 1.f / d.y, 1.f / d.z);
+    int stack[RGS_STACK];
+    int sp = 0;
+    int node = 0;
+    bool ok = true;
+    while (true) {
+        const BvhNode nd = sc.nodes[node];
+        const int cl = nd.d.x, cr = nd.d.y;
+        bool hl = slab(nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y, o, inv, tmax);
+        bool hr = slab(nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w, o, inv, tmax);
+        if (hl && cl < 0) {
+            f(~cl);
+            hl = false;
+        }
+        if (hr && cr < 0) {
+            f(~cr);
+            hr = false;
+        }
+        if (hl && hr) {
+            if (sp < RGS_STACK) stack[sp++] = cr;
+            else ok = false;
+            node = cl;
+        } else if (hl) {
+            node = cl;
+        } else if (hr) {
+            node = cr;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    return ok;
+}
+
+// ------------------------------------------------------------------ host-side handles
+struct rgs_scene {
+    int device = 0;
+    int n = 0, cap = 0, L = 0, nc = 1, alpha_model = 0;
+    float4 *P = nullptr, *N4 = nullptr, *FU = nullptr, *FV = nullptr;
+    float *cl = nullptr, *kk = nullptr;
+    int *uid = nullptr, *inv = nullptr;
+    BvhNode *nodes = nullptr;
+    float *boxes = nullptr; // [2n-1][6]
+    int *parent = nullptr, *visit = nullptr;
+    unsigned *keys = nullptr, *keys_alt = nullptr;
+    int *vals = nullptr, *vals_alt = nullptr;
+    int *hist = nullptr;
+    int hist_cap = 0;
+    int *bounds = nullptr; // 6 ordered ints
+    float *eps_plane = nullptr;
+    int *flags = nullptr;
+    SceneDev dev() const {
+        SceneDev s;
+        s.n = n;
+        s.L = L;
+        s.alpha_model = alpha_model;
+        s.cutoff2 = (alpha_model == RGS_ALPHA_DISC) ? 1.f : 9.f;
+        s.P = P;
+        s.N4 = N4;
+        s.FU = FU;
+        s.FV = FV;
+        s.cl = cl;
+        s.uid = uid;
+        s.nodes = nodes;
+        s.eps_plane = eps_plane;
+        return s;
+    }
+};
+
+struct rgs_transport {
+    rgs_scene *sc = nullptr;
+    int n = 0, L = 0, nc = 1;
+    int nd = 0, na = 1, nbs = 1;
+    unsigned long long seed = 0;
+    int nl = 0, C = 3;
+    float *lpos = nullptr, *lint = nullptr;
+    int lcap = 0;
+    // hemisphere hit records
+    long long cap_slots = 0;
+    int2 *rec_ja = nullptr;
+    float *rec_g = nullptr;
+    long long *warp_base = nullptr;
+    int *cnt = nullptr;
+    long long rays_cap = 0;
+    unsigned long long *counter = nullptr;
+    int *flags = nullptr;
+    long long n_hits = 0, n_slots = 0, n_full = 0;
+    // transposed index (records grouped by source surfel)
+    long long *src_off = nullptr;
+    int *src_cnt = nullptr;
+    unsigned long long *cursor = nullptr;
+    int2 *tr = nullptr; // (ray id, bits of a)
+    long long tr_cap = 0; // entries allocated in tr
+    int src_cap = 0;      // surfels allocated in src_off / src_cnt / cursor
+    long long *scan_tmp = nullptr;
+    int scan_tmp_cap = 0;
+    // direct term D [N][C][NC]
+    float *D = nullptr;
+    long long nc_cap = 0; // capacity (floats) of one [N][C][NC] array
+    // iterates
+    int nb_last = -1;
+    int iters_cap = 0;  // number of [N][C][NC] arrays allocated in iters / Q
+    float *iters = nullptr; // B^(0..nb)
+    float *Q = nullptr;     // Q^(0..nb-1)
+    double *norm2 = nullptr; // [RGS_MAX_BOUNCES + 1]
+    // adjoint workspace
+    float *v = nullptr; // v^(0..nb)
+    int v_cap = 0;
+    float *u = nullptr;
+    float *Pg = nullptr;  // [N][4][3]
+    float *dop = nullptr; // [N]
+    int pg_cap = 0;       // surfels allocated in Pg / dop
+    long long device_bytes = 0;
+    RaysDev rays() const {
+        RaysDev r;
+        r.nd = nd;
+        r.na = na;
+        r.nbs = nbs;
+        r.seed = seed;
+        r.rec_ja = rec_ja;
+        r.rec_g = rec_g;
+        r.warp_base = warp_base;
+        r.cnt = cnt;
+        return r;
+    }
+    size_t arr() const { return (size_t)n * C * nc; }
+};
+
+// ------------------------------------------------------------------ host helpers (rgs_api.cu)
+// Brackets exactly one kernel launch: counts it and, while profiling is enabled, records
+// CUDA events before and after it on its stream (rgs_profile_report reads them).
+struct ProfScope {
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+    int rec = -1;
+    cudaStream_t st;
+};
+void rgs_set_error(const char *fmt, ...);
+rgs_status rgs_cuda_fail(cudaError_t e, const char *what);
+#define RGS_CUDA(call)                                                                                                 \
+    do {                                                                                                               \
+        cudaError_t e_ = (call);                                                                                       \
+        if (e_ != cudaSuccess) return rgs_cuda_fail(e_, #call);                                                        \
+    } while (0)
+#define RGS_LAUNCH(what)                                                                                               \
+    do {                                                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                                                           \
+        if (e_ != cudaSuccess) return rgs_cuda_fail(e_, what);                                                         \
+    } while (0)
+
+template <class T>
+rgs_status dev_alloc(T **p, size_t count, long long *acct = nullptr) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        rgs_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return RGS_ERR_OOM;
+    }
+    if (acct) *acct += (long long)(count * sizeof(T));
+    return RGS_OK;
+}
+template <class T> void dev_free(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// entry points implemented per translation unit
+rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_build_opts *o, cudaStream_t st);
+rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace_opts *o, cudaStream_t st);
+rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, float *B_out, rgs_solve_stats *stats,
+                          cudaStream_t st);
+rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st);
+rgs_status rgs_get_iterate_impl(rgs_transport *t, int b, float *out, cudaStream_t st);
+// device-wide exclusive scan of int counts into int64 offsets (offsets[n] = total)
+rgs_status rgs_scan_counts(const int *cnt, long long *off, int n, long long *tmp, int tmp_cap, cudaStream_t st);
+int rgs_scan_tmp_size(int n);

@@ -1,0 +1,206 @@
+// Bounce iteration (rgs_solve): B^(0) = S = E + D, B^(k) = S + K B^(k-1).
+//
+// k_bounce is the gather/projection of Eq. final-radiosity in its ray-factored form:
+// one CTA per receiver i and column tile; each thread owns rays of i and, per ray,
+// gathers the stored hits' radiance x_r[c] = sum_h a_rh Y(-d_r) . B_{j_h}[c]; the CTA then
+// projects Q_i[c][k] = (pi/nd) sum_r Y_k(R_i d_r) x_r[c] and writes Q^(k-1),
+// B^(k) = S + o_i c_i (x) Q and the FP64 partial sum of (B^(k) - B^(k-1))^2.
+#include "rgs_internal.cuh"
+
+namespace {
+
+constexpr int BOUNCE_THREADS = 128;
+
+// internal [N][C][NC] <- user [N][nc][3] emission broadcast over the columns, plus D
+template <int NC>
+__global__ void k_make_S(int n, int C, const int *__restrict__ uid, const float *__restrict__ E,
+                         const float *__restrict__ D, float *S) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * C * NC) return;
+    const int k = (int)(idx % NC);
+    const size_t ic = idx / NC;
+    const int c = (int)(ic % C);
+    const int i = (int)(ic / C);
+    float e = E ? E[((size_t)uid[i] * NC + k) * 3 + (c % 3)] : 0.f;
+    S[idx] = e + D[idx];
+}
+
+// internal [N][C][NC] -> user [N][nc][C]
+template <int NC>
+__global__ void k_to_user(int n, int C, const int *__restrict__ uid, const float *__restrict__ X, float *Y) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * C * NC) return;
+    const int k = (int)(idx % NC);
+    const size_t ic = idx / NC;
+    const int c = (int)(ic % C);
+    const int i = (int)(ic / C);
+    Y[((size_t)uid[i] * NC + k) * C + c] = X[idx];
+}
+
+template <int NC, int CT>
+__global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev rays, int C, const float *__restrict__ Bin,
+                                                          const float *__restrict__ S, float *__restrict__ Qout,
+                                                          float *__restrict__ Bout, double *norm2) {
+    const int i = blockIdx.x;
+    const int col0 = blockIdx.y * CT;
+    const int nd = rays.nd;
+    const float3 tu = f3(sc.FU[i]), tv = f3(sc.FV[i]), n = f3(sc.N4[i]);
+    const int uid = sc.uid[i];
+    float acc[NC][CT];
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[k][c] = 0.f;
+
+    for (int q = threadIdx.x; q < nd; q += BOUNCE_THREADS) {
+        const float3 d = ray_dir(rays.seed, uid, q, rays.na, rays.nbs, tu, tv, n);
+        float Yo[NC], Yi[NC];
+        sh_eval<NC>(neg3(d), Yo);
+        sh_eval<NC>(reflect_n(n, d), Yi);
+        const long long r = (long long)i * nd + q;
+        const int cnt = rays.cnt[r];
+        const long long base = rays.warp_base[r >> 5] + (r & 31);
+        float x[CT];
+#pragma unroll
+        for (int c = 0; c < CT; ++c) x[c] = 0.f;
+        for (int h = 0; h < cnt; ++h) {
+            const int2 ja = __ldg(&rays.rec_ja[base + (long long)h * 32]);
+            const float a = __int_as_float(ja.y);
+            const float *Bj = Bin + ((size_t)ja.x * C + col0) * NC;
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s += Yo[k] * __ldg(&Bj[c * NC + k]);
+                x[c] += a * s;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[k][c] += Yi[k] * x[c];
+    }
+    // CTA reduction of acc
+    __shared__ float red[BOUNCE_THREADS / 32][NC * CT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            float v = acc[k][c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) red[warp][k * CT + c] = v;
+        }
+    __syncthreads();
+    double dsq = 0.0;
+    const float w = 3.14159265358979f / (float)nd;
+    for (int e = threadIdx.x; e < NC * CT; e += BOUNCE_THREADS) {
+        float v = 0.f;
+        for (int q = 0; q < BOUNCE_THREADS / 32; ++q) v += red[q][e];
+        const int k = e / CT, c = e - k * CT;
+        const int col = col0 + c;
+        const float Q = w * v;
+        const size_t idx = ((size_t)i * C + col) * NC + k;
+        Qout[idx] = Q;
+        const float oc = sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (col % 3)];
+        const float b = S[idx] + oc * Q;
+        Bout[idx] = b;
+        const double df = (double)b - (double)Bin[idx];
+        dsq += df * df;
+    }
+    // FP64 residual norm: warp reduce, one atomic per warp with work
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dsq += __shfl_xor_sync(0xffffffffu, dsq, off);
+    if (lane == 0 && warp * 32 < NC * CT) atomicAdd(norm2, dsq);
+}
+
+template <int NC>
+rgs_status launch_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, const float *Bin, const float *S, float *Q,
+                         float *Bout, double *norm2, cudaStream_t st) {
+    dim3 grid(t->n, t->C / 3);
+    { ProfScope ps_("k_bounce", st); k_bounce<NC, 3><<<grid, BOUNCE_THREADS, 0, st>>>(sd, rd, t->C, Bin, S, Q, Bout, norm2); }
+    RGS_LAUNCH("bounce");
+    return RGS_OK;
+}
+
+template <int NC>
+void launch_make_S(const rgs_transport *t, const float *E, float *S, cudaStream_t st) {
+    size_t tot = t->arr();
+    { ProfScope ps_("k_make_S", st); k_make_S<NC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t->n, t->C, t->sc->uid, E, t->D, S); }
+}
+template <int NC>
+void launch_to_user(const rgs_transport *t, const float *X, float *Y, cudaStream_t st) {
+    size_t tot = t->arr();
+    { ProfScope ps_("k_to_user", st); k_to_user<NC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t->n, t->C, t->sc->uid, X, Y); }
+}
+
+} // namespace
+
+rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, float *B_out, rgs_solve_stats *stats,
+                          cudaStream_t st) {
+    rgs_status r;
+    const size_t A = t->arr();
+    if (nb + 1 > t->iters_cap) {
+        if ((r = dev_alloc(&t->iters, A * (nb + 1), &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->Q, A * (nb > 0 ? nb : 1), &t->device_bytes)) != RGS_OK) return r;
+        t->iters_cap = nb + 1;
+    }
+    if (!t->norm2 && (r = dev_alloc(&t->norm2, RGS_MAX_BOUNCES + 1, &t->device_bytes)) != RGS_OK) return r;
+    RGS_CUDA(cudaMemsetAsync(t->norm2, 0, sizeof(double) * (RGS_MAX_BOUNCES + 1), st));
+    SceneDev sd = t->sc->dev();
+    RaysDev rd = t->rays();
+    switch (t->nc) {
+    case 1: launch_make_S<1>(t, E, t->iters, st); break;
+    case 4: launch_make_S<4>(t, E, t->iters, st); break;
+    case 9: launch_make_S<9>(t, E, t->iters, st); break;
+    default: launch_make_S<16>(t, E, t->iters, st);
+    }
+    RGS_LAUNCH("make_S");
+    for (int b = 1; b <= nb; ++b) {
+        const float *Bin = t->iters + A * (b - 1);
+        float *Bout = t->iters + A * b;
+        float *Q = t->Q + A * (b - 1);
+        switch (t->nc) {
+        case 1: r = launch_bounce<1>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st); break;
+        case 4: r = launch_bounce<4>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st); break;
+        case 9: r = launch_bounce<9>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st); break;
+        default: r = launch_bounce<16>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st);
+        }
+        if (r != RGS_OK) return r;
+    }
+    t->nb_last = nb;
+    if (B_out) {
+        switch (t->nc) {
+        case 1: launch_to_user<1>(t, t->iters + A * nb, B_out, st); break;
+        case 4: launch_to_user<4>(t, t->iters + A * nb, B_out, st); break;
+        case 9: launch_to_user<9>(t, t->iters + A * nb, B_out, st); break;
+        default: launch_to_user<16>(t, t->iters + A * nb, B_out, st);
+        }
+        RGS_LAUNCH("to_user");
+    }
+    if (stats) {
+        double nrm[RGS_MAX_BOUNCES + 1];
+        RGS_CUDA(cudaMemcpyAsync(nrm, t->norm2, sizeof nrm, cudaMemcpyDeviceToHost, st));
+        RGS_CUDA(cudaStreamSynchronize(st));
+        stats->n_bounces = nb;
+        stats->n_cols = t->C;
+        for (int b = 0; b < RGS_MAX_BOUNCES; ++b) stats->residual_norm[b] = (b < nb) ? sqrt(nrm[b + 1]) : 0.0;
+        stats->n_hits = t->n_hits;
+        stats->n_hit_slots = t->n_slots;
+        stats->n_full_rays = t->n_full;
+    }
+    return RGS_OK;
+}
+
+rgs_status rgs_get_iterate_impl(rgs_transport *t, int b, float *out, cudaStream_t st) {
+    const size_t A = t->arr();
+    switch (t->nc) {
+    case 1: launch_to_user<1>(t, t->iters + A * b, out, st); break;
+    case 4: launch_to_user<4>(t, t->iters + A * b, out, st); break;
+    case 9: launch_to_user<9>(t, t->iters + A * b, out, st); break;
+    default: launch_to_user<16>(t, t->iters + A * b, out, st);
+    }
+    RGS_LAUNCH("get_iterate");
+    return RGS_OK;
+}

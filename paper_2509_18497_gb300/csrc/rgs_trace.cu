@@ -1,0 +1,303 @@
+// Transport tracing (rgs_trace_transport).
+//
+//  k_trace_hemi : one thread per hemisphere ray (App. B); a warp is 32 consecutive rays
+//                 of one surfel.  Hits are collected during BVH traversal, put in depth
+//                 order (near-equal depths by caller index), alpha-composited (Eq. L_I)
+//                 and stored as warp-interleaved records (coalesced 256-B rows).
+//  k_direct     : one thread per (surfel, light) shadow ray; transmittance product and
+//                 the direct term D (Sec. 5.2) for every column of that light.
+//  k_src_*      : the same records grouped by source surfel (transposed index) for the
+//                 adjoint's gather form of K^T.
+#include "rgs_internal.cuh"
+
+namespace {
+
+__global__ void __launch_bounds__(128) k_trace_hemi(SceneDev sc, RaysDev rays, int n_rays, long long cap_slots,
+                                                    unsigned long long *counter, int2 *rec_ja, float *rec_g,
+                                                    long long *warp_base, int *cnt_out, int *flags) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps only (n_rays % 32 == 0)
+    const int lane = threadIdx.x & 31;
+    const int i = r / rays.nd, q = r - i * rays.nd;
+    const float4 Pi = sc.P[i];
+    const float3 o = f3(Pi);
+    const float3 d = ray_dir(rays.seed, sc.uid[i], q, rays.na, rays.nbs, f3(sc.FU[i]), f3(sc.FV[i]), f3(sc.N4[i]));
+    const float eps = *sc.eps_plane;
+
+    float ht[RGS_HMAX];
+    int hj[RGS_HMAX];
+    float hg[RGS_HMAX];
+    int H = 0;
+    bool full = false;
+    auto visit = [&](int j) {
+        float t, g;
+        if (!hit_surfel(sc, j, i, o, d, INFINITY, eps, t, g)) return;
+        if (H < RGS_HMAX) {
+            ht[H] = t;
+            hj[H] = j;
+            hg[H] = g;
+            ++H;
+            return;
+        }
+        full = true; // keep the RGS_HMAX nearest: replace the farthest if this one is nearer
+        int far = 0;
+        for (int m = 1; m < RGS_HMAX; ++m)
+            if (ht[m] > ht[far]) far = m;
+        if (t < ht[far]) {
+            ht[far] = t;
+            hj[far] = j;
+            hg[far] = g;
+        }
+    };
+    bool ok = bvh_traverse(sc, o, d, INFINITY, visit);
+    if (!ok) atomicAdd(&flags[FLAG_STACK], 1);
+    if (full) atomicAdd(&flags[FLAG_FULL_RAYS], 1);
+
+    // depth order with caller-index tie break, then runs of near-equal depth by caller index
+    for (int a = 1; a < H; ++a) {
+        float t = ht[a];
+        int j = hj[a];
+        float g = hg[a];
+        int uj = sc.uid[j];
+        int b = a - 1;
+        while (b >= 0 && (ht[b] > t || (ht[b] == t && sc.uid[hj[b]] > uj))) {
+            ht[b + 1] = ht[b];
+            hj[b + 1] = hj[b];
+            hg[b + 1] = hg[b];
+            --b;
+        }
+        ht[b + 1] = t;
+        hj[b + 1] = j;
+        hg[b + 1] = g;
+    }
+    for (int k = 0; k < H;) {
+        int e = k;
+        while (e + 1 < H && ht[e + 1] - ht[e] <= 1e-6f * fmaxf(1.f, ht[e])) ++e;
+        for (int a = k + 1; a <= e; ++a) { // insertion sort of the run by caller index
+            int j = hj[a];
+            float g = hg[a];
+            int uj = sc.uid[j];
+            int b = a - 1;
+            while (b >= k && sc.uid[hj[b]] > uj) {
+                hj[b + 1] = hj[b];
+                hg[b + 1] = hg[b];
+                --b;
+            }
+            hj[b + 1] = j;
+            hg[b + 1] = g;
+        }
+        k = e + 1;
+    }
+    // composite: a_h = alpha_h prod_{k<h} (1 - alpha_k); stop below RGS_T_EPS
+    float T = 1.f;
+    int kept = 0;
+    for (; kept < H; ++kept) {
+        if (T < RGS_T_EPS) break;
+        const float alpha = __ldg(&sc.P[hj[kept]].w) * hg[kept];
+        ht[kept] = alpha * T; // reuse ht for the weights
+        T *= (1.f - alpha);
+    }
+    // warp allocation of kept-count rows
+    int rows = __reduce_max_sync(0xffffffffu, kept);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, (unsigned long long)rows * 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const bool fits = base + (unsigned long long)rows * 32ull <= (unsigned long long)cap_slots;
+    if (lane == 0) {
+        warp_base[r >> 5] = (long long)base;
+        if (!fits) atomicAdd(&flags[FLAG_CAPACITY], 1);
+    }
+    cnt_out[r] = fits ? kept : 0;
+    if (!fits) return;
+    for (int h = 0; h < kept; ++h) {
+        size_t s = base + (size_t)h * 32 + lane;
+        rec_ja[s] = make_int2(hj[h], __float_as_int(ht[h]));
+        rec_g[s] = hg[h];
+    }
+}
+
+// Direct term (Sec. 5.2): D_i[L*3+ch][k] = o_i c_{i,l(k),ch} Y_k(R_i w) I_{L,ch} (n_i.w)/r^2 T
+template <int NC>
+__global__ void k_direct(SceneDev sc, int nl, const float *__restrict__ lpos, const float *__restrict__ lint, int C,
+                         float *D, int *flags) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= sc.n * nl) return;
+    const int i = tid / nl, lt = tid - i * nl;
+    const float4 Pi = sc.P[i];
+    const float3 o = f3(Pi), n = f3(sc.N4[i]);
+    const float3 l = make_float3(lpos[3 * lt] - o.x, lpos[3 * lt + 1] - o.y, lpos[3 * lt + 2] - o.z);
+    const float r = sqrtf(dot3(l, l));
+    const float3 w = (1.f / r) * l;
+    const float cs = dot3(n, w);
+    float *Dout = D + ((size_t)i * C + lt * 3) * NC;
+    if (!(cs > 0.f)) {
+        for (int q = 0; q < 3 * NC; ++q) Dout[q] = 0.f;
+        return;
+    }
+    const float eps = *sc.eps_plane;
+    float T = 1.f;
+    auto visit = [&](int j) {
+        float t, g;
+        if (hit_surfel(sc, j, i, o, w, r, eps, t, g)) T *= 1.f - __ldg(&sc.P[j].w) * g;
+    };
+    if (!bvh_traverse(sc, o, w, r, visit)) atomicAdd(&flags[FLAG_STACK], 1);
+    float Y[NC];
+    sh_eval<NC>(reflect_n(n, w), Y);
+    const float pre = Pi.w * cs / (r * r) * T;
+    for (int ch = 0; ch < 3; ++ch) {
+        const float I = lint[3 * lt + ch];
+        for (int k = 0; k < NC; ++k) Dout[ch * NC + k] = sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch] * Y[k] * I * pre;
+    }
+}
+
+__global__ void k_src_count(RaysDev rays, int n_rays, int *src_cnt) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const long long base = rays.warp_base[r >> 5];
+    const int c = rays.cnt[r], lane = r & 31;
+    for (int h = 0; h < c; ++h) atomicAdd(&src_cnt[rays.rec_ja[base + (long long)h * 32 + lane].x], 1);
+}
+
+__global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const long long base = rays.warp_base[r >> 5];
+    const int c = rays.cnt[r], lane = r & 31;
+    for (int h = 0; h < c; ++h) {
+        const int2 ja = rays.rec_ja[base + (long long)h * 32 + lane];
+        const unsigned long long pos = atomicAdd(&cursor[ja.x], 1ull);
+        tr[pos] = make_int2(r, ja.y);
+    }
+}
+
+__global__ void k_copy_off(const long long *off, unsigned long long *cursor, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cursor[i] = (unsigned long long)off[i];
+}
+
+} // namespace
+
+static int strata_a(int nd) {
+    int na = 1;
+    while ((2 * na) * (2 * na) <= nd) na *= 2;
+    return na;
+}
+
+rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace_opts *o, cudaStream_t st) {
+    rgs_scene *sc = t->sc;
+    const int n = sc->n;
+    t->n = n;
+    t->L = sc->L;
+    t->nc = sc->nc;
+    t->nd = o->nd;
+    t->na = strata_a(o->nd);
+    t->nbs = o->nd / t->na;
+    t->seed = o->seed;
+    t->nl = L ? L->n_lights : 0;
+    t->C = 3 * (t->nl > 0 ? t->nl : 1);
+    t->nb_last = -1;
+    rgs_status r;
+    const long long n_rays = (long long)n * o->nd;
+    // lights (device copies)
+    if (t->nl > t->lcap) {
+        if ((r = dev_alloc(&t->lpos, 3 * (size_t)t->nl, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->lint, 3 * (size_t)t->nl, &t->device_bytes)) != RGS_OK) return r;
+        t->lcap = t->nl;
+    }
+    if (t->nl > 0) {
+        RGS_CUDA(cudaMemcpyAsync(t->lpos, L->pos, sizeof(float) * 3 * t->nl, cudaMemcpyDeviceToDevice, st));
+        RGS_CUDA(cudaMemcpyAsync(t->lint, L->intensity, sizeof(float) * 3 * t->nl, cudaMemcpyDeviceToDevice, st));
+    }
+    // per-ray / per-surfel arrays
+    if (n_rays > t->rays_cap) {
+        if ((r = dev_alloc(&t->cnt, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->warp_base, (size_t)(n_rays / 32), &t->device_bytes)) != RGS_OK) return r;
+        t->rays_cap = n_rays;
+    }
+    if (!t->counter && (r = dev_alloc(&t->counter, 1, &t->device_bytes)) != RGS_OK) return r;
+    if (!t->flags && (r = dev_alloc(&t->flags, FLAG_COUNT, &t->device_bytes)) != RGS_OK) return r;
+    const long long arr = (long long)n * t->C * t->nc;
+    if (arr > t->nc_cap) {
+        if ((r = dev_alloc(&t->D, (size_t)arr, &t->device_bytes)) != RGS_OK) return r;
+        t->nc_cap = arr;
+        t->iters_cap = 0; // iterate buffers are sized by the array size: force regrowth
+        t->v_cap = 0;
+    }
+    if (n > t->src_cap) {
+        if ((r = dev_alloc(&t->src_off, (size_t)n + 1, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->src_cnt, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->cursor, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
+        t->scan_tmp_cap = rgs_scan_tmp_size(n);
+        if ((r = dev_alloc(&t->scan_tmp, (size_t)t->scan_tmp_cap, &t->device_bytes)) != RGS_OK) return r;
+        t->src_cap = n;
+    }
+
+    long long want = o->hit_capacity > 0 ? o->hit_capacity : (t->cap_slots > 0 ? t->cap_slots : n_rays * 24);
+    SceneDev sd = sc->dev();
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (want > t->cap_slots) {
+            if ((r = dev_alloc(&t->rec_ja, (size_t)want, &t->device_bytes)) != RGS_OK) return r;
+            if ((r = dev_alloc(&t->rec_g, (size_t)want, &t->device_bytes)) != RGS_OK) return r;
+            t->cap_slots = want;
+        }
+        RGS_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
+        RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));
+        RaysDev rd = t->rays();
+        const int TB = 128;
+        { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter,
+                                                                        t->rec_ja, t->rec_g, t->warp_base, t->cnt,
+                                                                        t->flags); }
+        RGS_LAUNCH("trace_hemi");
+        unsigned long long used = 0;
+        int flags[FLAG_COUNT];
+        RGS_CUDA(cudaMemcpyAsync(&used, t->counter, sizeof used, cudaMemcpyDeviceToHost, st));
+        RGS_CUDA(cudaMemcpyAsync(flags, t->flags, sizeof flags, cudaMemcpyDeviceToHost, st));
+        RGS_CUDA(cudaStreamSynchronize(st));
+        t->n_slots = (long long)used;
+        t->n_full = flags[FLAG_FULL_RAYS];
+        if (flags[FLAG_STACK]) {
+            rgs_set_error("BVH traversal stack overflow on %d rays", flags[FLAG_STACK]);
+            return RGS_ERR_CAPACITY;
+        }
+        if (!flags[FLAG_CAPACITY]) break;
+        if (o->hit_capacity > 0 || attempt == 1) {
+            rgs_set_error("hit-record capacity %lld slots too small (%llu needed)", t->cap_slots, used);
+            return RGS_ERR_CAPACITY;
+        }
+        want = (long long)(used + used / 8 + 1024);
+    }
+
+    // direct term
+    if (t->nl > 0) {
+        const int nth = n * t->nl;
+        switch (t->nc) {
+        case 1: { ProfScope ps_("k_direct", st); k_direct<1><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        case 4: { ProfScope ps_("k_direct", st); k_direct<4><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        case 9: { ProfScope ps_("k_direct", st); k_direct<9><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        default: { ProfScope ps_("k_direct", st); k_direct<16><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); }
+        }
+        RGS_LAUNCH("direct");
+    } else {
+        RGS_CUDA(cudaMemsetAsync(t->D, 0, sizeof(float) * (size_t)arr, st));
+    }
+
+    // transposed index: records grouped by source surfel
+    RaysDev rd = t->rays();
+    RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
+    { ProfScope ps_("k_src_count", st); k_src_count<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->src_cnt); }
+    RGS_LAUNCH("src_count");
+    if ((r = rgs_scan_counts(t->src_cnt, t->src_off, n, t->scan_tmp, t->scan_tmp_cap, st)) != RGS_OK) return r;
+    long long total = 0;
+    RGS_CUDA(cudaMemcpyAsync(&total, t->src_off + n, sizeof total, cudaMemcpyDeviceToHost, st));
+    RGS_CUDA(cudaStreamSynchronize(st));
+    t->n_hits = total;
+    if (total > t->tr_cap) {
+        const long long want_tr = total + total / 8 + 1024;
+        if ((r = dev_alloc(&t->tr, (size_t)want_tr, &t->device_bytes)) != RGS_OK) return r;
+        t->tr_cap = want_tr;
+    }
+    { ProfScope ps_("k_copy_off", st); k_copy_off<<<(n + 255) / 256, 256, 0, st>>>(t->src_off, t->cursor, n); }
+    { ProfScope ps_("k_src_fill", st); k_src_fill<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->cursor, t->tr); }
+    RGS_LAUNCH("src_fill");
+    return RGS_OK;
+}

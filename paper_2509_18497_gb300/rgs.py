@@ -1,0 +1,283 @@
+"""Python binding of librgs (include/rgs.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does nothing but
+check tensor placement/shape/dtype, pass raw device pointers and the current CUDA
+stream, and turn a non-zero rgs_status into an exception.  All computation runs in
+the CUDA kernels of librgs.so; there is no CPU or PyTorch fallback: if the library
+is missing, importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librgs.so")
+
+RGS_MAX_SH_DEGREE = 3
+RGS_MAX_BOUNCES = 64
+RGS_ALPHA_GAUSS, RGS_ALPHA_DISC = 0, 1
+RGS_FP32 = 0
+
+STATUS = {0: "RGS_OK", 1: "RGS_ERR_ARG", 2: "RGS_ERR_CUDA", 3: "RGS_ERR_OOM", 4: "RGS_ERR_CAPACITY",
+          5: "RGS_ERR_NONFINITE", 6: "RGS_ERR_TIMEOUT", 7: "RGS_ERR_STATE"}
+
+# names exported by librgs.so, as declared in include/rgs.h
+EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
+           "rgs_transport_info_get", "rgs_destroy_transport", "rgs_destroy_scene", "rgs_profile_enable",
+           "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
+           "rgs_last_error", "rgs_abi_version")
+
+
+class RgsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rgs_surfels(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("sh_degree", ct.c_int32)] + [
+        (k, ct.c_void_p) for k in ("p", "tu", "tv", "s", "o", "ad", "k", "as_", "shin")]
+
+
+class rgs_build_opts(ct.Structure):
+    _fields_ = [("alpha_model", ct.c_int32), ("check_finite", ct.c_int32)]
+
+
+class rgs_lights(ct.Structure):
+    _fields_ = [("n_lights", ct.c_int32), ("pos", ct.c_void_p), ("intensity", ct.c_void_p)]
+
+
+class rgs_trace_opts(ct.Structure):
+    _fields_ = [("nd", ct.c_int32), ("reserved0", ct.c_int32), ("seed", ct.c_uint64), ("hit_capacity", ct.c_int64)]
+
+
+class rgs_solve_stats(ct.Structure):
+    _fields_ = [("n_bounces", ct.c_int32), ("n_cols", ct.c_int32),
+                ("residual_norm", ct.c_double * RGS_MAX_BOUNCES),
+                ("n_hits", ct.c_int64), ("n_hit_slots", ct.c_int64), ("n_full_rays", ct.c_int64)]
+
+
+class rgs_kernel_time(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("total_ms", ct.c_double)]
+
+
+class rgs_transport_info(ct.Structure):
+    _fields_ = [(k, ct.c_int32) for k in ("n", "sh_degree", "nc", "n_cols", "nd", "n_lights")] + [
+        (k, ct.c_int64) for k in ("n_hits", "n_hit_slots", "n_full_rays", "device_bytes")]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load librgs.so (built in-tree by build.py).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librgs.so not found at {path}: run paper_2509_18497_gb300/build.py "
+                           "(the CUDA library is required; there is no fallback)")
+    L = ct.CDLL(path)
+    vp = ct.c_void_p
+    L.rgs_build_scene.argtypes = [ct.POINTER(rgs_surfels), ct.POINTER(rgs_build_opts), vp, ct.POINTER(vp)]
+    L.rgs_trace_transport.argtypes = [vp, ct.POINTER(rgs_lights), ct.POINTER(rgs_trace_opts), vp, ct.POINTER(vp)]
+    L.rgs_solve.argtypes = [vp, vp, ct.c_int32, ct.c_int32, vp, ct.POINTER(rgs_solve_stats), vp]
+    L.rgs_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.rgs_get_iterate.argtypes = [vp, ct.c_int32, vp, vp]
+    L.rgs_transport_info_get.argtypes = [vp, ct.POINTER(rgs_transport_info)]
+    L.rgs_destroy_transport.argtypes = [vp]
+    L.rgs_destroy_transport.restype = None
+    L.rgs_destroy_scene.argtypes = [vp]
+    L.rgs_destroy_scene.restype = None
+    L.rgs_status_string.restype = ct.c_char_p
+    L.rgs_status_string.argtypes = [ct.c_int]
+    L.rgs_last_error.restype = ct.c_char_p
+    L.rgs_abi_version.restype = ct.c_int32
+    L.rgs_profile_enable.argtypes = [ct.c_int32]
+    L.rgs_profile_enable.restype = None
+    L.rgs_profile_reset.argtypes = []
+    L.rgs_profile_reset.restype = None
+    L.rgs_profile_report.argtypes = [ct.POINTER(rgs_kernel_time), ct.c_int32]
+    L.rgs_profile_report.restype = ct.c_int32
+    L.rgs_launch_count.restype = ct.c_int64
+    for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
+               "rgs_transport_info_get"):
+        getattr(L, fn).restype = ct.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise RgsError(status, load().rgs_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _dev(t, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return ct.c_void_p(t.data_ptr())
+
+
+class Scene:
+    """Owner of an rgs_scene handle (and references to the tensors it was built from)."""
+
+    def __init__(self):
+        self.h = ct.c_void_p(None)
+        self.n = 0
+        self.L = 0
+        self._keep = None
+
+    def __del__(self):
+        if self.h and _lib is not None:
+            _lib.rgs_destroy_scene(self.h)
+            self.h = ct.c_void_p(None)
+
+
+class Transport:
+    """Owner of an rgs_transport handle."""
+
+    def __init__(self, scene):
+        self.h = ct.c_void_p(None)
+        self.scene = scene
+        self.C = 3
+        self.nb = -1
+        self._keep = None
+
+    @property
+    def n(self):
+        return self.scene.n
+
+    @property
+    def nc(self):
+        return (self.scene.L + 1) ** 2
+
+    def __del__(self):
+        if self.h and _lib is not None:
+            _lib.rgs_destroy_transport(self.h)
+            self.h = ct.c_void_p(None)
+
+
+def rgs_build_scene(p, tu, tv, s, o, ad, k, as_, shin, sh_degree, alpha_model=RGS_ALPHA_GAUSS,
+                    check_finite=False, stream=None, scene=None):
+    """rgs_build_scene: surfel arrays are CUDA float32 tensors in the caller's order."""
+    L = load()
+    n = int(p.shape[0])
+    shapes = dict(p=(n, 3), tu=(n, 3), tv=(n, 3), s=(n, 2), o=(n,), ad=(n, 3), k=(n,), as_=(n, 3), shin=(n,))
+    arrs = dict(p=p, tu=tu, tv=tv, s=s, o=o, ad=ad, k=k, as_=as_, shin=shin)
+    sf = rgs_surfels(n, int(sh_degree), *[_dev(arrs[key], shapes[key], key) for key in shapes])
+    opts = rgs_build_opts(int(alpha_model), int(bool(check_finite)))
+    sc = scene if scene is not None else Scene()
+    h = ct.c_void_p(sc.h.value)
+    _check(L.rgs_build_scene(ct.byref(sf), ct.byref(opts), _stream(stream), ct.byref(h)))
+    sc.h = h
+    sc.n = n
+    sc.L = int(sh_degree)
+    sc._keep = arrs
+    return sc
+
+
+def rgs_trace_transport(scene, light_pos, light_I, nd, seed, hit_capacity=0, stream=None, transport=None):
+    """rgs_trace_transport: light_pos / light_I are CUDA float32 [NL,3] (NL may be 0)."""
+    L = load()
+    nl = int(light_pos.shape[0])
+    lt = rgs_lights(nl, _dev(light_pos, (nl, 3), "light_pos") if nl else None,
+                    _dev(light_I, (nl, 3), "light_I") if nl else None)
+    opts = rgs_trace_opts(int(nd), 0, int(seed), int(hit_capacity))
+    tr = transport if transport is not None else Transport(scene)
+    tr.scene = scene
+    h = ct.c_void_p(tr.h.value)
+    _check(L.rgs_trace_transport(scene.h, ct.byref(lt), ct.byref(opts), _stream(stream), ct.byref(h)))
+    tr.h = h
+    tr.C = 3 * max(nl, 1)
+    tr.nb = -1
+    return tr
+
+
+def rgs_solve(transport, E, n_bounces, B_out=None, stats=False, precision=RGS_FP32, stream=None):
+    """rgs_solve: E is CUDA float32 [N,nc,3] or None; returns (B_out [N,nc,C], stats or None)."""
+    L = load()
+    n, nc, C = transport.n, transport.nc, transport.C
+    if B_out is None:
+        B_out = torch.empty((n, nc, C), device="cuda", dtype=torch.float32)
+    st = rgs_solve_stats() if stats else None
+    _check(L.rgs_solve(transport.h, _dev(E, (n, nc, 3), "E") if E is not None else None, int(n_bounces),
+                       int(precision), _dev(B_out, (n, nc, C), "B_out"), ct.byref(st) if st is not None else None,
+                       _stream(stream)))
+    transport.nb = int(n_bounces)
+    if st is None:
+        return B_out, None
+    stats_d = dict(n_bounces=st.n_bounces, n_cols=st.n_cols,
+                   residual_norm=[st.residual_norm[b] for b in range(st.n_bounces)],
+                   n_hits=st.n_hits, n_hit_slots=st.n_hit_slots, n_full_rays=st.n_full_rays)
+    return B_out, stats_d
+
+
+def rgs_adjoint(transport, dL_dB, dL_dE=None, dL_dalbedo=None, dL_dopacity=None, want=("E", "albedo", "opacity"),
+                stream=None):
+    """rgs_adjoint: returns (dL/dE [N,nc,3], dL/da^d [N,3], dL/do [N]); entries not in `want` are None."""
+    L = load()
+    n, nc, C = transport.n, transport.nc, transport.C
+    if dL_dE is None and "E" in want:
+        dL_dE = torch.empty((n, nc, 3), device="cuda", dtype=torch.float32)
+    if dL_dalbedo is None and "albedo" in want:
+        dL_dalbedo = torch.empty((n, 3), device="cuda", dtype=torch.float32)
+    if dL_dopacity is None and "opacity" in want:
+        dL_dopacity = torch.empty((n,), device="cuda", dtype=torch.float32)
+    _check(L.rgs_adjoint(transport.h, _dev(dL_dB, (n, nc, C), "dL_dB"),
+                         _dev(dL_dE, (n, nc, 3), "dL_dE") if dL_dE is not None else None,
+                         _dev(dL_dalbedo, (n, 3), "dL_dalbedo") if dL_dalbedo is not None else None,
+                         _dev(dL_dopacity, (n,), "dL_dopacity") if dL_dopacity is not None else None,
+                         _stream(stream)))
+    return dL_dE, dL_dalbedo, dL_dopacity
+
+
+def rgs_get_iterate(transport, b, out=None, stream=None):
+    L = load()
+    n, nc, C = transport.n, transport.nc, transport.C
+    if out is None:
+        out = torch.empty((n, nc, C), device="cuda", dtype=torch.float32)
+    _check(L.rgs_get_iterate(transport.h, int(b), _dev(out, (n, nc, C), "out"), _stream(stream)))
+    return out
+
+
+def rgs_transport_info_get(transport):
+    L = load()
+    info = rgs_transport_info()
+    _check(L.rgs_transport_info_get(transport.h, ct.byref(info)))
+    return {k: getattr(info, k) for k, _ in rgs_transport_info._fields_}
+
+
+def rgs_abi_version():
+    return int(load().rgs_abi_version())
+
+
+def rgs_profile_enable(on=True):
+    load().rgs_profile_enable(1 if on else 0)
+
+
+def rgs_profile_reset():
+    load().rgs_profile_reset()
+
+
+def rgs_profile_report():
+    """{kernel name: (launches, total device ms)} for the launches since the last reset."""
+    L = load()
+    buf = (rgs_kernel_time * 64)()
+    m = L.rgs_profile_report(buf, 64)
+    if m < 0:
+        raise RgsError(2, L.rgs_last_error().decode(errors="replace"))
+    return {buf[q].name.decode(): (int(buf[q].launches), float(buf[q].total_ms)) for q in range(min(m, 64))}
+
+
+def rgs_launch_count():
+    return int(load().rgs_launch_count())
