@@ -53,7 +53,12 @@ def _src_sha(name):
 
 # DRAM bytes per launch from one ncu capture (profiles/), keyed by kernel; valid only
 # while the kernel's source file is unchanged since the capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "k_trace_hemi": {"bytes_per_launch": 6.238852e9 + 12.022045e9, "n": 10000, "src_sha": "39d3ef415f7b0f34"},
+    "k_bounce": {"bytes_per_launch": 0.879334e9 + 0.006455e9, "n": 10000, "src_sha": "ae4e5a315773ea56"},
+    "k_adj_bounce": {"bytes_per_launch": 0.400631e9 + 0.006990e9, "n": 10000, "src_sha": "90eee932693e628b"},
+    "k_hemi_opacity_bwd": {"bytes_per_launch": 3.571173e9 + 1.144471e9, "n": 10000, "src_sha": "90eee932693e628b"},
+}
 
 
 def algorithmic_bytes(kernel, info, n, nd, nb, C, nc):
@@ -173,7 +178,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=50000, help="surfel count (default: the 50,000-surfel workload)")
     ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
-    ap.add_argument("--ref-sample", type=int, default=2500, help="surfels per reference-arm step")
+    ap.add_argument("--ref-sample", type=int, default=1500, help="surfels per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
