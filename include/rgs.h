@@ -178,6 +178,26 @@ rgs_status rgs_adjoint(rgs_transport *t, const float *dL_dB, float *dL_dE, float
  * array out [N][nc][C].  Asynchronous.  Errors: RGS_ERR_STATE, RGS_ERR_ARG, RGS_ERR_CUDA. */
 rgs_status rgs_get_iterate(rgs_transport *t, int32_t b, float *out, void *stream);
 
+/* FP64 residual norm ||x - y||_2 of two device float arrays of n elements, written to the
+ * device double *norm_out -- the same quantity rgs_solve reports per bounce, for two
+ * iterates the caller holds.  The paper has no counterpart: this is a library service.
+ *
+ * It allocates no device memory, for callers that cannot: a host application that has
+ * reserved its whole device-memory budget and passes the library only buffers it owns,
+ * or a latency-critical loop that must not pay cudaMalloc's device-wide synchronisation.
+ * Its scratch (one FP64 partial per 8192-element block, 8192 blocks = 64 KiB) is a static
+ * device array inside librgs.so that every GPU loading the library keeps until exit.
+ *   x, y     : device float arrays, n elements each (caller-owned, read only).
+ *   n        : 0 <= n <= 8192 * 8192 = 67,108,864; larger n returns RGS_ERR_ARG.
+ *   norm_out : device double (caller-owned), written on `stream`.
+ * The first call on each device looks up the scratch's device address (with that device
+ * current) and caches it; make that first call before any stream capture.  All calls share
+ * the one scratch array, which keeps the last call's contents (each call writes every slot
+ * it reads, so nothing needs clearing); calls that overlap on the GPU -- on different
+ * streams, or from different host threads -- race on it and must be serialised.
+ * Asynchronous.  Errors: RGS_ERR_ARG, RGS_ERR_CUDA. */
+rgs_status rgs_residual_norm_noalloc(const float *x, const float *y, int64_t n, double *norm_out, void *stream);
+
 /* Fills *info (host).  Synchronises nothing.  Errors: RGS_ERR_ARG. */
 rgs_status rgs_transport_info_get(const rgs_transport *t, rgs_transport_info *info);
 

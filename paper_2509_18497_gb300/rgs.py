@@ -28,7 +28,7 @@ STATUS = {0: "RGS_OK", 1: "RGS_ERR_ARG", 2: "RGS_ERR_CUDA", 3: "RGS_ERR_OOM", 4:
 EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
            "rgs_transport_info_get", "rgs_destroy_transport", "rgs_destroy_scene", "rgs_profile_enable",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
-           "rgs_last_error", "rgs_abi_version")
+           "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc")
 
 
 class RgsError(RuntimeError):
@@ -103,6 +103,8 @@ def load(path=LIB_PATH):
     L.rgs_profile_report.argtypes = [ct.POINTER(rgs_kernel_time), ct.c_int32]
     L.rgs_profile_report.restype = ct.c_int32
     L.rgs_launch_count.restype = ct.c_int64
+    L.rgs_residual_norm_noalloc.argtypes = [vp, vp, ct.c_int64, vp, vp]
+    L.rgs_residual_norm_noalloc.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
                "rgs_transport_info_get"):
         getattr(L, fn).restype = ct.c_int
@@ -281,3 +283,17 @@ def rgs_profile_report():
 
 def rgs_launch_count():
     return int(load().rgs_launch_count())
+
+
+def rgs_residual_norm_noalloc(x, y, norm_out=None, stream=None):
+    """rgs_residual_norm_noalloc: FP64 ||x - y||_2 of two equal-size float32 CUDA tensors into a
+    float64 CUDA scalar, using the library's static scratch (no device allocation inside)."""
+    L = load()
+    n = x.numel()
+    if norm_out is None:
+        norm_out = torch.empty((), device=x.device, dtype=torch.float64)
+    if not (norm_out.is_cuda and norm_out.dtype == torch.float64 and norm_out.numel() == 1):
+        raise TypeError("norm_out: expected a float64 CUDA scalar")
+    _check(L.rgs_residual_norm_noalloc(_dev(x, tuple(x.shape), "x"), _dev(y, tuple(x.shape), "y"), int(n),
+                                       ct.c_void_p(norm_out.data_ptr()), _stream(stream)))
+    return norm_out
