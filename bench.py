@@ -66,14 +66,19 @@ def algorithmic_bytes(kernel, info, n, nd, nb, C, nc):
     A = n * C * nc * 4          # one [N][C][nc] float array
     H = info["n_hits"]
     rays = n * nd
-    if kernel == "k_bounce":      # records + counts + B^(k-1) + S in; Q, B^(k) out
-        return H * 8 + rays * 4 + rays // 32 * 8 + 2 * A + 2 * A
-    if kernel == "k_adj_bounce":  # transposed records + offsets + v^(a-1) in; v^(a) out; u read+write
-        return H * 8 + (n + 1) * 8 + A + A + 2 * A
-    if kernel == "k_hemi_opacity_bwd":  # records (j, a, G) + counts; v^(0..nb-1), B^(0..nb-1); dL/do
-        return H * 12 + rays * 4 + rays // 32 * 8 + 2 * nb * A + n * 4
-    if kernel == "k_trace_hemi":  # scene (64 B/surfel + 64 B/node) in; records + counts out
-        return n * 64 + (n - 1) * 64 + info["n_hit_slots"] * 12 + rays * 4 + rays // 32 * 8
+    tile = A * 3 // C           # one 3-column tile of such an array
+    if kernel == "k_bounce":      # records + counts + directions + B^(k-1) + S in; Q, B^(k) out
+        return H * 8 + rays * (4 + 16) + rays // 32 * 8 + 4 * A
+    if kernel == "k_adj_src":     # transposed records, (direction, y) per ray, offsets; v^(a) tile out, u tile r+w
+        return H * 8 + rays * 32 + (n + 1) * 8 + 3 * tile
+    if kernel == "k_adj_ray":     # directions + v^(a-1) tile in; y per ray out
+        return rays * 32 + tile
+    if kernel == "k_opacity_g":   # records (j) + counts + directions; 4 iterates of v and B tiles; g per hit out
+        return H * (8 + 4) + rays * (4 + 16) + rays // 32 * 8 + 2 * min(nb, 4) * tile
+    if kernel == "k_opacity_rec":  # records (j, a) + G + g per hit, counts; dL/do
+        return H * (8 + 4 + 4) + rays * 4 + n * 4
+    if kernel == "k_trace_hemi":  # scene (64 B/surfel + 64 B/node) in; records, counts, directions out
+        return n * 64 + (n - 1) * 64 + H * 12 + rays * (4 + 16) + rays // 32 * 8 + n * 4
     return None
 
 
@@ -292,7 +297,8 @@ def main():
     alg = algorithmic_bytes(dom, info, n, nd, nb, C, nc)
     avg_ms = ms_dom / c_dom
     achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
-    src_file = {"k_bounce": "rgs_solve.cu", "k_adj_bounce": "rgs_adjoint.cu", "k_hemi_opacity_bwd": "rgs_adjoint.cu",
+    src_file = {"k_bounce": "rgs_solve.cu", "k_adj_src": "rgs_adjoint.cu", "k_adj_ray": "rgs_adjoint.cu",
+                "k_opacity_g": "rgs_adjoint.cu", "k_opacity_rec": "rgs_adjoint.cu",
                 "k_trace_hemi": "rgs_trace.cu"}.get(dom)
     traffic = None
     if dom in NCU_TRAFFIC and src_file and NCU_TRAFFIC[dom]["src_sha"] == _src_sha(src_file):

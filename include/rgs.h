@@ -111,7 +111,8 @@ typedef struct rgs_solve_stats {
     double residual_norm[RGS_MAX_BOUNCES]; /* FP64 ||B^(k) - B^(k-1)||_2 over all columns */
     int64_t n_hits;          /* stored hemisphere hit records */
     int64_t n_hit_slots;     /* reserved record slots actually used (with warp padding) */
-    int64_t n_full_rays;     /* rays whose hit buffer filled up (nearest hits kept) */
+    int64_t n_full_rays;     /* rays truncated: their nearest-hit buffer filled before the
+                                transmittance fell below the compositing cut */
 } rgs_solve_stats;
 
 typedef struct rgs_transport_info {

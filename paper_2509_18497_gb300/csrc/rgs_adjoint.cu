@@ -4,11 +4,13 @@
 //                                              decay reversed, propagating gradients)
 //   u = sum_a v^(a) = dL/dS,   P_i[l][ch] = sum_{k in l, light} (sum_{a<n} v^(a) Q^(n-1-a) + u Dgeo)
 //
-// k_adj_bounce gathers K^T v over the records grouped by source surfel j:
+// K^T v is a gather over the records grouped by source surfel j:
 //   (K^T v)_j[c][k] = sum_{hits e on j} a_e Y_k(-d_e) y_e[c],
 //   y_e[c] = (pi/nd) o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d_e) v_i[c][k']      (i = receiver of e)
-// k_hemi_opacity_bwd / k_shadow_bwd run the compositing backward of every hemisphere and
-// shadow ray (dL/dalpha_h = T_h (g_h - R_h), dL/dT = -prod of the other (1 - alpha)).
+// k_adj_ray forms y per ray once (ray-major, next to the stored direction) and k_adj_src
+// gathers (d, y) per entry, 32 bytes, instead of a 192-byte row of v_i per entry.
+// k_opacity_g / k_opacity_rec and k_shadow_bwd run the compositing backward of every
+// hemisphere and shadow ray (dL/dalpha_h = T_h (g_h - R_h), dL/dT = -prod of the other (1 - alpha)).
 #include "rgs_internal.cuh"
 
 namespace {
@@ -42,15 +44,40 @@ __global__ void k_pair_accum(int n, int C, const float *__restrict__ X, const fl
         for (int ch = 0; ch < 3; ++ch) P[(size_t)i * 12 + l * 3 + ch] += acc[l][ch];
 }
 
-template <int NC, int CT>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_bounce(SceneDev sc, RaysDev rays, int C,
-                                                           const long long *__restrict__ src_off,
-                                                           const int2 *__restrict__ tr, const float *__restrict__ vin,
-                                                           float *__restrict__ vout, float *__restrict__ u) {
+// Per ray r of receiver i (column tile col0..col0+2):
+//   y_r[c] = (pi/nd) o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) v_i[c][k']
+// stored next to the ray's direction for the by-source gather.
+template <int NC>
+__global__ void __launch_bounds__(256) k_adj_ray(SceneDev sc, RaysDev rays, int C, int col0,
+                                                 const float *__restrict__ vin, float4 *dy) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= sc.n * rays.nd) return;
+    const int i = r / rays.nd;
+    const float3 n = f3(sc.N4[i]);
+    const float3 d = f3(rays.dir[r]);
+    float Yi[NC];
+    sh_eval<NC>(reflect_n(n, d), Yi);
+    const float oi = sc.P[i].w * (3.14159265358979f / (float)rays.nd);
+    const float *vi = vin + ((size_t)i * C + col0) * NC;
+    float y[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int ch = (col0 + c) % 3;
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) s += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * Yi[k] * __ldg(&vi[c * NC + k]);
+        y[c] = oi * s;
+    }
+    dy[r] = make_float4(y[0], y[1], y[2], 0.f);
+}
+
+// (K^T v)_j[c][k] = sum_{entries e on j} a_e Y_k(-d_e) y_e[c]; one CTA per source j.
+template <int NC>
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_src(RaysDev rays, int C, int col0, const long long *__restrict__ src_off,
+                                                        const int2 *__restrict__ tr, const float4 *__restrict__ dy,
+                                                        float *__restrict__ vout, float *__restrict__ u) {
+    constexpr int CT = 3;
     const int j = blockIdx.x;
-    const int col0 = blockIdx.y * CT;
-    const int nd = rays.nd;
-    const float w = 3.14159265358979f / (float)nd;
     float acc[NC][CT];
 #pragma unroll
     for (int k = 0; k < NC; ++k)
@@ -59,27 +86,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_bounce(SceneDev sc, RaysDev
     const long long e0 = src_off[j], e1 = src_off[j + 1];
     for (long long e = e0 + threadIdx.x; e < e1; e += ADJ_THREADS) {
         const int2 ent = __ldg(&tr[e]);
-        const int r = ent.x;
         const float a = __int_as_float(ent.y);
-        const int i = r / nd, q = r - i * nd;
-        const float3 n = f3(__ldg(&sc.N4[i]));
-        const float3 d = ray_dir(rays.seed, __ldg(&sc.uid[i]), q, rays.na, rays.nbs, f3(__ldg(&sc.FU[i])),
-                                 f3(__ldg(&sc.FV[i])), n);
-        float Yo[NC], Yi[NC];
-        sh_eval<NC>(neg3(d), Yo);
-        sh_eval<NC>(reflect_n(n, d), Yi);
-        const float oi = __ldg(&sc.P[i].w) * w;
-        const float *vi = vin + ((size_t)i * C + col0) * NC;
+        const float4 d4 = __ldg(&rays.dir[ent.x]);
+        const float4 y4 = __ldg(&dy[ent.x]);
+        float Yo[NC];
+        sh_eval<NC>(make_float3(-d4.x, -d4.y, -d4.z), Yo);
+        const float y[3] = {a * y4.x, a * y4.y, a * y4.z};
 #pragma unroll
-        for (int c = 0; c < CT; ++c) {
-            const int ch = (col0 + c) % 3;
-            float y = 0.f;
+        for (int k = 0; k < NC; ++k)
 #pragma unroll
-            for (int k = 0; k < NC; ++k) y += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * Yi[k] * __ldg(&vi[c * NC + k]);
-            y *= oi * a;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) acc[k][c] += Yo[k] * y;
-        }
+            for (int c = 0; c < CT; ++c) acc[k][c] += Yo[k] * y[c];
     }
     __shared__ float red[ADJ_THREADS / 32][NC * CT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -162,71 +178,109 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, const float *__restrict__ lpos
     bvh_traverse(sc, o, w, r, pass2);
 }
 
-// Hemisphere rays: g_h = sum_{a<n} sum_c y^(a)[c] Y(-d).B^(n-1-a)_{j_h}[c], then back to front
-// R_{h-1} = alpha_h g_h + (1 - alpha_h) R_h and dL/do_{j_h} += T_h (g_h - R_h) G_h.
-template <int NC, int CT>
-__global__ void __launch_bounds__(128) k_hemi_opacity_bwd(SceneDev sc, RaysDev rays, int C, int nb, size_t A,
-                                                          const float *__restrict__ V, const float *__restrict__ Bit,
-                                                          float *dop) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// Hemisphere rays, part 1: for every stored hit h of ray r (receiver i, source j_h),
+//   g_h = sum_{a<n} sum_c y_r^(a)[c] Y(-d_r) . B^(n-1-a)_{j_h}[c],
+//   y_r^(a)[c] = (pi/nd) o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) v_i^(a)[c][k'],
+// accumulated into gh[slot] for iterates a0 .. a0+na-1 (first chunk writes, later add).
+template <int NC, int CT, int NA>
+__global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, int C, int col0, int nb, int a0, int na,
+                                                   size_t A, const float *__restrict__ V, const float *__restrict__ Bit,
+                                                   float *gh, bool first) {
+    using SL = Slice<NC>;
+    constexpr int G = SL::G, KPL = SL::KPL;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ray = t / G, g = t % G;
     const int n_rays = sc.n * rays.nd;
-    if (r >= n_rays) return;
-    const int cnt = rays.cnt[r];
-    if (cnt == 0) return;
-    const int col0 = blockIdx.y * CT;
-    const int i = r / rays.nd, q = r - i * rays.nd;
+    const bool live = ray < n_rays;
+    const int r = live ? ray : n_rays - 1;
+    const int cnt = live ? rays.cnt[r] : 0;
+    const int i = r / rays.nd;
     const float3 n = f3(sc.N4[i]);
-    const float3 d = ray_dir(rays.seed, sc.uid[i], q, rays.na, rays.nbs, f3(sc.FU[i]), f3(sc.FV[i]), n);
-    float Yo[NC], Yi[NC];
-    sh_eval<NC>(neg3(d), Yo);
-    sh_eval<NC>(reflect_n(n, d), Yi);
-    const float w = 3.14159265358979f / (float)rays.nd;
-    const float oi = sc.P[i].w * w;
-    const long long base = rays.warp_base[r >> 5] + (r & 31);
-    float g[RGS_HMAX];
-    for (int h = 0; h < cnt; ++h) g[h] = 0.f;
-    for (int a = 0; a < nb; ++a) {
-        float y[CT];
-        const float *vi = V + A * a + ((size_t)i * C + col0) * NC;
+    const float3 d = f3(rays.dir[r]);
+    float yo[KPL];
+    float y[NA][CT];
+    {
+        float Y[NC], yi[KPL];
+        sh_eval<NC>(neg3(d), Y);
+        SL::pick(Y, g, yo);
+        sh_eval<NC>(reflect_n(n, d), Y);
+        SL::pick(Y, g, yi);
+        const float oi = sc.P[i].w * (3.14159265358979f / (float)rays.nd);
 #pragma unroll
-        for (int c = 0; c < CT; ++c) {
-            const int ch = (col0 + c) % 3;
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) s += sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch] * Yi[k] * vi[c * NC + k];
-            y[c] = oi * s;
-        }
-        const float *Bb = Bit + A * (nb - 1 - a);
-        for (int h = 0; h < cnt; ++h) {
-            const int j = __ldg(&rays.rec_ja[base + (long long)h * 32]).x;
-            const float *Bj = Bb + ((size_t)j * C + col0) * NC;
-            float acc = 0.f;
+        for (int aa = 0; aa < NA; ++aa) {
 #pragma unroll
             for (int c = 0; c < CT; ++c) {
                 float s = 0.f;
+                if (aa < na) {
+                    const int ch = (col0 + c) % 3;
+                    float v[KPL];
+                    SL::load(V + A * (a0 + aa) + ((size_t)i * C + col0 + c) * NC, g, v);
 #pragma unroll
-                for (int k = 0; k < NC; ++k) s += Yo[k] * __ldg(&Bj[c * NC + k]);
-                acc += y[c] * s;
+                    for (int m = 0; m < KPL; ++m) {
+                        const int kk = SL::k(g, m);
+                        const float cl = (kk < NC) ? __ldg(&sc.cl[(size_t)i * 12 + band_of(kk) * 3 + ch]) : 0.f;
+                        s += cl * yi[m] * v[m];
+                    }
+                }
+                y[aa][c] = oi * SL::group_sum(s);
             }
-            g[h] += acc;
         }
     }
-    // transmittance in front of each hit, then the back-to-front recurrence
+    const long long base = rays.warp_base[r >> 5] + (r & 31);
+    const int rows = SL::G == 1 ? cnt : __reduce_max_sync(0xffffffffu, cnt); // groups of a warp stay converged
+    for (int h = 0; h < rows; ++h) {
+        float acc = 0.f;
+        int j = 0;
+        if (h < cnt) j = __ldg(&rays.rec_ja[base + (long long)h * 32]).x;
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            if (aa < na && h < cnt) {
+                const float *Bj = Bit + A * (nb - 1 - (a0 + aa)) + ((size_t)j * C + col0) * NC;
+#pragma unroll
+                for (int c = 0; c < CT; ++c) {
+                    float v[KPL];
+                    SL::load(Bj + c * NC, g, v);
+                    float s = 0.f;
+#pragma unroll
+                    for (int m = 0; m < KPL; ++m) s += yo[m] * v[m];
+                    acc += y[aa][c] * s;
+                }
+            }
+        }
+        acc = SL::group_sum(acc);
+        if (g == 0 && h < cnt) {
+            const long long slot = base + (long long)h * 32;
+            gh[slot] = first ? acc : gh[slot] + acc;
+        }
+    }
+}
+
+// Hemisphere rays, part 2: back to front, R_{h-1} = alpha_h g_h + (1 - alpha_h) R_h and
+// dL/do_{j_h} += T_h (g_h - R_h) G_h, with T_h the transmittance in front of hit h.
+__global__ void __launch_bounds__(256) k_opacity_rec(SceneDev sc, RaysDev rays, const float *__restrict__ gh,
+                                                     float *dop) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= sc.n * rays.nd) return;
+    const int cnt = rays.cnt[r];
+    if (cnt == 0) return;
+    const long long base = rays.warp_base[r >> 5] + (r & 31);
     float Th[RGS_HMAX];
     float T = 1.f;
     for (int h = 0; h < cnt; ++h) {
         Th[h] = T;
-        const int j = __ldg(&rays.rec_ja[base + (long long)h * 32]).x;
-        T *= 1.f - __ldg(&sc.P[j].w) * __ldg(&rays.rec_g[base + (long long)h * 32]);
+        const long long slot = base + (long long)h * 32;
+        T *= 1.f - __ldg(&sc.P[__ldg(&rays.rec_ja[slot]).x].w) * __ldg(&rays.rec_g[slot]);
     }
     float R = 0.f;
     for (int h = cnt - 1; h >= 0; --h) {
-        const int j = __ldg(&rays.rec_ja[base + (long long)h * 32]).x;
-        const float G = __ldg(&rays.rec_g[base + (long long)h * 32]);
+        const long long slot = base + (long long)h * 32;
+        const int j = __ldg(&rays.rec_ja[slot]).x;
+        const float G = __ldg(&rays.rec_g[slot]);
         const float alpha = __ldg(&sc.P[j].w) * G;
-        const float da = Th[h] * (g[h] - R);
+        const float g = gh[slot];
+        const float da = Th[h] * (g - R);
         if (da != 0.f) atomicAdd(&dop[j], da * G);
-        R = alpha * g[h] + (1.f - alpha) * R;
+        R = alpha * g + (1.f - alpha) * R;
     }
 }
 
@@ -271,10 +325,13 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     RGS_LAUNCH("adjoint init");
     const unsigned gn = (unsigned)((n + 127) / 128);
     if (nb >= 1) { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, t->v, t->Q + A * (nb - 1), t->Pg); }
+    const long long n_rays = (long long)n * t->nd;
+    const unsigned gr = (unsigned)((n_rays + 255) / 256);
     for (int a = 1; a <= nb; ++a) {
-        dim3 grid(n, C / 3);
-        { ProfScope ps_("k_adj_bounce", st); k_adj_bounce<NC, 3><<<grid, ADJ_THREADS, 0, st>>>(sd, rd, C, t->src_off, t->tr, t->v + A * (a - 1),
-                                                           t->v + A * a, t->u); }
+        for (int col0 = 0; col0 < C; col0 += 3) {
+            { ProfScope ps_("k_adj_ray", st); k_adj_ray<NC><<<gr, 256, 0, st>>>(sd, rd, C, col0, t->v + A * (a - 1), t->dy); }
+            { ProfScope ps_("k_adj_src", st); k_adj_src<NC><<<n, ADJ_THREADS, 0, st>>>(rd, C, col0, t->src_off, t->tr, t->dy, t->v + A * a, t->u); }
+        }
         RGS_LAUNCH("adjoint bounce");
         if (a <= nb - 1) { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, t->v + A * a, t->Q + A * (nb - 1 - a), t->Pg); }
     }
@@ -284,9 +341,15 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
-        const long long n_rays = (long long)n * t->nd;
-        dim3 grid((unsigned)((n_rays + 127) / 128), C / 3);
-        { ProfScope ps_("k_hemi_opacity_bwd", st); k_hemi_opacity_bwd<NC, 3><<<grid, 128, 0, st>>>(sd, rd, C, nb, A, t->v, t->iters, t->dop); }
+        constexpr int NA = 4;
+        const unsigned gg = (unsigned)((n_rays * Slice<NC>::G + 255) / 256);
+        for (int col0 = 0; col0 < C; col0 += 3) {
+            for (int a0 = 0; a0 < nb; a0 += NA) {
+                const int na = min(NA, nb - a0);
+                { ProfScope ps_("k_opacity_g", st); k_opacity_g<NC, 3, NA><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v, t->iters, t->gh, a0 == 0 && col0 == 0); }
+            }
+        }
+        { ProfScope ps_("k_opacity_rec", st); k_opacity_rec<<<gr, 256, 0, st>>>(sd, rd, t->gh, t->dop); }
         RGS_LAUNCH("hemisphere opacity backward");
     }
     { ProfScope ps_("k_finalize", st); k_finalize<NC><<<gn, 128, 0, st>>>(sd, C, t->u, t->Pg, t->sc->kk, t->dop, dE, dad, dopo); }
@@ -304,6 +367,10 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
         if ((r = dev_alloc(&t->v, A * (nb + 1), &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->u, A, &t->device_bytes)) != RGS_OK) return r;
         t->v_cap = nb + 1;
+    }
+    if (t->cap_slots > t->gh_cap) {
+        if ((r = dev_alloc(&t->gh, (size_t)t->cap_slots, &t->device_bytes)) != RGS_OK) return r;
+        t->gh_cap = t->cap_slots;
     }
     if (t->n > t->pg_cap) {
         if ((r = dev_alloc(&t->Pg, (size_t)t->n * 12, &t->device_bytes)) != RGS_OK) return r;

@@ -317,6 +317,9 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->u);
     dev_free(t->Pg);
     dev_free(t->dop);
+    dev_free(t->gh);
+    dev_free(t->dir);
+    dev_free(t->dy);
     delete t;
 }
 

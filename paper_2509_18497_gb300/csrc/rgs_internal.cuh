@@ -14,14 +14,14 @@
 
 #include "../../include/rgs.h"
 
-#define RGS_HMAX 128          // per-ray hit buffer; when full the nearest RGS_HMAX hits are kept
+#define RGS_HMAX 96           // per-ray hit buffer; when full the nearest RGS_HMAX hits are kept
 #define RGS_T_EPS 1e-6f       // compositing stops once the transmittance is below this
 #define RGS_STACK 64          // BVH traversal stack depth (tree depth is bounded by 32 + log2 N)
 
 // ------------------------------------------------------------------ error flags
 enum {
     FLAG_CAPACITY = 0,  // hit-record slots exhausted (warps that could not store)
-    FLAG_FULL_RAYS = 1, // rays whose RGS_HMAX buffer filled up
+    FLAG_FULL_RAYS = 1, // rays whose full RGS_HMAX buffer ended above the transmittance cut
     FLAG_STACK = 2,     // traversal stack overflow (the ray then misses the rest of the tree)
     FLAG_NONFINITE = 3,
     FLAG_COUNT = 8
@@ -54,6 +54,7 @@ struct RaysDev {
     const float *rec_g;
     const long long *warp_base;
     const int *cnt;
+    const float4 *dir; // per-ray direction (xyz), written by the trace
 };
 
 // ------------------------------------------------------------------ small math
@@ -113,6 +114,50 @@ __device__ __forceinline__ void sh_eval(float3 v, float *Y) {
 
 __host__ __device__ constexpr int band_of(int k) { return k == 0 ? 0 : (k < 4 ? 1 : (k < 9 ? 2 : 3)); }
 
+// Cooperative row slices for the gathers: G lanes share one ray (or one transposed entry)
+// and each lane owns KPL of the NC coefficients of every row.  nc = 16: 4 lanes x one
+// float4 each (the 4 lanes read 64 contiguous bytes of a row per load); nc = 9: 4 lanes,
+// interleaved scalars; nc <= 4: one lane per ray, the whole row (a float4 for nc = 4).
+template <int NC> struct Slice {
+    static constexpr int G = (NC >= 9) ? 4 : 1;
+    static constexpr int KPL = (NC + G - 1) / G;
+    static constexpr bool VEC = (NC % 4 == 0) && (NC / G == 4);
+    __device__ static constexpr int k(int g, int m) { return VEC ? 4 * g + m : g + m * G; }
+    // this lane's KPL entries of the NC-float row `row` (zero where k >= NC)
+    __device__ static void load(const float *__restrict__ row, int g, float *v) {
+        if constexpr (VEC) {
+            const float4 q4 = __ldg(reinterpret_cast<const float4 *>(row) + g);
+            v[0] = q4.x;
+            v[1] = q4.y;
+            v[2] = q4.z;
+            v[3] = q4.w;
+        } else {
+#pragma unroll
+            for (int m = 0; m < KPL; ++m) {
+                const int kk = k(g, m);
+                v[m] = (kk < NC) ? __ldg(row + kk) : 0.f;
+            }
+        }
+    }
+    // select this lane's entries of a full NC-vector held in registers (no dynamic indexing)
+    __device__ static void pick(const float *full, int g, float *v) {
+#pragma unroll
+        for (int m = 0; m < KPL; ++m) {
+            float x = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < NC; ++kk)
+                if (kk == k(g, m)) x = full[kk];
+            v[m] = x;
+        }
+    }
+    // sum over the G lanes of a group (lanes g = 0..G-1 are consecutive)
+    __device__ static float group_sum(float x) {
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        return x;
+    }
+};
+
 // ------------------------------------------------------------------ ray generation
 // SplitMix64 output function (Steele, Lea & Flood 2014) applied to a counter.
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
@@ -141,29 +186,49 @@ __device__ __forceinline__ float3 ray_dir(unsigned long long seed, int uid, int 
 }
 
 // ------------------------------------------------------------------ intersection
-// Ray o + t d against the plane of surfel j (Eq. G). Returns true with t and G when the
+// Squared local radius u^2 + v^2 of the point o + t d on the plane of surfel j (Eq. G),
+// with explicitly rounded operations so that every call site computes identical bits
+// (the trace recomputes it after sorting instead of storing it).
+__device__ __forceinline__ float surfel_r2(const SceneDev &sc, int j, float3 o, float3 d, float t) {
+    const float4 Pj = __ldg(&sc.P[j]);
+    const float wx = __fsub_rn(Pj.x, o.x), wy = __fsub_rn(Pj.y, o.y), wz = __fsub_rn(Pj.z, o.z);
+    const float qx = __fmaf_rn(t, d.x, -wx), qy = __fmaf_rn(t, d.y, -wy), qz = __fmaf_rn(t, d.z, -wz); // x - p_j
+    const float4 U = __ldg(&sc.FU[j]);
+    const float4 V = __ldg(&sc.FV[j]);
+    const float u = __fmul_rn(__fmaf_rn(qz, U.z, __fmaf_rn(qy, U.y, __fmul_rn(qx, U.x))), U.w);
+    const float v = __fmul_rn(__fmaf_rn(qz, V.z, __fmaf_rn(qy, V.y, __fmul_rn(qx, V.x))), V.w);
+    return __fmaf_rn(v, v, __fmul_rn(u, u));
+}
+
+__device__ __forceinline__ float surfel_G(const SceneDev &sc, float r2) {
+    return (sc.alpha_model == RGS_ALPHA_DISC) ? 1.f : expf(-0.5f * r2);
+}
+
+// Ray o + t d against the plane of surfel j (Eq. G). Returns true with t and r2 when the
 // hit is accepted: j != self, |n_j.(p_j - o)| > eps, 0 < t < tmax, inside the cutoff.
-__device__ __forceinline__ bool hit_surfel(const SceneDev &sc, int j, int self, float3 o, float3 d, float tmax,
-                                           float eps, float &t_out, float &g_out) {
+__device__ __forceinline__ bool hit_surfel_t(const SceneDev &sc, int j, int self, float3 o, float3 d, float tmax,
+                                             float eps, float &t_out, float &r2_out) {
     if (j == self) return false;
     const float4 Nj = __ldg(&sc.N4[j]);
     const float den = Nj.x * d.x + Nj.y * d.y + Nj.z * d.z;
     if (fabsf(den) < 1e-12f) return false;
     const float4 Pj = __ldg(&sc.P[j]);
-    const float3 w = make_float3(Pj.x - o.x, Pj.y - o.y, Pj.z - o.z);
-    const float h = Nj.x * w.x + Nj.y * w.y + Nj.z * w.z;
+    const float h = Nj.x * (Pj.x - o.x) + Nj.y * (Pj.y - o.y) + Nj.z * (Pj.z - o.z);
     if (fabsf(h) <= eps) return false;
     const float t = h / den;
     if (!(t > 0.f) || !(t < tmax)) return false;
-    const float3 q = make_float3(t * d.x - w.x, t * d.y - w.y, t * d.z - w.z); // x - p_j
-    const float4 U = __ldg(&sc.FU[j]);
-    const float4 V = __ldg(&sc.FV[j]);
-    const float u = (q.x * U.x + q.y * U.y + q.z * U.z) * U.w;
-    const float v = (q.x * V.x + q.y * V.y + q.z * V.z) * V.w;
-    const float r2 = u * u + v * v;
+    const float r2 = surfel_r2(sc, j, o, d, t);
     if (r2 > sc.cutoff2) return false;
     t_out = t;
-    g_out = (sc.alpha_model == RGS_ALPHA_DISC) ? 1.f : expf(-0.5f * r2);
+    r2_out = r2;
+    return true;
+}
+
+__device__ __forceinline__ bool hit_surfel(const SceneDev &sc, int j, int self, float3 o, float3 d, float tmax,
+                                           float eps, float &t_out, float &g_out) {
+    float r2;
+    if (!hit_surfel_t(sc, j, self, o, d, tmax, eps, t_out, r2)) return false;
+    g_out = surfel_G(sc, r2);
     return true;
 }
 
@@ -269,6 +334,8 @@ struct rgs_transport {
     float *rec_g = nullptr;
     long long *warp_base = nullptr;
     int *cnt = nullptr;
+    float4 *dir = nullptr; // per-ray direction
+    float4 *dy = nullptr;  // adjoint: per-ray (y[0..2], 0) for the current column tile
     long long rays_cap = 0;
     unsigned long long *counter = nullptr;
     int *flags = nullptr;
@@ -298,6 +365,8 @@ struct rgs_transport {
     float *Pg = nullptr;  // [N][4][3]
     float *dop = nullptr; // [N]
     int pg_cap = 0;       // surfels allocated in Pg / dop
+    float *gh = nullptr;  // per hit-record slot: dL/d(weight) accumulated over the bounces
+    long long gh_cap = 0;
     long long device_bytes = 0;
     RaysDev rays() const {
         RaysDev r;
@@ -309,6 +378,7 @@ struct rgs_transport {
         r.rec_g = rec_g;
         r.warp_base = warp_base;
         r.cnt = cnt;
+        r.dir = dir;
         return r;
     }
     size_t arr() const { return (size_t)n * C * nc; }

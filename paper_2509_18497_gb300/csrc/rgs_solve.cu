@@ -9,7 +9,7 @@
 
 namespace {
 
-constexpr int BOUNCE_THREADS = 128;
+constexpr int BOUNCE_THREADS = 256;
 
 // internal [N][C][NC] <- user [N][nc][3] emission broadcast over the columns, plus D
 template <int NC>
@@ -41,23 +41,30 @@ template <int NC, int CT>
 __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev rays, int C, const float *__restrict__ Bin,
                                                           const float *__restrict__ S, float *__restrict__ Qout,
                                                           float *__restrict__ Bout, double *norm2) {
+    using SL = Slice<NC>;
+    constexpr int G = SL::G, KPL = SL::KPL, GROUPS = BOUNCE_THREADS / G;
     const int i = blockIdx.x;
     const int col0 = blockIdx.y * CT;
     const int nd = rays.nd;
-    const float3 tu = f3(sc.FU[i]), tv = f3(sc.FV[i]), n = f3(sc.N4[i]);
-    const int uid = sc.uid[i];
-    float acc[NC][CT];
+    const int grp = threadIdx.x / G, g = threadIdx.x % G;
+    const float3 n = f3(sc.N4[i]);
+    float acc[KPL][CT];
 #pragma unroll
-    for (int k = 0; k < NC; ++k)
+    for (int m = 0; m < KPL; ++m)
 #pragma unroll
-        for (int c = 0; c < CT; ++c) acc[k][c] = 0.f;
+        for (int c = 0; c < CT; ++c) acc[m][c] = 0.f;
 
-    for (int q = threadIdx.x; q < nd; q += BOUNCE_THREADS) {
-        const float3 d = ray_dir(rays.seed, uid, q, rays.na, rays.nbs, tu, tv, n);
-        float Yo[NC], Yi[NC];
-        sh_eval<NC>(neg3(d), Yo);
-        sh_eval<NC>(reflect_n(n, d), Yi);
+    for (int q = grp; q < nd; q += GROUPS) {
         const long long r = (long long)i * nd + q;
+        const float3 d = f3(rays.dir[r]);
+        float yo[KPL], yi[KPL];
+        {
+            float Y[NC];
+            sh_eval<NC>(neg3(d), Y);
+            SL::pick(Y, g, yo);
+            sh_eval<NC>(reflect_n(n, d), Y);
+            SL::pick(Y, g, yi);
+        }
         const int cnt = rays.cnt[r];
         const long long base = rays.warp_base[r >> 5] + (r & 31);
         float x[CT];
@@ -69,36 +76,41 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev 
             const float *Bj = Bin + ((size_t)ja.x * C + col0) * NC;
 #pragma unroll
             for (int c = 0; c < CT; ++c) {
+                float v[KPL];
+                SL::load(Bj + c * NC, g, v);
                 float s = 0.f;
 #pragma unroll
-                for (int k = 0; k < NC; ++k) s += Yo[k] * __ldg(&Bj[c * NC + k]);
+                for (int m = 0; m < KPL; ++m) s += yo[m] * v[m];
                 x[c] += a * s;
             }
         }
 #pragma unroll
-        for (int k = 0; k < NC; ++k)
+        for (int c = 0; c < CT; ++c) {
+            const float xc = SL::group_sum(x[c]);
 #pragma unroll
-            for (int c = 0; c < CT; ++c) acc[k][c] += Yi[k] * x[c];
+            for (int m = 0; m < KPL; ++m) acc[m][c] += yi[m] * xc;
+        }
     }
-    // CTA reduction of acc
-    __shared__ float red[BOUNCE_THREADS / 32][NC * CT];
+    // reduce over the groups: lanes with equal g within the warp, then across warps
+    __shared__ float red[BOUNCE_THREADS / 32][G][KPL * CT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < NC; ++k)
+    for (int m = 0; m < KPL; ++m)
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
-            float v = acc[k][c];
+            float v = acc[m][c];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) red[warp][k * CT + c] = v;
+            for (int off = G; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane < G) red[warp][lane][m * CT + c] = v;
         }
     __syncthreads();
     double dsq = 0.0;
     const float w = 3.14159265358979f / (float)nd;
     for (int e = threadIdx.x; e < NC * CT; e += BOUNCE_THREADS) {
-        float v = 0.f;
-        for (int q = 0; q < BOUNCE_THREADS / 32; ++q) v += red[q][e];
         const int k = e / CT, c = e - k * CT;
+        const int gg = SL::VEC ? k / 4 : k % G, mm = SL::VEC ? k % 4 : k / G;
+        float v = 0.f;
+        for (int q = 0; q < BOUNCE_THREADS / 32; ++q) v += red[q][gg][mm * CT + c];
         const int col = col0 + c;
         const float Q = w * v;
         const size_t idx = ((size_t)i * C + col) * NC + k;

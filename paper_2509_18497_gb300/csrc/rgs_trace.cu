@@ -12,93 +12,89 @@
 
 namespace {
 
-__global__ void __launch_bounds__(128) k_trace_hemi(SceneDev sc, RaysDev rays, int n_rays, long long cap_slots,
-                                                    unsigned long long *counter, int2 *rec_ja, float *rec_g,
-                                                    long long *warp_base, int *cnt_out, int *flags) {
+// Hits are kept as one 64-bit key each, (bits of t) << 32 | j: t > 0, so the unsigned
+// key order is the depth order and ties of exactly equal t fall back to the internal index
+// (such ties are always re-ordered inside their run below).
+__global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays, int n_rays, long long cap_slots,
+                                                       unsigned long long *counter, int2 *rec_ja, float *rec_g,
+                                                       long long *warp_base, int *cnt_out, float4 *dir_out,
+                                                       int *src_cnt, int *flags) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps only (n_rays % 32 == 0)
     const int lane = threadIdx.x & 31;
     const int i = r / rays.nd, q = r - i * rays.nd;
-    const float4 Pi = sc.P[i];
-    const float3 o = f3(Pi);
+    const float3 o = f3(sc.P[i]);
     const float3 d = ray_dir(rays.seed, sc.uid[i], q, rays.na, rays.nbs, f3(sc.FU[i]), f3(sc.FV[i]), f3(sc.N4[i]));
+    dir_out[r] = make_float4(d.x, d.y, d.z, 0.f);
     const float eps = *sc.eps_plane;
 
-    float ht[RGS_HMAX];
-    int hj[RGS_HMAX];
-    float hg[RGS_HMAX];
+    unsigned long long key[RGS_HMAX];
     int H = 0;
     bool full = false;
     auto visit = [&](int j) {
-        float t, g;
-        if (!hit_surfel(sc, j, i, o, d, INFINITY, eps, t, g)) return;
+        float t, r2;
+        if (!hit_surfel_t(sc, j, i, o, d, INFINITY, eps, t, r2)) return;
+        const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)j;
         if (H < RGS_HMAX) {
-            ht[H] = t;
-            hj[H] = j;
-            hg[H] = g;
-            ++H;
+            key[H++] = k;
             return;
         }
         full = true; // keep the RGS_HMAX nearest: replace the farthest if this one is nearer
         int far = 0;
         for (int m = 1; m < RGS_HMAX; ++m)
-            if (ht[m] > ht[far]) far = m;
-        if (t < ht[far]) {
-            ht[far] = t;
-            hj[far] = j;
-            hg[far] = g;
-        }
+            if (key[m] > key[far]) far = m;
+        if (k < key[far]) key[far] = k;
     };
     bool ok = bvh_traverse(sc, o, d, INFINITY, visit);
     if (!ok) atomicAdd(&flags[FLAG_STACK], 1);
-    if (full) atomicAdd(&flags[FLAG_FULL_RAYS], 1);
 
-    // depth order with caller-index tie break, then runs of near-equal depth by caller index
-    for (int a = 1; a < H; ++a) {
-        float t = ht[a];
-        int j = hj[a];
-        float g = hg[a];
-        int uj = sc.uid[j];
+    for (int a = 1; a < H; ++a) { // insertion sort by key
+        const unsigned long long k = key[a];
         int b = a - 1;
-        while (b >= 0 && (ht[b] > t || (ht[b] == t && sc.uid[hj[b]] > uj))) {
-            ht[b + 1] = ht[b];
-            hj[b + 1] = hj[b];
-            hg[b + 1] = hg[b];
+        while (b >= 0 && key[b] > k) {
+            key[b + 1] = key[b];
             --b;
         }
-        ht[b + 1] = t;
-        hj[b + 1] = j;
-        hg[b + 1] = g;
+        key[b + 1] = k;
     }
-    for (int k = 0; k < H;) {
-        int e = k;
-        while (e + 1 < H && ht[e + 1] - ht[e] <= 1e-6f * fmaxf(1.f, ht[e])) ++e;
-        for (int a = k + 1; a <= e; ++a) { // insertion sort of the run by caller index
-            int j = hj[a];
-            float g = hg[a];
-            int uj = sc.uid[j];
+    // runs of near-equal depth are ordered by caller index (the tie rule)
+    for (int k0 = 0; k0 < H;) {
+        int e = k0;
+        float te = __uint_as_float((unsigned)(key[e] >> 32));
+        while (e + 1 < H) {
+            const float tn = __uint_as_float((unsigned)(key[e + 1] >> 32));
+            if (tn - te > 1e-6f * fmaxf(1.f, te)) break;
+            ++e;
+            te = tn;
+        }
+        for (int a = k0 + 1; a <= e; ++a) {
+            const unsigned long long k = key[a];
+            const int uk = sc.uid[(int)(unsigned)k];
             int b = a - 1;
-            while (b >= k && sc.uid[hj[b]] > uj) {
-                hj[b + 1] = hj[b];
-                hg[b + 1] = hg[b];
+            while (b >= k0 && sc.uid[(int)(unsigned)key[b]] > uk) {
+                key[b + 1] = key[b];
                 --b;
             }
-            hj[b + 1] = j;
-            hg[b + 1] = g;
+            key[b + 1] = k;
         }
-        k = e + 1;
+        k0 = e + 1;
     }
     // composite: a_h = alpha_h prod_{k<h} (1 - alpha_k); stop below RGS_T_EPS
-    float T = 1.f;
     int kept = 0;
-    for (; kept < H; ++kept) {
-        if (T < RGS_T_EPS) break;
-        const float alpha = __ldg(&sc.P[hj[kept]].w) * hg[kept];
-        ht[kept] = alpha * T; // reuse ht for the weights
-        T *= (1.f - alpha);
+    {
+        float T = 1.f;
+        for (; kept < H; ++kept) {
+            if (T < RGS_T_EPS) break;
+            T *= 1.f - __ldg(&sc.P[(int)(unsigned)key[kept]].w) *
+                           surfel_G(sc, surfel_r2(sc, (int)(unsigned)key[kept], o, d,
+                                                  __uint_as_float((unsigned)(key[kept] >> 32))));
+        }
+        // a full buffer only loses something if the transmittance is still above the cut
+        // after its last (nearest-kept) hit
+        if (full && kept == H && T >= RGS_T_EPS) atomicAdd(&flags[FLAG_FULL_RAYS], 1);
     }
     // warp allocation of kept-count rows
-    int rows = __reduce_max_sync(0xffffffffu, kept);
+    const int rows = __reduce_max_sync(0xffffffffu, kept);
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(counter, (unsigned long long)rows * 32ull);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -109,10 +105,16 @@ __global__ void __launch_bounds__(128) k_trace_hemi(SceneDev sc, RaysDev rays, i
     }
     cnt_out[r] = fits ? kept : 0;
     if (!fits) return;
+    float T = 1.f;
     for (int h = 0; h < kept; ++h) {
-        size_t s = base + (size_t)h * 32 + lane;
-        rec_ja[s] = make_int2(hj[h], __float_as_int(ht[h]));
-        rec_g[s] = hg[h];
+        const int j = (int)(unsigned)key[h];
+        const float G = surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[h] >> 32))));
+        const float alpha = __ldg(&sc.P[j].w) * G;
+        const size_t s = base + (size_t)h * 32 + lane;
+        rec_ja[s] = make_int2(j, __float_as_int(alpha * T));
+        rec_g[s] = G;
+        T *= 1.f - alpha;
+        atomicAdd(&src_cnt[j], 1); // transposed-index histogram
     }
 }
 
@@ -148,14 +150,6 @@ __global__ void k_direct(SceneDev sc, int nl, const float *__restrict__ lpos, co
         const float I = lint[3 * lt + ch];
         for (int k = 0; k < NC; ++k) Dout[ch * NC + k] = sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch] * Y[k] * I * pre;
     }
-}
-
-__global__ void k_src_count(RaysDev rays, int n_rays, int *src_cnt) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
-    const long long base = rays.warp_base[r >> 5];
-    const int c = rays.cnt[r], lane = r & 31;
-    for (int h = 0; h < c; ++h) atomicAdd(&src_cnt[rays.rec_ja[base + (long long)h * 32 + lane].x], 1);
 }
 
 __global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr) {
@@ -211,6 +205,8 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
     // per-ray / per-surfel arrays
     if (n_rays > t->rays_cap) {
         if ((r = dev_alloc(&t->cnt, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->dir, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->dy, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->warp_base, (size_t)(n_rays / 32), &t->device_bytes)) != RGS_OK) return r;
         t->rays_cap = n_rays;
     }
@@ -242,11 +238,12 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         }
         RGS_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
         RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));
+        RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
         RaysDev rd = t->rays();
         const int TB = 128;
         { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter,
                                                                         t->rec_ja, t->rec_g, t->warp_base, t->cnt,
-                                                                        t->flags); }
+                                                                        t->dir, t->src_cnt, t->flags); }
         RGS_LAUNCH("trace_hemi");
         unsigned long long used = 0;
         int flags[FLAG_COUNT];
@@ -283,9 +280,6 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
 
     // transposed index: records grouped by source surfel
     RaysDev rd = t->rays();
-    RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
-    { ProfScope ps_("k_src_count", st); k_src_count<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->src_cnt); }
-    RGS_LAUNCH("src_count");
     if ((r = rgs_scan_counts(t->src_cnt, t->src_off, n, t->scan_tmp, t->scan_tmp_cap, st)) != RGS_OK) return r;
     long long total = 0;
     RGS_CUDA(cudaMemcpyAsync(&total, t->src_off + n, sizeof total, cudaMemcpyDeviceToHost, st));
