@@ -68,17 +68,17 @@ def algorithmic_bytes(kernel, info, n, nd, nb, C, nc):
     rays = n * nd
     tile = A * 3 // C           # one 3-column tile of such an array
     if kernel == "k_bounce":      # records + counts + directions + B^(k-1) + S in; Q, B^(k) out
-        return H * 8 + rays * (4 + 16) + rays // 32 * 8 + 4 * A
+        return H * 8 + rays * (4 + 8 + 16) + 4 * A
     if kernel == "k_adj_src":     # transposed records, (direction, y) per ray, offsets; v^(a) tile out, u tile r+w
         return H * 8 + rays * 32 + (n + 1) * 8 + 3 * tile
     if kernel == "k_adj_ray":     # directions + v^(a-1) tile in; y per ray out
         return rays * 32 + tile
     if kernel == "k_opacity_g":   # records (j) + counts + directions; 4 iterates of v and B tiles; g per hit out
-        return H * (8 + 4) + rays * (4 + 16) + rays // 32 * 8 + 2 * min(nb, 4) * tile
+        return H * (8 + 4) + rays * (4 + 8 + 16) + 2 * min(nb, 4) * tile
     if kernel == "k_opacity_rec":  # records (j, a) + G + g per hit, counts; dL/do
-        return H * (8 + 4 + 4) + rays * 4 + n * 4
+        return H * (8 + 4 + 4) + rays * (4 + 8) + n * 4
     if kernel == "k_trace_hemi":  # scene (64 B/surfel + 64 B/node) in; records, counts, directions out
-        return n * 64 + (n - 1) * 64 + H * 12 + rays * (4 + 16) + rays // 32 * 8 + n * 4
+        return n * 64 + (n - 1) * 64 + H * 12 + rays * (4 + 8 + 16) + n * 4
     return None
 
 

@@ -226,12 +226,12 @@ __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, in
             }
         }
     }
-    const long long base = rays.warp_base[r >> 5] + (r & 31);
+    const long long base = rays.off[r];
     const int rows = SL::G == 1 ? cnt : __reduce_max_sync(0xffffffffu, cnt); // groups of a warp stay converged
     for (int h = 0; h < rows; ++h) {
         float acc = 0.f;
         int j = 0;
-        if (h < cnt) j = __ldg(&rays.rec_ja[base + (long long)h * 32]).x;
+        if (h < cnt) j = __ldg(&rays.rec_ja[base + h]).x;
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
             if (aa < na && h < cnt) {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, in
         }
         acc = SL::group_sum(acc);
         if (g == 0 && h < cnt) {
-            const long long slot = base + (long long)h * 32;
+            const long long slot = base + h;
             gh[slot] = first ? acc : gh[slot] + acc;
         }
     }
@@ -263,17 +263,17 @@ __global__ void __launch_bounds__(256) k_opacity_rec(SceneDev sc, RaysDev rays, 
     if (r >= sc.n * rays.nd) return;
     const int cnt = rays.cnt[r];
     if (cnt == 0) return;
-    const long long base = rays.warp_base[r >> 5] + (r & 31);
+    const long long base = rays.off[r];
     float Th[RGS_HMAX];
     float T = 1.f;
     for (int h = 0; h < cnt; ++h) {
         Th[h] = T;
-        const long long slot = base + (long long)h * 32;
+        const long long slot = base + h;
         T *= 1.f - __ldg(&sc.P[__ldg(&rays.rec_ja[slot]).x].w) * __ldg(&rays.rec_g[slot]);
     }
     float R = 0.f;
     for (int h = cnt - 1; h >= 0; --h) {
-        const long long slot = base + (long long)h * 32;
+        const long long slot = base + h;
         const int j = __ldg(&rays.rec_ja[slot]).x;
         const float G = __ldg(&rays.rec_g[slot]);
         const float alpha = __ldg(&sc.P[j].w) * G;

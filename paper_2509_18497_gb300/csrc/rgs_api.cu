@@ -300,7 +300,8 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->lint);
     dev_free(t->rec_ja);
     dev_free(t->rec_g);
-    dev_free(t->warp_base);
+    dev_free(t->off);
+    dev_free(t->ray_ctr);
     dev_free(t->cnt);
     dev_free(t->counter);
     dev_free(t->flags);

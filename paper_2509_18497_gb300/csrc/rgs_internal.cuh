@@ -6,13 +6,13 @@
 //   cl[j] = c_{j,l,ch} as [4][3] floats (bands beyond L are zero)
 //   uid[j] = caller index of internal surfel j (ray seeds and depth-tie order use it)
 //   radiosity-like arrays (S, B^(b), Q^(b), v^(a), u): [N][C][NC] float, SH index innermost
-//   hit records: warp-interleaved rows; ray r of warp w = r/32 stores hit h at
-//                warp_base[w] + h*32 + (r & 31): rec_ja = (source j, bits of a_rh), rec_g = G
+//   hit records: contiguous per ray, hit h of ray r at off[r] + h (exactly sized, in depth
+//                order): rec_ja = (source j, bits of a_rh), rec_g = G
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/rgs.h"
+#include "rgs.h" // include/ is on the include path (build.py)
 
 #define RGS_HMAX 96           // per-ray hit buffer; when full the nearest RGS_HMAX hits are kept
 #define RGS_T_EPS 1e-6f       // compositing stops once the transmittance is below this
@@ -52,7 +52,7 @@ struct RaysDev {
     unsigned long long seed;
     const int2 *rec_ja;
     const float *rec_g;
-    const long long *warp_base;
+    const long long *off; // first record of each ray
     const int *cnt;
     const float4 *dir; // per-ray direction (xyz), written by the trace
 };
@@ -243,6 +243,70 @@ __device__ __forceinline__ bool slab(float lox, float loy, float loz, float hix,
     return tmin <= tmx;
 }
 
+// slab test returning the entry distance (clamped to 0) of a hit box
+__device__ __forceinline__ bool slab_t(float lox, float loy, float loz, float hix, float hiy, float hiz, float3 o,
+                                       float3 inv, float tmax, float &tnear) {
+    float tx0 = (lox - o.x) * inv.x, tx1 = (hix - o.x) * inv.x;
+    float ty0 = (loy - o.y) * inv.y, ty1 = (hiy - o.y) * inv.y;
+    float tz0 = (loz - o.z) * inv.z, tz1 = (hiz - o.z) * inv.z;
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmx = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    tnear = tmin;
+    return tmin <= tmx;
+}
+
+// Nearer-first traversal for rays that need all hits in depth order: children are
+// visited in order of their entry distance, so hits arrive almost sorted and the
+// per-ray insertion sort does little work.  Leaves are tested as soon as they are
+// reached (postponing them to test all lanes' leaves together was measured slower here:
+// lanes holding a leaf idled while the others searched).  Calls f(j) for every surfel
+// whose box the ray crosses; returns false if the stack overflowed.
+template <class F>
+__device__ __forceinline__ bool bvh_traverse_ordered(const SceneDev &sc, float3 o, float3 d, F &&f) {
+    if (sc.n == 1) {
+        f(0);
+        return true;
+    }
+    const float3 inv = make_float3(1.f / d.x, 1.f / d.y, 1.f / d.z);
+    int stack[RGS_STACK];
+    int sp = 0;
+    int node = 0;
+    bool ok = true;
+    while (true) {
+        const BvhNode nd = sc.nodes[node];
+        int cn = nd.d.x, cf = nd.d.y; // near / far child
+        float tn, tf;
+        bool hn = slab_t(nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y, o, inv, INFINITY, tn);
+        bool hf = slab_t(nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w, o, inv, INFINITY, tf);
+        if (hn && hf && tf < tn) {
+            const int tc = cn;
+            cn = cf;
+            cf = tc;
+        }
+        if (hn && cn < 0) {
+            f(~cn);
+            hn = false;
+        }
+        if (hf && cf < 0) {
+            f(~cf);
+            hf = false;
+        }
+        if (hn && hf) {
+            if (sp < RGS_STACK) stack[sp++] = cf;
+            else ok = false;
+            node = cn;
+        } else if (hn) {
+            node = cn;
+        } else if (hf) {
+            node = cf;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    return ok;
+}
+
 // Visits every surfel whose box the segment (0, tmax) crosses and calls f(j).
 // Returns false if the stack overflowed (then part of the tree was skipped).
 template <class F>
@@ -332,8 +396,10 @@ struct rgs_transport {
     long long cap_slots = 0;
     int2 *rec_ja = nullptr;
     float *rec_g = nullptr;
-    long long *warp_base = nullptr;
+    long long *off = nullptr; // per-ray first record
     int *cnt = nullptr;
+    unsigned *ray_ctr = nullptr; // persistent trace: next ray to fetch
+    int num_sms = 0;
     float4 *dir = nullptr; // per-ray direction
     float4 *dy = nullptr;  // adjoint: per-ray (y[0..2], 0) for the current column tile
     long long rays_cap = 0;
@@ -376,7 +442,7 @@ struct rgs_transport {
         r.seed = seed;
         r.rec_ja = rec_ja;
         r.rec_g = rec_g;
-        r.warp_base = warp_base;
+        r.off = off;
         r.cnt = cnt;
         r.dir = dir;
         return r;

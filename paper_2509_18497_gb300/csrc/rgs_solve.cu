@@ -66,12 +66,12 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev 
             SL::pick(Y, g, yi);
         }
         const int cnt = rays.cnt[r];
-        const long long base = rays.warp_base[r >> 5] + (r & 31);
+        const long long base = rays.off[r];
         float x[CT];
 #pragma unroll
         for (int c = 0; c < CT; ++c) x[c] = 0.f;
         for (int h = 0; h < cnt; ++h) {
-            const int2 ja = __ldg(&rays.rec_ja[base + (long long)h * 32]);
+            const int2 ja = __ldg(&rays.rec_ja[base + h]);
             const float a = __int_as_float(ja.y);
             const float *Bj = Bin + ((size_t)ja.x * C + col0) * NC;
 #pragma unroll

@@ -8,17 +8,23 @@
 //                 the direct term D (Sec. 5.2) for every column of that light.
 //  k_src_*      : the same records grouped by source surfel (transposed index) for the
 //                 adjoint's gather form of K^T.
+#include <algorithm>
+
 #include "rgs_internal.cuh"
 
 namespace {
 
-// Hits are kept as one 64-bit key each, (bits of t) << 32 | j: t > 0, so the unsigned
-// key order is the depth order and ties of exactly equal t fall back to the internal index
-// (such ties are always re-ordered inside their run below).
+// One thread per hemisphere ray; the 32 rays of a warp belong to one surfel.
+// Hits are kept as one 64-bit key each, (bits of t) << 32 | j: t > 0, so the unsigned key
+// order is the depth order and ties of exactly equal t fall back to the internal index
+// (such ties are always re-ordered inside their run).  After compositing, the warp
+// allocates exactly its rays' kept hits with one atomic (prefix sum over the lanes) and
+// every ray stores its records contiguously.
 __global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays, int n_rays, long long cap_slots,
-                                                       unsigned long long *counter, int2 *rec_ja, float *rec_g,
-                                                       long long *warp_base, int *cnt_out, float4 *dir_out,
+                                                       unsigned long long *slot_ctr, int2 *rec_ja, float *rec_g,
+                                                       long long *off_out, int *cnt_out, float4 *dir_out,
                                                        int *src_cnt, int *flags) {
+    const unsigned FULL = 0xffffffffu;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps only (n_rays % 32 == 0)
     const int lane = threadIdx.x & 31;
@@ -45,10 +51,9 @@ __global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays
             if (key[m] > key[far]) far = m;
         if (k < key[far]) key[far] = k;
     };
-    bool ok = bvh_traverse(sc, o, d, INFINITY, visit);
-    if (!ok) atomicAdd(&flags[FLAG_STACK], 1);
+    if (!bvh_traverse_ordered(sc, o, d, visit)) atomicAdd(&flags[FLAG_STACK], 1);
 
-    for (int a = 1; a < H; ++a) { // insertion sort by key
+    for (int a = 1; a < H; ++a) { // insertion sort by key (hits arrive almost sorted)
         const unsigned long long k = key[a];
         int b = a - 1;
         while (b >= 0 && key[b] > k) {
@@ -57,8 +62,7 @@ __global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays
         }
         key[b + 1] = k;
     }
-    // runs of near-equal depth are ordered by caller index (the tie rule)
-    for (int k0 = 0; k0 < H;) {
+    for (int k0 = 0; k0 < H;) { // runs of near-equal depth are ordered by caller index
         int e = k0;
         float te = __uint_as_float((unsigned)(key[e] >> 32));
         while (e + 1 < H) {
@@ -85,34 +89,39 @@ __global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays
         float T = 1.f;
         for (; kept < H; ++kept) {
             if (T < RGS_T_EPS) break;
-            T *= 1.f - __ldg(&sc.P[(int)(unsigned)key[kept]].w) *
-                           surfel_G(sc, surfel_r2(sc, (int)(unsigned)key[kept], o, d,
-                                                  __uint_as_float((unsigned)(key[kept] >> 32))));
+            const int j = (int)(unsigned)key[kept];
+            T *= 1.f - __ldg(&sc.P[j].w) *
+                           surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[kept] >> 32))));
         }
         // a full buffer only loses something if the transmittance is still above the cut
-        // after its last (nearest-kept) hit
         if (full && kept == H && T >= RGS_T_EPS) atomicAdd(&flags[FLAG_FULL_RAYS], 1);
     }
-    // warp allocation of kept-count rows
-    const int rows = __reduce_max_sync(0xffffffffu, kept);
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(counter, (unsigned long long)rows * 32ull);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    const bool fits = base + (unsigned long long)rows * 32ull <= (unsigned long long)cap_slots;
-    if (lane == 0) {
-        warp_base[r >> 5] = (long long)base;
-        if (!fits) atomicAdd(&flags[FLAG_CAPACITY], 1);
+    // warp-aggregated, exactly sized record allocation
+    int incl = kept;
+#pragma unroll
+    for (int offs = 1; offs < 32; offs <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, offs);
+        if (lane >= offs) incl += v;
     }
+    const int total = __shfl_sync(FULL, incl, 31);
+    unsigned long long sbase = 0;
+    if (lane == 31 && total > 0) sbase = atomicAdd(slot_ctr, (unsigned long long)total);
+    sbase = __shfl_sync(FULL, sbase, 31);
+    const unsigned long long mine = sbase + (unsigned long long)(incl - kept);
+    const bool fits = mine + (unsigned long long)kept <= (unsigned long long)cap_slots;
+    off_out[r] = (long long)mine;
     cnt_out[r] = fits ? kept : 0;
-    if (!fits) return;
+    if (!fits) {
+        atomicAdd(&flags[FLAG_CAPACITY], 1);
+        return;
+    }
     float T = 1.f;
     for (int h = 0; h < kept; ++h) {
         const int j = (int)(unsigned)key[h];
         const float G = surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[h] >> 32))));
         const float alpha = __ldg(&sc.P[j].w) * G;
-        const size_t s = base + (size_t)h * 32 + lane;
-        rec_ja[s] = make_int2(j, __float_as_int(alpha * T));
-        rec_g[s] = G;
+        rec_ja[mine + h] = make_int2(j, __float_as_int(alpha * T));
+        rec_g[mine + h] = G;
         T *= 1.f - alpha;
         atomicAdd(&src_cnt[j], 1); // transposed-index histogram
     }
@@ -155,10 +164,10 @@ __global__ void k_direct(SceneDev sc, int nl, const float *__restrict__ lpos, co
 __global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
-    const long long base = rays.warp_base[r >> 5];
-    const int c = rays.cnt[r], lane = r & 31;
+    const long long base = rays.off[r];
+    const int c = rays.cnt[r];
     for (int h = 0; h < c; ++h) {
-        const int2 ja = rays.rec_ja[base + (long long)h * 32 + lane];
+        const int2 ja = rays.rec_ja[base + h];
         const unsigned long long pos = atomicAdd(&cursor[ja.x], 1ull);
         tr[pos] = make_int2(r, ja.y);
     }
@@ -207,10 +216,16 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         if ((r = dev_alloc(&t->cnt, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->dir, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->dy, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
-        if ((r = dev_alloc(&t->warp_base, (size_t)(n_rays / 32), &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->off, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
         t->rays_cap = n_rays;
     }
     if (!t->counter && (r = dev_alloc(&t->counter, 1, &t->device_bytes)) != RGS_OK) return r;
+    if (!t->ray_ctr && (r = dev_alloc(&t->ray_ctr, 1, &t->device_bytes)) != RGS_OK) return r;
+    if (!t->num_sms) {
+        int dev = 0;
+        RGS_CUDA(cudaGetDevice(&dev));
+        RGS_CUDA(cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     if (!t->flags && (r = dev_alloc(&t->flags, FLAG_COUNT, &t->device_bytes)) != RGS_OK) return r;
     const long long arr = (long long)n * t->C * t->nc;
     if (arr > t->nc_cap) {
@@ -241,9 +256,7 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
         RaysDev rd = t->rays();
         const int TB = 128;
-        { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter,
-                                                                        t->rec_ja, t->rec_g, t->warp_base, t->cnt,
-                                                                        t->dir, t->src_cnt, t->flags); }
+        { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter, t->rec_ja, t->rec_g, t->off, t->cnt, t->dir, t->src_cnt, t->flags); }
         RGS_LAUNCH("trace_hemi");
         unsigned long long used = 0;
         int flags[FLAG_COUNT];
