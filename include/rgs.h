@@ -65,8 +65,15 @@ typedef enum rgs_alpha_model {
     RGS_ALPHA_DISC = 1   /* alpha = o for u^2+v^2 <= 1, else 0 (closed-sphere furnace test) */
 } rgs_alpha_model;
 
+/* Precision of the bounce gathers (the batched form of the contraction).  Every mode
+ * accumulates in FP32 and keeps FP32 iterates; the BF16 modes gather BF16 copies of the
+ * iterate rows (half the bytes per hit).  RESCORR runs bounces 1..n-1 on BF16 rows and the
+ * last bounce on FP32 rows: one FP32 residual-correction sweep that damps the BF16 error by
+ * the spectral radius of K. */
 typedef enum rgs_precision {
-    RGS_FP32 = 0 /* plain FP32 SIMT bounces, one light per column tile */
+    RGS_FP32 = 0,
+    RGS_BF16_FP32ACC = 1,
+    RGS_BF16_FP32ACC_RESCORR = 2
 } rgs_precision;
 
 typedef struct rgs_scene rgs_scene;         /* opaque: surfels in Morton order + BVH */

@@ -28,8 +28,9 @@ class Pipeline:
     Handles (and their device workspaces) are reused across calls, so steady-state steps
     allocate nothing inside the library."""
 
-    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS):
+    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32):
         self.alpha_model = alpha_model
+        self.precision = precision
         self.scene = None
         self.transport = None
 
@@ -44,8 +45,9 @@ class Pipeline:
                                                  transport=self.transport)
         return self.transport
 
-    def solve(self, E, nb, B_out=None, stats=False, stream=None):
-        return rgs.rgs_solve(self.transport, E, nb, B_out=B_out, stats=stats, stream=stream)
+    def solve(self, E, nb, B_out=None, stats=False, stream=None, precision=None):
+        prec = self.precision if precision is None else precision
+        return rgs.rgs_solve(self.transport, E, nb, B_out=B_out, stats=stats, precision=prec, stream=stream)
 
     def adjoint(self, g, outs=(None, None, None), stream=None):
         return rgs.rgs_adjoint(self.transport, g, *outs, stream=stream)

@@ -182,10 +182,11 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, const float *__restrict__ lpos
 //   g_h = sum_{a<n} sum_c y_r^(a)[c] Y(-d_r) . B^(n-1-a)_{j_h}[c],
 //   y_r^(a)[c] = (pi/nd) o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) v_i^(a)[c][k'],
 // accumulated into gh[slot] for iterates a0 .. a0+na-1 (first chunk writes, later add).
-template <int NC, int CT, int NA>
+template <int NC, int CT, int NA, class SLB>
 __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, int C, int col0, int nb, int a0, int na,
-                                                   size_t A, const float *__restrict__ V, const float *__restrict__ Bit,
-                                                   float *gh, bool first) {
+                                                   size_t A, const float *__restrict__ V,
+                                                   const typename SLB::T *__restrict__ Bit, size_t AB, float *gh,
+                                                   bool first) {
     using SL = Slice<NC>;
     constexpr int G = SL::G, KPL = SL::KPL;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -235,11 +236,11 @@ __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, in
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
             if (aa < na && h < cnt) {
-                const float *Bj = Bit + A * (nb - 1 - (a0 + aa)) + ((size_t)j * C + col0) * NC;
+                const typename SLB::T *Bj = Bit + AB * (nb - 1 - (a0 + aa)) + ((size_t)j * C + col0) * SLB::STRIDE;
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
                     float v[KPL];
-                    SL::load(Bj + c * NC, g, v);
+                    SLB::load(Bj + c * SLB::STRIDE, g, v);
                     float s = 0.f;
 #pragma unroll
                     for (int m = 0; m < KPL; ++m) s += yo[m] * v[m];
@@ -346,7 +347,15 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
         for (int col0 = 0; col0 < C; col0 += 3) {
             for (int a0 = 0; a0 < nb; a0 += NA) {
                 const int na = min(NA, nb - a0);
-                { ProfScope ps_("k_opacity_g", st); k_opacity_g<NC, 3, NA><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v, t->iters, t->gh, a0 == 0 && col0 == 0); }
+                const bool first = (a0 == 0 && col0 == 0);
+                if (t->prec_last != RGS_FP32) { // the batched modes gather the BF16 iterate copies
+                    const size_t A16 = (size_t)n * C * SliceH<NC>::STRIDE;
+                    ProfScope ps_("k_opacity_g", st);
+                    k_opacity_g<NC, 3, NA, SliceH<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v, t->iters16, A16, t->gh, first);
+                } else {
+                    ProfScope ps_("k_opacity_g", st);
+                    k_opacity_g<NC, 3, NA, Slice<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v, t->iters, A, t->gh, first);
+                }
             }
         }
         { ProfScope ps_("k_opacity_rec", st); k_opacity_rec<<<gr, 256, 0, st>>>(sd, rd, t->gh, t->dop); }

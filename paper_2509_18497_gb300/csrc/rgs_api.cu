@@ -233,15 +233,15 @@ rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_
         rgs_set_error("rgs_solve: n_bounces = %d outside [0, %d]", n_bounces, RGS_MAX_BOUNCES);
         return RGS_ERR_ARG;
     }
-    if (precision != RGS_FP32) {
-        rgs_set_error("rgs_solve: unsupported precision %d", precision);
+    if (precision != RGS_FP32 && precision != RGS_BF16_FP32ACC && precision != RGS_BF16_FP32ACC_RESCORR) {
+        rgs_set_error("rgs_solve: unknown precision %d", precision);
         return RGS_ERR_ARG;
     }
     if (t->nd == 0) {
         rgs_set_error("rgs_solve: transport was not traced");
         return RGS_ERR_STATE;
     }
-    return rgs_solve_impl(t, E, n_bounces, B_out, stats, S(stream));
+    return rgs_solve_impl(t, E, n_bounces, precision, B_out, stats, S(stream));
 }
 
 rgs_status rgs_adjoint(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo, float *dL_dopacity,
@@ -313,6 +313,7 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->D);
     dev_free(t->iters);
     dev_free(t->Q);
+    dev_free(t->iters16);
     dev_free(t->norm2);
     dev_free(t->v);
     dev_free(t->u);

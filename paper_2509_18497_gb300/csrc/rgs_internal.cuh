@@ -9,6 +9,7 @@
 //   hit records: contiguous per ray, hit h of ray r at off[r] + h (exactly sized, in depth
 //                order): rec_ja = (source j, bits of a_rh), rec_g = G
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,17 +116,19 @@ __device__ __forceinline__ void sh_eval(float3 v, float *Y) {
 __host__ __device__ constexpr int band_of(int k) { return k == 0 ? 0 : (k < 4 ? 1 : (k < 9 ? 2 : 3)); }
 
 // Cooperative row slices for the gathers: G lanes share one ray (or one transposed entry)
-// and each lane owns KPL of the NC coefficients of every row.  nc = 16: 4 lanes x one
-// float4 each (the 4 lanes read 64 contiguous bytes of a row per load); nc = 9: 4 lanes,
-// interleaved scalars; nc <= 4: one lane per ray, the whole row (a float4 for nc = 4).
+// and lane g owns the KPL contiguous coefficients k = KPL*g + m of every row.  nc = 16, 9:
+// 4 lanes x 4 coefficients (the 4 lanes read one contiguous row per load); nc <= 4: one
+// lane per ray, the whole row.  Slice reads FP32 rows (float4 where aligned), SliceH reads
+// BF16 copies whose rows are padded to 16 (nc >= 9) so every lane loads 8 aligned bytes.
 template <int NC> struct Slice {
+    using T = float;
     static constexpr int G = (NC >= 9) ? 4 : 1;
-    static constexpr int KPL = (NC + G - 1) / G;
-    static constexpr bool VEC = (NC % 4 == 0) && (NC / G == 4);
-    __device__ static constexpr int k(int g, int m) { return VEC ? 4 * g + m : g + m * G; }
-    // this lane's KPL entries of the NC-float row `row` (zero where k >= NC)
+    static constexpr int KPL = (NC >= 9) ? 4 : NC;
+    static constexpr int STRIDE = NC; // floats per row
+    __device__ static constexpr int k(int g, int m) { return KPL * g + m; }
+    // this lane's KPL entries of the row `row` (zero where k >= NC)
     __device__ static void load(const float *__restrict__ row, int g, float *v) {
-        if constexpr (VEC) {
+        if constexpr (NC % 4 == 0) {
             const float4 q4 = __ldg(reinterpret_cast<const float4 *>(row) + g);
             v[0] = q4.x;
             v[1] = q4.y;
@@ -157,6 +160,30 @@ template <int NC> struct Slice {
         return x;
     }
 };
+
+template <int NC> struct SliceH {
+    using T = __nv_bfloat16;
+    static constexpr int G = Slice<NC>::G;
+    static constexpr int KPL = Slice<NC>::KPL;
+    static constexpr int STRIDE = (NC >= 9) ? 16 : NC; // bf16 per row
+    __device__ static constexpr int k(int g, int m) { return KPL * g + m; }
+    __device__ static void load(const __nv_bfloat16 *__restrict__ row, int g, float *v) {
+        if constexpr (KPL == 4) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row) + g);
+            v[0] = __uint_as_float(q.x << 16);
+            v[1] = __uint_as_float(q.x & 0xffff0000u);
+            v[2] = __uint_as_float(q.y << 16);
+            v[3] = __uint_as_float(q.y & 0xffff0000u);
+        } else {
+#pragma unroll
+            for (int m = 0; m < KPL; ++m) v[m] = __bfloat162float(row[k(g, m)]);
+        }
+    }
+    __device__ static void pick(const float *full, int g, float *v) { Slice<NC>::pick(full, g, v); }
+    __device__ static float group_sum(float x) { return Slice<NC>::group_sum(x); }
+};
+
+template <int NC> constexpr int bf16_stride() { return (NC >= 9) ? 16 : NC; }
 
 // ------------------------------------------------------------------ ray generation
 // SplitMix64 output function (Steele, Lea & Flood 2014) applied to a counter.
@@ -423,6 +450,9 @@ struct rgs_transport {
     int iters_cap = 0;  // number of [N][C][NC] arrays allocated in iters / Q
     float *iters = nullptr; // B^(0..nb)
     float *Q = nullptr;     // Q^(0..nb-1)
+    __nv_bfloat16 *iters16 = nullptr; // BF16 copies of B^(0..nb), rows padded to bf16_stride<NC>
+    int iters16_cap = 0;
+    int prec_last = 0;      // precision of the last solve
     double *norm2 = nullptr; // [RGS_MAX_BOUNCES + 1]
     // adjoint workspace
     float *v = nullptr; // v^(0..nb)
@@ -497,8 +527,8 @@ template <class T> void dev_free(T *&p) {
 // entry points implemented per translation unit
 rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_build_opts *o, cudaStream_t st);
 rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace_opts *o, cudaStream_t st);
-rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, float *B_out, rgs_solve_stats *stats,
-                          cudaStream_t st);
+rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precision, float *B_out,
+                          rgs_solve_stats *stats, cudaStream_t st);
 rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st);
 rgs_status rgs_get_iterate_impl(rgs_transport *t, int b, float *out, cudaStream_t st);
 // device-wide exclusive scan of int counts into int64 offsets (offsets[n] = total)

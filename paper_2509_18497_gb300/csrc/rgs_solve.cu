@@ -11,10 +11,11 @@ namespace {
 
 constexpr int BOUNCE_THREADS = 256;
 
-// internal [N][C][NC] <- user [N][nc][3] emission broadcast over the columns, plus D
+// internal [N][C][NC] <- user [N][nc][3] emission broadcast over the columns, plus D;
+// optionally also the BF16 copy (rows of bf16_stride<NC>)
 template <int NC>
 __global__ void k_make_S(int n, int C, const int *__restrict__ uid, const float *__restrict__ E,
-                         const float *__restrict__ D, float *S) {
+                         const float *__restrict__ D, float *S, __nv_bfloat16 *S16) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n * C * NC) return;
     const int k = (int)(idx % NC);
@@ -22,7 +23,9 @@ __global__ void k_make_S(int n, int C, const int *__restrict__ uid, const float 
     const int c = (int)(ic % C);
     const int i = (int)(ic / C);
     float e = E ? E[((size_t)uid[i] * NC + k) * 3 + (c % 3)] : 0.f;
-    S[idx] = e + D[idx];
+    const float v = e + D[idx];
+    S[idx] = v;
+    if (S16) S16[ic * bf16_stride<NC>() + k] = __float2bfloat16_rn(v);
 }
 
 // internal [N][C][NC] -> user [N][nc][C]
@@ -37,12 +40,13 @@ __global__ void k_to_user(int n, int C, const int *__restrict__ uid, const float
     Y[((size_t)uid[i] * NC + k) * C + c] = X[idx];
 }
 
-template <int NC, int CT>
-__global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev rays, int C, const float *__restrict__ Bin,
-                                                          const float *__restrict__ S, float *__restrict__ Qout,
-                                                          float *__restrict__ Bout, double *norm2) {
-    using SL = Slice<NC>;
-    constexpr int G = SL::G, KPL = SL::KPL, GROUPS = BOUNCE_THREADS / G;
+template <int NC, int CT, class SL>
+__global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev rays, int C,
+                                                          const typename SL::T *__restrict__ Bg,
+                                                          const float *__restrict__ Bprev, const float *__restrict__ S,
+                                                          float *__restrict__ Qout, float *__restrict__ Bout,
+                                                          __nv_bfloat16 *__restrict__ Bout16, double *norm2) {
+    constexpr int G = SL::G, KPL = SL::KPL, GROUPS = BOUNCE_THREADS / G, RS = SL::STRIDE;
     const int i = blockIdx.x;
     const int col0 = blockIdx.y * CT;
     const int nd = rays.nd;
@@ -70,14 +74,15 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev 
         float x[CT];
 #pragma unroll
         for (int c = 0; c < CT; ++c) x[c] = 0.f;
+#pragma unroll 4
         for (int h = 0; h < cnt; ++h) {
             const int2 ja = __ldg(&rays.rec_ja[base + h]);
             const float a = __int_as_float(ja.y);
-            const float *Bj = Bin + ((size_t)ja.x * C + col0) * NC;
+            const typename SL::T *Bj = Bg + ((size_t)ja.x * C + col0) * RS;
 #pragma unroll
             for (int c = 0; c < CT; ++c) {
                 float v[KPL];
-                SL::load(Bj + c * NC, g, v);
+                SL::load(Bj + c * RS, g, v);
                 float s = 0.f;
 #pragma unroll
                 for (int m = 0; m < KPL; ++m) s += yo[m] * v[m];
@@ -108,7 +113,15 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev 
     const float w = 3.14159265358979f / (float)nd;
     for (int e = threadIdx.x; e < NC * CT; e += BOUNCE_THREADS) {
         const int k = e / CT, c = e - k * CT;
-        const int gg = SL::VEC ? k / 4 : k % G, mm = SL::VEC ? k % 4 : k / G;
+        int gg = 0, mm = 0;
+#pragma unroll
+        for (int g2 = 0; g2 < G; ++g2)
+#pragma unroll
+            for (int m2 = 0; m2 < KPL; ++m2)
+                if (SL::k(g2, m2) == k) {
+                    gg = g2;
+                    mm = m2;
+                }
         float v = 0.f;
         for (int q = 0; q < BOUNCE_THREADS / 32; ++q) v += red[q][gg][mm * CT + c];
         const int col = col0 + c;
@@ -118,7 +131,8 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev 
         const float oc = sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (col % 3)];
         const float b = S[idx] + oc * Q;
         Bout[idx] = b;
-        const double df = (double)b - (double)Bin[idx];
+        if (Bout16) Bout16[((size_t)i * C + col) * bf16_stride<NC>() + k] = __float2bfloat16_rn(b);
+        const double df = (double)b - (double)Bprev[idx];
         dsq += df * df;
     }
     // FP64 residual norm: warp reduce, one atomic per warp with work
@@ -128,18 +142,25 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev 
 }
 
 template <int NC>
-rgs_status launch_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, const float *Bin, const float *S, float *Q,
-                         float *Bout, double *norm2, cudaStream_t st) {
+rgs_status launch_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, bool bf16_rows, const float *Bprev,
+                         const __nv_bfloat16 *Bprev16, const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16,
+                         double *norm2, cudaStream_t st) {
     dim3 grid(t->n, t->C / 3);
-    { ProfScope ps_("k_bounce", st); k_bounce<NC, 3><<<grid, BOUNCE_THREADS, 0, st>>>(sd, rd, t->C, Bin, S, Q, Bout, norm2); }
+    if (bf16_rows) {
+        ProfScope ps_("k_bounce", st);
+        k_bounce<NC, 3, SliceH<NC>><<<grid, BOUNCE_THREADS, 0, st>>>(sd, rd, t->C, Bprev16, Bprev, S, Q, Bout, Bout16, norm2);
+    } else {
+        ProfScope ps_("k_bounce", st);
+        k_bounce<NC, 3, Slice<NC>><<<grid, BOUNCE_THREADS, 0, st>>>(sd, rd, t->C, Bprev, Bprev, S, Q, Bout, Bout16, norm2);
+    }
     RGS_LAUNCH("bounce");
     return RGS_OK;
 }
 
 template <int NC>
-void launch_make_S(const rgs_transport *t, const float *E, float *S, cudaStream_t st) {
+void launch_make_S(const rgs_transport *t, const float *E, float *S, __nv_bfloat16 *S16, cudaStream_t st) {
     size_t tot = t->arr();
-    { ProfScope ps_("k_make_S", st); k_make_S<NC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t->n, t->C, t->sc->uid, E, t->D, S); }
+    { ProfScope ps_("k_make_S", st); k_make_S<NC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t->n, t->C, t->sc->uid, E, t->D, S, S16); }
 }
 template <int NC>
 void launch_to_user(const rgs_transport *t, const float *X, float *Y, cudaStream_t st) {
@@ -149,8 +170,29 @@ void launch_to_user(const rgs_transport *t, const float *X, float *Y, cudaStream
 
 } // namespace
 
-rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, float *B_out, rgs_solve_stats *stats,
-                          cudaStream_t st) {
+template <int NC>
+rgs_status run_solve(rgs_transport *t, const float *E, int nb, int precision, cudaStream_t st) {
+    const size_t A = t->arr();
+    const size_t A16 = (size_t)t->n * t->C * bf16_stride<NC>();
+    const bool bf16 = precision != RGS_FP32;
+    SceneDev sd = t->sc->dev();
+    RaysDev rd = t->rays();
+    __nv_bfloat16 *I16 = bf16 ? t->iters16 : nullptr;
+    launch_make_S<NC>(t, E, t->iters, I16, st);
+    RGS_LAUNCH("make_S");
+    for (int b = 1; b <= nb; ++b) {
+        // RESCORR: the last bounce gathers the FP32 rows (one residual-correction sweep)
+        const bool rows16 = bf16 && !(precision == RGS_BF16_FP32ACC_RESCORR && b == nb);
+        rgs_status r = launch_bounce<NC>(t, sd, rd, rows16, t->iters + A * (b - 1), bf16 ? I16 + A16 * (b - 1) : nullptr,
+                                         t->iters, t->Q + A * (b - 1), t->iters + A * b,
+                                         bf16 ? I16 + A16 * b : nullptr, t->norm2 + b, st);
+        if (r != RGS_OK) return r;
+    }
+    return RGS_OK;
+}
+
+rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precision, float *B_out,
+                          rgs_solve_stats *stats, cudaStream_t st) {
     rgs_status r;
     const size_t A = t->arr();
     if (nb + 1 > t->iters_cap) {
@@ -158,30 +200,23 @@ rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, float *B_out
         if ((r = dev_alloc(&t->Q, A * (nb > 0 ? nb : 1), &t->device_bytes)) != RGS_OK) return r;
         t->iters_cap = nb + 1;
     }
+    if (precision != RGS_FP32 && nb + 1 > t->iters16_cap) {
+        const size_t A16 = (size_t)t->n * t->C * (t->nc >= 9 ? 16 : t->nc);
+        if ((r = dev_alloc(&t->iters16, A16 * (nb + 1), &t->device_bytes)) != RGS_OK) return r;
+        RGS_CUDA(cudaMemsetAsync(t->iters16, 0, sizeof(__nv_bfloat16) * A16 * (nb + 1), st)); // row padding stays 0
+        t->iters16_cap = nb + 1;
+    }
     if (!t->norm2 && (r = dev_alloc(&t->norm2, RGS_MAX_BOUNCES + 1, &t->device_bytes)) != RGS_OK) return r;
     RGS_CUDA(cudaMemsetAsync(t->norm2, 0, sizeof(double) * (RGS_MAX_BOUNCES + 1), st));
-    SceneDev sd = t->sc->dev();
-    RaysDev rd = t->rays();
     switch (t->nc) {
-    case 1: launch_make_S<1>(t, E, t->iters, st); break;
-    case 4: launch_make_S<4>(t, E, t->iters, st); break;
-    case 9: launch_make_S<9>(t, E, t->iters, st); break;
-    default: launch_make_S<16>(t, E, t->iters, st);
+    case 1: r = run_solve<1>(t, E, nb, precision, st); break;
+    case 4: r = run_solve<4>(t, E, nb, precision, st); break;
+    case 9: r = run_solve<9>(t, E, nb, precision, st); break;
+    default: r = run_solve<16>(t, E, nb, precision, st);
     }
-    RGS_LAUNCH("make_S");
-    for (int b = 1; b <= nb; ++b) {
-        const float *Bin = t->iters + A * (b - 1);
-        float *Bout = t->iters + A * b;
-        float *Q = t->Q + A * (b - 1);
-        switch (t->nc) {
-        case 1: r = launch_bounce<1>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st); break;
-        case 4: r = launch_bounce<4>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st); break;
-        case 9: r = launch_bounce<9>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st); break;
-        default: r = launch_bounce<16>(t, sd, rd, Bin, t->iters, Q, Bout, t->norm2 + b, st);
-        }
-        if (r != RGS_OK) return r;
-    }
+    if (r != RGS_OK) return r;
     t->nb_last = nb;
+    t->prec_last = precision;
     if (B_out) {
         switch (t->nc) {
         case 1: launch_to_user<1>(t, t->iters + A * nb, B_out, st); break;

@@ -232,6 +232,7 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         if ((r = dev_alloc(&t->D, (size_t)arr, &t->device_bytes)) != RGS_OK) return r;
         t->nc_cap = arr;
         t->iters_cap = 0; // iterate buffers are sized by the array size: force regrowth
+        t->iters16_cap = 0;
         t->v_cap = 0;
     }
     if (n > t->src_cap) {

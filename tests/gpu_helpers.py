@@ -14,10 +14,10 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=False):
+def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=False, precision=rgs.RGS_FP32):
     """build -> trace -> solve (-> adjoint with dL/dB = W) on cuda:0; numpy float64 out."""
     d = api.upload(sc)
-    pipe = api.Pipeline(alpha_model)
+    pipe = api.Pipeline(alpha_model, precision)
     pipe.build(d)
     pipe.trace(d)
     B, st = pipe.solve(d["E"], d["nb"], stats=stats)
