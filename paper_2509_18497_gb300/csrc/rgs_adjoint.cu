@@ -328,8 +328,13 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     if (nb >= 1) { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, t->v, t->Q + A * (nb - 1), t->Pg); }
     const long long n_rays = (long long)n * t->nd;
     const unsigned gr = (unsigned)((n_rays + 255) / 256);
+    const bool mc = C >= RGS_MC_MIN_COLS;
     for (int a = 1; a <= nb; ++a) {
-        for (int col0 = 0; col0 < C; col0 += 3) {
+        if (mc) {
+            rgs_status r = mc_adjoint_bounce<NC>(t, sd, rd, t->v + A * (a - 1), t->v + A * a, st);
+            if (r != RGS_OK) return r;
+        }
+        for (int col0 = 0; !mc && col0 < C; col0 += 3) {
             { ProfScope ps_("k_adj_ray", st); k_adj_ray<NC><<<gr, 256, 0, st>>>(sd, rd, C, col0, t->v + A * (a - 1), t->dy); }
             { ProfScope ps_("k_adj_src", st); k_adj_src<NC><<<n, ADJ_THREADS, 0, st>>>(rd, C, col0, t->src_off, t->tr, t->dy, t->v + A * a, t->u); }
         }
@@ -342,19 +347,26 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
-        constexpr int NA = 4;
-        const unsigned gg = (unsigned)((n_rays * Slice<NC>::G + 255) / 256);
-        for (int col0 = 0; col0 < C; col0 += 3) {
-            for (int a0 = 0; a0 < nb; a0 += NA) {
-                const int na = min(NA, nb - a0);
-                const bool first = (a0 == 0 && col0 == 0);
-                if (t->prec_last != RGS_FP32) { // the batched modes gather the BF16 iterate copies
-                    const size_t A16 = (size_t)n * C * SliceH<NC>::STRIDE;
-                    ProfScope ps_("k_opacity_g", st);
-                    k_opacity_g<NC, 3, NA, SliceH<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v, t->iters16, A16, t->gh, first);
-                } else {
-                    ProfScope ps_("k_opacity_g", st);
-                    k_opacity_g<NC, 3, NA, Slice<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v, t->iters, A, t->gh, first);
+        if (mc) {
+            rgs_status r = mc_opacity<NC>(t, sd, rd, nb, st);
+            if (r != RGS_OK) return r;
+        } else {
+            constexpr int NA = 4;
+            const unsigned gg = (unsigned)((n_rays * Slice<NC>::G + 255) / 256);
+            for (int col0 = 0; col0 < C; col0 += 3) {
+                for (int a0 = 0; a0 < nb; a0 += NA) {
+                    const int na = min(NA, nb - a0);
+                    const bool first = (a0 == 0 && col0 == 0);
+                    if (t->prec_last != RGS_FP32) { // the batched modes gather the BF16 iterate copies
+                        const size_t A16 = (size_t)n * C * SliceH<NC>::STRIDE;
+                        ProfScope ps_("k_opacity_g", st);
+                        k_opacity_g<NC, 3, NA, SliceH<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v,
+                                                                              t->iters16, A16, t->gh, first);
+                    } else {
+                        ProfScope ps_("k_opacity_g", st);
+                        k_opacity_g<NC, 3, NA, Slice<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v,
+                                                                             t->iters, A, t->gh, first);
+                    }
                 }
             }
         }
@@ -376,6 +388,11 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
         if ((r = dev_alloc(&t->v, A * (nb + 1), &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->u, A, &t->device_bytes)) != RGS_OK) return r;
         t->v_cap = nb + 1;
+    }
+    const long long n_rays_all = (long long)t->n * t->nd;
+    if (t->C >= RGS_MC_MIN_COLS && n_rays_all * 32 > t->dy_mc_cap) {
+        if ((r = dev_alloc(&t->dy_mc, (size_t)n_rays_all * 32, &t->device_bytes)) != RGS_OK) return r;
+        t->dy_mc_cap = n_rays_all * 32;
     }
     if (t->cap_slots > t->gh_cap) {
         if ((r = dev_alloc(&t->gh, (size_t)t->cap_slots, &t->device_bytes)) != RGS_OK) return r;

@@ -322,6 +322,7 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->gh);
     dev_free(t->dir);
     dev_free(t->dy);
+    dev_free(t->dy_mc);
     delete t;
 }
 

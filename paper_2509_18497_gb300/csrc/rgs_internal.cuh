@@ -429,6 +429,8 @@ struct rgs_transport {
     int num_sms = 0;
     float4 *dir = nullptr; // per-ray direction
     float4 *dy = nullptr;  // adjoint: per-ray (y[0..2], 0) for the current column tile
+    float *dy_mc = nullptr; // adjoint, many columns: per-ray y of one 32-column tile
+    long long dy_mc_cap = 0;
     long long rays_cap = 0;
     unsigned long long *counter = nullptr;
     int *flags = nullptr;
@@ -523,6 +525,16 @@ template <class T> void dev_free(T *&p) {
     if (p) cudaFree(p);
     p = nullptr;
 }
+
+// many-column kernels (rgs_manycol.cu), used when C >= RGS_MC_MIN_COLS
+#define RGS_MC_MIN_COLS 48
+template <int NC>
+rgs_status mc_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, bool rows16, const float *Bprev,
+                     const __nv_bfloat16 *Bprev16, const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16,
+                     double *norm2, cudaStream_t st);
+template <int NC>
+rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const float *vin, float *vout, cudaStream_t st);
+template <int NC> rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int nb, cudaStream_t st);
 
 // entry points implemented per translation unit
 rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_build_opts *o, cudaStream_t st);

@@ -1,0 +1,317 @@
+// Many right-hand sides (many lights): kernels with one lane per column.
+//
+// With C columns the per-hit work of the gather is a row of C x nc coefficients of the
+// source surfel.  The 3-column kernels (rgs_solve.cu, rgs_adjoint.cu) would re-read every
+// hit record once per 3-column tile; here a warp takes one ray (or one transposed entry) at
+// a time and its 32 lanes take 32 consecutive columns, so each hit is read once per
+// 32-column tile and every row load is one contiguous 512-byte (BF16) or 1-KiB (FP32)
+// warp access.  Used when C >= RGS_MC_MIN_COLS.
+#include "rgs_internal.cuh"
+
+namespace {
+
+constexpr int MC_WARPS = 8;
+constexpr int MC_THREADS = MC_WARPS * 32;
+
+// the NC coefficients of one column of a row (FP32 rows of NC floats, BF16 rows padded)
+template <int NC> __device__ __forceinline__ void load_col(const float *__restrict__ p, float *v) {
+    if constexpr (NC % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < NC / 4; ++q) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            v[4 * q] = f.x;
+            v[4 * q + 1] = f.y;
+            v[4 * q + 2] = f.z;
+            v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) v[k] = __ldg(p + k);
+    }
+}
+template <int NC> __device__ __forceinline__ void load_col(const __nv_bfloat16 *__restrict__ p, float *v) {
+    if constexpr (NC >= 9) { // padded to 16
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+            const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k0 = 8 * q + 2 * m;
+                if (k0 < NC) v[k0] = __uint_as_float(u[m] << 16);
+                if (k0 + 1 < NC) v[k0 + 1] = __uint_as_float(u[m] & 0xffff0000u);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) v[k] = __bfloat162float(p[k]);
+    }
+}
+template <int NC, class T> constexpr int row_stride() {
+    return sizeof(T) == 2 ? ((NC >= 9) ? 16 : NC) : NC;
+}
+
+// ------------------------------------------------------------------ forward bounce
+template <int NC, class T>
+__global__ void __launch_bounds__(MC_THREADS) k_bounce_mc(SceneDev sc, RaysDev rays, int C, const T *__restrict__ Bg,
+                                                         const float *__restrict__ Bprev, const float *__restrict__ S,
+                                                         float *__restrict__ Qout, float *__restrict__ Bout,
+                                                         __nv_bfloat16 *__restrict__ Bout16, double *norm2) {
+    constexpr int RS = row_stride<NC, T>();
+    const int i = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col = blockIdx.y * 32 + lane;
+    const bool live = col < C;
+    const int colc = live ? col : C - 1;
+    const int nd = rays.nd;
+    const float3 n = f3(sc.N4[i]);
+    float acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = 0.f;
+    for (int q = warp; q < nd; q += MC_WARPS) {
+        const long long r = (long long)i * nd + q;
+        const float3 d = f3(rays.dir[r]);
+        float Yo[NC];
+        sh_eval<NC>(neg3(d), Yo);
+        const int cnt = rays.cnt[r];
+        const long long base = rays.off[r];
+        float x = 0.f;
+#pragma unroll 2
+        for (int h = 0; h < cnt; ++h) {
+            const int2 ja = __ldg(&rays.rec_ja[base + h]);
+            float v[NC];
+            load_col<NC>(Bg + ((size_t)ja.x * C + colc) * RS, v);
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
+            x += __int_as_float(ja.y) * s;
+        }
+        float Yi[NC];
+        sh_eval<NC>(reflect_n(n, d), Yi);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[k] += Yi[k] * x;
+    }
+    __shared__ float red[MC_WARPS][NC][32];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) red[warp][k][lane] = acc[k];
+    __syncthreads();
+    double dsq = 0.0;
+    const float w = 3.14159265358979f / (float)nd;
+    for (int e = threadIdx.x; e < NC * 32; e += MC_THREADS) {
+        const int k = e >> 5, c = e & 31;
+        const int cc = blockIdx.y * 32 + c;
+        if (cc >= C) continue;
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < MC_WARPS; ++q) v += red[q][k][c];
+        const float Q = w * v;
+        const size_t idx = ((size_t)i * C + cc) * NC + k;
+        Qout[idx] = Q;
+        const float b = S[idx] + sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (cc % 3)] * Q;
+        Bout[idx] = b;
+        if (Bout16) Bout16[((size_t)i * C + cc) * ((NC >= 9) ? 16 : NC) + k] = __float2bfloat16_rn(b);
+        const double df = (double)b - (double)Bprev[idx];
+        dsq += df * df;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dsq += __shfl_xor_sync(0xffffffffu, dsq, off);
+    if (lane == 0) atomicAdd(norm2, dsq);
+}
+
+// ------------------------------------------------------------------ adjoint
+// y_r[c] = (pi/nd) o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) v_i[c][k'] for the 32 columns of
+// tile `ct`, stored as dy[r*32 + lane]
+template <int NC>
+__global__ void __launch_bounds__(MC_THREADS) k_adj_ray_mc(SceneDev sc, RaysDev rays, int C, int ct,
+                                                          const float *__restrict__ vin, float *dy) {
+    const int i = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col = ct * 32 + lane;
+    const bool live = col < C;
+    const int nd = rays.nd;
+    const float3 n = f3(sc.N4[i]);
+    float cv[NC]; // c_{i,l(k),ch(col)} * v_i[col][k] * o_i pi/nd
+    {
+        const float oi = sc.P[i].w * (3.14159265358979f / (float)nd);
+        float v[NC];
+        if (live) load_col<NC>(vin + ((size_t)i * C + col) * NC, v);
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            cv[k] = live ? oi * __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + col % 3]) * v[k] : 0.f;
+    }
+    for (int q = warp; q < nd; q += MC_WARPS) {
+        const long long r = (long long)i * nd + q;
+        const float3 d = f3(rays.dir[r]);
+        float Yi[NC];
+        sh_eval<NC>(reflect_n(n, d), Yi);
+        float y = 0.f;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) y += cv[k] * Yi[k];
+        dy[r * 32 + lane] = y;
+    }
+}
+
+// (K^T v)_j[c][k] = sum_{entries e on j} a_e Y_k(-d_e) y_e[c], one CTA per source j
+template <int NC>
+__global__ void __launch_bounds__(MC_THREADS) k_adj_src_mc(RaysDev rays, int C, int ct,
+                                                          const long long *__restrict__ src_off,
+                                                          const int2 *__restrict__ tr, const float *__restrict__ dy,
+                                                          float *__restrict__ vout, float *__restrict__ u) {
+    const int j = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = 0.f;
+    const long long e0 = src_off[j], e1 = src_off[j + 1];
+    for (long long e = e0 + warp; e < e1; e += MC_WARPS) {
+        const int2 ent = __ldg(&tr[e]);
+        const float4 d4 = __ldg(&rays.dir[ent.x]);
+        float Yo[NC];
+        sh_eval<NC>(make_float3(-d4.x, -d4.y, -d4.z), Yo);
+        const float y = __int_as_float(ent.y) * __ldg(&dy[(long long)ent.x * 32 + lane]);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[k] += Yo[k] * y;
+    }
+    __shared__ float red[MC_WARPS][NC][32];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) red[warp][k][lane] = acc[k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < NC * 32; e += MC_THREADS) {
+        const int k = e >> 5, c = e & 31;
+        const int cc = ct * 32 + c;
+        if (cc >= C) continue;
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < MC_WARPS; ++q) v += red[q][k][c];
+        const size_t idx = ((size_t)j * C + cc) * NC + k;
+        vout[idx] = v;
+        u[idx] += v;
+    }
+}
+
+// opacity backward: per hit g_h (partial over this column tile and iterate chunk)
+// accumulated into gh[slot]; a warp per ray, lanes over columns
+template <int NC, int NA, class T>
+__global__ void __launch_bounds__(MC_THREADS) k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int ct, int nb, int a0,
+                                                            int na, size_t A, const float *__restrict__ V,
+                                                            const T *__restrict__ Bit, size_t AB, float *gh,
+                                                            bool first) {
+    constexpr int RS = row_stride<NC, T>();
+    const int warp_g = (int)((blockIdx.x * (size_t)MC_THREADS + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int n_rays = sc.n * rays.nd;
+    if (warp_g >= n_rays) return; // whole warps
+    const int r = warp_g;
+    const int cnt = rays.cnt[r];
+    if (cnt == 0) return;
+    const int col = ct * 32 + lane;
+    const bool live = col < C;
+    const int colc = live ? col : C - 1;
+    const int i = r / rays.nd;
+    const float3 n = f3(sc.N4[i]);
+    const float3 d = f3(rays.dir[r]);
+    float Yo[NC], y[NA];
+    {
+        float Yi[NC];
+        sh_eval<NC>(neg3(d), Yo);
+        sh_eval<NC>(reflect_n(n, d), Yi);
+        const float oi = sc.P[i].w * (3.14159265358979f / (float)rays.nd);
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            float s = 0.f;
+            if (aa < na && live) {
+                float v[NC];
+                load_col<NC>(V + A * (a0 + aa) + ((size_t)i * C + col) * NC, v);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + col % 3]) * Yi[k] * v[k];
+            }
+            y[aa] = oi * s;
+        }
+    }
+    const long long base = rays.off[r];
+    for (int h = 0; h < cnt; ++h) {
+        const int j = __ldg(&rays.rec_ja[base + h]).x;
+        float acc = 0.f;
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            if (aa < na) {
+                float v[NC];
+                load_col<NC>(Bit + AB * (nb - 1 - (a0 + aa)) + ((size_t)j * C + colc) * RS, v);
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
+                acc += y[aa] * s;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) gh[base + h] = first ? acc : gh[base + h] + acc;
+    }
+}
+
+} // namespace
+
+// ------------------------------------------------------------------ launchers
+template <int NC>
+rgs_status mc_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, bool rows16, const float *Bprev,
+                     const __nv_bfloat16 *Bprev16, const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16,
+                     double *norm2, cudaStream_t st) {
+    dim3 grid(t->n, (t->C + 31) / 32);
+    if (rows16) {
+        ProfScope ps_("k_bounce_mc", st);
+        k_bounce_mc<NC, __nv_bfloat16><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, Bprev16, Bprev, S, Q, Bout, Bout16, norm2);
+    } else {
+        ProfScope ps_("k_bounce_mc", st);
+        k_bounce_mc<NC, float><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, Bprev, Bprev, S, Q, Bout, Bout16, norm2);
+    }
+    RGS_LAUNCH("bounce_mc");
+    return RGS_OK;
+}
+
+template <int NC>
+rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const float *vin, float *vout,
+                             cudaStream_t st) {
+    for (int ct = 0; ct * 32 < t->C; ++ct) {
+        { ProfScope ps_("k_adj_ray_mc", st); k_adj_ray_mc<NC><<<t->n, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, vin, t->dy_mc); }
+        { ProfScope ps_("k_adj_src_mc", st); k_adj_src_mc<NC><<<t->n, MC_THREADS, 0, st>>>(rd, t->C, ct, t->src_off, t->tr, t->dy_mc, vout, t->u); }
+    }
+    RGS_LAUNCH("adjoint bounce mc");
+    return RGS_OK;
+}
+
+template <int NC>
+rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int nb, cudaStream_t st) {
+    constexpr int NA = 4;
+    const size_t A = t->arr();
+    const long long n_rays = (long long)t->n * t->nd;
+    const unsigned grid = (unsigned)((n_rays * 32 + MC_THREADS - 1) / MC_THREADS);
+    for (int ct = 0; ct * 32 < t->C; ++ct)
+        for (int a0 = 0; a0 < nb; a0 += NA) {
+            const int na = min(NA, nb - a0);
+            const bool first = (ct == 0 && a0 == 0);
+            if (t->prec_last != RGS_FP32) {
+                const size_t A16 = (size_t)t->n * t->C * ((NC >= 9) ? 16 : NC);
+                ProfScope ps_("k_opacity_g_mc", st);
+                k_opacity_g_mc<NC, NA, __nv_bfloat16><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, nb, a0, na, A, t->v,
+                                                                                   t->iters16, A16, t->gh, first);
+            } else {
+                ProfScope ps_("k_opacity_g_mc", st);
+                k_opacity_g_mc<NC, NA, float><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, nb, a0, na, A, t->v,
+                                                                           t->iters, A, t->gh, first);
+            }
+        }
+    RGS_LAUNCH("opacity mc");
+    return RGS_OK;
+}
+
+#define RGS_MC_INSTANTIATE(NC)                                                                                         \
+    template rgs_status mc_bounce<NC>(const rgs_transport *, SceneDev, RaysDev, bool, const float *,                   \
+                                      const __nv_bfloat16 *, const float *, float *, float *, __nv_bfloat16 *,         \
+                                      double *, cudaStream_t);                                                         \
+    template rgs_status mc_adjoint_bounce<NC>(rgs_transport *, SceneDev, RaysDev, const float *, float *,              \
+                                              cudaStream_t);                                                           \
+    template rgs_status mc_opacity<NC>(rgs_transport *, SceneDev, RaysDev, int, cudaStream_t);
+RGS_MC_INSTANTIATE(1)
+RGS_MC_INSTANTIATE(4)
+RGS_MC_INSTANTIATE(9)
+RGS_MC_INSTANTIATE(16)

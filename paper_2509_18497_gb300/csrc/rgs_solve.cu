@@ -183,9 +183,10 @@ rgs_status run_solve(rgs_transport *t, const float *E, int nb, int precision, cu
     for (int b = 1; b <= nb; ++b) {
         // RESCORR: the last bounce gathers the FP32 rows (one residual-correction sweep)
         const bool rows16 = bf16 && !(precision == RGS_BF16_FP32ACC_RESCORR && b == nb);
-        rgs_status r = launch_bounce<NC>(t, sd, rd, rows16, t->iters + A * (b - 1), bf16 ? I16 + A16 * (b - 1) : nullptr,
-                                         t->iters, t->Q + A * (b - 1), t->iters + A * b,
-                                         bf16 ? I16 + A16 * b : nullptr, t->norm2 + b, st);
+        rgs_status r =
+            (t->C >= RGS_MC_MIN_COLS ? mc_bounce<NC> : launch_bounce<NC>)(
+                t, sd, rd, rows16, t->iters + A * (b - 1), bf16 ? I16 + A16 * (b - 1) : nullptr, t->iters,
+                t->Q + A * (b - 1), t->iters + A * b, bf16 ? I16 + A16 * b : nullptr, t->norm2 + b, st);
         if (r != RGS_OK) return r;
     }
     return RGS_OK;
