@@ -34,6 +34,9 @@ UNIT = "surfel·light·bounces/s"
 WORKLOAD = ("fruit bowl: 50,000 Gaussian surfels on 12 spheres in a hemispherical bowl on a ground plane, "
             "SH degree 3 (16 x RGB), 256 stratified hemisphere rays/surfel, 4 bounces, 1 point light, "
             "FP32, forward + adjoint (emission, albedo, opacity gradients)")
+MULTI_WORKLOAD = ("multi-light batch: 200,000 fruit-bowl surfels, 100 point lights on a Fibonacci sphere of radius 3 "
+                  "(intensity U[5,20]) as 300 right-hand sides, SH degree 3, 256 rays/surfel, 4 bounces, "
+                  "forward + adjoint")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -54,10 +57,7 @@ def _src_sha(name):
 # DRAM bytes per launch from one ncu capture (profiles/), keyed by kernel; valid only
 # while the kernel's source file is unchanged since the capture.
 NCU_TRAFFIC = {
-    "k_trace_hemi": {"bytes_per_launch": 6.238852e9 + 12.022045e9, "n": 10000, "src_sha": "39d3ef415f7b0f34"},
-    "k_bounce": {"bytes_per_launch": 0.879334e9 + 0.006455e9, "n": 10000, "src_sha": "ae4e5a315773ea56"},
-    "k_adj_bounce": {"bytes_per_launch": 0.400631e9 + 0.006990e9, "n": 10000, "src_sha": "90eee932693e628b"},
-    "k_hemi_opacity_bwd": {"bytes_per_launch": 3.571173e9 + 1.144471e9, "n": 10000, "src_sha": "90eee932693e628b"},
+    "k_trace_hemi": {"bytes_per_launch": 0.834729e9 + 2.153428e9, "n": 10000, "src_sha": "35405e494984794e"},
 }
 
 
@@ -77,6 +77,14 @@ def algorithmic_bytes(kernel, info, n, nd, nb, C, nc):
         return H * (8 + 4) + rays * (4 + 8 + 16) + 2 * min(nb, 4) * tile
     if kernel == "k_opacity_rec":  # records (j, a) + G + g per hit, counts; dL/do
         return H * (8 + 4 + 4) + rays * (4 + 8) + n * 4
+    tiles = (C + 31) // 32
+    A16 = n * C * 16 * 2        # BF16 copy of an iterate (rows padded to 16)
+    if kernel == "k_bounce_mc":   # per 32-column tile: records, counts, offsets, directions; iterate rows once
+        return tiles * (H * 8 + rays * (4 + 8 + 16)) + A16 + 4 * A + A16
+    if kernel == "k_opacity_g_mc":  # per tile: records + ray data; 4 iterates of v (FP32) and B (BF16); g per hit
+        return tiles * (H * (8 + 4) + rays * (4 + 8 + 16)) + min(nb, 4) * (A + A16)
+    if kernel == "k_adj_src_mc":  # per tile: transposed records, directions, y; v tile out, u r+w
+        return tiles * (H * 8 + rays * (16 + 128) + (n + 1) * 8) + 3 * A
     if kernel == "k_trace_hemi":  # scene (64 B/surfel + 64 B/node) in; records, counts, directions out
         return n * 64 + (n - 1) * 64 + H * 12 + rays * (4 + 8 + 16) + n * 4
     return None
@@ -182,6 +190,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=50000, help="surfel count (default: the 50,000-surfel workload)")
+    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light"],
+                    help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights")
     ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1500, help="surfels per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -204,8 +214,11 @@ def main():
 
     build.build()
     rgs.load()
-    sc = scenes.fruit_bowl(n=args.n)
-    n, nd, nb, nc, nl = sc["n"], sc["nd"], sc["nb"], 16, 1
+    if args.workload == "multi_light":
+        sc = scenes.multi_light(n=200000 if args.n == 50000 else args.n)
+    else:
+        sc = scenes.fruit_bowl(n=args.n)
+    n, nd, nb, nc, nl = sc["n"], sc["nd"], sc["nb"], 16, sc["light_pos"].shape[0]
     C = 3 * nl
     units_per_step = n * nl * nb
 
@@ -319,6 +332,7 @@ def main():
     avg_ms = ms_dom / c_dom
     achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
     src_file = {"k_bounce": "rgs_solve.cu", "k_adj_src": "rgs_adjoint.cu", "k_adj_ray": "rgs_adjoint.cu",
+                "k_bounce_mc": "rgs_manycol.cu", "k_opacity_g_mc": "rgs_manycol.cu", "k_adj_src_mc": "rgs_manycol.cu",
                 "k_opacity_g": "rgs_adjoint.cu", "k_opacity_rec": "rgs_adjoint.cu",
                 "k_trace_hemi": "rgs_trace.cu"}.get(dom)
     traffic = None
@@ -337,7 +351,7 @@ def main():
             "ms_per_step": sum(step_ms) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16-gather/f32-acc" if headline == "batched" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_surfels": n, "sh_degree": 3, "rays_per_surfel": nd, "bounces": nb,
+            "config": {"workload": WORKLOAD if args.workload == "fruit_bowl" else MULTI_WORKLOAD, "n_surfels": n, "sh_degree": 3, "rays_per_surfel": nd, "bounces": nb,
                        "lights": nl, "precision": headline, "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas x{world}", "hit_records": info["n_hits"]},
             "batched_vs_plain": {"batched": value_b, "plain": value_p, "speedup": value_b / value_p,

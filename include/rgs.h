@@ -182,6 +182,37 @@ rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_
 rgs_status rgs_adjoint(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo, float *dL_dopacity,
                        void *stream);
 
+typedef struct rgs_batch_opts {
+    int32_t precision;  /* rgs_precision, for every scene of the batch */
+    int32_t use_graph;  /* nonzero: capture the batch's launches into a CUDA graph on the first call with
+                           these arguments and replay the graph on later calls */
+    int32_t autotune;   /* nonzero: on the first call, time the candidate numbers of resident blocks per SM
+                           of the persistent kernel and keep the fastest */
+    int32_t spin_limit; /* polls of each inter-bounce grid-barrier wait before the kernel gives up with
+                           RGS_ERR_TIMEOUT; 0 = default (about a second) */
+} rgs_batch_opts;
+
+/* Solves `count` traced transports together -- scenes of uneven surfel count, SH degree, rays
+ * per surfel and bounce count (the batching of right-hand sides and scenes; Sec. 7 hybrid solver,
+ * Eq. final-radiosity per scene).  S = E + D is formed per scene; then every bounce of every scene
+ * runs in one persistent cooperative kernel whose blocks take (scene, receiver, 3-column tile)
+ * items from one queue per bounce level, with a bounded grid barrier between levels.  Each
+ * transport keeps its iterates, so rgs_adjoint and rgs_get_iterate work per scene afterwards.
+ *   ts        : host array of count traced transports (distinct).
+ *   E         : host array of count device pointers [N_s][nc_s][3] (entries may be NULL), or NULL.
+ *   n_bounces : host array of count bounce counts in [0, RGS_MAX_BOUNCES].
+ *   opts      : host, may be NULL (FP32, graph, autotune, default wait limit).
+ *   B_out     : host array of count device pointers [N_s][nc_s][C_s] (entries may be NULL), or NULL.
+ *   residual_norms : host [count][RGS_MAX_BOUNCES] FP64 norms per bounce, or NULL.
+ * Launch plans (device descriptors, graph, tuned shape) are cached per argument set; the first
+ * call with new arguments also runs the autotuning candidates.  Synchronises `stream` (the
+ * device-side timeout flag is read back).  Errors: RGS_ERR_ARG, RGS_ERR_STATE (untraced
+ * transport), RGS_ERR_OOM, RGS_ERR_CUDA, RGS_ERR_TIMEOUT (a barrier wait ran out; the iterates
+ * of the batch are then invalid, the context stays usable). */
+rgs_status rgs_solve_batched(rgs_transport *const *ts, int32_t count, const float *const *E,
+                             const int32_t *n_bounces, const rgs_batch_opts *opts, float *const *B_out,
+                             double *residual_norms, void *stream);
+
 /* Copies iterate B^(b) (0 <= b <= last n_bounces) of the last rgs_solve to the device
  * array out [N][nc][C].  Asynchronous.  Errors: RGS_ERR_STATE, RGS_ERR_ARG, RGS_ERR_CUDA. */
 rgs_status rgs_get_iterate(rgs_transport *t, int32_t b, float *out, void *stream);

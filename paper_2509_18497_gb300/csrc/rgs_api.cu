@@ -258,6 +258,41 @@ rgs_status rgs_adjoint(rgs_transport *t, const float *dL_dB, float *dL_dE, float
     return rgs_adjoint_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, S(stream));
 }
 
+rgs_status rgs_solve_batched(rgs_transport *const *ts, int32_t count, const float *const *E,
+                             const int32_t *n_bounces, const rgs_batch_opts *opts, float *const *B_out,
+                             double *residual_norms, void *stream) {
+    g_err[0] = 0;
+    if (!ts || !n_bounces || count < 1 || count > 4096) {
+        rgs_set_error("rgs_solve_batched: need 1..4096 transports and their bounce counts");
+        return RGS_ERR_ARG;
+    }
+    const int precision = opts ? opts->precision : RGS_FP32;
+    if (precision != RGS_FP32 && precision != RGS_BF16_FP32ACC && precision != RGS_BF16_FP32ACC_RESCORR) {
+        rgs_set_error("rgs_solve_batched: unknown precision %d", precision);
+        return RGS_ERR_ARG;
+    }
+    for (int s = 0; s < count; ++s) {
+        if (!ts[s] || !ts[s]->sc) {
+            rgs_set_error("rgs_solve_batched: transport %d is NULL", s);
+            return RGS_ERR_ARG;
+        }
+        if (ts[s]->nd == 0) {
+            rgs_set_error("rgs_solve_batched: transport %d was not traced", s);
+            return RGS_ERR_STATE;
+        }
+        if (n_bounces[s] < 0 || n_bounces[s] > RGS_MAX_BOUNCES) {
+            rgs_set_error("rgs_solve_batched: n_bounces[%d] = %d outside [0, %d]", s, n_bounces[s], RGS_MAX_BOUNCES);
+            return RGS_ERR_ARG;
+        }
+        for (int q = 0; q < s; ++q)
+            if (ts[q] == ts[s]) {
+                rgs_set_error("rgs_solve_batched: transport %d appears twice", s);
+                return RGS_ERR_ARG;
+            }
+    }
+    return rgs_solve_batched_impl(ts, count, E, n_bounces, opts, B_out, residual_norms, S(stream));
+}
+
 rgs_status rgs_get_iterate(rgs_transport *t, int32_t b, float *out, void *stream) {
     g_err[0] = 0;
     if (!t || !out) {
@@ -296,6 +331,7 @@ rgs_status rgs_transport_info_get(const rgs_transport *t, rgs_transport_info *in
 void rgs_destroy_transport(rgs_transport *t) {
     if (!t) return;
     cudaDeviceSynchronize();
+    rgs_batch_forget(t);
     dev_free(t->lpos);
     dev_free(t->lint);
     dev_free(t->rec_ja);

@@ -543,6 +543,10 @@ rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precisio
                           rgs_solve_stats *stats, cudaStream_t st);
 rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st);
 rgs_status rgs_get_iterate_impl(rgs_transport *t, int b, float *out, cudaStream_t st);
+rgs_status rgs_solve_prepare(rgs_transport *t, int nb, int precision, cudaStream_t st);
+rgs_status rgs_solve_batched_impl(rgs_transport *const *ts, int count, const float *const *E, const int32_t *nbs,
+                                  const rgs_batch_opts *opts, float *const *B_out, double *norms, cudaStream_t st);
+void rgs_batch_forget(const rgs_transport *t);
 // device-wide exclusive scan of int counts into int64 offsets (offsets[n] = total)
 rgs_status rgs_scan_counts(const int *cnt, long long *off, int n, long long *tmp, int tmp_cap, cudaStream_t st);
 int rgs_scan_tmp_size(int n);

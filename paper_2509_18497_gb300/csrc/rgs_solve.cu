@@ -5,11 +5,10 @@
 // gathers the stored hits' radiance x_r[c] = sum_h a_rh Y(-d_r) . B_{j_h}[c]; the CTA then
 // projects Q_i[c][k] = (pi/nd) sum_r Y_k(R_i d_r) x_r[c] and writes Q^(k-1),
 // B^(k) = S + o_i c_i (x) Q and the FP64 partial sum of (B^(k) - B^(k-1))^2.
-#include "rgs_internal.cuh"
+#include "rgs_bounce_body.cuh"
 
 namespace {
 
-constexpr int BOUNCE_THREADS = 256;
 
 // internal [N][C][NC] <- user [N][nc][3] emission broadcast over the columns, plus D;
 // optionally also the BF16 copy (rows of bf16_stride<NC>)
@@ -46,99 +45,8 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev 
                                                           const float *__restrict__ Bprev, const float *__restrict__ S,
                                                           float *__restrict__ Qout, float *__restrict__ Bout,
                                                           __nv_bfloat16 *__restrict__ Bout16, double *norm2) {
-    constexpr int G = SL::G, KPL = SL::KPL, GROUPS = BOUNCE_THREADS / G, RS = SL::STRIDE;
-    const int i = blockIdx.x;
-    const int col0 = blockIdx.y * CT;
-    const int nd = rays.nd;
-    const int grp = threadIdx.x / G, g = threadIdx.x % G;
-    const float3 n = f3(sc.N4[i]);
-    float acc[KPL][CT];
-#pragma unroll
-    for (int m = 0; m < KPL; ++m)
-#pragma unroll
-        for (int c = 0; c < CT; ++c) acc[m][c] = 0.f;
-
-    for (int q = grp; q < nd; q += GROUPS) {
-        const long long r = (long long)i * nd + q;
-        const float3 d = f3(rays.dir[r]);
-        float yo[KPL], yi[KPL];
-        {
-            float Y[NC];
-            sh_eval<NC>(neg3(d), Y);
-            SL::pick(Y, g, yo);
-            sh_eval<NC>(reflect_n(n, d), Y);
-            SL::pick(Y, g, yi);
-        }
-        const int cnt = rays.cnt[r];
-        const long long base = rays.off[r];
-        float x[CT];
-#pragma unroll
-        for (int c = 0; c < CT; ++c) x[c] = 0.f;
-#pragma unroll 4
-        for (int h = 0; h < cnt; ++h) {
-            const int2 ja = __ldg(&rays.rec_ja[base + h]);
-            const float a = __int_as_float(ja.y);
-            const typename SL::T *Bj = Bg + ((size_t)ja.x * C + col0) * RS;
-#pragma unroll
-            for (int c = 0; c < CT; ++c) {
-                float v[KPL];
-                SL::load(Bj + c * RS, g, v);
-                float s = 0.f;
-#pragma unroll
-                for (int m = 0; m < KPL; ++m) s += yo[m] * v[m];
-                x[c] += a * s;
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < CT; ++c) {
-            const float xc = SL::group_sum(x[c]);
-#pragma unroll
-            for (int m = 0; m < KPL; ++m) acc[m][c] += yi[m] * xc;
-        }
-    }
-    // reduce over the groups: lanes with equal g within the warp, then across warps
-    __shared__ float red[BOUNCE_THREADS / 32][G][KPL * CT];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int m = 0; m < KPL; ++m)
-#pragma unroll
-        for (int c = 0; c < CT; ++c) {
-            float v = acc[m][c];
-#pragma unroll
-            for (int off = G; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane < G) red[warp][lane][m * CT + c] = v;
-        }
-    __syncthreads();
-    double dsq = 0.0;
-    const float w = 3.14159265358979f / (float)nd;
-    for (int e = threadIdx.x; e < NC * CT; e += BOUNCE_THREADS) {
-        const int k = e / CT, c = e - k * CT;
-        int gg = 0, mm = 0;
-#pragma unroll
-        for (int g2 = 0; g2 < G; ++g2)
-#pragma unroll
-            for (int m2 = 0; m2 < KPL; ++m2)
-                if (SL::k(g2, m2) == k) {
-                    gg = g2;
-                    mm = m2;
-                }
-        float v = 0.f;
-        for (int q = 0; q < BOUNCE_THREADS / 32; ++q) v += red[q][gg][mm * CT + c];
-        const int col = col0 + c;
-        const float Q = w * v;
-        const size_t idx = ((size_t)i * C + col) * NC + k;
-        Qout[idx] = Q;
-        const float oc = sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (col % 3)];
-        const float b = S[idx] + oc * Q;
-        Bout[idx] = b;
-        if (Bout16) Bout16[((size_t)i * C + col) * bf16_stride<NC>() + k] = __float2bfloat16_rn(b);
-        const double df = (double)b - (double)Bprev[idx];
-        dsq += df * df;
-    }
-    // FP64 residual norm: warp reduce, one atomic per warp with work
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) dsq += __shfl_xor_sync(0xffffffffu, dsq, off);
-    if (lane == 0 && warp * 32 < NC * CT) atomicAdd(norm2, dsq);
+    __shared__ float red[(BOUNCE_THREADS / 32) * SL::G * SL::KPL * CT];
+    bounce_receiver<NC, CT, SL>(sc, rays, C, Bg, Bprev, S, Qout, Bout, Bout16, norm2, blockIdx.x, blockIdx.y * CT, red);
 }
 
 template <int NC>
@@ -192,8 +100,8 @@ rgs_status run_solve(rgs_transport *t, const float *E, int nb, int precision, cu
     return RGS_OK;
 }
 
-rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precision, float *B_out,
-                          rgs_solve_stats *stats, cudaStream_t st) {
+// iterate buffers for nb bounces at the given precision (kept for the adjoint)
+rgs_status rgs_solve_prepare(rgs_transport *t, int nb, int precision, cudaStream_t st) {
     rgs_status r;
     const size_t A = t->arr();
     if (nb + 1 > t->iters_cap) {
@@ -208,6 +116,14 @@ rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precisio
         t->iters16_cap = nb + 1;
     }
     if (!t->norm2 && (r = dev_alloc(&t->norm2, RGS_MAX_BOUNCES + 1, &t->device_bytes)) != RGS_OK) return r;
+    return RGS_OK;
+}
+
+rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precision, float *B_out,
+                          rgs_solve_stats *stats, cudaStream_t st) {
+    rgs_status r;
+    const size_t A = t->arr();
+    if ((r = rgs_solve_prepare(t, nb, precision, st)) != RGS_OK) return r;
     RGS_CUDA(cudaMemsetAsync(t->norm2, 0, sizeof(double) * (RGS_MAX_BOUNCES + 1), st));
     switch (t->nc) {
     case 1: r = run_solve<1>(t, E, nb, precision, st); break;

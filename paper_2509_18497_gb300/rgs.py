@@ -28,7 +28,7 @@ STATUS = {0: "RGS_OK", 1: "RGS_ERR_ARG", 2: "RGS_ERR_CUDA", 3: "RGS_ERR_OOM", 4:
 EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
            "rgs_transport_info_get", "rgs_destroy_transport", "rgs_destroy_scene", "rgs_profile_enable",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
-           "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc")
+           "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched")
 
 
 class RgsError(RuntimeError):
@@ -58,6 +58,11 @@ class rgs_solve_stats(ct.Structure):
     _fields_ = [("n_bounces", ct.c_int32), ("n_cols", ct.c_int32),
                 ("residual_norm", ct.c_double * RGS_MAX_BOUNCES),
                 ("n_hits", ct.c_int64), ("n_hit_slots", ct.c_int64), ("n_full_rays", ct.c_int64)]
+
+
+class rgs_batch_opts(ct.Structure):
+    _fields_ = [("precision", ct.c_int32), ("use_graph", ct.c_int32), ("autotune", ct.c_int32),
+                ("spin_limit", ct.c_int32)]
 
 
 class rgs_kernel_time(ct.Structure):
@@ -104,6 +109,9 @@ def load(path=LIB_PATH):
     L.rgs_profile_report.restype = ct.c_int32
     L.rgs_launch_count.restype = ct.c_int64
     L.rgs_residual_norm_noalloc.argtypes = [vp, vp, ct.c_int64, vp, vp]
+    L.rgs_solve_batched.argtypes = [ct.POINTER(vp), ct.c_int32, ct.POINTER(vp), ct.POINTER(ct.c_int32),
+                                    ct.POINTER(rgs_batch_opts), ct.POINTER(vp), ct.POINTER(ct.c_double), vp]
+    L.rgs_solve_batched.restype = ct.c_int
     L.rgs_residual_norm_noalloc.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
                "rgs_transport_info_get"):
@@ -297,3 +305,28 @@ def rgs_residual_norm_noalloc(x, y, norm_out=None, stream=None):
     _check(L.rgs_residual_norm_noalloc(_dev(x, tuple(x.shape), "x"), _dev(y, tuple(x.shape), "y"), int(n),
                                        ct.c_void_p(norm_out.data_ptr()), _stream(stream)))
     return norm_out
+
+
+def rgs_solve_batched(transports, E_list, n_bounces, precision=RGS_FP32, use_graph=True, autotune=True,
+                      spin_limit=0, B_outs=None, norms=False, stream=None):
+    """rgs_solve_batched over a list of traced Transport objects; returns (list of B tensors, norms or None)."""
+    L = load()
+    m = len(transports)
+    hs = (ct.c_void_p * m)(*[t.h.value for t in transports])
+    Es = None
+    if E_list is not None:
+        Es = (ct.c_void_p * m)(*[(_dev(E, (t.n, t.nc, 3), "E").value if E is not None else None)
+                                 for t, E in zip(transports, E_list)])
+    nbs = (ct.c_int32 * m)(*[int(b) for b in n_bounces])
+    if B_outs is None:
+        B_outs = [torch.empty((t.n, t.nc, t.C), device="cuda", dtype=torch.float32) for t in transports]
+    Bs = (ct.c_void_p * m)(*[_dev(B, (t.n, t.nc, t.C), "B_out").value for t, B in zip(transports, B_outs)])
+    nrm = (ct.c_double * (m * RGS_MAX_BOUNCES))() if norms else None
+    opts = rgs_batch_opts(int(precision), int(bool(use_graph)), int(bool(autotune)), int(spin_limit))
+    _check(L.rgs_solve_batched(hs, m, Es, nbs, ct.byref(opts), Bs, nrm, _stream(stream)))
+    for t, b in zip(transports, n_bounces):
+        t.nb = int(b)
+    out_norms = None
+    if norms:
+        out_norms = [[nrm[s * RGS_MAX_BOUNCES + b] for b in range(int(n_bounces[s]))] for s in range(m)]
+    return B_outs, out_norms
