@@ -2,7 +2,8 @@
 """Throughput of the surfel light-transport hot path on one or more GB300s.
 
 A step is one pass of the whole path on the 50,000-surfel fruit-bowl scene (SH degree
-3, 256 hemisphere rays per surfel, 4 bounces, one point light): scene build (frames,
+3, 256 hemisphere rays per surfel, 4 bounces, one point light; `--workload` selects the
+200,000-surfel 100-light batch or the 32-scene uneven batch instead): scene build (frames,
 BRDF coefficients, Morton sort, BVH), hemisphere and shadow-ray tracing with alpha
 compositing, the bounce iteration, and the adjoint (transposed bounces, emission,
 albedo and opacity gradients).  Metric: surfel x light x bounces per second.
@@ -37,6 +38,9 @@ WORKLOAD = ("fruit bowl: 50,000 Gaussian surfels on 12 spheres in a hemispherica
 MULTI_WORKLOAD = ("multi-light batch: 200,000 fruit-bowl surfels, 100 point lights on a Fibonacci sphere of radius 3 "
                   "(intensity U[5,20]) as 300 right-hand sides, SH degree 3, 256 rays/surfel, 4 bounces, "
                   "forward + adjoint")
+UNEVEN_WORKLOAD = ("uneven batch: 32 independent fruit-bowl scenes (seeds 1000..1031), surfel counts log-uniform in "
+                   "[5,000, 300,000], SH degree 2 or 3, 128/192/256 rays/surfel, 3-5 bounces, 8 point lights each; "
+                   "all bounces of all scenes in one persistent graph-captured launch (autotuned), forward + adjoint")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -61,33 +65,50 @@ NCU_TRAFFIC = {
 }
 
 
-def algorithmic_bytes(kernel, info, n, nd, nb, C, nc):
-    """Compulsory HBM bytes of one launch of `kernel` (reads + writes, each array once)."""
+def _launch_bytes(kernel, sc):
+    """Compulsory HBM bytes of ONE launch of `kernel` on scene `sc` (each array read or
+    written once) and the number of such launches in one step; (None, 0) if unknown."""
+    n, nd, nb, C, nc, H = sc["n"], sc["nd"], sc["nb"], sc["C"], sc["nc"], sc["n_hits"]
     A = n * C * nc * 4          # one [N][C][nc] float array
-    H = info["n_hits"]
     rays = n * nd
     tile = A * 3 // C           # one 3-column tile of such an array
-    if kernel == "k_bounce":      # records + counts + directions + B^(k-1) + S in; Q, B^(k) out
-        return H * 8 + rays * (4 + 8 + 16) + 4 * A
-    if kernel == "k_adj_src":     # transposed records, (direction, y) per ray, offsets; v^(a) tile out, u tile r+w
-        return H * 8 + rays * 32 + (n + 1) * 8 + 3 * tile
-    if kernel == "k_adj_ray":     # directions + v^(a-1) tile in; y per ray out
-        return rays * 32 + tile
-    if kernel == "k_opacity_g":   # records (j) + counts + directions; 4 iterates of v and B tiles; g per hit out
-        return H * (8 + 4) + rays * (4 + 8 + 16) + 2 * min(nb, 4) * tile
-    if kernel == "k_opacity_rec":  # records (j, a) + G + g per hit, counts; dL/do
-        return H * (8 + 4 + 4) + rays * (4 + 8) + n * 4
-    tiles = (C + 31) // 32
-    A16 = n * C * 16 * 2        # BF16 copy of an iterate (rows padded to 16)
-    if kernel == "k_bounce_mc":   # per 32-column tile: records, counts, offsets, directions; iterate rows once
-        return tiles * (H * 8 + rays * (4 + 8 + 16)) + A16 + 4 * A + A16
-    if kernel == "k_opacity_g_mc":  # per tile: records + ray data; 4 iterates of v (FP32) and B (BF16); g per hit
-        return tiles * (H * (8 + 4) + rays * (4 + 8 + 16)) + min(nb, 4) * (A + A16)
-    if kernel == "k_adj_src_mc":  # per tile: transposed records, directions, y; v tile out, u r+w
-        return tiles * (H * 8 + rays * (16 + 128) + (n + 1) * 8) + 3 * A
-    if kernel == "k_trace_hemi":  # scene (64 B/surfel + 64 B/node) in; records, counts, directions out
-        return n * 64 + (n - 1) * 64 + H * 12 + rays * (4 + 8 + 16) + n * 4
-    return None
+    T3 = C // 3                 # 3-column tiles
+    tiles = (C + 31) // 32      # 32-column tiles
+    A16 = n * C * (16 if nc >= 9 else nc) * 2  # BF16 copy of an iterate (rows padded)
+    bounce = H * 8 + rays * (4 + 8 + 16) + 4 * A  # records, counts, offsets, directions; B^(k-1), S in; Q, B^(k) out
+    table = {
+        # scene (64 B/surfel + 64 B/node) in; records (j, a), counts, offsets, directions, per-source counts out
+        "k_trace_hemi": (n * 64 + (n - 1) * 64 + H * 8 + rays * (4 + 8 + 16) + n * 4, 1),
+        "k_bounce": (bounce, nb),
+        "k_bounce_persistent": (bounce * nb, 1),  # summed over the scenes of the launch
+        # transposed records, (direction, y) per ray, offsets; v^(a) tile out, u tile read + written
+        "k_adj_src": (H * 8 + rays * 32 + (n + 1) * 8 + 3 * tile, nb * T3),
+        "k_adj_ray": (rays * 32 + tile, nb * T3),   # directions + v^(a-1) tile in; y per ray out
+        # records (j) + counts + offsets + directions; four iterates of v and B tiles; g per hit out
+        "k_opacity_g": (H * (8 + 4) + rays * (4 + 8 + 16) + 2 * min(nb, 4) * tile, -(-nb // 4) * T3),
+        # records (j) + g per hit, counts, offsets, directions, geometry of the hit surfels; dL/do
+        "k_opacity_rec": (H * (8 + 4) + rays * (4 + 8 + 16) + n * 64 + n * 4, 1),
+        # records in, transposed entries out, counts, offsets, cursors
+        "k_src_fill": (H * 16 + rays * 12 + n * 8, 1),
+        # per 32-column tile: records, counts, offsets, directions; the iterate rows once
+        "k_bounce_mc": (tiles * (H * 8 + rays * (4 + 8 + 16)) + A16 + 4 * A + A16, nb),
+        # one tile and up to four iterates: records + ray data; v (FP32) and B (BF16) tiles; g per hit
+        "k_opacity_g_mc": (H * (8 + 4) + rays * (4 + 8 + 16) + min(nb, 4) * (A + A16) // tiles, -(-nb // 4) * tiles),
+        # one tile: transposed records, directions, y; v tile out, u read + written
+        "k_adj_src_mc": (H * 8 + rays * (16 + 128) + (n + 1) * 8 + 3 * A // tiles, nb * tiles),
+    }
+    return table.get(kernel, (None, 0))
+
+
+def step_algorithmic_bytes(kernel, scenes_info):
+    """Compulsory HBM bytes of all launches of `kernel` in one step over the given scenes."""
+    total = 0
+    for sc in scenes_info:
+        b, cnt = _launch_bytes(kernel, sc)
+        if b is None:
+            return None
+        total += b * cnt
+    return total
 
 
 class Clocks:
@@ -183,6 +204,43 @@ def run_reference(args):
     return 0
 
 
+class Form:
+    """One way of running the step over the workload's scenes: per-scene pipelines with
+    their output buffers; `launch` = "batched" solves every scene in one rgs_solve_batched
+    call (the persistent graph-captured kernel), "per_scene" calls rgs_solve per scene."""
+
+    def __init__(self, api, rgs, torch, datas, precision, launch, dev):
+        self.api, self.rgs, self.torch = api, rgs, torch
+        self.precision, self.launch = precision, launch
+        self.pipes = [api.Pipeline(precision=precision) for _ in datas]
+        self.Bs = [torch.empty((d["n"], (d["L"] + 1) ** 2, 3 * max(1, d["light_pos"].shape[0])), device=dev)
+                   for d in datas]
+        self.grads = [(torch.empty((d["n"], (d["L"] + 1) ** 2, 3), device=dev), torch.empty((d["n"], 3), device=dev),
+                       torch.empty((d["n"],), device=dev)) for d in datas]
+
+    def step(self, datas, gs, Bs=None, grads=None):
+        Bs = self.Bs if Bs is None else Bs
+        grads = self.grads if grads is None else grads
+        for p, d in zip(self.pipes, datas):
+            p.build(d)
+            p.trace(d)
+        if self.launch == "batched":
+            self.rgs.rgs_solve_batched([p.transport for p in self.pipes], [d["E"] for d in datas],
+                                       [d["nb"] for d in datas], precision=self.precision, B_outs=Bs)
+        else:
+            for p, d, B in zip(self.pipes, datas, Bs):
+                p.solve(d["E"], d["nb"], B_out=B)
+        for p, g, gr in zip(self.pipes, gs, grads):
+            p.adjoint(g, gr)
+        return Bs, grads
+
+
+def _rel(a_list, b_list, torch):
+    num = sum(float(torch.linalg.norm(a.double() - b.double()) ** 2) for a, b in zip(a_list, b_list))
+    den = sum(float(torch.linalg.norm(b.double()) ** 2) for b in b_list)
+    return math.sqrt(num / den) if den > 0 else 0.0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,8 +248,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=50000, help="surfel count (default: the 50,000-surfel workload)")
-    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light"],
-                    help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights")
+    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven"],
+                    help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights; "
+                         "uneven: 32 scenes of uneven size in one persistent launch")
     ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1500, help="surfels per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -215,40 +274,44 @@ def main():
     build.build()
     rgs.load()
     if args.workload == "multi_light":
-        sc = scenes.multi_light(n=200000 if args.n == 50000 else args.n)
+        scs = [scenes.multi_light(n=200000 if args.n == 50000 else args.n)]
+        workload = MULTI_WORKLOAD
+    elif args.workload == "uneven":
+        scs = scenes.uneven_batch(32)
+        workload = UNEVEN_WORKLOAD
     else:
-        sc = scenes.fruit_bowl(n=args.n)
-    n, nd, nb, nc, nl = sc["n"], sc["nd"], sc["nb"], 16, sc["light_pos"].shape[0]
-    C = 3 * nl
-    units_per_step = n * nl * nb
+        scs = [scenes.fruit_bowl(n=args.n)]
+        workload = WORKLOAD
+    units_per_step = sum(sc["n"] * sc["light_pos"].shape[0] * sc["nb"] for sc in scs)
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    d = api.upload(sc, device=dev)
-    g = torch.as_tensor(np.random.default_rng(1).normal(size=(n, nc, C)).astype(np.float32), device=dev)
+    datas = [api.upload(sc, device=dev) for sc in scs]
+    rng = np.random.default_rng(1)
+    gs = [torch.as_tensor(rng.normal(size=(sc["n"], (sc["L"] + 1) ** 2, 3 * sc["light_pos"].shape[0]))
+                          .astype(np.float32), device=dev) for sc in scs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def make(precision):
-        B = torch.empty((n, nc, C), device=dev)
-        grads = (torch.empty((n, nc, 3), device=dev), torch.empty((n, 3), device=dev), torch.empty((n,), device=dev))
-        return api.Pipeline(precision=precision), B, grads
-
-    # batched form (BF16 gathers, FP32 accumulation, one FP32 residual-correction bounce)
-    # and the plain FP32 form, on the same inputs
-    forms = {"batched": make(rgs.RGS_BF16_FP32ACC_RESCORR), "plain": make(rgs.RGS_FP32)}
-    for pipe, B, grads in forms.values():
+    # batched form (BF16 gathers, FP32 accumulation, one FP32 residual-correction bounce;
+    # scenes of a batch in one persistent launch) and the plain FP32 form, on the same inputs
+    batched_launch = "batched" if len(scs) > 1 else "per_scene"
+    forms = {"batched": Form(api, rgs, torch, datas, rgs.RGS_BF16_FP32ACC_RESCORR, batched_launch, dev),
+             "plain": Form(api, rgs, torch, datas, rgs.RGS_FP32, "per_scene", dev)}
+    for f in forms.values():
         for _ in range(max(args.warmup, 3)):
-            pipe.step(d, g, B_out=B, grads=grads)
+            f.step(datas, gs)
     torch.cuda.synchronize()
-    info = rgs.rgs_transport_info_get(forms["batched"][0].transport)
+    infos = []
+    for sc, p in zip(scs, forms["batched"].pipes):
+        info = rgs.rgs_transport_info_get(p.transport)
+        infos.append(dict(n=sc["n"], nd=sc["nd"], nb=sc["nb"], C=info["n_cols"], nc=info["nc"], n_hits=info["n_hits"]))
     # accuracy of the batched form against the FP32 form (which the tests hold to 1e-4 of the oracle)
-    Bb, Bp = forms["batched"][1].double(), forms["plain"][1].double()
-    rel_err = float(torch.linalg.norm(Bb - Bp) / torch.linalg.norm(Bp))
-    grad_err = max(float(torch.linalg.norm(a.double() - b.double()) / torch.linalg.norm(b.double()))
-                   for a, b in zip(forms["batched"][2], forms["plain"][2]))
+    rel_err = _rel(forms["batched"].Bs, forms["plain"].Bs, torch)
+    grad_err = max(_rel([g[q] for g in forms["batched"].grads], [g[q] for g in forms["plain"].grads], torch)
+                   for q in range(3))
 
     def timed(form, profile):
-        pipe, B, grads = forms[form]
+        f = forms[form]
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if world > 1:
             dist.barrier()
@@ -261,7 +324,7 @@ def main():
         for k in range(args.steps):
             flush.zero_()  # evict L2 between steps (outside the step's events)
             ev[k][0].record(stream)
-            pipe.step(d, g, B_out=B, grads=grads)
+            f.step(datas, gs)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -288,26 +351,30 @@ def main():
     value_o, step_ms_o, _, _, _ = timed(other, False)
     value_b, value_p = (value, value_o) if headline == "batched" else (value_o, value)
     step_ms_b, step_ms_p = (step_ms, step_ms_o) if headline == "batched" else (step_ms_o, step_ms)
-    pipe, B, grads = forms[headline]
+    f = forms[headline]
 
     # ---------------------------------------------------------- end to end (host buffers)
-    host = {k: d[k].cpu().pin_memory() for k in api.SURFEL_KEYS + ("light_pos", "light_I")}
-    g_host = g.cpu().pin_memory()
-    outs_host = [torch.empty(B.shape, pin_memory=True)] + [torch.empty(x.shape, pin_memory=True) for x in grads]
-    d_e2e = dict(d)
-    h2d = sum(v.numel() * 4 for v in host.values()) + g_host.numel() * 4
-    d2h = sum(x.numel() * 4 for x in outs_host)
+    keys = api.SURFEL_KEYS + ("light_pos", "light_I")
+    hosts = [{k: d[k].cpu().pin_memory() for k in keys} for d in datas]
+    g_hosts = [g.cpu().pin_memory() for g in gs]
+    outs_host = [[torch.empty(B.shape, pin_memory=True)] + [torch.empty(x.shape, pin_memory=True) for x in gr]
+                 for B, gr in zip(f.Bs, f.grads)]
+    d_e2e = [dict(d) for d in datas]
+    h2d = sum(v.numel() * 4 for h in hosts for v in h.values()) + sum(g.numel() * 4 for g in g_hosts)
+    d2h = sum(x.numel() * 4 for o in outs_host for x in o)
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.zero_()
         e2e_ev[k][0].record(stream)
-        for key, v in host.items():
-            d_e2e[key] = v.to(dev, non_blocking=True)
-        g_dev = g_host.to(dev, non_blocking=True)
-        Bk, gr = pipe.step(d_e2e, g_dev)
-        for dst, src in zip(outs_host, (Bk,) + tuple(gr)):
-            dst.copy_(src, non_blocking=True)
+        for de, h in zip(d_e2e, hosts):
+            for key, v in h.items():
+                de[key] = v.to(dev, non_blocking=True)
+        g_dev = [g.to(dev, non_blocking=True) for g in g_hosts]
+        Bk, gk = f.step(d_e2e, g_dev)
+        for o, B, gr in zip(outs_host, Bk, gk):
+            for dst, src in zip(o, (B,) + tuple(gr)):
+                dst.copy_(src, non_blocking=True)
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
@@ -324,40 +391,52 @@ def main():
 
     # ---------------------------------------------------------- roofline of the dominant kernel
     peak, peak_kind = _peaks()
-    kernels = {k: {"launches_per_step": c / args.steps, "ms_per_step": ms / args.steps,
-                   "share": ms / max(1e-9, sum(v[1] for v in prof.values()))} for k, (c, ms) in prof.items()}
+    tot_ms = max(1e-9, sum(v[1] for v in prof.values()))
+    kernels = {k: {"launches_per_step": c / args.steps, "ms_per_step": ms / args.steps, "share": ms / tot_ms}
+               for k, (c, ms) in prof.items()}
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
     c_dom, ms_dom = prof[dom]
-    alg = algorithmic_bytes(dom, info, n, nd, nb, C, nc)
-    avg_ms = ms_dom / c_dom
-    achieved = alg / (avg_ms * 1e-3) / 1e9 if alg else None
+    alg_step = step_algorithmic_bytes(dom, infos)
+    ms_dom_step = ms_dom / args.steps
+    achieved = alg_step / (ms_dom_step * 1e-3) / 1e9 if alg_step else None
+    launches_dom = c_dom / args.steps
     src_file = {"k_bounce": "rgs_solve.cu", "k_adj_src": "rgs_adjoint.cu", "k_adj_ray": "rgs_adjoint.cu",
                 "k_bounce_mc": "rgs_manycol.cu", "k_opacity_g_mc": "rgs_manycol.cu", "k_adj_src_mc": "rgs_manycol.cu",
                 "k_opacity_g": "rgs_adjoint.cu", "k_opacity_rec": "rgs_adjoint.cu",
-                "k_trace_hemi": "rgs_trace.cu"}.get(dom)
+                "k_bounce_persistent": "rgs_batch.cu", "k_trace_hemi": "rgs_trace.cu"}.get(dom)
     traffic = None
-    if dom in NCU_TRAFFIC and src_file and NCU_TRAFFIC[dom]["src_sha"] == _src_sha(src_file):
-        traffic = NCU_TRAFFIC[dom]["bytes_per_launch"] * (n / NCU_TRAFFIC[dom]["n"])
+    if len(scs) == 1 and dom in NCU_TRAFFIC and src_file and NCU_TRAFFIC[dom]["src_sha"] == _src_sha(src_file):
+        traffic = NCU_TRAFFIC[dom]["bytes_per_launch"] * (scs[0]["n"] / NCU_TRAFFIC[dom]["n"])
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "algorithmic_bytes": alg, "avg_launch_ms": avg_ms, "peak_source": peak_kind}
+                "algorithmic_bytes": alg_step / launches_dom if alg_step else None,
+                "avg_launch_ms": ms_dom_step / launches_dom, "peak_source": peak_kind}
 
     cb = None
     if not args.no_cpu_baseline and world == 1:
         cb, _ = cpu_baseline(args.cpu_sample)
 
+    if len(scs) == 1:
+        sc = scs[0]
+        config = {"workload": workload, "n_surfels": sc["n"], "sh_degree": sc["L"], "rays_per_surfel": sc["nd"],
+                  "bounces": sc["nb"], "lights": int(sc["light_pos"].shape[0]), "hit_records": infos[0]["n_hits"]}
+    else:
+        config = {"workload": workload, "scenes": len(scs), "n_surfels_total": sum(x["n"] for x in scs),
+                  "rays_total": sum(x["n"] * x["nd"] for x in scs), "lights_per_scene": 8,
+                  "hit_records": sum(x["n_hits"] for x in infos), "units_per_step": units_per_step}
+    config.update({"precision": headline, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3),
             "ms_per_step": sum(step_ms) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16-gather/f32-acc" if headline == "batched" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "fruit_bowl" else MULTI_WORKLOAD, "n_surfels": n, "sh_degree": 3, "rays_per_surfel": nd, "bounces": nb,
-                       "lights": nl, "precision": headline, "l2": "flushed between steps (512 MiB write)",
-                       "parallelism": f"replicas x{world}", "hit_records": info["n_hits"]},
+            "config": config,
             "batched_vs_plain": {"batched": value_b, "plain": value_p, "speedup": value_b / value_p,
                                  "batched_rel_l2_vs_fp32": rel_err, "batched_grad_rel_l2_vs_fp32": grad_err,
                                  "plain_ms_per_step": sum(step_ms_p) / args.steps,
-                                 "batched_ms_per_step": sum(step_ms_b) / args.steps},
+                                 "batched_ms_per_step": sum(step_ms_b) / args.steps,
+                                 "batched_launch": batched_launch},
             "roofline": roofline, "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clk, "wall_s_timed": t_wall, "kernels": kernels}

@@ -125,7 +125,8 @@ typedef struct rgs_solve_stats {
 typedef struct rgs_transport_info {
     int32_t n, sh_degree, nc, n_cols, nd, n_lights;
     int64_t n_hits, n_hit_slots, n_full_rays;
-    int64_t device_bytes; /* device memory held by the transport handle */
+    int64_t device_bytes; /* device memory held by the transport handle (not counting the shared
+                             workspace pool that rgs_adjoint and rgs_get_iterate draw from) */
 } rgs_transport_info;
 
 /* ---------------------------------------------------------------- entry points */
@@ -144,8 +145,8 @@ rgs_status rgs_build_scene(const rgs_surfels *surfels, const rgs_build_opts *opt
 
 /* Traces N * nd stratified cosine-weighted hemisphere rays from the surfel centres over
  * their front hemispheres (App. B; weight pi/nd), alpha-composites the hits in depth order
- * (Eq. L_I) and stores per-ray hit records (source surfel, compositing weight, Gaussian
- * value); traces the N * NL shadow rays of the direct term (Sec. 5.2) and forms
+ * (Eq. L_I) and stores per-ray hit records (source surfel, compositing weight: 8 bytes
+ * per hit); traces the N * NL shadow rays of the direct term (Sec. 5.2) and forms
  * S = E + D (E added in rgs_solve).  Rays start at the surfel centre (kappa_i = Dirac),
  * a surfel never hits itself (Sec. 5.1) nor planes within eps = 1e-5 * (bounding-box
  * diagonal) of the ray origin; compositing stops once the transmittance drops below 1e-6.
@@ -178,7 +179,12 @@ rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_
  *   dL/do[i]         = receiver factor + backward through the compositing of every
  *                      hemisphere and shadow ray that hits surfel i           (device [N])
  * Each output may be NULL (not computed).  dL_dB: device [N][nc][C].
- * Asynchronous.  Errors: RGS_ERR_STATE (no prior rgs_solve), RGS_ERR_ARG, RGS_ERR_CUDA. */
+ * K^T is a gather over the hit records grouped by source surfel; that transposed index is
+ * built at the start of every call, in the workspace pool (see rgs_trim_workspace) with
+ * the call's other scratch, and returned to the pool at its end.  After a checkpointed
+ * solve (rgs_set_checkpointing) the iterates between checkpoints are recomputed here.
+ * Asynchronous.  Errors: RGS_ERR_STATE (no prior rgs_solve), RGS_ERR_ARG, RGS_ERR_OOM,
+ * RGS_ERR_CUDA. */
 rgs_status rgs_adjoint(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo, float *dL_dopacity,
                        void *stream);
 
@@ -214,8 +220,30 @@ rgs_status rgs_solve_batched(rgs_transport *const *ts, int32_t count, const floa
                              double *residual_norms, void *stream);
 
 /* Copies iterate B^(b) (0 <= b <= last n_bounces) of the last rgs_solve to the device
- * array out [N][nc][C].  Asynchronous.  Errors: RGS_ERR_STATE, RGS_ERR_ARG, RGS_ERR_CUDA. */
+ * array out [N][nc][C].  An iterate that a checkpointed solve did not keep is recomputed
+ * from the checkpoint below it (bit-identical to the solve's value) in pooled scratch.
+ * Asynchronous.  Errors: RGS_ERR_STATE, RGS_ERR_ARG, RGS_ERR_OOM, RGS_ERR_CUDA. */
 rgs_status rgs_get_iterate(rgs_transport *t, int32_t b, float *out, void *stream);
+
+/* Iterate storage of the following rgs_solve calls on t (bounce-iterate checkpointing):
+ *   stride = 0 : keep every B^(b) and Q^(b) for the adjoint (default, fastest adjoint);
+ *   stride = s >= 1 : keep only the checkpoints B^(0), B^(s), B^(2s), ... below n_bounces and
+ *                two running iterates; rgs_adjoint recomputes the others segment by segment
+ *                from the checkpoint below them (one extra forward pass, bit-identical
+ *                iterates), holding s iterates at a time;
+ *   stride = -1 : automatic -- every iterate is kept when the solve's and the adjoint's
+ *                buffers fit in free device memory, else s = ceil(sqrt(n_bounces)).
+ * rgs_solve_batched always keeps every iterate.  Host-only.  Errors: RGS_ERR_ARG
+ * (stride < -1 or > RGS_MAX_BOUNCES). */
+rgs_status rgs_set_checkpointing(rgs_transport *t, int32_t stride);
+
+/* Workspace pool: the per-call scratch of rgs_adjoint (the transposed hit index, 8 bytes per
+ * hit; per-hit opacity sums, 4 bytes; v^(a) and u; per-ray adjoint values) and of
+ * rgs_get_iterate comes from one stream-ordered memory pool per device, so transports used
+ * one after another on a stream share it.  The pool keeps its memory reserved between calls;
+ * this returns the unused part to the device.  Synchronises the current device.
+ * Errors: RGS_ERR_CUDA. */
+rgs_status rgs_trim_workspace(void);
 
 /* FP64 residual norm ||x - y||_2 of two device float arrays of n elements, written to the
  * device double *norm_out -- the same quantity rgs_solve reports per bounce, for two

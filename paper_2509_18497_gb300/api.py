@@ -25,12 +25,14 @@ def upload(sc, device="cuda"):
 
 class Pipeline:
     """Reusable handles for one scene shape: build, trace, solve and adjoint in sequence.
-    Handles (and their device workspaces) are reused across calls, so steady-state steps
-    allocate nothing inside the library."""
+    Handles and their buffers are reused across calls; the adjoint's scratch comes from the
+    library's stream-ordered pool, which keeps it reserved, so steady-state steps make no
+    cudaMalloc inside the library."""
 
-    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32):
+    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32, checkpoint=0):
         self.alpha_model = alpha_model
         self.precision = precision
+        self.checkpoint = checkpoint  # iterate checkpoint stride (0 all kept, -1 automatic)
         self.scene = None
         self.transport = None
 
@@ -43,6 +45,7 @@ class Pipeline:
         self.transport = rgs.rgs_trace_transport(self.scene, d["light_pos"], d["light_I"], d["nd"], d["seed"],
                                                  hit_capacity=hit_capacity, stream=stream,
                                                  transport=self.transport)
+        rgs.rgs_set_checkpointing(self.transport, self.checkpoint)
         return self.transport
 
     def solve(self, E, nb, B_out=None, stats=False, stream=None, precision=None):

@@ -11,6 +11,8 @@
 // gathers (d, y) per entry, 32 bytes, instead of a 192-byte row of v_i per entry.
 // k_opacity_g / k_opacity_rec and k_shadow_bwd run the compositing backward of every
 // hemisphere and shadow ray (dL/dalpha_h = T_h (g_h - R_h), dL/dT = -prod of the other (1 - alpha)).
+#include <vector>
+
 #include "rgs_internal.cuh"
 
 namespace {
@@ -183,10 +185,8 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, const float *__restrict__ lpos
 //   y_r^(a)[c] = (pi/nd) o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) v_i^(a)[c][k'],
 // accumulated into gh[slot] for iterates a0 .. a0+na-1 (first chunk writes, later add).
 template <int NC, int CT, int NA, class SLB>
-__global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, int C, int col0, int nb, int a0, int na,
-                                                   size_t A, const float *__restrict__ V,
-                                                   const typename SLB::T *__restrict__ Bit, size_t AB, float *gh,
-                                                   bool first) {
+__global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, int C, int col0, int na,
+                                                   OpaSet<typename SLB::T, NA> it, float *gh, bool first) {
     using SL = Slice<NC>;
     constexpr int G = SL::G, KPL = SL::KPL;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, in
                 if (aa < na) {
                     const int ch = (col0 + c) % 3;
                     float v[KPL];
-                    SL::load(V + A * (a0 + aa) + ((size_t)i * C + col0 + c) * NC, g, v);
+                    SL::load(it.v[aa] + ((size_t)i * C + col0 + c) * NC, g, v);
 #pragma unroll
                     for (int m = 0; m < KPL; ++m) {
                         const int kk = SL::k(g, m);
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, in
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
             if (aa < na && h < cnt) {
-                const typename SLB::T *Bj = Bit + AB * (nb - 1 - (a0 + aa)) + ((size_t)j * C + col0) * SLB::STRIDE;
+                const typename SLB::T *Bj = it.b[aa] + ((size_t)j * C + col0) * SLB::STRIDE;
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
                     float v[KPL];
@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, in
 
 // Hemisphere rays, part 2: back to front, R_{h-1} = alpha_h g_h + (1 - alpha_h) R_h and
 // dL/do_{j_h} += T_h (g_h - R_h) G_h, with T_h the transmittance in front of hit h.
+// G_h is recomputed from the stored direction (bit-identical to the trace's value).
 __global__ void __launch_bounds__(256) k_opacity_rec(SceneDev sc, RaysDev rays, const float *__restrict__ gh,
                                                      float *dop) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,18 +266,23 @@ __global__ void __launch_bounds__(256) k_opacity_rec(SceneDev sc, RaysDev rays, 
     const int cnt = rays.cnt[r];
     if (cnt == 0) return;
     const long long base = rays.off[r];
-    float Th[RGS_HMAX];
+    const int i = r / rays.nd;
+    const float3 o = f3(sc.P[i]);
+    const float3 d = f3(rays.dir[r]);
+    float Th[RGS_HMAX], Gh[RGS_HMAX];
     float T = 1.f;
     for (int h = 0; h < cnt; ++h) {
+        const int j = __ldg(&rays.rec_ja[base + h]).x;
+        const float G = stored_hit_G(sc, j, o, d);
         Th[h] = T;
-        const long long slot = base + h;
-        T *= 1.f - __ldg(&sc.P[__ldg(&rays.rec_ja[slot]).x].w) * __ldg(&rays.rec_g[slot]);
+        Gh[h] = G;
+        T *= 1.f - __ldg(&sc.P[j].w) * G;
     }
     float R = 0.f;
     for (int h = cnt - 1; h >= 0; --h) {
         const long long slot = base + h;
         const int j = __ldg(&rays.rec_ja[slot]).x;
-        const float G = __ldg(&rays.rec_g[slot]);
+        const float G = Gh[h];
         const float alpha = __ldg(&sc.P[j].w) * G;
         const float g = gh[slot];
         const float da = Th[h] * (g - R);
@@ -311,65 +317,166 @@ __global__ void k_finalize(SceneDev sc, int C, const float *__restrict__ u, cons
     }
 }
 
+// transposed index: the records of every ray scattered into per-source lists of (ray, a)
+__global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const long long base = rays.off[r];
+    const int c = rays.cnt[r];
+    for (int h = 0; h < c; ++h) {
+        const int2 ja = rays.rec_ja[base + h];
+        const unsigned long long pos = atomicAdd(&cursor[ja.x], 1ull);
+        tr[pos] = make_int2(r, ja.y);
+    }
+}
+
+__global__ void k_copy_off(const long long *off, unsigned long long *cursor, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cursor[i] = (unsigned long long)off[i];
+}
+
+
+// g_h (+)= the na iterates of one group, all column tiles; first: the group that writes gh
+template <int NC>
+rgs_status opacity_group(rgs_transport *t, SceneDev sd, RaysDev rd, int na, const float *const *v,
+                         const float *const *Bf, const __nv_bfloat16 *const *Bh, bool first, cudaStream_t st) {
+    if (wide_opacity(t->C, Bh != nullptr)) return mc_opacity<NC>(t, sd, rd, na, v, Bf, Bh, first, st);
+    constexpr int NA = 4;
+    const long long n_rays = (long long)t->n * t->nd;
+    const unsigned gg = (unsigned)((n_rays * Slice<NC>::G + 255) / 256);
+    OpaSet<float, NA> sf = {};
+    OpaSet<__nv_bfloat16, NA> sh = {};
+    for (int a = 0; a < na; ++a) {
+        sf.v[a] = sh.v[a] = v[a];
+        sf.b[a] = Bf[a];
+        sh.b[a] = Bh ? Bh[a] : nullptr;
+    }
+    for (int col0 = 0; col0 < t->C; col0 += 3) {
+        const bool wr = first && col0 == 0;
+        if (Bh) { // the batched modes gather the BF16 iterate copies
+            ProfScope ps_("k_opacity_g", st);
+            k_opacity_g<NC, 3, NA, SliceH<NC>><<<gg, 256, 0, st>>>(sd, rd, t->C, col0, na, sh, t->gh, wr);
+        } else {
+            ProfScope ps_("k_opacity_g", st);
+            k_opacity_g<NC, 3, NA, Slice<NC>><<<gg, 256, 0, st>>>(sd, rd, t->C, col0, na, sf, t->gh, wr);
+        }
+    }
+    RGS_LAUNCH("opacity gather");
+    return RGS_OK;
+}
+
+// The adjoint walks the bounces backwards, b = n-1 .. 0 (a = n-1-b = 0 .. n-1), in segments
+// [lo, hi] that end at a stored iterate: one segment holding everything when every iterate
+// was kept, else one per checkpoint, whose B^(b) and Q^(b) are recomputed from B^(lo) into
+// pooled scratch before the segment's v^(a) are formed and used.
 template <int NC>
 rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, float *dopo, cudaStream_t st) {
-    const int n = t->n, C = t->C, nb = t->nb_last;
+    const int n = t->n, C = t->C, nb = t->nb_last, s = t->stride;
     const size_t A = t->arr();
+    const size_t A16 = (size_t)n * C * bf16_stride<NC>();
+    const bool bf16 = t->prec_last != RGS_FP32;
+    const bool mc = wide_adjoint(C);
     SceneDev sd = t->sc->dev();
     RaysDev rd = t->rays();
     const unsigned ga = (unsigned)((A + 255) / 256);
+    const unsigned gn = (unsigned)((n + 127) / 128);
+    const long long n_rays = (long long)n * t->nd;
+    const unsigned gr = (unsigned)((n_rays + 255) / 256);
+    auto vp = [&](int a) { return t->v + A * (s ? a % (s + 1) : a); };
     // v^(0) = g (internal layout), u = v^(0), P = 0, dop = 0
-    { ProfScope ps_("k_from_user", st); k_from_user<NC><<<ga, 256, 0, st>>>(n, C, t->sc->uid, g, t->v); }
-    RGS_CUDA(cudaMemcpyAsync(t->u, t->v, sizeof(float) * A, cudaMemcpyDeviceToDevice, st));
+    { ProfScope ps_("k_from_user", st); k_from_user<NC><<<ga, 256, 0, st>>>(n, C, t->sc->uid, g, vp(0)); }
+    RGS_CUDA(cudaMemcpyAsync(t->u, vp(0), sizeof(float) * A, cudaMemcpyDeviceToDevice, st));
     RGS_CUDA(cudaMemsetAsync(t->Pg, 0, sizeof(float) * 12 * (size_t)n, st));
     RGS_CUDA(cudaMemsetAsync(t->dop, 0, sizeof(float) * (size_t)n, st));
     RGS_LAUNCH("adjoint init");
-    const unsigned gn = (unsigned)((n + 127) / 128);
-    if (nb >= 1) { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, t->v, t->Q + A * (nb - 1), t->Pg); }
-    const long long n_rays = (long long)n * t->nd;
-    const unsigned gr = (unsigned)((n_rays + 255) / 256);
-    const bool mc = C >= RGS_MC_MIN_COLS;
-    for (int a = 1; a <= nb; ++a) {
-        if (mc) {
-            rgs_status r = mc_adjoint_bounce<NC>(t, sd, rd, t->v + A * (a - 1), t->v + A * a, st);
-            if (r != RGS_OK) return r;
-        }
-        for (int col0 = 0; !mc && col0 < C; col0 += 3) {
-            { ProfScope ps_("k_adj_ray", st); k_adj_ray<NC><<<gr, 256, 0, st>>>(sd, rd, C, col0, t->v + A * (a - 1), t->dy); }
-            { ProfScope ps_("k_adj_src", st); k_adj_src<NC><<<n, ADJ_THREADS, 0, st>>>(rd, C, col0, t->src_off, t->tr, t->dy, t->v + A * a, t->u); }
+    auto KT = [&](int a) -> rgs_status { // v^(a) = K^T v^(a-1), u += v^(a)
+        if (mc) return mc_adjoint_bounce<NC>(t, sd, rd, vp(a - 1), vp(a), st);
+        for (int col0 = 0; col0 < C; col0 += 3) {
+            { ProfScope ps_("k_adj_ray", st); k_adj_ray<NC><<<gr, 256, 0, st>>>(sd, rd, C, col0, vp(a - 1), t->dy); }
+            { ProfScope ps_("k_adj_src", st); k_adj_src<NC><<<n, ADJ_THREADS, 0, st>>>(rd, C, col0, t->src_off, t->tr, t->dy, vp(a), t->u); }
         }
         RGS_LAUNCH("adjoint bounce");
-        if (a <= nb - 1) { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, t->v + A * a, t->Q + A * (nb - 1 - a), t->Pg); }
+        return RGS_OK;
+    };
+    // segment scratch (checkpointing): B^(lo+1 .. lo+s) FP32 (+BF16) and Q^(lo .. lo+s-1)
+    struct SegScratch {
+        cudaStream_t st;
+        std::vector<float *> B, Q;
+        std::vector<__nv_bfloat16 *> B16;
+        double *nrm = nullptr;
+        ~SegScratch() {
+            for (auto &p : B) pool_release(p, st);
+            for (auto &p : Q) pool_release(p, st);
+            for (auto &p : B16) pool_release(p, st);
+            pool_release(nrm, st);
+        }
+    } seg{st, {}, {}, {}, nullptr};
+    rgs_status r;
+    if (s) {
+        seg.B.assign(s, nullptr);
+        seg.Q.assign(s, nullptr);
+        seg.B16.assign(s, nullptr);
+        for (int k = 0; k < s; ++k) {
+            if ((r = pool_alloc(&seg.B[k], A, st)) != RGS_OK) return r;
+            if ((r = pool_alloc(&seg.Q[k], A, st)) != RGS_OK) return r;
+            if (bf16) {
+                if ((r = pool_alloc(&seg.B16[k], A16, st)) != RGS_OK) return r;
+                RGS_CUDA(cudaMemsetAsync(seg.B16[k], 0, sizeof(__nv_bfloat16) * A16, st)); // row padding
+            }
+        }
+        if ((r = pool_alloc(&seg.nrm, RGS_MAX_BOUNCES + 1, st)) != RGS_OK) return r;
     }
+    bool first_g = true;
+    for (int hi = nb - 1; hi >= 0;) {
+        const int lo = s ? (hi / s) * s : 0;
+        // iterates B^(b) (FP32, BF16) and Q^(b) of this segment, indexed by b - lo
+        std::vector<const float *> Bf(hi - lo + 1), Qb(hi - lo + 1);
+        std::vector<const __nv_bfloat16 *> Bh(hi - lo + 1);
+        if (!s) {
+            for (int b = lo; b <= hi; ++b) {
+                Bf[b - lo] = t->iters + A * b;
+                Bh[b - lo] = bf16 ? t->iters16 + A16 * b : nullptr;
+                Qb[b - lo] = t->Q + A * b;
+            }
+        } else {
+            if ((r = rgs_recompute(t, lo, hi + 1, seg.B.data(), seg.B16.data(), seg.Q.data(), seg.nrm, st)) != RGS_OK)
+                return r;
+            for (int b = lo; b <= hi; ++b) {
+                Bf[b - lo] = b == lo ? t->iters + A * t->slot(lo) : seg.B[b - lo - 1];
+                Bh[b - lo] = !bf16 ? nullptr : (b == lo ? t->iters16 + A16 * t->slot(lo) : seg.B16[b - lo - 1]);
+                Qb[b - lo] = seg.Q[b - lo];
+            }
+        }
+        for (int b = hi; b >= lo; --b) {
+            const int a = nb - 1 - b;
+            if (a > 0 && (r = KT(a)) != RGS_OK) return r;
+            { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, vp(a), Qb[b - lo], t->Pg); }
+            RGS_LAUNCH("pair accum");
+        }
+        if (dopo) { // g_h over this segment's iterates, four per launch
+            for (int b0 = hi; b0 >= lo; b0 -= 4) {
+                const int na = min(4, b0 - lo + 1);
+                const float *vv[4], *bb[4];
+                const __nv_bfloat16 *hh[4];
+                for (int q = 0; q < na; ++q) {
+                    const int b = b0 - q;
+                    vv[q] = vp(nb - 1 - b);
+                    bb[q] = Bf[b - lo];
+                    hh[q] = Bh[b - lo];
+                }
+                if ((r = opacity_group<NC>(t, sd, rd, na, vv, bb, bf16 ? hh : nullptr, first_g, st)) != RGS_OK) return r;
+                first_g = false;
+            }
+        }
+        hi = lo - 1;
+    }
+    if (nb >= 1 && (r = KT(nb)) != RGS_OK) return r; // v^(n) only adds to u
     if (t->nl > 0) {
         const int nth = n * t->nl;
         { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, C, t->u, t->Pg, t->dop); }
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
-        if (mc) {
-            rgs_status r = mc_opacity<NC>(t, sd, rd, nb, st);
-            if (r != RGS_OK) return r;
-        } else {
-            constexpr int NA = 4;
-            const unsigned gg = (unsigned)((n_rays * Slice<NC>::G + 255) / 256);
-            for (int col0 = 0; col0 < C; col0 += 3) {
-                for (int a0 = 0; a0 < nb; a0 += NA) {
-                    const int na = min(NA, nb - a0);
-                    const bool first = (a0 == 0 && col0 == 0);
-                    if (t->prec_last != RGS_FP32) { // the batched modes gather the BF16 iterate copies
-                        const size_t A16 = (size_t)n * C * SliceH<NC>::STRIDE;
-                        ProfScope ps_("k_opacity_g", st);
-                        k_opacity_g<NC, 3, NA, SliceH<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v,
-                                                                              t->iters16, A16, t->gh, first);
-                    } else {
-                        ProfScope ps_("k_opacity_g", st);
-                        k_opacity_g<NC, 3, NA, Slice<NC>><<<gg, 256, 0, st>>>(sd, rd, C, col0, nb, a0, na, A, t->v,
-                                                                             t->iters, A, t->gh, first);
-                    }
-                }
-            }
-        }
         { ProfScope ps_("k_opacity_rec", st); k_opacity_rec<<<gr, 256, 0, st>>>(sd, rd, t->gh, t->dop); }
         RGS_LAUNCH("hemisphere opacity backward");
     }
@@ -384,24 +491,43 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
     rgs_status r;
     const int nb = t->nb_last;
     const size_t A = t->arr();
-    if (nb + 1 > t->v_cap) {
-        if ((r = dev_alloc(&t->v, A * (nb + 1), &t->device_bytes)) != RGS_OK) return r;
-        if ((r = dev_alloc(&t->u, A, &t->device_bytes)) != RGS_OK) return r;
-        t->v_cap = nb + 1;
-    }
-    const long long n_rays_all = (long long)t->n * t->nd;
-    if (t->C >= RGS_MC_MIN_COLS && n_rays_all * 32 > t->dy_mc_cap) {
-        if ((r = dev_alloc(&t->dy_mc, (size_t)n_rays_all * 32, &t->device_bytes)) != RGS_OK) return r;
-        t->dy_mc_cap = n_rays_all * 32;
-    }
-    if (t->cap_slots > t->gh_cap) {
-        if ((r = dev_alloc(&t->gh, (size_t)t->cap_slots, &t->device_bytes)) != RGS_OK) return r;
-        t->gh_cap = t->cap_slots;
-    }
+    const long long n_rays = (long long)t->n * t->nd;
     if (t->n > t->pg_cap) {
         if ((r = dev_alloc(&t->Pg, (size_t)t->n * 12, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->dop, (size_t)t->n, &t->device_bytes)) != RGS_OK) return r;
         t->pg_cap = t->n;
+    }
+    // Workspaces that live only inside this call come from the stream-ordered pool and are
+    // returned to it on every exit path: v^(0..n), u, the transposed index, the per-ray
+    // adjoint values and the per-record opacity sums.
+    struct Scratch {
+        rgs_transport *t;
+        cudaStream_t st;
+        ~Scratch() {
+            pool_release(t->v, st);
+            pool_release(t->u, st);
+            pool_release(t->tr, st);
+            pool_release(t->dy, st);
+            pool_release(t->dy_mc, st);
+            pool_release(t->gh, st);
+        }
+    } scratch{t, st};
+    const bool mc = wide_adjoint(t->C);
+    if ((r = pool_alloc(&t->v, A * (t->stride ? t->stride + 1 : nb + 1), st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&t->u, A, st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&t->tr, (size_t)t->n_hits, st)) != RGS_OK) return r;
+    if (mc) {
+        if ((r = pool_alloc(&t->dy_mc, (size_t)n_rays * 32, st)) != RGS_OK) return r;
+    } else {
+        if ((r = pool_alloc(&t->dy, (size_t)n_rays, st)) != RGS_OK) return r;
+    }
+    if (dop && nb >= 1 && (r = pool_alloc(&t->gh, (size_t)t->n_slots, st)) != RGS_OK) return r;
+    {
+        const int n = t->n;
+        RaysDev rd = t->rays();
+        { ProfScope ps_("k_copy_off", st); k_copy_off<<<(n + 255) / 256, 256, 0, st>>>(t->src_off, t->cursor, n); }
+        { ProfScope ps_("k_src_fill", st); k_src_fill<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->cursor, t->tr); }
+        RGS_LAUNCH("transposed index");
     }
     switch (t->nc) {
     case 1: return run_adjoint<1>(t, g, dE, dad, dop, st);

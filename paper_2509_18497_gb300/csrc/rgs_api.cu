@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "rgs_internal.cuh"
@@ -29,6 +30,75 @@ rgs_status rgs_cuda_fail(cudaError_t e, const char *what) {
 }
 
 static cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+// ---------------------------------------------------------------- allocation sizes
+namespace {
+std::mutex g_alloc_mu;
+std::unordered_map<void *, size_t> g_alloc_sizes;
+} // namespace
+
+void rgs_alloc_note(void *p, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc_sizes[p] = bytes;
+}
+
+size_t rgs_alloc_forget(void *p) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = g_alloc_sizes.find(p);
+    if (it == g_alloc_sizes.end()) return 0;
+    const size_t b = it->second;
+    g_alloc_sizes.erase(it);
+    return b;
+}
+
+// ---------------------------------------------------------------- workspace pool
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mempool_mu;
+cudaMemPool_t g_mempool[kMaxDevices] = {};
+
+rgs_status device_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    RGS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        rgs_set_error("device ordinal %d out of range", dev);
+        return RGS_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mempool_mu);
+    if (!g_mempool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        RGS_CUDA(cudaMemPoolCreate(&p, &props));
+        unsigned long long keep = ~0ull; // keep freed blocks reserved for the next call
+        RGS_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_mempool[dev] = p;
+    }
+    *out = g_mempool[dev];
+    return RGS_OK;
+}
+} // namespace
+
+rgs_status pool_alloc_bytes(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    cudaMemPool_t pool = nullptr;
+    rgs_status r = device_pool(&pool);
+    if (r != RGS_OK) return r;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        rgs_set_error("workspace allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? RGS_ERR_OOM : RGS_ERR_CUDA;
+    }
+    return RGS_OK;
+}
+
+void pool_free(void *p, cudaStream_t st) {
+    if (p && cudaFreeAsync(p, st) != cudaSuccess) cudaGetLastError();
+}
 
 // ---------------------------------------------------------------- launch profiler
 namespace {
@@ -310,6 +380,33 @@ rgs_status rgs_get_iterate(rgs_transport *t, int32_t b, float *out, void *stream
     return rgs_get_iterate_impl(t, b, out, S(stream));
 }
 
+rgs_status rgs_set_checkpointing(rgs_transport *t, int32_t stride) {
+    if (!t) {
+        rgs_set_error("rgs_set_checkpointing: NULL transport");
+        return RGS_ERR_ARG;
+    }
+    if (stride < -1 || stride > RGS_MAX_BOUNCES) {
+        rgs_set_error("rgs_set_checkpointing: stride %d outside [-1, %d]", stride, RGS_MAX_BOUNCES);
+        return RGS_ERR_ARG;
+    }
+    t->ckpt_req = stride;
+    return RGS_OK;
+}
+
+rgs_status rgs_trim_workspace(void) {
+    int dev = 0;
+    RGS_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mempool_mu);
+        if (dev >= 0 && dev < kMaxDevices) p = g_mempool[dev];
+    }
+    if (!p) return RGS_OK;
+    RGS_CUDA(cudaDeviceSynchronize());
+    RGS_CUDA(cudaMemPoolTrimTo(p, 0));
+    return RGS_OK;
+}
+
 rgs_status rgs_transport_info_get(const rgs_transport *t, rgs_transport_info *info) {
     if (!t || !info) {
         rgs_set_error("rgs_transport_info_get: NULL argument");
@@ -335,7 +432,6 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->lpos);
     dev_free(t->lint);
     dev_free(t->rec_ja);
-    dev_free(t->rec_g);
     dev_free(t->off);
     dev_free(t->ray_ctr);
     dev_free(t->cnt);
@@ -344,21 +440,15 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->src_off);
     dev_free(t->src_cnt);
     dev_free(t->cursor);
-    dev_free(t->tr);
     dev_free(t->scan_tmp);
     dev_free(t->D);
     dev_free(t->iters);
     dev_free(t->Q);
     dev_free(t->iters16);
     dev_free(t->norm2);
-    dev_free(t->v);
-    dev_free(t->u);
     dev_free(t->Pg);
     dev_free(t->dop);
-    dev_free(t->gh);
     dev_free(t->dir);
-    dev_free(t->dy);
-    dev_free(t->dy_mc);
     delete t;
 }
 

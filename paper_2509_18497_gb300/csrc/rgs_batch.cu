@@ -11,6 +11,8 @@
 // and replayed on later calls with the same arguments; the number of resident blocks per
 // SM is chosen by timing the candidates on the first call (autotuning).
 #include <map>
+#include <memory>
+#include <type_traits>
 #include <mutex>
 #include <vector>
 
@@ -22,38 +24,67 @@ struct BatchSceneDev {
     SceneDev sc;
     RaysDev rays;
     int C, nc, nb, prec;
+    // item shape of the levels that gather BF16 rows (16) and FP32 rows (32):
+    // 0 = 3-column tiles (4 lanes per ray), 1 = 32-column tiles (lane per column)
+    int wide16, wide32;
+    int tiles16, tiles32; // column tiles per receiver for each shape
     float *iters, *Q;
     __nv_bfloat16 *iters16;
     long long A, A16;
     double *norm2;
 };
+static_assert(sizeof(BatchSceneDev) % 4 == 0, "descriptor is copied as 32-bit words");
 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned *p) { return *(const volatile unsigned *)p; }
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 
-template <int NC, class SL>
-__device__ __forceinline__ void batch_item(const BatchSceneDev &S, int b, int i, int col0, float *red) {
-    const bool rows16 = S.prec != RGS_FP32 && !(S.prec == RGS_BF16_FP32ACC_RESCORR && b == S.nb);
+// one (receiver, column tile) item of bounce b: gathers rows of B^(b-1) (BF16 copies or FP32)
+template <int NC, bool ROWS16, bool WIDE>
+__device__ __forceinline__ void batch_item(const BatchSceneDev &S, int b, int i, int tile, float *red) {
     const float *Bprev = S.iters + S.A * (b - 1);
     __nv_bfloat16 *Bout16 = S.prec != RGS_FP32 ? S.iters16 + S.A16 * b : nullptr;
-    if constexpr (sizeof(typename SL::T) == 2) {
-        (void)rows16;
-        bounce_receiver<NC, 3, SL>(S.sc, S.rays, S.C, S.iters16 + S.A16 * (b - 1), Bprev, S.iters, S.Q + S.A * (b - 1),
-                                   S.iters + S.A * b, Bout16, S.norm2 + b, i, col0, red);
+    using T = typename std::conditional<ROWS16, __nv_bfloat16, float>::type;
+    const T *Bg;
+    if constexpr (ROWS16) Bg = S.iters16 + S.A16 * (b - 1);
+    else Bg = Bprev;
+    if constexpr (WIDE) {
+        bounce_receiver_mc<NC, T>(S.sc, S.rays, S.C, Bg, Bprev, S.iters, S.Q + S.A * (b - 1), S.iters + S.A * b,
+                                  Bout16, S.norm2 + b, i, tile, red);
     } else {
-        bounce_receiver<NC, 3, SL>(S.sc, S.rays, S.C, Bprev, Bprev, S.iters, S.Q + S.A * (b - 1), S.iters + S.A * b,
-                                   Bout16, S.norm2 + b, i, col0, red);
+        using SL = typename std::conditional<ROWS16, SliceH<NC>, Slice<NC>>::type;
+        bounce_receiver<NC, 3, SL>(S.sc, S.rays, S.C, Bg, Bprev, S.iters, S.Q + S.A * (b - 1), S.iters + S.A * b,
+                                   Bout16, S.norm2 + b, i, tile * 3, red);
     }
 }
 
-__global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce_persistent(const BatchSceneDev *__restrict__ scenes,
-                                                                     int count, const long long *__restrict__ level_off,
-                                                                     int maxnb, unsigned long long *counters,
-                                                                     unsigned *barrier, int spin_limit, int *err) {
-    __shared__ float red[(BOUNCE_THREADS / 32) * 4 * 4 * 3]; // largest G * KPL * CT (nc = 16)
+template <int NC>
+__device__ __forceinline__ void batch_item_nc(const BatchSceneDev &S, int b, bool rows16, bool wide, int i, int tile,
+                                              float *red) {
+    if (wide) {
+        if (rows16) batch_item<NC, true, true>(S, b, i, tile, red);
+        else batch_item<NC, false, true>(S, b, i, tile, red);
+    } else {
+        if (rows16) batch_item<NC, true, false>(S, b, i, tile, red);
+        else batch_item<NC, false, false>(S, b, i, tile, red);
+    }
+}
+
+// Levels b0..b1 of every scene.  Items of a level are numbered scene by scene
+// (level_off[b][s] .. level_off[b][s+1]) and, within a scene, tile-major: neighbouring
+// items are neighbouring receivers (Morton order) of one column tile, whose rays gather
+// largely the same source rows (measured faster than receiver-major for the per-scene
+// kernels, whose grids use the same order).
+template <int MINB>
+__global__ void __launch_bounds__(BOUNCE_THREADS, MINB) k_bounce_persistent(const BatchSceneDev *__restrict__ scenes,
+                                                                        int count, const long long *__restrict__ level_off,
+                                                                        int b0, int b1, int force32,
+                                                                        unsigned long long *counters,
+                                                                        unsigned *barrier, int spin_limit, int *err) {
+    __shared__ float red[MC_WARPS * 16 * 32]; // the larger of the two bodies' scratch
     __shared__ long long s_item;
+    __shared__ BatchSceneDev s_scene;
     __shared__ int s_abort;
-    for (int b = 1; b <= maxnb; ++b) {
+    for (int b = b0; b <= b1; ++b) {
         const long long *off = level_off + (size_t)b * (count + 1);
         const long long total = off[count];
         while (true) {
@@ -64,25 +95,31 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce_persistent(const Batc
             if (item >= total) break;
             int s = 0;
             while (s + 1 < count && off[s + 1] <= item) ++s;
-            const BatchSceneDev &S = scenes[s];
+            // the scene's descriptor in shared memory: its fields are read where used instead
+            // of being held in registers across the item
+            if (threadIdx.x < sizeof(BatchSceneDev) / 4)
+                reinterpret_cast<int *>(&s_scene)[threadIdx.x] = reinterpret_cast<const int *>(scenes + s)[threadIdx.x];
+            __syncthreads();
+            const BatchSceneDev &S = s_scene;
+            const bool rows16 =
+                !force32 && S.prec != RGS_FP32 && !(S.prec == RGS_BF16_FP32ACC_RESCORR && b == S.nb);
+            const bool wide = rows16 ? S.wide16 : S.wide32;
             const long long local = item - off[s];
-            const int T = S.C / 3;
-            const int i = (int)(local / T), col0 = (int)(local % T) * 3;
-            const bool rows16 = S.prec != RGS_FP32 && !(S.prec == RGS_BF16_FP32ACC_RESCORR && b == S.nb);
+            const int tile = (int)(local / S.sc.n), i = (int)(local - (long long)tile * S.sc.n);
             switch (S.nc) {
-            case 1: rows16 ? batch_item<1, SliceH<1>>(S, b, i, col0, red) : batch_item<1, Slice<1>>(S, b, i, col0, red); break;
-            case 4: rows16 ? batch_item<4, SliceH<4>>(S, b, i, col0, red) : batch_item<4, Slice<4>>(S, b, i, col0, red); break;
-            case 9: rows16 ? batch_item<9, SliceH<9>>(S, b, i, col0, red) : batch_item<9, Slice<9>>(S, b, i, col0, red); break;
-            default: rows16 ? batch_item<16, SliceH<16>>(S, b, i, col0, red) : batch_item<16, Slice<16>>(S, b, i, col0, red);
+            case 1: batch_item_nc<1>(S, b, rows16, wide, i, tile, red); break;
+            case 4: batch_item_nc<4>(S, b, rows16, wide, i, tile, red); break;
+            case 9: batch_item_nc<9>(S, b, rows16, wide, i, tile, red); break;
+            default: batch_item_nc<16>(S, b, rows16, wide, i, tile, red);
             }
         }
-        if (b == maxnb) break;
+        if (b == b1) break;
         // grid barrier between bounce levels, with a bounded wait
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(barrier, 1u);
-            const unsigned target = gridDim.x * (unsigned)b;
+            const unsigned target = gridDim.x * (unsigned)(b - b0 + 1);
             bool ok = true;
             int polls = 0;
             while (ld_volatile(barrier) < target) {
@@ -111,8 +148,20 @@ struct Plan {
     int *d_err = nullptr;
     int maxnb = 0, count = 0;
     int blocks = 0;         // persistent grid size (autotuned)
+    int minb = 3;           // kernel instance: registers for 2 or 3 resident blocks per SM (autotuned)
+    int pol16 = 1, pol32 = 1; // item-shape policy of the BF16-row and FP32-row levels (autotuned):
+                              // 0 = 3-column items, 1 = wide_bounce's choice, 2 = 32-column items
+                              // wherever C >= kWideMinCols
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        dev_free(d_scenes);
+        dev_free(d_level_off);
+        dev_free(d_counters);
+        dev_free(d_barrier);
+        dev_free(d_err);
+    }
 };
 
 std::mutex g_plan_mu;
@@ -121,15 +170,42 @@ std::map<std::vector<const void *>, Plan *> g_plans;
 template <int NC>
 void enqueue_make_S(rgs_transport *t, const float *E, cudaStream_t st, bool bf16);
 
-rgs_status enqueue_batch(Plan &P, const std::vector<rgs_transport *> &ts, const float *const *E, float *const *B_out,
-                         int spin_limit, cudaStream_t st) {
-    const size_t L = (size_t)(P.maxnb + 1);
-    RGS_CUDA(cudaMemsetAsync(P.d_counters, 0, sizeof(unsigned long long) * L, st));
-    RGS_CUDA(cudaMemsetAsync(P.d_barrier, 0, sizeof(unsigned), st));
-    RGS_CUDA(cudaMemsetAsync(P.d_err, 0, sizeof(int), st));
+// columns from which policy 2 gives a scene 32-column items
+constexpr int kWideMinCols = 6;
+
+bool policy_wide(int pol, int C, bool rows16) {
+    return pol == 0 ? false : (pol == 1 ? wide_bounce(C, rows16) : C >= kWideMinCols);
+}
+
+// item shapes of every scene under the plan's policies, the level offsets they imply, and
+// their upload
+rgs_status upload_shape(Plan &P, cudaStream_t st, bool force32 = false) {
+    const int count = P.count;
+    for (auto &b : P.host) {
+        b.wide16 = policy_wide(P.pol16, b.C, true) ? 1 : 0;
+        b.wide32 = policy_wide(P.pol32, b.C, false) ? 1 : 0;
+        b.tiles16 = b.wide16 ? (b.C + 31) / 32 : b.C / 3;
+        b.tiles32 = b.wide32 ? (b.C + 31) / 32 : b.C / 3;
+    }
+    std::vector<long long> off((size_t)(P.maxnb + 1) * (count + 1), 0);
+    for (int b = 1; b <= P.maxnb; ++b)
+        for (int s = 0; s < count; ++s) {
+            const BatchSceneDev &h = P.host[s];
+            const bool rows16 =
+                !force32 && h.prec != RGS_FP32 && !(h.prec == RGS_BF16_FP32ACC_RESCORR && b == h.nb);
+            const long long items = h.nb >= b ? (long long)h.sc.n * (rows16 ? h.tiles16 : h.tiles32) : 0;
+            off[(size_t)b * (count + 1) + s + 1] = off[(size_t)b * (count + 1) + s] + items;
+        }
+    RGS_CUDA(cudaMemcpyAsync(P.d_scenes, P.host.data(), sizeof(BatchSceneDev) * count, cudaMemcpyHostToDevice, st));
+    RGS_CUDA(cudaMemcpyAsync(P.d_level_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st));
+    RGS_CUDA(cudaStreamSynchronize(st)); // the host vectors are released on return
+    return RGS_OK;
+}
+
+// S = E + D per scene (plain launches, before the graph)
+rgs_status enqueue_make_S_all(Plan &P, const std::vector<rgs_transport *> &ts, const float *const *E, cudaStream_t st) {
     for (int s = 0; s < P.count; ++s) {
         rgs_transport *t = ts[s];
-        RGS_CUDA(cudaMemsetAsync(t->norm2, 0, sizeof(double) * (RGS_MAX_BOUNCES + 1), st));
         const bool bf16 = P.host[s].prec != RGS_FP32;
         switch (t->nc) {
         case 1: enqueue_make_S<1>(t, E ? E[s] : nullptr, st, bf16); break;
@@ -139,6 +215,18 @@ rgs_status enqueue_batch(Plan &P, const std::vector<rgs_transport *> &ts, const 
         }
     }
     RGS_LAUNCH("batch make_S");
+    return RGS_OK;
+}
+
+// counter and norm resets and the persistent kernel: the part captured into the graph
+rgs_status enqueue_core(Plan &P, const std::vector<rgs_transport *> &ts, int spin_limit, cudaStream_t st,
+                        int level0 = 0, int level1 = 0, bool force32 = false) {
+    const size_t L = (size_t)(P.maxnb + 1);
+    RGS_CUDA(cudaMemsetAsync(P.d_counters, 0, sizeof(unsigned long long) * L, st));
+    RGS_CUDA(cudaMemsetAsync(P.d_barrier, 0, sizeof(unsigned), st));
+    RGS_CUDA(cudaMemsetAsync(P.d_err, 0, sizeof(int), st));
+    for (int s = 0; s < P.count; ++s)
+        RGS_CUDA(cudaMemsetAsync(ts[s]->norm2, 0, sizeof(double) * (RGS_MAX_BOUNCES + 1), st));
     if (P.maxnb > 0) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(P.blocks);
@@ -149,17 +237,51 @@ rgs_status enqueue_batch(Plan &P, const std::vector<rgs_transport *> &ts, const 
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        ProfScope ps_("k_bounce_persistent", st);
-        RGS_CUDA(cudaLaunchKernelEx(&cfg, k_bounce_persistent, (const BatchSceneDev *)P.d_scenes, P.count,
-                                    (const long long *)P.d_level_off, P.maxnb, P.d_counters, P.d_barrier, spin_limit,
-                                    P.d_err));
+        const int b0 = level0 > 0 ? level0 : 1, b1 = level1 > 0 ? level1 : P.maxnb;
+        if (P.minb == 2)
+            RGS_CUDA(cudaLaunchKernelEx(&cfg, k_bounce_persistent<2>, (const BatchSceneDev *)P.d_scenes, P.count,
+                                        (const long long *)P.d_level_off, b0, b1, force32 ? 1 : 0, P.d_counters, P.d_barrier,
+                                        spin_limit, P.d_err));
+        else
+            RGS_CUDA(cudaLaunchKernelEx(&cfg, k_bounce_persistent<3>, (const BatchSceneDev *)P.d_scenes, P.count,
+                                        (const long long *)P.d_level_off, b0, b1, force32 ? 1 : 0, P.d_counters, P.d_barrier,
+                                        spin_limit, P.d_err));
     }
+    return RGS_OK;
+}
+
+// B^(n) of every scene to the caller's layout (plain launches, after the graph)
+rgs_status enqueue_outputs(Plan &P, const std::vector<rgs_transport *> &ts, float *const *B_out, cudaStream_t st) {
     for (int s = 0; s < P.count; ++s)
         if (B_out && B_out[s]) {
             rgs_status r = rgs_get_iterate_impl(ts[s], P.host[s].nb, B_out[s], st);
             if (r != RGS_OK) return r;
         }
     return RGS_OK;
+}
+
+rgs_status enqueue_batch(Plan &P, const std::vector<rgs_transport *> &ts, const float *const *E, float *const *B_out,
+                         int spin_limit, cudaStream_t st) {
+    rgs_status r;
+    if ((r = enqueue_make_S_all(P, ts, E, st)) != RGS_OK) return r;
+    {
+        ProfScope ps_("k_bounce_persistent", st);
+        if ((r = enqueue_core(P, ts, spin_limit, st)) != RGS_OK) return r;
+    }
+    return enqueue_outputs(P, ts, B_out, st);
+}
+
+// library-owned stream the batch graphs are captured on (capture is not possible on the
+// legacy or per-thread default streams a caller may pass); created once per device
+cudaStream_t capture_stream() {
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
 }
 
 } // namespace
@@ -186,7 +308,6 @@ template <int NC> void enqueue_make_S(rgs_transport *t, const float *E, cudaStre
 }
 } // namespace
 
-rgs_status rgs_solve_prepare(rgs_transport *t, int nb, int precision, cudaStream_t st);
 
 rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const float *const *E, const int32_t *nbs,
                                   const rgs_batch_opts *opts, float *const *B_out, double *norms, cudaStream_t st) {
@@ -197,7 +318,7 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
     std::vector<rgs_transport *> ts(tsp, tsp + count);
     rgs_status r;
     for (int s = 0; s < count; ++s)
-        if ((r = rgs_solve_prepare(ts[s], nbs[s], precision, st)) != RGS_OK) return r;
+        if ((r = rgs_solve_prepare(ts[s], nbs[s], precision, 0, st)) != RGS_OK) return r;
 
     // plan: keyed by every pointer and size the launches bake in
     std::vector<const void *> key;
@@ -223,8 +344,10 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
     std::lock_guard<std::mutex> lk(g_plan_mu);
     Plan *P = g_plans.count(key) ? g_plans[key] : nullptr;
     const bool fresh = (P == nullptr);
+    std::unique_ptr<Plan> owner; // a new plan is freed if its set-up fails
     if (fresh) {
-        P = new Plan();
+        owner.reset(new Plan());
+        P = owner.get();
         P->count = count;
         for (int s = 0; s < count; ++s) P->maxnb = std::max(P->maxnb, (int)nbs[s]);
         for (int s = 0; s < count; ++s) {
@@ -244,63 +367,88 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
             b.norm2 = t->norm2;
             P->host.push_back(b);
         }
-        std::vector<long long> off((size_t)(P->maxnb + 1) * (count + 1), 0);
-        for (int b = 1; b <= P->maxnb; ++b)
-            for (int s = 0; s < count; ++s)
-                off[(size_t)b * (count + 1) + s + 1] =
-                    off[(size_t)b * (count + 1) + s] + (nbs[s] >= b ? (long long)ts[s]->n * (ts[s]->C / 3) : 0);
         if ((r = dev_alloc(&P->d_scenes, (size_t)count)) != RGS_OK) return r;
-        if ((r = dev_alloc(&P->d_level_off, off.size())) != RGS_OK) return r;
+        if ((r = dev_alloc(&P->d_level_off, (size_t)(P->maxnb + 1) * (count + 1))) != RGS_OK) return r;
         if ((r = dev_alloc(&P->d_counters, (size_t)P->maxnb + 1)) != RGS_OK) return r;
         if ((r = dev_alloc(&P->d_barrier, 1)) != RGS_OK) return r;
         if ((r = dev_alloc(&P->d_err, 1)) != RGS_OK) return r;
-        RGS_CUDA(cudaMemcpyAsync(P->d_scenes, P->host.data(), sizeof(BatchSceneDev) * count, cudaMemcpyHostToDevice, st));
-        RGS_CUDA(cudaMemcpyAsync(P->d_level_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st));
-        // resident blocks per SM: the occupancy limit, or the fastest of the candidates
-        int dev = 0, sms = 0, occ = 0;
+        int dev = 0, sms = 0, occ2 = 0, occ3 = 0;
         RGS_CUDA(cudaGetDevice(&dev));
         RGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce_persistent, BOUNCE_THREADS, 0));
-        if (occ < 1) {
+        RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_bounce_persistent<2>, BOUNCE_THREADS, 0));
+        RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_bounce_persistent<3>, BOUNCE_THREADS, 0));
+        if (occ2 < 1 || occ3 < 1) {
             rgs_set_error("rgs_solve_batched: the persistent kernel cannot be resident");
             return RGS_ERR_CUDA;
         }
-        P->blocks = sms * occ;
-        if (autotune && P->maxnb > 0 && occ > 1) {
+        auto configure = [&](int pol16, int pol32, int minb, bool force32) -> rgs_status {
+            P->pol16 = pol16;
+            P->pol32 = pol32;
+            P->minb = minb;
+            P->blocks = sms * (minb == 2 ? occ2 : occ3);
+            return upload_shape(*P, st, force32);
+        };
+        if ((r = configure(1, 1, 3, false)) != RGS_OK) return r; // default: the measured crossovers, 3 blocks/SM
+        if (autotune && P->maxnb > 0) {
+            // Time bounce level 1 per candidate and keep the fastest: first the item-shape policy
+            // of the rows level 1 gathers (BF16 in the batched modes) with the kernel occupancy,
+            // then, for the residual-corrected mode, the policy of its FP32-row level, timed as
+            // level 1 gathering FP32 rows.  S must exist for level 1.
+            if ((r = enqueue_make_S_all(*P, ts, E, st)) != RGS_OK) return r;
             cudaEvent_t e0, e1;
             RGS_CUDA(cudaEventCreate(&e0));
             RGS_CUDA(cudaEventCreate(&e1));
-            float best = 1e30f;
-            int best_blocks = P->blocks;
-            for (int per = occ; per >= 1; per = (per > 2 ? per / 2 : per - 1)) {
-                P->blocks = sms * per;
+            auto time_level1 = [&](int pol16, int pol32, int minb, bool force32, float *ms) -> rgs_status {
+                rgs_status q;
+                if ((q = configure(pol16, pol32, minb, force32)) != RGS_OK) return q;
                 RGS_CUDA(cudaEventRecord(e0, st));
-                if ((r = enqueue_batch(*P, ts, E, B_out, spin_limit, st)) != RGS_OK) return r;
+                if ((q = enqueue_core(*P, ts, spin_limit, st, 1, 1, force32)) != RGS_OK) return q;
                 RGS_CUDA(cudaEventRecord(e1, st));
                 RGS_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                RGS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
-                    best = ms;
-                    best_blocks = P->blocks;
+                RGS_CUDA(cudaEventElapsedTime(ms, e0, e1));
+                return RGS_OK;
+            };
+            const bool bf16 = precision != RGS_FP32;
+            float best = 1e30f;
+            int best_pol = 1, best_minb = 3;
+            for (int pol = 0; pol <= 2 && r == RGS_OK; ++pol)
+                for (int minb = 2; minb <= 3 && r == RGS_OK; ++minb) {
+                    float ms = 0.f;
+                    r = time_level1(bf16 ? pol : 1, bf16 ? 1 : pol, minb, false, &ms);
+                    if (r == RGS_OK && ms < best) {
+                        best = ms;
+                        best_pol = pol;
+                        best_minb = minb;
+                    }
+                }
+            int pol16 = bf16 ? best_pol : 1, pol32 = bf16 ? 1 : best_pol;
+            if (r == RGS_OK && precision == RGS_BF16_FP32ACC_RESCORR) {
+                float best32 = 1e30f;
+                for (int pol = 0; pol <= 2 && r == RGS_OK; ++pol) {
+                    float ms = 0.f;
+                    r = time_level1(pol16, pol, best_minb, true, &ms);
+                    if (r == RGS_OK && ms < best32) {
+                        best32 = ms;
+                        pol32 = pol;
+                    }
                 }
             }
-            P->blocks = best_blocks;
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
+            if (r != RGS_OK) return r;
+            if ((r = configure(pol16, pol32, best_minb, false)) != RGS_OK) return r;
         }
-        g_plans[key] = P;
+        g_plans[key] = owner.release();
     }
     bool launched = false;
     if (use_graph && !P->graph_failed) {
-        if (!P->exec) {
+        if (!P->exec) { // capture the core once, on the library's own stream
             cudaGraph_t graph = nullptr;
-            cudaStreamCaptureStatus cs;
-            bool ok = cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
-                      cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            cudaStream_t cs = capture_stream();
+            bool ok = cs && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                rgs_status er = enqueue_batch(*P, ts, E, B_out, spin_limit, st);
-                ok = (cudaStreamEndCapture(st, &graph) == cudaSuccess) && er == RGS_OK;
+                rgs_status er = enqueue_core(*P, ts, spin_limit, cs);
+                ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && er == RGS_OK;
                 ok = ok && cudaGraphInstantiate(&P->exec, graph, 0) == cudaSuccess;
                 if (graph) cudaGraphDestroy(graph);
             }
@@ -311,8 +459,12 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
             }
         }
         if (P->exec) {
-            ProfScope ps_("batch_graph", st);
-            RGS_CUDA(cudaGraphLaunch(P->exec, st));
+            if ((r = enqueue_make_S_all(*P, ts, E, st)) != RGS_OK) return r;
+            {
+                ProfScope ps_("k_bounce_persistent", st); // the graph: resets + the persistent kernel
+                RGS_CUDA(cudaGraphLaunch(P->exec, st));
+            }
+            if ((r = enqueue_outputs(*P, ts, B_out, st)) != RGS_OK) return r;
             launched = true;
         }
     }
@@ -344,16 +496,7 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
 
 void rgs_batch_plans_release(void) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
-    for (auto &kv : g_plans) {
-        Plan *P = kv.second;
-        if (P->exec) cudaGraphExecDestroy(P->exec);
-        dev_free(P->d_scenes);
-        dev_free(P->d_level_off);
-        dev_free(P->d_counters);
-        dev_free(P->d_barrier);
-        dev_free(P->d_err);
-        delete P;
-    }
+    for (auto &kv : g_plans) delete kv.second;
     g_plans.clear();
 }
 
@@ -365,14 +508,7 @@ void rgs_batch_forget(const rgs_transport *t) {
         for (const void *k : it->first)
             if (k == (const void *)t) uses = true;
         if (uses) {
-            Plan *P = it->second;
-            if (P->exec) cudaGraphExecDestroy(P->exec);
-            dev_free(P->d_scenes);
-            dev_free(P->d_level_off);
-            dev_free(P->d_counters);
-            dev_free(P->d_barrier);
-            dev_free(P->d_err);
-            delete P;
+            delete it->second;
             it = g_plans.erase(it);
         } else {
             ++it;

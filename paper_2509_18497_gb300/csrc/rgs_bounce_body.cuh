@@ -6,6 +6,51 @@
 
 #define BOUNCE_THREADS 256
 
+// many-column (lane-per-column) layout: a warp takes one ray at a time and its 32 lanes take
+// 32 consecutive columns of one tile
+constexpr int MC_WARPS = 8;
+constexpr int MC_THREADS = MC_WARPS * 32;
+static_assert(MC_THREADS == BOUNCE_THREADS, "the batch kernel runs both bodies in one block");
+
+// the NC coefficients of one column of a row (FP32 rows of NC floats, BF16 rows padded)
+template <int NC> __device__ __forceinline__ void load_col(const float *__restrict__ p, float *v) {
+    if constexpr (NC % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < NC / 4; ++q) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            v[4 * q] = f.x;
+            v[4 * q + 1] = f.y;
+            v[4 * q + 2] = f.z;
+            v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) v[k] = __ldg(p + k);
+    }
+}
+template <int NC> __device__ __forceinline__ void load_col(const __nv_bfloat16 *__restrict__ p, float *v) {
+    if constexpr (NC >= 9) { // padded to 16
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+            const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k0 = 8 * q + 2 * m;
+                if (k0 < NC) v[k0] = __uint_as_float(u[m] << 16);
+                if (k0 + 1 < NC) v[k0 + 1] = __uint_as_float(u[m] & 0xffff0000u);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) v[k] = __bfloat162float(p[k]);
+    }
+}
+template <int NC, class T> constexpr int row_stride() {
+    return sizeof(T) == 2 ? ((NC >= 9) ? 16 : NC) : NC;
+}
+
+
 template <int NC, int CT, class SL>
 __device__ __forceinline__ void bounce_receiver(const SceneDev &sc, const RaysDev &rays, int C,
                                                 const typename SL::T *__restrict__ Bg, const float *__restrict__ Bprev,
@@ -103,5 +148,73 @@ __device__ __forceinline__ void bounce_receiver(const SceneDev &sc, const RaysDe
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dsq += __shfl_xor_sync(0xffffffffu, dsq, off);
     if (lane == 0 && warp * 32 < NC * CT) atomicAdd(norm2, dsq);
+    __syncthreads(); // red is reused by the caller's next receiver
+}
+
+// Lane-per-column bounce for one receiver and one 32-column tile (the body of k_bounce_mc and
+// of the persistent batch kernel's wide items); red = shared scratch of MC_WARPS * NC * 32 floats.
+template <int NC, class T>
+__device__ __forceinline__ void bounce_receiver_mc(const SceneDev &sc, const RaysDev &rays, int C,
+                                                   const T *__restrict__ Bg, const float *__restrict__ Bprev,
+                                                   const float *__restrict__ S, float *__restrict__ Qout,
+                                                   float *__restrict__ Bout, __nv_bfloat16 *__restrict__ Bout16,
+                                                   double *norm2, int i, int tile, float *red) {
+    constexpr int RS = row_stride<NC, T>();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col = tile * 32 + lane;
+    const bool live = col < C;
+    const int colc = live ? col : C - 1;
+    const int nd = rays.nd;
+    const float3 n = f3(sc.N4[i]);
+    float acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = 0.f;
+    for (int q = warp; q < nd; q += MC_WARPS) {
+        const long long r = (long long)i * nd + q;
+        const float3 d = f3(rays.dir[r]);
+        float Yo[NC];
+        sh_eval<NC>(neg3(d), Yo);
+        const int cnt = rays.cnt[r];
+        const long long base = rays.off[r];
+        float x = 0.f;
+#pragma unroll 2
+        for (int h = 0; h < cnt; ++h) {
+            const int2 ja = __ldg(&rays.rec_ja[base + h]);
+            float v[NC];
+            load_col<NC>(Bg + ((size_t)ja.x * C + colc) * RS, v);
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
+            x += __int_as_float(ja.y) * s;
+        }
+        float Yi[NC];
+        sh_eval<NC>(reflect_n(n, d), Yi);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[k] += Yi[k] * x;
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) red[(warp * NC + k) * 32 + lane] = acc[k];
+    __syncthreads();
+    double dsq = 0.0;
+    const float w = 3.14159265358979f / (float)nd;
+    for (int e = threadIdx.x; e < NC * 32; e += MC_THREADS) {
+        const int k = e >> 5, c = e & 31;
+        const int cc = tile * 32 + c;
+        if (cc >= C) continue;
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < MC_WARPS; ++q) v += red[(q * NC + k) * 32 + c];
+        const float Q = w * v;
+        const size_t idx = ((size_t)i * C + cc) * NC + k;
+        Qout[idx] = Q;
+        const float b = S[idx] + sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (cc % 3)] * Q;
+        Bout[idx] = b;
+        if (Bout16) Bout16[((size_t)i * C + cc) * ((NC >= 9) ? 16 : NC) + k] = __float2bfloat16_rn(b);
+        const double df = (double)b - (double)Bprev[idx];
+        dsq += df * df;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dsq += __shfl_xor_sync(0xffffffffu, dsq, off);
+    if (lane == 0) atomicAdd(norm2, dsq);
     __syncthreads(); // red is reused by the caller's next receiver
 }

@@ -7,7 +7,7 @@
 //   uid[j] = caller index of internal surfel j (ray seeds and depth-tie order use it)
 //   radiosity-like arrays (S, B^(b), Q^(b), v^(a), u): [N][C][NC] float, SH index innermost
 //   hit records: contiguous per ray, hit h of ray r at off[r] + h (exactly sized, in depth
-//                order): rec_ja = (source j, bits of a_rh), rec_g = G
+//                order): rec_ja = (source j, bits of a_rh); G is recomputed where needed
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -52,7 +52,6 @@ struct RaysDev {
     int nd, na, nbs; // rays per surfel, strata n_a x n_b
     unsigned long long seed;
     const int2 *rec_ja;
-    const float *rec_g;
     const long long *off; // first record of each ray
     const int *cnt;
     const float4 *dir; // per-ray direction (xyz), written by the trace
@@ -237,18 +236,30 @@ __device__ __forceinline__ bool hit_surfel_t(const SceneDev &sc, int j, int self
                                              float eps, float &t_out, float &r2_out) {
     if (j == self) return false;
     const float4 Nj = __ldg(&sc.N4[j]);
-    const float den = Nj.x * d.x + Nj.y * d.y + Nj.z * d.z;
+    const float den = __fmaf_rn(Nj.z, d.z, __fmaf_rn(Nj.y, d.y, __fmul_rn(Nj.x, d.x)));
     if (fabsf(den) < 1e-12f) return false;
     const float4 Pj = __ldg(&sc.P[j]);
-    const float h = Nj.x * (Pj.x - o.x) + Nj.y * (Pj.y - o.y) + Nj.z * (Pj.z - o.z);
+    const float h = __fmaf_rn(Nj.z, __fsub_rn(Pj.z, o.z),
+                              __fmaf_rn(Nj.y, __fsub_rn(Pj.y, o.y), __fmul_rn(Nj.x, __fsub_rn(Pj.x, o.x))));
     if (fabsf(h) <= eps) return false;
-    const float t = h / den;
+    const float t = __fdiv_rn(h, den);
     if (!(t > 0.f) || !(t < tmax)) return false;
     const float r2 = surfel_r2(sc, j, o, d, t);
     if (r2 > sc.cutoff2) return false;
     t_out = t;
     r2_out = r2;
     return true;
+}
+
+// G of a hit that the trace stored (ray o + t d on surfel j), recomputed with the same
+// rounding as hit_surfel_t, so it equals the value the compositing used bit for bit.
+__device__ __forceinline__ float stored_hit_G(const SceneDev &sc, int j, float3 o, float3 d) {
+    const float4 Nj = __ldg(&sc.N4[j]);
+    const float den = __fmaf_rn(Nj.z, d.z, __fmaf_rn(Nj.y, d.y, __fmul_rn(Nj.x, d.x)));
+    const float4 Pj = __ldg(&sc.P[j]);
+    const float h = __fmaf_rn(Nj.z, __fsub_rn(Pj.z, o.z),
+                              __fmaf_rn(Nj.y, __fsub_rn(Pj.y, o.y), __fmul_rn(Nj.x, __fsub_rn(Pj.x, o.x))));
+    return surfel_G(sc, surfel_r2(sc, j, o, d, __fdiv_rn(h, den)));
 }
 
 __device__ __forceinline__ bool hit_surfel(const SceneDev &sc, int j, int self, float3 o, float3 d, float tmax,
@@ -422,15 +433,15 @@ struct rgs_transport {
     // hemisphere hit records
     long long cap_slots = 0;
     int2 *rec_ja = nullptr;
-    float *rec_g = nullptr;
     long long *off = nullptr; // per-ray first record
     int *cnt = nullptr;
     unsigned *ray_ctr = nullptr; // persistent trace: next ray to fetch
     int num_sms = 0;
     float4 *dir = nullptr; // per-ray direction
+    // adjoint scratch (dy, dy_mc, tr, v, u, gh): taken from the workspace pool at the start
+    // of rgs_adjoint and returned at its end; null outside that call
     float4 *dy = nullptr;  // adjoint: per-ray (y[0..2], 0) for the current column tile
     float *dy_mc = nullptr; // adjoint, many columns: per-ray y of one 32-column tile
-    long long dy_mc_cap = 0;
     long long rays_cap = 0;
     unsigned long long *counter = nullptr;
     int *flags = nullptr;
@@ -440,31 +451,42 @@ struct rgs_transport {
     int *src_cnt = nullptr;
     unsigned long long *cursor = nullptr;
     int2 *tr = nullptr; // (ray id, bits of a)
-    long long tr_cap = 0; // entries allocated in tr
     int src_cap = 0;      // surfels allocated in src_off / src_cnt / cursor
     long long *scan_tmp = nullptr;
     int scan_tmp_cap = 0;
     // direct term D [N][C][NC]
     float *D = nullptr;
     long long nc_cap = 0; // capacity (floats) of one [N][C][NC] array
-    // iterates
+    // iterates.  stride 0: iters holds B^(0..nb) at slot b and Q holds Q^(0..nb-1).
+    // stride s >= 1 (checkpointing): slots 0..n_ckpt-1 hold the checkpoints B^(0), B^(s), ...
+    // (every multiple of s below nb), slots n_ckpt and n_ckpt+1 the running iterate by parity
+    // of b, and Q one scratch array; the adjoint recomputes the rest from the checkpoints.
     int nb_last = -1;
-    int iters_cap = 0;  // number of [N][C][NC] arrays allocated in iters / Q
-    float *iters = nullptr; // B^(0..nb)
-    float *Q = nullptr;     // Q^(0..nb-1)
-    __nv_bfloat16 *iters16 = nullptr; // BF16 copies of B^(0..nb), rows padded to bf16_stride<NC>
+    int ckpt_req = 0;   // rgs_set_checkpointing: 0 store all, s >= 1 every s-th, -1 automatic
+    int stride = 0;     // checkpoint stride of the last solve
+    int n_ckpt = 0;     // checkpoints stored by the last solve
+    int iters_cap = 0;  // number of [N][C][NC] arrays allocated in iters
+    int q_cap = 0;      // number of arrays allocated in Q
+    float *iters = nullptr;
+    float *Q = nullptr;
+    __nv_bfloat16 *iters16 = nullptr; // BF16 copies of the iters slots, rows padded to bf16_stride<NC>
     int iters16_cap = 0;
     int prec_last = 0;      // precision of the last solve
     double *norm2 = nullptr; // [RGS_MAX_BOUNCES + 1]
+    // forward slot of B^(b) for the last solve
+    int slot(int b) const {
+        if (!stride) return b;
+        if (b % stride == 0 && b / stride < n_ckpt) return b / stride;
+        return n_ckpt + (b & 1);
+    }
+    bool is_stored(int b) const { return !stride || b == nb_last || (b % stride == 0 && b / stride < n_ckpt); }
     // adjoint workspace
-    float *v = nullptr; // v^(0..nb)
-    int v_cap = 0;
+    float *v = nullptr; // v^(0..nb), or a ring of stride + 1 arrays when checkpointing
     float *u = nullptr;
     float *Pg = nullptr;  // [N][4][3]
     float *dop = nullptr; // [N]
     int pg_cap = 0;       // surfels allocated in Pg / dop
     float *gh = nullptr;  // per hit-record slot: dL/d(weight) accumulated over the bounces
-    long long gh_cap = 0;
     long long device_bytes = 0;
     RaysDev rays() const {
         RaysDev r;
@@ -473,7 +495,6 @@ struct rgs_transport {
         r.nbs = nbs;
         r.seed = seed;
         r.rec_ja = rec_ja;
-        r.rec_g = rec_g;
         r.off = off;
         r.cnt = cnt;
         r.dir = dir;
@@ -504,9 +525,16 @@ rgs_status rgs_cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return rgs_cuda_fail(e_, what);                                                         \
     } while (0)
 
+// sizes of the library's live cudaMalloc blocks (rgs_api.cu), so that reallocation keeps
+// each handle's device_bytes equal to what it holds
+void rgs_alloc_note(void *p, size_t bytes);
+size_t rgs_alloc_forget(void *p);
+
 template <class T>
 rgs_status dev_alloc(T **p, size_t count, long long *acct = nullptr) {
     if (*p) {
+        const size_t old = rgs_alloc_forget(*p);
+        if (acct) *acct -= (long long)old;
         cudaFree(*p);
         *p = nullptr;
     }
@@ -518,23 +546,59 @@ rgs_status dev_alloc(T **p, size_t count, long long *acct = nullptr) {
         rgs_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
         return RGS_ERR_OOM;
     }
+    rgs_alloc_note(*p, count * sizeof(T));
     if (acct) *acct += (long long)(count * sizeof(T));
     return RGS_OK;
 }
 template <class T> void dev_free(T *&p) {
-    if (p) cudaFree(p);
+    if (p) {
+        rgs_alloc_forget(p);
+        cudaFree(p);
+    }
     p = nullptr;
 }
 
-// many-column kernels (rgs_manycol.cu), used when C >= RGS_MC_MIN_COLS
-#define RGS_MC_MIN_COLS 48
+// Stream-ordered scratch from a library-owned memory pool (one per device, created on
+// first use, memory kept reserved between calls until rgs_trim_workspace).  Used for the
+// workspaces that live only inside one call (adjoint), so that transports that run one
+// after another on a stream share the same memory.
+rgs_status pool_alloc_bytes(void **p, size_t bytes, cudaStream_t st);
+void pool_free(void *p, cudaStream_t st);
+template <class T> rgs_status pool_alloc(T **p, size_t count, cudaStream_t st) {
+    *p = nullptr;
+    return pool_alloc_bytes(reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(T), st);
+}
+template <class T> void pool_release(T *&p, cudaStream_t st) {
+    if (p) pool_free(p, st);
+    p = nullptr;
+}
+
+// Column layout of the gathers.  The 3-column kernels (4 lanes share a ray, each lane a
+// slice of the coefficients of 3 columns) re-read the hit records and re-evaluate the SH
+// per 3-column tile; the lane-per-column kernels (rgs_manycol.cu) read them once per
+// 32-column tile but leave lanes idle when C is not a multiple of 32, and load a full
+// column row per lane (32 bytes BF16, 64 bytes FP32).  Crossovers measured on GB300 with
+// SH degree 3 and 50,000 surfels: the bounce on BF16 rows from 18 columns, on FP32 rows
+// from 64; the opacity gather on BF16 rows from 12, on FP32 rows from 64; the adjoint
+// (FP32) when one 32-column tile costs less than 26.5 three-column passes would.
+__host__ __device__ inline bool wide_bounce(int C, bool rows16) { return C >= (rows16 ? 18 : 64); }
+__host__ __device__ inline bool wide_opacity(int C, bool rows16) { return C >= (rows16 ? 12 : 64); }
+__host__ __device__ inline bool wide_adjoint(int C) { return 2 * C > 53 * ((C + 31) / 32); }
 template <int NC>
 rgs_status mc_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, bool rows16, const float *Bprev,
                      const __nv_bfloat16 *Bprev16, const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16,
                      double *norm2, cudaStream_t st);
 template <int NC>
 rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const float *vin, float *vout, cudaStream_t st);
-template <int NC> rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int nb, cudaStream_t st);
+// per-launch set of up to NA adjoint iterates v^(a) and the matching B^(n-1-a) (FP32 or BF16)
+template <class T, int NA> struct OpaSet {
+    const float *v[NA];
+    const T *b[NA];
+};
+// g_h += sum over the na iterates of the set, for every column (first: write instead of add)
+template <int NC>
+rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int na, const float *const *v, const float *const *Bf,
+                      const __nv_bfloat16 *const *Bh, bool first, cudaStream_t st);
 
 // entry points implemented per translation unit
 rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_build_opts *o, cudaStream_t st);
@@ -543,7 +607,13 @@ rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precisio
                           rgs_solve_stats *stats, cudaStream_t st);
 rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st);
 rgs_status rgs_get_iterate_impl(rgs_transport *t, int b, float *out, cudaStream_t st);
-rgs_status rgs_solve_prepare(rgs_transport *t, int nb, int precision, cudaStream_t st);
+rgs_status rgs_solve_prepare(rgs_transport *t, int nb, int precision, int stride, cudaStream_t st);
+// B^(b) for b in (c, e] from the stored checkpoint or iterate B^(c), with Q^(b-1); outputs are
+// indexed by b - c - 1 (B, B16) and b - c - 1 (Q).  Uses the precision of the last solve.
+rgs_status rgs_recompute(rgs_transport *t, int c, int e, float *const *B, __nv_bfloat16 *const *B16,
+                         float *const *Q, double *norm2, cudaStream_t st);
+// stride the automatic checkpoint mode picks for nb bounces at this precision
+int rgs_auto_stride(const rgs_transport *t, int nb, int precision);
 rgs_status rgs_solve_batched_impl(rgs_transport *const *ts, int count, const float *const *E, const int32_t *nbs,
                                   const rgs_batch_opts *opts, float *const *B_out, double *norms, cudaStream_t st);
 void rgs_batch_forget(const rgs_transport *t);

@@ -5,51 +5,11 @@
 // hit record once per 3-column tile; here a warp takes one ray (or one transposed entry) at
 // a time and its 32 lanes take 32 consecutive columns, so each hit is read once per
 // 32-column tile and every row load is one contiguous 512-byte (BF16) or 1-KiB (FP32)
-// warp access.  Used when C >= RGS_MC_MIN_COLS.
-#include "rgs_internal.cuh"
+// warp access.  Which layout a launch uses is decided per kernel family by wide_bounce,
+// wide_opacity and wide_adjoint (rgs_internal.cuh).
+#include "rgs_bounce_body.cuh"
 
 namespace {
-
-constexpr int MC_WARPS = 8;
-constexpr int MC_THREADS = MC_WARPS * 32;
-
-// the NC coefficients of one column of a row (FP32 rows of NC floats, BF16 rows padded)
-template <int NC> __device__ __forceinline__ void load_col(const float *__restrict__ p, float *v) {
-    if constexpr (NC % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < NC / 4; ++q) {
-            const float4 f = __ldg(reinterpret_cast<const float4 *>(p) + q);
-            v[4 * q] = f.x;
-            v[4 * q + 1] = f.y;
-            v[4 * q + 2] = f.z;
-            v[4 * q + 3] = f.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < NC; ++k) v[k] = __ldg(p + k);
-    }
-}
-template <int NC> __device__ __forceinline__ void load_col(const __nv_bfloat16 *__restrict__ p, float *v) {
-    if constexpr (NC >= 9) { // padded to 16
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p) + q);
-            const unsigned u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int k0 = 8 * q + 2 * m;
-                if (k0 < NC) v[k0] = __uint_as_float(u[m] << 16);
-                if (k0 + 1 < NC) v[k0 + 1] = __uint_as_float(u[m] & 0xffff0000u);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < NC; ++k) v[k] = __bfloat162float(p[k]);
-    }
-}
-template <int NC, class T> constexpr int row_stride() {
-    return sizeof(T) == 2 ? ((NC >= 9) ? 16 : NC) : NC;
-}
 
 // ------------------------------------------------------------------ forward bounce
 template <int NC, class T>
@@ -57,65 +17,8 @@ __global__ void __launch_bounds__(MC_THREADS) k_bounce_mc(SceneDev sc, RaysDev r
                                                          const float *__restrict__ Bprev, const float *__restrict__ S,
                                                          float *__restrict__ Qout, float *__restrict__ Bout,
                                                          __nv_bfloat16 *__restrict__ Bout16, double *norm2) {
-    constexpr int RS = row_stride<NC, T>();
-    const int i = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int col = blockIdx.y * 32 + lane;
-    const bool live = col < C;
-    const int colc = live ? col : C - 1;
-    const int nd = rays.nd;
-    const float3 n = f3(sc.N4[i]);
-    float acc[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) acc[k] = 0.f;
-    for (int q = warp; q < nd; q += MC_WARPS) {
-        const long long r = (long long)i * nd + q;
-        const float3 d = f3(rays.dir[r]);
-        float Yo[NC];
-        sh_eval<NC>(neg3(d), Yo);
-        const int cnt = rays.cnt[r];
-        const long long base = rays.off[r];
-        float x = 0.f;
-#pragma unroll 2
-        for (int h = 0; h < cnt; ++h) {
-            const int2 ja = __ldg(&rays.rec_ja[base + h]);
-            float v[NC];
-            load_col<NC>(Bg + ((size_t)ja.x * C + colc) * RS, v);
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
-            x += __int_as_float(ja.y) * s;
-        }
-        float Yi[NC];
-        sh_eval<NC>(reflect_n(n, d), Yi);
-#pragma unroll
-        for (int k = 0; k < NC; ++k) acc[k] += Yi[k] * x;
-    }
-    __shared__ float red[MC_WARPS][NC][32];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) red[warp][k][lane] = acc[k];
-    __syncthreads();
-    double dsq = 0.0;
-    const float w = 3.14159265358979f / (float)nd;
-    for (int e = threadIdx.x; e < NC * 32; e += MC_THREADS) {
-        const int k = e >> 5, c = e & 31;
-        const int cc = blockIdx.y * 32 + c;
-        if (cc >= C) continue;
-        float v = 0.f;
-#pragma unroll
-        for (int q = 0; q < MC_WARPS; ++q) v += red[q][k][c];
-        const float Q = w * v;
-        const size_t idx = ((size_t)i * C + cc) * NC + k;
-        Qout[idx] = Q;
-        const float b = S[idx] + sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (cc % 3)] * Q;
-        Bout[idx] = b;
-        if (Bout16) Bout16[((size_t)i * C + cc) * ((NC >= 9) ? 16 : NC) + k] = __float2bfloat16_rn(b);
-        const double df = (double)b - (double)Bprev[idx];
-        dsq += df * df;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) dsq += __shfl_xor_sync(0xffffffffu, dsq, off);
-    if (lane == 0) atomicAdd(norm2, dsq);
+    __shared__ float red[MC_WARPS * NC * 32];
+    bounce_receiver_mc<NC, T>(sc, rays, C, Bg, Bprev, S, Qout, Bout, Bout16, norm2, blockIdx.x, blockIdx.y, red);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -192,10 +95,8 @@ __global__ void __launch_bounds__(MC_THREADS) k_adj_src_mc(RaysDev rays, int C, 
 // opacity backward: per hit g_h (partial over this column tile and iterate chunk)
 // accumulated into gh[slot]; a warp per ray, lanes over columns
 template <int NC, int NA, class T>
-__global__ void __launch_bounds__(MC_THREADS) k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int ct, int nb, int a0,
-                                                            int na, size_t A, const float *__restrict__ V,
-                                                            const T *__restrict__ Bit, size_t AB, float *gh,
-                                                            bool first) {
+__global__ void __launch_bounds__(MC_THREADS) k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int ct, int na,
+                                                            OpaSet<T, NA> it, float *gh, bool first) {
     constexpr int RS = row_stride<NC, T>();
     const int warp_g = (int)((blockIdx.x * (size_t)MC_THREADS + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -221,7 +122,7 @@ __global__ void __launch_bounds__(MC_THREADS) k_opacity_g_mc(SceneDev sc, RaysDe
             float s = 0.f;
             if (aa < na && live) {
                 float v[NC];
-                load_col<NC>(V + A * (a0 + aa) + ((size_t)i * C + col) * NC, v);
+                load_col<NC>(it.v[aa] + ((size_t)i * C + col) * NC, v);
 #pragma unroll
                 for (int k = 0; k < NC; ++k) s += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + col % 3]) * Yi[k] * v[k];
             }
@@ -236,7 +137,7 @@ __global__ void __launch_bounds__(MC_THREADS) k_opacity_g_mc(SceneDev sc, RaysDe
         for (int aa = 0; aa < NA; ++aa) {
             if (aa < na) {
                 float v[NC];
-                load_col<NC>(Bit + AB * (nb - 1 - (a0 + aa)) + ((size_t)j * C + colc) * RS, v);
+                load_col<NC>(it.b[aa] + ((size_t)j * C + colc) * RS, v);
                 float s = 0.f;
 #pragma unroll
                 for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
@@ -280,26 +181,27 @@ rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const fl
 }
 
 template <int NC>
-rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int nb, cudaStream_t st) {
+rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int na, const float *const *v, const float *const *Bf,
+                      const __nv_bfloat16 *const *Bh, bool first, cudaStream_t st) {
     constexpr int NA = 4;
-    const size_t A = t->arr();
     const long long n_rays = (long long)t->n * t->nd;
     const unsigned grid = (unsigned)((n_rays * 32 + MC_THREADS - 1) / MC_THREADS);
-    for (int ct = 0; ct * 32 < t->C; ++ct)
-        for (int a0 = 0; a0 < nb; a0 += NA) {
-            const int na = min(NA, nb - a0);
-            const bool first = (ct == 0 && a0 == 0);
-            if (t->prec_last != RGS_FP32) {
-                const size_t A16 = (size_t)t->n * t->C * ((NC >= 9) ? 16 : NC);
-                ProfScope ps_("k_opacity_g_mc", st);
-                k_opacity_g_mc<NC, NA, __nv_bfloat16><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, nb, a0, na, A, t->v,
-                                                                                   t->iters16, A16, t->gh, first);
-            } else {
-                ProfScope ps_("k_opacity_g_mc", st);
-                k_opacity_g_mc<NC, NA, float><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, nb, a0, na, A, t->v,
-                                                                           t->iters, A, t->gh, first);
-            }
+    OpaSet<float, NA> sf = {};
+    OpaSet<__nv_bfloat16, NA> sh = {};
+    for (int a = 0; a < na; ++a) {
+        sf.v[a] = sh.v[a] = v[a];
+        sf.b[a] = Bf[a];
+        sh.b[a] = Bh ? Bh[a] : nullptr;
+    }
+    for (int ct = 0; ct * 32 < t->C; ++ct) {
+        if (Bh) {
+            ProfScope ps_("k_opacity_g_mc", st);
+            k_opacity_g_mc<NC, NA, __nv_bfloat16><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, na, sh, t->gh, first && ct == 0);
+        } else {
+            ProfScope ps_("k_opacity_g_mc", st);
+            k_opacity_g_mc<NC, NA, float><<<grid, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, na, sf, t->gh, first && ct == 0);
         }
+    }
     RGS_LAUNCH("opacity mc");
     return RGS_OK;
 }
@@ -310,7 +212,8 @@ rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int nb, cudaStr
                                       double *, cudaStream_t);                                                         \
     template rgs_status mc_adjoint_bounce<NC>(rgs_transport *, SceneDev, RaysDev, const float *, float *,              \
                                               cudaStream_t);                                                           \
-    template rgs_status mc_opacity<NC>(rgs_transport *, SceneDev, RaysDev, int, cudaStream_t);
+    template rgs_status mc_opacity<NC>(rgs_transport *, SceneDev, RaysDev, int, const float *const *,                 \
+                                       const float *const *, const __nv_bfloat16 *const *, bool, cudaStream_t);
 RGS_MC_INSTANTIATE(1)
 RGS_MC_INSTANTIATE(4)
 RGS_MC_INSTANTIATE(9)

@@ -21,7 +21,7 @@ namespace {
 // allocates exactly its rays' kept hits with one atomic (prefix sum over the lanes) and
 // every ray stores its records contiguously.
 __global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays, int n_rays, long long cap_slots,
-                                                       unsigned long long *slot_ctr, int2 *rec_ja, float *rec_g,
+                                                       unsigned long long *slot_ctr, int2 *rec_ja,
                                                        long long *off_out, int *cnt_out, float4 *dir_out,
                                                        int *src_cnt, int *flags) {
     const unsigned FULL = 0xffffffffu;
@@ -121,7 +121,6 @@ __global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays
         const float G = surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[h] >> 32))));
         const float alpha = __ldg(&sc.P[j].w) * G;
         rec_ja[mine + h] = make_int2(j, __float_as_int(alpha * T));
-        rec_g[mine + h] = G;
         T *= 1.f - alpha;
         atomicAdd(&src_cnt[j], 1); // transposed-index histogram
     }
@@ -161,23 +160,6 @@ __global__ void k_direct(SceneDev sc, int nl, const float *__restrict__ lpos, co
     }
 }
 
-__global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
-    const long long base = rays.off[r];
-    const int c = rays.cnt[r];
-    for (int h = 0; h < c; ++h) {
-        const int2 ja = rays.rec_ja[base + h];
-        const unsigned long long pos = atomicAdd(&cursor[ja.x], 1ull);
-        tr[pos] = make_int2(r, ja.y);
-    }
-}
-
-__global__ void k_copy_off(const long long *off, unsigned long long *cursor, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) cursor[i] = (unsigned long long)off[i];
-}
-
 } // namespace
 
 static int strata_a(int nd) {
@@ -215,7 +197,6 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
     if (n_rays > t->rays_cap) {
         if ((r = dev_alloc(&t->cnt, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->dir, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
-        if ((r = dev_alloc(&t->dy, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->off, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
         t->rays_cap = n_rays;
     }
@@ -233,7 +214,6 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         t->nc_cap = arr;
         t->iters_cap = 0; // iterate buffers are sized by the array size: force regrowth
         t->iters16_cap = 0;
-        t->v_cap = 0;
     }
     if (n > t->src_cap) {
         if ((r = dev_alloc(&t->src_off, (size_t)n + 1, &t->device_bytes)) != RGS_OK) return r;
@@ -249,7 +229,6 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (want > t->cap_slots) {
             if ((r = dev_alloc(&t->rec_ja, (size_t)want, &t->device_bytes)) != RGS_OK) return r;
-            if ((r = dev_alloc(&t->rec_g, (size_t)want, &t->device_bytes)) != RGS_OK) return r;
             t->cap_slots = want;
         }
         RGS_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
@@ -257,7 +236,7 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
         RaysDev rd = t->rays();
         const int TB = 128;
-        { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter, t->rec_ja, t->rec_g, t->off, t->cnt, t->dir, t->src_cnt, t->flags); }
+        { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter, t->rec_ja, t->off, t->cnt, t->dir, t->src_cnt, t->flags); }
         RGS_LAUNCH("trace_hemi");
         unsigned long long used = 0;
         int flags[FLAG_COUNT];
@@ -292,20 +271,11 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         RGS_CUDA(cudaMemsetAsync(t->D, 0, sizeof(float) * (size_t)arr, st));
     }
 
-    // transposed index: records grouped by source surfel
-    RaysDev rd = t->rays();
+    // per-source hit counts -> offsets of the transposed index (filled by rgs_adjoint)
     if ((r = rgs_scan_counts(t->src_cnt, t->src_off, n, t->scan_tmp, t->scan_tmp_cap, st)) != RGS_OK) return r;
     long long total = 0;
     RGS_CUDA(cudaMemcpyAsync(&total, t->src_off + n, sizeof total, cudaMemcpyDeviceToHost, st));
     RGS_CUDA(cudaStreamSynchronize(st));
     t->n_hits = total;
-    if (total > t->tr_cap) {
-        const long long want_tr = total + total / 8 + 1024;
-        if ((r = dev_alloc(&t->tr, (size_t)want_tr, &t->device_bytes)) != RGS_OK) return r;
-        t->tr_cap = want_tr;
-    }
-    { ProfScope ps_("k_copy_off", st); k_copy_off<<<(n + 255) / 256, 256, 0, st>>>(t->src_off, t->cursor, n); }
-    { ProfScope ps_("k_src_fill", st); k_src_fill<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->cursor, t->tr); }
-    RGS_LAUNCH("src_fill");
     return RGS_OK;
 }

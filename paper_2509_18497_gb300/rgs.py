@@ -28,7 +28,8 @@ STATUS = {0: "RGS_OK", 1: "RGS_ERR_ARG", 2: "RGS_ERR_CUDA", 3: "RGS_ERR_OOM", 4:
 EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
            "rgs_transport_info_get", "rgs_destroy_transport", "rgs_destroy_scene", "rgs_profile_enable",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
-           "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched")
+           "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
+           "rgs_set_checkpointing", "rgs_trim_workspace")
 
 
 class RgsError(RuntimeError):
@@ -113,6 +114,10 @@ def load(path=LIB_PATH):
                                     ct.POINTER(rgs_batch_opts), ct.POINTER(vp), ct.POINTER(ct.c_double), vp]
     L.rgs_solve_batched.restype = ct.c_int
     L.rgs_residual_norm_noalloc.restype = ct.c_int
+    L.rgs_set_checkpointing.argtypes = [vp, ct.c_int32]
+    L.rgs_set_checkpointing.restype = ct.c_int
+    L.rgs_trim_workspace.argtypes = []
+    L.rgs_trim_workspace.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
                "rgs_transport_info_get"):
         getattr(L, fn).restype = ct.c_int
@@ -258,6 +263,17 @@ def rgs_get_iterate(transport, b, out=None, stream=None):
         out = torch.empty((n, nc, C), device="cuda", dtype=torch.float32)
     _check(L.rgs_get_iterate(transport.h, int(b), _dev(out, (n, nc, C), "out"), _stream(stream)))
     return out
+
+
+def rgs_set_checkpointing(transport, stride):
+    """0: keep every iterate; s >= 1: keep B^(0), B^(s), ... and recompute in the adjoint;
+    -1: automatic (checkpoint only when the full storage does not fit)."""
+    _check(load().rgs_set_checkpointing(transport.h, int(stride)))
+
+
+def rgs_trim_workspace():
+    """Return the unused part of the library's workspace pool to the device."""
+    _check(load().rgs_trim_workspace())
 
 
 def rgs_transport_info_get(transport):

@@ -272,6 +272,75 @@ def uneven_batch(count=32, base_seed=1000, n_lights=8):
     return out
 
 
+def _lattice_hash(ix, iy, iz, salt):
+    """Integer lattice hash -> [0, 1): a 32-bit multiply-xorshift mix of the three
+    coordinates (wrapped to uint32) and a salt."""
+    m = np.uint64(0xFFFFFFFF)
+    h = (ix.astype(np.int64).astype(np.uint64) * np.uint64(0x8DA6B343)) & m
+    h ^= (iy.astype(np.int64).astype(np.uint64) * np.uint64(0xD8163841)) & m
+    h ^= (iz.astype(np.int64).astype(np.uint64) * np.uint64(0xCB1AB31F)) & m
+    h ^= np.uint64(salt) & m
+    h = (h ^ (h >> np.uint64(16))) * np.uint64(0x7FEB352D) & m
+    h = (h ^ (h >> np.uint64(15))) * np.uint64(0x846CA68B) & m
+    h ^= h >> np.uint64(16)
+    return (h & m).astype(np.float64) / 4294967296.0
+
+
+def value_noise(x, salt=0):
+    """Value noise on the integer lattice: hashed corner values blended trilinearly with
+    smoothstep weights. x: [M,3] -> [M] in [0, 1)."""
+    x = np.asarray(x, np.float64)
+    i0 = np.floor(x)
+    f = x - i0
+    w = f * f * (3.0 - 2.0 * f)
+    i0 = i0.astype(np.int64)
+    out = np.zeros(x.shape[0])
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                wt = ((w[:, 0] if dx else 1.0 - w[:, 0]) * (w[:, 1] if dy else 1.0 - w[:, 1])
+                      * (w[:, 2] if dz else 1.0 - w[:, 2]))
+                out += wt * _lattice_hash(i0[:, 0] + dx, i0[:, 1] + dy, i0[:, 2] + dz, salt)
+    return out
+
+
+def large_scene(n=1000000, seed=0, L=3, nd=512, nb=6, n_lights=16, scale=4.0, room=20.0):
+    """The fruit bowl scaled by `scale` inside a room: four walls and a ceiling of side
+    `room` (x, z in [-room/2, room/2], y in [0, room]) facing inward, whose diffuse albedo
+    is 0.2 + 0.6 * value_noise(0.5 * x) per channel (three lattice salts). Surfel counts
+    are proportional to area over all parts, scales U[0.4,0.9]*sqrt(A/N) as in fruit_bowl.
+    `n_lights` white lights U[5,20] on a Fibonacci sphere of radius 0.4*room centred at
+    mid-height, so that every light is inside the room."""
+    rng = np.random.default_rng(seed)
+    parts = _bowl_parts(rng, scale)
+    h = room / 2.0
+    walls = [
+        _Rect((-h, room, -h), (1, 0, 0), (0, 0, 1), room, room, (0, -1, 0)),  # ceiling
+        _Rect((-h, 0, -h), (0, 1, 0), (1, 0, 0), room, room, (0, 0, 1)),      # z = -h
+        _Rect((-h, 0, h), (1, 0, 0), (0, 1, 0), room, room, (0, 0, -1)),      # z = +h
+        _Rect((-h, 0, -h), (0, 0, 1), (0, 1, 0), room, room, (1, 0, 0)),      # x = -h
+        _Rect((h, 0, -h), (0, 1, 0), (0, 0, 1), room, room, (-1, 0, 0)),      # x = +h
+    ]
+    parts = parts + walls
+    areas = [q.area() for q in parts]
+    counts = _split_counts(areas, n)
+    spacing = math.sqrt(sum(areas) / n)
+    sc = _assemble(parts, counts, rng, lambda m: rng.uniform(0.4, 0.9, size=(m, 2)) * spacing,
+                   (0.1, 0.9), (0.5, 1.0), L, False)
+    n_wall = int(sum(counts[-len(walls):]))
+    pw = sc["p"][-n_wall:]
+    tex = np.stack([value_noise(0.5 * pw, salt=c) for c in range(3)], axis=1)
+    ad = sc["ad"].copy()
+    ad[-n_wall:] = 0.2 + 0.6 * tex
+    k, as_ = sc["k"], sc["as_"].copy()
+    cap = (0.95 - k[-n_wall:, None] * ad[-n_wall:]) / np.maximum(1.0 - k[-n_wall:, None], 1e-12)
+    as_[-n_wall:] = np.minimum(as_[-n_wall:], np.maximum(cap, 0.0))
+    sc["ad"], sc["as_"] = ad, as_
+    lp = fibonacci_sphere(n_lights, 0.4 * room, (0.0, h, 0.0))
+    li = np.repeat(rng.uniform(5.0, 20.0, size=(n_lights, 1)), 3, axis=1)
+    return _finish(sc, L, nd, nb, seed, lp, li, name=f"large_{n}")
+
+
 def with_emission(sc, seed=1, scale=0.5, dc_only=False):
     """Attach a seeded emission E[N,nc,3] (used by the gradient tests)."""
     rng = np.random.default_rng(seed)

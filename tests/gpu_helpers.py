@@ -14,10 +14,11 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=False, precision=rgs.RGS_FP32):
+def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=False, precision=rgs.RGS_FP32,
+            checkpoint=0):
     """build -> trace -> solve (-> adjoint with dL/dB = W) on cuda:0; numpy float64 out."""
     d = api.upload(sc)
-    pipe = api.Pipeline(alpha_model, precision)
+    pipe = api.Pipeline(alpha_model, precision, checkpoint=checkpoint)
     pipe.build(d)
     pipe.trace(d)
     B, st = pipe.solve(d["E"], d["nb"], stats=stats)
