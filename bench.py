@@ -41,6 +41,9 @@ MULTI_WORKLOAD = ("multi-light batch: 200,000 fruit-bowl surfels, 100 point ligh
 UNEVEN_WORKLOAD = ("uneven batch: 32 independent fruit-bowl scenes (seeds 1000..1031), surfel counts log-uniform in "
                    "[5,000, 300,000], SH degree 2 or 3, 128/192/256 rays/surfel, 3-5 bounces, 8 point lights each; "
                    "all bounces of all scenes in one persistent graph-captured launch (autotuned), forward + adjoint")
+LARGE_WORKLOAD = ("large scene: 1,000,000 surfels (fruit bowl scaled x4 inside a 20 x 20 x 20 room whose walls "
+                  "carry value-noise albedo), SH degree 3, 512 rays/surfel, 6 bounces, 16 point lights, "
+                  "iterates checkpointed as memory asks (automatic stride), forward + adjoint")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -209,10 +212,10 @@ class Form:
     their output buffers; `launch` = "batched" solves every scene in one rgs_solve_batched
     call (the persistent graph-captured kernel), "per_scene" calls rgs_solve per scene."""
 
-    def __init__(self, api, rgs, torch, datas, precision, launch, dev):
+    def __init__(self, api, rgs, torch, datas, precision, launch, dev, checkpoint=0):
         self.api, self.rgs, self.torch = api, rgs, torch
         self.precision, self.launch = precision, launch
-        self.pipes = [api.Pipeline(precision=precision) for _ in datas]
+        self.pipes = [api.Pipeline(precision=precision, checkpoint=checkpoint) for _ in datas]
         self.Bs = [torch.empty((d["n"], (d["L"] + 1) ** 2, 3 * max(1, d["light_pos"].shape[0])), device=dev)
                    for d in datas]
         self.grads = [(torch.empty((d["n"], (d["L"] + 1) ** 2, 3), device=dev), torch.empty((d["n"], 3), device=dev),
@@ -248,9 +251,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=50000, help="surfel count (default: the 50,000-surfel workload)")
-    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven"],
+    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven", "large"],
                     help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights; "
-                         "uneven: 32 scenes of uneven size in one persistent launch")
+                         "uneven: 32 scenes of uneven size in one persistent launch; large: 1,000,000 surfels, "
+                         "512 rays, 6 bounces, 16 lights, checkpointed iterates")
     ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1500, help="surfels per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -279,6 +283,9 @@ def main():
     elif args.workload == "uneven":
         scs = scenes.uneven_batch(32)
         workload = UNEVEN_WORKLOAD
+    elif args.workload == "large":
+        scs = [scenes.large_scene(n=1000000 if args.n == 50000 else args.n)]
+        workload = LARGE_WORKLOAD
     else:
         scs = [scenes.fruit_bowl(n=args.n)]
         workload = WORKLOAD
@@ -293,25 +300,23 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # batched form (BF16 gathers, FP32 accumulation, one FP32 residual-correction bounce;
-    # scenes of a batch in one persistent launch) and the plain FP32 form, on the same inputs
+    # scenes of a batch in one persistent launch) and the plain FP32 form, on the same inputs.
+    # Each form is built, warmed up and timed in turn; the large scene releases one form's
+    # device memory before building the next (both would not fit at once).
     batched_launch = "batched" if len(scs) > 1 else "per_scene"
-    forms = {"batched": Form(api, rgs, torch, datas, rgs.RGS_BF16_FP32ACC_RESCORR, batched_launch, dev),
-             "plain": Form(api, rgs, torch, datas, rgs.RGS_FP32, "per_scene", dev)}
-    for f in forms.values():
+    sequential = args.workload == "large"
+    ckpt = -1 if args.workload == "large" else 0
+    specs = {"plain": (rgs.RGS_FP32, "per_scene"), "batched": (rgs.RGS_BF16_FP32ACC_RESCORR, batched_launch)}
+
+    def make_form(name):
+        prec, launch = specs[name]
+        f = Form(api, rgs, torch, datas, prec, launch, dev, checkpoint=ckpt)
         for _ in range(max(args.warmup, 3)):
             f.step(datas, gs)
-    torch.cuda.synchronize()
-    infos = []
-    for sc, p in zip(scs, forms["batched"].pipes):
-        info = rgs.rgs_transport_info_get(p.transport)
-        infos.append(dict(n=sc["n"], nd=sc["nd"], nb=sc["nb"], C=info["n_cols"], nc=info["nc"], n_hits=info["n_hits"]))
-    # accuracy of the batched form against the FP32 form (which the tests hold to 1e-4 of the oracle)
-    rel_err = _rel(forms["batched"].Bs, forms["plain"].Bs, torch)
-    grad_err = max(_rel([g[q] for g in forms["batched"].grads], [g[q] for g in forms["plain"].grads], torch)
-                   for q in range(3))
+        torch.cuda.synchronize()
+        return f
 
-    def timed(form, profile):
-        f = forms[form]
+    def timed(f, profile):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if world > 1:
             dist.barrier()
@@ -342,16 +347,41 @@ def main():
             dist.barrier()
         return units_per_step * args.steps * world / total_s, step_ms, launches, prof, t_wall
 
+    clocks = Clocks(local)
+    res, outs = {}, {}
+    f = None
+    for name in ("plain", "batched"):
+        if f is not None and sequential:
+            del f
+            torch.cuda.synchronize()
+            rgs.rgs_trim_workspace()
+            torch.cuda.empty_cache()
+        f = make_form(name)
+        res[name] = timed(f, True)
+        keep = (lambda x: x.cpu()) if sequential else (lambda x: x.clone())
+        outs[name] = ([keep(B) for B in f.Bs], [tuple(keep(x) for x in gr) for gr in f.grads])
+        if name == "batched":
+            infos = []
+            for sc, p in zip(scs, f.pipes):
+                info = rgs.rgs_transport_info_get(p.transport)
+                infos.append(dict(n=sc["n"], nd=sc["nd"], nb=sc["nb"], C=info["n_cols"], nc=info["nc"],
+                                  n_hits=info["n_hits"], device_bytes=info["device_bytes"]))
+    clk = clocks.stop()
+    # accuracy of the batched form against the FP32 form (which the tests hold to 1e-4 of the oracle)
+    rel_err = _rel(outs["batched"][0], outs["plain"][0], torch)
+    grad_err = max(_rel([g[q] for g in outs["batched"][1]], [g[q] for g in outs["plain"][1]], torch)
+                   for q in range(3))
+    del outs
     # the headline is the batched form when it meets the 1e-3 accuracy gate, else plain
     headline = "batched" if rel_err <= 1e-3 else "plain"
-    other = "plain" if headline == "batched" else "batched"
-    clocks = Clocks(local)
-    value, step_ms, launches, prof, t_wall = timed(headline, True)
-    clk = clocks.stop()
-    value_o, step_ms_o, _, _, _ = timed(other, False)
-    value_b, value_p = (value, value_o) if headline == "batched" else (value_o, value)
-    step_ms_b, step_ms_p = (step_ms, step_ms_o) if headline == "batched" else (step_ms_o, step_ms)
-    f = forms[headline]
+    value, step_ms, launches, prof, t_wall = res[headline]
+    value_b, step_ms_b = res["batched"][0], res["batched"][1]
+    value_p, step_ms_p = res["plain"][0], res["plain"][1]
+    if headline == "plain":  # the last form built is the batched one
+        del f
+        torch.cuda.synchronize()
+        rgs.rgs_trim_workspace()
+        f = make_form("plain")
 
     # ---------------------------------------------------------- end to end (host buffers)
     keys = api.SURFEL_KEYS + ("light_pos", "light_I")
@@ -424,6 +454,7 @@ def main():
         config = {"workload": workload, "scenes": len(scs), "n_surfels_total": sum(x["n"] for x in scs),
                   "rays_total": sum(x["n"] * x["nd"] for x in scs), "lights_per_scene": 8,
                   "hit_records": sum(x["n_hits"] for x in infos), "units_per_step": units_per_step}
+    config["transport_device_bytes"] = sum(x["device_bytes"] for x in infos)
     config.update({"precision": headline, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -237,6 +237,15 @@ rgs_status rgs_get_iterate(rgs_transport *t, int32_t b, float *out, void *stream
  * (stride < -1 or > RGS_MAX_BOUNCES). */
 rgs_status rgs_set_checkpointing(rgs_transport *t, int32_t stride);
 
+/* Device-memory budget of t: the bytes its own buffers and the pooled scratch of its calls
+ * may take (0 = no budget: the device's free memory decides).  It steers the two memory
+ * choices the library makes on its own: the automatic checkpoint stride (stride -1 of
+ * rgs_set_checkpointing) and the number of parts rgs_adjoint splits the transposed hit
+ * index into (8 bytes per hit; each part is rebuilt from the records for every transposed
+ * bounce, so more parts cost time, not accuracy).  Buffers the solve needs regardless are
+ * allocated even above the budget.  Host-only.  Errors: RGS_ERR_ARG. */
+rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
+
 /* Workspace pool: the per-call scratch of rgs_adjoint (the transposed hit index, 8 bytes per
  * hit; per-hit opacity sums, 4 bytes; v^(a) and u; per-ray adjoint values) and of
  * rgs_get_iterate comes from one stream-ordered memory pool per device, so transports used

@@ -29,10 +29,11 @@ class Pipeline:
     library's stream-ordered pool, which keeps it reserved, so steady-state steps make no
     cudaMalloc inside the library."""
 
-    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32, checkpoint=0):
+    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32, checkpoint=0, mem_budget=0):
         self.alpha_model = alpha_model
         self.precision = precision
         self.checkpoint = checkpoint  # iterate checkpoint stride (0 all kept, -1 automatic)
+        self.mem_budget = mem_budget  # device bytes the transport may hold with its scratch (0: none)
         self.scene = None
         self.transport = None
 
@@ -46,6 +47,7 @@ class Pipeline:
                                                  hit_capacity=hit_capacity, stream=stream,
                                                  transport=self.transport)
         rgs.rgs_set_checkpointing(self.transport, self.checkpoint)
+        rgs.rgs_set_memory_budget(self.transport, self.mem_budget)
         return self.transport
 
     def solve(self, E, nb, B_out=None, stats=False, stream=None, precision=None):

@@ -11,6 +11,7 @@
 // gathers (d, y) per entry, 32 bytes, instead of a 192-byte row of v_i per entry.
 // k_opacity_g / k_opacity_rec and k_shadow_bwd run the compositing backward of every
 // hemisphere and shadow ray (dL/dalpha_h = T_h (g_h - R_h), dL/dT = -prod of the other (1 - alpha)).
+#include <algorithm>
 #include <vector>
 
 #include "rgs_internal.cuh"
@@ -77,15 +78,16 @@ __global__ void __launch_bounds__(256) k_adj_ray(SceneDev sc, RaysDev rays, int 
 template <int NC>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_src(RaysDev rays, int C, int col0, const long long *__restrict__ src_off,
                                                         const int2 *__restrict__ tr, const float4 *__restrict__ dy,
-                                                        float *__restrict__ vout, float *__restrict__ u) {
+                                                        float *__restrict__ vout, float *__restrict__ u, int j0,
+                                                        long long ebase) {
     constexpr int CT = 3;
-    const int j = blockIdx.x;
+    const int j = j0 + blockIdx.x; // sources j0 .. of this index part; its entries start at ebase
     float acc[NC][CT];
 #pragma unroll
     for (int k = 0; k < NC; ++k)
 #pragma unroll
         for (int c = 0; c < CT; ++c) acc[k][c] = 0.f;
-    const long long e0 = src_off[j], e1 = src_off[j + 1];
+    const long long e0 = src_off[j] - ebase, e1 = src_off[j + 1] - ebase;
     for (long long e = e0 + threadIdx.x; e < e1; e += ADJ_THREADS) {
         const int2 ent = __ldg(&tr[e]);
         const float a = __int_as_float(ent.y);
@@ -317,16 +319,19 @@ __global__ void k_finalize(SceneDev sc, int C, const float *__restrict__ u, cons
     }
 }
 
-// transposed index: the records of every ray scattered into per-source lists of (ray, a)
-__global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr) {
+// transposed index: the records of every ray on a source j0 <= j < j1 scattered into
+// per-source lists of (ray, a), stored from entry ebase = src_off[j0] on
+__global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr, int j0, int j1,
+                           long long ebase) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     const long long base = rays.off[r];
     const int c = rays.cnt[r];
     for (int h = 0; h < c; ++h) {
         const int2 ja = rays.rec_ja[base + h];
+        if (ja.x < j0 || ja.x >= j1) continue;
         const unsigned long long pos = atomicAdd(&cursor[ja.x], 1ull);
-        tr[pos] = make_int2(r, ja.y);
+        tr[(long long)pos - ebase] = make_int2(r, ja.y);
     }
 }
 
@@ -335,6 +340,17 @@ __global__ void k_copy_off(const long long *off, unsigned long long *cursor, int
     if (i < n) cursor[i] = (unsigned long long)off[i];
 }
 
+
+// the transposed index of sources j0 .. j1-1 into t->tr (entries from ebase on)
+rgs_status build_index(rgs_transport *t, int j0, int j1, long long ebase, cudaStream_t st) {
+    const int n = t->n;
+    const long long n_rays = (long long)n * t->nd;
+    RaysDev rd = t->rays();
+    { ProfScope ps_("k_copy_off", st); k_copy_off<<<(n + 255) / 256, 256, 0, st>>>(t->src_off, t->cursor, n); }
+    { ProfScope ps_("k_src_fill", st); k_src_fill<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->cursor, t->tr, j0, j1, ebase); }
+    RGS_LAUNCH("transposed index");
+    return RGS_OK;
+}
 
 // g_h (+)= the na iterates of one group, all column tiles; first: the group that writes gh
 template <int NC>
@@ -370,7 +386,8 @@ rgs_status opacity_group(rgs_transport *t, SceneDev sd, RaysDev rd, int na, cons
 // was kept, else one per checkpoint, whose B^(b) and Q^(b) are recomputed from B^(lo) into
 // pooled scratch before the segment's v^(a) are formed and used.
 template <int NC>
-rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, float *dopo, cudaStream_t st) {
+rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, float *dopo,
+                       const std::vector<int> &parts, const std::vector<long long> &part_base, cudaStream_t st) {
     const int n = t->n, C = t->C, nb = t->nb_last, s = t->stride;
     const size_t A = t->arr();
     const size_t A16 = (size_t)n * C * bf16_stride<NC>();
@@ -389,13 +406,25 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     RGS_CUDA(cudaMemsetAsync(t->Pg, 0, sizeof(float) * 12 * (size_t)n, st));
     RGS_CUDA(cudaMemsetAsync(t->dop, 0, sizeof(float) * (size_t)n, st));
     RGS_LAUNCH("adjoint init");
-    auto KT = [&](int a) -> rgs_status { // v^(a) = K^T v^(a-1), u += v^(a)
-        if (mc) return mc_adjoint_bounce<NC>(t, sd, rd, vp(a - 1), vp(a), st);
-        for (int col0 = 0; col0 < C; col0 += 3) {
-            { ProfScope ps_("k_adj_ray", st); k_adj_ray<NC><<<gr, 256, 0, st>>>(sd, rd, C, col0, vp(a - 1), t->dy); }
-            { ProfScope ps_("k_adj_src", st); k_adj_src<NC><<<n, ADJ_THREADS, 0, st>>>(rd, C, col0, t->src_off, t->tr, t->dy, vp(a), t->u); }
+    // v^(a) = K^T v^(a-1), u += v^(a): per part of the transposed index (one part holding
+    // every source unless memory asked for more), per column tile
+    auto KT = [&](int a) -> rgs_status {
+        rgs_status q;
+        for (size_t p = 0; p + 1 < parts.size(); ++p) {
+            const int j0 = parts[p], j1 = parts[p + 1];
+            if (j1 <= j0) continue;
+            const long long eb = part_base[p];
+            if (parts.size() > 2 && (q = build_index(t, j0, j1, eb, st)) != RGS_OK) return q;
+            if (mc) {
+                if ((q = mc_adjoint_bounce<NC>(t, sd, rd, vp(a - 1), vp(a), j0, j1, eb, st)) != RGS_OK) return q;
+                continue;
+            }
+            for (int col0 = 0; col0 < C; col0 += 3) {
+                { ProfScope ps_("k_adj_ray", st); k_adj_ray<NC><<<gr, 256, 0, st>>>(sd, rd, C, col0, vp(a - 1), t->dy); }
+                { ProfScope ps_("k_adj_src", st); k_adj_src<NC><<<j1 - j0, ADJ_THREADS, 0, st>>>(rd, C, col0, t->src_off, t->tr, t->dy, vp(a), t->u, j0, eb); }
+            }
+            RGS_LAUNCH("adjoint bounce");
         }
-        RGS_LAUNCH("adjoint bounce");
         return RGS_OK;
     };
     // segment scratch (checkpointing): B^(lo+1 .. lo+s) FP32 (+BF16) and Q^(lo .. lo+s-1)
@@ -489,13 +518,13 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
 
 rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st) {
     rgs_status r;
-    const int nb = t->nb_last;
+    const int nb = t->nb_last, n = t->n;
     const size_t A = t->arr();
-    const long long n_rays = (long long)t->n * t->nd;
-    if (t->n > t->pg_cap) {
-        if ((r = dev_alloc(&t->Pg, (size_t)t->n * 12, &t->device_bytes)) != RGS_OK) return r;
-        if ((r = dev_alloc(&t->dop, (size_t)t->n, &t->device_bytes)) != RGS_OK) return r;
-        t->pg_cap = t->n;
+    const long long n_rays = (long long)n * t->nd;
+    if (n > t->pg_cap) {
+        if ((r = dev_alloc(&t->Pg, (size_t)n * 12, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->dop, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
+        t->pg_cap = n;
     }
     // Workspaces that live only inside this call come from the stream-ordered pool and are
     // returned to it on every exit path: v^(0..n), u, the transposed index, the per-ray
@@ -513,26 +542,55 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
         }
     } scratch{t, st};
     const bool mc = wide_adjoint(t->C);
-    if ((r = pool_alloc(&t->v, A * (t->stride ? t->stride + 1 : nb + 1), st)) != RGS_OK) return r;
+    const bool want_gh = dop && nb >= 1;
+    const int n_v = t->stride ? t->stride + 1 : nb + 1;
+    if ((r = pool_alloc(&t->v, A * n_v, st)) != RGS_OK) return r;
     if ((r = pool_alloc(&t->u, A, st)) != RGS_OK) return r;
-    if ((r = pool_alloc(&t->tr, (size_t)t->n_hits, st)) != RGS_OK) return r;
     if (mc) {
         if ((r = pool_alloc(&t->dy_mc, (size_t)n_rays * 32, st)) != RGS_OK) return r;
     } else {
         if ((r = pool_alloc(&t->dy, (size_t)n_rays, st)) != RGS_OK) return r;
     }
-    if (dop && nb >= 1 && (r = pool_alloc(&t->gh, (size_t)t->n_slots, st)) != RGS_OK) return r;
-    {
-        const int n = t->n;
-        RaysDev rd = t->rays();
-        { ProfScope ps_("k_copy_off", st); k_copy_off<<<(n + 255) / 256, 256, 0, st>>>(t->src_off, t->cursor, n); }
-        { ProfScope ps_("k_src_fill", st); k_src_fill<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->cursor, t->tr); }
-        RGS_LAUNCH("transposed index");
+    if (want_gh && (r = pool_alloc(&t->gh, (size_t)t->n_slots, st)) != RGS_OK) return r;
+    // The transposed index in one part when it fits next to the segment scratch of a
+    // checkpointed adjoint, else in P parts of about equal entry counts, each rebuilt from
+    // the records for every transposed bounce.
+    const double A16 = t->prec_last != RGS_FP32 ? 2.0 * n * t->C * (t->nc >= 9 ? 16 : t->nc) : 0.0;
+    const double seg = t->stride ? t->stride * (8.0 * A + A16) + 8.0 * (RGS_MAX_BOUNCES + 1) : 0.0;
+    const double tr_all = 8.0 * (double)t->n_hits;
+    double avail = 0.92 * (double)pool_available_bytes() - seg;
+    if (t->mem_budget > 0) {
+        const double scratch = 4.0 * A * (n_v + 1) + (mc ? 128.0 : 16.0) * n_rays + (want_gh ? 4.0 * t->n_slots : 0.0);
+        avail = std::min(avail, (double)t->mem_budget - (double)t->device_bytes - scratch - seg);
     }
+    int P = 1;
+    while (P < 64 && tr_all / P > avail) P *= 2;
+    std::vector<int> parts{0};
+    std::vector<long long> base{0};
+    if (P > 1) {
+        std::vector<long long> off((size_t)n + 1);
+        RGS_CUDA(cudaMemcpyAsync(off.data(), t->src_off, sizeof(long long) * (n + 1), cudaMemcpyDeviceToHost, st));
+        RGS_CUDA(cudaStreamSynchronize(st));
+        int j = 0;
+        for (int p = 1; p < P; ++p) {
+            const long long target = (long long)((double)t->n_hits * p / P);
+            while (j < n && off[j] < target) ++j;
+            parts.push_back(j);
+            base.push_back(off[j]);
+        }
+    }
+    parts.push_back(n);
+    long long biggest = 0;
+    for (size_t p = 0; p + 1 < parts.size(); ++p) {
+        const long long e1 = p + 2 < parts.size() ? base[p + 1] : t->n_hits;
+        biggest = std::max(biggest, e1 - base[p]);
+    }
+    if ((r = pool_alloc(&t->tr, (size_t)std::max(biggest, 1ll), st)) != RGS_OK) return r;
+    if (parts.size() == 2 && (r = build_index(t, 0, n, 0, st)) != RGS_OK) return r;
     switch (t->nc) {
-    case 1: return run_adjoint<1>(t, g, dE, dad, dop, st);
-    case 4: return run_adjoint<4>(t, g, dE, dad, dop, st);
-    case 9: return run_adjoint<9>(t, g, dE, dad, dop, st);
-    default: return run_adjoint<16>(t, g, dE, dad, dop, st);
+    case 1: return run_adjoint<1>(t, g, dE, dad, dop, parts, base, st);
+    case 4: return run_adjoint<4>(t, g, dE, dad, dop, parts, base, st);
+    case 9: return run_adjoint<9>(t, g, dE, dad, dop, parts, base, st);
+    default: return run_adjoint<16>(t, g, dE, dad, dop, parts, base, st);
     }
 }

@@ -96,6 +96,23 @@ rgs_status pool_alloc_bytes(void **p, size_t bytes, cudaStream_t st) {
     return RGS_OK;
 }
 
+size_t pool_available_bytes() {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaMemPool_t pool = nullptr;
+    if (device_pool(&pool) != RGS_OK) return free_b;
+    unsigned long long reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+        cudaGetLastError();
+        return free_b;
+    }
+    return free_b + (size_t)(reserved > used ? reserved - used : 0);
+}
+
 void pool_free(void *p, cudaStream_t st) {
     if (p && cudaFreeAsync(p, st) != cudaSuccess) cudaGetLastError();
 }
@@ -390,6 +407,15 @@ rgs_status rgs_set_checkpointing(rgs_transport *t, int32_t stride) {
         return RGS_ERR_ARG;
     }
     t->ckpt_req = stride;
+    return RGS_OK;
+}
+
+rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes) {
+    if (!t || bytes < 0) {
+        rgs_set_error("rgs_set_memory_budget: NULL transport or negative budget");
+        return RGS_ERR_ARG;
+    }
+    t->mem_budget = bytes;
     return RGS_OK;
 }
 

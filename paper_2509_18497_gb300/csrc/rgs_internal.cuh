@@ -450,7 +450,7 @@ struct rgs_transport {
     long long *src_off = nullptr;
     int *src_cnt = nullptr;
     unsigned long long *cursor = nullptr;
-    int2 *tr = nullptr; // (ray id, bits of a)
+    int2 *tr = nullptr; // (ray id, bits of a), for the sources of the current index part
     int src_cap = 0;      // surfels allocated in src_off / src_cnt / cursor
     long long *scan_tmp = nullptr;
     int scan_tmp_cap = 0;
@@ -463,6 +463,7 @@ struct rgs_transport {
     // of b, and Q one scratch array; the adjoint recomputes the rest from the checkpoints.
     int nb_last = -1;
     int ckpt_req = 0;   // rgs_set_checkpointing: 0 store all, s >= 1 every s-th, -1 automatic
+    long long mem_budget = 0; // rgs_set_memory_budget: bytes this transport may hold with its scratch (0: none)
     int stride = 0;     // checkpoint stride of the last solve
     int n_ckpt = 0;     // checkpoints stored by the last solve
     int iters_cap = 0;  // number of [N][C][NC] arrays allocated in iters
@@ -563,6 +564,8 @@ template <class T> void dev_free(T *&p) {
 // workspaces that live only inside one call (adjoint), so that transports that run one
 // after another on a stream share the same memory.
 rgs_status pool_alloc_bytes(void **p, size_t bytes, cudaStream_t st);
+// device memory a pool allocation could get now: free memory plus what the pool holds unused
+size_t pool_available_bytes();
 void pool_free(void *p, cudaStream_t st);
 template <class T> rgs_status pool_alloc(T **p, size_t count, cudaStream_t st) {
     *p = nullptr;
@@ -588,8 +591,10 @@ template <int NC>
 rgs_status mc_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, bool rows16, const float *Bprev,
                      const __nv_bfloat16 *Bprev16, const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16,
                      double *norm2, cudaStream_t st);
+// K^T for the sources j0 .. j1-1, whose transposed entries start at ebase in t->tr
 template <int NC>
-rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const float *vin, float *vout, cudaStream_t st);
+rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const float *vin, float *vout, int j0, int j1,
+                             long long ebase, cudaStream_t st);
 // per-launch set of up to NA adjoint iterates v^(a) and the matching B^(n-1-a) (FP32 or BF16)
 template <class T, int NA> struct OpaSet {
     const float *v[NA];

@@ -59,13 +59,14 @@ template <int NC>
 __global__ void __launch_bounds__(MC_THREADS) k_adj_src_mc(RaysDev rays, int C, int ct,
                                                           const long long *__restrict__ src_off,
                                                           const int2 *__restrict__ tr, const float *__restrict__ dy,
-                                                          float *__restrict__ vout, float *__restrict__ u) {
-    const int j = blockIdx.x;
+                                                          float *__restrict__ vout, float *__restrict__ u, int j0,
+                                                          long long ebase) {
+    const int j = j0 + blockIdx.x; // sources j0 .. of this index part; its entries start at ebase
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float acc[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) acc[k] = 0.f;
-    const long long e0 = src_off[j], e1 = src_off[j + 1];
+    const long long e0 = src_off[j] - ebase, e1 = src_off[j + 1] - ebase;
     for (long long e = e0 + warp; e < e1; e += MC_WARPS) {
         const int2 ent = __ldg(&tr[e]);
         const float4 d4 = __ldg(&rays.dir[ent.x]);
@@ -170,11 +171,11 @@ rgs_status mc_bounce(const rgs_transport *t, SceneDev sd, RaysDev rd, bool rows1
 }
 
 template <int NC>
-rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const float *vin, float *vout,
-                             cudaStream_t st) {
+rgs_status mc_adjoint_bounce(rgs_transport *t, SceneDev sd, RaysDev rd, const float *vin, float *vout, int j0, int j1,
+                             long long ebase, cudaStream_t st) {
     for (int ct = 0; ct * 32 < t->C; ++ct) {
         { ProfScope ps_("k_adj_ray_mc", st); k_adj_ray_mc<NC><<<t->n, MC_THREADS, 0, st>>>(sd, rd, t->C, ct, vin, t->dy_mc); }
-        { ProfScope ps_("k_adj_src_mc", st); k_adj_src_mc<NC><<<t->n, MC_THREADS, 0, st>>>(rd, t->C, ct, t->src_off, t->tr, t->dy_mc, vout, t->u); }
+        { ProfScope ps_("k_adj_src_mc", st); k_adj_src_mc<NC><<<j1 - j0, MC_THREADS, 0, st>>>(rd, t->C, ct, t->src_off, t->tr, t->dy_mc, vout, t->u, j0, ebase); }
     }
     RGS_LAUNCH("adjoint bounce mc");
     return RGS_OK;
@@ -210,8 +211,8 @@ rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int na, const f
     template rgs_status mc_bounce<NC>(const rgs_transport *, SceneDev, RaysDev, bool, const float *,                   \
                                       const __nv_bfloat16 *, const float *, float *, float *, __nv_bfloat16 *,         \
                                       double *, cudaStream_t);                                                         \
-    template rgs_status mc_adjoint_bounce<NC>(rgs_transport *, SceneDev, RaysDev, const float *, float *,              \
-                                              cudaStream_t);                                                           \
+    template rgs_status mc_adjoint_bounce<NC>(rgs_transport *, SceneDev, RaysDev, const float *, float *, int, int,    \
+                                              long long, cudaStream_t);                                                \
     template rgs_status mc_opacity<NC>(rgs_transport *, SceneDev, RaysDev, int, const float *const *,                 \
                                        const float *const *, const __nv_bfloat16 *const *, bool, cudaStream_t);
 RGS_MC_INSTANTIATE(1)

@@ -5,6 +5,7 @@
 // gathers the stored hits' radiance x_r[c] = sum_h a_rh Y(-d_r) . B_{j_h}[c]; the CTA then
 // projects Q_i[c][k] = (pi/nd) sum_r Y_k(R_i d_r) x_r[c] and writes Q^(k-1),
 // B^(k) = S + o_i c_i (x) Q and the FP64 partial sum of (B^(k) - B^(k-1))^2.
+#include <algorithm>
 #include <vector>
 
 #include "rgs_bounce_body.cuh"
@@ -141,13 +142,10 @@ int rgs_auto_stride(const rgs_transport *t, int nb, int precision) {
     const double rays = (double)t->n * t->nd;
     const double fwd = (nb + 1) * (A + A16) + nb * A;
     const double adj = (nb + 2) * A + 8.0 * t->n_hits + 4.0 * t->n_slots + rays * (wide_adjoint(t->C) ? 128 : 16);
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
     const double held = t->iters_cap * A + t->q_cap * A + t->iters16_cap * A16;
-    if (fwd + adj <= 0.95 * ((double)free_b + held)) return 0;
+    double room = 0.95 * ((double)pool_available_bytes() + held);
+    if (t->mem_budget > 0) room = std::min(room, (double)t->mem_budget - ((double)t->device_bytes - held));
+    if (fwd + adj <= room) return 0;
     int s = 1;
     while (s * s < nb) ++s;
     return s;

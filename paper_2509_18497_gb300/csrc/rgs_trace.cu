@@ -225,6 +225,14 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
     }
 
     long long want = o->hit_capacity > 0 ? o->hit_capacity : (t->cap_slots > 0 ? t->cap_slots : n_rays * 24);
+    if (o->hit_capacity <= 0 && t->cap_slots == 0) {
+        // first trace of a large transport: rather than reserve a guess of 24 slots per ray,
+        // let the first pass only count (no slots: every warp's store is refused, the
+        // counter still adds up) and reserve what it needs
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+        if ((double)want * sizeof(int2) > 0.25 * (double)free_b) want = 0;
+    }
     SceneDev sd = sc->dev();
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (want > t->cap_slots) {
@@ -254,7 +262,8 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
             rgs_set_error("hit-record capacity %lld slots too small (%llu needed)", t->cap_slots, used);
             return RGS_ERR_CAPACITY;
         }
-        want = (long long)(used + used / 8 + 1024);
+        const unsigned long long slack = used > (1ull << 30) ? used / 32 : used / 8; // for later re-traces
+        want = (long long)(used + slack + 1024);
     }
 
     // direct term

@@ -29,7 +29,7 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_transport_info_get", "rgs_destroy_transport", "rgs_destroy_scene", "rgs_profile_enable",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
-           "rgs_set_checkpointing", "rgs_trim_workspace")
+           "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget")
 
 
 class RgsError(RuntimeError):
@@ -116,6 +116,8 @@ def load(path=LIB_PATH):
     L.rgs_residual_norm_noalloc.restype = ct.c_int
     L.rgs_set_checkpointing.argtypes = [vp, ct.c_int32]
     L.rgs_set_checkpointing.restype = ct.c_int
+    L.rgs_set_memory_budget.argtypes = [vp, ct.c_int64]
+    L.rgs_set_memory_budget.restype = ct.c_int
     L.rgs_trim_workspace.argtypes = []
     L.rgs_trim_workspace.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
@@ -269,6 +271,12 @@ def rgs_set_checkpointing(transport, stride):
     """0: keep every iterate; s >= 1: keep B^(0), B^(s), ... and recompute in the adjoint;
     -1: automatic (checkpoint only when the full storage does not fit)."""
     _check(load().rgs_set_checkpointing(transport.h, int(stride)))
+
+
+def rgs_set_memory_budget(transport, nbytes):
+    """Bytes the transport may hold with its pooled scratch (0: no budget); steers the
+    automatic checkpoint stride and the number of transposed-index parts of the adjoint."""
+    _check(load().rgs_set_memory_budget(transport.h, int(nbytes)))
 
 
 def rgs_trim_workspace():
