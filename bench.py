@@ -255,6 +255,8 @@ def main():
                     help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights; "
                          "uneven: 32 scenes of uneven size in one persistent launch; large: 1,000,000 surfels, "
                          "512 rays, 6 bounces, 16 lights, checkpointed iterates")
+    ap.add_argument("--scenes", type=int, default=32, help="uneven workload: number of scenes (profiling cases)")
+    ap.add_argument("--scale", type=float, default=1.0, help="uneven workload: surfel-count factor (profiling cases)")
     ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1500, help="surfels per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -281,8 +283,10 @@ def main():
         scs = [scenes.multi_light(n=200000 if args.n == 50000 else args.n)]
         workload = MULTI_WORKLOAD
     elif args.workload == "uneven":
-        scs = scenes.uneven_batch(32)
+        scs = scenes.uneven_batch(args.scenes, scale=args.scale)
         workload = UNEVEN_WORKLOAD
+        if args.scenes != 32 or args.scale != 1.0:
+            workload = f"reduced uneven batch ({args.scenes} scenes, counts x{args.scale}) of: " + workload
     elif args.workload == "large":
         scs = [scenes.large_scene(n=1000000 if args.n == 50000 else args.n)]
         workload = LARGE_WORKLOAD
@@ -453,6 +457,7 @@ def main():
     else:
         config = {"workload": workload, "scenes": len(scs), "n_surfels_total": sum(x["n"] for x in scs),
                   "rays_total": sum(x["n"] * x["nd"] for x in scs), "lights_per_scene": 8,
+                  "surfels_per_scene": [x["n"] for x in scs],
                   "hit_records": sum(x["n_hits"] for x in infos), "units_per_step": units_per_step}
     config["transport_device_bytes"] = sum(x["device_bytes"] for x in infos)
     config.update({"precision": headline, "l2": "flushed between steps (512 MiB write)",

@@ -19,6 +19,7 @@
 namespace {
 
 constexpr int ADJ_THREADS = 128;
+static_assert(ADJ_THREADS == 128, "RGS_ADJ_LB assumes 128 threads");
 
 // user [N][nc][C] -> internal [N][C][NC]
 template <int NC>
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(256) k_adj_ray(SceneDev sc, RaysDev rays, int 
 
 // (K^T v)_j[c][k] = sum_{entries e on j} a_e Y_k(-d_e) y_e[c]; one CTA per source j.
 template <int NC>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_src(RaysDev rays, int C, int col0, const long long *__restrict__ src_off,
+__global__ void RGS_ADJ_LB k_adj_src(RaysDev rays, int C, int col0, const long long *__restrict__ src_off,
                                                         const int2 *__restrict__ tr, const float4 *__restrict__ dy,
                                                         float *__restrict__ vout, float *__restrict__ u, int j0,
                                                         long long ebase) {
@@ -187,7 +188,7 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, const float *__restrict__ lpos
 //   y_r^(a)[c] = (pi/nd) o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) v_i^(a)[c][k'],
 // accumulated into gh[slot] for iterates a0 .. a0+na-1 (first chunk writes, later add).
 template <int NC, int CT, int NA, class SLB>
-__global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, int C, int col0, int na,
+__global__ void RGS_OPA_LB k_opacity_g(SceneDev sc, RaysDev rays, int C, int col0, int na,
                                                    OpaSet<typename SLB::T, NA> it, float *gh, bool first) {
     using SL = Slice<NC>;
     constexpr int G = SL::G, KPL = SL::KPL;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256) k_opacity_g(SceneDev sc, RaysDev rays, in
 // Hemisphere rays, part 2: back to front, R_{h-1} = alpha_h g_h + (1 - alpha_h) R_h and
 // dL/do_{j_h} += T_h (g_h - R_h) G_h, with T_h the transmittance in front of hit h.
 // G_h is recomputed from the stored direction (bit-identical to the trace's value).
-__global__ void __launch_bounds__(256) k_opacity_rec(SceneDev sc, RaysDev rays, const float *__restrict__ gh,
+__global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const float *__restrict__ gh,
                                                      float *dop) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= sc.n * rays.nd) return;

@@ -11,6 +11,7 @@
 constexpr int MC_WARPS = 8;
 constexpr int MC_THREADS = MC_WARPS * 32;
 static_assert(MC_THREADS == BOUNCE_THREADS, "the batch kernel runs both bodies in one block");
+static_assert(BOUNCE_THREADS == 256, "RGS_BOUNCE_LB and RGS_MC_LB assume 256 threads");
 
 // the NC coefficients of one column of a row (FP32 rows of NC floats, BF16 rows padded)
 template <int NC> __device__ __forceinline__ void load_col(const float *__restrict__ p, float *v) {

@@ -19,6 +19,47 @@
 #define RGS_T_EPS 1e-6f       // compositing stops once the transmittance is below this
 #define RGS_STACK 64          // BVH traversal stack depth (tree depth is bounded by 32 + log2 N)
 
+// Launch bounds of the gather kernels: with RGS_<KERNEL>_MINB defined, the register budget
+// is sized for that many resident blocks per SM (these latency-bound kernels gain from more
+// resident warps as long as nothing spills); undefined, the compiler's default budget.
+// Build-time knobs, set from measurements on GB300 (50,000-surfel bowl, 1 and 16 lights):
+// 5 blocks for the 3-column bounce (-9 %, despite a few spilled registers) and 4 for the
+// lane-per-column bounce (-18 %); the opacity and adjoint gathers keep the default (tighter
+// budgets measured slower).
+#define RGS_LB_(threads, minb) __launch_bounds__(threads, minb)
+#ifndef RGS_BOUNCE_MINB
+#define RGS_BOUNCE_MINB 5
+#endif
+#ifndef RGS_MCB_MINB
+#define RGS_MCB_MINB 4
+#endif
+#define RGS_MCB_LB RGS_LB_(256, RGS_MCB_MINB)
+#ifdef RGS_BOUNCE_MINB
+#define RGS_BOUNCE_LB RGS_LB_(256, RGS_BOUNCE_MINB)
+#else
+#define RGS_BOUNCE_LB __launch_bounds__(256)
+#endif
+#ifdef RGS_OPA_MINB
+#define RGS_OPA_LB RGS_LB_(256, RGS_OPA_MINB)
+#else
+#define RGS_OPA_LB __launch_bounds__(256)
+#endif
+#ifdef RGS_OPAREC_MINB
+#define RGS_OPAREC_LB RGS_LB_(256, RGS_OPAREC_MINB)
+#else
+#define RGS_OPAREC_LB __launch_bounds__(256)
+#endif
+#ifdef RGS_ADJ_MINB
+#define RGS_ADJ_LB RGS_LB_(128, RGS_ADJ_MINB)
+#else
+#define RGS_ADJ_LB __launch_bounds__(128)
+#endif
+#ifdef RGS_MC_MINB
+#define RGS_MC_LB RGS_LB_(256, RGS_MC_MINB)
+#else
+#define RGS_MC_LB __launch_bounds__(256)
+#endif
+
 // ------------------------------------------------------------------ error flags
 enum {
     FLAG_CAPACITY = 0,  // hit-record slots exhausted (warps that could not store)

@@ -13,7 +13,7 @@ namespace {
 
 // ------------------------------------------------------------------ forward bounce
 template <int NC, class T>
-__global__ void __launch_bounds__(MC_THREADS) k_bounce_mc(SceneDev sc, RaysDev rays, int C, const T *__restrict__ Bg,
+__global__ void RGS_MCB_LB k_bounce_mc(SceneDev sc, RaysDev rays, int C, const T *__restrict__ Bg,
                                                          const float *__restrict__ Bprev, const float *__restrict__ S,
                                                          float *__restrict__ Qout, float *__restrict__ Bout,
                                                          __nv_bfloat16 *__restrict__ Bout16, double *norm2) {
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(MC_THREADS) k_adj_ray_mc(SceneDev sc, RaysDev 
 
 // (K^T v)_j[c][k] = sum_{entries e on j} a_e Y_k(-d_e) y_e[c], one CTA per source j
 template <int NC>
-__global__ void __launch_bounds__(MC_THREADS) k_adj_src_mc(RaysDev rays, int C, int ct,
+__global__ void RGS_MC_LB k_adj_src_mc(RaysDev rays, int C, int ct,
                                                           const long long *__restrict__ src_off,
                                                           const int2 *__restrict__ tr, const float *__restrict__ dy,
                                                           float *__restrict__ vout, float *__restrict__ u, int j0,
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(MC_THREADS) k_adj_src_mc(RaysDev rays, int C, 
 // opacity backward: per hit g_h (partial over this column tile and iterate chunk)
 // accumulated into gh[slot]; a warp per ray, lanes over columns
 template <int NC, int NA, class T>
-__global__ void __launch_bounds__(MC_THREADS) k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int ct, int na,
+__global__ void RGS_MC_LB k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int ct, int na,
                                                             OpaSet<T, NA> it, float *gh, bool first) {
     constexpr int RS = row_stride<NC, T>();
     const int warp_g = (int)((blockIdx.x * (size_t)MC_THREADS + threadIdx.x) >> 5);

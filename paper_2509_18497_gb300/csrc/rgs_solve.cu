@@ -43,7 +43,7 @@ __global__ void k_to_user(int n, int C, const int *__restrict__ uid, const float
 }
 
 template <int NC, int CT, class SL>
-__global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(SceneDev sc, RaysDev rays, int C,
+__global__ void RGS_BOUNCE_LB k_bounce(SceneDev sc, RaysDev rays, int C,
                                                           const typename SL::T *__restrict__ Bg,
                                                           const float *__restrict__ Bprev, const float *__restrict__ S,
                                                           float *__restrict__ Qout, float *__restrict__ Bout,

@@ -12,6 +12,13 @@
 
 #include "rgs_internal.cuh"
 
+#ifndef RGS_TRACE_PATCH_A
+#define RGS_TRACE_PATCH_A 8
+#endif
+#ifndef RGS_TRACE_MINB
+#define RGS_TRACE_MINB 12 // resident 128-thread blocks per SM the register budget is sized for (measured best)
+#endif
+
 namespace {
 
 // One thread per hemisphere ray; the 32 rays of a warp belong to one surfel.
@@ -20,15 +27,24 @@ namespace {
 // (such ties are always re-ordered inside their run).  After compositing, the warp
 // allocates exactly its rays' kept hits with one atomic (prefix sum over the lanes) and
 // every ray stores its records contiguously.
-__global__ void __launch_bounds__(128, 4) k_trace_hemi(SceneDev sc, RaysDev rays, int n_rays, long long cap_slots,
+__global__ void __launch_bounds__(128, RGS_TRACE_MINB) k_trace_hemi(SceneDev sc, RaysDev rays, int n_rays, long long cap_slots,
                                                        unsigned long long *slot_ctr, int2 *rec_ja,
                                                        long long *off_out, int *cnt_out, float4 *dir_out,
-                                                       int *src_cnt, int *flags) {
+                                                       int *src_cnt, int *flags, int pa) {
     const unsigned FULL = 0xffffffffu;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps only (n_rays % 32 == 0)
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps only (n_rays % 32 == 0)
     const int lane = threadIdx.x & 31;
-    const int i = r / rays.nd, q = r - i * rays.nd;
+    // the warps of surfel i take patches of pa x (32 / pa) strata (elevation x azimuth) of its
+    // na x nbs grid, so that a warp's rays leave in similar directions; pa = 0: 32 consecutive rays
+    const int i = tid / rays.nd;
+    int q = tid - i * rays.nd;
+    if (pa > 0) {
+        const int pb = 32 / pa, w = q >> 5, per_row = rays.nbs / pb;
+        const int a = (w / per_row) * pa + lane / pb, b = (w % per_row) * pb + lane % pb;
+        q = a * rays.nbs + b;
+    }
+    const int r = i * rays.nd + q; // the ray this thread traces (outputs are indexed by ray)
     const float3 o = f3(sc.P[i]);
     const float3 d = ray_dir(rays.seed, sc.uid[i], q, rays.na, rays.nbs, f3(sc.FU[i]), f3(sc.FV[i]), f3(sc.N4[i]));
     dir_out[r] = make_float4(d.x, d.y, d.z, 0.f);
@@ -234,6 +250,11 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         if ((double)want * sizeof(int2) > 0.25 * (double)free_b) want = 0;
     }
     SceneDev sd = sc->dev();
+    // warp patch of the strata grid: the largest pa <= RGS_TRACE_PATCH_A dividing na with
+    // 32 / pa dividing nbs; none (0) keeps 32 consecutive rays per warp
+    int pa = 0;
+    for (int c = RGS_TRACE_PATCH_A; c >= 1 && !pa; c >>= 1)
+        if (t->na % c == 0 && 32 % c == 0 && t->nbs % (32 / c) == 0) pa = c;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (want > t->cap_slots) {
             if ((r = dev_alloc(&t->rec_ja, (size_t)want, &t->device_bytes)) != RGS_OK) return r;
@@ -244,7 +265,7 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
         RaysDev rd = t->rays();
         const int TB = 128;
-        { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter, t->rec_ja, t->off, t->cnt, t->dir, t->src_cnt, t->flags); }
+        { ProfScope ps_("k_trace_hemi", st); k_trace_hemi<<<(unsigned)((n_rays + TB - 1) / TB), TB, 0, st>>>(sd, rd, (int)n_rays, t->cap_slots, t->counter, t->rec_ja, t->off, t->cnt, t->dir, t->src_cnt, t->flags, pa); }
         RGS_LAUNCH("trace_hemi");
         unsigned long long used = 0;
         int flags[FLAG_COUNT];

@@ -258,13 +258,14 @@ def multi_light(n=200000, seed=0, n_lights=100, L=3, nd=256, nb=4):
     return fruit_bowl(n=n, seed=seed, L=L, nd=nd, nb=nb, n_lights=n_lights)
 
 
-def uneven_batch(count=32, base_seed=1000, n_lights=8):
-    """Independent fruit-bowl scenes with log-uniform surfel counts in [5e3, 3e5],
-    SH degree 2 or 3, 128/192/256 rays per surfel and 3-5 bounces."""
+def uneven_batch(count=32, base_seed=1000, n_lights=8, scale=1.0):
+    """Independent fruit-bowl scenes with log-uniform surfel counts in [5e3, 3e5] (times
+    `scale`, for reduced profiling cases), SH degree 2 or 3, 128/192/256 rays per surfel and
+    3-5 bounces."""
     out = []
     for s in range(count):
         rng = np.random.default_rng(base_seed + s)
-        ns = int(round(math.exp(rng.uniform(math.log(5e3), math.log(3e5)))))
+        ns = int(round(math.exp(rng.uniform(math.log(5e3), math.log(3e5))) * scale))
         L = int(rng.choice([2, 3]))
         nd = int(rng.choice([128, 192, 256]))
         nb = int(rng.choice([3, 4, 5]))
