@@ -64,7 +64,7 @@ def _src_sha(name):
 # DRAM bytes per launch from one ncu capture (profiles/), keyed by kernel; valid only
 # while the kernel's source file is unchanged since the capture.
 NCU_TRAFFIC = {
-    "k_trace_hemi": {"bytes_per_launch": 0.834729e9 + 2.153428e9, "n": 10000, "src_sha": "35405e494984794e"},
+    "k_trace_hemi": {"bytes_per_launch": 0.986917e9 + 2.053628e9, "n": 10000, "src_sha": "5509d3f1294b98a4"},
 }
 
 
