@@ -143,6 +143,15 @@ typedef struct {
     int *sh_j;
     double *sh_alpha, *sh_G;
     double *sh_pre; /* [n*nl] = Y-free prefactor I*cos/r^2 (0 if back-facing) */
+    /* center-to-center transport (pmode = 1): per receiver i the pairs (i, j) */
+    int pmode;
+    double *lam;                  /* [n] lambda_j */
+    long *pair_off;               /* [n+1] */
+    int *pair_j;
+    double *pair_V, *pair_T, *pair_geo; /* V_ji, T_ij, |n_i.w||n_j.w|/r^2 */
+    long *poc_off;                /* [npairs+1] occluders of each pair's segment */
+    int *poc_j;
+    double *poc_alpha, *poc_G;
 } or_scene;
 
 static double *dup_arr(const double *src, size_t cnt) {
@@ -301,6 +310,24 @@ static void free_transport(or_scene *s) {
     s->sh_off = NULL;
     s->sh_j = NULL;
     s->sh_alpha = s->sh_G = s->sh_pre = NULL;
+    free(s->lam);
+    free(s->pair_off);
+    free(s->pair_j);
+    free(s->pair_V);
+    free(s->pair_T);
+    free(s->pair_geo);
+    free(s->poc_off);
+    free(s->poc_j);
+    free(s->poc_alpha);
+    free(s->poc_G);
+    s->lam = NULL;
+    s->pair_off = NULL;
+    s->pair_j = NULL;
+    s->pair_V = s->pair_T = s->pair_geo = NULL;
+    s->poc_off = NULL;
+    s->poc_j = NULL;
+    s->poc_alpha = s->poc_G = NULL;
+    s->pmode = 0;
 }
 
 void or_scene_free(or_scene *s) {
@@ -503,53 +530,10 @@ static void reflect(const double *n, const double *d, double *r) { /* R d = 2 (n
     for (int q = 0; q < 3; ++q) r[q] = 2.0 * nd * n[q] - d[q];
 }
 
-/* Traces every surfel's Nd hemisphere rays (App. B, Eq. L_I) and the N x NL shadow
- * rays of the direct term (Sec. 5.2), and stores per-ray hit records in compositing
- * order with their weights a_h = alpha_h * prod_{k<h} (1 - alpha_k). */
-int or_transport(or_scene *s, int nd, uint64_t seed, int nl, const double *lp, const double *li) {
-    free_transport(s);
-    int n = s->n, nc = s->nc, L = s->L;
-    s->nd = nd;
-    s->seed = seed;
-    s->nl = nl;
-    s->C = 3 * (nl > 0 ? nl : 1); /* one right-hand side per light; emission only: one */
-    int C = s->C;
-    s->lp = dup_arr(lp, 3 * (size_t)nl);
-    s->li = dup_arr(li, 3 * (size_t)nl);
-    s->nrays = (long)n * nd;
-    hitvec *per = (hitvec *)calloc((size_t)(s->nrays ? s->nrays : 1), sizeof(hitvec));
-#pragma omp parallel for schedule(dynamic, 4)
-    for (int i = 0; i < n; ++i) {
-        for (int r = 0; r < nd; ++r) {
-            double d[3];
-            or_ray_dir(s, i, nd, seed, r, d);
-            trace_all(s, i, s->p + i * 3, d, INFINITY, &per[(long)i * nd + r]);
-        }
-    }
-    s->ray_off = (long *)malloc(sizeof(long) * (s->nrays + 1));
-    s->ray_off[0] = 0;
-    for (long r = 0; r < s->nrays; ++r) s->ray_off[r + 1] = s->ray_off[r] + per[r].cnt;
-    long H = s->ray_off[s->nrays];
-    s->hit_j = (int *)malloc(sizeof(int) * (H ? H : 1));
-    s->hit_alpha = dup_arr(NULL, H);
-    s->hit_G = dup_arr(NULL, H);
-    s->hit_a = dup_arr(NULL, H);
-    s->hit_t = dup_arr(NULL, H);
-    for (long r = 0; r < s->nrays; ++r) {
-        double T = 1.0;
-        for (int q = 0; q < per[r].cnt; ++q) {
-            long e = s->ray_off[r] + q;
-            s->hit_j[e] = per[r].h[q].j;
-            s->hit_t[e] = per[r].h[q].t;
-            s->hit_alpha[e] = per[r].h[q].alpha;
-            s->hit_G[e] = per[r].h[q].G;
-            s->hit_a[e] = per[r].h[q].alpha * T;
-            T *= (1.0 - per[r].h[q].alpha);
-        }
-        free(per[r].h);
-    }
-    free(per);
-
+/* Direct term (Sec. 5.2) of every receiver: Dgeo (the direct term without the o_i c_i
+ * factor) and the shadow-ray hit lists kept for the opacity backward. */
+static void direct_term(or_scene *s, int nl, const double *lp, const double *li) {
+    int n = s->n, nc = s->nc, L = s->L, C = s->C;
     /* Direct term (Sec. 5.2): lights are infinitesimal emissive surfels sampled at their
      * centre, with the light's normal factor dropped (Sec. 5.3); Y^T E_light = I. */
     s->Dgeo = dup_arr(NULL, (size_t)n * nc * C);
@@ -597,6 +581,55 @@ int or_transport(or_scene *s, int nd, uint64_t seed, int nl, const double *lp, c
         free(sper[q].h);
     }
     free(sper);
+}
+
+/* Traces every surfel's Nd hemisphere rays (App. B, Eq. L_I) and the N x NL shadow
+ * rays of the direct term (Sec. 5.2), and stores per-ray hit records in compositing
+ * order with their weights a_h = alpha_h * prod_{k<h} (1 - alpha_k). */
+int or_transport(or_scene *s, int nd, uint64_t seed, int nl, const double *lp, const double *li) {
+    free_transport(s);
+    int n = s->n;
+    s->nd = nd;
+    s->seed = seed;
+    s->nl = nl;
+    s->C = 3 * (nl > 0 ? nl : 1); /* one right-hand side per light; emission only: one */
+    s->lp = dup_arr(lp, 3 * (size_t)nl);
+    s->li = dup_arr(li, 3 * (size_t)nl);
+    s->nrays = (long)n * nd;
+    hitvec *per = (hitvec *)calloc((size_t)(s->nrays ? s->nrays : 1), sizeof(hitvec));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i) {
+        for (int r = 0; r < nd; ++r) {
+            double d[3];
+            or_ray_dir(s, i, nd, seed, r, d);
+            trace_all(s, i, s->p + i * 3, d, INFINITY, &per[(long)i * nd + r]);
+        }
+    }
+    s->ray_off = (long *)malloc(sizeof(long) * (s->nrays + 1));
+    s->ray_off[0] = 0;
+    for (long r = 0; r < s->nrays; ++r) s->ray_off[r + 1] = s->ray_off[r] + per[r].cnt;
+    long H = s->ray_off[s->nrays];
+    s->hit_j = (int *)malloc(sizeof(int) * (H ? H : 1));
+    s->hit_alpha = dup_arr(NULL, H);
+    s->hit_G = dup_arr(NULL, H);
+    s->hit_a = dup_arr(NULL, H);
+    s->hit_t = dup_arr(NULL, H);
+    for (long r = 0; r < s->nrays; ++r) {
+        double T = 1.0;
+        for (int q = 0; q < per[r].cnt; ++q) {
+            long e = s->ray_off[r] + q;
+            s->hit_j[e] = per[r].h[q].j;
+            s->hit_t[e] = per[r].h[q].t;
+            s->hit_alpha[e] = per[r].h[q].alpha;
+            s->hit_G[e] = per[r].h[q].G;
+            s->hit_a[e] = per[r].h[q].alpha * T;
+            T *= (1.0 - per[r].h[q].alpha);
+        }
+        free(per[r].h);
+    }
+    free(per);
+
+    direct_term(s, nl, lp, li);
     return 0;
 }
 
@@ -624,11 +657,242 @@ void or_direct(const or_scene *s, double *D) {
                     s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * s->Dgeo[((size_t)i * nc + kk) * C + c];
 }
 
+
+/* ------------------------------------------------------------------ center-to-center
+ * Sec. 8 ("Approximations"), the approximated forward rendering equation:
+ *   B_i = E_i + sum_j f_i(w_I) (Y(w_I)^T B_j) V_ji,
+ *   V_ji = lambda_j (int_{P_j} alpha_j dx) prod_k (1 - alpha_k) |n_i.w_I| |n_j.w_I| / |p_i - p_j|^2,
+ * one segment per pair of centres, with f_i absorbing alpha_i(p_i) = o_i.  In the notation
+ * of the hemisphere form: d = (p_j - p_i)/r is the direction from the receiver to the
+ * source, f_i = o_i c_i (x) Y(R_i d), and the source radiates Y(-d)^T B_j.
+ * Readings (listed in the design notes):
+ *   - w_I is the unit vector between the centres (the printed squared norm is garbled);
+ *   - only sources in the receiver's front hemisphere (d.n_i > 0), as for the rays;
+ *   - the transmittance runs over the surfels k != i, j that the open segment (0, r)
+ *     meets under the hemisphere-ray hit rules and whose plane is more than eps_plane from
+ *     the far end p_j as well (coplanar neighbours of the source do not occlude it);
+ *   - int_{P_j} alpha_j dx in closed form for the opacity model: the Gaussian truncated at
+ *     3 sigma gives 2 pi s^u s^v o (1 - e^{-9/2}), the disc pi s^u s^v o.               */
+static double alpha_area_unit(const or_scene *s, int j) { /* int alpha_j dx / o_j */
+    if (s->alpha_model == OR_ALPHA_DISC) return OR_PI * s->su[j] * s->sv[j];
+    return 2.0 * OR_PI * s->su[j] * s->sv[j] * (1.0 - exp(-4.5));
+}
+double or_alpha_area(const or_scene *s, int j) { return s->o[j] * alpha_area_unit(s, j); }
+
+/* Occluders of the segment from p_i to p_j, in compositing order. */
+static void pair_segment(const or_scene *s, int i, int j, const double *d, double r, hitvec *out) {
+    trace_all(s, i, s->p + i * 3, d, r, out);
+    int w = 0;
+    for (int q = 0; q < out->cnt; ++q) {
+        int k = out->h[q].j;
+        if (k == j) continue;
+        const double *nk = s->nrm + k * 3, *pk = s->p + k * 3;
+        double e[3] = {s->p[j * 3] - pk[0], s->p[j * 3 + 1] - pk[1], s->p[j * 3 + 2] - pk[2]};
+        if (fabs(dot3(nk, e)) <= s->eps_plane) continue;
+        out->h[w++] = out->h[q];
+    }
+    out->cnt = w;
+}
+
+/* Builds the pairs of every receiver and the direct term; lam may be NULL (all 1). */
+int or_pairs(or_scene *s, const double *lam, int nl, const double *lp, const double *li) {
+    free_transport(s);
+    int n = s->n;
+    s->pmode = 1;
+    s->nd = 0;
+    s->nl = nl;
+    s->C = 3 * (nl > 0 ? nl : 1);
+    s->lp = dup_arr(lp, 3 * (size_t)nl);
+    s->li = dup_arr(li, 3 * (size_t)nl);
+    s->lam = dup_arr(NULL, n);
+    for (int i = 0; i < n; ++i) s->lam[i] = lam ? lam[i] : 1.0;
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3] = {s->p[j * 3] - s->p[i * 3], s->p[j * 3 + 1] - s->p[i * 3 + 1], s->p[j * 3 + 2] - s->p[i * 3 + 2]};
+            if (dot3(d, d) > 0.0 && dot3(s->nrm + i * 3, d) > 0.0) cnt[i]++;
+        }
+    s->pair_off = (long *)malloc(sizeof(long) * ((size_t)n + 1));
+    s->pair_off[0] = 0;
+    for (int i = 0; i < n; ++i) s->pair_off[i + 1] = s->pair_off[i] + cnt[i];
+    long P = s->pair_off[n];
+    s->pair_j = (int *)malloc(sizeof(int) * (P ? P : 1));
+    s->pair_V = dup_arr(NULL, P);
+    s->pair_T = dup_arr(NULL, P);
+    s->pair_geo = dup_arr(NULL, P);
+    hitvec *occ = (hitvec *)calloc((size_t)(P ? P : 1), sizeof(hitvec));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i) {
+        long e = s->pair_off[i];
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3] = {s->p[j * 3] - s->p[i * 3], s->p[j * 3 + 1] - s->p[i * 3 + 1], s->p[j * 3 + 2] - s->p[i * 3 + 2]};
+            double r2 = dot3(d, d);
+            if (!(r2 > 0.0) || !(dot3(s->nrm + i * 3, d) > 0.0)) continue;
+            double r = sqrt(r2);
+            for (int q = 0; q < 3; ++q) d[q] /= r;
+            pair_segment(s, i, j, d, r, &occ[e]);
+            double T = 1.0;
+            for (int q = 0; q < occ[e].cnt; ++q) T *= 1.0 - occ[e].h[q].alpha;
+            double geo = fabs(dot3(s->nrm + i * 3, d)) * fabs(dot3(s->nrm + j * 3, d)) / r2;
+            s->pair_j[e] = j;
+            s->pair_T[e] = T;
+            s->pair_geo[e] = geo;
+            s->pair_V[e] = s->lam[j] * or_alpha_area(s, j) * T * geo;
+            ++e;
+        }
+    }
+    s->poc_off = (long *)malloc(sizeof(long) * ((size_t)P + 1));
+    s->poc_off[0] = 0;
+    for (long e = 0; e < P; ++e) s->poc_off[e + 1] = s->poc_off[e] + occ[e].cnt;
+    long O = s->poc_off[P];
+    s->poc_j = (int *)malloc(sizeof(int) * (O ? O : 1));
+    s->poc_alpha = dup_arr(NULL, O);
+    s->poc_G = dup_arr(NULL, O);
+    for (long e = 0; e < P; ++e) {
+        for (int q = 0; q < occ[e].cnt; ++q) {
+            s->poc_j[s->poc_off[e] + q] = occ[e].h[q].j;
+            s->poc_alpha[s->poc_off[e] + q] = occ[e].h[q].alpha;
+            s->poc_G[s->poc_off[e] + q] = occ[e].h[q].G;
+        }
+        free(occ[e].h);
+    }
+    free(occ);
+    free(cnt);
+    direct_term(s, nl, lp, li);
+    return 0;
+}
+
+long or_num_pairs(const or_scene *s) { return s->pair_off ? s->pair_off[s->n] : 0; }
+void or_get_pairs(const or_scene *s, long *off, int *j, double *V, double *T) {
+    long P = or_num_pairs(s);
+    memcpy(off, s->pair_off, sizeof(long) * ((size_t)s->n + 1));
+    memcpy(j, s->pair_j, sizeof(int) * P);
+    memcpy(V, s->pair_V, sizeof(double) * P);
+    memcpy(T, s->pair_T, sizeof(double) * P);
+}
+
+static void pair_dir(const or_scene *s, int i, int j, double *d) {
+    double r = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        d[q] = s->p[j * 3 + q] - s->p[i * 3 + q];
+        r += d[q] * d[q];
+    }
+    r = sqrt(r);
+    for (int q = 0; q < 3; ++q) d[q] /= r;
+}
+
+/* (K B)_i = o_i c_i (x) Q_i,  Q_i = sum_j Y(R_i d) V_ji Y(-d)^T B_j */
+static void pair_apply_K(const or_scene *s, const double *Bin, double *Bout, double *Q) {
+    int n = s->n, nc = s->nc, C = s->C, L = s->L;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i) {
+        double Yo[1024], Yi[1024], acc[16384];
+        memset(acc, 0, sizeof(double) * nc * C);
+        for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
+            double d[3], md[3], rd[3];
+            pair_dir(s, i, s->pair_j[e], d);
+            for (int q = 0; q < 3; ++q) md[q] = -d[q];
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            const double *Bj = Bin + (size_t)s->pair_j[e] * nc * C;
+            for (int c = 0; c < C; ++c) {
+                double sv = 0.0;
+                for (int kk = 0; kk < nc; ++kk) sv += Yo[kk] * Bj[kk * C + c];
+                for (int kk = 0; kk < nc; ++kk) acc[kk * C + c] += Yi[kk] * s->pair_V[e] * sv;
+            }
+        }
+        for (int kk = 0; kk < nc; ++kk)
+            for (int c = 0; c < C; ++c) {
+                size_t idx = ((size_t)i * nc + kk) * C + c;
+                if (Q) Q[idx] = acc[kk * C + c];
+                if (Bout) Bout[idx] = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
+            }
+    }
+}
+
+/* transpose: y_e[c] = o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d) Vin_i[k'][c];  Vout_j += V_ji Y(-d) y_e */
+static void pair_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
+    int n = s->n, nc = s->nc, C = s->C, L = s->L;
+    memset(Vout, 0, sizeof(double) * (size_t)n * nc * C);
+    double Yo[1024], Yi[1024], y[4096];
+    for (int i = 0; i < n; ++i)
+        for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
+            double d[3], md[3], rd[3];
+            pair_dir(s, i, s->pair_j[e], d);
+            for (int q = 0; q < 3; ++q) md[q] = -d[q];
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            for (int c = 0; c < C; ++c) {
+                double sv = 0.0;
+                for (int kk = 0; kk < nc; ++kk)
+                    sv += s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Yi[kk] * Vin[((size_t)i * nc + kk) * C + c];
+                y[c] = s->o[i] * sv;
+            }
+            double *Vj = Vout + (size_t)s->pair_j[e] * nc * C;
+            for (int kk = 0; kk < nc; ++kk)
+                for (int c = 0; c < C; ++c) Vj[kk * C + c] += s->pair_V[e] * Yo[kk] * y[c];
+        }
+}
+
+/* Source-side gradients of the pairs: with g_e = dL/dV_ji (summed over the bounces),
+ *   dL/dlambda_j += g_e A_j T geo,  dL/do_j += g_e lambda_j (A_j / o_j) T geo,
+ *   dL/do_k      += g_e lambda_j A_j geo * (-prod_{m != k} (1 - alpha_m)) G_k   (occluders). */
+static void pair_backward(const or_scene *s, int nb, const double *iters, const double *v, double *dop, double *dlam) {
+    int n = s->n, nc = s->nc, C = s->C, L = s->L;
+    size_t M = (size_t)n * nc * C;
+    double Yo[1024], Yi[1024];
+    double *y = dup_arr(NULL, (size_t)(nb > 0 ? nb : 1) * C);
+    for (int i = 0; i < n; ++i)
+        for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
+            int j = s->pair_j[e];
+            double d[3], md[3], rd[3];
+            pair_dir(s, i, j, d);
+            for (int q = 0; q < 3; ++q) md[q] = -d[q];
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            double g = 0.0;
+            for (int a = 0; a < nb; ++a) {
+                const double *Bb = iters + (size_t)(nb - 1 - a) * M + (size_t)j * nc * C;
+                for (int c = 0; c < C; ++c) {
+                    double yv = 0.0, sv = 0.0;
+                    for (int kk = 0; kk < nc; ++kk) {
+                        yv += s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Yi[kk] *
+                              v[(size_t)a * M + ((size_t)i * nc + kk) * C + c];
+                        sv += Yo[kk] * Bb[kk * C + c];
+                    }
+                    g += s->o[i] * yv * sv;
+                }
+            }
+            if (g == 0.0) continue;
+            const double Au = alpha_area_unit(s, j), T = s->pair_T[e], geo = s->pair_geo[e];
+            if (dlam) dlam[j] += g * s->o[j] * Au * T * geo;
+            if (dop) {
+                dop[j] += g * s->lam[j] * Au * T * geo;
+                for (long q = s->poc_off[e]; q < s->poc_off[e + 1]; ++q) {
+                    double others = 1.0;
+                    for (long m = s->poc_off[e]; m < s->poc_off[e + 1]; ++m)
+                        if (m != q) others *= 1.0 - s->poc_alpha[m];
+                    dop[s->poc_j[q]] += -g * s->lam[j] * s->o[j] * Au * geo * others * s->poc_G[q];
+                }
+            }
+        }
+    free(y);
+}
+
 /* Eq. final-radiosity with the hemisphere integral taken by the stored rays:
  *   Q_i = sum_r (pi/Nd) Y(R_i d_r) sum_h a_rh Y(-d_r)^T B_{j_h}        (geometric gather)
  *   (K B)_i = o_i c_i (x) Q_i.
  * Bout may be NULL; Q (un-scaled gather) may be NULL. */
 void or_apply_K(const or_scene *s, const double *Bin, double *Bout, double *Q) {
+    if (s->pmode) {
+        pair_apply_K(s, Bin, Bout, Q);
+        return;
+    }
     int n = s->n, nc = s->nc, C = s->C, nd = s->nd, L = s->L;
     double w = OR_PI / nd;
 #pragma omp parallel for schedule(dynamic, 4)
@@ -669,6 +933,10 @@ void or_apply_K(const or_scene *s, const double *Bin, double *Bout, double *Q) {
  *   y_r[c]          = o_i (pi/Nd) sum_k' c_{i,l(k'),ch} Y_k'(R_i d_r) Vin_i[k'][c]
  *   Vout_{j_h}[k][c] += a_rh Y_k(-d_r) y_r[c]                                         */
 void or_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
+    if (s->pmode) {
+        pair_apply_KT(s, Vin, Vout);
+        return;
+    }
     int n = s->n, nc = s->nc, C = s->C, nd = s->nd, L = s->L;
     double w = OR_PI / nd;
     memset(Vout, 0, sizeof(double) * (size_t)n * nc * C);
@@ -739,9 +1007,11 @@ void or_solve(const or_scene *s, const double *E, int nb, double *B, double *ite
  *   dL/do_i           = sum_{l,ch} c_i[l][ch] P_i[l][ch]                  (receiver factor)
  *                     + sum over hemisphere hits on i of T_h (g_h - R_h) G_h  (compositing)
  *                     + sum over shadow hits on i of -q prod_{m!=h}(1-alpha_m) G_h.
- * Outputs may be NULL.  dc: [N][L+1][3]. */
+ * For the center-to-center transport the hemisphere term is replaced by the pairs'
+ * source and occluder terms (pair_backward), which also give dL/dlambda.
+ * Outputs may be NULL.  dc: [N][L+1][3], dlam: [N] (center-to-center only). */
 void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, double *dE, double *dad, double *dop,
-                double *dc) {
+                double *dc, double *dlam) {
     int n = s->n, nc = s->nc, C = s->C, nd = s->nd, L = s->L, nl = s->nl;
     size_t M = (size_t)n * nc * C;
     double w = OR_PI / nd;
@@ -788,6 +1058,10 @@ void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, dou
             for (int q = 0; q < (L + 1) * 3; ++q) acc += s->c[(size_t)i * (L + 1) * 3 + q] * P[(size_t)i * (L + 1) * 3 + q];
             dop[i] = acc;
         }
+    }
+    if (dlam) memset(dlam, 0, sizeof(double) * (size_t)n);
+    if (s->pmode && (dop || dlam)) pair_backward(s, nb, iters, v, dop, dlam);
+    if (dop) {
         /* hemisphere rays: backward through a_h = alpha_h prod_{k<h}(1 - alpha_k) */
         double Yo[1024], Yi[1024];
         double *y = dup_arr(NULL, (size_t)(nb > 0 ? nb : 1) * C);
@@ -909,9 +1183,26 @@ void or_brdf_grad_closed_form(const or_scene *s, const double *E, int nb, const 
 void or_dense_K(const or_scene *s, int col, double *Kd) {
     int n = s->n, nc = s->nc, nd = s->nd, L = s->L;
     size_t Mm = (size_t)n * nc;
-    double w = OR_PI / nd;
+    double w = s->pmode ? 1.0 : OR_PI / nd;
     memset(Kd, 0, sizeof(double) * Mm * Mm);
     double Yo[1024], Yi[1024];
+    if (s->pmode) {
+        for (int i = 0; i < n; ++i)
+            for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
+                double d[3], md[3], rd[3];
+                pair_dir(s, i, s->pair_j[e], d);
+                for (int q = 0; q < 3; ++q) md[q] = -d[q];
+                reflect(s->nrm + i * 3, d, rd);
+                or_sh_eval(L, md, Yo);
+                or_sh_eval(L, rd, Yi);
+                int j = s->pair_j[e];
+                for (int kp = 0; kp < nc; ++kp) {
+                    double f = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kp)) * 3 + col % 3] * w * Yi[kp] * s->pair_V[e];
+                    for (int kk = 0; kk < nc; ++kk) Kd[((size_t)i * nc + kp) * Mm + (size_t)j * nc + kk] += f * Yo[kk];
+                }
+            }
+        return;
+    }
     for (int i = 0; i < n; ++i)
         for (int r = 0; r < nd; ++r) {
             double d[3], md[3], rd[3];

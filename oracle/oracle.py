@@ -72,7 +72,14 @@ def lib():
             L.or_apply_K.argtypes = [ct.c_void_p, _dp, _dp, _dp]
             L.or_apply_KT.argtypes = [ct.c_void_p, _dp, _dp]
             L.or_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
-            L.or_adjoint.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp, _dp, _dp]
+            L.or_adjoint.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.or_pairs.restype = ct.c_int
+            L.or_pairs.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
+            L.or_num_pairs.restype = ct.c_long
+            L.or_num_pairs.argtypes = [ct.c_void_p]
+            L.or_get_pairs.argtypes = [ct.c_void_p, _lp, _ip, _dp, _dp]
+            L.or_alpha_area.restype = ct.c_double
+            L.or_alpha_area.argtypes = [ct.c_void_p, ct.c_int]
             L.or_brdf_grad_closed_form.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
             L.or_dense_K.argtypes = [ct.c_void_p, ct.c_int, _dp]
             L.or_sample_direct.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, ct.c_int, _ip, _dp]
@@ -186,6 +193,30 @@ class Oracle:
         lib().or_transport(self.h, self.nd, self.seed, self.nl, _ptr(lp), _ptr(li))
         return self
 
+    def pairs(self, lam=None, light_pos=None, light_I=None):
+        """Center-to-center transport (Sec. 8): one segment per pair of surfel centres."""
+        lp = _d(self.sc["light_pos"] if light_pos is None else light_pos).reshape(-1, 3)
+        li = _d(self.sc["light_I"] if light_I is None else light_I).reshape(-1, 3)
+        self.nd, self.seed, self.nl = 0, 0, lp.shape[0]
+        self.C = 3 * max(self.nl, 1)
+        self._lights = (lp, li)
+        self._lam = None if lam is None else _d(lam).reshape(self.n)
+        self.pmode = True
+        lib().or_pairs(self.h, _ptr(self._lam), self.nl, _ptr(lp), _ptr(li))
+        return self
+
+    def pair_list(self):
+        L = lib()
+        P = L.or_num_pairs(self.h)
+        off = np.zeros(self.n + 1, np.int64)
+        j = np.zeros(max(P, 1), np.int32)
+        V, T = np.zeros(max(P, 1)), np.zeros(max(P, 1))
+        L.or_get_pairs(self.h, off.ctypes.data_as(_lp), j.ctypes.data_as(_ip), _ptr(V), _ptr(T))
+        return dict(off=off, j=j[:P], V=V[:P], T=T[:P])
+
+    def alpha_area(self, j):
+        return lib().or_alpha_area(self.h, int(j))
+
     def hits(self):
         L = lib()
         H = L.or_num_hits(self.h)
@@ -235,8 +266,12 @@ class Oracle:
         dad = np.zeros((self.n, 3))
         dop = np.zeros(self.n)
         dc = np.zeros((self.n, self.L + 1, 3))
-        lib().or_adjoint(self.h, _ptr(E), int(nb), _ptr(g), _ptr(dE), _ptr(dad), _ptr(dop), _ptr(dc))
-        return dict(dE=dE, dad=dad, dop=dop, dc=dc)
+        dlam = np.zeros(self.n)
+        lib().or_adjoint(self.h, _ptr(E), int(nb), _ptr(g), _ptr(dE), _ptr(dad), _ptr(dop), _ptr(dc), _ptr(dlam))
+        out = dict(dE=dE, dad=dad, dop=dop, dc=dc)
+        if getattr(self, "pmode", False):
+            out["dlam"] = dlam
+        return out
 
     def brdf_grad_closed_form(self, g, E=None, nb=None):
         nb = self.sc["nb"] if nb is None else nb
