@@ -44,6 +44,9 @@ UNEVEN_WORKLOAD = ("uneven batch: 32 independent fruit-bowl scenes (seeds 1000..
 LARGE_WORKLOAD = ("large scene: 1,000,000 surfels (fruit bowl scaled x4 inside a 20 x 20 x 20 room whose walls "
                   "carry value-noise albedo), SH degree 3, 512 rays/surfel, 6 bounces, 16 point lights, "
                   "iterates checkpointed as memory asks (automatic stride), forward + adjoint")
+PAIRS_WORKLOAD = ("center-to-center approximation (one segment per pair of surfel centres, Sec. 8): fruit bowl, "
+                  "20,000 surfels, SH degree 3, 4 bounces, 1 point light, forward + adjoint with the lambda gradient "
+                  "left out (the rgs_adjoint outputs)")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -93,6 +96,12 @@ def _launch_bytes(kernel, sc):
         "k_opacity_rec": (H * (8 + 4) + rays * (4 + 8 + 16) + n * 64 + n * 4, 1),
         # records in, transposed entries out, counts, offsets, cursors
         "k_src_fill": (H * 16 + rays * 12 + n * 8, 1),
+        # center-to-center (H = pairs): the pair records written once (traversal reads are
+        # the scene and tree); the bounce reads them with the iterate rows once
+        "k_pair_fill": (n * 64 + (n - 1) * 64 + H * 8, 1),
+        "k_bounce_pairs": (H * 8 + 4 * A, nb),
+        "k_adj_src_pairs": (H * 8 + 3 * A, nb),
+        "k_pair_bwd": (H * 8 + 2 * min(nb, 64) * A, 1),
         # per 32-column tile: records, counts, offsets, directions; the iterate rows once
         "k_bounce_mc": (tiles * (H * 8 + rays * (4 + 8 + 16)) + A16 + 4 * A + A16, nb),
         # one tile and up to four iterates: records + ray data; v (FP32) and B (BF16) tiles; g per hit
@@ -212,10 +221,10 @@ class Form:
     their output buffers; `launch` = "batched" solves every scene in one rgs_solve_batched
     call (the persistent graph-captured kernel), "per_scene" calls rgs_solve per scene."""
 
-    def __init__(self, api, rgs, torch, datas, precision, launch, dev, checkpoint=0):
+    def __init__(self, api, rgs, torch, datas, precision, launch, dev, checkpoint=0, pairs=False):
         self.api, self.rgs, self.torch = api, rgs, torch
         self.precision, self.launch = precision, launch
-        self.pipes = [api.Pipeline(precision=precision, checkpoint=checkpoint) for _ in datas]
+        self.pipes = [api.Pipeline(precision=precision, checkpoint=checkpoint, pairs=pairs) for _ in datas]
         self.Bs = [torch.empty((d["n"], (d["L"] + 1) ** 2, 3 * max(1, d["light_pos"].shape[0])), device=dev)
                    for d in datas]
         self.grads = [(torch.empty((d["n"], (d["L"] + 1) ** 2, 3), device=dev), torch.empty((d["n"], 3), device=dev),
@@ -251,10 +260,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=50000, help="surfel count (default: the 50,000-surfel workload)")
-    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven", "large"],
+    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven", "large", "pairs"],
                     help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights; "
                          "uneven: 32 scenes of uneven size in one persistent launch; large: 1,000,000 surfels, "
-                         "512 rays, 6 bounces, 16 lights, checkpointed iterates")
+                         "512 rays, 6 bounces, 16 lights, checkpointed iterates; pairs: the center-to-center "
+                         "approximation on a 20,000-surfel bowl")
     ap.add_argument("--scenes", type=int, default=32, help="uneven workload: number of scenes (profiling cases)")
     ap.add_argument("--scale", type=float, default=1.0, help="uneven workload: surfel-count factor (profiling cases)")
     ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
@@ -287,6 +297,9 @@ def main():
         workload = UNEVEN_WORKLOAD
         if args.scenes != 32 or args.scale != 1.0:
             workload = f"reduced uneven batch ({args.scenes} scenes, counts x{args.scale}) of: " + workload
+    elif args.workload == "pairs":
+        scs = [scenes.fruit_bowl(n=20000 if args.n == 50000 else args.n)]
+        workload = PAIRS_WORKLOAD
     elif args.workload == "large":
         scs = [scenes.large_scene(n=1000000 if args.n == 50000 else args.n)]
         workload = LARGE_WORKLOAD
@@ -314,7 +327,7 @@ def main():
 
     def make_form(name):
         prec, launch = specs[name]
-        f = Form(api, rgs, torch, datas, prec, launch, dev, checkpoint=ckpt)
+        f = Form(api, rgs, torch, datas, prec, launch, dev, checkpoint=ckpt, pairs=args.workload == "pairs")
         for _ in range(max(args.warmup, 3)):
             f.step(datas, gs)
         torch.cuda.synchronize()
@@ -437,7 +450,8 @@ def main():
     src_file = {"k_bounce": "rgs_solve.cu", "k_adj_src": "rgs_adjoint.cu", "k_adj_ray": "rgs_adjoint.cu",
                 "k_bounce_mc": "rgs_manycol.cu", "k_opacity_g_mc": "rgs_manycol.cu", "k_adj_src_mc": "rgs_manycol.cu",
                 "k_opacity_g": "rgs_adjoint.cu", "k_opacity_rec": "rgs_adjoint.cu",
-                "k_bounce_persistent": "rgs_batch.cu", "k_trace_hemi": "rgs_trace.cu"}.get(dom)
+                "k_bounce_persistent": "rgs_batch.cu", "k_trace_hemi": "rgs_trace.cu",
+                "k_pair_fill": "rgs_pairs.cu", "k_bounce_pairs": "rgs_pairs.cu"}.get(dom)
     traffic = None
     if len(scs) == 1 and dom in NCU_TRAFFIC and src_file and NCU_TRAFFIC[dom]["src_sha"] == _src_sha(src_file):
         traffic = NCU_TRAFFIC[dom]["bytes_per_launch"] * (scs[0]["n"] / NCU_TRAFFIC[dom]["n"])

@@ -15,6 +15,8 @@
  *                        direct term first, then a fixed number of bounces)
  *   rgs_adjoint          transposed bounces and parameter gradients (Eq. final_dL_dE,
  *                        Eq. final-dl-dbrdf, Eq. dl-dgeo-0 restricted to opacity)
+ *   rgs_trace_pairs      the center-to-center approximation (Sec. 8) in place of the
+ *                        hemisphere rays, and rgs_adjoint_pairs with its lambda gradient
  *
  * CONVENTIONS (all entry points)
  *  - Every pointer documented "device" must point to memory of the current CUDA device;
@@ -112,6 +114,11 @@ typedef struct rgs_trace_opts {
     int64_t hit_capacity; /* hit-record slots to reserve; 0 = automatic (grown on demand) */
 } rgs_trace_opts;
 
+/* Options of the center-to-center transport (rgs_trace_pairs). */
+typedef struct rgs_pair_opts {
+    const float *lambda; /* device [N]: the per-surfel scale lambda_j of Sec. 8, or NULL (all 1) */
+} rgs_pair_opts;
+
 typedef struct rgs_solve_stats {
     int32_t n_bounces;
     int32_t n_cols;
@@ -124,7 +131,7 @@ typedef struct rgs_solve_stats {
 
 typedef struct rgs_transport_info {
     int32_t n, sh_degree, nc, n_cols, nd, n_lights;
-    int64_t n_hits, n_hit_slots, n_full_rays;
+    int64_t n_hits, n_hit_slots, n_full_rays; /* center-to-center: pairs, pairs, 0 */
     int64_t device_bytes; /* device memory held by the transport handle (not counting the shared
                              workspace pool that rgs_adjoint and rgs_get_iterate draw from) */
 } rgs_transport_info;
@@ -156,6 +163,33 @@ rgs_status rgs_build_scene(const rgs_surfels *surfels, const rgs_build_opts *opt
  * RGS_ERR_OOM, RGS_ERR_CUDA, RGS_ERR_CAPACITY (opts->hit_capacity too small). */
 rgs_status rgs_trace_transport(rgs_scene *scene, const rgs_lights *lights, const rgs_trace_opts *opts, void *stream,
                                rgs_transport **inout);
+
+/* Center-to-center transport (Sec. 8, the approximated forward rendering equation): one
+ * segment per pair of surfel centres instead of hemisphere rays,
+ *   (K B)_i = o_i c_i (x) sum_j Y(R_i d) V_ji Y(-d)^T B_j,   d = (p_j - p_i)/|p_j - p_i|,
+ *   V_ji = lambda_j (int alpha_j dx) T_ij |n_i.d| |n_j.d| / |p_j - p_i|^2,
+ * over the sources j lying more than eps_plane in front of receiver i's plane.  T_ij is the
+ * product of (1 - alpha_k) over the surfels k != i, j the open segment meets under the
+ * hemisphere-ray hit rules whose plane lies more than eps_plane from p_j as well.
+ * int alpha_j dx = 2 pi s^u s^v o (1 - e^{-9/2}) (Gaussian to 3 sigma) or pi s^u s^v o
+ * (disc).  The direct term is that of rgs_trace_transport.  The result is a transport
+ * handle that rgs_solve, rgs_get_iterate and rgs_adjoint accept (every iterate is kept;
+ * rgs_solve_batched does not take it).  Cost: N^2 front tests and one segment trace per
+ * front pair; memory 8 bytes per pair.
+ *   opts : host, may be NULL (lambda = 1).  Other arguments as rgs_trace_transport.
+ * Synchronises `stream` (the pair count decides the buffer size).  Errors: RGS_ERR_ARG,
+ * RGS_ERR_OOM, RGS_ERR_CUDA, RGS_ERR_CAPACITY (traversal stack). */
+rgs_status rgs_trace_pairs(rgs_scene *scene, const rgs_lights *lights, const rgs_pair_opts *opts, void *stream,
+                           rgs_transport **inout);
+
+/* rgs_adjoint for a center-to-center transport, with the gradient of L with respect to
+ * lambda as well:  dL/dlambda_j = sum over pairs (i -> j) of g_ij V_ji / lambda_j, where
+ * g_ij = dL/dV_ji; dL/do adds the source term through int alpha_j and the occluders of
+ * every pair's segment.  dL_dlambda: device [N] or NULL; the rest as rgs_adjoint.
+ * Asynchronous.  Errors: RGS_ERR_ARG (not a center-to-center transport), RGS_ERR_STATE,
+ * RGS_ERR_OOM, RGS_ERR_CUDA. */
+rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
+                             float *dL_dopacity, float *dL_dlambda, void *stream);
 
 /* Runs B^(0) = S = E + D, B^(k) = S + K B^(k-1) for k = 1..n_bounces with
  * (K B)_i = o_i c_i (x) sum_r (pi/nd) Y(R_i d_r) sum_h a_rh Y(-d_r)^T B_{j_h}

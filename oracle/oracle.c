@@ -667,7 +667,9 @@ void or_direct(const or_scene *s, double *D) {
  * source, f_i = o_i c_i (x) Y(R_i d), and the source radiates Y(-d)^T B_j.
  * Readings (listed in the design notes):
  *   - w_I is the unit vector between the centres (the printed squared norm is garbled);
- *   - only sources in the receiver's front hemisphere (d.n_i > 0), as for the rays;
+ *   - only sources in the receiver's front hemisphere, as for the rays, and farther than
+ *     eps_plane from the receiver's plane (n_i.(p_j - p_i) > eps_plane: coplanar
+ *     neighbours, which would meet at |n_i.w| ~ 0, are not pairs);
  *   - the transmittance runs over the surfels k != i, j that the open segment (0, r)
  *     meets under the hemisphere-ray hit rules and whose plane is more than eps_plane from
  *     the far end p_j as well (coplanar neighbours of the source do not occlude it);
@@ -711,7 +713,7 @@ int or_pairs(or_scene *s, const double *lam, int nl, const double *lp, const dou
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3] = {s->p[j * 3] - s->p[i * 3], s->p[j * 3 + 1] - s->p[i * 3 + 1], s->p[j * 3 + 2] - s->p[i * 3 + 2]};
-            if (dot3(d, d) > 0.0 && dot3(s->nrm + i * 3, d) > 0.0) cnt[i]++;
+            if (dot3(s->nrm + i * 3, d) > s->eps_plane) cnt[i]++;
         }
     s->pair_off = (long *)malloc(sizeof(long) * ((size_t)n + 1));
     s->pair_off[0] = 0;
@@ -728,8 +730,8 @@ int or_pairs(or_scene *s, const double *lam, int nl, const double *lp, const dou
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3] = {s->p[j * 3] - s->p[i * 3], s->p[j * 3 + 1] - s->p[i * 3 + 1], s->p[j * 3 + 2] - s->p[i * 3 + 2]};
+            if (!(dot3(s->nrm + i * 3, d) > s->eps_plane)) continue;
             double r2 = dot3(d, d);
-            if (!(r2 > 0.0) || !(dot3(s->nrm + i * 3, d) > 0.0)) continue;
             double r = sqrt(r2);
             for (int q = 0; q < 3; ++q) d[q] /= r;
             pair_segment(s, i, j, d, r, &occ[e]);

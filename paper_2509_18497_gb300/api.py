@@ -18,6 +18,8 @@ def upload(sc, device="cuda"):
     out["light_pos"] = torch.as_tensor(np.ascontiguousarray(sc["light_pos"], np.float32).reshape(-1, 3), device=device)
     out["light_I"] = torch.as_tensor(np.ascontiguousarray(sc["light_I"], np.float32).reshape(-1, 3), device=device)
     out["E"] = None if sc.get("E") is None else torch.as_tensor(np.ascontiguousarray(sc["E"], np.float32), device=device)
+    out["lam"] = None if sc.get("lam") is None else torch.as_tensor(np.ascontiguousarray(sc["lam"], np.float32),
+                                                                     device=device)
     for key in ("L", "nd", "nb", "seed", "n"):
         out[key] = int(sc[key])
     return out
@@ -29,7 +31,9 @@ class Pipeline:
     library's stream-ordered pool, which keeps it reserved, so steady-state steps make no
     cudaMalloc inside the library."""
 
-    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32, checkpoint=0, mem_budget=0):
+    def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32, checkpoint=0, mem_budget=0,
+                 pairs=False):
+        self.pairs = pairs  # center-to-center transport (Sec. 8) instead of hemisphere rays
         self.alpha_model = alpha_model
         self.precision = precision
         self.checkpoint = checkpoint  # iterate checkpoint stride (0 all kept, -1 automatic)
@@ -43,9 +47,13 @@ class Pipeline:
         return self.scene
 
     def trace(self, d, stream=None, hit_capacity=0):
-        self.transport = rgs.rgs_trace_transport(self.scene, d["light_pos"], d["light_I"], d["nd"], d["seed"],
-                                                 hit_capacity=hit_capacity, stream=stream,
-                                                 transport=self.transport)
+        if self.pairs:
+            self.transport = rgs.rgs_trace_pairs(self.scene, d["light_pos"], d["light_I"], lam=d.get("lam"),
+                                                 stream=stream, transport=self.transport)
+        else:
+            self.transport = rgs.rgs_trace_transport(self.scene, d["light_pos"], d["light_I"], d["nd"], d["seed"],
+                                                     hit_capacity=hit_capacity, stream=stream,
+                                                     transport=self.transport)
         rgs.rgs_set_checkpointing(self.transport, self.checkpoint)
         rgs.rgs_set_memory_budget(self.transport, self.mem_budget)
         return self.transport
@@ -56,6 +64,10 @@ class Pipeline:
 
     def adjoint(self, g, outs=(None, None, None), stream=None):
         return rgs.rgs_adjoint(self.transport, g, *outs, stream=stream)
+
+    def adjoint_pairs(self, g, stream=None):
+        """Center-to-center gradients (dL/dE, dL/da^d, dL/do, dL/dlambda)."""
+        return rgs.rgs_adjoint_pairs(self.transport, g, stream=stream)
 
     def step(self, d, g, B_out=None, grads=(None, None, None), stream=None):
         """One full pass of the path: scene build, trace, n bounces, adjoint."""

@@ -517,7 +517,67 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
 
 } // namespace
 
+// ------------------------------------------------------------------ pieces shared with the
+// center-to-center adjoint (rgs_pairs.cu)
+void rgs_copy_offsets(const long long *off, unsigned long long *cursor, int n, cudaStream_t st) {
+    k_copy_off<<<(n + 255) / 256, 256, 0, st>>>(off, cursor, n);
+}
+
+namespace {
+template <int NC> rgs_status prologue_nc(rgs_transport *t, const float *g, cudaStream_t st) {
+    const int n = t->n, C = t->C, nb = t->nb_last;
+    const size_t A = t->arr();
+    { ProfScope ps_("k_from_user", st); k_from_user<NC><<<(unsigned)((A + 255) / 256), 256, 0, st>>>(n, C, t->sc->uid, g, t->v); }
+    RGS_CUDA(cudaMemcpyAsync(t->u, t->v, sizeof(float) * A, cudaMemcpyDeviceToDevice, st));
+    RGS_CUDA(cudaMemsetAsync(t->Pg, 0, sizeof(float) * 12 * (size_t)n, st));
+    RGS_CUDA(cudaMemsetAsync(t->dop, 0, sizeof(float) * (size_t)n, st));
+    if (nb >= 1) { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<(n + 127) / 128, 128, 0, st>>>(n, C, t->v, t->Q + A * (nb - 1), t->Pg); }
+    RGS_LAUNCH("adjoint init");
+    return RGS_OK;
+}
+template <int NC> rgs_status accum_nc(rgs_transport *t, const float *X, const float *Y, cudaStream_t st) {
+    { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<(t->n + 127) / 128, 128, 0, st>>>(t->n, t->C, X, Y, t->Pg); }
+    RGS_LAUNCH("pair accum");
+    return RGS_OK;
+}
+template <int NC> rgs_status shadow_nc(rgs_transport *t, cudaStream_t st) {
+    if (t->nl <= 0) return RGS_OK;
+    const int nth = t->n * t->nl;
+    { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->nl, t->lpos, t->lint, t->C, t->u, t->Pg, t->dop); }
+    RGS_LAUNCH("shadow backward");
+    return RGS_OK;
+}
+template <int NC> rgs_status finalize_nc(rgs_transport *t, float *dE, float *dad, float *dop, cudaStream_t st) {
+    { ProfScope ps_("k_finalize", st); k_finalize<NC><<<(t->n + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->C, t->u, t->Pg, t->sc->kk, t->dop, dE, dad, dop); }
+    RGS_LAUNCH("finalize");
+    return RGS_OK;
+}
+} // namespace
+
+#define RGS_NC_SWITCH(nc, call1, call4, call9, call16)                                                                 \
+    switch (nc) {                                                                                                      \
+    case 1: return call1;                                                                                              \
+    case 4: return call4;                                                                                              \
+    case 9: return call9;                                                                                              \
+    default: return call16;                                                                                            \
+    }
+rgs_status rgs_adjoint_prologue(rgs_transport *t, int nc, const float *g, cudaStream_t st) {
+    RGS_NC_SWITCH(nc, prologue_nc<1>(t, g, st), prologue_nc<4>(t, g, st), prologue_nc<9>(t, g, st), prologue_nc<16>(t, g, st))
+}
+rgs_status rgs_pair_accum(rgs_transport *t, int nc, const float *X, const float *Y, cudaStream_t st) {
+    RGS_NC_SWITCH(nc, accum_nc<1>(t, X, Y, st), accum_nc<4>(t, X, Y, st), accum_nc<9>(t, X, Y, st), accum_nc<16>(t, X, Y, st))
+}
+rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st) {
+    RGS_NC_SWITCH(nc, shadow_nc<1>(t, st), shadow_nc<4>(t, st), shadow_nc<9>(t, st), shadow_nc<16>(t, st))
+}
+rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st) {
+    RGS_NC_SWITCH(nc, finalize_nc<1>(t, dE, dad, dop, st), finalize_nc<4>(t, dE, dad, dop, st),
+                  finalize_nc<9>(t, dE, dad, dop, st), finalize_nc<16>(t, dE, dad, dop, st))
+}
+#undef RGS_NC_SWITCH
+
 rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st) {
+    if (t->kind == RGS_KIND_PAIRS) return rgs_adjoint_pairs_impl(t, g, dE, dad, dop, nullptr, st);
     rgs_status r;
     const int nb = t->nb_last, n = t->n;
     const size_t A = t->arr();

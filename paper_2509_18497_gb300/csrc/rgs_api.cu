@@ -309,6 +309,54 @@ rgs_status rgs_trace_transport(rgs_scene *scene, const rgs_lights *lights, const
     return RGS_OK;
 }
 
+rgs_status rgs_trace_pairs(rgs_scene *scene, const rgs_lights *lights, const rgs_pair_opts *opts, void *stream,
+                           rgs_transport **inout) {
+    g_err[0] = 0;
+    if (!scene || !inout) {
+        rgs_set_error("rgs_trace_pairs: NULL argument");
+        return RGS_ERR_ARG;
+    }
+    if (lights && (lights->n_lights < 0 || lights->n_lights > 4096 ||
+                   (lights->n_lights > 0 && (!lights->pos || !lights->intensity)))) {
+        rgs_set_error("rgs_trace_pairs: invalid lights");
+        return RGS_ERR_ARG;
+    }
+    rgs_transport *t = *inout;
+    bool created = false;
+    if (!t) {
+        t = new (std::nothrow) rgs_transport();
+        if (!t) return RGS_ERR_OOM;
+        created = true;
+    }
+    t->sc = scene;
+    rgs_status r = rgs_trace_pairs_impl(t, lights, opts ? opts->lambda : nullptr, S(stream));
+    if (r != RGS_OK) {
+        if (created) rgs_destroy_transport(t);
+        else t->nb_last = -1;
+        return r;
+    }
+    *inout = t;
+    return RGS_OK;
+}
+
+rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
+                             float *dL_dopacity, float *dL_dlambda, void *stream) {
+    g_err[0] = 0;
+    if (!t || !dL_dB) {
+        rgs_set_error("rgs_adjoint_pairs: NULL argument");
+        return RGS_ERR_ARG;
+    }
+    if (t->kind != RGS_KIND_PAIRS) {
+        rgs_set_error("rgs_adjoint_pairs: not a center-to-center transport");
+        return RGS_ERR_ARG;
+    }
+    if (t->nb_last < 0) {
+        rgs_set_error("rgs_adjoint_pairs: no rgs_solve on this transport since it was traced");
+        return RGS_ERR_STATE;
+    }
+    return rgs_adjoint_pairs_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda, S(stream));
+}
+
 rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_t precision, float *B_out,
                      rgs_solve_stats *stats, void *stream) {
     g_err[0] = 0;
@@ -324,7 +372,7 @@ rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_
         rgs_set_error("rgs_solve: unknown precision %d", precision);
         return RGS_ERR_ARG;
     }
-    if (t->nd == 0) {
+    if (t->kind == RGS_KIND_NONE) {
         rgs_set_error("rgs_solve: transport was not traced");
         return RGS_ERR_STATE;
     }
@@ -363,9 +411,13 @@ rgs_status rgs_solve_batched(rgs_transport *const *ts, int32_t count, const floa
             rgs_set_error("rgs_solve_batched: transport %d is NULL", s);
             return RGS_ERR_ARG;
         }
-        if (ts[s]->nd == 0) {
+        if (ts[s]->kind == RGS_KIND_NONE) {
             rgs_set_error("rgs_solve_batched: transport %d was not traced", s);
             return RGS_ERR_STATE;
+        }
+        if (ts[s]->kind != RGS_KIND_HEMISPHERE) {
+            rgs_set_error("rgs_solve_batched: transport %d is a center-to-center transport (solve it with rgs_solve)", s);
+            return RGS_ERR_ARG;
         }
         if (n_bounces[s] < 0 || n_bounces[s] > RGS_MAX_BOUNCES) {
             rgs_set_error("rgs_solve_batched: n_bounces[%d] = %d outside [0, %d]", s, n_bounces[s], RGS_MAX_BOUNCES);
@@ -475,6 +527,12 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->Pg);
     dev_free(t->dop);
     dev_free(t->dir);
+    dev_free(t->pair_off);
+    dev_free(t->pair_rec);
+    dev_free(t->chunk_off);
+    dev_free(t->chunk_cnt);
+    dev_free(t->chunk_tmp);
+    dev_free(t->lam);
     delete t;
 }
 

@@ -53,6 +53,13 @@ template <int NC, class T> constexpr int row_stride() {
 
 
 template <int NC, int CT, class SL>
+__device__ __forceinline__ void bounce_epilogue(const SceneDev &sc, int C, const float (&acc)[SL::KPL][CT], float w,
+                                                const float *__restrict__ Bprev, const float *__restrict__ S,
+                                                float *__restrict__ Qout, float *__restrict__ Bout,
+                                                __nv_bfloat16 *__restrict__ Bout16, double *norm2, int i, int col0,
+                                                float *red);
+
+template <int NC, int CT, class SL>
 __device__ __forceinline__ void bounce_receiver(const SceneDev &sc, const RaysDev &rays, int C,
                                                 const typename SL::T *__restrict__ Bg, const float *__restrict__ Bprev,
                                                 const float *__restrict__ S, float *__restrict__ Qout,
@@ -107,6 +114,20 @@ __device__ __forceinline__ void bounce_receiver(const SceneDev &sc, const RaysDe
             for (int m = 0; m < KPL; ++m) acc[m][c] += yi[m] * xc;
         }
     }
+    bounce_epilogue<NC, CT, SL>(sc, C, acc, 3.14159265358979f / (float)nd, Bprev, S, Qout, Bout, Bout16, norm2, i, col0,
+                                red);
+}
+
+// Reduction of the per-thread projections acc over the CTA and the bounce update of one
+// (receiver, column tile): Q = w * sum, B = S + o_i c_i (x) Q, its BF16 copy, and the FP64
+// partial of ||B - Bprev||^2.  Ends with __syncthreads (red is reused).
+template <int NC, int CT, class SL>
+__device__ __forceinline__ void bounce_epilogue(const SceneDev &sc, int C, const float (&acc)[SL::KPL][CT], float w,
+                                                const float *__restrict__ Bprev, const float *__restrict__ S,
+                                                float *__restrict__ Qout, float *__restrict__ Bout,
+                                                __nv_bfloat16 *__restrict__ Bout16, double *norm2, int i, int col0,
+                                                float *red) {
+    constexpr int G = SL::G, KPL = SL::KPL;
     // reduce over the groups: lanes with equal g within the warp, then across warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -120,7 +141,6 @@ __device__ __forceinline__ void bounce_receiver(const SceneDev &sc, const RaysDe
         }
     __syncthreads();
     double dsq = 0.0;
-    const float w = 3.14159265358979f / (float)nd;
     for (int e = threadIdx.x; e < NC * CT; e += BOUNCE_THREADS) {
         const int k = e / CT, c = e - k * CT;
         int gg = 0, mm = 0;

@@ -463,14 +463,29 @@ struct rgs_scene {
     }
 };
 
+enum { RGS_KIND_NONE = 0, RGS_KIND_HEMISPHERE = 1, RGS_KIND_PAIRS = 2 };
+
 struct rgs_transport {
     rgs_scene *sc = nullptr;
+    int kind = RGS_KIND_NONE; // which trace built it: hemisphere rays or center-to-center pairs
     int n = 0, L = 0, nc = 1;
     int nd = 0, na = 1, nbs = 1;
     unsigned long long seed = 0;
     int nl = 0, C = 3;
     float *lpos = nullptr, *lint = nullptr;
     int lcap = 0;
+    // center-to-center pairs: receiver i's pairs at pair_off[i] .. pair_off[i+1], each
+    // (source j, bits of V_ji); chunk_off: first pair of each (receiver, 256-source chunk)
+    long long *pair_off = nullptr;
+    int2 *pair_rec = nullptr;
+    long long pair_cap = 0, n_pairs = 0;
+    long long *chunk_off = nullptr;
+    int *chunk_cnt = nullptr;
+    long long chunk_cap = 0;
+    long long *chunk_tmp = nullptr;
+    int chunk_tmp_cap = 0;
+    float *lam = nullptr; // lambda in internal order
+    int lam_cap = 0;
     // hemisphere hit records
     long long cap_slots = 0;
     int2 *rec_ja = nullptr;
@@ -665,4 +680,21 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *ts, int count, const flo
 void rgs_batch_forget(const rgs_transport *t);
 // device-wide exclusive scan of int counts into int64 offsets (offsets[n] = total)
 rgs_status rgs_scan_counts(const int *cnt, long long *off, int n, long long *tmp, int tmp_cap, cudaStream_t st);
+// light copies and per-surfel buffers shared by both transports; the direct term
+rgs_status rgs_transport_common(rgs_transport *t, const rgs_lights *L, cudaStream_t st);
+rgs_status rgs_direct_term(rgs_transport *t, cudaStream_t st);
+// center-to-center transport (rgs_pairs.cu)
+rgs_status rgs_trace_pairs_impl(rgs_transport *t, const rgs_lights *L, const float *lambda, cudaStream_t st);
+template <int NC>
+rgs_status pairs_bounce(const rgs_transport *t, bool rows16, const float *Bprev, const __nv_bfloat16 *Bprev16,
+                        const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16, double *norm2, cudaStream_t st);
+rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, float *dlam,
+                                  cudaStream_t st);
+// adjoint pieces shared by both transports (rgs_adjoint.cu): v^(0) = dL/dB, u = v^(0),
+// P = v^(0) Q^(n-1), dop = 0; P += X Y; the shadow-ray backward; the outputs
+rgs_status rgs_adjoint_prologue(rgs_transport *t, int nc, const float *g, cudaStream_t st);
+rgs_status rgs_pair_accum(rgs_transport *t, int nc, const float *X, const float *Y, cudaStream_t st);
+rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st);
+rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st);
+void rgs_copy_offsets(const long long *off, unsigned long long *cursor, int n, cudaStream_t st);
 int rgs_scan_tmp_size(int n);

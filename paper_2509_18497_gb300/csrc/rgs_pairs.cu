@@ -1,0 +1,485 @@
+// Center-to-center transport (Sec. 8, the approximated forward rendering equation):
+//
+//   B_i = E_i + sum_j f_i(w) (Y(w)^T B_j) V_ji,
+//   V_ji = lambda_j (int alpha_j dx) prod_k (1 - alpha_k) |n_i.w| |n_j.w| / |p_i - p_j|^2,
+//
+// one segment per pair of surfel centres instead of hemisphere rays; f_i absorbs
+// alpha_i(p_i) = o_i, so with d = (p_j - p_i)/r the pair adds o_i c_i (x) Y(R_i d) V_ji
+// Y(-d)^T B_j to the receiver, exactly the hemisphere gather with one "hit" of weight V_ji
+// per direction and no pi/nd.  Sources count when they lie more than eps_plane in front
+// of the receiver's plane; the segment's occluders follow the hemisphere-ray hit rules and
+// must lie more than eps_plane from the source's end too; int alpha_j is closed-form.
+//
+// Storage: the pairs of receiver i are contiguous (pair_off[i] .. pair_off[i+1]), each one
+// record (j, bits of V_ji), sources in increasing internal index.  A count pass sizes
+// every (receiver, 256-source chunk) block exactly; the fill pass traces each front pair's
+// segment and writes its record at the chunk's offset plus its rank in the block.
+#include <algorithm>
+#include <vector>
+
+#include "rgs_bounce_body.cuh"
+
+namespace {
+
+constexpr int PCH = 256;      // sources per block of the count / fill passes
+constexpr int PAIR_THREADS = 128;
+
+// int alpha_j dx / o_j for the opacity model (App. E for this build's models): the
+// Gaussian truncated at 3 sigma 2 pi s^u s^v (1 - e^{-9/2}), the disc pi s^u s^v
+__device__ __forceinline__ float alpha_area_unit(const SceneDev &sc, int j) {
+    const float su = 1.f / __ldg(&sc.FU[j].w), sv = 1.f / __ldg(&sc.FV[j].w);
+    if (sc.alpha_model == RGS_ALPHA_DISC) return 3.14159265358979f * su * sv;
+    return 6.28318530717959f * su * sv * 0.98889100346175773f; // 1 - e^{-4.5}
+}
+
+// source j in front of receiver i: n_i.(p_j - p_i) > eps (explicitly rounded, so the count
+// and the fill pass agree bit for bit)
+__device__ __forceinline__ bool pair_front(const SceneDev &sc, float3 pi, float3 ni, int j, float eps, float3 &dv) {
+    const float4 Pj = __ldg(&sc.P[j]);
+    dv = make_float3(__fsub_rn(Pj.x, pi.x), __fsub_rn(Pj.y, pi.y), __fsub_rn(Pj.z, pi.z));
+    const float h = __fmaf_rn(ni.z, dv.z, __fmaf_rn(ni.y, dv.y, __fmul_rn(ni.x, dv.x)));
+    return h > eps;
+}
+
+__device__ __forceinline__ float3 unit_dir(float3 dv, float &r) {
+    r = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
+    const float inv = 1.f / r;
+    return make_float3(dv.x * inv, dv.y * inv, dv.z * inv);
+}
+
+// occluder k of the segment i -> j (t in (0, r)): a regular hit that is not the source and
+// whose plane is more than eps from the source's centre
+__device__ __forceinline__ bool pair_occluder(const SceneDev &sc, int k, int i, int j, float3 o, float3 d, float r,
+                                              float3 pj, float eps, float &g) {
+    if (k == j) return false;
+    float t;
+    if (!hit_surfel(sc, k, i, o, d, r, eps, t, g)) return false;
+    const float4 Nk = __ldg(&sc.N4[k]);
+    const float4 Pk = __ldg(&sc.P[k]);
+    const float e = Nk.x * (pj.x - Pk.x) + Nk.y * (pj.y - Pk.y) + Nk.z * (pj.z - Pk.z);
+    return fabsf(e) > eps;
+}
+
+__global__ void __launch_bounds__(PCH) k_pair_count(SceneDev sc, int n, int chunks, int *chunk_cnt, int *src_cnt) {
+    const int blk = blockIdx.x;
+    const int i = blk / chunks, c = blk - i * chunks;
+    const int j = c * PCH + threadIdx.x;
+    const float eps = *sc.eps_plane;
+    const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
+    float3 dv;
+    const bool front = j < n && j != i && pair_front(sc, pi, ni, j, eps, dv);
+    const int cnt = __syncthreads_count(front);
+    if (threadIdx.x == 0) chunk_cnt[blk] = cnt;
+    if (front) atomicAdd(&src_cnt[j], 1);
+}
+
+__global__ void __launch_bounds__(PCH) k_pair_fill(SceneDev sc, int n, int chunks, const long long *__restrict__ chunk_off,
+                                                   const float *__restrict__ lam, int2 *rec, int *flags) {
+    __shared__ int warp_base[PCH / 32];
+    const int blk = blockIdx.x;
+    const int i = blk / chunks, c = blk - i * chunks;
+    const int j = c * PCH + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float eps = *sc.eps_plane;
+    const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
+    float3 dv;
+    const bool front = j < n && j != i && pair_front(sc, pi, ni, j, eps, dv);
+    // rank of this pair in the block (sources in increasing order)
+    const unsigned bal = __ballot_sync(0xffffffffu, front);
+    if (lane == 0) warp_base[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < warp; ++w) base += warp_base[w];
+    if (!front) return;
+    const int rank = base + __popc(bal & ((1u << lane) - 1u));
+    float r;
+    const float3 d = unit_dir(dv, r);
+    const float3 pj = f3(sc.P[j]);
+    float T = 1.f;
+    auto visit = [&](int k) {
+        float g;
+        if (pair_occluder(sc, k, i, j, pi, d, r, pj, eps, g)) T *= 1.f - __ldg(&sc.P[k].w) * g;
+    };
+    if (!bvh_traverse(sc, pi, d, r, visit)) atomicAdd(&flags[FLAG_STACK], 1);
+    const float3 nj = f3(sc.N4[j]);
+    const float geo = fabsf(dot3(ni, d)) * fabsf(dot3(nj, d)) / (r * r);
+    const float V = __ldg(&lam[j]) * __ldg(&sc.P[j].w) * alpha_area_unit(sc, j) * T * geo;
+    rec[chunk_off[blk] + rank] = make_int2(j, __float_as_int(V));
+}
+
+__global__ void k_pair_off(const long long *chunk_off, int chunks, int n, long long *pair_off) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) pair_off[i] = chunk_off[(size_t)i * chunks];
+}
+
+// lambda in internal order (1 where the caller gives none)
+__global__ void k_lam_in(int n, const int *__restrict__ uid, const float *__restrict__ lam_user, float *lam) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) lam[i] = lam_user ? lam_user[uid[i]] : 1.f;
+}
+
+// ------------------------------------------------------------------ bounce
+// One receiver and one 3-column tile: G lanes per pair, each a slice of the coefficients.
+template <int NC, int CT, class SL>
+__global__ void RGS_BOUNCE_LB k_bounce_pairs(SceneDev sc, const long long *__restrict__ pair_off,
+                                             const int2 *__restrict__ rec, int C, const typename SL::T *__restrict__ Bg,
+                                             const float *__restrict__ Bprev, const float *__restrict__ S,
+                                             float *__restrict__ Qout, float *__restrict__ Bout,
+                                             __nv_bfloat16 *__restrict__ Bout16, double *norm2) {
+    __shared__ float red[(BOUNCE_THREADS / 32) * SL::G * SL::KPL * CT];
+    constexpr int G = SL::G, KPL = SL::KPL, GROUPS = BOUNCE_THREADS / G, RS = SL::STRIDE;
+    const int i = blockIdx.x, col0 = blockIdx.y * CT;
+    const int grp = threadIdx.x / G, g = threadIdx.x % G;
+    const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
+    float acc[KPL][CT];
+#pragma unroll
+    for (int m = 0; m < KPL; ++m)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[m][c] = 0.f;
+    const long long e0 = pair_off[i], e1 = pair_off[i + 1];
+    // every lane makes the same number of trips (the group sums shuffle across the warp);
+    // a group past the receiver's last pair contributes zero
+    for (long long eb = e0; eb < e1; eb += GROUPS) {
+        const long long e = eb + grp;
+        const bool live = e < e1;
+        const int2 jv = __ldg(&rec[live ? e : e1 - 1]);
+        const float V = live ? __int_as_float(jv.y) : 0.f;
+        const float4 Pj = __ldg(&sc.P[jv.x]);
+        float r;
+        const float3 d = unit_dir(make_float3(Pj.x - pi.x, Pj.y - pi.y, Pj.z - pi.z), r);
+        float yo[KPL], yi[KPL];
+        {
+            float Y[NC];
+            sh_eval<NC>(neg3(d), Y);
+            SL::pick(Y, g, yo);
+            sh_eval<NC>(reflect_n(ni, d), Y);
+            SL::pick(Y, g, yi);
+        }
+        const typename SL::T *Bj = Bg + ((size_t)jv.x * C + col0) * RS;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            float v[KPL];
+            SL::load(Bj + c * RS, g, v);
+            float s = 0.f;
+#pragma unroll
+            for (int m = 0; m < KPL; ++m) s += yo[m] * v[m];
+            const float xc = V * SL::group_sum(s);
+#pragma unroll
+            for (int m = 0; m < KPL; ++m) acc[m][c] += yi[m] * xc;
+        }
+    }
+    bounce_epilogue<NC, CT, SL>(sc, C, acc, 1.f, Bprev, S, Qout, Bout, Bout16, norm2, i, col0, red);
+}
+
+// ------------------------------------------------------------------ adjoint
+// transposed index: for every pair (i -> j) the entry (i, bits of V) in source j's list
+__global__ void k_pair_src_fill(int n, const long long *__restrict__ pair_off, const int2 *__restrict__ rec,
+                                unsigned long long *cursor, int2 *tr) {
+    const int i = blockIdx.x;
+    for (long long e = pair_off[i] + threadIdx.x; e < pair_off[i + 1]; e += blockDim.x) {
+        const int2 jv = rec[e];
+        const unsigned long long pos = atomicAdd(&cursor[jv.x], 1ull);
+        tr[pos] = make_int2(i, jv.y);
+    }
+}
+
+// (K^T v)_j[c][k] = sum_{pairs i -> j} V_ji Y_k(-d) y_i[c],
+// y_i[c] = o_i sum_k' c_{i,l(k'),ch} Y_k'(R_i d) v_i[c][k']; one CTA per source, all tiles
+template <int NC>
+__global__ void __launch_bounds__(PAIR_THREADS) k_adj_src_pairs(SceneDev sc, int C, const long long *__restrict__ src_off,
+                                                               const int2 *__restrict__ tr, const float *__restrict__ vin,
+                                                               float *__restrict__ vout, float *__restrict__ u) {
+    constexpr int CT = 3;
+    __shared__ float red[PAIR_THREADS / 32][NC * CT];
+    const int j = blockIdx.x;
+    const float4 Pj = __ldg(&sc.P[j]);
+    const long long e0 = src_off[j], e1 = src_off[j + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int col0 = 0; col0 < C; col0 += CT) {
+        float acc[NC][CT];
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[k][c] = 0.f;
+        for (long long e = e0 + threadIdx.x; e < e1; e += PAIR_THREADS) {
+            const int2 iv = __ldg(&tr[e]);
+            const int i = iv.x;
+            const float V = __int_as_float(iv.y);
+            const float4 Pi = __ldg(&sc.P[i]);
+            float r;
+            const float3 d = unit_dir(make_float3(Pj.x - Pi.x, Pj.y - Pi.y, Pj.z - Pi.z), r);
+            float Yi[NC], Yo[NC];
+            sh_eval<NC>(reflect_n(f3(sc.N4[i]), d), Yi);
+            sh_eval<NC>(neg3(d), Yo);
+            const float *vi = vin + ((size_t)i * C + col0) * NC;
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const int ch = (col0 + c) % 3;
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * Yi[k] * __ldg(&vi[c * NC + k]);
+                const float y = V * Pi.w * s;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) acc[k][c] += Yo[k] * y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                float v = acc[k][c];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0) red[warp][k * CT + c] = v;
+            }
+        __syncthreads();
+        for (int q = threadIdx.x; q < NC * CT; q += PAIR_THREADS) {
+            float v = 0.f;
+            for (int w = 0; w < PAIR_THREADS / 32; ++w) v += red[w][q];
+            const int k = q / CT, c = q - k * CT;
+            const size_t idx = ((size_t)j * C + col0 + c) * NC + k;
+            vout[idx] = v;
+            u[idx] += v;
+        }
+        __syncthreads();
+    }
+}
+
+// Source-side gradients of every pair (i -> j): with g = dL/dV_ji summed over the bounces,
+//   g = sum_{a<n} sum_c y_i^(a)[c] Y(-d) . B_j^(n-1-a)[c],
+//   dL/dlambda_j += g A_j T geo,  dL/do_j += g lambda_j (A_j/o_j) T geo,
+//   dL/do_k += -g lambda_j A_j geo prod_{m != k}(1 - alpha_m) G_k for the segment's occluders
+// (the segment is traced again: once for T and the zero factors, once for the occluders).
+template <int NC>
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair_bwd(SceneDev sc, int C, int nb, const long long *__restrict__ pair_off,
+                                                          const int2 *__restrict__ rec, const float *__restrict__ lam,
+                                                          size_t A, const float *__restrict__ V,
+                                                          const float *__restrict__ Bit, float *dop, float *dlam,
+                                                          int *flags) {
+    const int i = blockIdx.x;
+    const float4 Pi = __ldg(&sc.P[i]);
+    const float3 pi = f3(Pi), ni = f3(sc.N4[i]);
+    const float eps = *sc.eps_plane;
+    for (long long e = pair_off[i] + threadIdx.x; e < pair_off[i + 1]; e += PAIR_THREADS) {
+        const int j = __ldg(&rec[e]).x;
+        const float3 pj = f3(sc.P[j]);
+        float r;
+        const float3 d = unit_dir(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), r);
+        float Yi[NC], Yo[NC];
+        sh_eval<NC>(reflect_n(ni, d), Yi);
+        sh_eval<NC>(neg3(d), Yo);
+        float g = 0.f;
+        for (int a = 0; a < nb; ++a) {
+            const float *va = V + A * a + (size_t)i * C * NC;
+            const float *Bb = Bit + A * (nb - 1 - a) + (size_t)j * C * NC;
+            for (int c = 0; c < C; ++c) {
+                const int ch = c % 3;
+                float y = 0.f, s = 0.f;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    y += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * Yi[k] * __ldg(&va[c * NC + k]);
+                    s += Yo[k] * __ldg(&Bb[c * NC + k]);
+                }
+                g += y * s;
+            }
+        }
+        g *= Pi.w;
+        if (g == 0.f) continue;
+        const float Au = alpha_area_unit(sc, j);
+        const float oj = __ldg(&sc.P[j].w), lj = __ldg(&lam[j]);
+        const float geo = fabsf(dot3(ni, d)) * fabsf(dot3(f3(sc.N4[j]), d)) / (r * r);
+        float Tnz = 1.f;
+        int nzero = 0;
+        auto pass1 = [&](int k) {
+            float gk;
+            if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
+            const float om = 1.f - __ldg(&sc.P[k].w) * gk;
+            if (om == 0.f) ++nzero;
+            else Tnz *= om;
+        };
+        if (!bvh_traverse(sc, pi, d, r, pass1)) atomicAdd(&flags[FLAG_STACK], 1);
+        const float T = nzero ? 0.f : Tnz;
+        if (dlam) atomicAdd(&dlam[j], g * oj * Au * T * geo);
+        if (!dop) continue;
+        if (T != 0.f) atomicAdd(&dop[j], g * lj * Au * T * geo);
+        if (nzero > 1) continue;
+        const float q = -g * lj * oj * Au * geo;
+        auto pass2 = [&](int k) {
+            float gk;
+            if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
+            const float om = 1.f - __ldg(&sc.P[k].w) * gk;
+            float others;
+            if (nzero == 0) others = Tnz / om;
+            else others = (om == 0.f) ? Tnz : 0.f;
+            if (others != 0.f) atomicAdd(&dop[k], q * others * gk);
+        };
+        bvh_traverse(sc, pi, d, r, pass2);
+    }
+}
+
+__global__ void k_lam_out(int n, const int *__restrict__ uid, const float *__restrict__ dlam, float *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[uid[i]] = dlam[i];
+}
+
+} // namespace
+
+// ------------------------------------------------------------------ host side
+rgs_status rgs_trace_pairs_impl(rgs_transport *t, const rgs_lights *L, const float *lambda, cudaStream_t st) {
+    rgs_status r;
+    t->kind = RGS_KIND_PAIRS;
+    t->nd = 0;
+    if ((r = rgs_transport_common(t, L, st)) != RGS_OK) return r;
+    const int n = t->n;
+    const int chunks = (n + PCH - 1) / PCH;
+    const long long nchunk = (long long)n * chunks;
+    if (nchunk >= (1ll << 31)) {
+        rgs_set_error("rgs_trace_pairs: %d surfels give too many (receiver, source-chunk) blocks", n);
+        return RGS_ERR_ARG;
+    }
+    if (nchunk > t->chunk_cap) {
+        if ((r = dev_alloc(&t->chunk_cnt, (size_t)nchunk, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->chunk_off, (size_t)nchunk + 1, &t->device_bytes)) != RGS_OK) return r;
+        t->chunk_tmp_cap = rgs_scan_tmp_size((int)nchunk);
+        if ((r = dev_alloc(&t->chunk_tmp, (size_t)t->chunk_tmp_cap, &t->device_bytes)) != RGS_OK) return r;
+        t->chunk_cap = nchunk;
+    }
+    if (n > t->lam_cap) {
+        if ((r = dev_alloc(&t->lam, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->pair_off, (size_t)n + 1, &t->device_bytes)) != RGS_OK) return r;
+        t->lam_cap = n;
+    }
+    SceneDev sd = t->sc->dev();
+    { ProfScope ps_("k_lam_in", st); k_lam_in<<<(n + 255) / 256, 256, 0, st>>>(n, t->sc->uid, lambda, t->lam); }
+    RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));
+    RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
+    { ProfScope ps_("k_pair_count", st); k_pair_count<<<(unsigned)nchunk, PCH, 0, st>>>(sd, n, chunks, t->chunk_cnt, t->src_cnt); }
+    RGS_LAUNCH("pair count");
+    if ((r = rgs_scan_counts(t->chunk_cnt, t->chunk_off, (int)nchunk, t->chunk_tmp, t->chunk_tmp_cap, st)) != RGS_OK)
+        return r;
+    long long total = 0;
+    RGS_CUDA(cudaMemcpyAsync(&total, t->chunk_off + nchunk, sizeof total, cudaMemcpyDeviceToHost, st));
+    RGS_CUDA(cudaStreamSynchronize(st));
+    if (total > t->pair_cap) {
+        if ((r = dev_alloc(&t->pair_rec, (size_t)total, &t->device_bytes)) != RGS_OK) return r;
+        t->pair_cap = total;
+    }
+    t->n_pairs = total;
+    t->n_hits = total;
+    t->n_slots = total;
+    t->n_full = 0;
+    { ProfScope ps_("k_pair_fill", st); k_pair_fill<<<(unsigned)nchunk, PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->pair_rec, t->flags); }
+    { ProfScope ps_("k_pair_off", st); k_pair_off<<<(n + 256) / 256, 256, 0, st>>>(t->chunk_off, chunks, n, t->pair_off); }
+    RGS_LAUNCH("pair fill");
+    if ((r = rgs_direct_term(t, st)) != RGS_OK) return r;
+    // per-source counts -> offsets of the transposed index (filled by the adjoint)
+    if ((r = rgs_scan_counts(t->src_cnt, t->src_off, n, t->scan_tmp, t->scan_tmp_cap, st)) != RGS_OK) return r;
+    int flags[FLAG_COUNT];
+    RGS_CUDA(cudaMemcpyAsync(flags, t->flags, sizeof flags, cudaMemcpyDeviceToHost, st));
+    RGS_CUDA(cudaStreamSynchronize(st));
+    if (flags[FLAG_STACK]) {
+        rgs_set_error("BVH traversal stack overflow on %d segments", flags[FLAG_STACK]);
+        return RGS_ERR_CAPACITY;
+    }
+    return RGS_OK;
+}
+
+template <int NC>
+rgs_status pairs_bounce(const rgs_transport *t, bool rows16, const float *Bprev, const __nv_bfloat16 *Bprev16,
+                        const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16, double *norm2, cudaStream_t st) {
+    dim3 grid(t->n, t->C / 3);
+    SceneDev sd = t->sc->dev();
+    if (rows16) {
+        ProfScope ps_("k_bounce_pairs", st);
+        k_bounce_pairs<NC, 3, SliceH<NC>><<<grid, BOUNCE_THREADS, 0, st>>>(sd, t->pair_off, t->pair_rec, t->C, Bprev16,
+                                                                         Bprev, S, Q, Bout, Bout16, norm2);
+    } else {
+        ProfScope ps_("k_bounce_pairs", st);
+        k_bounce_pairs<NC, 3, Slice<NC>><<<grid, BOUNCE_THREADS, 0, st>>>(sd, t->pair_off, t->pair_rec, t->C, Bprev, Bprev,
+                                                                        S, Q, Bout, Bout16, norm2);
+    }
+    RGS_LAUNCH("bounce pairs");
+    return RGS_OK;
+}
+template rgs_status pairs_bounce<1>(const rgs_transport *, bool, const float *, const __nv_bfloat16 *, const float *,
+                                    float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
+template rgs_status pairs_bounce<4>(const rgs_transport *, bool, const float *, const __nv_bfloat16 *, const float *,
+                                    float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
+template rgs_status pairs_bounce<9>(const rgs_transport *, bool, const float *, const __nv_bfloat16 *, const float *,
+                                    float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
+template rgs_status pairs_bounce<16>(const rgs_transport *, bool, const float *, const __nv_bfloat16 *, const float *,
+                                     float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
+
+namespace {
+template <int NC>
+rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float *dad, float *dopo, float *dlam_acc,
+                             cudaStream_t st) {
+    const int n = t->n, C = t->C, nb = t->nb_last;
+    const size_t A = t->arr();
+    SceneDev sd = t->sc->dev();
+    const unsigned ga = (unsigned)((A + 255) / 256);
+    const unsigned gn = (unsigned)((n + 127) / 128);
+    rgs_status r;
+    if ((r = rgs_adjoint_prologue(t, NC, g, st)) != RGS_OK) return r;
+    for (int a = 1; a <= nb; ++a) {
+        { ProfScope ps_("k_adj_src_pairs", st); k_adj_src_pairs<NC><<<n, PAIR_THREADS, 0, st>>>(sd, C, t->src_off, t->tr, t->v + A * (a - 1), t->v + A * a, t->u); }
+        RGS_LAUNCH("adjoint pairs");
+        if (a <= nb - 1 && (r = rgs_pair_accum(t, NC, t->v + A * a, t->Q + A * (nb - 1 - a), st)) != RGS_OK) return r;
+    }
+    if ((r = rgs_shadow_backward(t, NC, st)) != RGS_OK) return r;
+    if (nb >= 1 && (dopo || dlam_acc)) {
+        { ProfScope ps_("k_pair_bwd", st); k_pair_bwd<NC><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, t->lam, A, t->v, t->iters, dopo ? t->dop : nullptr, dlam_acc, t->flags); }
+        RGS_LAUNCH("pair backward");
+    }
+    (void)ga;
+    (void)gn;
+    return rgs_adjoint_finalize(t, NC, dE, dad, dopo, st);
+}
+} // namespace
+
+rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, float *dlam,
+                                  cudaStream_t st) {
+    rgs_status r;
+    const int nb = t->nb_last, n = t->n;
+    const size_t A = t->arr();
+    if (n > t->pg_cap) {
+        if ((r = dev_alloc(&t->Pg, (size_t)n * 12, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->dop, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
+        t->pg_cap = n;
+    }
+    float *dlam_acc = nullptr;
+    struct Scratch {
+        rgs_transport *t;
+        cudaStream_t st;
+        float **dl;
+        ~Scratch() {
+            pool_release(t->v, st);
+            pool_release(t->u, st);
+            pool_release(t->tr, st);
+            pool_release(*dl, st);
+        }
+    } scratch{t, st, &dlam_acc};
+    if ((r = pool_alloc(&t->v, A * (nb + 1), st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&t->u, A, st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&t->tr, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK) return r;
+    if (dlam) {
+        if ((r = pool_alloc(&dlam_acc, (size_t)n, st)) != RGS_OK) return r;
+        RGS_CUDA(cudaMemsetAsync(dlam_acc, 0, sizeof(float) * n, st));
+    }
+    { ProfScope ps_("k_copy_off", st); rgs_copy_offsets(t->src_off, t->cursor, n, st); }
+    { ProfScope ps_("k_pair_src_fill", st); k_pair_src_fill<<<n, 256, 0, st>>>(n, t->pair_off, t->pair_rec, t->cursor, t->tr); }
+    RGS_LAUNCH("pair transposed index");
+    RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));
+    switch (t->nc) {
+    case 1: r = run_adjoint_pairs<1>(t, g, dE, dad, dop, dlam_acc, st); break;
+    case 4: r = run_adjoint_pairs<4>(t, g, dE, dad, dop, dlam_acc, st); break;
+    case 9: r = run_adjoint_pairs<9>(t, g, dE, dad, dop, dlam_acc, st); break;
+    default: r = run_adjoint_pairs<16>(t, g, dE, dad, dop, dlam_acc, st);
+    }
+    if (r != RGS_OK) return r;
+    if (dlam) {
+        { ProfScope ps_("k_lam_out", st); k_lam_out<<<(n + 255) / 256, 256, 0, st>>>(n, t->sc->uid, dlam_acc, dlam); }
+        RGS_LAUNCH("lambda gradient");
+    }
+    return RGS_OK;
+}

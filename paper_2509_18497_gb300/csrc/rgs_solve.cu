@@ -95,9 +95,14 @@ rgs_status run_solve(rgs_transport *t, const float *E, int nb, int precision, cu
         // RESCORR: the last bounce gathers the FP32 rows (one residual-correction sweep)
         const bool rows16 = bf16 && !(precision == RGS_BF16_FP32ACC_RESCORR && b == nb);
         const int sp = t->slot(b - 1), so = t->slot(b);
-        rgs_status r = (wide_bounce(t->C, rows16) ? mc_bounce<NC> : launch_bounce<NC>)(
-            t, sd, rd, rows16, t->iters + A * sp, bf16 ? I16 + A16 * sp : nullptr, t->iters,
-            t->Q + A * (t->stride ? 0 : b - 1), t->iters + A * so, bf16 ? I16 + A16 * so : nullptr, t->norm2 + b, st);
+        rgs_status r;
+        if (t->kind == RGS_KIND_PAIRS)
+            r = pairs_bounce<NC>(t, rows16, t->iters + A * sp, bf16 ? I16 + A16 * sp : nullptr, t->iters,
+                                 t->Q + A * (b - 1), t->iters + A * so, bf16 ? I16 + A16 * so : nullptr, t->norm2 + b, st);
+        else
+            r = (wide_bounce(t->C, rows16) ? mc_bounce<NC> : launch_bounce<NC>)(
+                t, sd, rd, rows16, t->iters + A * sp, bf16 ? I16 + A16 * sp : nullptr, t->iters,
+                t->Q + A * (t->stride ? 0 : b - 1), t->iters + A * so, bf16 ? I16 + A16 * so : nullptr, t->norm2 + b, st);
         if (r != RGS_OK) return r;
     }
     return RGS_OK;
@@ -188,7 +193,8 @@ rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precisio
                           rgs_solve_stats *stats, cudaStream_t st) {
     rgs_status r;
     const size_t A = t->arr();
-    const int stride = t->ckpt_req < 0 ? rgs_auto_stride(t, nb, precision) : t->ckpt_req;
+    // the center-to-center adjoint keeps every iterate (its pairs are few next to the rays)
+    const int stride = t->kind == RGS_KIND_PAIRS ? 0 : (t->ckpt_req < 0 ? rgs_auto_stride(t, nb, precision) : t->ckpt_req);
     if ((r = rgs_solve_prepare(t, nb, precision, stride, st)) != RGS_OK) return r;
     RGS_CUDA(cudaMemsetAsync(t->norm2, 0, sizeof(double) * (RGS_MAX_BOUNCES + 1), st));
     switch (t->nc) {

@@ -184,22 +184,18 @@ static int strata_a(int nd) {
     return na;
 }
 
-rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace_opts *o, cudaStream_t st) {
+// Shared by both transports: the light copies, the per-surfel buffers (flags, D, the
+// per-source counts and offsets of the transposed index) sized for the scene.
+rgs_status rgs_transport_common(rgs_transport *t, const rgs_lights *L, cudaStream_t st) {
     rgs_scene *sc = t->sc;
     const int n = sc->n;
     t->n = n;
     t->L = sc->L;
     t->nc = sc->nc;
-    t->nd = o->nd;
-    t->na = strata_a(o->nd);
-    t->nbs = o->nd / t->na;
-    t->seed = o->seed;
     t->nl = L ? L->n_lights : 0;
     t->C = 3 * (t->nl > 0 ? t->nl : 1);
     t->nb_last = -1;
     rgs_status r;
-    const long long n_rays = (long long)n * o->nd;
-    // lights (device copies)
     if (t->nl > t->lcap) {
         if ((r = dev_alloc(&t->lpos, 3 * (size_t)t->nl, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->lint, 3 * (size_t)t->nl, &t->device_bytes)) != RGS_OK) return r;
@@ -209,26 +205,14 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         RGS_CUDA(cudaMemcpyAsync(t->lpos, L->pos, sizeof(float) * 3 * t->nl, cudaMemcpyDeviceToDevice, st));
         RGS_CUDA(cudaMemcpyAsync(t->lint, L->intensity, sizeof(float) * 3 * t->nl, cudaMemcpyDeviceToDevice, st));
     }
-    // per-ray / per-surfel arrays
-    if (n_rays > t->rays_cap) {
-        if ((r = dev_alloc(&t->cnt, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
-        if ((r = dev_alloc(&t->dir, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
-        if ((r = dev_alloc(&t->off, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
-        t->rays_cap = n_rays;
-    }
     if (!t->counter && (r = dev_alloc(&t->counter, 1, &t->device_bytes)) != RGS_OK) return r;
-    if (!t->ray_ctr && (r = dev_alloc(&t->ray_ctr, 1, &t->device_bytes)) != RGS_OK) return r;
-    if (!t->num_sms) {
-        int dev = 0;
-        RGS_CUDA(cudaGetDevice(&dev));
-        RGS_CUDA(cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    }
     if (!t->flags && (r = dev_alloc(&t->flags, FLAG_COUNT, &t->device_bytes)) != RGS_OK) return r;
     const long long arr = (long long)n * t->C * t->nc;
     if (arr > t->nc_cap) {
         if ((r = dev_alloc(&t->D, (size_t)arr, &t->device_bytes)) != RGS_OK) return r;
         t->nc_cap = arr;
         t->iters_cap = 0; // iterate buffers are sized by the array size: force regrowth
+        t->q_cap = 0;
         t->iters16_cap = 0;
     }
     if (n > t->src_cap) {
@@ -238,6 +222,45 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         t->scan_tmp_cap = rgs_scan_tmp_size(n);
         if ((r = dev_alloc(&t->scan_tmp, (size_t)t->scan_tmp_cap, &t->device_bytes)) != RGS_OK) return r;
         t->src_cap = n;
+    }
+    return RGS_OK;
+}
+
+// D = o c (x) Y(R w) I cos / r^2 T for every (surfel, light), or 0 without lights
+rgs_status rgs_direct_term(rgs_transport *t, cudaStream_t st) {
+    SceneDev sd = t->sc->dev();
+    if (t->nl > 0) {
+        const int nth = t->n * t->nl;
+        switch (t->nc) {
+        case 1: { ProfScope ps_("k_direct", st); k_direct<1><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        case 4: { ProfScope ps_("k_direct", st); k_direct<4><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        case 9: { ProfScope ps_("k_direct", st); k_direct<9><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        default: { ProfScope ps_("k_direct", st); k_direct<16><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); }
+        }
+        RGS_LAUNCH("direct");
+    } else {
+        RGS_CUDA(cudaMemsetAsync(t->D, 0, sizeof(float) * t->arr(), st));
+    }
+    return RGS_OK;
+}
+
+rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace_opts *o, cudaStream_t st) {
+    rgs_scene *sc = t->sc;
+    const int n = sc->n;
+    rgs_status r;
+    t->kind = RGS_KIND_HEMISPHERE;
+    t->nd = o->nd;
+    t->na = strata_a(o->nd);
+    t->nbs = o->nd / t->na;
+    t->seed = o->seed;
+    if ((r = rgs_transport_common(t, L, st)) != RGS_OK) return r;
+    const long long n_rays = (long long)n * o->nd;
+    // per-ray arrays
+    if (n_rays > t->rays_cap) {
+        if ((r = dev_alloc(&t->cnt, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->dir, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->off, (size_t)n_rays, &t->device_bytes)) != RGS_OK) return r;
+        t->rays_cap = n_rays;
     }
 
     long long want = o->hit_capacity > 0 ? o->hit_capacity : (t->cap_slots > 0 ? t->cap_slots : n_rays * 24);
@@ -287,19 +310,7 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
         want = (long long)(used + slack + 1024);
     }
 
-    // direct term
-    if (t->nl > 0) {
-        const int nth = n * t->nl;
-        switch (t->nc) {
-        case 1: { ProfScope ps_("k_direct", st); k_direct<1><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
-        case 4: { ProfScope ps_("k_direct", st); k_direct<4><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
-        case 9: { ProfScope ps_("k_direct", st); k_direct<9><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
-        default: { ProfScope ps_("k_direct", st); k_direct<16><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); }
-        }
-        RGS_LAUNCH("direct");
-    } else {
-        RGS_CUDA(cudaMemsetAsync(t->D, 0, sizeof(float) * (size_t)arr, st));
-    }
+    if ((r = rgs_direct_term(t, st)) != RGS_OK) return r;
 
     // per-source hit counts -> offsets of the transposed index (filled by rgs_adjoint)
     if ((r = rgs_scan_counts(t->src_cnt, t->src_off, n, t->scan_tmp, t->scan_tmp_cap, st)) != RGS_OK) return r;

@@ -29,7 +29,8 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_transport_info_get", "rgs_destroy_transport", "rgs_destroy_scene", "rgs_profile_enable",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
-           "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget")
+           "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_trace_pairs",
+           "rgs_adjoint_pairs")
 
 
 class RgsError(RuntimeError):
@@ -53,6 +54,10 @@ class rgs_lights(ct.Structure):
 
 class rgs_trace_opts(ct.Structure):
     _fields_ = [("nd", ct.c_int32), ("reserved0", ct.c_int32), ("seed", ct.c_uint64), ("hit_capacity", ct.c_int64)]
+
+
+class rgs_pair_opts(ct.Structure):
+    _fields_ = [("lambda_", ct.c_void_p)]
 
 
 class rgs_solve_stats(ct.Structure):
@@ -116,6 +121,10 @@ def load(path=LIB_PATH):
     L.rgs_residual_norm_noalloc.restype = ct.c_int
     L.rgs_set_checkpointing.argtypes = [vp, ct.c_int32]
     L.rgs_set_checkpointing.restype = ct.c_int
+    L.rgs_trace_pairs.argtypes = [vp, ct.POINTER(rgs_lights), ct.POINTER(rgs_pair_opts), vp, ct.POINTER(vp)]
+    L.rgs_trace_pairs.restype = ct.c_int
+    L.rgs_adjoint_pairs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.rgs_adjoint_pairs.restype = ct.c_int
     L.rgs_set_memory_budget.argtypes = [vp, ct.c_int64]
     L.rgs_set_memory_budget.restype = ct.c_int
     L.rgs_trim_workspace.argtypes = []
@@ -218,6 +227,38 @@ def rgs_trace_transport(scene, light_pos, light_I, nd, seed, hit_capacity=0, str
     tr.C = 3 * max(nl, 1)
     tr.nb = -1
     return tr
+
+
+def rgs_trace_pairs(scene, light_pos, light_I, lam=None, stream=None, transport=None):
+    """rgs_trace_pairs (center-to-center transport): lam is a CUDA float32 [N] or None (1)."""
+    L = load()
+    nl = int(light_pos.shape[0])
+    lt = rgs_lights(nl, _dev(light_pos, (nl, 3), "light_pos") if nl else None,
+                    _dev(light_I, (nl, 3), "light_I") if nl else None)
+    opts = rgs_pair_opts(_dev(lam, (scene.n,), "lambda").value if lam is not None else None)
+    tr = transport if transport is not None else Transport(scene)
+    tr.scene = scene
+    h = ct.c_void_p(tr.h.value)
+    _check(L.rgs_trace_pairs(scene.h, ct.byref(lt), ct.byref(opts), _stream(stream), ct.byref(h)))
+    tr.h = h
+    tr.C = 3 * max(nl, 1)
+    tr.nb = -1
+    tr.pairs = True
+    return tr
+
+
+def rgs_adjoint_pairs(transport, dL_dB, stream=None):
+    """rgs_adjoint_pairs: returns (dL/dE, dL/da^d, dL/do, dL/dlambda)."""
+    L = load()
+    n, nc, C = transport.n, transport.nc, transport.C
+    dE = torch.empty((n, nc, 3), device="cuda", dtype=torch.float32)
+    dad = torch.empty((n, 3), device="cuda", dtype=torch.float32)
+    dop = torch.empty((n,), device="cuda", dtype=torch.float32)
+    dlam = torch.empty((n,), device="cuda", dtype=torch.float32)
+    _check(L.rgs_adjoint_pairs(transport.h, _dev(dL_dB, (n, nc, C), "dL_dB"), _dev(dE, (n, nc, 3), "dL_dE"),
+                               _dev(dad, (n, 3), "dL_dalbedo"), _dev(dop, (n,), "dL_dopacity"),
+                               _dev(dlam, (n,), "dL_dlambda"), _stream(stream)))
+    return dE, dad, dop, dlam
 
 
 def rgs_solve(transport, E, n_bounces, B_out=None, stats=False, precision=RGS_FP32, stream=None):

@@ -15,10 +15,11 @@ def rel_l2(a, b):
 
 
 def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=False, precision=rgs.RGS_FP32,
-            checkpoint=0):
-    """build -> trace -> solve (-> adjoint with dL/dB = W) on cuda:0; numpy float64 out."""
+            checkpoint=0, pairs=False):
+    """build -> trace -> solve (-> adjoint with dL/dB = W) on cuda:0; numpy float64 out.
+    pairs: the center-to-center transport (the adjoint then also returns dlam)."""
     d = api.upload(sc)
-    pipe = api.Pipeline(alpha_model, precision, checkpoint=checkpoint)
+    pipe = api.Pipeline(alpha_model, precision, checkpoint=checkpoint, pairs=pairs)
     pipe.build(d)
     pipe.trace(d)
     B, st = pipe.solve(d["E"], d["nb"], stats=stats)
@@ -27,15 +28,20 @@ def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=F
         out["iters"] = [rgs.rgs_get_iterate(pipe.transport, b).double().cpu().numpy() for b in range(d["nb"] + 1)]
     if W is not None:
         g = torch.as_tensor(np.ascontiguousarray(W, np.float32), device="cuda")
-        dE, dad, dop = pipe.adjoint(g)
+        if pairs:
+            dE, dad, dop, dlam = pipe.adjoint_pairs(g)
+            out["dlam"] = dlam.double().cpu().numpy()
+        else:
+            dE, dad, dop = pipe.adjoint(g)
         out.update(dE=dE.double().cpu().numpy(), dad=dad.double().cpu().numpy(), dop=dop.double().cpu().numpy())
     out["info"] = rgs.rgs_transport_info_get(pipe.transport)
     torch.cuda.synchronize()
     return out
 
 
-def run_oracle(sc, W=None, alpha_model=O.ALPHA_GAUSS, iterates=False):
-    orc = O.Oracle(sc, alpha_model=alpha_model).transport()
+def run_oracle(sc, W=None, alpha_model=O.ALPHA_GAUSS, iterates=False, pairs=False):
+    orc = O.Oracle(sc, alpha_model=alpha_model)
+    orc = orc.pairs(lam=sc.get("lam")) if pairs else orc.transport()
     out = dict(orc=orc)
     if iterates:
         B, it = orc.solve(E=sc["E"], nb=sc["nb"], iters=True)
