@@ -101,7 +101,8 @@ def _launch_bytes(kernel, sc):
         "k_pair_fill": (n * 64 + (n - 1) * 64 + H * 8, 1),
         "k_bounce_pairs": (H * 8 + 4 * A, nb),
         "k_adj_src_pairs": (H * 8 + 3 * A, nb),
-        "k_pair_bwd": (H * 8 + 2 * min(nb, 64) * A, 1),
+        "k_pair_g": (H * (8 + 4) + 2 * nb * A, 1),
+        "k_pair_grad": (n * 64 + (n - 1) * 64 + H * 4 + n * 8, 1),
         # per 32-column tile: records, counts, offsets, directions; the iterate rows once
         "k_bounce_mc": (tiles * (H * 8 + rays * (4 + 8 + 16)) + A16 + 4 * A + A16, nb),
         # one tile and up to four iterates: records + ray data; v (FP32) and B (BF16) tiles; g per hit
@@ -451,7 +452,7 @@ def main():
                 "k_bounce_mc": "rgs_manycol.cu", "k_opacity_g_mc": "rgs_manycol.cu", "k_adj_src_mc": "rgs_manycol.cu",
                 "k_opacity_g": "rgs_adjoint.cu", "k_opacity_rec": "rgs_adjoint.cu",
                 "k_bounce_persistent": "rgs_batch.cu", "k_trace_hemi": "rgs_trace.cu",
-                "k_pair_fill": "rgs_pairs.cu", "k_bounce_pairs": "rgs_pairs.cu"}.get(dom)
+                "k_pair_fill": "rgs_pairs.cu", "k_bounce_pairs": "rgs_pairs.cu", "k_pair_grad": "rgs_pairs.cu"}.get(dom)
     traffic = None
     if len(scs) == 1 and dom in NCU_TRAFFIC and src_file and NCU_TRAFFIC[dom]["src_sha"] == _src_sha(src_file):
         traffic = NCU_TRAFFIC[dom]["bytes_per_launch"] * (scs[0]["n"] / NCU_TRAFFIC[dom]["n"])

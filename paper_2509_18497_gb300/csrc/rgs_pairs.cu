@@ -245,26 +245,21 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_adj_src_pairs(SceneDev sc, int
     }
 }
 
-// Source-side gradients of every pair (i -> j): with g = dL/dV_ji summed over the bounces,
-//   g = sum_{a<n} sum_c y_i^(a)[c] Y(-d) . B_j^(n-1-a)[c],
-//   dL/dlambda_j += g A_j T geo,  dL/do_j += g lambda_j (A_j/o_j) T geo,
-//   dL/do_k += -g lambda_j A_j geo prod_{m != k}(1 - alpha_m) G_k for the segment's occluders
-// (the segment is traced again: once for T and the zero factors, once for the occluders).
+// g_e = dL/dV_ji of every pair e = (i -> j), summed over the bounces:
+//   g = o_i sum_{a<n} sum_c (c_i (x) Y(R_i d) . v_i^(a)[c]) (Y(-d) . B_j^(n-1-a)[c])
 template <int NC>
-__global__ void __launch_bounds__(PAIR_THREADS) k_pair_bwd(SceneDev sc, int C, int nb, const long long *__restrict__ pair_off,
-                                                          const int2 *__restrict__ rec, const float *__restrict__ lam,
-                                                          size_t A, const float *__restrict__ V,
-                                                          const float *__restrict__ Bit, float *dop, float *dlam,
-                                                          int *flags) {
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int nb, const long long *__restrict__ pair_off,
+                                                        const int2 *__restrict__ rec, size_t A,
+                                                        const float *__restrict__ V, const float *__restrict__ Bit,
+                                                        float *gpair) {
     const int i = blockIdx.x;
     const float4 Pi = __ldg(&sc.P[i]);
     const float3 pi = f3(Pi), ni = f3(sc.N4[i]);
-    const float eps = *sc.eps_plane;
     for (long long e = pair_off[i] + threadIdx.x; e < pair_off[i + 1]; e += PAIR_THREADS) {
         const int j = __ldg(&rec[e]).x;
-        const float3 pj = f3(sc.P[j]);
+        const float4 Pj = __ldg(&sc.P[j]);
         float r;
-        const float3 d = unit_dir(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), r);
+        const float3 d = unit_dir(make_float3(Pj.x - pi.x, Pj.y - pi.y, Pj.z - pi.z), r);
         float Yi[NC], Yo[NC];
         sh_eval<NC>(reflect_n(ni, d), Yi);
         sh_eval<NC>(neg3(d), Yo);
@@ -283,38 +278,68 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_bwd(SceneDev sc, int C, i
                 g += y * s;
             }
         }
-        g *= Pi.w;
-        if (g == 0.f) continue;
-        const float Au = alpha_area_unit(sc, j);
-        const float oj = __ldg(&sc.P[j].w), lj = __ldg(&lam[j]);
-        const float geo = fabsf(dot3(ni, d)) * fabsf(dot3(f3(sc.N4[j]), d)) / (r * r);
-        float Tnz = 1.f;
-        int nzero = 0;
-        auto pass1 = [&](int k) {
-            float gk;
-            if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
-            const float om = 1.f - __ldg(&sc.P[k].w) * gk;
-            if (om == 0.f) ++nzero;
-            else Tnz *= om;
-        };
-        if (!bvh_traverse(sc, pi, d, r, pass1)) atomicAdd(&flags[FLAG_STACK], 1);
-        const float T = nzero ? 0.f : Tnz;
-        if (dlam) atomicAdd(&dlam[j], g * oj * Au * T * geo);
-        if (!dop) continue;
-        if (T != 0.f) atomicAdd(&dop[j], g * lj * Au * T * geo);
-        if (nzero > 1) continue;
-        const float q = -g * lj * oj * Au * geo;
-        auto pass2 = [&](int k) {
-            float gk;
-            if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
-            const float om = 1.f - __ldg(&sc.P[k].w) * gk;
-            float others;
-            if (nzero == 0) others = Tnz / om;
-            else others = (om == 0.f) ? Tnz : 0.f;
-            if (others != 0.f) atomicAdd(&dop[k], q * others * gk);
-        };
-        bvh_traverse(sc, pi, d, r, pass2);
+        gpair[e] = g * Pi.w;
     }
+}
+
+// Source-side gradients of every pair, laid out as the fill pass (one block per receiver
+// and 256-source chunk, a thread per source, so a warp's segments leave one centre towards
+// neighbouring sources):
+//   dL/dlambda_j += g A_j T geo,  dL/do_j += g lambda_j (A_j/o_j) T geo,
+//   dL/do_k += -g lambda_j A_j geo prod_{m != k}(1 - alpha_m) G_k for the segment's occluders
+// (the segment is traced again: once for T and the zero factors, once for the occluders).
+__global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunks, const long long *__restrict__ chunk_off,
+                                                   const float *__restrict__ lam, const float *__restrict__ gpair,
+                                                   float *dop, float *dlam, int *flags) {
+    __shared__ int warp_base[PCH / 32];
+    const int blk = blockIdx.x;
+    const int i = blk / chunks, c = blk - i * chunks;
+    const int j = c * PCH + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float eps = *sc.eps_plane;
+    const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
+    float3 dv;
+    const bool front = j < n && j != i && pair_front(sc, pi, ni, j, eps, dv);
+    const unsigned bal = __ballot_sync(0xffffffffu, front);
+    if (lane == 0) warp_base[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < warp; ++w) base += warp_base[w];
+    if (!front) return;
+    const float g = gpair[chunk_off[blk] + base + __popc(bal & ((1u << lane) - 1u))];
+    if (g == 0.f) return;
+    float r;
+    const float3 d = unit_dir(dv, r);
+    const float3 pj = f3(sc.P[j]);
+    const float Au = alpha_area_unit(sc, j);
+    const float oj = __ldg(&sc.P[j].w), lj = __ldg(&lam[j]);
+    const float geo = fabsf(dot3(ni, d)) * fabsf(dot3(f3(sc.N4[j]), d)) / (r * r);
+    float Tnz = 1.f;
+    int nzero = 0;
+    auto pass1 = [&](int k) {
+        float gk;
+        if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
+        const float om = 1.f - __ldg(&sc.P[k].w) * gk;
+        if (om == 0.f) ++nzero;
+        else Tnz *= om;
+    };
+    if (!bvh_traverse(sc, pi, d, r, pass1)) atomicAdd(&flags[FLAG_STACK], 1);
+    const float T = nzero ? 0.f : Tnz;
+    if (dlam) atomicAdd(&dlam[j], g * oj * Au * T * geo);
+    if (!dop) return;
+    if (T != 0.f) atomicAdd(&dop[j], g * lj * Au * T * geo);
+    if (nzero > 1) return;
+    const float q = -g * lj * oj * Au * geo;
+    auto pass2 = [&](int k) {
+        float gk;
+        if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
+        const float om = 1.f - __ldg(&sc.P[k].w) * gk;
+        float others;
+        if (nzero == 0) others = Tnz / om;
+        else others = (om == 0.f) ? Tnz : 0.f;
+        if (others != 0.f) atomicAdd(&dop[k], q * others * gk);
+    };
+    bvh_traverse(sc, pi, d, r, pass2);
 }
 
 __global__ void k_lam_out(int n, const int *__restrict__ uid, const float *__restrict__ dlam, float *out) {
@@ -428,7 +453,9 @@ rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float 
     }
     if ((r = rgs_shadow_backward(t, NC, st)) != RGS_OK) return r;
     if (nb >= 1 && (dopo || dlam_acc)) {
-        { ProfScope ps_("k_pair_bwd", st); k_pair_bwd<NC><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, t->lam, A, t->v, t->iters, dopo ? t->dop : nullptr, dlam_acc, t->flags); }
+        const int chunks = (n + PCH - 1) / PCH;
+        { ProfScope ps_("k_pair_g", st); k_pair_g<NC><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh); }
+        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->gh, dopo ? t->dop : nullptr, dlam_acc, t->flags); }
         RGS_LAUNCH("pair backward");
     }
     (void)ga;
@@ -456,12 +483,15 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
             pool_release(t->v, st);
             pool_release(t->u, st);
             pool_release(t->tr, st);
+            pool_release(t->gh, st);
             pool_release(*dl, st);
         }
     } scratch{t, st, &dlam_acc};
     if ((r = pool_alloc(&t->v, A * (nb + 1), st)) != RGS_OK) return r;
     if ((r = pool_alloc(&t->u, A, st)) != RGS_OK) return r;
     if ((r = pool_alloc(&t->tr, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK) return r;
+    if ((dop || dlam) && nb >= 1 && (r = pool_alloc(&t->gh, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK)
+        return r; // g per pair
     if (dlam) {
         if ((r = pool_alloc(&dlam_acc, (size_t)n, st)) != RGS_OK) return r;
         RGS_CUDA(cudaMemsetAsync(dlam_acc, 0, sizeof(float) * n, st));
