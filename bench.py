@@ -47,6 +47,9 @@ LARGE_WORKLOAD = ("large scene: 1,000,000 surfels (fruit bowl scaled x4 inside a
 PAIRS_WORKLOAD = ("center-to-center approximation (one segment per pair of surfel centres, Sec. 8): fruit bowl, "
                   "20,000 surfels, SH degree 3, 4 bounces, 1 point light, forward + adjoint with the lambda gradient "
                   "left out (the rgs_adjoint outputs)")
+ENV_WORKLOAD = ("environment map: fruit bowl, 50,000 surfels, SH degree 3, 256 rays/surfel, 4 bounces, lit by a "
+                "16 x 32 latitude-longitude map of directional lights (512 lights, 1,536 right-hand sides), "
+                "forward + adjoint")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -261,11 +264,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=50000, help="surfel count (default: the 50,000-surfel workload)")
-    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven", "large", "pairs"],
+    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven", "large", "pairs", "envmap"],
                     help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights; "
                          "uneven: 32 scenes of uneven size in one persistent launch; large: 1,000,000 surfels, "
                          "512 rays, 6 bounces, 16 lights, checkpointed iterates; pairs: the center-to-center "
-                         "approximation on a 20,000-surfel bowl")
+                         "approximation on a 20,000-surfel bowl; envmap: the 50,000-surfel bowl under a 16 x 32 "
+                         "environment map of directional lights (1,536 columns)")
     ap.add_argument("--scenes", type=int, default=32, help="uneven workload: number of scenes (profiling cases)")
     ap.add_argument("--scale", type=float, default=1.0, help="uneven workload: surfel-count factor (profiling cases)")
     ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
@@ -301,6 +305,9 @@ def main():
     elif args.workload == "pairs":
         scs = [scenes.fruit_bowl(n=20000 if args.n == 50000 else args.n)]
         workload = PAIRS_WORKLOAD
+    elif args.workload == "envmap":
+        scs = [scenes.with_env_map(scenes.fruit_bowl(n=args.n))]
+        workload = ENV_WORKLOAD
     elif args.workload == "large":
         scs = [scenes.large_scene(n=1000000 if args.n == 50000 else args.n)]
         workload = LARGE_WORKLOAD
@@ -322,7 +329,7 @@ def main():
     # Each form is built, warmed up and timed in turn; the large scene releases one form's
     # device memory before building the next (both would not fit at once).
     batched_launch = "batched" if len(scs) > 1 else "per_scene"
-    sequential = args.workload == "large"
+    sequential = args.workload in ("large", "envmap")
     ckpt = -1 if args.workload == "large" else 0
     specs = {"plain": (rgs.RGS_FP32, "per_scene"), "batched": (rgs.RGS_BF16_FP32ACC_RESCORR, batched_launch)}
 

@@ -100,9 +100,15 @@ typedef struct rgs_build_opts {
 
 /* Point lights (Sec. 5.1 "Lighting", Sec. 5.3): infinitesimal emitters sampled at their
  * centre, isotropic, intensity I (RGB) so that the received radiance is I / r^2.
- * Device pointers pos[NL][3], intensity[NL][3]; NL may be 0. */
+ * Directional lights (directional != 0; Sec. 5.1: "far away" point lights without the
+ * inverse-square falloff, and the 16 x 32 environment map of Sec. 9 as such lights): pos
+ * is the direction towards the light (any length), intensity the irradiance it gives a
+ * surface facing it, no 1/r^2, and shadow rays run to infinity.
+ * Device pointers pos[NL][3], intensity[NL][3]; NL may be 0.  All lights of a call are of
+ * one kind. */
 typedef struct rgs_lights {
     int32_t n_lights;
+    int32_t directional;
     const float *pos;
     const float *intensity;
 } rgs_lights;

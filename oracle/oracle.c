@@ -12,7 +12,8 @@
  *   Sec. 3.2         real SH basis, ordering [Y00, Y1-1, Y10, Y11, ...], Ybar(w)=Y(-w)
  *   Eq. sh-brdf      SH expansion of a reciprocal BRDF, c_lm = (-1)^m c_l0
  *   Eq. brdf         diffuse + Phong mixture;  App. A  closed-form coefficients
- *   Eq. primal (DI)  direct illumination, Sec. 5.2;  light = infinitesimal surfel (Sec. 5.3)
+ *   Eq. primal (DI)  direct illumination, Sec. 5.2;  light = infinitesimal surfel (Sec. 5.3);
+ *                    directional lights (an environment map as distant lights, Sec. 5.1)
  *   Eq. before-final-radiosity / final-radiosity (Sec. 5.3), solid-angle form App. B
  *   Eq. final_dL_dE  adjoint (dual) transport (Sec. 6, App. C)
  *   Eq. final-dl-dbrdf closed-form BRDF gradient (limit n -> infinity)
@@ -143,6 +144,7 @@ typedef struct {
     int *sh_j;
     double *sh_alpha, *sh_G;
     double *sh_pre; /* [n*nl] = Y-free prefactor I*cos/r^2 (0 if back-facing) */
+    int ldir; /* lights are directional: lp holds directions towards them, no 1/r^2 */
     /* center-to-center transport (pmode = 1): per receiver i the pairs (i, j) */
     int pmode;
     double *lam;                  /* [n] lambda_j */
@@ -530,6 +532,26 @@ static void reflect(const double *n, const double *d, double *r) { /* R d = 2 (n
     for (int q = 0; q < 3; ++q) r[q] = 2.0 * nd * n[q] - d[q];
 }
 
+/* Light lt seen from surfel i: unit direction w towards it, distance r (infinite for a
+ * directional light) and the Y-free factor cos/r^2 (cos alone for a directional light,
+ * whose intensity is the irradiance on a surface facing it); 0 when the light is behind. */
+static double light_geom(const or_scene *s, int i, const double *pl, double *w, double *r) {
+    double l[3];
+    if (s->ldir) {
+        for (int q = 0; q < 3; ++q) l[q] = pl[q];
+    } else {
+        for (int q = 0; q < 3; ++q) l[q] = pl[q] - s->p[i * 3 + q];
+    }
+    double len = sqrt(dot3(l, l));
+    for (int q = 0; q < 3; ++q) w[q] = l[q] / len;
+    *r = s->ldir ? INFINITY : len;
+    double cs = dot3(s->nrm + i * 3, w);
+    if (!(cs > 0.0)) return 0.0; /* only the front hemisphere Omega receives */
+    return s->ldir ? cs : cs / (len * len);
+}
+
+void or_set_directional(or_scene *s, int directional) { s->ldir = directional ? 1 : 0; }
+
 /* Direct term (Sec. 5.2) of every receiver: Dgeo (the direct term without the o_i c_i
  * factor) and the shadow-ray hit lists kept for the opacity backward. */
 static void direct_term(or_scene *s, int nl, const double *lp, const double *li) {
@@ -544,18 +566,14 @@ static void direct_term(or_scene *s, int nl, const double *lp, const double *li)
     for (int i = 0; i < n; ++i) {
         double Y[1024];
         for (int lt = 0; lt < nl; ++lt) {
-            const double *pl = lp + lt * 3;
-            double l[3] = {pl[0] - s->p[i * 3], pl[1] - s->p[i * 3 + 1], pl[2] - s->p[i * 3 + 2]};
-            double r = sqrt(dot3(l, l));
-            double w[3] = {l[0] / r, l[1] / r, l[2] / r};
-            double cs = dot3(s->nrm + i * 3, w);
+            double w[3], r;
+            const double pre = light_geom(s, i, lp + lt * 3, w, &r);
             s->sh_pre[(long)i * nl + lt] = 0.0;
-            if (!(cs > 0.0)) continue; /* only the front hemisphere Omega receives */
+            if (pre == 0.0) continue;
             hitvec *hv = &sper[(long)i * nl + lt];
             trace_all(s, i, s->p + i * 3, w, r, hv);
             double T = 1.0;
             for (int q = 0; q < hv->cnt; ++q) T *= (1.0 - hv->h[q].alpha);
-            double pre = cs / (r * r);
             s->sh_pre[(long)i * nl + lt] = pre;
             double rw[3];
             reflect(s->nrm + i * 3, w, rw);
@@ -1122,10 +1140,8 @@ void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, dou
                 long q0 = s->sh_off[(long)i * nl + lt], q1 = s->sh_off[(long)i * nl + lt + 1];
                 double pre = s->sh_pre[(long)i * nl + lt];
                 if (q1 == q0 || pre == 0.0) continue;
-                const double *pl = s->lp + lt * 3;
-                double l[3] = {pl[0] - s->p[i * 3], pl[1] - s->p[i * 3 + 1], pl[2] - s->p[i * 3 + 2]};
-                double r = sqrt(dot3(l, l));
-                double wv[3] = {l[0] / r, l[1] / r, l[2] / r}, rw[3];
+                double wv[3], rw[3], r;
+                light_geom(s, i, s->lp + lt * 3, wv, &r);
                 reflect(s->nrm + i * 3, wv, rw);
                 or_sh_eval(L, rw, Yi);
                 double qv = 0.0;
@@ -1236,12 +1252,9 @@ void or_sample_direct(const or_scene *s, int nl, const double *lp, const double 
         hitvec hv = {0};
         for (int kk = 0; kk < nc * C; ++kk) out[(size_t)q * nc * C + kk] = 0.0;
         for (int lt = 0; lt < nl; ++lt) {
-            const double *pl = lp + lt * 3;
-            double l[3] = {pl[0] - s->p[i * 3], pl[1] - s->p[i * 3 + 1], pl[2] - s->p[i * 3 + 2]};
-            double r = sqrt(dot3(l, l));
-            double w[3] = {l[0] / r, l[1] / r, l[2] / r};
-            double cs = dot3(s->nrm + i * 3, w);
-            if (!(cs > 0.0)) continue;
+            double w[3], r;
+            const double pre = light_geom(s, i, lp + lt * 3, w, &r);
+            if (pre == 0.0) continue;
             trace_all(s, i, s->p + i * 3, w, r, &hv);
             double T = 1.0;
             for (int e = 0; e < hv.cnt; ++e) T *= (1.0 - hv.h[e].alpha);
@@ -1251,7 +1264,7 @@ void or_sample_direct(const or_scene *s, int nl, const double *lp, const double 
             for (int kk = 0; kk < nc; ++kk)
                 for (int ch = 0; ch < 3; ++ch)
                     out[((size_t)q * nc + kk) * C + lt * 3 + ch] =
-                        s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + ch] * Y[kk] * li[lt * 3 + ch] * cs / (r * r) * T;
+                        s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + ch] * Y[kk] * li[lt * 3 + ch] * pre * T;
         }
         free(hv.h);
     }

@@ -73,6 +73,7 @@ def lib():
             L.or_apply_KT.argtypes = [ct.c_void_p, _dp, _dp]
             L.or_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
             L.or_adjoint.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.or_set_directional.argtypes = [ct.c_void_p, ct.c_int]
             L.or_pairs.restype = ct.c_int
             L.or_pairs.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
             L.or_num_pairs.restype = ct.c_long
@@ -142,6 +143,7 @@ class Oracle:
         self.h = L.or_scene_new(self.n, self.L, *[_ptr(a) for a in self._keep], int(alpha_model), int(use_bvh))
         if not self.h:
             raise ValueError("oracle: invalid scene")
+        L.or_set_directional(self.h, 1 if sc.get("light_dir") else 0)
         self.C = None
 
     def __del__(self):

@@ -22,6 +22,7 @@ def upload(sc, device="cuda"):
                                                                      device=device)
     for key in ("L", "nd", "nb", "seed", "n"):
         out[key] = int(sc[key])
+    out["light_dir"] = bool(sc.get("light_dir", False))
     return out
 
 
@@ -49,11 +50,12 @@ class Pipeline:
     def trace(self, d, stream=None, hit_capacity=0):
         if self.pairs:
             self.transport = rgs.rgs_trace_pairs(self.scene, d["light_pos"], d["light_I"], lam=d.get("lam"),
-                                                 stream=stream, transport=self.transport)
+                                                 stream=stream, transport=self.transport,
+                                                 directional=d.get("light_dir", False))
         else:
             self.transport = rgs.rgs_trace_transport(self.scene, d["light_pos"], d["light_I"], d["nd"], d["seed"],
                                                      hit_capacity=hit_capacity, stream=stream,
-                                                     transport=self.transport)
+                                                     transport=self.transport, directional=d.get("light_dir", False))
         rgs.rgs_set_checkpointing(self.transport, self.checkpoint)
         rgs.rgs_set_memory_budget(self.transport, self.mem_budget)
         return self.transport

@@ -127,16 +127,15 @@ __global__ void RGS_ADJ_LB k_adj_src(RaysDev rays, int C, int col0, const long l
 // Shadow rays: dL/dT_L = q = sum_{k,ch} u_i[L,ch][k] o_i c_{i,l,ch} Y_k(R_i w) I cos/r^2,
 // dT/dalpha_m = -prod_{m' != m} (1 - alpha_m'); also adds u (x) Dgeo to P.
 template <int NC>
-__global__ void k_shadow_bwd(SceneDev sc, int nl, const float *__restrict__ lpos, const float *__restrict__ lint, int C,
-                             const float *__restrict__ u, float *P, float *dop) {
+__global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restrict__ lpos, const float *__restrict__ lint,
+                             int C, const float *__restrict__ u, float *P, float *dop) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= sc.n * nl) return;
     const int i = tid / nl, lt = tid - i * nl;
     const float4 Pi = sc.P[i];
     const float3 o = f3(Pi), n = f3(sc.N4[i]);
-    const float3 l = make_float3(lpos[3 * lt] - o.x, lpos[3 * lt + 1] - o.y, lpos[3 * lt + 2] - o.z);
-    const float r = sqrtf(dot3(l, l));
-    const float3 w = (1.f / r) * l;
+    float r, fall;
+    const float3 w = light_dir(lpos, lt, o, ldir, r, fall);
     const float cs = dot3(n, w);
     if (!(cs > 0.f)) return;
     const float eps = *sc.eps_plane;
@@ -153,7 +152,7 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, const float *__restrict__ lpos
     const float T = nzero ? 0.f : Tnz;
     float Y[NC];
     sh_eval<NC>(reflect_n(n, w), Y);
-    const float pre = cs / (r * r);
+    const float pre = cs * fall;
     const float *ui = u + ((size_t)i * C + lt * 3) * NC;
     float qv = 0.f;
     float acc[4][3] = {};
@@ -503,7 +502,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     if (nb >= 1 && (r = KT(nb)) != RGS_OK) return r; // v^(n) only adds to u
     if (t->nl > 0) {
         const int nth = n * t->nl;
-        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, C, t->u, t->Pg, t->dop); }
+        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, C, t->u, t->Pg, t->dop); }
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
@@ -543,7 +542,7 @@ template <int NC> rgs_status accum_nc(rgs_transport *t, const float *X, const fl
 template <int NC> rgs_status shadow_nc(rgs_transport *t, cudaStream_t st) {
     if (t->nl <= 0) return RGS_OK;
     const int nth = t->n * t->nl;
-    { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->nl, t->lpos, t->lint, t->C, t->u, t->Pg, t->dop); }
+    { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->nl, t->ldir, t->lpos, t->lint, t->C, t->u, t->Pg, t->dop); }
     RGS_LAUNCH("shadow backward");
     return RGS_OK;
 }

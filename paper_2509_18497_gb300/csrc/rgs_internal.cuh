@@ -106,6 +106,20 @@ __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_fl
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float3 neg3(float3 a) { return make_float3(-a.x, -a.y, -a.z); }
 
+// Light lt seen from o: the unit direction w towards it, its distance r (infinite for a
+// directional light, whose lpos is the direction towards it) and the falloff 1/r^2 (1 for a
+// directional light: Sec. 5.1 puts such lights far away without the inverse-square falloff)
+__device__ __forceinline__ float3 light_dir(const float *__restrict__ lpos, int lt, float3 o, int ldir, float &r,
+                                           float &fall) {
+    const float3 l = ldir ? make_float3(lpos[3 * lt], lpos[3 * lt + 1], lpos[3 * lt + 2])
+                          : make_float3(lpos[3 * lt] - o.x, lpos[3 * lt + 1] - o.y, lpos[3 * lt + 2] - o.z);
+    const float len = sqrtf(l.x * l.x + l.y * l.y + l.z * l.z);
+    r = ldir ? INFINITY : len;
+    fall = ldir ? 1.f : 1.f / (len * len);
+    const float inv = 1.f / len;
+    return make_float3(l.x * inv, l.y * inv, l.z * inv);
+}
+
 // mirror of d about the normal n: R d = 2 (n.d) n - d (places the Phong lobe, Eq. sh-brdf)
 __device__ __forceinline__ float3 reflect_n(float3 n, float3 d) {
     float s = 2.f * dot3(n, d);
@@ -472,6 +486,7 @@ struct rgs_transport {
     int nd = 0, na = 1, nbs = 1;
     unsigned long long seed = 0;
     int nl = 0, C = 3;
+    int ldir = 0; // directional lights (lpos = directions towards them)
     float *lpos = nullptr, *lint = nullptr;
     int lcap = 0;
     // center-to-center pairs: receiver i's pairs at pair_off[i] .. pair_off[i+1], each

@@ -143,17 +143,17 @@ __global__ void __launch_bounds__(128, RGS_TRACE_MINB) k_trace_hemi(SceneDev sc,
 }
 
 // Direct term (Sec. 5.2): D_i[L*3+ch][k] = o_i c_{i,l(k),ch} Y_k(R_i w) I_{L,ch} (n_i.w)/r^2 T
+// (no 1/r^2 and a shadow ray to infinity for a directional light)
 template <int NC>
-__global__ void k_direct(SceneDev sc, int nl, const float *__restrict__ lpos, const float *__restrict__ lint, int C,
-                         float *D, int *flags) {
+__global__ void k_direct(SceneDev sc, int nl, int ldir, const float *__restrict__ lpos, const float *__restrict__ lint,
+                         int C, float *D, int *flags) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= sc.n * nl) return;
     const int i = tid / nl, lt = tid - i * nl;
     const float4 Pi = sc.P[i];
     const float3 o = f3(Pi), n = f3(sc.N4[i]);
-    const float3 l = make_float3(lpos[3 * lt] - o.x, lpos[3 * lt + 1] - o.y, lpos[3 * lt + 2] - o.z);
-    const float r = sqrtf(dot3(l, l));
-    const float3 w = (1.f / r) * l;
+    float r, fall;
+    const float3 w = light_dir(lpos, lt, o, ldir, r, fall);
     const float cs = dot3(n, w);
     float *Dout = D + ((size_t)i * C + lt * 3) * NC;
     if (!(cs > 0.f)) {
@@ -169,7 +169,7 @@ __global__ void k_direct(SceneDev sc, int nl, const float *__restrict__ lpos, co
     if (!bvh_traverse(sc, o, w, r, visit)) atomicAdd(&flags[FLAG_STACK], 1);
     float Y[NC];
     sh_eval<NC>(reflect_n(n, w), Y);
-    const float pre = Pi.w * cs / (r * r) * T;
+    const float pre = Pi.w * cs * fall * T;
     for (int ch = 0; ch < 3; ++ch) {
         const float I = lint[3 * lt + ch];
         for (int k = 0; k < NC; ++k) Dout[ch * NC + k] = sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch] * Y[k] * I * pre;
@@ -193,6 +193,7 @@ rgs_status rgs_transport_common(rgs_transport *t, const rgs_lights *L, cudaStrea
     t->L = sc->L;
     t->nc = sc->nc;
     t->nl = L ? L->n_lights : 0;
+    t->ldir = (L && L->directional) ? 1 : 0;
     t->C = 3 * (t->nl > 0 ? t->nl : 1);
     t->nb_last = -1;
     rgs_status r;
@@ -232,10 +233,10 @@ rgs_status rgs_direct_term(rgs_transport *t, cudaStream_t st) {
     if (t->nl > 0) {
         const int nth = t->n * t->nl;
         switch (t->nc) {
-        case 1: { ProfScope ps_("k_direct", st); k_direct<1><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
-        case 4: { ProfScope ps_("k_direct", st); k_direct<4><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
-        case 9: { ProfScope ps_("k_direct", st); k_direct<9><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); } break;
-        default: { ProfScope ps_("k_direct", st); k_direct<16><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->lpos, t->lint, t->C, t->D, t->flags); }
+        case 1: { ProfScope ps_("k_direct", st); k_direct<1><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        case 4: { ProfScope ps_("k_direct", st); k_direct<4><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        case 9: { ProfScope ps_("k_direct", st); k_direct<9><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, t->C, t->D, t->flags); } break;
+        default: { ProfScope ps_("k_direct", st); k_direct<16><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, t->C, t->D, t->flags); }
         }
         RGS_LAUNCH("direct");
     } else {

@@ -49,7 +49,7 @@ class rgs_build_opts(ct.Structure):
 
 
 class rgs_lights(ct.Structure):
-    _fields_ = [("n_lights", ct.c_int32), ("pos", ct.c_void_p), ("intensity", ct.c_void_p)]
+    _fields_ = [("n_lights", ct.c_int32), ("directional", ct.c_int32), ("pos", ct.c_void_p), ("intensity", ct.c_void_p)]
 
 
 class rgs_trace_opts(ct.Structure):
@@ -212,12 +212,18 @@ def rgs_build_scene(p, tu, tv, s, o, ad, k, as_, shin, sh_degree, alpha_model=RG
     return sc
 
 
-def rgs_trace_transport(scene, light_pos, light_I, nd, seed, hit_capacity=0, stream=None, transport=None):
-    """rgs_trace_transport: light_pos / light_I are CUDA float32 [NL,3] (NL may be 0)."""
-    L = load()
+def _lights(light_pos, light_I, directional):
     nl = int(light_pos.shape[0])
-    lt = rgs_lights(nl, _dev(light_pos, (nl, 3), "light_pos") if nl else None,
-                    _dev(light_I, (nl, 3), "light_I") if nl else None)
+    return nl, rgs_lights(nl, 1 if directional else 0, _dev(light_pos, (nl, 3), "light_pos") if nl else None,
+                          _dev(light_I, (nl, 3), "light_I") if nl else None)
+
+
+def rgs_trace_transport(scene, light_pos, light_I, nd, seed, hit_capacity=0, stream=None, transport=None,
+                        directional=False):
+    """rgs_trace_transport: light_pos / light_I are CUDA float32 [NL,3] (NL may be 0); directional:
+    light_pos holds directions towards distant lights (no 1/r^2)."""
+    L = load()
+    nl, lt = _lights(light_pos, light_I, directional)
     opts = rgs_trace_opts(int(nd), 0, int(seed), int(hit_capacity))
     tr = transport if transport is not None else Transport(scene)
     tr.scene = scene
@@ -229,12 +235,10 @@ def rgs_trace_transport(scene, light_pos, light_I, nd, seed, hit_capacity=0, str
     return tr
 
 
-def rgs_trace_pairs(scene, light_pos, light_I, lam=None, stream=None, transport=None):
+def rgs_trace_pairs(scene, light_pos, light_I, lam=None, stream=None, transport=None, directional=False):
     """rgs_trace_pairs (center-to-center transport): lam is a CUDA float32 [N] or None (1)."""
     L = load()
-    nl = int(light_pos.shape[0])
-    lt = rgs_lights(nl, _dev(light_pos, (nl, 3), "light_pos") if nl else None,
-                    _dev(light_I, (nl, 3), "light_I") if nl else None)
+    nl, lt = _lights(light_pos, light_I, directional)
     opts = rgs_pair_opts(_dev(lam, (scene.n,), "lambda").value if lam is not None else None)
     tr = transport if transport is not None else Transport(scene)
     tr.scene = scene

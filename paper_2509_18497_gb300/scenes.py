@@ -342,6 +342,35 @@ def large_scene(n=1000000, seed=0, L=3, nd=512, nb=6, n_lights=16, scale=4.0, ro
     return _finish(sc, L, nd, nb, seed, lp, li, name=f"large_{n}")
 
 
+def env_map(n_theta=16, n_phi=32, sun=(0.35, 0.8, 0.45), seed=0):
+    """An environment map on an n_theta x n_phi latitude-longitude grid as directional lights
+    (the paper's 16 x 32 map of distant lights without inverse-square falloff): one light per
+    cell centre, direction from the polar angle theta (from +y) and azimuth phi, intensity =
+    radiance x the cell's solid angle sin(theta) dtheta dphi.  Radiance: a sky gradient
+    0.4 + 0.6 max(0, y) plus a sun lobe 8 max(0, w.sun)^16, per channel tinted by a seeded
+    colour in [0.8, 1].  Returns (directions [M,3], intensities [M,3])."""
+    rng = np.random.default_rng(seed)
+    tint = rng.uniform(0.8, 1.0, size=3)
+    th = (np.arange(n_theta) + 0.5) * math.pi / n_theta
+    ph = (np.arange(n_phi) + 0.5) * 2.0 * math.pi / n_phi
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    w = np.stack([np.sin(T) * np.cos(P), np.cos(T), np.sin(T) * np.sin(P)], axis=-1).reshape(-1, 3)
+    s = _unit(np.asarray(sun, np.float64)[None])[0]
+    rad = 0.4 + 0.6 * np.maximum(0.0, w[:, 1]) + 8.0 * np.maximum(0.0, w @ s) ** 16
+    dom = (np.sin(T) * (math.pi / n_theta) * (2.0 * math.pi / n_phi)).reshape(-1)
+    return w, (rad * dom)[:, None] * tint[None, :]
+
+
+def with_env_map(sc, n_theta=16, n_phi=32, seed=0):
+    """The scene lit by `env_map` instead of its point lights (directional lights)."""
+    w, I = env_map(n_theta, n_phi, seed=seed)
+    out = dict(sc)
+    out["light_pos"], out["light_I"] = _f(w), _f(I)
+    out["light_dir"] = True
+    out["name"] = sc.get("name", "") + f"_env{n_theta}x{n_phi}"
+    return out
+
+
 def with_emission(sc, seed=1, scale=0.5, dc_only=False):
     """Attach a seeded emission E[N,nc,3] (used by the gradient tests)."""
     rng = np.random.default_rng(seed)
