@@ -35,7 +35,7 @@ def _directional(sc, n_lights, seed):
 
 @pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("maker", [
-    lambda: _directional(scenes.with_emission(scenes.box_scene(n=800, nb=3), seed=1), 4, 2),
+    lambda: _directional(scenes.with_emission(scenes.fruit_bowl(n=2000, L=2, nd=64, nb=3), seed=1), 4, 2),
     lambda: scenes.with_env_map(scenes.fruit_bowl(n=1200, L=2, nd=64, nb=3), n_theta=4, n_phi=8),
 ])
 def test_directional_lights_match_oracle(maker, pairs):
