@@ -25,7 +25,9 @@
  *     reflection R_i d = 2(n_i.d)n_i - d:  f_i(d) = c_i (x) Y(R_i d), d = -w_I.
  *   - c_l (same for all m of band l): l=0: 4 k a^d + (1-k) a^s; l>=1: (1-k) a^s rho_l(s).
  *   - alpha = o_j * exp(-(u^2+v^2)/2) with a 3-sigma cutoff (u^2+v^2 <= 9), or the
- *     furnace-only disc model alpha = o_j for u^2+v^2 <= 1.
+ *     furnace-only disc model alpha = o_j for u^2+v^2 <= 1, or the GFSGS form of App. E,
+ *     alpha = 1 - exp(-0.03279 (o_j exp(-(u^2+v^2)/2))^3.4) with the same cutoff (o_j then
+ *     plays the unbounded opacity parameter g_j).
  *   - hemisphere directions: Nd = n_a x n_b stratified cosine-weighted (Malley) samples
  *     with SplitMix64 jitter; weight pi/Nd.  Hits with |n_j.(p_j-o)| <= eps_plane are
  *     ignored (coplanar neighbours); hits are sorted by t and runs of near-equal t are
@@ -47,7 +49,7 @@
 
 #define OR_PI 3.14159265358979323846
 
-enum { OR_ALPHA_GAUSS = 0, OR_ALPHA_DISC = 1 };
+enum { OR_ALPHA_GAUSS = 0, OR_ALPHA_DISC = 1, OR_ALPHA_GFSGS = 2 };
 
 /* ------------------------------------------------------------------ small vectors */
 static inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -414,6 +416,57 @@ static void hv_push(hitvec *v, or_hit x) {
     v->h[v->cnt++] = x;
 }
 
+/* Opacity of a hit with Gaussian value G on a surfel of opacity parameter o, and its
+ * derivative in o: o G for the Gaussian and disc models; App. E's GFSGS form
+ * 1 - exp(-0.03279 (o G)^3.4) otherwise.  The receiver's own alpha_i(p_i) is G = 1. */
+static double alpha_of(const or_scene *s, double o, double G) {
+    if (s->alpha_model == OR_ALPHA_GFSGS) {
+        double x = o * G;
+        if (!(x > 0.0)) return 0.0;
+        return -expm1(-0.03279 * pow(x, 3.4));
+    }
+    return o * G;
+}
+static double dalpha_do(const or_scene *s, double o, double G) {
+    if (s->alpha_model == OR_ALPHA_GFSGS) {
+        double x = o * G;
+        if (!(x > 0.0)) return 0.0;
+        double p = 0.03279 * pow(x, 3.4);
+        return exp(-p) * 3.4 * p / o;
+    }
+    return G;
+}
+static double alpha_c(const or_scene *s, int i) { return alpha_of(s, s->o[i], 1.0); }
+static double dalpha_c(const or_scene *s, int i) { return dalpha_do(s, s->o[i], 1.0); }
+
+/* Ein(x) = int_0^x (1 - e^{-y}) / y dy: its power series sum_k (-1)^{k+1} x^k / (k k!)
+ * for x <= 2; beyond, E1(x) + ln x + gamma with the exponential integral E1 from its
+ * continued fraction e^{-x} / (x + 1 - 1/(x + 3 - 4/(x + 5 - ...))) (Lentz's method). */
+double or_ein(double x) {
+    if (!(x > 0.0)) return 0.0;
+    if (x <= 2.0) {
+        double term = x, sum = x;
+        for (int k = 2; k < 80; ++k) {
+            term *= -x / k;
+            sum += term / k;
+            if (fabs(term / k) < 1e-18 * fabs(sum)) break;
+        }
+        return sum;
+    }
+    const double tiny = 1e-300;
+    double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+    for (int i = 1; i < 500; ++i) {
+        double an = -(double)i * i;
+        b += 2.0;
+        d = 1.0 / (an * d + b);
+        c = b + an / c;
+        double del = c * d;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-16) break;
+    }
+    return h * exp(-x) + log(x) + 0.57721566490153286061;
+}
+
 /* Eq. G: the ray o + t d meets the plane of surfel j at t = n_j.(p_j - o) / n_j.d; the
  * hit's local coordinates are (u,v) = ((x-p_j).t^u_j / s^u_j, (x-p_j).t^v_j / s^v_j). */
 static void test_surfel(const or_scene *s, int self, const double *o, const double *d, double tmax, int j, hitvec *out) {
@@ -438,7 +491,7 @@ static void test_surfel(const or_scene *s, int self, const double *o, const doub
         if (r2 > 9.0) return;
         G = exp(-0.5 * r2);
     }
-    or_hit x = {t, s->o[j] * G, G, j};
+    or_hit x = {t, alpha_of(s, s->o[j], G), G, j};
     hv_push(out, x);
 }
 
@@ -672,7 +725,7 @@ void or_direct(const or_scene *s, double *D) {
         for (int kk = 0; kk < nc; ++kk)
             for (int c = 0; c < C; ++c)
                 D[((size_t)i * nc + kk) * C + c] =
-                    s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * s->Dgeo[((size_t)i * nc + kk) * C + c];
+                    alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * s->Dgeo[((size_t)i * nc + kk) * C + c];
 }
 
 
@@ -693,11 +746,23 @@ void or_direct(const or_scene *s, double *D) {
  *     the far end p_j as well (coplanar neighbours of the source do not occlude it);
  *   - int_{P_j} alpha_j dx in closed form for the opacity model: the Gaussian truncated at
  *     3 sigma gives 2 pi s^u s^v o (1 - e^{-9/2}), the disc pi s^u s^v o.               */
-static double alpha_area_unit(const or_scene *s, int j) { /* int alpha_j dx / o_j */
+/* int_{P_j} alpha_j dx and its derivative in o_j: the linear models o_j times a constant
+ * area; the GFSGS form (App. E) (2 pi / 3.4) s^u s^v Ein(0.03279 o^3.4), whose derivative
+ * is 2 pi s^u s^v alpha_j(p_j) / o_j. */
+static double alpha_area_unit(const or_scene *s, int j) {
     if (s->alpha_model == OR_ALPHA_DISC) return OR_PI * s->su[j] * s->sv[j];
     return 2.0 * OR_PI * s->su[j] * s->sv[j] * (1.0 - exp(-4.5));
 }
-double or_alpha_area(const or_scene *s, int j) { return s->o[j] * alpha_area_unit(s, j); }
+double or_alpha_area(const or_scene *s, int j) {
+    if (s->alpha_model == OR_ALPHA_GFSGS)
+        return 2.0 * OR_PI / 3.4 * s->su[j] * s->sv[j] * or_ein(0.03279 * pow(s->o[j], 3.4));
+    return s->o[j] * alpha_area_unit(s, j);
+}
+static double dalpha_area(const or_scene *s, int j) {
+    if (s->alpha_model == OR_ALPHA_GFSGS)
+        return s->o[j] > 0.0 ? 2.0 * OR_PI * s->su[j] * s->sv[j] * alpha_c(s, j) / s->o[j] : 0.0;
+    return alpha_area_unit(s, j);
+}
 
 /* Occluders of the segment from p_i to p_j, in compositing order. */
 static void pair_segment(const or_scene *s, int i, int j, const double *d, double r, hitvec *out) {
@@ -828,7 +893,7 @@ static void pair_apply_K(const or_scene *s, const double *Bin, double *Bout, dou
             for (int c = 0; c < C; ++c) {
                 size_t idx = ((size_t)i * nc + kk) * C + c;
                 if (Q) Q[idx] = acc[kk * C + c];
-                if (Bout) Bout[idx] = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
+                if (Bout) Bout[idx] = alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
             }
     }
 }
@@ -850,7 +915,7 @@ static void pair_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
                 double sv = 0.0;
                 for (int kk = 0; kk < nc; ++kk)
                     sv += s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Yi[kk] * Vin[((size_t)i * nc + kk) * C + c];
-                y[c] = s->o[i] * sv;
+                y[c] = alpha_c(s, i) * sv;
             }
             double *Vj = Vout + (size_t)s->pair_j[e] * nc * C;
             for (int kk = 0; kk < nc; ++kk)
@@ -859,8 +924,8 @@ static void pair_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
 }
 
 /* Source-side gradients of the pairs: with g_e = dL/dV_ji (summed over the bounces),
- *   dL/dlambda_j += g_e A_j T geo,  dL/do_j += g_e lambda_j (A_j / o_j) T geo,
- *   dL/do_k      += g_e lambda_j A_j geo * (-prod_{m != k} (1 - alpha_m)) G_k   (occluders). */
+ *   dL/dlambda_j += g_e A_j T geo,  dL/do_j += g_e lambda_j (dA_j/do_j) T geo,
+ *   dL/do_k      += g_e lambda_j A_j geo * (-prod_{m != k} (1 - alpha_m)) dalpha_k/do_k  (occluders). */
 static void pair_backward(const or_scene *s, int nb, const double *iters, const double *v, double *dop, double *dlam) {
     int n = s->n, nc = s->nc, C = s->C, L = s->L;
     size_t M = (size_t)n * nc * C;
@@ -885,19 +950,20 @@ static void pair_backward(const or_scene *s, int nb, const double *iters, const 
                               v[(size_t)a * M + ((size_t)i * nc + kk) * C + c];
                         sv += Yo[kk] * Bb[kk * C + c];
                     }
-                    g += s->o[i] * yv * sv;
+                    g += alpha_c(s, i) * yv * sv;
                 }
             }
             if (g == 0.0) continue;
-            const double Au = alpha_area_unit(s, j), T = s->pair_T[e], geo = s->pair_geo[e];
-            if (dlam) dlam[j] += g * s->o[j] * Au * T * geo;
+            const double A = or_alpha_area(s, j), dA = dalpha_area(s, j), T = s->pair_T[e], geo = s->pair_geo[e];
+            if (dlam) dlam[j] += g * A * T * geo;
             if (dop) {
-                dop[j] += g * s->lam[j] * Au * T * geo;
+                dop[j] += g * s->lam[j] * dA * T * geo;
                 for (long q = s->poc_off[e]; q < s->poc_off[e + 1]; ++q) {
                     double others = 1.0;
                     for (long m = s->poc_off[e]; m < s->poc_off[e + 1]; ++m)
                         if (m != q) others *= 1.0 - s->poc_alpha[m];
-                    dop[s->poc_j[q]] += -g * s->lam[j] * s->o[j] * Au * geo * others * s->poc_G[q];
+                    const int k = s->poc_j[q];
+                    dop[k] += -g * s->lam[j] * A * geo * others * dalpha_do(s, s->o[k], s->poc_G[q]);
                 }
             }
         }
@@ -943,7 +1009,7 @@ void or_apply_K(const or_scene *s, const double *Bin, double *Bout, double *Q) {
             for (int c = 0; c < C; ++c) {
                 size_t idx = ((size_t)i * nc + kk) * C + c;
                 if (Q) Q[idx] = acc[kk * C + c];
-                if (Bout) Bout[idx] = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
+                if (Bout) Bout[idx] = alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
             }
     }
 }
@@ -973,7 +1039,7 @@ void or_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
                 double sv = 0.0;
                 for (int kk = 0; kk < nc; ++kk)
                     sv += s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Yi[kk] * Vin[((size_t)i * nc + kk) * C + c];
-                y[c] = s->o[i] * w * sv;
+                y[c] = alpha_c(s, i) * w * sv;
             }
             long ray = (long)i * nd + r;
             for (long e = s->ray_off[ray]; e < s->ray_off[ray + 1]; ++e) {
@@ -1068,15 +1134,15 @@ void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, dou
             }
     if (dc)
         for (int i = 0; i < n; ++i)
-            for (int q = 0; q < (L + 1) * 3; ++q) dc[(size_t)i * (L + 1) * 3 + q] = s->o[i] * P[(size_t)i * (L + 1) * 3 + q];
+            for (int q = 0; q < (L + 1) * 3; ++q) dc[(size_t)i * (L + 1) * 3 + q] = alpha_c(s, i) * P[(size_t)i * (L + 1) * 3 + q];
     if (dad)
         for (int i = 0; i < n; ++i)
-            for (int ch = 0; ch < 3; ++ch) dad[i * 3 + ch] = 4.0 * s->k[i] * s->o[i] * P[((size_t)i * (L + 1)) * 3 + ch];
+            for (int ch = 0; ch < 3; ++ch) dad[i * 3 + ch] = 4.0 * s->k[i] * alpha_c(s, i) * P[((size_t)i * (L + 1)) * 3 + ch];
     if (dop) {
         for (int i = 0; i < n; ++i) {
             double acc = 0.0;
             for (int q = 0; q < (L + 1) * 3; ++q) acc += s->c[(size_t)i * (L + 1) * 3 + q] * P[(size_t)i * (L + 1) * 3 + q];
-            dop[i] = acc;
+            dop[i] = dalpha_c(s, i) * acc;
         }
     }
     if (dlam) memset(dlam, 0, sizeof(double) * (size_t)n);
@@ -1102,7 +1168,7 @@ void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, dou
                         for (int kk = 0; kk < nc; ++kk)
                             sv += s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Yi[kk] *
                                   v[(size_t)a * M + ((size_t)i * nc + kk) * C + c];
-                        y[a * C + c] = s->o[i] * w * sv;
+                        y[a * C + c] = alpha_c(s, i) * w * sv;
                     }
                 int H = (int)(e1 - e0);
                 double *gh = dup_arr(NULL, H), *Th = dup_arr(NULL, H);
@@ -1126,7 +1192,7 @@ void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, dou
                 for (int h = H - 1; h >= 0; --h) {
                     long e = e0 + h;
                     double dalpha = Th[h] * (gh[h] - R);
-                    dop[s->hit_j[e]] += dalpha * s->hit_G[e];
+                    dop[s->hit_j[e]] += dalpha * dalpha_do(s, s->o[s->hit_j[e]], s->hit_G[e]);
                     R = s->hit_alpha[e] * gh[h] + (1.0 - s->hit_alpha[e]) * R;
                 }
                 free(gh);
@@ -1147,13 +1213,13 @@ void or_adjoint(const or_scene *s, const double *E, int nb, const double *g, dou
                 double qv = 0.0;
                 for (int kk = 0; kk < nc; ++kk)
                     for (int ch = 0; ch < 3; ++ch)
-                        qv += u[((size_t)i * nc + kk) * C + lt * 3 + ch] * s->o[i] *
+                        qv += u[((size_t)i * nc + kk) * C + lt * 3 + ch] * alpha_c(s, i) *
                               s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + ch] * Yi[kk] * s->li[lt * 3 + ch] * pre;
                 for (long e = q0; e < q1; ++e) {
                     double others = 1.0;
                     for (long m = q0; m < q1; ++m)
                         if (m != e) others *= (1.0 - s->sh_alpha[m]);
-                    dop[s->sh_j[e]] += -qv * others * s->sh_G[e];
+                    dop[s->sh_j[e]] += -qv * others * dalpha_do(s, s->o[s->sh_j[e]], s->sh_G[e]);
                 }
             }
         }
@@ -1215,7 +1281,7 @@ void or_dense_K(const or_scene *s, int col, double *Kd) {
                 or_sh_eval(L, rd, Yi);
                 int j = s->pair_j[e];
                 for (int kp = 0; kp < nc; ++kp) {
-                    double f = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kp)) * 3 + col % 3] * w * Yi[kp] * s->pair_V[e];
+                    double f = alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kp)) * 3 + col % 3] * w * Yi[kp] * s->pair_V[e];
                     for (int kk = 0; kk < nc; ++kk) Kd[((size_t)i * nc + kp) * Mm + (size_t)j * nc + kk] += f * Yo[kk];
                 }
             }
@@ -1233,7 +1299,7 @@ void or_dense_K(const or_scene *s, int col, double *Kd) {
             for (long e = s->ray_off[ray]; e < s->ray_off[ray + 1]; ++e) {
                 int j = s->hit_j[e];
                 for (int kp = 0; kp < nc; ++kp) {
-                    double f = s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kp)) * 3 + col % 3] * w * Yi[kp] * s->hit_a[e];
+                    double f = alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kp)) * 3 + col % 3] * w * Yi[kp] * s->hit_a[e];
                     for (int kk = 0; kk < nc; ++kk) Kd[((size_t)i * nc + kp) * Mm + (size_t)j * nc + kk] += f * Yo[kk];
                 }
             }
@@ -1264,7 +1330,7 @@ void or_sample_direct(const or_scene *s, int nl, const double *lp, const double 
             for (int kk = 0; kk < nc; ++kk)
                 for (int ch = 0; ch < 3; ++ch)
                     out[((size_t)q * nc + kk) * C + lt * 3 + ch] =
-                        s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + ch] * Y[kk] * li[lt * 3 + ch] * pre * T;
+                        alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + ch] * Y[kk] * li[lt * 3 + ch] * pre * T;
         }
         free(hv.h);
     }
@@ -1319,7 +1385,7 @@ void or_sample_bounce1(const or_scene *s, int nd, uint64_t seed, int nl, const d
         }
         for (int kk = 0; kk < nc; ++kk)
             for (int c = 0; c < C; ++c)
-                acc[kk * C + c] += s->o[i] * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Q[kk * C + c];
+                acc[kk * C + c] += alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * Q[kk * C + c];
         free(hv.h);
         free(Q);
         free(Sj);

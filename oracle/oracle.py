@@ -18,7 +18,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ALPHA_GAUSS, ALPHA_DISC = 0, 1
+ALPHA_GAUSS, ALPHA_DISC, ALPHA_GFSGS = 0, 1, 2
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
@@ -74,6 +74,8 @@ def lib():
             L.or_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
             L.or_adjoint.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
             L.or_set_directional.argtypes = [ct.c_void_p, ct.c_int]
+            L.or_ein.restype = ct.c_double
+            L.or_ein.argtypes = [ct.c_double]
             L.or_pairs.restype = ct.c_int
             L.or_pairs.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
             L.or_num_pairs.restype = ct.c_long
@@ -124,6 +126,11 @@ def jitter(seed, i, r, dim):
 
 def strata_a(nd):
     return lib().or_strata_a(nd)
+
+
+def ein(x):
+    """Ein(x) = int_0^x (1 - e^{-y}) / y dy (the oracle's own implementation)."""
+    return lib().or_ein(float(x))
 
 
 def num_threads():
