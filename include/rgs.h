@@ -64,7 +64,10 @@ typedef enum rgs_status {
 
 typedef enum rgs_alpha_model {
     RGS_ALPHA_GAUSS = 0, /* alpha = o * exp(-(u^2+v^2)/2) for u^2+v^2 <= 9 (3-sigma cutoff) */
-    RGS_ALPHA_DISC = 1   /* alpha = o for u^2+v^2 <= 1, else 0 (closed-sphere furnace test) */
+    RGS_ALPHA_DISC = 1,  /* alpha = o for u^2+v^2 <= 1, else 0 (closed-sphere furnace test) */
+    RGS_ALPHA_GFSGS = 2  /* App. E: alpha = 1 - exp(-0.03279 (o exp(-(u^2+v^2)/2))^3.4) for u^2+v^2 <= 9,
+                            o the unbounded opacity parameter g; the receiver's own alpha_i(p_i)
+                            (the o_i factor of the other models) is 1 - exp(-0.03279 o_i^3.4) */
 } rgs_alpha_model;
 
 /* Precision of the bounce gathers (the batched form of the contraction).  Every mode

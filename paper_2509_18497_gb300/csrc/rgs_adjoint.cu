@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_adj_ray(SceneDev sc, RaysDev rays, int 
     const float3 d = f3(rays.dir[r]);
     float Yi[NC];
     sh_eval<NC>(reflect_n(n, d), Yi);
-    const float oi = sc.P[i].w * (3.14159265358979f / (float)rays.nd);
+    const float oi = alpha_center(sc, i) * (3.14159265358979f / (float)rays.nd);
     const float *vi = vin + ((size_t)i * C + col0) * NC;
     float y[3];
 #pragma unroll
@@ -144,7 +144,7 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
     auto pass1 = [&](int j) {
         float t, g;
         if (!hit_surfel(sc, j, i, o, w, r, eps, t, g)) return;
-        const float om = 1.f - __ldg(&sc.P[j].w) * g;
+        const float om = 1.f - alpha_of(sc, __ldg(&sc.P[j].w), g);
         if (om == 0.f) ++nzero;
         else Tnz *= om;
     };
@@ -168,16 +168,17 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
     for (int b = 0; b < 4; ++b)
         for (int ch = 0; ch < 3; ++ch)
             if (acc[b][ch] != 0.f) atomicAdd(&P[(size_t)i * 12 + b * 3 + ch], acc[b][ch]);
-    qv *= Pi.w;
+    qv *= alpha_center(sc, i);
     if (qv == 0.f || nzero > 1) return;
     auto pass2 = [&](int j) {
         float t, g;
         if (!hit_surfel(sc, j, i, o, w, r, eps, t, g)) return;
-        const float om = 1.f - __ldg(&sc.P[j].w) * g;
+        const float oj = __ldg(&sc.P[j].w);
+        const float om = 1.f - alpha_of(sc, oj, g);
         float others;
         if (nzero == 0) others = Tnz / om;
         else others = (om == 0.f) ? Tnz : 0.f;
-        if (others != 0.f) atomicAdd(&dop[j], -qv * others * g);
+        if (others != 0.f) atomicAdd(&dop[j], -qv * others * dalpha_do(sc, oj, g));
     };
     bvh_traverse(sc, o, w, r, pass2);
 }
@@ -208,7 +209,7 @@ __global__ void RGS_OPA_LB k_opacity_g(SceneDev sc, RaysDev rays, int C, int col
         SL::pick(Y, g, yo);
         sh_eval<NC>(reflect_n(n, d), Y);
         SL::pick(Y, g, yi);
-        const float oi = sc.P[i].w * (3.14159265358979f / (float)rays.nd);
+        const float oi = alpha_center(sc, i) * (3.14159265358979f / (float)rays.nd);
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
 #pragma unroll
@@ -278,17 +279,18 @@ __global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const flo
         const float G = stored_hit_G(sc, j, o, d);
         Th[h] = T;
         Gh[h] = G;
-        T *= 1.f - __ldg(&sc.P[j].w) * G;
+        T *= 1.f - alpha_of(sc, __ldg(&sc.P[j].w), G);
     }
     float R = 0.f;
     for (int h = cnt - 1; h >= 0; --h) {
         const long long slot = base + h;
         const int j = __ldg(&rays.rec_ja[slot]).x;
         const float G = Gh[h];
-        const float alpha = __ldg(&sc.P[j].w) * G;
+        const float oj = __ldg(&sc.P[j].w);
+        const float alpha = alpha_of(sc, oj, G);
         const float g = gh[slot];
         const float da = Th[h] * (g - R);
-        if (da != 0.f) atomicAdd(&dop[j], da * G);
+        if (da != 0.f) atomicAdd(&dop[j], da * dalpha_do(sc, oj, G));
         R = alpha * g + (1.f - alpha) * R;
     }
 }
@@ -309,13 +311,13 @@ __global__ void k_finalize(SceneDev sc, int C, const float *__restrict__ u, cons
                 dE[((size_t)ui * NC + k) * 3 + ch] = s;
             }
     }
-    const float o = sc.P[i].w;
+    const float ai = alpha_center(sc, i);
     if (dad)
-        for (int ch = 0; ch < 3; ++ch) dad[(size_t)ui * 3 + ch] = 4.f * kk[i] * o * Pi[ch];
+        for (int ch = 0; ch < 3; ++ch) dad[(size_t)ui * 3 + ch] = 4.f * kk[i] * ai * Pi[ch];
     if (dop) {
-        float s = dop_acc[i];
+        float s = 0.f;
         for (int q = 0; q < 12; ++q) s += sc.cl[(size_t)i * 12 + q] * Pi[q];
-        dop[ui] = s;
+        dop[ui] = dop_acc[i] + dalpha_center(sc, i) * s;
     }
 }
 

@@ -246,7 +246,8 @@ rgs_status rgs_build_scene(const rgs_surfels *surfels, const rgs_build_opts *opt
         rgs_set_error("rgs_build_scene: NULL surfel array");
         return RGS_ERR_ARG;
     }
-    if (opts && opts->alpha_model != RGS_ALPHA_GAUSS && opts->alpha_model != RGS_ALPHA_DISC) {
+    if (opts && opts->alpha_model != RGS_ALPHA_GAUSS && opts->alpha_model != RGS_ALPHA_DISC &&
+        opts->alpha_model != RGS_ALPHA_GFSGS) {
         rgs_set_error("rgs_build_scene: unknown alpha model %d", opts->alpha_model);
         return RGS_ERR_ARG;
     }
@@ -533,6 +534,8 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->chunk_cnt);
     dev_free(t->chunk_tmp);
     dev_free(t->lam);
+    dev_free(t->aarea);
+    dev_free(t->daarea);
     delete t;
 }
 

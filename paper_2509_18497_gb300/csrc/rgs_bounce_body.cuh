@@ -158,7 +158,7 @@ __device__ __forceinline__ void bounce_epilogue(const SceneDev &sc, int C, const
         const float Q = w * v;
         const size_t idx = ((size_t)i * C + col) * NC + k;
         Qout[idx] = Q;
-        const float oc = sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (col % 3)];
+        const float oc = alpha_center(sc, i) * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (col % 3)];
         const float b = S[idx] + oc * Q;
         Bout[idx] = b;
         if (Bout16) Bout16[((size_t)i * C + col) * bf16_stride<NC>() + k] = __float2bfloat16_rn(b);
@@ -228,7 +228,7 @@ __device__ __forceinline__ void bounce_receiver_mc(const SceneDev &sc, const Ray
         const float Q = w * v;
         const size_t idx = ((size_t)i * C + cc) * NC + k;
         Qout[idx] = Q;
-        const float b = S[idx] + sc.P[i].w * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (cc % 3)] * Q;
+        const float b = S[idx] + alpha_center(sc, i) * sc.cl[(size_t)i * 12 + band_of(k) * 3 + (cc % 3)] * Q;
         Bout[idx] = b;
         if (Bout16) Bout16[((size_t)i * C + cc) * ((NC >= 9) ? 16 : NC) + k] = __float2bfloat16_rn(b);
         const double df = (double)b - (double)Bprev[idx];

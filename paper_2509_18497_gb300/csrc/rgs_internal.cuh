@@ -285,6 +285,31 @@ __device__ __forceinline__ float surfel_G(const SceneDev &sc, float r2) {
     return (sc.alpha_model == RGS_ALPHA_DISC) ? 1.f : expf(-0.5f * r2);
 }
 
+// Opacity of a hit with Gaussian value G on a surfel of opacity parameter o, and its
+// derivative in o: o G for the Gaussian and disc models; App. E's GFSGS form
+// 1 - exp(-0.03279 (o G)^3.4) otherwise (o is then the unbounded parameter g).
+__device__ __forceinline__ float alpha_of(const SceneDev &sc, float o, float G) {
+    if (sc.alpha_model == RGS_ALPHA_GFSGS) {
+        const float x = o * G;
+        return x > 0.f ? -expm1f(-0.03279f * powf(x, 3.4f)) : 0.f;
+    }
+    return o * G;
+}
+__device__ __forceinline__ float dalpha_do(const SceneDev &sc, float o, float G) {
+    if (sc.alpha_model == RGS_ALPHA_GFSGS) {
+        const float x = o * G;
+        if (!(x > 0.f)) return 0.f;
+        const float p = 0.03279f * powf(x, 3.4f);
+        return expf(-p) * 3.4f * p / o;
+    }
+    return G;
+}
+// the receiver's own alpha_i(p_i) (kappa_i a Dirac at the centre: G = 1) and its derivative
+__device__ __forceinline__ float alpha_center(const SceneDev &sc, int i) { return alpha_of(sc, __ldg(&sc.P[i].w), 1.f); }
+__device__ __forceinline__ float dalpha_center(const SceneDev &sc, int i) {
+    return dalpha_do(sc, __ldg(&sc.P[i].w), 1.f);
+}
+
 // Ray o + t d against the plane of surfel j (Eq. G). Returns true with t and r2 when the
 // hit is accepted: j != self, |n_j.(p_j - o)| > eps, 0 < t < tmax, inside the cutoff.
 __device__ __forceinline__ bool hit_surfel_t(const SceneDev &sc, int j, int self, float3 o, float3 d, float tmax,
@@ -500,6 +525,7 @@ struct rgs_transport {
     long long *chunk_tmp = nullptr;
     int chunk_tmp_cap = 0;
     float *lam = nullptr; // lambda in internal order
+    float *aarea = nullptr, *daarea = nullptr; // int alpha_j dx and its derivative in o_j
     int lam_cap = 0;
     // hemisphere hit records
     long long cap_slots = 0;

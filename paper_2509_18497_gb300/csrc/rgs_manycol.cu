@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(MC_THREADS) k_adj_ray_mc(SceneDev sc, RaysDev 
     const float3 n = f3(sc.N4[i]);
     float cv[NC]; // c_{i,l(k),ch(col)} * v_i[col][k] * o_i pi/nd
     {
-        const float oi = sc.P[i].w * (3.14159265358979f / (float)nd);
+        const float oi = alpha_center(sc, i) * (3.14159265358979f / (float)nd);
         float v[NC];
         if (live) load_col<NC>(vin + ((size_t)i * C + col) * NC, v);
 #pragma unroll
@@ -117,7 +117,7 @@ __global__ void RGS_MC_LB k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int c
         float Yi[NC];
         sh_eval<NC>(neg3(d), Yo);
         sh_eval<NC>(reflect_n(n, d), Yi);
-        const float oi = sc.P[i].w * (3.14159265358979f / (float)rays.nd);
+        const float oi = alpha_center(sc, i) * (3.14159265358979f / (float)rays.nd);
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
             float s = 0.f;

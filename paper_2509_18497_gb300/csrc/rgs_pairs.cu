@@ -24,12 +24,43 @@ namespace {
 constexpr int PCH = 256;      // sources per block of the count / fill passes
 constexpr int PAIR_THREADS = 128;
 
-// int alpha_j dx / o_j for the opacity model (App. E for this build's models): the
-// Gaussian truncated at 3 sigma 2 pi s^u s^v (1 - e^{-9/2}), the disc pi s^u s^v
-__device__ __forceinline__ float alpha_area_unit(const SceneDev &sc, int j) {
-    const float su = 1.f / __ldg(&sc.FU[j].w), sv = 1.f / __ldg(&sc.FV[j].w);
-    if (sc.alpha_model == RGS_ALPHA_DISC) return 3.14159265358979f * su * sv;
-    return 6.28318530717959f * su * sv * 0.98889100346175773f; // 1 - e^{-4.5}
+// Ein(x) = int_0^x (1 - e^{-y}) / y dy in double: its power series sum (-1)^{k+1} x^k / (k k!)
+// up to x = 20 (the largest term is ~2e6 there, so the sum keeps ~1e-10 relative), and
+// ln x + gamma beyond, where the remainder E1(x) < e^{-x}/x < 1e-10.
+__device__ double ein_d(double x) {
+    if (!(x > 0.0)) return 0.0;
+    if (x > 20.0) return log(x) + 0.5772156649015329;
+    double term = x, sum = x;
+    for (int k = 2; k < 120; ++k) {
+        term *= -x / k;
+        const double add = term / k;
+        sum += add;
+        if (fabs(add) < 1e-17 * fabs(sum)) break;
+    }
+    return sum;
+}
+
+// int alpha_j dx over the tangent plane and its derivative in o_j, per surfel: the
+// Gaussian truncated at 3 sigma 2 pi s^u s^v o (1 - e^{-9/2}), the disc pi s^u s^v o, and
+// App. E's GFSGS closed form (2 pi / 3.4) s^u s^v Ein(0.03279 o^3.4), whose derivative
+// is 2 pi s^u s^v alpha_j(p_j) / o.
+__global__ void k_alpha_area(SceneDev sc, float *aarea, float *daarea) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= sc.n) return;
+    const double su = 1.0 / (double)sc.FU[j].w, sv = 1.0 / (double)sc.FV[j].w, o = sc.P[j].w;
+    const double two_pi = 6.283185307179586;
+    double A, dA;
+    if (sc.alpha_model == RGS_ALPHA_GFSGS) {
+        A = two_pi / 3.4 * su * sv * ein_d(0.03279 * pow(o, 3.4));
+        dA = o > 0.0 ? two_pi * su * sv * (-expm1(-0.03279 * pow(o, 3.4))) / o : 0.0;
+    } else {
+        const double unit = (sc.alpha_model == RGS_ALPHA_DISC) ? 0.5 * two_pi * su * sv
+                                                                : two_pi * su * sv * (1.0 - exp(-4.5));
+        A = o * unit;
+        dA = unit;
+    }
+    aarea[j] = (float)A;
+    daarea[j] = (float)dA;
 }
 
 // source j in front of receiver i: n_i.(p_j - p_i) > eps (explicitly rounded, so the count
@@ -74,7 +105,8 @@ __global__ void __launch_bounds__(PCH) k_pair_count(SceneDev sc, int n, int chun
 }
 
 __global__ void __launch_bounds__(PCH) k_pair_fill(SceneDev sc, int n, int chunks, const long long *__restrict__ chunk_off,
-                                                   const float *__restrict__ lam, int2 *rec, int *flags) {
+                                                   const float *__restrict__ lam, const float *__restrict__ aarea,
+                                                   int2 *rec, int *flags) {
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
@@ -98,12 +130,12 @@ __global__ void __launch_bounds__(PCH) k_pair_fill(SceneDev sc, int n, int chunk
     float T = 1.f;
     auto visit = [&](int k) {
         float g;
-        if (pair_occluder(sc, k, i, j, pi, d, r, pj, eps, g)) T *= 1.f - __ldg(&sc.P[k].w) * g;
+        if (pair_occluder(sc, k, i, j, pi, d, r, pj, eps, g)) T *= 1.f - alpha_of(sc, __ldg(&sc.P[k].w), g);
     };
     if (!bvh_traverse(sc, pi, d, r, visit)) atomicAdd(&flags[FLAG_STACK], 1);
     const float3 nj = f3(sc.N4[j]);
     const float geo = fabsf(dot3(ni, d)) * fabsf(dot3(nj, d)) / (r * r);
-    const float V = __ldg(&lam[j]) * __ldg(&sc.P[j].w) * alpha_area_unit(sc, j) * T * geo;
+    const float V = __ldg(&lam[j]) * __ldg(&aarea[j]) * T * geo;
     rec[chunk_off[blk] + rank] = make_int2(j, __float_as_int(V));
 }
 
@@ -206,6 +238,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_adj_src_pairs(SceneDev sc, int
             const int i = iv.x;
             const float V = __int_as_float(iv.y);
             const float4 Pi = __ldg(&sc.P[i]);
+            const float ai = alpha_center(sc, i);
             float r;
             const float3 d = unit_dir(make_float3(Pj.x - Pi.x, Pj.y - Pi.y, Pj.z - Pi.z), r);
             float Yi[NC], Yo[NC];
@@ -218,7 +251,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_adj_src_pairs(SceneDev sc, int
                 float s = 0.f;
 #pragma unroll
                 for (int k = 0; k < NC; ++k) s += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * Yi[k] * __ldg(&vi[c * NC + k]);
-                const float y = V * Pi.w * s;
+                const float y = V * ai * s;
 #pragma unroll
                 for (int k = 0; k < NC; ++k) acc[k][c] += Yo[k] * y;
             }
@@ -278,7 +311,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int
                 g += y * s;
             }
         }
-        gpair[e] = g * Pi.w;
+        gpair[e] = g * alpha_center(sc, i);
     }
 }
 
@@ -289,7 +322,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int
 //   dL/do_k += -g lambda_j A_j geo prod_{m != k}(1 - alpha_m) G_k for the segment's occluders
 // (the segment is traced again: once for T and the zero factors, once for the occluders).
 __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunks, const long long *__restrict__ chunk_off,
-                                                   const float *__restrict__ lam, const float *__restrict__ gpair,
+                                                   const float *__restrict__ lam, const float *__restrict__ aarea,
+                                                   const float *__restrict__ daarea, const float *__restrict__ gpair,
                                                    float *dop, float *dlam, int *flags) {
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
@@ -311,33 +345,33 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     float r;
     const float3 d = unit_dir(dv, r);
     const float3 pj = f3(sc.P[j]);
-    const float Au = alpha_area_unit(sc, j);
-    const float oj = __ldg(&sc.P[j].w), lj = __ldg(&lam[j]);
+    const float Aj = __ldg(&aarea[j]), dAj = __ldg(&daarea[j]), lj = __ldg(&lam[j]);
     const float geo = fabsf(dot3(ni, d)) * fabsf(dot3(f3(sc.N4[j]), d)) / (r * r);
     float Tnz = 1.f;
     int nzero = 0;
     auto pass1 = [&](int k) {
         float gk;
         if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
-        const float om = 1.f - __ldg(&sc.P[k].w) * gk;
+        const float om = 1.f - alpha_of(sc, __ldg(&sc.P[k].w), gk);
         if (om == 0.f) ++nzero;
         else Tnz *= om;
     };
     if (!bvh_traverse(sc, pi, d, r, pass1)) atomicAdd(&flags[FLAG_STACK], 1);
     const float T = nzero ? 0.f : Tnz;
-    if (dlam) atomicAdd(&dlam[j], g * oj * Au * T * geo);
+    if (dlam) atomicAdd(&dlam[j], g * Aj * T * geo);
     if (!dop) return;
-    if (T != 0.f) atomicAdd(&dop[j], g * lj * Au * T * geo);
+    if (T != 0.f) atomicAdd(&dop[j], g * lj * dAj * T * geo);
     if (nzero > 1) return;
-    const float q = -g * lj * oj * Au * geo;
+    const float q = -g * lj * Aj * geo;
     auto pass2 = [&](int k) {
         float gk;
         if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
-        const float om = 1.f - __ldg(&sc.P[k].w) * gk;
+        const float ok = __ldg(&sc.P[k].w);
+        const float om = 1.f - alpha_of(sc, ok, gk);
         float others;
         if (nzero == 0) others = Tnz / om;
         else others = (om == 0.f) ? Tnz : 0.f;
-        if (others != 0.f) atomicAdd(&dop[k], q * others * gk);
+        if (others != 0.f) atomicAdd(&dop[k], q * others * dalpha_do(sc, ok, gk));
     };
     bvh_traverse(sc, pi, d, r, pass2);
 }
@@ -371,11 +405,14 @@ rgs_status rgs_trace_pairs_impl(rgs_transport *t, const rgs_lights *L, const flo
     }
     if (n > t->lam_cap) {
         if ((r = dev_alloc(&t->lam, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->aarea, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
+        if ((r = dev_alloc(&t->daarea, (size_t)n, &t->device_bytes)) != RGS_OK) return r;
         if ((r = dev_alloc(&t->pair_off, (size_t)n + 1, &t->device_bytes)) != RGS_OK) return r;
         t->lam_cap = n;
     }
     SceneDev sd = t->sc->dev();
     { ProfScope ps_("k_lam_in", st); k_lam_in<<<(n + 255) / 256, 256, 0, st>>>(n, t->sc->uid, lambda, t->lam); }
+    { ProfScope ps_("k_alpha_area", st); k_alpha_area<<<(n + 255) / 256, 256, 0, st>>>(sd, t->aarea, t->daarea); }
     RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));
     RGS_CUDA(cudaMemsetAsync(t->src_cnt, 0, sizeof(int) * n, st));
     { ProfScope ps_("k_pair_count", st); k_pair_count<<<(unsigned)nchunk, PCH, 0, st>>>(sd, n, chunks, t->chunk_cnt, t->src_cnt); }
@@ -393,7 +430,7 @@ rgs_status rgs_trace_pairs_impl(rgs_transport *t, const rgs_lights *L, const flo
     t->n_hits = total;
     t->n_slots = total;
     t->n_full = 0;
-    { ProfScope ps_("k_pair_fill", st); k_pair_fill<<<(unsigned)nchunk, PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->pair_rec, t->flags); }
+    { ProfScope ps_("k_pair_fill", st); k_pair_fill<<<(unsigned)nchunk, PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->pair_rec, t->flags); }
     { ProfScope ps_("k_pair_off", st); k_pair_off<<<(n + 256) / 256, 256, 0, st>>>(t->chunk_off, chunks, n, t->pair_off); }
     RGS_LAUNCH("pair fill");
     if ((r = rgs_direct_term(t, st)) != RGS_OK) return r;
@@ -455,7 +492,7 @@ rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float 
     if (nb >= 1 && (dopo || dlam_acc)) {
         const int chunks = (n + PCH - 1) / PCH;
         { ProfScope ps_("k_pair_g", st); k_pair_g<NC><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh); }
-        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->gh, dopo ? t->dop : nullptr, dlam_acc, t->flags); }
+        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, dopo ? t->dop : nullptr, dlam_acc, t->flags); }
         RGS_LAUNCH("pair backward");
     }
     (void)ga;

@@ -106,8 +106,8 @@ __global__ void __launch_bounds__(128, RGS_TRACE_MINB) k_trace_hemi(SceneDev sc,
         for (; kept < H; ++kept) {
             if (T < RGS_T_EPS) break;
             const int j = (int)(unsigned)key[kept];
-            T *= 1.f - __ldg(&sc.P[j].w) *
-                           surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[kept] >> 32))));
+            T *= 1.f - alpha_of(sc, __ldg(&sc.P[j].w),
+                                surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[kept] >> 32)))));
         }
         // a full buffer only loses something if the transmittance is still above the cut
         if (full && kept == H && T >= RGS_T_EPS) atomicAdd(&flags[FLAG_FULL_RAYS], 1);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128, RGS_TRACE_MINB) k_trace_hemi(SceneDev sc,
     for (int h = 0; h < kept; ++h) {
         const int j = (int)(unsigned)key[h];
         const float G = surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[h] >> 32))));
-        const float alpha = __ldg(&sc.P[j].w) * G;
+        const float alpha = alpha_of(sc, __ldg(&sc.P[j].w), G);
         rec_ja[mine + h] = make_int2(j, __float_as_int(alpha * T));
         T *= 1.f - alpha;
         atomicAdd(&src_cnt[j], 1); // transposed-index histogram
@@ -164,12 +164,12 @@ __global__ void k_direct(SceneDev sc, int nl, int ldir, const float *__restrict_
     float T = 1.f;
     auto visit = [&](int j) {
         float t, g;
-        if (hit_surfel(sc, j, i, o, w, r, eps, t, g)) T *= 1.f - __ldg(&sc.P[j].w) * g;
+        if (hit_surfel(sc, j, i, o, w, r, eps, t, g)) T *= 1.f - alpha_of(sc, __ldg(&sc.P[j].w), g);
     };
     if (!bvh_traverse(sc, o, w, r, visit)) atomicAdd(&flags[FLAG_STACK], 1);
     float Y[NC];
     sh_eval<NC>(reflect_n(n, w), Y);
-    const float pre = Pi.w * cs * fall * T;
+    const float pre = alpha_center(sc, i) * cs * fall * T;
     for (int ch = 0; ch < 3; ++ch) {
         const float I = lint[3 * lt + ch];
         for (int k = 0; k < NC; ++k) Dout[ch * NC + k] = sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch] * Y[k] * I * pre;

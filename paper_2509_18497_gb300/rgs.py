@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "librgs.so")
 
 RGS_MAX_SH_DEGREE = 3
 RGS_MAX_BOUNCES = 64
-RGS_ALPHA_GAUSS, RGS_ALPHA_DISC = 0, 1
+RGS_ALPHA_GAUSS, RGS_ALPHA_DISC, RGS_ALPHA_GFSGS = 0, 1, 2
 RGS_FP32, RGS_BF16_FP32ACC, RGS_BF16_FP32ACC_RESCORR = 0, 1, 2
 
 STATUS = {0: "RGS_OK", 1: "RGS_ERR_ARG", 2: "RGS_ERR_CUDA", 3: "RGS_ERR_OOM", 4: "RGS_ERR_CAPACITY",

@@ -1,0 +1,44 @@
+"""The GFSGS opacity model (App. E: alpha = 1 - exp(-0.03279 (g G)^3.4), the surfel's o
+playing the unbounded g) on the GPU against the FP64 oracle, for the hemisphere and the
+center-to-center transports (the latter with App. E's Ein closed form for int alpha):
+iterates and the gradients with respect to E, a^d, o (and lambda)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2509_18497_gb300 import rgs, scenes
+
+from gpu_helpers import rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_18497_gb300 import build
+    build.build()
+
+
+def _gfsgs(sc, seed):
+    out = dict(sc)
+    out["o"] = np.random.default_rng(seed).uniform(1.0, 5.0, sc["n"]).astype(np.float32).astype(np.float64)
+    return out
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+def test_gfsgs_matches_oracle(pairs):
+    sc = _gfsgs(scenes.with_emission(scenes.fruit_bowl(n=1500, L=2, nd=64, nb=3, n_lights=2), seed=3), 4)
+    if pairs:
+        sc["lam"] = np.random.default_rng(6).uniform(0.5, 1.5, sc["n"]).astype(np.float32).astype(np.float64)
+    W = np.random.default_rng(5).normal(size=(sc["n"], 9, 6))
+    o = run_oracle(sc, W=W, iterates=True, alpha_model=O.ALPHA_GFSGS, pairs=pairs)
+    g = run_gpu(sc, W=W, iterates=True, alpha_model=rgs.RGS_ALPHA_GFSGS, pairs=pairs)
+    for b, (gi, oi) in enumerate(zip(g["iters"], o["iters"])):
+        assert rel_l2(gi, oi) <= TOL, b
+    for key in (("dE", "dad", "dop", "dlam") if pairs else ("dE", "dad", "dop")):
+        assert rel_l2(g[key], o[key]) <= TOL, key
