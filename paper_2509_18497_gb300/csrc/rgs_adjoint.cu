@@ -261,10 +261,9 @@ __global__ void RGS_OPA_LB k_opacity_g(SceneDev sc, RaysDev rays, int C, int col
 
 // Hemisphere rays, part 2: back to front, R_{h-1} = alpha_h g_h + (1 - alpha_h) R_h and
 // dL/do_{j_h} += T_h (g_h - R_h) dalpha_h/do, with T_h the transmittance in front of hit h.
-// G_h is recomputed from the stored direction (bit-identical to the trace's value).  With
-// per_slot the contribution replaces g_h in gh (k_dop_src sums them per source without
-// atomics); otherwise it is added to dop atomically.
-__global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, float *gh, float *dop, int per_slot) {
+// G_h is recomputed from the stored direction (bit-identical to the trace's value).
+__global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const float *__restrict__ gh,
+                                                     float *dop) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= sc.n * rays.nd) return;
     const int cnt = rays.cnt[r];
@@ -291,30 +290,8 @@ __global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, float *gh
         const float alpha = alpha_of(sc, oj, G);
         const float g = gh[slot];
         const float da = Th[h] * (g - R);
-        if (per_slot) gh[slot] = da * dalpha_do(sc, oj, G);
-        else if (da != 0.f) atomicAdd(&dop[j], da * dalpha_do(sc, oj, G));
+        if (da != 0.f) atomicAdd(&dop[j], da * dalpha_do(sc, oj, G));
         R = alpha * g + (1.f - alpha) * R;
-    }
-}
-
-// dL/do_j += sum of the per-record contributions of k_opacity_rec over source j's records,
-// found through the transposed index (entry e: ray tr[e].x, hit tr_h[e]); one CTA per source
-__global__ void __launch_bounds__(ADJ_THREADS) k_dop_src(RaysDev rays, const long long *__restrict__ src_off,
-                                                        const int2 *__restrict__ tr, const unsigned char *__restrict__ tr_h,
-                                                        const float *__restrict__ per_slot, float *dop) {
-    __shared__ float red[ADJ_THREADS / 32];
-    const int j = blockIdx.x;
-    float s = 0.f;
-    for (long long e = src_off[j] + threadIdx.x; e < src_off[j + 1]; e += ADJ_THREADS)
-        s += __ldg(&per_slot[__ldg(&rays.off[__ldg(&tr[e]).x]) + __ldg(&tr_h[e])]);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < ADJ_THREADS / 32; ++w) t += red[w];
-        dop[j] += t;
     }
 }
 
@@ -346,8 +323,8 @@ __global__ void k_finalize(SceneDev sc, int C, const float *__restrict__ u, cons
 
 // transposed index: the records of every ray on a source j0 <= j < j1 scattered into
 // per-source lists of (ray, a), stored from entry ebase = src_off[j0] on
-__global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr, unsigned char *tr_h,
-                           int j0, int j1, long long ebase) {
+__global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor, int2 *tr, int j0, int j1,
+                           long long ebase) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     const long long base = rays.off[r];
@@ -357,7 +334,6 @@ __global__ void k_src_fill(RaysDev rays, int n_rays, unsigned long long *cursor,
         if (ja.x < j0 || ja.x >= j1) continue;
         const unsigned long long pos = atomicAdd(&cursor[ja.x], 1ull);
         tr[(long long)pos - ebase] = make_int2(r, ja.y);
-        if (tr_h) tr_h[(long long)pos - ebase] = (unsigned char)h; // the entry's slot is off[r] + h
     }
 }
 
@@ -373,7 +349,7 @@ rgs_status build_index(rgs_transport *t, int j0, int j1, long long ebase, cudaSt
     const long long n_rays = (long long)n * t->nd;
     RaysDev rd = t->rays();
     { ProfScope ps_("k_copy_off", st); k_copy_off<<<(n + 255) / 256, 256, 0, st>>>(t->src_off, t->cursor, n); }
-    { ProfScope ps_("k_src_fill", st); k_src_fill<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->cursor, t->tr, t->tr_h, j0, j1, ebase); }
+    { ProfScope ps_("k_src_fill", st); k_src_fill<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, (int)n_rays, t->cursor, t->tr, j0, j1, ebase); }
     RGS_LAUNCH("transposed index");
     return RGS_OK;
 }
@@ -532,9 +508,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
-        const int per_slot = t->tr_h != nullptr;
-        { ProfScope ps_("k_opacity_rec", st); k_opacity_rec<<<gr, 256, 0, st>>>(sd, rd, t->gh, t->dop, per_slot); }
-        if (per_slot) { ProfScope ps_("k_dop_src", st); k_dop_src<<<n, ADJ_THREADS, 0, st>>>(rd, t->src_off, t->tr, t->tr_h, t->gh, t->dop); }
+        { ProfScope ps_("k_opacity_rec", st); k_opacity_rec<<<gr, 256, 0, st>>>(sd, rd, t->gh, t->dop); }
         RGS_LAUNCH("hemisphere opacity backward");
     }
     { ProfScope ps_("k_finalize", st); k_finalize<NC><<<gn, 128, 0, st>>>(sd, C, t->u, t->Pg, t->sc->kk, t->dop, dE, dad, dopo); }
@@ -624,7 +598,6 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
             pool_release(t->v, st);
             pool_release(t->u, st);
             pool_release(t->tr, st);
-            pool_release(t->tr_h, st);
             pool_release(t->dy, st);
             pool_release(t->dy_mc, st);
             pool_release(t->gh, st);
@@ -675,10 +648,6 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
         biggest = std::max(biggest, e1 - base[p]);
     }
     if ((r = pool_alloc(&t->tr, (size_t)std::max(biggest, 1ll), st)) != RGS_OK) return r;
-    // with the index in one part, the opacity recurrence's per-record terms are summed per
-    // source through it (no atomics); the record's position in its ray rides along (1 byte)
-    if (parts.size() == 2 && want_gh && (r = pool_alloc(&t->tr_h, (size_t)std::max(t->n_hits, 1ll), st)) != RGS_OK)
-        return r;
     if (parts.size() == 2 && (r = build_index(t, 0, n, 0, st)) != RGS_OK) return r;
     switch (t->nc) {
     case 1: return run_adjoint<1>(t, g, dE, dad, dop, parts, base, st);

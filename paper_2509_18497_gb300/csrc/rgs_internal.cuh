@@ -548,7 +548,6 @@ struct rgs_transport {
     int *src_cnt = nullptr;
     unsigned long long *cursor = nullptr;
     int2 *tr = nullptr; // (ray id, bits of a), for the sources of the current index part
-    unsigned char *tr_h = nullptr; // hit position of each entry in its ray (one-part index only)
     int src_cap = 0;      // surfels allocated in src_off / src_cnt / cursor
     long long *scan_tmp = nullptr;
     int scan_tmp_cap = 0;
