@@ -53,6 +53,24 @@ ENV_WORKLOAD = ("environment map: fruit bowl, 50,000 surfels, SH degree 3, 256 r
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's `x` (seconds of the timed region), followed by a
+    barrier; with one process, `x` itself.  The job's time is its slowest rank's."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(units_per_step, steps, world, total_s):
+    """Whole-job units per second: every rank processes `units_per_step` per step
+    (replicas), over the slowest rank's `total_s`."""
+    return units_per_step * steps * world / total_s
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -364,13 +382,8 @@ def main():
             rgs.rgs_profile_enable(False)
             prof = rgs.rgs_profile_report()
         step_ms = [a.elapsed_time(b) for a, b in ev]
-        total_s = sum(step_ms) / 1e3
-        if world > 1:
-            t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
-            dist.barrier()
-        return units_per_step * args.steps * world / total_s, step_ms, launches, prof, t_wall
+        total_s = max_over_ranks(sum(step_ms) / 1e3, dist if world > 1 else None, dev)
+        return job_throughput(units_per_step, args.steps, world, total_s), step_ms, launches, prof, t_wall
 
     clocks = Clocks(local)
     res, outs = {}, {}
@@ -432,12 +445,8 @@ def main():
                 dst.copy_(src, non_blocking=True)
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
-    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = units_per_step * args.steps * world / e2e_s
+    e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dist if world > 1 else None, dev)
+    e2e_value = job_throughput(units_per_step, args.steps, world, e2e_s)
 
     if rank != 0:
         if world > 1:
