@@ -88,7 +88,7 @@ def _src_sha(name):
 # DRAM bytes per launch from one ncu capture (profiles/), keyed by kernel; valid only
 # while the kernel's source file is unchanged since the capture.
 NCU_TRAFFIC = {
-    "k_trace_hemi": {"bytes_per_launch": 0.986917e9 + 2.053628e9, "n": 10000, "src_sha": "5509d3f1294b98a4"},
+    "k_trace_hemi": {"bytes_per_launch": 0.999770e9 + 2.009972e9, "n": 10000, "src_sha": "77c7ef57011d69f1"},
 }
 
 
