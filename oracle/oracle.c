@@ -1399,3 +1399,301 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ geometry gradients
+ * Gradient of the real SH basis (the polynomial form or_sh_eval evaluates, in x, y, z):
+ * dY[a * nc + k] = dY_k / d(dir_a).  Only its tangential part enters the gradients below
+ * (every direction they differentiate is a unit vector), so the extension of Y off the
+ * sphere does not matter.  Obtained by differentiating or_sh_eval's recurrences:
+ *   d Pt[l][m]/dz from the same three-term recurrence, and d(x + i y)^m = m (x + i y)^{m-1}
+ *   (dx + i dy). */
+void or_sh_grad(int L, const double *dir, double *Y, double *dY) {
+    double x = dir[0], y = dir[1], z = dir[2];
+    int nc = (L + 1) * (L + 1);
+    double Pt[32][32], Pd[32][32];
+    for (int m = 0; m <= L; ++m) {
+        double pmm = 1.0;
+        for (int q = 1; q <= m; ++q) pmm *= -(2.0 * q - 1.0);
+        Pt[m][m] = pmm;
+        Pd[m][m] = 0.0;
+        if (m + 1 <= L) {
+            Pt[m + 1][m] = z * (2.0 * m + 1.0) * pmm;
+            Pd[m + 1][m] = (2.0 * m + 1.0) * pmm;
+        }
+        for (int l = m + 2; l <= L; ++l) {
+            Pt[l][m] = ((2.0 * l - 1.0) * z * Pt[l - 1][m] - (l + m - 1.0) * Pt[l - 2][m]) / (double)(l - m);
+            Pd[l][m] = ((2.0 * l - 1.0) * (Pt[l - 1][m] + z * Pd[l - 1][m]) - (l + m - 1.0) * Pd[l - 2][m]) /
+                       (double)(l - m);
+        }
+    }
+    double cm[32], sm[32];
+    cm[0] = 1.0;
+    sm[0] = 0.0;
+    for (int m = 1; m <= L; ++m) {
+        cm[m] = cm[m - 1] * x - sm[m - 1] * y;
+        sm[m] = cm[m - 1] * y + sm[m - 1] * x;
+    }
+    for (int q = 0; q < 3 * nc; ++q) dY[q] = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        for (int m = 0; m <= l; ++m) {
+            double ratio = 1.0;
+            for (int q = l - m + 1; q <= l + m; ++q) ratio /= (double)q;
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * ratio);
+            if (m == 0) {
+                int k = l * l + l;
+                if (Y) Y[k] = K * Pt[l][0];
+                dY[2 * nc + k] = K * Pd[l][0];
+            } else {
+                double c2 = sqrt(2.0) * K;
+                int kc = l * l + l + m, ks = l * l + l - m;
+                if (Y) {
+                    Y[kc] = c2 * Pt[l][m] * cm[m];
+                    Y[ks] = c2 * Pt[l][m] * sm[m];
+                }
+                dY[0 * nc + kc] = c2 * Pt[l][m] * m * cm[m - 1];
+                dY[1 * nc + kc] = -c2 * Pt[l][m] * m * sm[m - 1];
+                dY[2 * nc + kc] = c2 * Pd[l][m] * cm[m];
+                dY[0 * nc + ks] = c2 * Pt[l][m] * m * sm[m - 1];
+                dY[1 * nc + ks] = c2 * Pt[l][m] * m * cm[m - 1];
+                dY[2 * nc + ks] = c2 * Pd[l][m] * sm[m];
+            }
+        }
+    }
+}
+
+/* out = sum_k coef[k] grad Y_k(w) */
+static void sh_grad_dot(int L, const double *w, const double *coef, double *out) {
+    int nc = (L + 1) * (L + 1);
+    double dY[3 * 1024];
+    or_sh_grad(L, w, NULL, dY);
+    for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k < nc; ++k) acc += coef[k] * dY[a * nc + k];
+        out[a] = acc;
+    }
+}
+
+/* d alpha / d q of a hit at squared local radius q = u^2 + v^2 (G = exp(-q/2)):
+ * -o G / 2 for the Gaussian, 0 inside the disc, -1.7 p e^{-p} for GFSGS (p = 0.03279 (o G)^3.4). */
+static double dalpha_dq(const or_scene *s, double o, double G) {
+    if (s->alpha_model == OR_ALPHA_DISC) return 0.0;
+    if (s->alpha_model == OR_ALPHA_GFSGS) {
+        double xx = o * G;
+        if (!(xx > 0.0)) return 0.0;
+        double p = 0.03279 * pow(xx, 3.4);
+        return -1.7 * p * exp(-p);
+    }
+    return -0.5 * o * G;
+}
+
+/* Crossing of the segment o + t d with the plane of occluder k: returns q = u^2 + v^2 and
+ * fills pw = P_k^T grad_x q (with P_k = I - d n_k^T / (n_k.d) the projector onto plane k
+ * along d), t, u and v.  Then dq = pw . (do - dp_k + t dd) and dq/ds^u_k = -2 u^2 / s^u_k,
+ * dq/ds^v_k = -2 v^2 / s^v_k. */
+static double occluder_crossing(const or_scene *s, int k, const double *o, const double *d, double *pw, double *t,
+                                double *u, double *v) {
+    const double *nk = s->nrm + k * 3, *pk = s->p + k * 3, *tu = s->tu + k * 3, *tv = s->tv + k * 3;
+    double den = dot3(nk, d);
+    double w[3] = {pk[0] - o[0], pk[1] - o[1], pk[2] - o[2]};
+    *t = dot3(nk, w) / den;
+    double q[3] = {*t * d[0] - w[0], *t * d[1] - w[1], *t * d[2] - w[2]};
+    *u = dot3(q, tu) / s->su[k];
+    *v = dot3(q, tv) / s->sv[k];
+    double g[3];
+    for (int a = 0; a < 3; ++a) g[a] = 2.0 * (*u * tu[a] / s->su[k] + *v * tv[a] / s->sv[k]);
+    double dg = dot3(d, g) / den;
+    for (int a = 0; a < 3; ++a) pw[a] = g[a] - nk[a] * dg;
+    return *u * *u + *v * *v;
+}
+
+/* Adds the gradient of T = prod_m (1 - alpha_m) over the occluders (k[m], G[m]) of the
+ * segment o + t d, scaled by up, to the origin's position (gpo), the direction (gd) and
+ * the occluders' positions and scales. */
+static void occluder_backward(const or_scene *s, const double *o, const double *d, int cnt, const int *kk,
+                              const double *al, const double *G, double up, double *gpo, double *gd, double *dp,
+                              double *ds) {
+    for (int q = 0; q < cnt; ++q) {
+        double others = 1.0;
+        for (int m = 0; m < cnt; ++m)
+            if (m != q) others *= 1.0 - al[m];
+        const int k = kk[q];
+        double pw[3], t, u, v;
+        occluder_crossing(s, k, o, d, pw, &t, &u, &v);
+        /* dL = up * dT = -up * others * dalpha/dq * dq */
+        double coef = -up * others * dalpha_dq(s, s->o[k], G[q]);
+        for (int a = 0; a < 3; ++a) {
+            gpo[a] += coef * pw[a];
+            gd[a] += coef * t * pw[a];
+            if (dp) dp[k * 3 + a] -= coef * pw[a];
+        }
+        if (ds) {
+            ds[k * 2] += coef * (-2.0 * u * u / s->su[k]);
+            ds[k * 2 + 1] += coef * (-2.0 * v * v / s->sv[k]);
+        }
+    }
+}
+
+/* Geometry gradients (Eqs. dl-dgeo-0 and dl-dgeo-1, Sec. 6 / App. C) of L(B^(nb)) with
+ * g = dL/dB^(nb), for the center-to-center transport: dp [N][3] = dL/dp_i and
+ * ds [N][2] = dL/d(s^u_i, s^v_i), frames held fixed.  Per pair (i <- j), with
+ * L_e = V_ji sum_{a,c} y_c^(a) s_c^(nb-1-a), y_c = o_i sum_k c_{i,l(k),ch} Y_k(R_i d) v_i^(a)[k][c]
+ * and s_c = sum_k Y_k(-d) B_j[k][c]:
+ *   - the decay term V_ji = lambda_j A_j T geo: geo = (n_i.d)|n_j.d|/r^2 through d and r,
+ *     A_j proportional to s^u_j s^v_j, and T through every occluder's crossing point
+ *     (which moves with p_i, d and p_k) and its scales;
+ *   - the directional effects: Y(R_i d) and Y(-d) through d;
+ *   d = (p_j - p_i)/r moves with (I - d d^T)/r (dp_j - dp_i), r with d.(dp_j - dp_i).
+ * The direct term adds, per (receiver, light), the derivative of
+ * sum_k h_k Y_k(R_i w) (n_i.w) fall T in w = (p_L - p_i)/r, in fall = 1/r^2 and in its
+ * shadow occluders (a directional light has a fixed w and fall = 1).  Discrete events
+ * (front tests, the 3-sigma cutoff, the eps_plane rules) are held fixed: the gradient is
+ * the derivative of the smooth piece the scene sits on.  Returns 0, or -1 without a
+ * center-to-center transport. */
+int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g, double *dp, double *ds) {
+    if (!s->pmode) return -1;
+    int n = s->n, nc = s->nc, C = s->C, L = s->L, nl = s->nl;
+    size_t M = (size_t)n * nc * C;
+    double *iters = dup_arr(NULL, M * (nb + 1));
+    double *Bn = dup_arr(NULL, M);
+    or_solve(s, E, nb, Bn, iters);
+    double *v = dup_arr(NULL, M * (nb + 1));
+    memcpy(v, g, sizeof(double) * M);
+    for (int a = 1; a <= nb; ++a) or_apply_KT(s, v + (size_t)(a - 1) * M, v + (size_t)a * M);
+    double *u = dup_arr(NULL, M);
+    memset(u, 0, sizeof(double) * M);
+    for (int a = 0; a <= nb; ++a)
+        for (size_t q = 0; q < M; ++q) u[q] += v[(size_t)a * M + q];
+    memset(dp, 0, sizeof(double) * (size_t)n * 3);
+    memset(ds, 0, sizeof(double) * (size_t)n * 2);
+    double Yo[1024], Yi[1024], wi[1024], wo[1024];
+    int *kk = NULL;
+    double *al = NULL, *Gk = NULL;
+    int kcap = 0;
+    /* pairs */
+    for (int i = 0; i < n; ++i)
+        for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
+            const int j = s->pair_j[e];
+            double dv[3] = {s->p[j * 3] - s->p[i * 3], s->p[j * 3 + 1] - s->p[i * 3 + 1], s->p[j * 3 + 2] - s->p[i * 3 + 2]};
+            double r = sqrt(dot3(dv, dv)), d[3], md[3], rd[3];
+            for (int a = 0; a < 3; ++a) {
+                d[a] = dv[a] / r;
+                md[a] = -d[a];
+            }
+            reflect(s->nrm + i * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            double ge = 0.0;
+            for (int k = 0; k < nc; ++k) wi[k] = wo[k] = 0.0;
+            for (int a = 0; a < nb; ++a) {
+                const double *Bb = iters + (size_t)(nb - 1 - a) * M + (size_t)j * nc * C;
+                const double *va = v + (size_t)a * M + (size_t)i * nc * C;
+                for (int c = 0; c < C; ++c) {
+                    double yv = 0.0, sv = 0.0;
+                    for (int k = 0; k < nc; ++k) {
+                        const double cy = alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(k)) * 3 + c % 3];
+                        yv += cy * Yi[k] * va[k * C + c];
+                        sv += Yo[k] * Bb[k * C + c];
+                    }
+                    ge += yv * sv;
+                    for (int k = 0; k < nc; ++k) {
+                        wi[k] += sv * alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(k)) * 3 + c % 3] * va[k * C + c];
+                        wo[k] += yv * Bb[k * C + c];
+                    }
+                }
+            }
+            const double A = or_alpha_area(s, j), T = s->pair_T[e], geo = s->pair_geo[e], lam = s->lam[j];
+            const double V = lam * A * T * geo;
+            double gd[3] = {0.0, 0.0, 0.0}, gpi[3] = {0.0, 0.0, 0.0};
+            /* directional effects: Y(R_i d) (R_i symmetric) and Y(-d) */
+            double t1[3], t2[3], t3[3];
+            sh_grad_dot(L, rd, wi, t1);
+            reflect(s->nrm + i * 3, t1, t3); /* R_i t1 = 2 (n.t1) n - t1 */
+            sh_grad_dot(L, md, wo, t2);
+            for (int a = 0; a < 3; ++a) gd[a] += V * (t3[a] - t2[a]);
+            /* decay term: geo through d and r */
+            const double ni_d = dot3(s->nrm + i * 3, d), nj_d = dot3(s->nrm + j * 3, d);
+            const double sj = nj_d >= 0.0 ? 1.0 : -1.0;
+            for (int a = 0; a < 3; ++a)
+                gd[a] += ge * lam * A * T * (fabs(nj_d) * s->nrm[i * 3 + a] + ni_d * sj * s->nrm[j * 3 + a]) / (r * r);
+            const double gr = ge * lam * A * T * (-2.0 * geo / r);
+            /* source scales through A_j */
+            ds[j * 2] += ge * lam * T * geo * A / s->su[j];
+            ds[j * 2 + 1] += ge * lam * T * geo * A / s->sv[j];
+            /* occluders */
+            const long q0 = s->poc_off[e], q1 = s->poc_off[e + 1];
+            const int cnt = (int)(q1 - q0);
+            if (cnt > kcap) {
+                kcap = 2 * cnt;
+                kk = (int *)realloc(kk, sizeof(int) * kcap);
+                al = (double *)realloc(al, sizeof(double) * kcap);
+                Gk = (double *)realloc(Gk, sizeof(double) * kcap);
+            }
+            for (int q = 0; q < cnt; ++q) {
+                kk[q] = s->poc_j[q0 + q];
+                al[q] = s->poc_alpha[q0 + q];
+                Gk[q] = s->poc_G[q0 + q];
+            }
+            occluder_backward(s, s->p + i * 3, d, cnt, kk, al, Gk, ge * lam * A * geo, gpi, gd, dp, ds);
+            /* d and r in p_i, p_j */
+            const double dd = dot3(d, gd);
+            for (int a = 0; a < 3; ++a) {
+                const double gp = (gd[a] - d[a] * dd) / r + d[a] * gr;
+                dp[j * 3 + a] += gp;
+                dp[i * 3 + a] += gpi[a] - gp;
+            }
+        }
+    /* direct term */
+    for (int i = 0; i < n; ++i)
+        for (int lt = 0; lt < nl; ++lt) {
+            const double pre = s->sh_pre[(long)i * nl + lt];
+            if (pre == 0.0) continue;
+            double w[3], rw[3], r;
+            light_geom(s, i, s->lp + lt * 3, w, &r);
+            reflect(s->nrm + i * 3, w, rw);
+            or_sh_eval(L, rw, Yi);
+            double H = 0.0;
+            for (int k = 0; k < nc; ++k) {
+                double hk = 0.0;
+                for (int ch = 0; ch < 3; ++ch)
+                    hk += u[((size_t)i * nc + k) * C + lt * 3 + ch] * alpha_c(s, i) *
+                          s->c[((size_t)i * (L + 1) + band_of(k)) * 3 + ch] * s->li[lt * 3 + ch];
+                wi[k] = hk;
+                H += hk * Yi[k];
+            }
+            const long q0 = s->sh_off[(long)i * nl + lt], q1 = s->sh_off[(long)i * nl + lt + 1];
+            const int cnt = (int)(q1 - q0);
+            if (cnt > kcap) {
+                kcap = 2 * cnt;
+                kk = (int *)realloc(kk, sizeof(int) * kcap);
+                al = (double *)realloc(al, sizeof(double) * kcap);
+                Gk = (double *)realloc(Gk, sizeof(double) * kcap);
+            }
+            double T = 1.0;
+            for (int q = 0; q < cnt; ++q) {
+                kk[q] = s->sh_j[q0 + q];
+                al[q] = s->sh_alpha[q0 + q];
+                Gk[q] = s->sh_G[q0 + q];
+                T *= 1.0 - al[q];
+            }
+            const double cs = dot3(s->nrm + i * 3, w);
+            const double fall = s->ldir ? 1.0 : 1.0 / (r * r);
+            double gw[3] = {0.0, 0.0, 0.0}, gpi[3] = {0.0, 0.0, 0.0}, t1[3], t3[3];
+            sh_grad_dot(L, rw, wi, t1);
+            reflect(s->nrm + i * 3, t1, t3);
+            for (int a = 0; a < 3; ++a) gw[a] += fall * T * (cs * t3[a] + H * s->nrm[i * 3 + a]);
+            occluder_backward(s, s->p + i * 3, w, cnt, kk, al, Gk, H * cs * fall, gpi, gw, dp, ds);
+            for (int a = 0; a < 3; ++a) dp[i * 3 + a] += gpi[a];
+            if (!s->ldir) { /* w = (p_L - p_i)/r, fall = 1/r^2 */
+                const double ww = dot3(w, gw), gr = H * cs * T * (-2.0 / (r * r * r));
+                for (int a = 0; a < 3; ++a) dp[i * 3 + a] += -(gw[a] - w[a] * ww) / r - w[a] * gr;
+            }
+        }
+    free(kk);
+    free(al);
+    free(Gk);
+    free(iters);
+    free(Bn);
+    free(v);
+    free(u);
+    return 0;
+}

@@ -88,6 +88,9 @@ def lib():
             L.or_sample_direct.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, ct.c_int, _ip, _dp]
             L.or_sample_bounce1.argtypes = [ct.c_void_p, ct.c_int, ct.c_uint64, ct.c_int, _dp, _dp, _dp,
                                             ct.c_int, _ip, _dp]
+            L.or_sh_grad.argtypes = [ct.c_int, _dp, _dp, _dp]
+            L.or_geometry_grad.restype = ct.c_int
+            L.or_geometry_grad.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp]
             L.or_num_threads.restype = ct.c_int
             _lib = L
     return _lib
@@ -110,6 +113,15 @@ def sh_eval(L, d):
     out = np.zeros((L + 1) ** 2)
     lib().or_sh_eval(L, _ptr(d), _ptr(out))
     return out
+
+
+def sh_grad(L, d):
+    """(Y, dY) at direction d: dY[a, k] = dY_k/d(d_a) of the polynomial form."""
+    d = _d(d).reshape(3)
+    Y = np.zeros((L + 1) ** 2)
+    dY = np.zeros((3, (L + 1) ** 2))
+    lib().or_sh_grad(L, _ptr(d), _ptr(Y), _ptr(dY))
+    return Y, dY
 
 
 def phong_rho(l, s):
@@ -281,6 +293,16 @@ class Oracle:
         if getattr(self, "pmode", False):
             out["dlam"] = dlam
         return out
+
+    def geometry_grad(self, g, E=None, nb=None):
+        """Center-to-center transport: dL/dp [N][3] and dL/d(s^u, s^v) [N][2]."""
+        nb = self.sc["nb"] if nb is None else nb
+        dp = np.zeros((self.n, 3))
+        ds = np.zeros((self.n, 2))
+        rc = lib().or_geometry_grad(self.h, _ptr(_d(E)), int(nb), _ptr(_d(g).reshape(self._shape())), _ptr(dp), _ptr(ds))
+        if rc != 0:
+            raise RuntimeError("geometry gradients need the center-to-center transport (pairs())")
+        return dict(dp=dp, ds=ds)
 
     def brdf_grad_closed_form(self, g, E=None, nb=None):
         nb = self.sc["nb"] if nb is None else nb

@@ -1,0 +1,107 @@
+"""Pins of the oracle's geometry gradients (Eqs. dl-dgeo-0 and dl-dgeo-1) for the
+center-to-center transport: the SH gradient against tangent differences of the SH
+(which is itself pinned to scipy), the lone plane's direct term against its closed form,
+and the full dL/dp, dL/ds against central differences of the whole forward solve for the
+Gaussian and GFSGS opacity models, point and directional lights (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_18497_gb300 import scenes
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_sh_gradient_matches_tangent_differences(L):
+    rng = np.random.default_rng(L)
+    for _ in range(8):
+        w = rng.normal(size=3)
+        w /= np.linalg.norm(w)
+        t = np.cross(w, rng.normal(size=3))
+        t /= np.linalg.norm(t)
+        Y, dY = O.sh_grad(L, w)
+        np.testing.assert_allclose(Y, O.sh_eval(L, w), rtol=1e-14, atol=1e-15)
+
+        def Yat(a):
+            x = w + a * t
+            return O.sh_eval(L, x / np.linalg.norm(x))
+        h = 1e-4
+        num = (4 * (Yat(h / 2) - Yat(-h / 2)) / h - (Yat(h) - Yat(-h)) / (2 * h)) / 3
+        np.testing.assert_allclose(dY.T @ t, num, atol=1e-10)
+    # band 1 is linear: Y_1-1 = -c y, Y_10 = c z, Y_11 = -c x (Condon-Shortley phase)
+    c = math.sqrt(3.0 / (4.0 * math.pi))
+    _, dY = O.sh_grad(1, np.array([0.3, -0.5, math.sqrt(1 - 0.34)]))
+    np.testing.assert_allclose(dY[:, 1], [0, -c, 0], atol=1e-15)
+    np.testing.assert_allclose(dY[:, 2], [0, 0, c], atol=1e-15)
+    np.testing.assert_allclose(dY[:, 3], [-c, 0, 0], atol=1e-15)
+
+
+def test_lone_plane_position_gradient_closed_form():
+    """B_00 = 2 sqrt(pi) (o k a^d / pi) I n.l / |l|^3 with l = p_L - p, so
+    dB_00/dp = 2 sqrt(pi) (o k a^d / pi) I (-n / |l|^3 + 3 (n.l) l / |l|^5)."""
+    sc = scenes.lone_plane(L=2, o=0.8, ad=(0.5, 0.3, 0.2), k=1.0)
+    orc = O.Oracle(sc).pairs()
+    W = np.zeros((1, orc.nc, orc.C))
+    W[0, 0, 1] = 1.0  # L = B_00 of the green channel
+    gg = orc.geometry_grad(W, nb=2)
+    lp, I = sc["light_pos"][0], sc["light_I"][0][1]
+    l = lp - sc["p"][0]
+    r = np.linalg.norm(l)
+    n = np.array([0.0, 0.0, 1.0])
+    pre = 2 * math.sqrt(math.pi) * sc["o"][0] * sc["ad"][0][1] / math.pi * I
+    expect = pre * (-n / r ** 3 + 3 * (n @ l) * l / r ** 5)
+    np.testing.assert_allclose(gg["dp"][0], expect, rtol=1e-12)
+    np.testing.assert_allclose(gg["ds"][0], 0.0, atol=1e-15)  # nothing depends on the scale
+
+
+def _fd_check(sc, alpha_model=O.ALPHA_GAUSS, directional=False, stride=3):
+    def make(s2):
+        o2 = O.Oracle(s2, alpha_model=alpha_model)
+        if directional:
+            O.lib().or_set_directional(o2.h, 1)
+        return o2.pairs()
+    orc = make(sc)
+    W = np.random.default_rng(9).normal(size=(sc["n"], orc.nc, orc.C))
+    gg = orc.geometry_grad(W, E=sc["E"], nb=sc["nb"])
+
+    def loss(s2):
+        return float(np.sum(W * make(s2).solve(E=s2["E"], nb=s2["nb"])))
+
+    def fd(key, idx, h=1e-5):
+        def at(hh):
+            s2 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+            s2[key][idx] += hh
+            return loss(s2)
+        def cd(hh):
+            return (at(hh) - at(-hh)) / (2 * hh)
+        return (4 * cd(h / 2) - cd(h)) / 3
+
+    # central differences of a loss of size |L0| carry a rounding error of about
+    # |L0| eps / h = 1e-11 |L0|; the truncation error of the extrapolated form is far below
+    floor = 1e-9 * abs(loss(sc))
+    for key, m in (("p", 3), ("s", 2)):
+        an = gg["d" + key]
+        scale = np.abs(an).max()
+        assert scale > 0
+        for i in range(0, sc["n"], stride):
+            for a in range(m):
+                num = fd(key, (i, a))
+                assert abs(num - an[i, a]) <= 1e-7 * scale + floor, (key, i, a, num, an[i, a])
+
+
+def test_geometry_gradients_match_finite_differences():
+    sc = scenes.with_emission(scenes.random_cluster(n=40, seed=7, L=2, nb=3, n_lights=2), seed=5)
+    _fd_check(sc)
+
+
+def test_geometry_gradients_gfsgs_and_directional():
+    sc = scenes.with_emission(scenes.random_cluster(n=30, seed=3, L=2, nb=3, n_lights=2), seed=5)
+    _fd_check(sc, alpha_model=O.ALPHA_GFSGS, stride=4)
+    _fd_check(sc, directional=True, stride=4)
+
+
+def test_geometry_gradients_need_pairs():
+    sc = scenes.lone_plane()
+    with pytest.raises(RuntimeError):
+        O.Oracle(sc).transport().geometry_grad(np.zeros((1, 9, 3)), nb=1)
