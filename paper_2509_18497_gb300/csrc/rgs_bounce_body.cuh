@@ -51,6 +51,55 @@ template <int NC, class T> constexpr int row_stride() {
     return sizeof(T) == 2 ? ((NC >= 9) ? 16 : NC) : NC;
 }
 
+// Dot products of Y with the 32 columns of one FP32 source row tile (nc = 16: 64 B per
+// column, 2 KB per tile), read as four contiguous 512-B warp requests, a lane taking 16 B
+// (a quarter of one column).  Each lane forms its partial dot products with its quarter of
+// Y, and a reduce-scatter over the 4 lanes holding each column leaves lane l with the
+// whole dot product of tile column own(l).  A 64-B column row per lane at a 64-B stride
+// costs the L1 about twice the wavefronts for the same bytes (measured: the FP32 form of
+// the 300- and 1,536-column workloads 6 % and 25 % faster).  For BF16 rows (32 B per
+// column) the same scheme measured 3-7 % slower than a row per lane and is not used.
+// Columns past the tile's `ncols` live ones read the last live column (their results are
+// not used).  All 32 lanes take part (the shuffles use the full mask).
+template <class T, int NC> struct TileDot;
+
+template <int NC> struct TileDot<float, NC> {
+    static_assert(NC == 16, "FP32 tiles of 16 coefficients per column");
+    static constexpr int KPL = 4;
+    __device__ static int own(int lane) {
+        const int g = lane & 3;
+        return 8 * (2 * (g & 1) + (g >> 1)) + (lane >> 2);
+    }
+    __device__ static void pick(const float *Y, int lane, float (&y)[KPL]) {
+        const int g = lane & 3;
+#pragma unroll
+        for (int m = 0; m < KPL; ++m) {
+            float v = Y[m];
+            v = g == 1 ? Y[4 + m] : v;
+            v = g == 2 ? Y[8 + m] : v;
+            v = g == 3 ? Y[12 + m] : v;
+            y[m] = v;
+        }
+    }
+    // tile: the tile's first column in source row j; ncols: its live columns (1..32)
+    __device__ static float dot(const float *__restrict__ tile, int ncols, int lane, const float (&y)[KPL]) {
+        const int g = lane & 3, a = lane >> 2;
+        float p[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = min(8 * q + a, ncols - 1);
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(tile + c * 16) + g);
+            p[q] = y[0] * f.x + y[1] * f.y + y[2] * f.z + y[3] * f.w;
+        }
+        const bool b0 = (g & 1) != 0, b1 = (g & 2) != 0;
+        const float r0 = __shfl_xor_sync(0xffffffffu, b0 ? p[0] : p[2], 1);
+        const float r1 = __shfl_xor_sync(0xffffffffu, b0 ? p[1] : p[3], 1);
+        const float s0 = (b0 ? p[2] : p[0]) + r0, s1 = (b0 ? p[3] : p[1]) + r1;
+        const float r = __shfl_xor_sync(0xffffffffu, b1 ? s0 : s1, 2);
+        return (b1 ? s1 : s0) + r;
+    }
+};
+
 
 template <int NC, int CT, class SL>
 __device__ __forceinline__ void bounce_epilogue(const SceneDev &sc, int C, const float (&acc)[SL::KPL][CT], float w,
@@ -181,10 +230,14 @@ __device__ __forceinline__ void bounce_receiver_mc(const SceneDev &sc, const Ray
                                                    float *__restrict__ Bout, __nv_bfloat16 *__restrict__ Bout16,
                                                    double *norm2, int i, int tile, float *red) {
     constexpr int RS = row_stride<NC, T>();
+    constexpr bool COOP = sizeof(T) == 4 && NC == 16; // whole-tile reads (TileDot)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int col = tile * 32 + lane;
+    int own = lane; // the tile column whose sums this lane keeps
+    if constexpr (COOP) own = TileDot<T, NC>::own(lane);
+    const int col = tile * 32 + own;
     const bool live = col < C;
     const int colc = live ? col : C - 1;
+    const int ncols = min(32, C - tile * 32);
     const int nd = rays.nd;
     const float3 n = f3(sc.N4[i]);
     float acc[NC];
@@ -198,15 +251,25 @@ __device__ __forceinline__ void bounce_receiver_mc(const SceneDev &sc, const Ray
         const int cnt = rays.cnt[r];
         const long long base = rays.off[r];
         float x = 0.f;
+        if constexpr (COOP) {
+            float ys[TileDot<T, NC>::KPL];
+            TileDot<T, NC>::pick(Yo, lane, ys);
 #pragma unroll 2
-        for (int h = 0; h < cnt; ++h) {
-            const int2 ja = __ldg(&rays.rec_ja[base + h]);
-            float v[NC];
-            load_col<NC>(Bg + ((size_t)ja.x * C + colc) * RS, v);
-            float s = 0.f;
+            for (int h = 0; h < cnt; ++h) {
+                const int2 ja = __ldg(&rays.rec_ja[base + h]);
+                x += __int_as_float(ja.y) * TileDot<T, NC>::dot(Bg + ((size_t)ja.x * C + tile * 32) * RS, ncols, lane, ys);
+            }
+        } else {
+#pragma unroll 2
+            for (int h = 0; h < cnt; ++h) {
+                const int2 ja = __ldg(&rays.rec_ja[base + h]);
+                float v[NC];
+                load_col<NC>(Bg + ((size_t)ja.x * C + colc) * RS, v);
+                float s = 0.f;
 #pragma unroll
-            for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
-            x += __int_as_float(ja.y) * s;
+                for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
+                x += __int_as_float(ja.y) * s;
+            }
         }
         float Yi[NC];
         sh_eval<NC>(reflect_n(n, d), Yi);
@@ -214,7 +277,7 @@ __device__ __forceinline__ void bounce_receiver_mc(const SceneDev &sc, const Ray
         for (int k = 0; k < NC; ++k) acc[k] += Yi[k] * x;
     }
 #pragma unroll
-    for (int k = 0; k < NC; ++k) red[(warp * NC + k) * 32 + lane] = acc[k];
+    for (int k = 0; k < NC; ++k) red[(warp * NC + k) * 32 + own] = acc[k];
     __syncthreads();
     double dsq = 0.0;
     const float w = 3.14159265358979f / (float)nd;

@@ -99,6 +99,7 @@ template <int NC, int NA, class T>
 __global__ void RGS_MC_LB k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int ct, int na,
                                                             OpaSet<T, NA> it, float *gh, bool first) {
     constexpr int RS = row_stride<NC, T>();
+    constexpr bool COOP = sizeof(T) == 4 && NC == 16; // whole-tile reads (TileDot)
     const int warp_g = (int)((blockIdx.x * (size_t)MC_THREADS + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     const int n_rays = sc.n * rays.nd;
@@ -106,9 +107,12 @@ __global__ void RGS_MC_LB k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int c
     const int r = warp_g;
     const int cnt = rays.cnt[r];
     if (cnt == 0) return;
-    const int col = ct * 32 + lane;
+    int own = lane; // the tile column whose terms this lane forms
+    if constexpr (COOP) own = TileDot<T, NC>::own(lane);
+    const int col = ct * 32 + own;
     const bool live = col < C;
     const int colc = live ? col : C - 1;
+    const int ncols = min(32, C - ct * 32);
     const int i = r / rays.nd;
     const float3 n = f3(sc.N4[i]);
     const float3 d = f3(rays.dir[r]);
@@ -131,17 +135,23 @@ __global__ void RGS_MC_LB k_opacity_g_mc(SceneDev sc, RaysDev rays, int C, int c
         }
     }
     const long long base = rays.off[r];
+    [[maybe_unused]] float ys[4]; // this lane's quarter of Y(-d) (TileDot)
+    if constexpr (COOP) TileDot<T, NC>::pick(Yo, lane, ys);
     for (int h = 0; h < cnt; ++h) {
         const int j = __ldg(&rays.rec_ja[base + h]).x;
         float acc = 0.f;
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
             if (aa < na) {
-                float v[NC];
-                load_col<NC>(it.b[aa] + ((size_t)j * C + colc) * RS, v);
                 float s = 0.f;
+                if constexpr (COOP) {
+                    s = TileDot<T, NC>::dot(it.b[aa] + ((size_t)j * C + ct * 32) * RS, ncols, lane, ys);
+                } else {
+                    float v[NC];
+                    load_col<NC>(it.b[aa] + ((size_t)j * C + colc) * RS, v);
 #pragma unroll
-                for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
+                    for (int k = 0; k < NC; ++k) s += Yo[k] * v[k];
+                }
                 acc += y[aa] * s;
             }
         }
