@@ -125,10 +125,14 @@ __global__ void RGS_ADJ_LB k_adj_src(RaysDev rays, int C, int col0, const long l
 }
 
 // Shadow rays: dL/dT_L = q = sum_{k,ch} u_i[L,ch][k] o_i c_{i,l,ch} Y_k(R_i w) I cos/r^2,
-// dT/dalpha_m = -prod_{m' != m} (1 - alpha_m'); also adds u (x) Dgeo to P.
+// dT/dalpha_m = -prod_{m' != m} (1 - alpha_m'); also adds u (x) Dgeo to P.  With dp (and
+// ds) the geometry gradients of the direct term as well (Eq. dl-dgeo-1 for the light's
+// direction): with h_k = sum_ch u_i[L,ch][k] o_i c_{i,l(k),ch} I_ch and H = h . Y(R_i w), the
+// term H (n_i.w) fall T moves with w (through Y(R_i w) and n_i.w), with fall = 1/r^2 and with
+// each shadow occluder's crossing point; a directional light has a fixed w and fall = 1.
 template <int NC>
 __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restrict__ lpos, const float *__restrict__ lint,
-                             int C, const float *__restrict__ u, float *P, float *dop) {
+                             int C, const float *__restrict__ u, float *P, float *dop, float *dp, float *ds) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= sc.n * nl) return;
     const int i = tid / nl, lt = tid - i * nl;
@@ -150,37 +154,82 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
     };
     bvh_traverse(sc, o, w, r, pass1);
     const float T = nzero ? 0.f : Tnz;
-    float Y[NC];
-    sh_eval<NC>(reflect_n(n, w), Y);
+    float Y[NC], h[NC];
+    const float3 rw = reflect_n(n, w);
+    sh_eval<NC>(rw, Y);
     const float pre = cs * fall;
     const float *ui = u + ((size_t)i * C + lt * 3) * NC;
+    const float ai = alpha_center(sc, i);
     float qv = 0.f;
     float acc[4][3] = {};
+#pragma unroll
+    for (int k = 0; k < NC; ++k) h[k] = 0.f;
     for (int ch = 0; ch < 3; ++ch) {
         const float I = lint[3 * lt + ch];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
+            const float cl = sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch];
             const float uy = ui[ch * NC + k] * Y[k] * I * pre;
-            qv += uy * sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch];
+            qv += uy * cl;
             acc[band_of(k)][ch] += uy * T;
+            h[k] += ui[ch * NC + k] * I * cl;
         }
     }
     for (int b = 0; b < 4; ++b)
         for (int ch = 0; ch < 3; ++ch)
             if (acc[b][ch] != 0.f) atomicAdd(&P[(size_t)i * 12 + b * 3 + ch], acc[b][ch]);
-    qv *= alpha_center(sc, i);
-    if (qv == 0.f || nzero > 1) return;
-    auto pass2 = [&](int j) {
-        float t, g;
-        if (!hit_surfel(sc, j, i, o, w, r, eps, t, g)) return;
-        const float oj = __ldg(&sc.P[j].w);
-        const float om = 1.f - alpha_of(sc, oj, g);
-        float others;
-        if (nzero == 0) others = Tnz / om;
-        else others = (om == 0.f) ? Tnz : 0.f;
-        if (others != 0.f) atomicAdd(&dop[j], -qv * others * dalpha_do(sc, oj, g));
-    };
-    bvh_traverse(sc, o, w, r, pass2);
+    qv *= ai;
+    float3 gw = make_float3(0.f, 0.f, 0.f), gpi = make_float3(0.f, 0.f, 0.f);
+    float H = 0.f;
+    if (dp) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            h[k] *= ai;
+            H += h[k] * Y[k];
+        }
+        const float3 t3 = reflect_n(n, sh_grad_dot<NC>(rw, h));
+        const float f = fall * T;
+        gw = make_float3(f * (cs * t3.x + H * n.x), f * (cs * t3.y + H * n.y), f * (cs * t3.z + H * n.z));
+    }
+    if (qv != 0.f && nzero <= 1) {
+        auto pass2 = [&](int j) {
+            float t, g;
+            if (!hit_surfel(sc, j, i, o, w, r, eps, t, g)) return;
+            const float oj = __ldg(&sc.P[j].w);
+            const float om = 1.f - alpha_of(sc, oj, g);
+            float others;
+            if (nzero == 0) others = Tnz / om;
+            else others = (om == 0.f) ? Tnz : 0.f;
+            if (others == 0.f) return;
+            atomicAdd(&dop[j], -qv * others * dalpha_do(sc, oj, g));
+            if (dp) {
+                const float coef = -qv * others * dalpha_dq(sc, oj, g);
+                if (coef == 0.f) return;
+                float uu, vv;
+                const float3 pw = crossing_pw(sc, j, o, w, t, uu, vv);
+                gpi = gpi + coef * pw;
+                gw = gw + (coef * t) * pw;
+                atomicAdd(&dp[3 * j], -coef * pw.x);
+                atomicAdd(&dp[3 * j + 1], -coef * pw.y);
+                atomicAdd(&dp[3 * j + 2], -coef * pw.z);
+                atomicAdd(&ds[2 * j], coef * (-2.f * uu * uu * __ldg(&sc.FU[j].w)));
+                atomicAdd(&ds[2 * j + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[j].w)));
+            }
+        };
+        bvh_traverse(sc, o, w, r, pass2);
+    }
+    if (dp) {
+        float3 gp = gpi;
+        if (!ldir) { // w = (p_L - p_i)/r, fall = 1/r^2
+            const float ww = dot3(w, gw), gr = H * cs * T * (-2.f * fall / r);
+            gp.x += -(gw.x - w.x * ww) / r - w.x * gr;
+            gp.y += -(gw.y - w.y * ww) / r - w.y * gr;
+            gp.z += -(gw.z - w.z * ww) / r - w.z * gr;
+        }
+        atomicAdd(&dp[3 * i], gp.x);
+        atomicAdd(&dp[3 * i + 1], gp.y);
+        atomicAdd(&dp[3 * i + 2], gp.z);
+    }
 }
 
 // Hemisphere rays, part 1: for every stored hit h of ray r (receiver i, source j_h),
@@ -504,7 +553,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     if (nb >= 1 && (r = KT(nb)) != RGS_OK) return r; // v^(n) only adds to u
     if (t->nl > 0) {
         const int nth = n * t->nl;
-        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, C, t->u, t->Pg, t->dop); }
+        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, C, t->u, t->Pg, t->dop, nullptr, nullptr); }
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
@@ -541,10 +590,10 @@ template <int NC> rgs_status accum_nc(rgs_transport *t, const float *X, const fl
     RGS_LAUNCH("pair accum");
     return RGS_OK;
 }
-template <int NC> rgs_status shadow_nc(rgs_transport *t, cudaStream_t st) {
+template <int NC> rgs_status shadow_nc(rgs_transport *t, cudaStream_t st, float *dp, float *ds) {
     if (t->nl <= 0) return RGS_OK;
     const int nth = t->n * t->nl;
-    { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->nl, t->ldir, t->lpos, t->lint, t->C, t->u, t->Pg, t->dop); }
+    { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->nl, t->ldir, t->lpos, t->lint, t->C, t->u, t->Pg, t->dop, dp, ds); }
     RGS_LAUNCH("shadow backward");
     return RGS_OK;
 }
@@ -568,8 +617,9 @@ rgs_status rgs_adjoint_prologue(rgs_transport *t, int nc, const float *g, cudaSt
 rgs_status rgs_pair_accum(rgs_transport *t, int nc, const float *X, const float *Y, cudaStream_t st) {
     RGS_NC_SWITCH(nc, accum_nc<1>(t, X, Y, st), accum_nc<4>(t, X, Y, st), accum_nc<9>(t, X, Y, st), accum_nc<16>(t, X, Y, st))
 }
-rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st) {
-    RGS_NC_SWITCH(nc, shadow_nc<1>(t, st), shadow_nc<4>(t, st), shadow_nc<9>(t, st), shadow_nc<16>(t, st))
+rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float *dp, float *ds) {
+    RGS_NC_SWITCH(nc, shadow_nc<1>(t, st, dp, ds), shadow_nc<4>(t, st, dp, ds), shadow_nc<9>(t, st, dp, ds),
+                  shadow_nc<16>(t, st, dp, ds))
 }
 rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st) {
     RGS_NC_SWITCH(nc, finalize_nc<1>(t, dE, dad, dop, st), finalize_nc<4>(t, dE, dad, dop, st),
@@ -578,7 +628,7 @@ rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad,
 #undef RGS_NC_SWITCH
 
 rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st) {
-    if (t->kind == RGS_KIND_PAIRS) return rgs_adjoint_pairs_impl(t, g, dE, dad, dop, nullptr, st);
+    if (t->kind == RGS_KIND_PAIRS) return rgs_adjoint_pairs_impl(t, g, dE, dad, dop, nullptr, nullptr, nullptr, st);
     rgs_status r;
     const int nb = t->nb_last, n = t->n;
     const size_t A = t->arr();

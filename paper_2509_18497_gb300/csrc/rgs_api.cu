@@ -340,22 +340,36 @@ rgs_status rgs_trace_pairs(rgs_scene *scene, const rgs_lights *lights, const rgs
     return RGS_OK;
 }
 
-rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
-                             float *dL_dopacity, float *dL_dlambda, void *stream) {
+static rgs_status adjoint_pairs_checked(const char *fn, rgs_transport *t, const float *dL_dB, float *dL_dE,
+                                        float *dL_dalbedo, float *dL_dopacity, float *dL_dlambda, float *dL_dp,
+                                        float *dL_ds, void *stream) {
     g_err[0] = 0;
     if (!t || !dL_dB) {
-        rgs_set_error("rgs_adjoint_pairs: NULL argument");
+        rgs_set_error("%s: NULL argument", fn);
         return RGS_ERR_ARG;
     }
     if (t->kind != RGS_KIND_PAIRS) {
-        rgs_set_error("rgs_adjoint_pairs: not a center-to-center transport");
+        rgs_set_error("%s: not a center-to-center transport", fn);
         return RGS_ERR_ARG;
     }
     if (t->nb_last < 0) {
-        rgs_set_error("rgs_adjoint_pairs: no rgs_solve on this transport since it was traced");
+        rgs_set_error("%s: no rgs_solve on this transport since it was traced", fn);
         return RGS_ERR_STATE;
     }
-    return rgs_adjoint_pairs_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda, S(stream));
+    return rgs_adjoint_pairs_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda, dL_dp, dL_ds, S(stream));
+}
+
+rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
+                             float *dL_dopacity, float *dL_dlambda, void *stream) {
+    return adjoint_pairs_checked("rgs_adjoint_pairs", t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda, nullptr,
+                                 nullptr, stream);
+}
+
+rgs_status rgs_adjoint_pairs_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
+                                      float *dL_dopacity, float *dL_dlambda, float *dL_dp, float *dL_ds,
+                                      void *stream) {
+    return adjoint_pairs_checked("rgs_adjoint_pairs_geometry", t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda,
+                                 dL_dp, dL_ds, stream);
 }
 
 rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_t precision, float *B_out,

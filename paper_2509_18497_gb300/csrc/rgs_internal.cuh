@@ -167,6 +167,53 @@ __device__ __forceinline__ void sh_eval(float3 v, float *Y) {
     }
 }
 
+// sum_k coef[k] grad Y_k(v): the gradient of sh_eval's polynomials (their tangential part is
+// the derivative along the sphere, the only part the geometry gradients use)
+template <int NC>
+__device__ __forceinline__ float3 sh_grad_dot(float3 v, const float *coef) {
+    const float x = v.x, y = v.y, z = v.z;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (NC > 1) {
+        const float c1 = 0.4886025119029199f;
+        gy -= c1 * coef[1];
+        gz += c1 * coef[2];
+        gx -= c1 * coef[3];
+    }
+    if (NC > 4) {
+        const float c21 = 1.0925484305920792f, c20 = 0.31539156525252005f, c22 = 0.5462742152960396f;
+        gx += c21 * y * coef[4];
+        gy += c21 * x * coef[4];
+        gy -= c21 * z * coef[5];
+        gz -= c21 * y * coef[5];
+        gz += 6.f * c20 * z * coef[6];
+        gx -= c21 * z * coef[7];
+        gz -= c21 * x * coef[7];
+        gx += 2.f * c22 * x * coef[8];
+        gy -= 2.f * c22 * y * coef[8];
+    }
+    if (NC > 9) {
+        const float c33 = 0.5900435899266435f, c32a = 2.890611442640554f, c31 = 0.4570457994644658f;
+        const float c30 = 0.3731763325901154f, c32b = 1.445305721320277f;
+        const float zz5 = 5.f * z * z;
+        gx -= 6.f * c33 * x * y * coef[9];
+        gy -= 3.f * c33 * (x * x - y * y) * coef[9];
+        gx += c32a * y * z * coef[10];
+        gy += c32a * x * z * coef[10];
+        gz += c32a * x * y * coef[10];
+        gy -= c31 * (zz5 - 1.f) * coef[11];
+        gz -= 10.f * c31 * y * z * coef[11];
+        gz += c30 * (3.f * zz5 - 3.f) * coef[12];
+        gx -= c31 * (zz5 - 1.f) * coef[13];
+        gz -= 10.f * c31 * x * z * coef[13];
+        gx += 2.f * c32b * x * z * coef[14];
+        gy -= 2.f * c32b * y * z * coef[14];
+        gz += c32b * (x * x - y * y) * coef[14];
+        gx -= 3.f * c33 * (x * x - y * y) * coef[15];
+        gy += 6.f * c33 * x * y * coef[15];
+    }
+    return make_float3(gx, gy, gz);
+}
+
 __host__ __device__ constexpr int band_of(int k) { return k == 0 ? 0 : (k < 4 ? 1 : (k < 9 ? 2 : 3)); }
 
 // Cooperative row slices for the gathers: G lanes share one ray (or one transposed entry)
@@ -294,6 +341,35 @@ __device__ __forceinline__ float alpha_of(const SceneDev &sc, float o, float G) 
         return x > 0.f ? -expm1f(-0.03279f * powf(x, 3.4f)) : 0.f;
     }
     return o * G;
+}
+// d alpha / d q of a hit at squared local radius q = u^2 + v^2 (G = exp(-q/2)): -o G / 2
+// for the Gaussian, 0 inside the disc, -1.7 p e^{-p} for GFSGS with p = 0.03279 (o G)^3.4
+__device__ __forceinline__ float dalpha_dq(const SceneDev &sc, float o, float G) {
+    if (sc.alpha_model == RGS_ALPHA_DISC) return 0.f;
+    if (sc.alpha_model == RGS_ALPHA_GFSGS) {
+        const float x = o * G;
+        if (!(x > 0.f)) return 0.f;
+        const float p = 0.03279f * powf(x, 3.4f);
+        return -1.7f * p * expf(-p);
+    }
+    return -0.5f * o * G;
+}
+// Crossing of the segment o + t d (t given) with the plane of surfel k: P_k^T grad_x q with
+// P_k = I - d n_k^T / (n_k.d) (the projector onto plane k along d), and u, v; a move of o,
+// d or p_k changes q by pw . (do + t dd - dp_k) and s^u_k by dq = -2 u^2 / s^u_k.
+__device__ __forceinline__ float3 crossing_pw(const SceneDev &sc, int k, float3 o, float3 d, float t, float &u,
+                                              float &v) {
+    const float4 Pk = __ldg(&sc.P[k]), Nk = __ldg(&sc.N4[k]), U = __ldg(&sc.FU[k]), V = __ldg(&sc.FV[k]);
+    const float3 q = make_float3(o.x + t * d.x - Pk.x, o.y + t * d.y - Pk.y, o.z + t * d.z - Pk.z);
+    u = (q.x * U.x + q.y * U.y + q.z * U.z) * U.w;
+    v = (q.x * V.x + q.y * V.y + q.z * V.z) * V.w;
+    const float a = 2.f * u * U.w, b = 2.f * v * V.w;
+    float3 g = make_float3(a * U.x + b * V.x, a * U.y + b * V.y, a * U.z + b * V.z);
+    const float s = (d.x * g.x + d.y * g.y + d.z * g.z) / (Nk.x * d.x + Nk.y * d.y + Nk.z * d.z);
+    g.x -= Nk.x * s;
+    g.y -= Nk.y * s;
+    g.z -= Nk.z * s;
+    return g;
 }
 __device__ __forceinline__ float dalpha_do(const SceneDev &sc, float o, float G) {
     if (sc.alpha_model == RGS_ALPHA_GFSGS) {
@@ -730,12 +806,12 @@ template <int NC>
 rgs_status pairs_bounce(const rgs_transport *t, bool rows16, const float *Bprev, const __nv_bfloat16 *Bprev16,
                         const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16, double *norm2, cudaStream_t st);
 rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, float *dlam,
-                                  cudaStream_t st);
+                                  float *dp, float *ds, cudaStream_t st);
 // adjoint pieces shared by both transports (rgs_adjoint.cu): v^(0) = dL/dB, u = v^(0),
 // P = v^(0) Q^(n-1), dop = 0; P += X Y; the shadow-ray backward; the outputs
 rgs_status rgs_adjoint_prologue(rgs_transport *t, int nc, const float *g, cudaStream_t st);
 rgs_status rgs_pair_accum(rgs_transport *t, int nc, const float *X, const float *Y, cudaStream_t st);
-rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st);
+rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float *dp = nullptr, float *ds = nullptr);
 rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st);
 void rgs_copy_offsets(const long long *off, unsigned long long *cursor, int n, cudaStream_t st);
 int rgs_scan_tmp_size(int n);

@@ -81,9 +81,8 @@ __device__ __forceinline__ float3 unit_dir(float3 dv, float &r) {
 // occluder k of the segment i -> j (t in (0, r)): a regular hit that is not the source and
 // whose plane is more than eps from the source's centre
 __device__ __forceinline__ bool pair_occluder(const SceneDev &sc, int k, int i, int j, float3 o, float3 d, float r,
-                                              float3 pj, float eps, float &g) {
+                                              float3 pj, float eps, float &g, float &t) {
     if (k == j) return false;
-    float t;
     if (!hit_surfel(sc, k, i, o, d, r, eps, t, g)) return false;
     const float4 Nk = __ldg(&sc.N4[k]);
     const float4 Pk = __ldg(&sc.P[k]);
@@ -129,8 +128,8 @@ __global__ void __launch_bounds__(PCH) k_pair_fill(SceneDev sc, int n, int chunk
     const float3 pj = f3(sc.P[j]);
     float T = 1.f;
     auto visit = [&](int k) {
-        float g;
-        if (pair_occluder(sc, k, i, j, pi, d, r, pj, eps, g)) T *= 1.f - alpha_of(sc, __ldg(&sc.P[k].w), g);
+        float g, t;
+        if (pair_occluder(sc, k, i, j, pi, d, r, pj, eps, g, t)) T *= 1.f - alpha_of(sc, __ldg(&sc.P[k].w), g);
     };
     if (!bvh_traverse(sc, pi, d, r, visit)) atomicAdd(&flags[FLAG_STACK], 1);
     const float3 nj = f3(sc.N4[j]);
@@ -279,39 +278,67 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_adj_src_pairs(SceneDev sc, int
 }
 
 // g_e = dL/dV_ji of every pair e = (i -> j), summed over the bounces:
-//   g = o_i sum_{a<n} sum_c (c_i (x) Y(R_i d) . v_i^(a)[c]) (Y(-d) . B_j^(n-1-a)[c])
-template <int NC>
+//   g = o_i sum_{a<n} sum_c (c_i (x) Y(R_i d) . v_i^(a)[c]) (Y(-d) . B_j^(n-1-a)[c]).
+// GEO: also the directional effects of Eq. dl-dgeo-1, the derivative of the pair's term in
+// its direction d through Y(R_i d) and Y(-d):
+//   gq_e = V_ji o_i (R_i sum_k wi_k grad Y_k(R_i d) - sum_k wo_k grad Y_k(-d)),
+//   wi_k = sum_{a,c} (Y(-d) . B_j[c]) c_{i,l(k),ch} v_i[c][k],  wo_k = sum_{a,c} y_c B_j[c][k].
+template <int NC, bool GEO>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int nb, const long long *__restrict__ pair_off,
                                                         const int2 *__restrict__ rec, size_t A,
                                                         const float *__restrict__ V, const float *__restrict__ Bit,
-                                                        float *gpair) {
+                                                        float *gpair, float4 *gq) {
     const int i = blockIdx.x;
     const float4 Pi = __ldg(&sc.P[i]);
     const float3 pi = f3(Pi), ni = f3(sc.N4[i]);
     for (long long e = pair_off[i] + threadIdx.x; e < pair_off[i + 1]; e += PAIR_THREADS) {
-        const int j = __ldg(&rec[e]).x;
+        const int2 jv = __ldg(&rec[e]);
+        const int j = jv.x;
         const float4 Pj = __ldg(&sc.P[j]);
         float r;
         const float3 d = unit_dir(make_float3(Pj.x - pi.x, Pj.y - pi.y, Pj.z - pi.z), r);
         float Yi[NC], Yo[NC];
-        sh_eval<NC>(reflect_n(ni, d), Yi);
+        const float3 rd = reflect_n(ni, d);
+        sh_eval<NC>(rd, Yi);
         sh_eval<NC>(neg3(d), Yo);
+        float wi[GEO ? NC : 1], wo[GEO ? NC : 1];
+        if constexpr (GEO) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) wi[k] = wo[k] = 0.f;
+        }
         float g = 0.f;
         for (int a = 0; a < nb; ++a) {
             const float *va = V + A * a + (size_t)i * C * NC;
             const float *Bb = Bit + A * (nb - 1 - a) + (size_t)j * C * NC;
             for (int c = 0; c < C; ++c) {
                 const int ch = c % 3;
+                float cv[NC], bv[NC];
                 float y = 0.f, s = 0.f;
 #pragma unroll
                 for (int k = 0; k < NC; ++k) {
-                    y += __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * Yi[k] * __ldg(&va[c * NC + k]);
-                    s += Yo[k] * __ldg(&Bb[c * NC + k]);
+                    cv[k] = __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * __ldg(&va[c * NC + k]);
+                    bv[k] = __ldg(&Bb[c * NC + k]);
+                    y += cv[k] * Yi[k];
+                    s += Yo[k] * bv[k];
                 }
                 g += y * s;
+                if constexpr (GEO) {
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) {
+                        wi[k] += s * cv[k];
+                        wo[k] += y * bv[k];
+                    }
+                }
             }
         }
-        gpair[e] = g * alpha_center(sc, i);
+        const float ai = alpha_center(sc, i);
+        gpair[e] = g * ai;
+        if constexpr (GEO) {
+            const float3 t3 = reflect_n(ni, sh_grad_dot<NC>(rd, wi));
+            const float3 t2 = sh_grad_dot<NC>(neg3(d), wo);
+            const float f = __int_as_float(jv.y) * ai;
+            gq[e] = make_float4(f * (t3.x - t2.x), f * (t3.y - t2.y), f * (t3.z - t2.z), 0.f);
+        }
     }
 }
 
@@ -321,10 +348,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int
 //   dL/dlambda_j += g A_j T geo,  dL/do_j += g lambda_j (A_j/o_j) T geo,
 //   dL/do_k += -g lambda_j A_j geo prod_{m != k}(1 - alpha_m) G_k for the segment's occluders
 // (the segment is traced again: once for T and the zero factors, once for the occluders).
+// With dp (and ds) also the geometry gradients of Eqs. dl-dgeo-0/1: the decay term
+// V = lambda_j A_j T geo through geo = (n_i.d)|n_j.d|/r^2, through A_j (proportional to
+// s^u_j s^v_j) and through every occluder's crossing point and scales, plus the directional
+// part gq from k_pair_g; d = (p_j - p_i)/r moves with (I - d d^T)/r (dp_j - dp_i).
 __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunks, const long long *__restrict__ chunk_off,
                                                    const float *__restrict__ lam, const float *__restrict__ aarea,
                                                    const float *__restrict__ daarea, const float *__restrict__ gpair,
-                                                   float *dop, float *dlam, int *flags) {
+                                                   const float4 *__restrict__ gq, float *dop, float *dlam, float *dp,
+                                                   float *ds, int *flags) {
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
@@ -340,18 +372,21 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     int base = 0;
     for (int w = 0; w < warp; ++w) base += warp_base[w];
     if (!front) return;
-    const float g = gpair[chunk_off[blk] + base + __popc(bal & ((1u << lane) - 1u))];
-    if (g == 0.f) return;
+    const long long e = chunk_off[blk] + base + __popc(bal & ((1u << lane) - 1u));
+    const float g = gpair[e];
+    const float4 gs = dp ? gq[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g == 0.f && gs.x == 0.f && gs.y == 0.f && gs.z == 0.f) return;
     float r;
     const float3 d = unit_dir(dv, r);
-    const float3 pj = f3(sc.P[j]);
+    const float3 pj = f3(sc.P[j]), nj = f3(sc.N4[j]);
     const float Aj = __ldg(&aarea[j]), dAj = __ldg(&daarea[j]), lj = __ldg(&lam[j]);
-    const float geo = fabsf(dot3(ni, d)) * fabsf(dot3(f3(sc.N4[j]), d)) / (r * r);
+    const float nid = dot3(ni, d), njd = dot3(nj, d);
+    const float geo = fabsf(nid) * fabsf(njd) / (r * r);
     float Tnz = 1.f;
     int nzero = 0;
     auto pass1 = [&](int k) {
-        float gk;
-        if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
+        float gk, tk;
+        if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk, tk)) return;
         const float om = 1.f - alpha_of(sc, __ldg(&sc.P[k].w), gk);
         if (om == 0.f) ++nzero;
         else Tnz *= om;
@@ -359,21 +394,68 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     if (!bvh_traverse(sc, pi, d, r, pass1)) atomicAdd(&flags[FLAG_STACK], 1);
     const float T = nzero ? 0.f : Tnz;
     if (dlam) atomicAdd(&dlam[j], g * Aj * T * geo);
-    if (!dop) return;
-    if (T != 0.f) atomicAdd(&dop[j], g * lj * dAj * T * geo);
-    if (nzero > 1) return;
-    const float q = -g * lj * Aj * geo;
-    auto pass2 = [&](int k) {
-        float gk;
-        if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk)) return;
-        const float ok = __ldg(&sc.P[k].w);
-        const float om = 1.f - alpha_of(sc, ok, gk);
-        float others;
-        if (nzero == 0) others = Tnz / om;
-        else others = (om == 0.f) ? Tnz : 0.f;
-        if (others != 0.f) atomicAdd(&dop[k], q * others * dalpha_do(sc, ok, gk));
-    };
-    bvh_traverse(sc, pi, d, r, pass2);
+    if (dop && T != 0.f) atomicAdd(&dop[j], g * lj * dAj * T * geo);
+    float3 gd = make_float3(gs.x, gs.y, gs.z), gpi = make_float3(0.f, 0.f, 0.f);
+    float gr = 0.f;
+    if (dp) {
+        const float f = g * lj * Aj * T / (r * r), sj = njd >= 0.f ? 1.f : -1.f;
+        gd = gd + f * (fabsf(njd) * ni + (fabsf(nid) * sj) * nj);
+        gr = g * lj * Aj * T * (-2.f * geo / r);
+        const float fs = g * lj * T * geo * Aj;
+        atomicAdd(&ds[2 * j], fs * __ldg(&sc.FU[j].w));
+        atomicAdd(&ds[2 * j + 1], fs * __ldg(&sc.FV[j].w));
+    }
+    if ((dop || dp) && nzero <= 1 && g != 0.f) {
+        const float q = -g * lj * Aj * geo;
+        auto pass2 = [&](int k) {
+            float gk, tk;
+            if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk, tk)) return;
+            const float ok = __ldg(&sc.P[k].w);
+            const float om = 1.f - alpha_of(sc, ok, gk);
+            float others;
+            if (nzero == 0) others = Tnz / om;
+            else others = (om == 0.f) ? Tnz : 0.f;
+            if (others == 0.f) return;
+            if (dop) atomicAdd(&dop[k], q * others * dalpha_do(sc, ok, gk));
+            if (dp) {
+                const float coef = q * others * dalpha_dq(sc, ok, gk);
+                if (coef == 0.f) return;
+                float uu, vv;
+                const float3 pw = crossing_pw(sc, k, pi, d, tk, uu, vv);
+                gpi = gpi + coef * pw;
+                gd = gd + (coef * tk) * pw;
+                atomicAdd(&dp[3 * k], -coef * pw.x);
+                atomicAdd(&dp[3 * k + 1], -coef * pw.y);
+                atomicAdd(&dp[3 * k + 2], -coef * pw.z);
+                atomicAdd(&ds[2 * k], coef * (-2.f * uu * uu * __ldg(&sc.FU[k].w)));
+                atomicAdd(&ds[2 * k + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[k].w)));
+            }
+        };
+        bvh_traverse(sc, pi, d, r, pass2);
+    }
+    if (dp) {
+        const float dd = dot3(d, gd);
+        const float3 gp = make_float3((gd.x - d.x * dd) / r + d.x * gr, (gd.y - d.y * dd) / r + d.y * gr,
+                                      (gd.z - d.z * dd) / r + d.z * gr);
+        atomicAdd(&dp[3 * j], gp.x);
+        atomicAdd(&dp[3 * j + 1], gp.y);
+        atomicAdd(&dp[3 * j + 2], gp.z);
+        atomicAdd(&dp[3 * i], gpi.x - gp.x);
+        atomicAdd(&dp[3 * i + 1], gpi.y - gp.y);
+        atomicAdd(&dp[3 * i + 2], gpi.z - gp.z);
+    }
+}
+
+// geometry gradients back to the caller's order
+__global__ void k_geo_out(int n, const int *__restrict__ uid, const float *__restrict__ dp_acc,
+                          const float *__restrict__ ds_acc, float *dp, float *ds) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int o = uid[i];
+    if (dp)
+        for (int a = 0; a < 3; ++a) dp[3 * o + a] = dp_acc[3 * i + a];
+    if (ds)
+        for (int a = 0; a < 2; ++a) ds[2 * o + a] = ds_acc[2 * i + a];
 }
 
 __global__ void k_lam_out(int n, const int *__restrict__ uid, const float *__restrict__ dlam, float *out) {
@@ -473,14 +555,17 @@ template rgs_status pairs_bounce<16>(const rgs_transport *, bool, const float *,
                                      float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
 
 namespace {
+struct GeoAcc { // internal-order accumulators of the geometry gradients (both or neither)
+    float *dp = nullptr, *ds = nullptr;
+    float4 *gq = nullptr;
+};
+
 template <int NC>
 rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float *dad, float *dopo, float *dlam_acc,
-                             cudaStream_t st) {
+                             const GeoAcc &geo, cudaStream_t st) {
     const int n = t->n, C = t->C, nb = t->nb_last;
     const size_t A = t->arr();
     SceneDev sd = t->sc->dev();
-    const unsigned ga = (unsigned)((A + 255) / 256);
-    const unsigned gn = (unsigned)((n + 127) / 128);
     rgs_status r;
     if ((r = rgs_adjoint_prologue(t, NC, g, st)) != RGS_OK) return r;
     for (int a = 1; a <= nb; ++a) {
@@ -488,21 +573,25 @@ rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float 
         RGS_LAUNCH("adjoint pairs");
         if (a <= nb - 1 && (r = rgs_pair_accum(t, NC, t->v + A * a, t->Q + A * (nb - 1 - a), st)) != RGS_OK) return r;
     }
-    if ((r = rgs_shadow_backward(t, NC, st)) != RGS_OK) return r;
-    if (nb >= 1 && (dopo || dlam_acc)) {
+    if ((r = rgs_shadow_backward(t, NC, st, geo.dp, geo.ds)) != RGS_OK) return r;
+    if (nb >= 1 && (dopo || dlam_acc || geo.dp)) {
         const int chunks = (n + PCH - 1) / PCH;
-        { ProfScope ps_("k_pair_g", st); k_pair_g<NC><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh); }
-        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, dopo ? t->dop : nullptr, dlam_acc, t->flags); }
+        if (geo.dp) {
+            ProfScope ps_("k_pair_g", st);
+            k_pair_g<NC, true><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh, geo.gq);
+        } else {
+            ProfScope ps_("k_pair_g", st);
+            k_pair_g<NC, false><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh, nullptr);
+        }
+        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, geo.gq, dopo ? t->dop : nullptr, dlam_acc, geo.dp, geo.ds, t->flags); }
         RGS_LAUNCH("pair backward");
     }
-    (void)ga;
-    (void)gn;
     return rgs_adjoint_finalize(t, NC, dE, dad, dopo, st);
 }
 } // namespace
 
 rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, float *dlam,
-                                  cudaStream_t st) {
+                                  float *dp, float *ds, cudaStream_t st) {
     rgs_status r;
     const int nb = t->nb_last, n = t->n;
     const size_t A = t->arr();
@@ -512,41 +601,58 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
         t->pg_cap = n;
     }
     float *dlam_acc = nullptr;
+    GeoAcc geo;
+    const bool want_geo = dp || ds;
     struct Scratch {
         rgs_transport *t;
         cudaStream_t st;
         float **dl;
+        GeoAcc *geo;
         ~Scratch() {
             pool_release(t->v, st);
             pool_release(t->u, st);
             pool_release(t->tr, st);
             pool_release(t->gh, st);
             pool_release(*dl, st);
+            pool_release(geo->dp, st);
+            pool_release(geo->ds, st);
+            pool_release(geo->gq, st);
         }
-    } scratch{t, st, &dlam_acc};
+    } scratch{t, st, &dlam_acc, &geo};
     if ((r = pool_alloc(&t->v, A * (nb + 1), st)) != RGS_OK) return r;
     if ((r = pool_alloc(&t->u, A, st)) != RGS_OK) return r;
     if ((r = pool_alloc(&t->tr, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK) return r;
-    if ((dop || dlam) && nb >= 1 && (r = pool_alloc(&t->gh, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK)
+    if ((dop || dlam || want_geo) && nb >= 1 && (r = pool_alloc(&t->gh, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK)
         return r; // g per pair
     if (dlam) {
         if ((r = pool_alloc(&dlam_acc, (size_t)n, st)) != RGS_OK) return r;
         RGS_CUDA(cudaMemsetAsync(dlam_acc, 0, sizeof(float) * n, st));
+    }
+    if (want_geo) {
+        if ((r = pool_alloc(&geo.dp, (size_t)n * 3, st)) != RGS_OK) return r;
+        if ((r = pool_alloc(&geo.ds, (size_t)n * 2, st)) != RGS_OK) return r;
+        if ((r = pool_alloc(&geo.gq, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK) return r;
+        RGS_CUDA(cudaMemsetAsync(geo.dp, 0, sizeof(float) * n * 3, st));
+        RGS_CUDA(cudaMemsetAsync(geo.ds, 0, sizeof(float) * n * 2, st));
     }
     { ProfScope ps_("k_copy_off", st); rgs_copy_offsets(t->src_off, t->cursor, n, st); }
     { ProfScope ps_("k_pair_src_fill", st); k_pair_src_fill<<<n, 256, 0, st>>>(n, t->pair_off, t->pair_rec, t->cursor, t->tr); }
     RGS_LAUNCH("pair transposed index");
     RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));
     switch (t->nc) {
-    case 1: r = run_adjoint_pairs<1>(t, g, dE, dad, dop, dlam_acc, st); break;
-    case 4: r = run_adjoint_pairs<4>(t, g, dE, dad, dop, dlam_acc, st); break;
-    case 9: r = run_adjoint_pairs<9>(t, g, dE, dad, dop, dlam_acc, st); break;
-    default: r = run_adjoint_pairs<16>(t, g, dE, dad, dop, dlam_acc, st);
+    case 1: r = run_adjoint_pairs<1>(t, g, dE, dad, dop, dlam_acc, geo, st); break;
+    case 4: r = run_adjoint_pairs<4>(t, g, dE, dad, dop, dlam_acc, geo, st); break;
+    case 9: r = run_adjoint_pairs<9>(t, g, dE, dad, dop, dlam_acc, geo, st); break;
+    default: r = run_adjoint_pairs<16>(t, g, dE, dad, dop, dlam_acc, geo, st);
     }
     if (r != RGS_OK) return r;
     if (dlam) {
         { ProfScope ps_("k_lam_out", st); k_lam_out<<<(n + 255) / 256, 256, 0, st>>>(n, t->sc->uid, dlam_acc, dlam); }
         RGS_LAUNCH("lambda gradient");
+    }
+    if (want_geo) {
+        { ProfScope ps_("k_geo_out", st); k_geo_out<<<(n + 255) / 256, 256, 0, st>>>(n, t->sc->uid, geo.dp, geo.ds, dp, ds); }
+        RGS_LAUNCH("geometry gradients");
     }
     return RGS_OK;
 }

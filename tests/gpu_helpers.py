@@ -15,7 +15,7 @@ def rel_l2(a, b):
 
 
 def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=False, precision=rgs.RGS_FP32,
-            checkpoint=0, pairs=False):
+            checkpoint=0, pairs=False, geometry=False):
     """build -> trace -> solve (-> adjoint with dL/dB = W) on cuda:0; numpy float64 out.
     pairs: the center-to-center transport (the adjoint then also returns dlam)."""
     d = api.upload(sc)
@@ -28,7 +28,10 @@ def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=F
         out["iters"] = [rgs.rgs_get_iterate(pipe.transport, b).double().cpu().numpy() for b in range(d["nb"] + 1)]
     if W is not None:
         g = torch.as_tensor(np.ascontiguousarray(W, np.float32), device="cuda")
-        if pairs:
+        if pairs and geometry:
+            dE, dad, dop, dlam, dp, ds = pipe.adjoint_pairs_geometry(g)
+            out.update(dlam=dlam.double().cpu().numpy(), dp=dp.double().cpu().numpy(), ds=ds.double().cpu().numpy())
+        elif pairs:
             dE, dad, dop, dlam = pipe.adjoint_pairs(g)
             out["dlam"] = dlam.double().cpu().numpy()
         else:
@@ -39,7 +42,7 @@ def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=F
     return out
 
 
-def run_oracle(sc, W=None, alpha_model=O.ALPHA_GAUSS, iterates=False, pairs=False):
+def run_oracle(sc, W=None, alpha_model=O.ALPHA_GAUSS, iterates=False, pairs=False, geometry=False):
     orc = O.Oracle(sc, alpha_model=alpha_model)
     orc = orc.pairs(lam=sc.get("lam")) if pairs else orc.transport()
     out = dict(orc=orc)
@@ -51,4 +54,6 @@ def run_oracle(sc, W=None, alpha_model=O.ALPHA_GAUSS, iterates=False, pairs=Fals
     out["B"] = B
     if W is not None:
         out.update(orc.adjoint(W, E=sc["E"], nb=sc["nb"]))
+        if geometry:
+            out.update(orc.geometry_grad(W, E=sc["E"], nb=sc["nb"]))
     return out

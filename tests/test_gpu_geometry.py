@@ -1,0 +1,90 @@
+"""Geometry gradients of the center-to-center transport (Eqs. dl-dgeo-0/1: dL/dp and
+dL/d(s^u, s^v) through the decay term, the directional effects and the direct term) on
+the GPU against the FP64 oracle, whose own values are pinned by central differences of
+the whole forward solve (test_oracle_geometry.py)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2509_18497_gb300 import rgs, scenes
+
+from gpu_helpers import rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4  # FP32 path against FP64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_18497_gb300 import build
+    build.build()
+
+
+def _with_lam(sc, seed):
+    out = dict(sc)
+    out["lam"] = np.random.default_rng(seed).uniform(0.5, 1.5, sc["n"]).astype(np.float32).astype(np.float64)
+    return out
+
+
+def _directional(sc, n_lights, seed):
+    rng = np.random.default_rng(seed)
+    out = dict(sc)
+    out["light_pos"] = rng.normal(size=(n_lights, 3)).astype(np.float32).astype(np.float64)
+    out["light_I"] = rng.uniform(0.5, 3.0, size=(n_lights, 3)).astype(np.float32).astype(np.float64)
+    out["light_dir"] = True
+    return out
+
+
+CASES = {
+    "cluster": (lambda: _with_lam(scenes.with_emission(scenes.random_cluster(n=300, L=2, nb=3, n_lights=3), seed=5), 6),
+                rgs.RGS_ALPHA_GAUSS, O.ALPHA_GAUSS),
+    "bowl": (lambda: _with_lam(scenes.with_emission(scenes.fruit_bowl(n=1500, L=3, nb=3, n_lights=2), seed=3), 4),
+             rgs.RGS_ALPHA_GAUSS, O.ALPHA_GAUSS),
+    "bowl_gfsgs": (lambda: scenes.with_emission(scenes.fruit_bowl(n=1200, L=2, nb=3, n_lights=2), seed=7),
+                   rgs.RGS_ALPHA_GFSGS, O.ALPHA_GFSGS),
+    "bowl_directional": (lambda: _directional(scenes.with_emission(scenes.fruit_bowl(n=1200, L=2, nb=3), seed=1), 3, 2),
+                         rgs.RGS_ALPHA_GAUSS, O.ALPHA_GAUSS),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_geometry_gradients_match_oracle(case):
+    maker, am_gpu, am_or = CASES[case]
+    sc = maker()
+    nc = (sc["L"] + 1) ** 2
+    C = 3 * max(1, sc["light_pos"].shape[0])
+    W = np.random.default_rng(11).normal(size=(sc["n"], nc, C))
+    o = run_oracle(sc, W=W, alpha_model=am_or, pairs=True, geometry=True)
+    g = run_gpu(sc, W=W, alpha_model=am_gpu, pairs=True, geometry=True)
+    for key in ("dp", "ds"):
+        assert np.all(np.isfinite(g[key])), key
+        assert rel_l2(g[key], o[key]) <= TOL, (key, rel_l2(g[key], o[key]))
+    # the other outputs of the same call are those of rgs_adjoint_pairs
+    for key in ("dE", "dad", "dop", "dlam"):
+        assert rel_l2(g[key], o[key]) <= TOL, key
+
+
+def test_geometry_call_leaves_other_gradients_unchanged():
+    sc = _with_lam(scenes.with_emission(scenes.random_cluster(n=200, L=2, nb=3, n_lights=2), seed=3), 2)
+    W = np.random.default_rng(4).normal(size=(sc["n"], 9, 6))
+    a = run_gpu(sc, W=W, pairs=True)
+    b = run_gpu(sc, W=W, pairs=True, geometry=True)
+    for key in ("dE", "dad", "dop", "dlam"):
+        assert rel_l2(b[key], a[key]) <= 1e-6, key  # atomics may sum in another order
+
+
+def test_geometry_needs_pairs_transport():
+    from paper_2509_18497_gb300 import api
+    sc = scenes.box_scene(n=200, nb=2)
+    d = api.upload(sc)
+    p = api.Pipeline()
+    p.build(d)
+    p.trace(d)
+    p.solve(d["E"], d["nb"])
+    g = torch.zeros((sc["n"], 9, 3), device="cuda")
+    with pytest.raises(rgs.RgsError):
+        p.adjoint_pairs_geometry(g)
