@@ -127,6 +127,7 @@ typedef struct {
 typedef struct {
     int n, L, nc, alpha_model, use_bvh;
     double *p, *tu, *tv, *nrm, *su, *sv, *o, *k, *ad, *as, *shin;
+    double *gs; /* [n][3] Gram-Schmidt lengths |tu|, |tv - (t^u.tv) t^u| and t^u.tv of the inputs */
     double *c; /* [n][L+1][3] */
     double eps_plane;
     /* BVH (median split) */
@@ -259,6 +260,7 @@ or_scene *or_scene_new(int n, int L, const double *p, const double *tu, const do
     s->su = dup_arr(NULL, n);
     s->sv = dup_arr(NULL, n);
     s->c = dup_arr(NULL, (size_t)n * (L + 1) * 3);
+    s->gs = dup_arr(NULL, 3 * (size_t)n);
     /* Eq. G: orthonormal tangent frame (Gram-Schmidt of the given directions), n = tu x tv */
     for (int i = 0; i < n; ++i) {
         double a[3] = {tu[i * 3], tu[i * 3 + 1], tu[i * 3 + 2]}, b[3] = {tv[i * 3], tv[i * 3 + 1], tv[i * 3 + 2]};
@@ -268,6 +270,9 @@ or_scene *or_scene_new(int n, int L, const double *p, const double *tu, const do
         for (int q = 0; q < 3; ++q) b[q] -= pr * a[q];
         double lb = sqrt(dot3(b, b));
         for (int q = 0; q < 3; ++q) b[q] /= lb;
+        s->gs[i * 3] = la;
+        s->gs[i * 3 + 1] = lb;
+        s->gs[i * 3 + 2] = pr;
         double nn[3];
         cross3(a, b, nn);
         memcpy(s->tu + i * 3, a, sizeof a);
@@ -341,6 +346,7 @@ void or_scene_free(or_scene *s) {
     free(s->tu);
     free(s->tv);
     free(s->nrm);
+    free(s->gs);
     free(s->su);
     free(s->sv);
     free(s->o);
@@ -1508,10 +1514,13 @@ static double occluder_crossing(const or_scene *s, int k, const double *o, const
 
 /* Adds the gradient of T = prod_m (1 - alpha_m) over the occluders (k[m], G[m]) of the
  * segment o + t d, scaled by up, to the origin's position (gpo), the direction (gd) and
- * the occluders' positions and scales. */
+ * the occluders' positions, scales and frames.  With x the crossing point and
+ * q = u^2 + v^2, u = (x - p_k).t^u_k / s^u_k:  dq/dt^u_k = 2 u (x - p_k) / s^u_k (likewise
+ * for t^v), and through t = n_k.(p_k - o)/(n_k.d):  dq/dn_k = -(grad_x q . d)/(n_k.d) (x - p_k).
+ * gF: [N][9] gradients with respect to (t^u, t^v, n) of every surfel, or NULL. */
 static void occluder_backward(const or_scene *s, const double *o, const double *d, int cnt, const int *kk,
                               const double *al, const double *G, double up, double *gpo, double *gd, double *dp,
-                              double *ds) {
+                              double *ds, double *gF) {
     for (int q = 0; q < cnt; ++q) {
         double others = 1.0;
         for (int m = 0; m < cnt; ++m)
@@ -1530,7 +1539,28 @@ static void occluder_backward(const or_scene *s, const double *o, const double *
             ds[k * 2] += coef * (-2.0 * u * u / s->su[k]);
             ds[k * 2 + 1] += coef * (-2.0 * v * v / s->sv[k]);
         }
+        if (gF) {
+            const double *pk = s->p + k * 3, *nk = s->nrm + k * 3, *tu = s->tu + k * 3, *tv = s->tv + k * 3;
+            double xm[3], gx[3];
+            for (int a = 0; a < 3; ++a) {
+                xm[a] = o[a] + t * d[a] - pk[a];
+                gx[a] = 2.0 * (u * tu[a] / s->su[k] + v * tv[a] / s->sv[k]);
+            }
+            const double fn = -dot3(gx, d) / dot3(nk, d);
+            for (int a = 0; a < 3; ++a) {
+                gF[k * 9 + a] += coef * 2.0 * u * xm[a] / s->su[k];
+                gF[k * 9 + 3 + a] += coef * 2.0 * v * xm[a] / s->sv[k];
+                gF[k * 9 + 6 + a] += coef * fn * xm[a];
+            }
+        }
     }
+}
+
+/* gF[i][6..8] += dL/dn_i of a term (upstream gR) . Y(R_i w): R_i w = 2 (n.w) n - w moves
+ * with n by 2 ((dn.w) n + (n.w) dn). */
+static void reflect_backward(const double *n, const double *w, const double *gR, double *gn) {
+    const double nw = dot3(n, w), ng = dot3(n, gR);
+    for (int a = 0; a < 3; ++a) gn[a] += 2.0 * (ng * w[a] + nw * gR[a]);
 }
 
 /* Geometry gradients (Eqs. dl-dgeo-0 and dl-dgeo-1, Sec. 6 / App. C) of L(B^(nb)) with
@@ -1545,12 +1575,19 @@ static void occluder_backward(const or_scene *s, const double *o, const double *
  *   d = (p_j - p_i)/r moves with (I - d d^T)/r (dp_j - dp_i), r with d.(dp_j - dp_i).
  * The direct term adds, per (receiver, light), the derivative of
  * sum_k h_k Y_k(R_i w) (n_i.w) fall T in w = (p_L - p_i)/r, in fall = 1/r^2 and in its
- * shadow occluders (a directional light has a fixed w and fall = 1).  Discrete events
+ * shadow occluders (a directional light has a fixed w and fall = 1).  With dtu, dtv also
+ * the gradients with respect to the frame inputs tu, tv: the normals enter geo, R_i and
+ * the direct term's cos, and every occluder's (t^u, t^v, n) its crossing point; the
+ * orthonormal frame's gradients are then carried back through the Gram-Schmidt
+ * construction of Eq. G.  Discrete events
  * (front tests, the 3-sigma cutoff, the eps_plane rules) are held fixed: the gradient is
  * the derivative of the smooth piece the scene sits on.  Returns 0, or -1 without a
  * center-to-center transport. */
-int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g, double *dp, double *ds) {
+int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g, double *dp, double *ds,
+                     double *dtu, double *dtv) {
     if (!s->pmode) return -1;
+    double *gF = (dtu || dtv) ? dup_arr(NULL, (size_t)s->n * 9) : NULL;
+    if (gF) memset(gF, 0, sizeof(double) * (size_t)s->n * 9);
     int n = s->n, nc = s->nc, C = s->C, L = s->L, nl = s->nl;
     size_t M = (size_t)n * nc * C;
     double *iters = dup_arr(NULL, M * (nb + 1));
@@ -1610,12 +1647,21 @@ int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g
             reflect(s->nrm + i * 3, t1, t3); /* R_i t1 = 2 (n.t1) n - t1 */
             sh_grad_dot(L, md, wo, t2);
             for (int a = 0; a < 3; ++a) gd[a] += V * (t3[a] - t2[a]);
+            if (gF) {
+                double gR[3] = {V * t1[0], V * t1[1], V * t1[2]};
+                reflect_backward(s->nrm + i * 3, d, gR, gF + i * 9 + 6);
+            }
             /* decay term: geo through d and r */
             const double ni_d = dot3(s->nrm + i * 3, d), nj_d = dot3(s->nrm + j * 3, d);
             const double sj = nj_d >= 0.0 ? 1.0 : -1.0;
             for (int a = 0; a < 3; ++a)
                 gd[a] += ge * lam * A * T * (fabs(nj_d) * s->nrm[i * 3 + a] + ni_d * sj * s->nrm[j * 3 + a]) / (r * r);
             const double gr = ge * lam * A * T * (-2.0 * geo / r);
+            if (gF)
+                for (int a = 0; a < 3; ++a) {
+                    gF[i * 9 + 6 + a] += ge * lam * A * T * fabs(nj_d) * d[a] / (r * r);
+                    gF[j * 9 + 6 + a] += ge * lam * A * T * ni_d * sj * d[a] / (r * r);
+                }
             /* source scales through A_j */
             ds[j * 2] += ge * lam * T * geo * A / s->su[j];
             ds[j * 2 + 1] += ge * lam * T * geo * A / s->sv[j];
@@ -1633,7 +1679,7 @@ int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g
                 al[q] = s->poc_alpha[q0 + q];
                 Gk[q] = s->poc_G[q0 + q];
             }
-            occluder_backward(s, s->p + i * 3, d, cnt, kk, al, Gk, ge * lam * A * geo, gpi, gd, dp, ds);
+            occluder_backward(s, s->p + i * 3, d, cnt, kk, al, Gk, ge * lam * A * geo, gpi, gd, dp, ds, gF);
             /* d and r in p_i, p_j */
             const double dd = dot3(d, gd);
             for (int a = 0; a < 3; ++a) {
@@ -1681,13 +1727,46 @@ int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g
             sh_grad_dot(L, rw, wi, t1);
             reflect(s->nrm + i * 3, t1, t3);
             for (int a = 0; a < 3; ++a) gw[a] += fall * T * (cs * t3[a] + H * s->nrm[i * 3 + a]);
-            occluder_backward(s, s->p + i * 3, w, cnt, kk, al, Gk, H * cs * fall, gpi, gw, dp, ds);
+            if (gF) {
+                double gR[3] = {fall * T * cs * t1[0], fall * T * cs * t1[1], fall * T * cs * t1[2]};
+                reflect_backward(s->nrm + i * 3, w, gR, gF + i * 9 + 6);
+                for (int a = 0; a < 3; ++a) gF[i * 9 + 6 + a] += H * fall * T * w[a]; /* cos = n_i.w */
+            }
+            occluder_backward(s, s->p + i * 3, w, cnt, kk, al, Gk, H * cs * fall, gpi, gw, dp, ds, gF);
             for (int a = 0; a < 3; ++a) dp[i * 3 + a] += gpi[a];
             if (!s->ldir) { /* w = (p_L - p_i)/r, fall = 1/r^2 */
                 const double ww = dot3(w, gw), gr = H * cs * T * (-2.0 / (r * r * r));
                 for (int a = 0; a < 3; ++a) dp[i * 3 + a] += -(gw[a] - w[a] * ww) / r - w[a] * gr;
             }
         }
+    /* frame: n = t^u x t^v, t^v = b'/|b'| with b' = tv - (t^u.tv) t^u, t^u = tu/|tu| (Eq. G) */
+    if (gF) {
+        for (int i = 0; i < n; ++i) {
+            const double *tu = s->tu + i * 3, *tv = s->tv + i * 3;
+            const double la = s->gs[i * 3], lb = s->gs[i * 3 + 1], pr = s->gs[i * 3 + 2];
+            double Gu[3], Gv[3], cu[3], cv[3];
+            cross3(tv, gF + i * 9 + 6, cu); /* d(tu x tv) -> t^v x Gn on t^u, Gn x t^u on t^v */
+            cross3(gF + i * 9 + 6, tu, cv);
+            for (int a = 0; a < 3; ++a) {
+                Gu[a] = gF[i * 9 + a] + cu[a];
+                Gv[a] = gF[i * 9 + 3 + a] + cv[a];
+            }
+            double gb[3], b[3]; /* dL/db' and the input b = lb t^v + pr t^u */
+            const double vg = dot3(tv, Gv);
+            for (int a = 0; a < 3; ++a) {
+                gb[a] = (Gv[a] - tv[a] * vg) / lb;
+                b[a] = lb * tv[a] + pr * tu[a];
+            }
+            const double ugb = dot3(tu, gb);
+            for (int a = 0; a < 3; ++a) Gu[a] -= pr * gb[a] + ugb * b[a];
+            const double ug = dot3(tu, Gu);
+            for (int a = 0; a < 3; ++a) {
+                if (dtu) dtu[i * 3 + a] = (Gu[a] - tu[a] * ug) / la;
+                if (dtv) dtv[i * 3 + a] = gb[a] - tu[a] * ugb;
+            }
+        }
+        free(gF);
+    }
     free(kk);
     free(al);
     free(Gk);

@@ -90,7 +90,7 @@ def lib():
                                             ct.c_int, _ip, _dp]
             L.or_sh_grad.argtypes = [ct.c_int, _dp, _dp, _dp]
             L.or_geometry_grad.restype = ct.c_int
-            L.or_geometry_grad.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp]
+            L.or_geometry_grad.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp, _dp, _dp, _dp]
             L.or_num_threads.restype = ct.c_int
             _lib = L
     return _lib
@@ -295,14 +295,18 @@ class Oracle:
         return out
 
     def geometry_grad(self, g, E=None, nb=None):
-        """Center-to-center transport: dL/dp [N][3] and dL/d(s^u, s^v) [N][2]."""
+        """Center-to-center transport: dL/dp [N][3], dL/d(s^u, s^v) [N][2] and dL/dtu,
+        dL/dtv [N][3] (the frame inputs)."""
         nb = self.sc["nb"] if nb is None else nb
         dp = np.zeros((self.n, 3))
         ds = np.zeros((self.n, 2))
-        rc = lib().or_geometry_grad(self.h, _ptr(_d(E)), int(nb), _ptr(_d(g).reshape(self._shape())), _ptr(dp), _ptr(ds))
+        dtu = np.zeros((self.n, 3))
+        dtv = np.zeros((self.n, 3))
+        rc = lib().or_geometry_grad(self.h, _ptr(_d(E)), int(nb), _ptr(_d(g).reshape(self._shape())), _ptr(dp), _ptr(ds),
+                                    _ptr(dtu), _ptr(dtv))
         if rc != 0:
             raise RuntimeError("geometry gradients need the center-to-center transport (pairs())")
-        return dict(dp=dp, ds=ds)
+        return dict(dp=dp, ds=ds, dtu=dtu, dtv=dtv)
 
     def brdf_grad_closed_form(self, g, E=None, nb=None):
         nb = self.sc["nb"] if nb is None else nb

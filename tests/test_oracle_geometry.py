@@ -1,8 +1,8 @@
 """Pins of the oracle's geometry gradients (Eqs. dl-dgeo-0 and dl-dgeo-1) for the
 center-to-center transport: the SH gradient against tangent differences of the SH
 (which is itself pinned to scipy), the lone plane's direct term against its closed form,
-and the full dL/dp, dL/ds against central differences of the whole forward solve for the
-Gaussian and GFSGS opacity models, point and directional lights (no GPU)."""
+and the full dL/dp, dL/ds, dL/dtu, dL/dtv against central differences of the whole forward
+solve for the Gaussian and GFSGS opacity models, point and directional lights (no GPU)."""
 import math
 
 import numpy as np
@@ -53,9 +53,16 @@ def test_lone_plane_position_gradient_closed_form():
     expect = pre * (-n / r ** 3 + 3 * (n @ l) * l / r ** 5)
     np.testing.assert_allclose(gg["dp"][0], expect, rtol=1e-12)
     np.testing.assert_allclose(gg["ds"][0], 0.0, atol=1e-15)  # nothing depends on the scale
+    # the normal: dB_00/dn = pre l / |l|^3 with n = t^u x t^v, t^u = e_x, t^v = e_y, so
+    # dL/dtu = (I - e_x e_x^T)(e_y x Gn) and dL/dtv = (I - e_x e_x^T)(I - e_y e_y^T)(Gn x e_x)
+    Gn = pre * l / r ** 3
+    ex, ey = np.eye(3)[0], np.eye(3)[1]
+    Px, Py = np.eye(3) - np.outer(ex, ex), np.eye(3) - np.outer(ey, ey)
+    np.testing.assert_allclose(gg["dtu"][0], Px @ np.cross(ey, Gn), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(gg["dtv"][0], Px @ Py @ np.cross(Gn, ex), rtol=1e-12, atol=1e-15)
 
 
-def _fd_check(sc, alpha_model=O.ALPHA_GAUSS, directional=False, stride=3):
+def _fd_check(sc, alpha_model=O.ALPHA_GAUSS, directional=False, stride=3, keys=(("p", 3), ("s", 2))):
     def make(s2):
         o2 = O.Oracle(s2, alpha_model=alpha_model)
         if directional:
@@ -80,7 +87,7 @@ def _fd_check(sc, alpha_model=O.ALPHA_GAUSS, directional=False, stride=3):
     # central differences of a loss of size |L0| carry a rounding error of about
     # |L0| eps / h = 1e-11 |L0|; the truncation error of the extrapolated form is far below
     floor = 1e-9 * abs(loss(sc))
-    for key, m in (("p", 3), ("s", 2)):
+    for key, m in keys:
         an = gg["d" + key]
         scale = np.abs(an).max()
         assert scale > 0
@@ -99,6 +106,19 @@ def test_geometry_gradients_gfsgs_and_directional():
     sc = scenes.with_emission(scenes.random_cluster(n=30, seed=3, L=2, nb=3, n_lights=2), seed=5)
     _fd_check(sc, alpha_model=O.ALPHA_GFSGS, stride=4)
     _fd_check(sc, directional=True, stride=4)
+
+
+def test_frame_gradients_match_finite_differences():
+    """dL/dtu and dL/dtv of unnormalised, non-orthogonal frame inputs (carried through
+    the Gram-Schmidt construction of Eq. G) against central differences."""
+    sc = scenes.with_emission(scenes.random_cluster(n=30, seed=3, L=2, nb=3, n_lights=2), seed=5)
+    rng = np.random.default_rng(1)
+    sc["tu"] = sc["tu"] * rng.uniform(0.5, 2.0, (sc["n"], 1)) + 0.2 * sc["tv"]
+    sc["tv"] = sc["tv"] * rng.uniform(0.5, 2.0, (sc["n"], 1))
+    frames = (("tu", 3), ("tv", 3))
+    _fd_check(sc, keys=frames)
+    _fd_check(sc, alpha_model=O.ALPHA_GFSGS, stride=4, keys=frames)
+    _fd_check(sc, directional=True, stride=4, keys=frames)
 
 
 def test_geometry_gradients_need_pairs():
