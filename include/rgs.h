@@ -203,7 +203,7 @@ rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE,
                              float *dL_dopacity, float *dL_dlambda, void *stream);
 
 /* rgs_adjoint_pairs with the geometry gradients as well (Sec. 6, Eqs. dl-dgeo-0 and
- * dl-dgeo-1, App. C), with respect to the surfel centres and scales, frames held fixed:
+ * dl-dgeo-1, App. C), with respect to the surfel centres, scales and frame inputs:
  *   - the decay term V_ji = lambda_j A_j T_ij |n_i.d| |n_j.d| / r^2 of every pair moves with
  *     p_i and p_j (d = (p_j - p_i)/r and r), with s^u_j, s^v_j (A_j is proportional to
  *     s^u_j s^v_j) and with the centre and scales of every occluder k of its segment
@@ -211,16 +211,21 @@ rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE,
  *   - the directional effects Y(R_i d) (receiver's BRDF lobe) and Y(-d) (source's
  *     radiance) move with d;
  *   - the direct term moves with p_i (the light direction, cos and 1/r^2 of a point light)
- *     and with its shadow occluders.
+ *     and with its shadow occluders;
+ *   - the normals enter geo, the lobe R_i and the direct term's cos, and every occluder's
+ *     frame (t^u, t^v, n) its crossing point; the orthonormal frame's gradients are carried
+ *     back through the Gram-Schmidt construction of rgs_build_scene (Eq. G) to the tu, tv
+ *     the caller passed (unnormalised inputs are fine).
  * Discrete events (the front and eps_plane tests, the 3-sigma cutoff) are held fixed, so
  * this is the derivative of the smooth piece the scene lies on.
  *   dL_dp : device [N][3] (dL/dp_i, caller order) or NULL.
  *   dL_ds : device [N][2] (dL/ds^u_i, dL/ds^v_i) or NULL.
+ *   dL_dtu, dL_dtv : device [N][3] (dL/dtu_i, dL/dtv_i of the frame inputs) or NULL.
  *   the rest as rgs_adjoint_pairs (every output may be NULL).
  * Asynchronous.  Errors as rgs_adjoint_pairs. */
 rgs_status rgs_adjoint_pairs_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
                                       float *dL_dopacity, float *dL_dlambda, float *dL_dp, float *dL_ds,
-                                      void *stream);
+                                      float *dL_dtu, float *dL_dtv, void *stream);
 
 /* Runs B^(0) = S = E + D, B^(k) = S + K B^(k-1) for k = 1..n_bounces with
  * (K B)_i = o_i c_i (x) sum_r (pi/nd) Y(R_i d_r) sum_h a_rh Y(-d_r)^T B_{j_h}

@@ -73,7 +73,7 @@ class Pipeline:
 
     def adjoint_pairs_geometry(self, g, stream=None):
         """Center-to-center gradients with the geometry ones (Eqs. dl-dgeo-0/1):
-        (dL/dE, dL/da^d, dL/do, dL/dlambda, dL/dp [N,3], dL/ds [N,2])."""
+        (dL/dE, dL/da^d, dL/do, dL/dlambda, dL/dp [N,3], dL/ds [N,2], dL/dtu [N,3], dL/dtv [N,3])."""
         return rgs.rgs_adjoint_pairs_geometry(self.transport, g, stream=stream)
 
     def step(self, d, g, B_out=None, grads=(None, None, None), stream=None):

@@ -130,9 +130,10 @@ __global__ void RGS_ADJ_LB k_adj_src(RaysDev rays, int C, int col0, const long l
 // direction): with h_k = sum_ch u_i[L,ch][k] o_i c_{i,l(k),ch} I_ch and H = h . Y(R_i w), the
 // term H (n_i.w) fall T moves with w (through Y(R_i w) and n_i.w), with fall = 1/r^2 and with
 // each shadow occluder's crossing point; a directional light has a fixed w and fall = 1.
+// gF (with dp): the frame gradients, through n_i (cos and R_i) and the occluders' frames.
 template <int NC>
 __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restrict__ lpos, const float *__restrict__ lint,
-                             int C, const float *__restrict__ u, float *P, float *dop, float *dp, float *ds) {
+                             int C, const float *__restrict__ u, float *P, float *dop, float *dp, float *ds, float *gF) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= sc.n * nl) return;
     const int i = tid / nl, lt = tid - i * nl;
@@ -187,9 +188,14 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
             h[k] *= ai;
             H += h[k] * Y[k];
         }
-        const float3 t3 = reflect_n(n, sh_grad_dot<NC>(rw, h));
+        const float3 t1 = sh_grad_dot<NC>(rw, h);
+        const float3 t3 = reflect_n(n, t1);
         const float f = fall * T;
         gw = make_float3(f * (cs * t3.x + H * n.x), f * (cs * t3.y + H * n.y), f * (cs * t3.z + H * n.z));
+        const float3 gn = reflect_grad_n(n, w, (f * cs) * t1) + (H * f) * w; // R_i w and cos = n_i.w
+        atomicAdd(&gF[9 * (size_t)i + 6], gn.x);
+        atomicAdd(&gF[9 * (size_t)i + 7], gn.y);
+        atomicAdd(&gF[9 * (size_t)i + 8], gn.z);
     }
     if (qv != 0.f && nzero <= 1) {
         auto pass2 = [&](int j) {
@@ -214,6 +220,7 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
                 atomicAdd(&dp[3 * j + 2], -coef * pw.z);
                 atomicAdd(&ds[2 * j], coef * (-2.f * uu * uu * __ldg(&sc.FU[j].w)));
                 atomicAdd(&ds[2 * j + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[j].w)));
+                occluder_frame_grad(sc, j, o, w, t, uu, vv, coef, gF);
             }
         };
         bvh_traverse(sc, o, w, r, pass2);
@@ -558,7 +565,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     if (nb >= 1 && (r = KT(nb)) != RGS_OK) return r; // v^(n) only adds to u
     if (t->nl > 0) {
         const int nth = n * t->nl;
-        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, C, t->u, t->Pg, t->dop, nullptr, nullptr); }
+        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, C, t->u, t->Pg, t->dop, nullptr, nullptr, nullptr); }
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
@@ -595,10 +602,10 @@ template <int NC> rgs_status accum_nc(rgs_transport *t, const float *X, const fl
     RGS_LAUNCH("pair accum");
     return RGS_OK;
 }
-template <int NC> rgs_status shadow_nc(rgs_transport *t, cudaStream_t st, float *dp, float *ds) {
+template <int NC> rgs_status shadow_nc(rgs_transport *t, cudaStream_t st, float *dp, float *ds, float *gF) {
     if (t->nl <= 0) return RGS_OK;
     const int nth = t->n * t->nl;
-    { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->nl, t->ldir, t->lpos, t->lint, t->C, t->u, t->Pg, t->dop, dp, ds); }
+    { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(t->sc->dev(), t->nl, t->ldir, t->lpos, t->lint, t->C, t->u, t->Pg, t->dop, dp, ds, gF); }
     RGS_LAUNCH("shadow backward");
     return RGS_OK;
 }
@@ -622,9 +629,9 @@ rgs_status rgs_adjoint_prologue(rgs_transport *t, int nc, const float *g, cudaSt
 rgs_status rgs_pair_accum(rgs_transport *t, int nc, const float *X, const float *Y, cudaStream_t st) {
     RGS_NC_SWITCH(nc, accum_nc<1>(t, X, Y, st), accum_nc<4>(t, X, Y, st), accum_nc<9>(t, X, Y, st), accum_nc<16>(t, X, Y, st))
 }
-rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float *dp, float *ds) {
-    RGS_NC_SWITCH(nc, shadow_nc<1>(t, st, dp, ds), shadow_nc<4>(t, st, dp, ds), shadow_nc<9>(t, st, dp, ds),
-                  shadow_nc<16>(t, st, dp, ds))
+rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float *dp, float *ds, float *gF) {
+    RGS_NC_SWITCH(nc, shadow_nc<1>(t, st, dp, ds, gF), shadow_nc<4>(t, st, dp, ds, gF), shadow_nc<9>(t, st, dp, ds, gF),
+                  shadow_nc<16>(t, st, dp, ds, gF))
 }
 rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st) {
     RGS_NC_SWITCH(nc, finalize_nc<1>(t, dE, dad, dop, st), finalize_nc<4>(t, dE, dad, dop, st),
@@ -633,7 +640,7 @@ rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad,
 #undef RGS_NC_SWITCH
 
 rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st) {
-    if (t->kind == RGS_KIND_PAIRS) return rgs_adjoint_pairs_impl(t, g, dE, dad, dop, nullptr, nullptr, nullptr, st);
+    if (t->kind == RGS_KIND_PAIRS) return rgs_adjoint_pairs_impl(t, g, dE, dad, dop, nullptr, nullptr, nullptr, nullptr, nullptr, st);
     rgs_status r;
     const int nb = t->nb_last, n = t->n;
     const size_t A = t->arr();

@@ -342,7 +342,7 @@ rgs_status rgs_trace_pairs(rgs_scene *scene, const rgs_lights *lights, const rgs
 
 static rgs_status adjoint_pairs_checked(const char *fn, rgs_transport *t, const float *dL_dB, float *dL_dE,
                                         float *dL_dalbedo, float *dL_dopacity, float *dL_dlambda, float *dL_dp,
-                                        float *dL_ds, void *stream) {
+                                        float *dL_ds, float *dL_dtu, float *dL_dtv, void *stream) {
     g_err[0] = 0;
     if (!t || !dL_dB) {
         rgs_set_error("%s: NULL argument", fn);
@@ -356,20 +356,21 @@ static rgs_status adjoint_pairs_checked(const char *fn, rgs_transport *t, const 
         rgs_set_error("%s: no rgs_solve on this transport since it was traced", fn);
         return RGS_ERR_STATE;
     }
-    return rgs_adjoint_pairs_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda, dL_dp, dL_ds, S(stream));
+    return rgs_adjoint_pairs_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda, dL_dp, dL_ds, dL_dtu, dL_dtv,
+                                  S(stream));
 }
 
 rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
                              float *dL_dopacity, float *dL_dlambda, void *stream) {
     return adjoint_pairs_checked("rgs_adjoint_pairs", t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda, nullptr,
-                                 nullptr, stream);
+                                 nullptr, nullptr, nullptr, stream);
 }
 
 rgs_status rgs_adjoint_pairs_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
                                       float *dL_dopacity, float *dL_dlambda, float *dL_dp, float *dL_ds,
-                                      void *stream) {
+                                      float *dL_dtu, float *dL_dtv, void *stream) {
     return adjoint_pairs_checked("rgs_adjoint_pairs_geometry", t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, dL_dlambda,
-                                 dL_dp, dL_ds, stream);
+                                 dL_dp, dL_ds, dL_dtu, dL_dtv, stream);
 }
 
 rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_t precision, float *B_out,
@@ -560,6 +561,7 @@ void rgs_destroy_scene(rgs_scene *s) {
     dev_free(s->N4);
     dev_free(s->FU);
     dev_free(s->FV);
+    dev_free(s->GS);
     dev_free(s->cl);
     dev_free(s->kk);
     dev_free(s->uid);

@@ -371,6 +371,30 @@ __device__ __forceinline__ float3 crossing_pw(const SceneDev &sc, int k, float3 
     g.z -= Nk.z * s;
     return g;
 }
+// Frame gradients of an occluder k crossed at o + t d (u, v from crossing_pw), scaled by
+// coef = dL/dq, added to gF[k] = (dL/dt^u, dL/dt^v, dL/dn): q = u^2 + v^2 with
+// u = (x - p_k).t^u_k / s^u_k moves with t^u_k by 2 u (x - p_k) / s^u_k, and with n_k through
+// t = n_k.(p_k - o)/(n_k.d) by -(grad_x q . d)/(n_k.d) (x - p_k).
+__device__ __forceinline__ void occluder_frame_grad(const SceneDev &sc, int k, float3 o, float3 d, float t, float u,
+                                                    float v, float coef, float *gF) {
+    const float4 Pk = __ldg(&sc.P[k]), Nk = __ldg(&sc.N4[k]), U = __ldg(&sc.FU[k]), V = __ldg(&sc.FV[k]);
+    const float xm[3] = {o.x + t * d.x - Pk.x, o.y + t * d.y - Pk.y, o.z + t * d.z - Pk.z};
+    const float a = 2.f * u * U.w, b = 2.f * v * V.w;
+    const float gxd = a * (U.x * d.x + U.y * d.y + U.z * d.z) + b * (V.x * d.x + V.y * d.y + V.z * d.z);
+    const float fn = -gxd / (Nk.x * d.x + Nk.y * d.y + Nk.z * d.z);
+    float *g = gF + 9 * (size_t)k;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        atomicAdd(&g[q], coef * a * xm[q]);
+        atomicAdd(&g[3 + q], coef * b * xm[q]);
+        atomicAdd(&g[6 + q], coef * fn * xm[q]);
+    }
+}
+// dL/dn of a term gR . Y(R w) with R w = 2 (n.w) n - w: 2 ((n.gR) w + (n.w) gR)
+__device__ __forceinline__ float3 reflect_grad_n(float3 n, float3 w, float3 gR) {
+    const float ng = dot3(n, gR), nw = dot3(n, w);
+    return make_float3(2.f * (ng * w.x + nw * gR.x), 2.f * (ng * w.y + nw * gR.y), 2.f * (ng * w.z + nw * gR.z));
+}
 __device__ __forceinline__ float dalpha_do(const SceneDev &sc, float o, float G) {
     if (sc.alpha_model == RGS_ALPHA_GFSGS) {
         const float x = o * G;
@@ -548,6 +572,7 @@ struct rgs_scene {
     int device = 0;
     int n = 0, cap = 0, L = 0, nc = 1, alpha_model = 0;
     float4 *P = nullptr, *N4 = nullptr, *FU = nullptr, *FV = nullptr;
+    float4 *GS = nullptr; // Gram-Schmidt record of the frame inputs: |tu|, |tv - (t^u.tv) t^u|, t^u.tv
     float *cl = nullptr, *kk = nullptr;
     int *uid = nullptr, *inv = nullptr;
     BvhNode *nodes = nullptr;
@@ -806,12 +831,13 @@ template <int NC>
 rgs_status pairs_bounce(const rgs_transport *t, bool rows16, const float *Bprev, const __nv_bfloat16 *Bprev16,
                         const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16, double *norm2, cudaStream_t st);
 rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, float *dlam,
-                                  float *dp, float *ds, cudaStream_t st);
+                                  float *dp, float *ds, float *dtu, float *dtv, cudaStream_t st);
 // adjoint pieces shared by both transports (rgs_adjoint.cu): v^(0) = dL/dB, u = v^(0),
 // P = v^(0) Q^(n-1), dop = 0; P += X Y; the shadow-ray backward; the outputs
 rgs_status rgs_adjoint_prologue(rgs_transport *t, int nc, const float *g, cudaStream_t st);
 rgs_status rgs_pair_accum(rgs_transport *t, int nc, const float *X, const float *Y, cudaStream_t st);
-rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float *dp = nullptr, float *ds = nullptr);
+rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float *dp = nullptr, float *ds = nullptr,
+                               float *gF = nullptr);
 rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st);
 void rgs_copy_offsets(const long long *off, unsigned long long *cursor, int n, cudaStream_t st);
 int rgs_scan_tmp_size(int n);

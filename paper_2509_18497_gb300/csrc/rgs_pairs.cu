@@ -282,15 +282,17 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_adj_src_pairs(SceneDev sc, int
 // GEO: also the directional effects of Eq. dl-dgeo-1, the derivative of the pair's term in
 // its direction d through Y(R_i d) and Y(-d):
 //   gq_e = V_ji o_i (R_i sum_k wi_k grad Y_k(R_i d) - sum_k wo_k grad Y_k(-d)),
-//   wi_k = sum_{a,c} (Y(-d) . B_j[c]) c_{i,l(k),ch} v_i[c][k],  wo_k = sum_{a,c} y_c B_j[c][k].
+//   wi_k = sum_{a,c} (Y(-d) . B_j[c]) c_{i,l(k),ch} v_i[c][k],  wo_k = sum_{a,c} y_c B_j[c][k],
+// and the receiver normal's share through R_i d, added to gF[i] (dL/dn_i).
 template <int NC, bool GEO>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int nb, const long long *__restrict__ pair_off,
                                                         const int2 *__restrict__ rec, size_t A,
                                                         const float *__restrict__ V, const float *__restrict__ Bit,
-                                                        float *gpair, float4 *gq) {
+                                                        float *gpair, float4 *gq, float *gF) {
     const int i = blockIdx.x;
     const float4 Pi = __ldg(&sc.P[i]);
     const float3 pi = f3(Pi), ni = f3(sc.N4[i]);
+    [[maybe_unused]] float3 gn = make_float3(0.f, 0.f, 0.f);
     for (long long e = pair_off[i] + threadIdx.x; e < pair_off[i + 1]; e += PAIR_THREADS) {
         const int2 jv = __ldg(&rec[e]);
         const int j = jv.x;
@@ -334,10 +336,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int
         const float ai = alpha_center(sc, i);
         gpair[e] = g * ai;
         if constexpr (GEO) {
-            const float3 t3 = reflect_n(ni, sh_grad_dot<NC>(rd, wi));
+            const float3 t1 = sh_grad_dot<NC>(rd, wi);
+            const float3 t3 = reflect_n(ni, t1);
             const float3 t2 = sh_grad_dot<NC>(neg3(d), wo);
             const float f = __int_as_float(jv.y) * ai;
             gq[e] = make_float4(f * (t3.x - t2.x), f * (t3.y - t2.y), f * (t3.z - t2.z), 0.f);
+            gn = gn + reflect_grad_n(ni, d, f * t1);
+        }
+    }
+    if constexpr (GEO) {
+        if (gn.x != 0.f || gn.y != 0.f || gn.z != 0.f) {
+            atomicAdd(&gF[9 * (size_t)i + 6], gn.x);
+            atomicAdd(&gF[9 * (size_t)i + 7], gn.y);
+            atomicAdd(&gF[9 * (size_t)i + 8], gn.z);
         }
     }
 }
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
                                                    const float *__restrict__ lam, const float *__restrict__ aarea,
                                                    const float *__restrict__ daarea, const float *__restrict__ gpair,
                                                    const float4 *__restrict__ gq, float *dop, float *dlam, float *dp,
-                                                   float *ds, int *flags) {
+                                                   float *ds, float *gF, int *flags) {
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
@@ -404,6 +415,14 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
         const float fs = g * lj * T * geo * Aj;
         atomicAdd(&ds[2 * j], fs * __ldg(&sc.FU[j].w));
         atomicAdd(&ds[2 * j + 1], fs * __ldg(&sc.FV[j].w));
+        // normals through geo: d geo/d n_i = |n_j.d| d / r^2, d geo/d n_j = (n_i.d) sgn(n_j.d) d / r^2
+        const float fi = f * fabsf(njd), fj = f * fabsf(nid) * sj;
+        atomicAdd(&gF[9 * (size_t)i + 6], fi * d.x);
+        atomicAdd(&gF[9 * (size_t)i + 7], fi * d.y);
+        atomicAdd(&gF[9 * (size_t)i + 8], fi * d.z);
+        atomicAdd(&gF[9 * (size_t)j + 6], fj * d.x);
+        atomicAdd(&gF[9 * (size_t)j + 7], fj * d.y);
+        atomicAdd(&gF[9 * (size_t)j + 8], fj * d.z);
     }
     if ((dop || dp) && nzero <= 1 && g != 0.f) {
         const float q = -g * lj * Aj * geo;
@@ -429,6 +448,7 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
                 atomicAdd(&dp[3 * k + 2], -coef * pw.z);
                 atomicAdd(&ds[2 * k], coef * (-2.f * uu * uu * __ldg(&sc.FU[k].w)));
                 atomicAdd(&ds[2 * k + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[k].w)));
+                occluder_frame_grad(sc, k, pi, d, tk, uu, vv, coef, gF);
             }
         };
         bvh_traverse(sc, pi, d, r, pass2);
@@ -446,9 +466,12 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     }
 }
 
-// geometry gradients back to the caller's order
-__global__ void k_geo_out(int n, const int *__restrict__ uid, const float *__restrict__ dp_acc,
-                          const float *__restrict__ ds_acc, float *dp, float *ds) {
+// geometry gradients back to the caller's order; the frame's (dL/dt^u, dL/dt^v, dL/dn)
+// carried back through the Gram-Schmidt construction of Eq. G: n = t^u x t^v,
+// t^v = b'/|b'| with b' = tv - (t^u.tv) t^u, t^u = tu/|tu| (GS holds |tu|, |b'|, t^u.tv)
+__global__ void k_geo_out(SceneDev sc, const float4 *__restrict__ GS, int n, const int *__restrict__ uid,
+                          const float *__restrict__ dp_acc, const float *__restrict__ ds_acc,
+                          const float *__restrict__ gF, float *dp, float *ds, float *dtu, float *dtv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = uid[i];
@@ -456,6 +479,32 @@ __global__ void k_geo_out(int n, const int *__restrict__ uid, const float *__res
         for (int a = 0; a < 3; ++a) dp[3 * o + a] = dp_acc[3 * i + a];
     if (ds)
         for (int a = 0; a < 2; ++a) ds[2 * o + a] = ds_acc[2 * i + a];
+    if (!dtu && !dtv) return;
+    const float3 tu = f3(sc.FU[i]), tv = f3(sc.FV[i]);
+    const float4 gs = GS[i];
+    const float *g = gF + 9 * (size_t)i;
+    const float3 Gn = make_float3(g[6], g[7], g[8]);
+    const float3 cu = make_float3(tv.y * Gn.z - tv.z * Gn.y, tv.z * Gn.x - tv.x * Gn.z, tv.x * Gn.y - tv.y * Gn.x);
+    const float3 cv = make_float3(Gn.y * tu.z - Gn.z * tu.y, Gn.z * tu.x - Gn.x * tu.z, Gn.x * tu.y - Gn.y * tu.x);
+    float3 Gu = make_float3(g[0] + cu.x, g[1] + cu.y, g[2] + cu.z);
+    const float3 Gv = make_float3(g[3] + cv.x, g[4] + cv.y, g[5] + cv.z);
+    const float vg = dot3(tv, Gv);
+    const float3 gb = (1.f / gs.y) * (Gv - vg * tv);
+    const float3 b = gs.y * tv + gs.z * tu;
+    const float ugb = dot3(tu, gb);
+    Gu = Gu - (gs.z * gb + ugb * b);
+    const float ug = dot3(tu, Gu);
+    const float3 du = (1.f / gs.x) * (Gu - ug * tu), dv = gb - ugb * tu;
+    if (dtu) {
+        dtu[3 * o] = du.x;
+        dtu[3 * o + 1] = du.y;
+        dtu[3 * o + 2] = du.z;
+    }
+    if (dtv) {
+        dtv[3 * o] = dv.x;
+        dtv[3 * o + 1] = dv.y;
+        dtv[3 * o + 2] = dv.z;
+    }
 }
 
 __global__ void k_lam_out(int n, const int *__restrict__ uid, const float *__restrict__ dlam, float *out) {
@@ -555,8 +604,8 @@ template rgs_status pairs_bounce<16>(const rgs_transport *, bool, const float *,
                                      float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
 
 namespace {
-struct GeoAcc { // internal-order accumulators of the geometry gradients (both or neither)
-    float *dp = nullptr, *ds = nullptr;
+struct GeoAcc { // internal-order accumulators of the geometry gradients (all or none)
+    float *dp = nullptr, *ds = nullptr, *gF = nullptr;
     float4 *gq = nullptr;
 };
 
@@ -573,17 +622,17 @@ rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float 
         RGS_LAUNCH("adjoint pairs");
         if (a <= nb - 1 && (r = rgs_pair_accum(t, NC, t->v + A * a, t->Q + A * (nb - 1 - a), st)) != RGS_OK) return r;
     }
-    if ((r = rgs_shadow_backward(t, NC, st, geo.dp, geo.ds)) != RGS_OK) return r;
+    if ((r = rgs_shadow_backward(t, NC, st, geo.dp, geo.ds, geo.gF)) != RGS_OK) return r;
     if (nb >= 1 && (dopo || dlam_acc || geo.dp)) {
         const int chunks = (n + PCH - 1) / PCH;
         if (geo.dp) {
             ProfScope ps_("k_pair_g", st);
-            k_pair_g<NC, true><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh, geo.gq);
+            k_pair_g<NC, true><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh, geo.gq, geo.gF);
         } else {
             ProfScope ps_("k_pair_g", st);
-            k_pair_g<NC, false><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh, nullptr);
+            k_pair_g<NC, false><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh, nullptr, nullptr);
         }
-        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, geo.gq, dopo ? t->dop : nullptr, dlam_acc, geo.dp, geo.ds, t->flags); }
+        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, geo.gq, dopo ? t->dop : nullptr, dlam_acc, geo.dp, geo.ds, geo.gF, t->flags); }
         RGS_LAUNCH("pair backward");
     }
     return rgs_adjoint_finalize(t, NC, dE, dad, dopo, st);
@@ -591,7 +640,7 @@ rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float 
 } // namespace
 
 rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, float *dlam,
-                                  float *dp, float *ds, cudaStream_t st) {
+                                  float *dp, float *ds, float *dtu, float *dtv, cudaStream_t st) {
     rgs_status r;
     const int nb = t->nb_last, n = t->n;
     const size_t A = t->arr();
@@ -602,7 +651,7 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
     }
     float *dlam_acc = nullptr;
     GeoAcc geo;
-    const bool want_geo = dp || ds;
+    const bool want_geo = dp || ds || dtu || dtv;
     struct Scratch {
         rgs_transport *t;
         cudaStream_t st;
@@ -617,6 +666,7 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
             pool_release(geo->dp, st);
             pool_release(geo->ds, st);
             pool_release(geo->gq, st);
+            pool_release(geo->gF, st);
         }
     } scratch{t, st, &dlam_acc, &geo};
     if ((r = pool_alloc(&t->v, A * (nb + 1), st)) != RGS_OK) return r;
@@ -632,8 +682,10 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
         if ((r = pool_alloc(&geo.dp, (size_t)n * 3, st)) != RGS_OK) return r;
         if ((r = pool_alloc(&geo.ds, (size_t)n * 2, st)) != RGS_OK) return r;
         if ((r = pool_alloc(&geo.gq, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK) return r;
+        if ((r = pool_alloc(&geo.gF, (size_t)n * 9, st)) != RGS_OK) return r;
         RGS_CUDA(cudaMemsetAsync(geo.dp, 0, sizeof(float) * n * 3, st));
         RGS_CUDA(cudaMemsetAsync(geo.ds, 0, sizeof(float) * n * 2, st));
+        RGS_CUDA(cudaMemsetAsync(geo.gF, 0, sizeof(float) * n * 9, st));
     }
     { ProfScope ps_("k_copy_off", st); rgs_copy_offsets(t->src_off, t->cursor, n, st); }
     { ProfScope ps_("k_pair_src_fill", st); k_pair_src_fill<<<n, 256, 0, st>>>(n, t->pair_off, t->pair_rec, t->cursor, t->tr); }
@@ -651,7 +703,7 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
         RGS_LAUNCH("lambda gradient");
     }
     if (want_geo) {
-        { ProfScope ps_("k_geo_out", st); k_geo_out<<<(n + 255) / 256, 256, 0, st>>>(n, t->sc->uid, geo.dp, geo.ds, dp, ds); }
+        { ProfScope ps_("k_geo_out", st); k_geo_out<<<(n + 255) / 256, 256, 0, st>>>(t->sc->dev(), t->sc->GS, n, t->sc->uid, geo.dp, geo.ds, geo.gF, dp, ds, dtu, dtv); }
         RGS_LAUNCH("geometry gradients");
     }
     return RGS_OK;

@@ -153,8 +153,8 @@ __global__ void k_radix_scatter(const unsigned *__restrict__ kin, const int *__r
 
 // ---------------------------------------------------------------- surfel gather
 __global__ void k_gather(rgs_surfels in, int n, int L, int alpha_model, const int *__restrict__ perm, float4 *P,
-                         float4 *N4, float4 *FU, float4 *FV, float *cl, float *kk, int *uid, int *inv, float *boxes,
-                         int *flags) {
+                         float4 *N4, float4 *FU, float4 *FV, float4 *GS, float *cl, float *kk, int *uid, int *inv,
+                         float *boxes, int *flags) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int i = perm[k];
@@ -166,9 +166,11 @@ __global__ void k_gather(rgs_surfels in, int n, int L, int alpha_model, const in
     // Gram-Schmidt, n = tu x tv (Eq. G)
     float la = sqrtf(dot3(a, a));
     a = (1.f / la) * a;
-    b = b - dot3(a, b) * a;
+    const float pr = dot3(a, b);
+    b = b - pr * a;
     float lb = sqrtf(dot3(b, b));
     b = (1.f / lb) * b;
+    GS[k] = make_float4(la, lb, pr, 0.f);
     float3 nn = make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
     float su = in.s[2 * i], sv = in.s[2 * i + 1];
     float o = in.o[i];
@@ -361,7 +363,7 @@ rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_b
         s->cap = 0;                                                                                                    \
         return r;                                                                                                      \
     }
-        ALLOC(P, n) ALLOC(N4, n) ALLOC(FU, n) ALLOC(FV, n) ALLOC(cl, (size_t)n * 12) ALLOC(kk, n) ALLOC(uid, n)
+        ALLOC(P, n) ALLOC(N4, n) ALLOC(FU, n) ALLOC(FV, n) ALLOC(GS, n) ALLOC(cl, (size_t)n * 12) ALLOC(kk, n) ALLOC(uid, n)
         ALLOC(inv, n) ALLOC(nodes, n > 1 ? n - 1 : 1) ALLOC(boxes, (size_t)(2 * n - 1) * 6) ALLOC(parent, 2 * n)
         ALLOC(visit, n) ALLOC(keys, n) ALLOC(keys_alt, n) ALLOC(vals, n) ALLOC(vals_alt, n)
 #undef ALLOC
@@ -401,7 +403,7 @@ rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_b
     }
     RGS_LAUNCH("radix sort");
     // after an even number of passes ka == keys, va == vals
-    { ProfScope ps_("k_gather", st); k_gather<<<(n + 127) / 128, 128, 0, st>>>(*in, n, s->L, s->alpha_model, va, s->P, s->N4, s->FU, s->FV, s->cl,
+    { ProfScope ps_("k_gather", st); k_gather<<<(n + 127) / 128, 128, 0, st>>>(*in, n, s->L, s->alpha_model, va, s->P, s->N4, s->FU, s->FV, s->GS, s->cl,
                                               s->kk, s->uid, s->inv, s->boxes, s->flags); }
     RGS_LAUNCH("gather");
     if (n > 1) {

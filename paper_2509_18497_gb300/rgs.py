@@ -125,7 +125,7 @@ def load(path=LIB_PATH):
     L.rgs_trace_pairs.restype = ct.c_int
     L.rgs_adjoint_pairs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.rgs_adjoint_pairs.restype = ct.c_int
-    L.rgs_adjoint_pairs_geometry.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rgs_adjoint_pairs_geometry.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rgs_adjoint_pairs_geometry.restype = ct.c_int
     L.rgs_set_memory_budget.argtypes = [vp, ct.c_int64]
     L.rgs_set_memory_budget.restype = ct.c_int
@@ -268,7 +268,7 @@ def rgs_adjoint_pairs(transport, dL_dB, stream=None):
 
 
 def rgs_adjoint_pairs_geometry(transport, dL_dB, stream=None):
-    """rgs_adjoint_pairs_geometry: returns (dL/dE, dL/da^d, dL/do, dL/dlambda, dL/dp, dL/ds)."""
+    """rgs_adjoint_pairs_geometry: returns (dL/dE, dL/da^d, dL/do, dL/dlambda, dL/dp, dL/ds, dL/dtu, dL/dtv)."""
     L = load()
     n, nc, C = transport.n, transport.nc, transport.C
     dE = torch.empty((n, nc, 3), device="cuda", dtype=torch.float32)
@@ -277,11 +277,14 @@ def rgs_adjoint_pairs_geometry(transport, dL_dB, stream=None):
     dlam = torch.empty((n,), device="cuda", dtype=torch.float32)
     dp = torch.empty((n, 3), device="cuda", dtype=torch.float32)
     ds = torch.empty((n, 2), device="cuda", dtype=torch.float32)
+    dtu = torch.empty((n, 3), device="cuda", dtype=torch.float32)
+    dtv = torch.empty((n, 3), device="cuda", dtype=torch.float32)
     _check(L.rgs_adjoint_pairs_geometry(transport.h, _dev(dL_dB, (n, nc, C), "dL_dB"), _dev(dE, (n, nc, 3), "dL_dE"),
                                         _dev(dad, (n, 3), "dL_dalbedo"), _dev(dop, (n,), "dL_dopacity"),
                                         _dev(dlam, (n,), "dL_dlambda"), _dev(dp, (n, 3), "dL_dp"),
-                                        _dev(ds, (n, 2), "dL_ds"), _stream(stream)))
-    return dE, dad, dop, dlam, dp, ds
+                                        _dev(ds, (n, 2), "dL_ds"), _dev(dtu, (n, 3), "dL_dtu"),
+                                        _dev(dtv, (n, 3), "dL_dtv"), _stream(stream)))
+    return dE, dad, dop, dlam, dp, ds, dtu, dtv
 
 
 def rgs_solve(transport, E, n_bounces, B_out=None, stats=False, precision=RGS_FP32, stream=None):

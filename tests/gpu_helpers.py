@@ -29,8 +29,9 @@ def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=F
     if W is not None:
         g = torch.as_tensor(np.ascontiguousarray(W, np.float32), device="cuda")
         if pairs and geometry:
-            dE, dad, dop, dlam, dp, ds = pipe.adjoint_pairs_geometry(g)
-            out.update(dlam=dlam.double().cpu().numpy(), dp=dp.double().cpu().numpy(), ds=ds.double().cpu().numpy())
+            dE, dad, dop, dlam, dp, ds, dtu, dtv = pipe.adjoint_pairs_geometry(g)
+            out.update(dlam=dlam.double().cpu().numpy(), dp=dp.double().cpu().numpy(), ds=ds.double().cpu().numpy(),
+                       dtu=dtu.double().cpu().numpy(), dtv=dtv.double().cpu().numpy())
         elif pairs:
             dE, dad, dop, dlam = pipe.adjoint_pairs(g)
             out["dlam"] = dlam.double().cpu().numpy()

@@ -1,5 +1,6 @@
-"""Geometry gradients of the center-to-center transport (Eqs. dl-dgeo-0/1: dL/dp and
-dL/d(s^u, s^v) through the decay term, the directional effects and the direct term) on
+"""Geometry gradients of the center-to-center transport (Eqs. dl-dgeo-0/1: dL/dp,
+dL/d(s^u, s^v) and dL/d(tu, tv) through the decay term, the directional effects and the
+direct term) on
 the GPU against the FP64 oracle, whose own values are pinned by central differences of
 the whole forward solve (test_oracle_geometry.py)."""
 import numpy as np
@@ -39,7 +40,20 @@ def _directional(sc, n_lights, seed):
     return out
 
 
+def _skewed_frames(sc, seed):
+    """Unnormalised, non-orthogonal frame inputs (the Gram-Schmidt backward has work to do)."""
+    rng = np.random.default_rng(seed)
+    out = dict(sc)
+    tu = sc["tu"] * rng.uniform(0.5, 2.0, (sc["n"], 1)) + 0.2 * sc["tv"]
+    out["tu"] = tu.astype(np.float32).astype(np.float64)
+    out["tv"] = (sc["tv"] * rng.uniform(0.5, 2.0, (sc["n"], 1))).astype(np.float32).astype(np.float64)
+    return out
+
+
 CASES = {
+    "cluster_skewed": (lambda: _skewed_frames(scenes.with_emission(scenes.random_cluster(n=300, L=2, nb=3, n_lights=2),
+                                                                   seed=8), 9),
+                       rgs.RGS_ALPHA_GAUSS, O.ALPHA_GAUSS),
     "cluster": (lambda: _with_lam(scenes.with_emission(scenes.random_cluster(n=300, L=2, nb=3, n_lights=3), seed=5), 6),
                 rgs.RGS_ALPHA_GAUSS, O.ALPHA_GAUSS),
     "bowl": (lambda: _with_lam(scenes.with_emission(scenes.fruit_bowl(n=1500, L=3, nb=3, n_lights=2), seed=3), 4),
@@ -60,7 +74,7 @@ def test_geometry_gradients_match_oracle(case):
     W = np.random.default_rng(11).normal(size=(sc["n"], nc, C))
     o = run_oracle(sc, W=W, alpha_model=am_or, pairs=True, geometry=True)
     g = run_gpu(sc, W=W, alpha_model=am_gpu, pairs=True, geometry=True)
-    for key in ("dp", "ds"):
+    for key in ("dp", "ds", "dtu", "dtv"):
         assert np.all(np.isfinite(g[key])), key
         assert rel_l2(g[key], o[key]) <= TOL, (key, rel_l2(g[key], o[key]))
     # the other outputs of the same call are those of rgs_adjoint_pairs
