@@ -393,14 +393,21 @@ int or_strata_a(int nd) { /* n_a = 2^floor(log2(nd)/2): largest power of two wit
 
 /* Ray r of surfel i: stratified cosine-weighted direction over the front hemisphere
  * Omega = {w_I . n_i < 0}, i.e. d . n_i > 0 (App. B).  Each ray carries weight pi/Nd. */
-void or_ray_dir(const or_scene *s, int i, int nd, uint64_t seed, int r, double *d) {
+/* the ray's direction in surfel i's frame (t^u, t^v, n): fixed by the strata and jitter */
+static void ray_local(int i, int nd, uint64_t seed, int r, double *c) {
     int na = or_strata_a(nd), nb = nd / na;
     int a = r / nb, b = r % nb;
     double u1 = (a + or_jitter(seed, (uint64_t)i, (uint64_t)r, 0)) / na;
     double u2 = (b + or_jitter(seed, (uint64_t)i, (uint64_t)r, 1)) / nb;
-    double rr = sqrt(u1), ph = 2.0 * OR_PI * u2, cz = sqrt(1.0 - u1);
-    double cx = rr * cos(ph), cy = rr * sin(ph);
-    for (int q = 0; q < 3; ++q) d[q] = cx * s->tu[i * 3 + q] + cy * s->tv[i * 3 + q] + cz * s->nrm[i * 3 + q];
+    double rr = sqrt(u1), ph = 2.0 * OR_PI * u2;
+    c[0] = rr * cos(ph);
+    c[1] = rr * sin(ph);
+    c[2] = sqrt(1.0 - u1);
+}
+void or_ray_dir(const or_scene *s, int i, int nd, uint64_t seed, int r, double *d) {
+    double c[3];
+    ray_local(i, nd, seed, r, c);
+    for (int q = 0; q < 3; ++q) d[q] = c[0] * s->tu[i * 3 + q] + c[1] * s->tv[i * 3 + q] + c[2] * s->nrm[i * 3 + q];
 }
 
 /* ------------------------------------------------------ ray / surfel intersection */
@@ -1518,6 +1525,35 @@ static double occluder_crossing(const or_scene *s, int k, const double *o, const
  * q = u^2 + v^2, u = (x - p_k).t^u_k / s^u_k:  dq/dt^u_k = 2 u (x - p_k) / s^u_k (likewise
  * for t^v), and through t = n_k.(p_k - o)/(n_k.d):  dq/dn_k = -(grad_x q . d)/(n_k.d) (x - p_k).
  * gF: [N][9] gradients with respect to (t^u, t^v, n) of every surfel, or NULL. */
+static void hit_geometry(const or_scene *s, int k, const double *o, const double *d, double coef, double *gpo,
+                         double *gd, double *dp, double *ds, double *gF) {
+    double pw[3], t, u, v;
+    occluder_crossing(s, k, o, d, pw, &t, &u, &v);
+    for (int a = 0; a < 3; ++a) {
+        gpo[a] += coef * pw[a];
+        gd[a] += coef * t * pw[a];
+        if (dp) dp[k * 3 + a] -= coef * pw[a];
+    }
+    if (ds) {
+        ds[k * 2] += coef * (-2.0 * u * u / s->su[k]);
+        ds[k * 2 + 1] += coef * (-2.0 * v * v / s->sv[k]);
+    }
+    if (gF) {
+        const double *pk = s->p + k * 3, *nk = s->nrm + k * 3, *tu = s->tu + k * 3, *tv = s->tv + k * 3;
+        double xm[3], gx[3];
+        for (int a = 0; a < 3; ++a) {
+            xm[a] = o[a] + t * d[a] - pk[a];
+            gx[a] = 2.0 * (u * tu[a] / s->su[k] + v * tv[a] / s->sv[k]);
+        }
+        const double fn = -dot3(gx, d) / dot3(nk, d);
+        for (int a = 0; a < 3; ++a) {
+            gF[k * 9 + a] += coef * 2.0 * u * xm[a] / s->su[k];
+            gF[k * 9 + 3 + a] += coef * 2.0 * v * xm[a] / s->sv[k];
+            gF[k * 9 + 6 + a] += coef * fn * xm[a];
+        }
+    }
+}
+
 static void occluder_backward(const or_scene *s, const double *o, const double *d, int cnt, const int *kk,
                               const double *al, const double *G, double up, double *gpo, double *gd, double *dp,
                               double *ds, double *gF) {
@@ -1526,33 +1562,8 @@ static void occluder_backward(const or_scene *s, const double *o, const double *
         for (int m = 0; m < cnt; ++m)
             if (m != q) others *= 1.0 - al[m];
         const int k = kk[q];
-        double pw[3], t, u, v;
-        occluder_crossing(s, k, o, d, pw, &t, &u, &v);
         /* dL = up * dT = -up * others * dalpha/dq * dq */
-        double coef = -up * others * dalpha_dq(s, s->o[k], G[q]);
-        for (int a = 0; a < 3; ++a) {
-            gpo[a] += coef * pw[a];
-            gd[a] += coef * t * pw[a];
-            if (dp) dp[k * 3 + a] -= coef * pw[a];
-        }
-        if (ds) {
-            ds[k * 2] += coef * (-2.0 * u * u / s->su[k]);
-            ds[k * 2 + 1] += coef * (-2.0 * v * v / s->sv[k]);
-        }
-        if (gF) {
-            const double *pk = s->p + k * 3, *nk = s->nrm + k * 3, *tu = s->tu + k * 3, *tv = s->tv + k * 3;
-            double xm[3], gx[3];
-            for (int a = 0; a < 3; ++a) {
-                xm[a] = o[a] + t * d[a] - pk[a];
-                gx[a] = 2.0 * (u * tu[a] / s->su[k] + v * tv[a] / s->sv[k]);
-            }
-            const double fn = -dot3(gx, d) / dot3(nk, d);
-            for (int a = 0; a < 3; ++a) {
-                gF[k * 9 + a] += coef * 2.0 * u * xm[a] / s->su[k];
-                gF[k * 9 + 3 + a] += coef * 2.0 * v * xm[a] / s->sv[k];
-                gF[k * 9 + 6 + a] += coef * fn * xm[a];
-            }
-        }
+        hit_geometry(s, k, o, d, -up * others * dalpha_dq(s, s->o[k], G[q]), gpo, gd, dp, ds, gF);
     }
 }
 
@@ -1564,7 +1575,9 @@ static void reflect_backward(const double *n, const double *w, const double *gR,
 }
 
 /* Geometry gradients (Eqs. dl-dgeo-0 and dl-dgeo-1, Sec. 6 / App. C) of L(B^(nb)) with
- * g = dL/dB^(nb), for the center-to-center transport: dp [N][3] = dL/dp_i and
+ * g = dL/dB^(nb), for either transport (the hemisphere rays below the pairs' description:
+ * their hit points move with p_i, the ray direction and the source's plane and frame, and
+ * the directional effects act per ray): dp [N][3] = dL/dp_i and
  * ds [N][2] = dL/d(s^u_i, s^v_i), frames held fixed.  Per pair (i <- j), with
  * L_e = V_ji sum_{a,c} y_c^(a) s_c^(nb-1-a), y_c = o_i sum_k c_{i,l(k),ch} Y_k(R_i d) v_i^(a)[k][c]
  * and s_c = sum_k Y_k(-d) B_j[k][c]:
@@ -1582,10 +1595,10 @@ static void reflect_backward(const double *n, const double *w, const double *gR,
  * construction of Eq. G.  Discrete events
  * (front tests, the 3-sigma cutoff, the eps_plane rules) are held fixed: the gradient is
  * the derivative of the smooth piece the scene sits on.  Returns 0, or -1 without a
- * center-to-center transport. */
+ * transport. */
 int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g, double *dp, double *ds,
                      double *dtu, double *dtv) {
-    if (!s->pmode) return -1;
+    if (!s->pmode && !s->ray_off) return -1;
     double *gF = (dtu || dtv) ? dup_arr(NULL, (size_t)s->n * 9) : NULL;
     if (gF) memset(gF, 0, sizeof(double) * (size_t)s->n * 9);
     int n = s->n, nc = s->nc, C = s->C, L = s->L, nl = s->nl;
@@ -1606,7 +1619,104 @@ int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g
     int *kk = NULL;
     double *al = NULL, *Gk = NULL;
     int kcap = 0;
+    /* hemisphere rays: per ray the directional effects (Y(R_i d) through the gathered
+     * radiance X, Y(-d) through every hit's source row) and, per hit, the compositing
+     * weights through q_h at the hit point (dL/dalpha_h = T_h (g_h - R_h)); the ray leaves
+     * p_i along d = c_x t^u_i + c_y t^v_i + c_z n_i with fixed c. */
+    if (!s->pmode) {
+        const int nd = s->nd;
+        const double w = OR_PI / nd;
+        double *y = dup_arr(NULL, (size_t)(nb > 0 ? nb : 1) * C), *X = dup_arr(NULL, (size_t)(nb > 0 ? nb : 1) * C);
+        for (int i = 0; i < n; ++i)
+            for (int r = 0; r < nd; ++r) {
+                long ray = (long)i * nd + r;
+                long e0 = s->ray_off[ray], e1 = s->ray_off[ray + 1];
+                if (e1 == e0 || nb == 0) continue;
+                double c3[3], d[3], md[3], rd[3];
+                ray_local(i, nd, s->seed, r, c3);
+                for (int a = 0; a < 3; ++a) {
+                    d[a] = c3[0] * s->tu[i * 3 + a] + c3[1] * s->tv[i * 3 + a] + c3[2] * s->nrm[i * 3 + a];
+                    md[a] = -d[a];
+                }
+                reflect(s->nrm + i * 3, d, rd);
+                or_sh_eval(L, md, Yo);
+                or_sh_eval(L, rd, Yi);
+                for (int a = 0; a < nb; ++a)
+                    for (int c = 0; c < C; ++c) {
+                        double sv = 0.0;
+                        for (int k = 0; k < nc; ++k)
+                            sv += s->c[((size_t)i * (L + 1) + band_of(k)) * 3 + c % 3] * Yi[k] *
+                                  v[(size_t)a * M + ((size_t)i * nc + k) * C + c];
+                        y[a * C + c] = alpha_c(s, i) * w * sv;
+                        X[a * C + c] = 0.0;
+                    }
+                const int H = (int)(e1 - e0);
+                double *gh = dup_arr(NULL, H), *Th = dup_arr(NULL, H);
+                for (int k = 0; k < nc; ++k) wo[k] = 0.0;
+                double T = 1.0;
+                for (int h = 0; h < H; ++h) {
+                    const long e = e0 + h;
+                    Th[h] = T;
+                    T *= 1.0 - s->hit_alpha[e];
+                    const double ah = s->hit_a[e];
+                    double acc = 0.0;
+                    for (int a = 0; a < nb; ++a) {
+                        const double *Bb = iters + (size_t)(nb - 1 - a) * M + (size_t)s->hit_j[e] * nc * C;
+                        for (int c = 0; c < C; ++c) {
+                            double sv = 0.0;
+                            for (int k = 0; k < nc; ++k) {
+                                sv += Yo[k] * Bb[k * C + c];
+                                wo[k] += ah * y[a * C + c] * Bb[k * C + c];
+                            }
+                            acc += y[a * C + c] * sv;
+                            X[a * C + c] += ah * sv;
+                        }
+                    }
+                    gh[h] = acc;
+                }
+                double gd[3] = {0.0, 0.0, 0.0}, gpi[3] = {0.0, 0.0, 0.0};
+                /* compositing: back to front as in the opacity backward */
+                double R = 0.0;
+                for (int h = H - 1; h >= 0; --h) {
+                    const long e = e0 + h;
+                    const int j = s->hit_j[e];
+                    const double dal = Th[h] * (gh[h] - R);
+                    hit_geometry(s, j, s->p + i * 3, d, dal * dalpha_dq(s, s->o[j], s->hit_G[e]), gpi, gd, dp, ds, gF);
+                    R = s->hit_alpha[e] * gh[h] + (1.0 - s->hit_alpha[e]) * R;
+                }
+                /* directional effects */
+                for (int k = 0; k < nc; ++k) {
+                    double acc = 0.0;
+                    for (int a = 0; a < nb; ++a)
+                        for (int c = 0; c < C; ++c)
+                            acc += X[a * C + c] * alpha_c(s, i) * w * s->c[((size_t)i * (L + 1) + band_of(k)) * 3 + c % 3] *
+                                   v[(size_t)a * M + ((size_t)i * nc + k) * C + c];
+                    wi[k] = acc;
+                }
+                double t1[3], t2[3], t3[3];
+                sh_grad_dot(L, rd, wi, t1);
+                reflect(s->nrm + i * 3, t1, t3);
+                sh_grad_dot(L, md, wo, t2);
+                for (int a = 0; a < 3; ++a) {
+                    gd[a] += t3[a] - t2[a];
+                    dp[i * 3 + a] += gpi[a];
+                }
+                if (gF) {
+                    reflect_backward(s->nrm + i * 3, d, t1, gF + i * 9 + 6);
+                    for (int a = 0; a < 3; ++a) {
+                        gF[i * 9 + a] += c3[0] * gd[a];
+                        gF[i * 9 + 3 + a] += c3[1] * gd[a];
+                        gF[i * 9 + 6 + a] += c3[2] * gd[a];
+                    }
+                }
+                free(gh);
+                free(Th);
+            }
+        free(y);
+        free(X);
+    }
     /* pairs */
+    if (s->pmode)
     for (int i = 0; i < n; ++i)
         for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
             const int j = s->pair_j[e];

@@ -295,8 +295,10 @@ class Oracle:
         return out
 
     def geometry_grad(self, g, E=None, nb=None):
-        """Center-to-center transport: dL/dp [N][3], dL/d(s^u, s^v) [N][2] and dL/dtu,
+        """Either transport: dL/dp [N][3], dL/d(s^u, s^v) [N][2] and dL/dtu,
         dL/dtv [N][3] (the frame inputs)."""
+        if getattr(self, "C", None) is None:
+            raise RuntimeError("geometry gradients need a transport (transport() or pairs())")
         nb = self.sc["nb"] if nb is None else nb
         dp = np.zeros((self.n, 3))
         ds = np.zeros((self.n, 2))
@@ -305,7 +307,7 @@ class Oracle:
         rc = lib().or_geometry_grad(self.h, _ptr(_d(E)), int(nb), _ptr(_d(g).reshape(self._shape())), _ptr(dp), _ptr(ds),
                                     _ptr(dtu), _ptr(dtv))
         if rc != 0:
-            raise RuntimeError("geometry gradients need the center-to-center transport (pairs())")
+            raise RuntimeError("geometry gradients need a transport (transport() or pairs())")
         return dict(dp=dp, ds=ds, dtu=dtu, dtv=dtv)
 
     def brdf_grad_closed_form(self, g, E=None, nb=None):

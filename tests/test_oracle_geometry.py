@@ -1,5 +1,5 @@
-"""Pins of the oracle's geometry gradients (Eqs. dl-dgeo-0 and dl-dgeo-1) for the
-center-to-center transport: the SH gradient against tangent differences of the SH
+"""Pins of the oracle's geometry gradients (Eqs. dl-dgeo-0 and dl-dgeo-1) for both
+transports: the SH gradient against tangent differences of the SH
 (which is itself pinned to scipy), the lone plane's direct term against its closed form,
 and the full dL/dp, dL/ds, dL/dtu, dL/dtv against central differences of the whole forward
 solve for the Gaussian and GFSGS opacity models, point and directional lights (no GPU)."""
@@ -121,7 +121,52 @@ def test_frame_gradients_match_finite_differences():
     _fd_check(sc, directional=True, stride=4, keys=frames)
 
 
-def test_geometry_gradients_need_pairs():
+def _fd_check_hemi(sc, alpha_model=O.ALPHA_GAUSS, stride=3):
+    """As _fd_check for the hemisphere-ray transport (smaller steps: the rays move with
+    p and the frames, so their hit points do too)."""
+    def make(s2):
+        return O.Oracle(s2, alpha_model=alpha_model).transport()
+    orc = make(sc)
+    W = np.random.default_rng(9).normal(size=(sc["n"], orc.nc, orc.C))
+    gg = orc.geometry_grad(W, E=sc["E"], nb=sc["nb"])
+
+    def loss(s2):
+        return float(np.sum(W * make(s2).solve(E=s2["E"], nb=s2["nb"])))
+
+    def fd(key, idx, h=1e-6):
+        def at(hh):
+            s2 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+            s2[key][idx] += hh
+            return loss(s2)
+        def cd(hh):
+            return (at(hh) - at(-hh)) / (2 * hh)
+        return (4 * cd(h / 2) - cd(h)) / 3
+
+    floor = 1e-8 * abs(loss(sc))  # rounding of the differences at h = 1e-6
+    for key, m in (("p", 3), ("s", 2), ("tu", 3), ("tv", 3)):
+        an = gg["d" + key]
+        scale = np.abs(an).max()
+        assert scale > 0
+        for i in range(0, sc["n"], stride):
+            for a in range(m):
+                num = fd(key, (i, a))
+                assert abs(num - an[i, a]) <= 1e-6 * scale + floor, (key, i, a, num, an[i, a])
+
+
+def test_hemisphere_geometry_gradients_match_finite_differences():
+    """The hemisphere-ray transport: every hit point moves with the receiver's centre and
+    frame (the rays leave p_i along fixed local directions) and with the source's plane,
+    frame and scales; the directional effects act per ray.  Skewed frame inputs."""
+    sc = scenes.with_emission(scenes.random_cluster(n=30, seed=3, L=2, nd=16, nb=3, n_lights=2), seed=5)
+    rng = np.random.default_rng(1)
+    sc["tu"] = sc["tu"] * rng.uniform(0.5, 2.0, (sc["n"], 1)) + 0.2 * sc["tv"]
+    sc["tv"] = sc["tv"] * rng.uniform(0.5, 2.0, (sc["n"], 1))
+    _fd_check_hemi(sc)
+    _fd_check_hemi(scenes.with_emission(scenes.random_cluster(n=24, seed=4, L=2, nd=16, nb=2, n_lights=1), seed=6),
+                   alpha_model=O.ALPHA_GFSGS, stride=4)
+
+
+def test_geometry_gradients_need_a_transport():
     sc = scenes.lone_plane()
     with pytest.raises(RuntimeError):
-        O.Oracle(sc).transport().geometry_grad(np.zeros((1, 9, 3)), nb=1)
+        O.Oracle(sc).geometry_grad(np.zeros((1, 9, 3)), nb=1)
