@@ -223,6 +223,26 @@ rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE,
  *   dL_dtu, dL_dtv : device [N][3] (dL/dtu_i, dL/dtv_i of the frame inputs) or NULL.
  *   the rest as rgs_adjoint_pairs (every output may be NULL).
  * Asynchronous.  Errors as rgs_adjoint_pairs. */
+/* rgs_adjoint with the geometry gradients as well (Sec. 6, Eqs. dl-dgeo-0/1, App. C),
+ * for either transport (a center-to-center transport gives what rgs_adjoint_pairs_geometry
+ * gives, without dL/dlambda).  For the hemisphere rays (rgs_trace_transport):
+ *   - every stored hit's alpha moves with its point on the source's plane, which moves with
+ *     the receiver's centre p_i, the ray's direction and the source's centre, scales and
+ *     frame (the hit set and depth order are held fixed); the compositing weights pass the
+ *     derivative on as in the opacity gradient;
+ *   - the directional effects Y(R_i d) and Y(-d) of every ray move with its direction;
+ *   - each ray leaves p_i along a direction fixed in the receiver's frame (its stratum and
+ *     jitter), so the frame's gradient collects the ray directions';
+ *   - the direct term as in rgs_adjoint_pairs_geometry.
+ * The hemisphere form needs every iterate: it returns RGS_ERR_STATE after a checkpointed
+ * solve (rgs_set_checkpointing with a stride other than 0).
+ *   dL_dp, dL_ds, dL_dtu, dL_dtv : device [N][3], [N][2], [N][3], [N][3] (caller order), or
+ *   NULL; the rest as rgs_adjoint.
+ * Asynchronous.  Errors: RGS_ERR_ARG, RGS_ERR_STATE, RGS_ERR_OOM, RGS_ERR_CUDA. */
+rgs_status rgs_adjoint_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
+                                float *dL_dopacity, float *dL_dp, float *dL_ds, float *dL_dtu, float *dL_dtv,
+                                void *stream);
+
 rgs_status rgs_adjoint_pairs_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
                                       float *dL_dopacity, float *dL_dlambda, float *dL_dp, float *dL_ds,
                                       float *dL_dtu, float *dL_dtv, void *stream);

@@ -71,6 +71,11 @@ class Pipeline:
         """Center-to-center gradients (dL/dE, dL/da^d, dL/do, dL/dlambda)."""
         return rgs.rgs_adjoint_pairs(self.transport, g, stream=stream)
 
+    def adjoint_geometry(self, g, stream=None):
+        """Gradients with the geometry ones, either transport:
+        (dL/dE, dL/da^d, dL/do, dL/dp, dL/ds, dL/dtu, dL/dtv)."""
+        return rgs.rgs_adjoint_geometry(self.transport, g, stream=stream)
+
     def adjoint_pairs_geometry(self, g, stream=None):
         """Center-to-center gradients with the geometry ones (Eqs. dl-dgeo-0/1):
         (dL/dE, dL/da^d, dL/do, dL/dlambda, dL/dp [N,3], dL/ds [N,2], dL/dtu [N,3], dL/dtv [N,3])."""

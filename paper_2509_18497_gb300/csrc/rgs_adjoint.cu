@@ -356,6 +356,121 @@ __global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const flo
     }
 }
 
+// Geometry gradients of the hemisphere-ray transport (Eqs. dl-dgeo-0/1), one thread per ray,
+// from every iterate B^(b), every v^(a) and the per-record g_h of the opacity backward:
+//  - compositing: each hit's alpha moves with q_h = u^2 + v^2 at the hit point on its
+//    source's plane, with dL/dalpha_h = T_h (g_h - R_h) (back to front, as k_opacity_rec);
+//    q_h moves with p_i, the ray direction and the source's centre, scales and frame;
+//  - directional effects: Y(R_i d) through X^(a)[c] = sum_h a_h Y(-d).B_{j_h}^(b)[c] and
+//    Y(-d) through every hit's source row;
+//  - the ray leaves p_i along d = c_x t^u_i + c_y t^v_i + c_z n_i with fixed c, so dL/dd
+//    goes to the receiver's frame, and R_i to its normal.
+// The receiver's terms are summed over the warp (nd is a multiple of 32, so a warp's rays
+// share their receiver) and added once per warp.
+template <int NC>
+__global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int C, int nb, size_t A,
+                                                 const float *__restrict__ V, const float *__restrict__ Bit,
+                                                 const float *__restrict__ gh, float *dp, float *ds, float *gF) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_rays = sc.n * rays.nd;
+    if (r - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps (n_rays % 32 == 0)
+    const int i = r / rays.nd;
+    const int cnt = rays.cnt[r];
+    const float3 o = f3(sc.P[i]), n = f3(sc.N4[i]), d = f3(rays.dir[r]);
+    float3 gpi = make_float3(0.f, 0.f, 0.f), gd = make_float3(0.f, 0.f, 0.f), t1 = make_float3(0.f, 0.f, 0.f);
+    if (cnt > 0 && nb > 0) {
+        const long long base = rays.off[r];
+        float Th[RGS_HMAX];
+        float T = 1.f;
+        for (int h = 0; h < cnt; ++h) {
+            const int j = __ldg(&rays.rec_ja[base + h]).x;
+            Th[h] = T;
+            T *= 1.f - alpha_of(sc, __ldg(&sc.P[j].w), stored_hit_G(sc, j, o, d));
+        }
+        float R = 0.f;
+        for (int h = cnt - 1; h >= 0; --h) {
+            const int j = __ldg(&rays.rec_ja[base + h]).x;
+            const float G = stored_hit_G(sc, j, o, d);
+            const float oj = __ldg(&sc.P[j].w);
+            const float al = alpha_of(sc, oj, G);
+            const float g = gh[base + h];
+            const float coef = Th[h] * (g - R) * dalpha_dq(sc, oj, G);
+            if (coef != 0.f) {
+                const float4 Nj = __ldg(&sc.N4[j]), Pj = __ldg(&sc.P[j]);
+                const float t = (Nj.x * (Pj.x - o.x) + Nj.y * (Pj.y - o.y) + Nj.z * (Pj.z - o.z)) /
+                                (Nj.x * d.x + Nj.y * d.y + Nj.z * d.z);
+                float uu, vv;
+                const float3 pw = crossing_pw(sc, j, o, d, t, uu, vv);
+                gpi = gpi + coef * pw;
+                gd = gd + (coef * t) * pw;
+                atomicAdd(&dp[3 * j], -coef * pw.x);
+                atomicAdd(&dp[3 * j + 1], -coef * pw.y);
+                atomicAdd(&dp[3 * j + 2], -coef * pw.z);
+                atomicAdd(&ds[2 * j], coef * (-2.f * uu * uu * __ldg(&sc.FU[j].w)));
+                atomicAdd(&ds[2 * j + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[j].w)));
+                occluder_frame_grad(sc, j, o, d, t, uu, vv, coef, gF);
+            }
+            R = al * g + (1.f - al) * R;
+        }
+        float Yo[NC], Yi[NC], wi[NC], wo[NC];
+        const float3 rd = reflect_n(n, d);
+        sh_eval<NC>(neg3(d), Yo);
+        sh_eval<NC>(rd, Yi);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) wi[k] = wo[k] = 0.f;
+        const float wa = alpha_center(sc, i) * (3.14159265358979f / (float)rays.nd);
+        for (int a = 0; a < nb; ++a) {
+            const float *va = V + A * a + (size_t)i * C * NC;
+            const float *Bb = Bit + A * (nb - 1 - a);
+            for (int c = 0; c < C; ++c) {
+                const int ch = c % 3;
+                float cv[NC], y = 0.f;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    cv[k] = wa * __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * __ldg(&va[c * NC + k]);
+                    y += cv[k] * Yi[k];
+                }
+                float X = 0.f;
+                for (int h = 0; h < cnt; ++h) {
+                    const int2 ja = __ldg(&rays.rec_ja[base + h]);
+                    const float ah = __int_as_float(ja.y);
+                    const float *row = Bb + ((size_t)ja.x * C + c) * NC;
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) {
+                        const float b = __ldg(&row[k]);
+                        s += Yo[k] * b;
+                        wo[k] += ah * y * b;
+                    }
+                    X += ah * s;
+                }
+#pragma unroll
+                for (int k = 0; k < NC; ++k) wi[k] += X * cv[k];
+            }
+        }
+        t1 = sh_grad_dot<NC>(rd, wi);
+        const float3 t3 = reflect_n(n, t1), t2 = sh_grad_dot<NC>(neg3(d), wo);
+        gd = gd + (t3 - t2);
+    }
+    const float3 tu = f3(sc.FU[i]), tv = f3(sc.FV[i]);
+    const float cx = dot3(d, tu), cy = dot3(d, tv), cz = dot3(d, n);
+    const float3 gn = reflect_grad_n(n, d, t1) + cz * gd;
+    float red[12] = {gpi.x, gpi.y, gpi.z, cx * gd.x, cx * gd.y, cx * gd.z, cy * gd.x, cy * gd.y, cy * gd.z,
+                     gn.x, gn.y, gn.z};
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) red[q] += __shfl_xor_sync(0xffffffffu, red[q], off);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (red[q] != 0.f) atomicAdd(&dp[3 * i + q], red[q]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            if (red[3 + q] != 0.f) atomicAdd(&gF[9 * (size_t)i + q], red[3 + q]);
+    }
+}
+
 template <int NC>
 __global__ void k_finalize(SceneDev sc, int C, const float *__restrict__ u, const float *__restrict__ P,
                            const float *__restrict__ kk, const float *__restrict__ dop_acc, float *dE, float *dad,
@@ -450,7 +565,8 @@ rgs_status opacity_group(rgs_transport *t, SceneDev sd, RaysDev rd, int na, cons
 // pooled scratch before the segment's v^(a) are formed and used.
 template <int NC>
 rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, float *dopo,
-                       const std::vector<int> &parts, const std::vector<long long> &part_base, cudaStream_t st) {
+                       const std::vector<int> &parts, const std::vector<long long> &part_base, cudaStream_t st,
+                       const RgsGeoAcc *geo) {
     const int n = t->n, C = t->C, nb = t->nb_last, s = t->stride;
     const size_t A = t->arr();
     const size_t A16 = (size_t)n * C * bf16_stride<NC>();
@@ -545,7 +661,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
             { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, vp(a), Qb[b - lo], t->Pg); }
             RGS_LAUNCH("pair accum");
         }
-        if (dopo) { // g_h over this segment's iterates, four per launch
+        if (dopo || geo) { // g_h over this segment's iterates, four per launch
             for (int b0 = hi; b0 >= lo; b0 -= 4) {
                 const int na = min(4, b0 - lo + 1);
                 const float *vv[4], *bb[4];
@@ -565,12 +681,17 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     if (nb >= 1 && (r = KT(nb)) != RGS_OK) return r; // v^(n) only adds to u
     if (t->nl > 0) {
         const int nth = n * t->nl;
-        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, C, t->u, t->Pg, t->dop, nullptr, nullptr, nullptr); }
+        { ProfScope ps_("k_shadow_bwd", st); k_shadow_bwd<NC><<<(nth + 127) / 128, 128, 0, st>>>(sd, t->nl, t->ldir, t->lpos, t->lint, C, t->u, t->Pg, t->dop, geo ? geo->dp : nullptr, geo ? geo->ds : nullptr, geo ? geo->gF : nullptr); }
         RGS_LAUNCH("shadow backward");
     }
     if (nb >= 1 && dopo) {
         { ProfScope ps_("k_opacity_rec", st); k_opacity_rec<<<gr, 256, 0, st>>>(sd, rd, t->gh, t->dop); }
         RGS_LAUNCH("hemisphere opacity backward");
+    }
+    if (nb >= 1 && geo) { // every iterate is kept (the caller checked the stride)
+        const long long n_rays = (long long)n * t->nd;
+        { ProfScope ps_("k_hemi_geo", st); k_hemi_geo<NC><<<(unsigned)((n_rays + 127) / 128), 128, 0, st>>>(sd, rd, C, nb, A, t->v, t->iters, t->gh, geo->dp, geo->ds, geo->gF); }
+        RGS_LAUNCH("hemisphere geometry backward");
     }
     { ProfScope ps_("k_finalize", st); k_finalize<NC><<<gn, 128, 0, st>>>(sd, C, t->u, t->Pg, t->sc->kk, t->dop, dE, dad, dopo); }
     RGS_LAUNCH("finalize");
@@ -639,8 +760,14 @@ rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad,
 }
 #undef RGS_NC_SWITCH
 
-rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st) {
-    if (t->kind == RGS_KIND_PAIRS) return rgs_adjoint_pairs_impl(t, g, dE, dad, dop, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st,
+                            float *dp, float *ds, float *dtu, float *dtv) {
+    if (t->kind == RGS_KIND_PAIRS) return rgs_adjoint_pairs_impl(t, g, dE, dad, dop, nullptr, dp, ds, dtu, dtv, st);
+    const bool want_geo = dp || ds || dtu || dtv;
+    if (want_geo && t->stride != 0) {
+        rgs_set_error("geometry gradients of the hemisphere transport need every iterate: solve with checkpointing off");
+        return RGS_ERR_STATE;
+    }
     rgs_status r;
     const int nb = t->nb_last, n = t->n;
     const size_t A = t->arr();
@@ -663,10 +790,24 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
             pool_release(t->dy, st);
             pool_release(t->dy_mc, st);
             pool_release(t->gh, st);
+            pool_release(geo.dp, st);
+            pool_release(geo.ds, st);
+            pool_release(geo.gF, st);
         }
-    } scratch{t, st};
+        RgsGeoAcc geo;
+    } scratch{t, st, {}};
     const bool mc = wide_adjoint(t->C);
-    const bool want_gh = dop && nb >= 1;
+    const bool want_gh = (dop || want_geo) && nb >= 1;
+    if (want_geo) {
+        RgsGeoAcc &geo = scratch.geo;
+        if ((r = pool_alloc(&geo.dp, (size_t)n * 3, st)) != RGS_OK) return r;
+        if ((r = pool_alloc(&geo.ds, (size_t)n * 2, st)) != RGS_OK) return r;
+        if ((r = pool_alloc(&geo.gF, (size_t)n * 9, st)) != RGS_OK) return r;
+        RGS_CUDA(cudaMemsetAsync(geo.dp, 0, sizeof(float) * n * 3, st));
+        RGS_CUDA(cudaMemsetAsync(geo.ds, 0, sizeof(float) * n * 2, st));
+        RGS_CUDA(cudaMemsetAsync(geo.gF, 0, sizeof(float) * n * 9, st));
+    }
+    const RgsGeoAcc *geop = want_geo ? &scratch.geo : nullptr;
     const int n_v = t->stride ? t->stride + 1 : nb + 1;
     if ((r = pool_alloc(&t->v, A * n_v, st)) != RGS_OK) return r;
     if ((r = pool_alloc(&t->u, A, st)) != RGS_OK) return r;
@@ -712,9 +853,11 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
     if ((r = pool_alloc(&t->tr, (size_t)std::max(biggest, 1ll), st)) != RGS_OK) return r;
     if (parts.size() == 2 && (r = build_index(t, 0, n, 0, st)) != RGS_OK) return r;
     switch (t->nc) {
-    case 1: return run_adjoint<1>(t, g, dE, dad, dop, parts, base, st);
-    case 4: return run_adjoint<4>(t, g, dE, dad, dop, parts, base, st);
-    case 9: return run_adjoint<9>(t, g, dE, dad, dop, parts, base, st);
-    default: return run_adjoint<16>(t, g, dE, dad, dop, parts, base, st);
+    case 1: r = run_adjoint<1>(t, g, dE, dad, dop, parts, base, st, geop); break;
+    case 4: r = run_adjoint<4>(t, g, dE, dad, dop, parts, base, st, geop); break;
+    case 9: r = run_adjoint<9>(t, g, dE, dad, dop, parts, base, st, geop); break;
+    default: r = run_adjoint<16>(t, g, dE, dad, dop, parts, base, st, geop);
     }
+    if (r != RGS_OK || !want_geo) return r;
+    return rgs_geometry_out(t, scratch.geo, dp, ds, dtu, dtv, st);
 }

@@ -409,6 +409,21 @@ rgs_status rgs_adjoint(rgs_transport *t, const float *dL_dB, float *dL_dE, float
     return rgs_adjoint_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, S(stream));
 }
 
+rgs_status rgs_adjoint_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
+                                float *dL_dopacity, float *dL_dp, float *dL_ds, float *dL_dtu, float *dL_dtv,
+                                void *stream) {
+    g_err[0] = 0;
+    if (!t || !dL_dB) {
+        rgs_set_error("rgs_adjoint_geometry: NULL argument");
+        return RGS_ERR_ARG;
+    }
+    if (t->nb_last < 0) {
+        rgs_set_error("rgs_adjoint_geometry: no rgs_solve on this transport since it was traced");
+        return RGS_ERR_STATE;
+    }
+    return rgs_adjoint_impl(t, dL_dB, dL_dE, dL_dalbedo, dL_dopacity, S(stream), dL_dp, dL_ds, dL_dtu, dL_dtv);
+}
+
 rgs_status rgs_solve_batched(rgs_transport *const *ts, int32_t count, const float *const *E,
                              const int32_t *n_bounces, const rgs_batch_opts *opts, float *const *B_out,
                              double *residual_norms, void *stream) {

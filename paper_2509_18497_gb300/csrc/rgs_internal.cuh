@@ -808,7 +808,16 @@ rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_b
 rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace_opts *o, cudaStream_t st);
 rgs_status rgs_solve_impl(rgs_transport *t, const float *E, int nb, int precision, float *B_out,
                           rgs_solve_stats *stats, cudaStream_t st);
-rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st);
+rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *dad, float *dop, cudaStream_t st,
+                            float *dp = nullptr, float *ds = nullptr, float *dtu = nullptr, float *dtv = nullptr);
+// internal-order accumulators of the geometry gradients: dL/dp [n][3], dL/ds [n][2] and the
+// orthonormal frame's (dL/dt^u, dL/dt^v, dL/dn) [n][9]
+struct RgsGeoAcc {
+    float *dp = nullptr, *ds = nullptr, *gF = nullptr;
+};
+// the accumulators back to the caller's order, the frame's through Gram-Schmidt (Eq. G)
+rgs_status rgs_geometry_out(rgs_transport *t, const RgsGeoAcc &acc, float *dp, float *ds, float *dtu, float *dtv,
+                            cudaStream_t st);
 rgs_status rgs_get_iterate_impl(rgs_transport *t, int b, float *out, cudaStream_t st);
 rgs_status rgs_solve_prepare(rgs_transport *t, int nb, int precision, int stride, cudaStream_t st);
 // B^(b) for b in (c, e] from the stored checkpoint or iterate B^(c), with Q^(b-1); outputs are

@@ -344,11 +344,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int
             gn = gn + reflect_grad_n(ni, d, f * t1);
         }
     }
-    if constexpr (GEO) {
-        if (gn.x != 0.f || gn.y != 0.f || gn.z != 0.f) {
-            atomicAdd(&gF[9 * (size_t)i + 6], gn.x);
-            atomicAdd(&gF[9 * (size_t)i + 7], gn.y);
-            atomicAdd(&gF[9 * (size_t)i + 8], gn.z);
+    if constexpr (GEO) { // every thread of the block has receiver i: one atomic per warp
+        float red[3] = {gn.x, gn.y, gn.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) red[q] += __shfl_xor_sync(0xffffffffu, red[q], off);
+            if ((threadIdx.x & 31) == 0 && red[q] != 0.f) atomicAdd(&gF[9 * (size_t)i + 6 + q], red[q]);
         }
     }
 }
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int
 // V = lambda_j A_j T geo through geo = (n_i.d)|n_j.d|/r^2, through A_j (proportional to
 // s^u_j s^v_j) and through every occluder's crossing point and scales, plus the directional
 // part gq from k_pair_g; d = (p_j - p_i)/r moves with (I - d d^T)/r (dp_j - dp_i).
+template <bool GEO>
 __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunks, const long long *__restrict__ chunk_off,
                                                    const float *__restrict__ lam, const float *__restrict__ aarea,
                                                    const float *__restrict__ daarea, const float *__restrict__ gpair,
@@ -382,87 +385,102 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     __syncthreads();
     int base = 0;
     for (int w = 0; w < warp; ++w) base += warp_base[w];
-    if (!front) return;
-    const long long e = chunk_off[blk] + base + __popc(bal & ((1u << lane) - 1u));
-    const float g = gpair[e];
-    const float4 gs = dp ? gq[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g == 0.f && gs.x == 0.f && gs.y == 0.f && gs.z == 0.f) return;
-    float r;
-    const float3 d = unit_dir(dv, r);
-    const float3 pj = f3(sc.P[j]), nj = f3(sc.N4[j]);
-    const float Aj = __ldg(&aarea[j]), dAj = __ldg(&daarea[j]), lj = __ldg(&lam[j]);
-    const float nid = dot3(ni, d), njd = dot3(nj, d);
-    const float geo = fabsf(nid) * fabsf(njd) / (r * r);
-    float Tnz = 1.f;
-    int nzero = 0;
-    auto pass1 = [&](int k) {
-        float gk, tk;
-        if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk, tk)) return;
-        const float om = 1.f - alpha_of(sc, __ldg(&sc.P[k].w), gk);
-        if (om == 0.f) ++nzero;
-        else Tnz *= om;
-    };
-    if (!bvh_traverse(sc, pi, d, r, pass1)) atomicAdd(&flags[FLAG_STACK], 1);
-    const float T = nzero ? 0.f : Tnz;
-    if (dlam) atomicAdd(&dlam[j], g * Aj * T * geo);
-    if (dop && T != 0.f) atomicAdd(&dop[j], g * lj * dAj * T * geo);
-    float3 gd = make_float3(gs.x, gs.y, gs.z), gpi = make_float3(0.f, 0.f, 0.f);
-    float gr = 0.f;
-    if (dp) {
-        const float f = g * lj * Aj * T / (r * r), sj = njd >= 0.f ? 1.f : -1.f;
-        gd = gd + f * (fabsf(njd) * ni + (fabsf(nid) * sj) * nj);
-        gr = g * lj * Aj * T * (-2.f * geo / r);
-        const float fs = g * lj * T * geo * Aj;
-        atomicAdd(&ds[2 * j], fs * __ldg(&sc.FU[j].w));
-        atomicAdd(&ds[2 * j + 1], fs * __ldg(&sc.FV[j].w));
-        // normals through geo: d geo/d n_i = |n_j.d| d / r^2, d geo/d n_j = (n_i.d) sgn(n_j.d) d / r^2
-        const float fi = f * fabsf(njd), fj = f * fabsf(nid) * sj;
-        atomicAdd(&gF[9 * (size_t)i + 6], fi * d.x);
-        atomicAdd(&gF[9 * (size_t)i + 7], fi * d.y);
-        atomicAdd(&gF[9 * (size_t)i + 8], fi * d.z);
-        atomicAdd(&gF[9 * (size_t)j + 6], fj * d.x);
-        atomicAdd(&gF[9 * (size_t)j + 7], fj * d.y);
-        atomicAdd(&gF[9 * (size_t)j + 8], fj * d.z);
-    }
-    if ((dop || dp) && nzero <= 1 && g != 0.f) {
-        const float q = -g * lj * Aj * geo;
-        auto pass2 = [&](int k) {
+    // the receiver's own position and normal terms are summed over the warp (all 32 lanes
+    // share receiver i) and added once per warp
+    float3 dpi = make_float3(0.f, 0.f, 0.f), gni = make_float3(0.f, 0.f, 0.f);
+    auto body = [&]() {
+        if (!front) return;
+        const long long e = chunk_off[blk] + base + __popc(bal & ((1u << lane) - 1u));
+        const float g = gpair[e];
+        const float4 gs = GEO ? gq[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g == 0.f && gs.x == 0.f && gs.y == 0.f && gs.z == 0.f) return;
+        float r;
+        const float3 d = unit_dir(dv, r);
+        const float3 pj = f3(sc.P[j]), nj = f3(sc.N4[j]);
+        const float Aj = __ldg(&aarea[j]), dAj = __ldg(&daarea[j]), lj = __ldg(&lam[j]);
+        const float nid = dot3(ni, d), njd = dot3(nj, d);
+        const float geo = fabsf(nid) * fabsf(njd) / (r * r);
+        float Tnz = 1.f;
+        int nzero = 0;
+        auto pass1 = [&](int k) {
             float gk, tk;
             if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk, tk)) return;
-            const float ok = __ldg(&sc.P[k].w);
-            const float om = 1.f - alpha_of(sc, ok, gk);
-            float others;
-            if (nzero == 0) others = Tnz / om;
-            else others = (om == 0.f) ? Tnz : 0.f;
-            if (others == 0.f) return;
-            if (dop) atomicAdd(&dop[k], q * others * dalpha_do(sc, ok, gk));
-            if (dp) {
-                const float coef = q * others * dalpha_dq(sc, ok, gk);
-                if (coef == 0.f) return;
-                float uu, vv;
-                const float3 pw = crossing_pw(sc, k, pi, d, tk, uu, vv);
-                gpi = gpi + coef * pw;
-                gd = gd + (coef * tk) * pw;
-                atomicAdd(&dp[3 * k], -coef * pw.x);
-                atomicAdd(&dp[3 * k + 1], -coef * pw.y);
-                atomicAdd(&dp[3 * k + 2], -coef * pw.z);
-                atomicAdd(&ds[2 * k], coef * (-2.f * uu * uu * __ldg(&sc.FU[k].w)));
-                atomicAdd(&ds[2 * k + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[k].w)));
-                occluder_frame_grad(sc, k, pi, d, tk, uu, vv, coef, gF);
-            }
+            const float om = 1.f - alpha_of(sc, __ldg(&sc.P[k].w), gk);
+            if (om == 0.f) ++nzero;
+            else Tnz *= om;
         };
-        bvh_traverse(sc, pi, d, r, pass2);
-    }
-    if (dp) {
-        const float dd = dot3(d, gd);
-        const float3 gp = make_float3((gd.x - d.x * dd) / r + d.x * gr, (gd.y - d.y * dd) / r + d.y * gr,
-                                      (gd.z - d.z * dd) / r + d.z * gr);
-        atomicAdd(&dp[3 * j], gp.x);
-        atomicAdd(&dp[3 * j + 1], gp.y);
-        atomicAdd(&dp[3 * j + 2], gp.z);
-        atomicAdd(&dp[3 * i], gpi.x - gp.x);
-        atomicAdd(&dp[3 * i + 1], gpi.y - gp.y);
-        atomicAdd(&dp[3 * i + 2], gpi.z - gp.z);
+        if (!bvh_traverse(sc, pi, d, r, pass1)) atomicAdd(&flags[FLAG_STACK], 1);
+        const float T = nzero ? 0.f : Tnz;
+        if (dlam) atomicAdd(&dlam[j], g * Aj * T * geo);
+        if (dop && T != 0.f) atomicAdd(&dop[j], g * lj * dAj * T * geo);
+        float3 gd = make_float3(gs.x, gs.y, gs.z), gpi = make_float3(0.f, 0.f, 0.f);
+        float gr = 0.f;
+        if constexpr (GEO) {
+            const float f = g * lj * Aj * T / (r * r), sj = njd >= 0.f ? 1.f : -1.f;
+            gd = gd + f * (fabsf(njd) * ni + (fabsf(nid) * sj) * nj);
+            gr = g * lj * Aj * T * (-2.f * geo / r);
+            const float fs = g * lj * T * geo * Aj;
+            atomicAdd(&ds[2 * j], fs * __ldg(&sc.FU[j].w));
+            atomicAdd(&ds[2 * j + 1], fs * __ldg(&sc.FV[j].w));
+            // normals through geo: d geo/d n_i = |n_j.d| d / r^2, d geo/d n_j = (n_i.d) sgn(n_j.d) d / r^2
+            const float fi = f * fabsf(njd), fj = f * fabsf(nid) * sj;
+            gni = gni + fi * d;
+            atomicAdd(&gF[9 * (size_t)j + 6], fj * d.x);
+            atomicAdd(&gF[9 * (size_t)j + 7], fj * d.y);
+            atomicAdd(&gF[9 * (size_t)j + 8], fj * d.z);
+        }
+        if ((dop || GEO) && nzero <= 1 && g != 0.f) {
+            const float q = -g * lj * Aj * geo;
+            auto pass2 = [&](int k) {
+                float gk, tk;
+                if (!pair_occluder(sc, k, i, j, pi, d, r, pj, eps, gk, tk)) return;
+                const float ok = __ldg(&sc.P[k].w);
+                const float om = 1.f - alpha_of(sc, ok, gk);
+                float others;
+                if (nzero == 0) others = Tnz / om;
+                else others = (om == 0.f) ? Tnz : 0.f;
+                if (others == 0.f) return;
+                if (dop) atomicAdd(&dop[k], q * others * dalpha_do(sc, ok, gk));
+                if constexpr (GEO) {
+                    const float coef = q * others * dalpha_dq(sc, ok, gk);
+                    if (coef == 0.f) return;
+                    float uu, vv;
+                    const float3 pw = crossing_pw(sc, k, pi, d, tk, uu, vv);
+                    gpi = gpi + coef * pw;
+                    gd = gd + (coef * tk) * pw;
+                    atomicAdd(&dp[3 * k], -coef * pw.x);
+                    atomicAdd(&dp[3 * k + 1], -coef * pw.y);
+                    atomicAdd(&dp[3 * k + 2], -coef * pw.z);
+                    atomicAdd(&ds[2 * k], coef * (-2.f * uu * uu * __ldg(&sc.FU[k].w)));
+                    atomicAdd(&ds[2 * k + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[k].w)));
+                    occluder_frame_grad(sc, k, pi, d, tk, uu, vv, coef, gF);
+                }
+            };
+            bvh_traverse(sc, pi, d, r, pass2);
+        }
+        if constexpr (GEO) {
+            const float dd = dot3(d, gd);
+            const float3 gp = make_float3((gd.x - d.x * dd) / r + d.x * gr, (gd.y - d.y * dd) / r + d.y * gr,
+                                          (gd.z - d.z * dd) / r + d.z * gr);
+            atomicAdd(&dp[3 * j], gp.x);
+            atomicAdd(&dp[3 * j + 1], gp.y);
+            atomicAdd(&dp[3 * j + 2], gp.z);
+            dpi = gpi - gp;
+        }
+    };
+    body();
+    if constexpr (!GEO) return;
+    float red[6] = {dpi.x, dpi.y, dpi.z, gni.x, gni.y, gni.z};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) red[q] += __shfl_xor_sync(0xffffffffu, red[q], off);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (red[q] != 0.f) atomicAdd(&dp[3 * i + q], red[q]);
+            if (red[3 + q] != 0.f) atomicAdd(&gF[9 * (size_t)i + 6 + q], red[3 + q]);
+        }
     }
 }
 
@@ -604,8 +622,7 @@ template rgs_status pairs_bounce<16>(const rgs_transport *, bool, const float *,
                                      float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
 
 namespace {
-struct GeoAcc { // internal-order accumulators of the geometry gradients (all or none)
-    float *dp = nullptr, *ds = nullptr, *gF = nullptr;
+struct GeoAcc : RgsGeoAcc { // with the pairs' directional derivatives (all or none)
     float4 *gq = nullptr;
 };
 
@@ -632,7 +649,13 @@ rgs_status run_adjoint_pairs(rgs_transport *t, const float *g, float *dE, float 
             ProfScope ps_("k_pair_g", st);
             k_pair_g<NC, false><<<n, PAIR_THREADS, 0, st>>>(sd, C, nb, t->pair_off, t->pair_rec, A, t->v, t->iters, t->gh, nullptr, nullptr);
         }
-        { ProfScope ps_("k_pair_grad", st); k_pair_grad<<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, geo.gq, dopo ? t->dop : nullptr, dlam_acc, geo.dp, geo.ds, geo.gF, t->flags); }
+        if (geo.dp) {
+            ProfScope ps_("k_pair_grad", st);
+            k_pair_grad<true><<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, geo.gq, dopo ? t->dop : nullptr, dlam_acc, geo.dp, geo.ds, geo.gF, t->flags);
+        } else {
+            ProfScope ps_("k_pair_grad", st);
+            k_pair_grad<false><<<(unsigned)((long long)n * chunks), PCH, 0, st>>>(sd, n, chunks, t->chunk_off, t->lam, t->aarea, t->daarea, t->gh, nullptr, dopo ? t->dop : nullptr, dlam_acc, nullptr, nullptr, nullptr, t->flags);
+        }
         RGS_LAUNCH("pair backward");
     }
     return rgs_adjoint_finalize(t, NC, dE, dad, dopo, st);
@@ -702,9 +725,14 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
         { ProfScope ps_("k_lam_out", st); k_lam_out<<<(n + 255) / 256, 256, 0, st>>>(n, t->sc->uid, dlam_acc, dlam); }
         RGS_LAUNCH("lambda gradient");
     }
-    if (want_geo) {
-        { ProfScope ps_("k_geo_out", st); k_geo_out<<<(n + 255) / 256, 256, 0, st>>>(t->sc->dev(), t->sc->GS, n, t->sc->uid, geo.dp, geo.ds, geo.gF, dp, ds, dtu, dtv); }
-        RGS_LAUNCH("geometry gradients");
-    }
+    if (want_geo) return rgs_geometry_out(t, geo, dp, ds, dtu, dtv, st);
+    return RGS_OK;
+}
+
+rgs_status rgs_geometry_out(rgs_transport *t, const RgsGeoAcc &acc, float *dp, float *ds, float *dtu, float *dtv,
+                            cudaStream_t st) {
+    const int n = t->n;
+    { ProfScope ps_("k_geo_out", st); k_geo_out<<<(n + 255) / 256, 256, 0, st>>>(t->sc->dev(), t->sc->GS, n, t->sc->uid, acc.dp, acc.ds, acc.gF, dp, ds, dtu, dtv); }
+    RGS_LAUNCH("geometry gradients");
     return RGS_OK;
 }

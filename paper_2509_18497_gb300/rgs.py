@@ -30,7 +30,7 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
            "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_trace_pairs",
-           "rgs_adjoint_pairs", "rgs_adjoint_pairs_geometry")
+           "rgs_adjoint_pairs", "rgs_adjoint_pairs_geometry", "rgs_adjoint_geometry")
 
 
 class RgsError(RuntimeError):
@@ -127,6 +127,8 @@ def load(path=LIB_PATH):
     L.rgs_adjoint_pairs.restype = ct.c_int
     L.rgs_adjoint_pairs_geometry.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rgs_adjoint_pairs_geometry.restype = ct.c_int
+    L.rgs_adjoint_geometry.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rgs_adjoint_geometry.restype = ct.c_int
     L.rgs_set_memory_budget.argtypes = [vp, ct.c_int64]
     L.rgs_set_memory_budget.restype = ct.c_int
     L.rgs_trim_workspace.argtypes = []
@@ -285,6 +287,19 @@ def rgs_adjoint_pairs_geometry(transport, dL_dB, stream=None):
                                         _dev(ds, (n, 2), "dL_ds"), _dev(dtu, (n, 3), "dL_dtu"),
                                         _dev(dtv, (n, 3), "dL_dtv"), _stream(stream)))
     return dE, dad, dop, dlam, dp, ds, dtu, dtv
+
+
+def rgs_adjoint_geometry(transport, dL_dB, stream=None):
+    """rgs_adjoint_geometry: returns (dL/dE, dL/da^d, dL/do, dL/dp, dL/ds, dL/dtu, dL/dtv)."""
+    L = load()
+    n, nc, C = transport.n, transport.nc, transport.C
+    f = lambda *shape: torch.empty(shape, device="cuda", dtype=torch.float32)
+    dE, dad, dop, dp, ds, dtu, dtv = f(n, nc, 3), f(n, 3), f(n), f(n, 3), f(n, 2), f(n, 3), f(n, 3)
+    _check(L.rgs_adjoint_geometry(transport.h, _dev(dL_dB, (n, nc, C), "dL_dB"), _dev(dE, (n, nc, 3), "dL_dE"),
+                                  _dev(dad, (n, 3), "dL_dalbedo"), _dev(dop, (n,), "dL_dopacity"),
+                                  _dev(dp, (n, 3), "dL_dp"), _dev(ds, (n, 2), "dL_ds"), _dev(dtu, (n, 3), "dL_dtu"),
+                                  _dev(dtv, (n, 3), "dL_dtv"), _stream(stream)))
+    return dE, dad, dop, dp, ds, dtu, dtv
 
 
 def rgs_solve(transport, E, n_bounces, B_out=None, stats=False, precision=RGS_FP32, stream=None):

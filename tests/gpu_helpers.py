@@ -35,6 +35,10 @@ def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=F
         elif pairs:
             dE, dad, dop, dlam = pipe.adjoint_pairs(g)
             out["dlam"] = dlam.double().cpu().numpy()
+        elif geometry:
+            dE, dad, dop, dp, ds, dtu, dtv = pipe.adjoint_geometry(g)
+            out.update(dp=dp.double().cpu().numpy(), ds=ds.double().cpu().numpy(),
+                       dtu=dtu.double().cpu().numpy(), dtv=dtv.double().cpu().numpy())
         else:
             dE, dad, dop = pipe.adjoint(g)
         out.update(dE=dE.double().cpu().numpy(), dad=dad.double().cpu().numpy(), dop=dop.double().cpu().numpy())
