@@ -6,7 +6,8 @@
  * The library computes, on one GPU, the outgoing radiance of every surfel held as
  * spherical-harmonic (SH) coefficients per RGB channel, under point lights, with
  * global illumination, and the gradients of a loss with respect to the surfels'
- * emission, diffuse albedo and opacity:
+ * emission, diffuse albedo and opacity, and (rgs_adjoint_geometry) their centres, scales
+ * and frames:
  *
  *   rgs_build_scene      surfel frames, BRDF coefficients, Morton order, BVH  (Eq. G, Eq. brdf, App. A)
  *   rgs_trace_transport  hemisphere rays with alpha compositing (Eq. L_I, App. B) and the
@@ -15,10 +16,12 @@
  *                        direct term first, then a fixed number of bounces)
  *   rgs_adjoint          transposed bounces and parameter gradients (Eq. final_dL_dE,
  *                        Eq. final-dl-dbrdf, Eq. dl-dgeo-0 restricted to opacity)
+ *   rgs_adjoint_geometry the same with the geometry gradients of Eqs. dl-dgeo-0/1
+ *                        (centres, scales, frames) for either transport
  *   rgs_trace_pairs      the center-to-center approximation (Sec. 8) in place of the
  *                        hemisphere rays, and rgs_adjoint_pairs with its lambda gradient
- *                        (rgs_adjoint_pairs_geometry: with the position and scale
- *                        gradients of Eqs. dl-dgeo-0/1 as well)
+ *                        (rgs_adjoint_pairs_geometry: with the position, scale and
+ *                        frame gradients of Eqs. dl-dgeo-0/1 as well)
  *
  * CONVENTIONS (all entry points)
  *  - Every pointer documented "device" must point to memory of the current CUDA device;
