@@ -477,6 +477,15 @@ def main():
                 "algorithmic_bytes": alg_step / launches_dom if alg_step else None,
                 "avg_launch_ms": ms_dom_step / launches_dom, "peak_source": peak_kind}
 
+    # the hemisphere trace on its own (rays per second of the live trace launches), and the
+    # fraction of the step it takes
+    trace = None
+    if "k_trace_hemi" in prof:
+        ms_tr = prof["k_trace_hemi"][1] / args.steps
+        rays = sum(x["n"] * x["nd"] for x in infos)
+        trace = {"rays_per_s": rays / (ms_tr * 1e-3), "ms_per_step": ms_tr, "rays": rays,
+                 "hit_records": sum(x["n_hits"] for x in infos), "share": ms_tr / (tot_ms / args.steps)}
+
     cb = None
     if not args.no_cpu_baseline and world == 1:
         cb, _ = cpu_baseline(args.cpu_sample)
@@ -504,7 +513,7 @@ def main():
                                  "plain_ms_per_step": sum(step_ms_p) / args.steps,
                                  "batched_ms_per_step": sum(step_ms_b) / args.steps,
                                  "batched_launch": batched_launch},
-            "roofline": roofline, "cpu_baseline": cb,
+            "roofline": roofline, "trace": trace, "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clk, "wall_s_timed": t_wall, "kernels": kernels}
     print(json.dumps(line))
