@@ -1886,3 +1886,206 @@ int or_geometry_grad(const or_scene *s, const double *E, int nb, const double *g
     free(u);
     return 0;
 }
+
+/* ------------------------------------------------------------------ Monte-Carlo solver
+ * Sec. 7 ("Monte-Carlo Solver", Alg. 1) with the next-event estimation of Sec. 7 and the
+ * variance-driven receiver selection of App. "Monte-Carlo Solver Details", on the
+ * center-to-center transport (the paper's pair form, Eq. one-point-estimator):
+ *   step t = 1..T: receivers a_1..a_N (all kernels for t <= 8, else N draws with
+ *   replacement with probability proportional to each kernel's tracked variance); for
+ *   each, one source b drawn from the receiver's pairs by weighted reservoir sampling with
+ *   p_b proportional to the proxy (no BRDF, no transmittance)
+ *       w_b = geo_ab (lum(|Y(-d)^T Bhat_b|) + floor),  geo = |n_a.w||n_b.w|/r^2,
+ *   and the estimate delta = S_a + (1/p_b) K_ab Bhat_b, with K_ab the pair's transport
+ *   (o_a c_a (x) Y(R_a d) V_ba Y(-d)^T, as in the deterministic bounce) and Bhat_b = the
+ *   running mean of b's estimates (0 before its first one).  Every estimate of a step uses
+ *   the means of the previous step; then S_a += delta, S2_a += delta^2, D_a += 1 (TD(0)
+ *   with the 1/(t+1) learning rate is this running mean).  B = S / D.
+ * Readings (listed in the design notes): S = E + D (the direct term plays the emission:
+ * the hybrid solver's light shooting); lum = 0.2126 R + 0.7152 G + 0.0722 B of the
+ * per-channel magnitudes, summed over the lights; floor = 1e-9 (1 + mean lum of Bhat), so
+ * that p_b > 0 wherever V_ba can be (the proxy of a source whose estimate is 0 would
+ * otherwise vanish while its true contribution need not: at t = 1 every Bhat is 0); the
+ * tracked variance is sum over coefficients of S2/D - (S/D)^2 plus 1e-30; random numbers
+ * are SplitMix64 outputs keyed by (seed, t, draw, stream).  K-means grouping of the
+ * sources (a two-level proposal) changes only the proposal, not the estimator, and is not
+ * part of this oracle. */
+static double mc_u(uint64_t seed, uint64_t t, uint64_t q, uint64_t stream) {
+    uint64_t k = or_splitmix64(or_splitmix64(or_splitmix64(seed) + t) + q) + stream;
+    return (double)(or_splitmix64(k) >> 11) * (1.0 / 9007199254740992.0); /* [0, 1), 53 bits */
+}
+
+static const double MC_LUM[3] = {0.2126, 0.7152, 0.0722};
+
+/* proxy weights of receiver a's pairs from the means Bhat; returns their sum */
+static double mc_weights(const or_scene *s, const double *Bhat, double floor, int a, double *w) {
+    int nc = s->nc, C = s->C, L = s->L;
+    double Yo[1024], tot = 0.0;
+    for (long e = s->pair_off[a]; e < s->pair_off[a + 1]; ++e) {
+        double d[3], md[3];
+        pair_dir(s, a, s->pair_j[e], d);
+        for (int q = 0; q < 3; ++q) md[q] = -d[q];
+        or_sh_eval(L, md, Yo);
+        const double *Bb = Bhat + (size_t)s->pair_j[e] * nc * C;
+        double lum = 0.0;
+        for (int c = 0; c < C; ++c) {
+            double sv = 0.0;
+            for (int k = 0; k < nc; ++k) sv += Yo[k] * Bb[k * C + c];
+            lum += MC_LUM[c % 3] * fabs(sv);
+        }
+        w[e - s->pair_off[a]] = s->pair_geo[e] * (lum + floor);
+        tot += w[e - s->pair_off[a]];
+    }
+    return tot;
+}
+
+/* delta = S_a + (1/p) K_ab Bhat_b for pair e of receiver a (p = 0: no source, delta = S_a) */
+static void mc_estimate(const or_scene *s, const double *S, const double *Bhat, int a, long e, double p,
+                        double *delta) {
+    int nc = s->nc, C = s->C, L = s->L;
+    memcpy(delta, S + (size_t)a * nc * C, sizeof(double) * nc * C);
+    if (!(p > 0.0)) return;
+    double d[3], md[3], rd[3], Yo[1024], Yi[1024];
+    pair_dir(s, a, s->pair_j[e], d);
+    for (int q = 0; q < 3; ++q) md[q] = -d[q];
+    reflect(s->nrm + a * 3, d, rd);
+    or_sh_eval(L, md, Yo);
+    or_sh_eval(L, rd, Yi);
+    const double *Bb = Bhat + (size_t)s->pair_j[e] * nc * C;
+    for (int c = 0; c < C; ++c) {
+        double sv = 0.0;
+        for (int k = 0; k < nc; ++k) sv += Yo[k] * Bb[k * C + c];
+        for (int k = 0; k < nc; ++k)
+            delta[k * C + c] += alpha_c(s, a) * s->c[((size_t)a * (L + 1) + band_of(k)) * 3 + c % 3] * Yi[k] *
+                                s->pair_V[e] * sv / p;
+    }
+}
+
+/* single-item weighted reservoir sampling (Chao): stream the np weights once, keeping
+ * candidate k with probability w_k / (running sum); returns the kept index (-1 if none) */
+static long mc_reservoir(const double *w, long np, uint64_t seed, int t, int q) {
+    long pick = -1;
+    double W = 0.0;
+    for (long k = 0; k < np; ++k) {
+        if (!(w[k] > 0.0)) continue;
+        W += w[k];
+        if (mc_u(seed, (uint64_t)t, (uint64_t)q, 1000 + (uint64_t)k) * W < w[k]) pick = k;
+    }
+    return pick;
+}
+
+static double mc_floor(const or_scene *s, const double *Bhat) {
+    size_t M = (size_t)s->n * s->nc * s->C;
+    double acc = 0.0;
+    for (size_t q = 0; q < M; ++q) acc += MC_LUM[(q % s->C) % 3] * fabs(Bhat[q]);
+    return 1e-9 * (1.0 + acc / (double)s->n);
+}
+
+/* The proposal of receiver a under the means Bhat, for tests: w [pairs of a] (unnormalised)
+ * and the floor used.  Returns the number of pairs of a, or -1 without pairs. */
+long or_mc_weights(const or_scene *s, const double *Bhat, int a, double *w, double *floor_out) {
+    if (!s->pmode) return -1;
+    const double fl = mc_floor(s, Bhat);
+    if (floor_out) *floor_out = fl;
+    mc_weights(s, Bhat, fl, a, w);
+    return s->pair_off[a + 1] - s->pair_off[a];
+}
+
+/* One estimate for tests: the pair (index within a's pairs) that weighted reservoir
+ * sampling picks with the uniforms of (seed, t, q), its probability, and delta. */
+long or_mc_pick(const or_scene *s, const double *E, const double *Bhat, uint64_t seed, int t, int q, int a,
+                double *p_out, double *delta) {
+    if (!s->pmode) return -1;
+    size_t M = (size_t)s->n * s->nc * s->C;
+    double *S = dup_arr(NULL, M);
+    make_S(s, E, S);
+    const long np = s->pair_off[a + 1] - s->pair_off[a];
+    double *w = dup_arr(NULL, (size_t)(np > 0 ? np : 1));
+    const double tot = mc_weights(s, Bhat, mc_floor(s, Bhat), a, w);
+    const long pick = mc_reservoir(w, np, seed, t, q);
+    const double p = pick >= 0 ? w[pick] / tot : 0.0;
+    if (p_out) *p_out = p;
+    if (delta) mc_estimate(s, S, Bhat, a, pick >= 0 ? s->pair_off[a] + pick : 0, p, delta);
+    free(w);
+    free(S);
+    return pick;
+}
+
+/* Alg. 1: T steps, N estimates per step; B receives S^B / D, visits (optional) D. */
+int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, double *B, double *visits) {
+    if (!s->pmode) return -1;
+    int n = s->n, nc = s->nc, C = s->C;
+    size_t M = (size_t)n * nc * C, R = (size_t)nc * C;
+    double *S = dup_arr(NULL, M), *SB = dup_arr(NULL, M), *SB2 = dup_arr(NULL, M), *Bhat = dup_arr(NULL, M);
+    double *D = dup_arr(NULL, n), *var = dup_arr(NULL, n), *delta = dup_arr(NULL, (size_t)n * R);
+    int *recv = (int *)malloc(sizeof(int) * n);
+    make_S(s, E, S);
+    memset(SB, 0, sizeof(double) * M);
+    memset(SB2, 0, sizeof(double) * M);
+    memset(Bhat, 0, sizeof(double) * M);
+    memset(D, 0, sizeof(double) * n);
+    for (int t = 1; t <= T; ++t) {
+        /* receivers: every kernel for t <= 8, else N draws with replacement by tracked variance */
+        if (t <= 8) {
+            for (int q = 0; q < n; ++q) recv[q] = q;
+        } else {
+            double tot = 0.0;
+            for (int i = 0; i < n; ++i) {
+                double v = 0.0;
+                for (size_t k = 0; k < R; ++k) {
+                    const double m = SB[i * R + k] / D[i];
+                    v += SB2[i * R + k] / D[i] - m * m;
+                }
+                var[i] = (v > 0.0 ? v : 0.0) + 1e-30;
+                tot += var[i];
+            }
+            for (int q = 0; q < n; ++q) {
+                const double u = mc_u(seed, (uint64_t)t, (uint64_t)q, 0) * tot;
+                double acc = 0.0;
+                int a = n - 1;
+                for (int i = 0; i < n; ++i) {
+                    acc += var[i];
+                    if (u < acc) {
+                        a = i;
+                        break;
+                    }
+                }
+                recv[q] = a;
+            }
+        }
+        const double fl = mc_floor(s, Bhat);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int q = 0; q < n; ++q) {
+            const int a = recv[q];
+            const long np = s->pair_off[a + 1] - s->pair_off[a];
+            double *w = (double *)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
+            const double tot = mc_weights(s, Bhat, fl, a, w);
+            const long pick = mc_reservoir(w, np, seed, t, q);
+            const double p = pick >= 0 ? w[pick] / tot : 0.0;
+            mc_estimate(s, S, Bhat, a, pick >= 0 ? s->pair_off[a] + pick : 0, p, delta + (size_t)q * R);
+            free(w);
+        }
+        for (int q = 0; q < n; ++q) {
+            const int a = recv[q];
+            for (size_t k = 0; k < R; ++k) {
+                SB[a * R + k] += delta[q * R + k];
+                SB2[a * R + k] += delta[q * R + k] * delta[q * R + k];
+            }
+            D[a] += 1.0;
+        }
+        for (int i = 0; i < n; ++i)
+            if (D[i] > 0.0)
+                for (size_t k = 0; k < R; ++k) Bhat[i * R + k] = SB[i * R + k] / D[i];
+    }
+    memcpy(B, Bhat, sizeof(double) * M);
+    if (visits) memcpy(visits, D, sizeof(double) * n);
+    free(S);
+    free(SB);
+    free(SB2);
+    free(Bhat);
+    free(D);
+    free(var);
+    free(delta);
+    free(recv);
+    return 0;
+}

@@ -1,0 +1,134 @@
+"""Pins of the oracle's Monte-Carlo solver (Sec. 7, Alg. 1; App. "Monte-Carlo Solver
+Details") on the center-to-center transport: the one-point estimator is unbiased for the
+deterministic bounce, weighted reservoir sampling draws from the proposal, the TD(0)
+running mean follows its recursion, the variance-driven selection leaves deterministic
+kernels alone, and the solver converges to the Neumann solution (no GPU)."""
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import oracle as O
+from paper_2509_18497_gb300 import scenes
+
+
+@pytest.fixture(scope="module")
+def cluster():
+    sc = scenes.with_emission(scenes.random_cluster(n=24, seed=2, L=2, nb=3, n_lights=1), seed=4)
+    return sc, O.Oracle(sc).pairs()
+
+
+def test_estimator_is_unbiased_for_the_bounce(cluster):
+    """sum over a receiver's pairs of p_b * (S_a + K_ab Bhat_b / p_b) = S_a + (K Bhat)_a
+    exactly, for any means Bhat (Eq. one-point-estimator)."""
+    sc, orc = cluster
+    Bhat = np.random.default_rng(0).normal(size=orc._shape())
+    S = orc.solve(E=sc["E"], nb=0)
+    KB = orc.apply_K(Bhat)[0]
+    off = orc.pair_list()["off"]
+    with_pairs = [a for a in range(sc["n"]) if off[a + 1] > off[a]]
+    for a in with_pairs[:4]:
+        w, _ = orc.mc_weights(Bhat, a)
+        assert len(w) == off[a + 1] - off[a] and np.all(w > 0)
+        seen = {}
+        for t in range(1, 20000):  # collect every pick's probability and estimate
+            k, pk, delta = orc.mc_pick(Bhat, 7, t, 0, a, E=sc["E"])
+            seen.setdefault(k, (pk, delta))
+            if len(seen) == len(w):
+                break
+        assert len(seen) == len(w)
+        for k, (pk, _) in seen.items():
+            assert pk == pytest.approx(w[k] / w.sum(), rel=1e-12)
+        expect = sum(pk * delta for pk, delta in seen.values())
+        ref = S[a] + KB[a]
+        assert np.linalg.norm(expect - ref) <= 1e-12 * np.linalg.norm(ref)
+    lonely = [a for a in range(sc["n"]) if off[a + 1] == off[a]]
+    for a in lonely[:2]:  # no source: no pick, and the estimate is S_a itself
+        k, pk, delta = orc.mc_pick(Bhat, 7, 1, 0, a, E=sc["E"])
+        assert k == -1 and pk == 0.0
+        np.testing.assert_allclose(delta, S[a], rtol=1e-15)
+
+
+def test_reservoir_sampling_draws_from_the_proposal(cluster):
+    sc, orc = cluster
+    Bhat = np.random.default_rng(1).normal(size=orc._shape())
+    a = 5
+    w, _ = orc.mc_weights(Bhat, a)
+    p = w / w.sum()
+    draws = 20000
+    cnt = np.zeros(len(w))
+    for t in range(draws):
+        k, _, _ = orc.mc_pick(Bhat, 11, t, 3, a)
+        cnt[k] += 1
+    chi2 = ((cnt - draws * p) ** 2 / (draws * p)).sum()
+    assert chi2 < stats.chi2.ppf(0.999, len(w) - 1)
+
+
+def test_proposal_follows_emission_and_geometry(cluster):
+    """w_b = geo_ab (lum(|Y(-d)^T Bhat_b|) + floor): with Bhat = 0 the proposal is the
+    geometric term alone (floor 1e-9), and scaling one source's mean raises its weight."""
+    sc, orc = cluster
+    Z = np.zeros(orc._shape())
+    w0, fl = orc.mc_weights(Z, 5)
+    assert fl == pytest.approx(1e-9)
+    pl = orc.pair_list()
+    off = pl["off"]
+    js = pl["j"][off[5]:off[6]]
+    geo = w0 / fl
+    assert np.all(geo > 0)
+    B1 = Z.copy()
+    B1[js[0], 0, :] = 1.0  # the DC band of one source
+    w1, _ = orc.mc_weights(B1, 5)
+    assert w1[0] > w0[0] * 1e6 and np.allclose(w1[1:] / w0[1:], w1[1] / w0[1])
+
+
+def test_td0_running_mean_recursion():
+    """Two facing surfels, each the other's only source (p = 1): the first 8 steps visit
+    every kernel, so B^(t) = (1/t) sum_{s<=t} (S + K B^(s-1)) with B^(0) = 0."""
+    sc = scenes.with_emission(scenes.random_cluster(n=2, seed=0, L=2, nb=1, n_lights=1), seed=1)
+    sc["p"] = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.4]])
+    sc["tu"] = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    sc["tv"] = np.array([[0.0, 1.0, 0.0], [0.0, -1.0, 0.0]])  # n = +z and -z: facing
+    sc["light_pos"] = np.array([[0.3, 0.2, 0.2]])
+    orc = O.Oracle(sc).pairs()
+    assert list(orc.pair_list()["off"]) == [0, 1, 2]
+    S = orc.solve(E=sc["E"], nb=0)
+    mean, acc = np.zeros(orc._shape()), np.zeros(orc._shape())
+    for t in range(1, 9):
+        acc += S + orc.apply_K(mean)[0]
+        mean = acc / t
+        B, D = orc.mc_solve(t, seed=5, E=sc["E"])
+        np.testing.assert_allclose(B, mean, rtol=1e-12, atol=1e-15)
+        assert np.all(D == t)
+
+
+def test_variance_selection_and_determinism(cluster):
+    sc, orc = cluster
+    B1, D1 = orc.mc_solve(256, seed=3, E=sc["E"])
+    B2, D2 = orc.mc_solve(256, seed=3, E=sc["E"])
+    np.testing.assert_array_equal(B1, B2)
+    B3, _ = orc.mc_solve(256, seed=4, E=sc["E"])
+    assert not np.array_equal(B1, B3)
+    # kernels without sources estimate S exactly every time: zero variance, never drawn
+    # again after the 8 sweeps; every step still makes N estimates
+    off = orc.pair_list()["off"]
+    lonely = np.diff(off) == 0
+    assert np.all(D1[lonely] == 8)
+    assert D1.sum() == 256 * sc["n"]
+    S = orc.solve(E=sc["E"], nb=0)
+    np.testing.assert_allclose(B1[lonely], S[lonely], rtol=1e-13)
+
+
+def test_solver_converges_to_the_neumann_solution(cluster):
+    sc, orc = cluster
+    ref = orc.solve(E=sc["E"], nb=300)
+    err = {}
+    for T in (64, 4096):
+        B, _ = orc.mc_solve(T, seed=3, E=sc["E"])
+        err[T] = np.linalg.norm(B - ref) / np.linalg.norm(ref)
+    assert err[4096] < 2e-3 and err[4096] < err[64] / 3
+
+
+def test_mc_needs_pairs():
+    sc = scenes.lone_plane()
+    with pytest.raises(RuntimeError):
+        O.Oracle(sc).transport().mc_solve(4)
