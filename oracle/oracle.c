@@ -2089,3 +2089,80 @@ int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, double
     free(recv);
     return 0;
 }
+
+/* ------------------------------------------------------------------ image formation
+ * Once the surfels carry their outgoing radiance B they are rendered from a viewpoint by
+ * Eq. L_I (the end of Sec. 5.3: the image is Eq. L_I evaluated for the camera's rays, which
+ * the paper runs as a tile rasterizer): the pixel's ray o + t d meets the surfels in depth
+ * order under the transport's hit rules (eps_plane, the cutoff, tie runs; no surfel
+ * excluded), each hit with a_h = alpha_h prod_{k<h}(1 - alpha_k), and the pixel's value in
+ * column c is the composited radiance leaving the surfels towards the camera,
+ *   I[c] = sum_h a_h Y(-d)^T B_{j_h}[:, c].
+ * Camera: cam = {o[3], forward[3], up[3]}; right = forward x up (normalised), the true up =
+ * right x forward; a pinhole with vertical field of view fov (radians), W x H pixels
+ * sampled at their centres (pixel (x, y), y down).  img: [H][W][C].  The image is linear
+ * in B; or_render_adjoint applies the transpose (dL/dB from dL/dimg). */
+static void pixel_ray(const double *cam, int W, int H, double fov, int x, int y, double *d) {
+    const double *f = cam + 3, *u0 = cam + 6;
+    double fn[3], r[3], u[3];
+    double lf = sqrt(dot3(f, f));
+    for (int a = 0; a < 3; ++a) fn[a] = f[a] / lf;
+    cross3(fn, u0, r);
+    double lr = sqrt(dot3(r, r));
+    for (int a = 0; a < 3; ++a) r[a] /= lr;
+    cross3(r, fn, u);
+    const double th = tan(0.5 * fov);
+    const double sx = (2.0 * (x + 0.5) / W - 1.0) * th * (double)W / (double)H;
+    const double sy = (1.0 - 2.0 * (y + 0.5) / H) * th;
+    for (int a = 0; a < 3; ++a) d[a] = fn[a] + sx * r[a] + sy * u[a];
+    double ld = sqrt(dot3(d, d));
+    for (int a = 0; a < 3; ++a) d[a] /= ld;
+}
+
+static void render_pass(const or_scene *s, const double *B, const double *dimg, const double *cam, int W, int H,
+                        double fov, double *img, double *dB) {
+    const int nc = s->nc, C = s->C, L = s->L;
+    if (dB) memset(dB, 0, sizeof(double) * (size_t)s->n * nc * C);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < H; ++y) {
+        hitvec hv = {0};
+        double d[3], md[3], Yo[1024];
+        for (int x = 0; x < W; ++x) {
+            pixel_ray(cam, W, H, fov, x, y, d);
+            for (int a = 0; a < 3; ++a) md[a] = -d[a];
+            or_sh_eval(L, md, Yo);
+            trace_all(s, -1, cam, d, INFINITY, &hv);
+            double *px = img ? img + ((size_t)y * W + x) * C : NULL;
+            if (px)
+                for (int c = 0; c < C; ++c) px[c] = 0.0;
+            double T = 1.0;
+            for (int h = 0; h < hv.cnt; ++h) {
+                const double a_h = hv.h[h].alpha * T;
+                T *= 1.0 - hv.h[h].alpha;
+                const int j = hv.h[h].j;
+                for (int c = 0; c < C; ++c) {
+                    if (px) {
+                        double sv = 0.0;
+                        for (int k = 0; k < nc; ++k) sv += Yo[k] * B[((size_t)j * nc + k) * C + c];
+                        px[c] += a_h * sv;
+                    }
+                    if (dB) {
+                        const double g = a_h * dimg[((size_t)y * W + x) * C + c];
+                        for (int k = 0; k < nc; ++k) {
+#pragma omp atomic
+                            dB[((size_t)j * nc + k) * C + c] += g * Yo[k];
+                        }
+                    }
+                }
+            }
+        }
+        free(hv.h);
+    }
+}
+
+void or_render(const or_scene *s, const double *B, const double *cam, int W, int H, double fov, double *img) {
+    render_pass(s, B, NULL, cam, W, H, fov, img, NULL);
+}
+void or_render_adjoint(const or_scene *s, const double *dimg, const double *cam, int W, int H, double fov, double *dB) {
+    render_pass(s, NULL, dimg, cam, W, H, fov, NULL, dB);
+}

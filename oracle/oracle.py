@@ -97,6 +97,8 @@ def lib():
             L.or_mc_pick.argtypes = [ct.c_void_p, _dp, _dp, ct.c_uint64, ct.c_int, ct.c_int, ct.c_int, _dp, _dp]
             L.or_mc_solve.restype = ct.c_int
             L.or_mc_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, ct.c_uint64, _dp, _dp]
+            L.or_render.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
+            L.or_render_adjoint.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
             L.or_num_threads.restype = ct.c_int
             _lib = L
     return _lib
@@ -343,6 +345,24 @@ class Oracle:
         k = lib().or_mc_pick(self.h, _ptr(_d(E)), _ptr(Bhat), ct.c_uint64(seed), int(t), int(q), int(a), ct.byref(p),
                              _ptr(delta))
         return int(k), p.value, delta
+
+    def render(self, B, cam, W, H, fov):
+        """Eq. L_I for a pinhole camera cam = (o, forward, up): image [H][W][C] of the radiance B."""
+        if getattr(self, "C", None) is None:
+            raise RuntimeError("render needs a transport (its column count)")
+        img = np.zeros((H, W, self.C))
+        lib().or_render(self.h, _ptr(_d(B).reshape(self._shape())), _ptr(_d(np.asarray(cam, float).reshape(9))),
+                        int(W), int(H), float(fov), _ptr(img))
+        return img
+
+    def render_adjoint(self, dimg, cam, W, H, fov):
+        """The transpose of render: dL/dB [N][nc][C] from dL/dimg [H][W][C]."""
+        if getattr(self, "C", None) is None:
+            raise RuntimeError("render needs a transport (its column count)")
+        dB = np.zeros(self._shape())
+        lib().or_render_adjoint(self.h, _ptr(_d(dimg).reshape(H, W, self.C)),
+                                _ptr(_d(np.asarray(cam, float).reshape(9))), int(W), int(H), float(fov), _ptr(dB))
+        return dB
 
     def brdf_grad_closed_form(self, g, E=None, nb=None):
         nb = self.sc["nb"] if nb is None else nb
