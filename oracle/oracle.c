@@ -1981,6 +1981,161 @@ static double mc_floor(const or_scene *s, const double *Bhat) {
     return 1e-9 * (1.0 + acc / (double)s->n);
 }
 
+/* Grouping of the sources (App. "Monte-Carlo Solver Details"): K-means of the surfels into
+ * G groups on the centre and the normal (the normal scaled by the centres' spread so both
+ * count), Lloyd's iterations from the surfels at evenly spaced indices until the
+ * assignment is stable (at most 50).  A group's proxy uses its mean centre, its mean
+ * normal and the sum of its members' current estimates. */
+typedef struct {
+    int G;
+    int *assign;    /* [n] */
+    double *gc, *gn; /* [G][3] mean centre, mean normal (normalised, 0 if degenerate) */
+} mc_groups;
+
+static void mc_kmeans(const or_scene *s, int G, mc_groups *g) {
+    const int n = s->n;
+    g->G = G;
+    g->assign = (int *)malloc(sizeof(int) * n);
+    g->gc = dup_arr(NULL, (size_t)G * 3);
+    g->gn = dup_arr(NULL, (size_t)G * 3);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], s->p[i * 3 + a]);
+            hi[a] = fmax(hi[a], s->p[i * 3 + a]);
+        }
+    const double ext = fmax(fmax(hi[0] - lo[0], hi[1] - lo[1]), fmax(hi[2] - lo[2], 1e-12));
+    double *f = dup_arr(NULL, (size_t)n * 6), *cen = dup_arr(NULL, (size_t)G * 6), *acc = dup_arr(NULL, (size_t)G * 6);
+    int *cnt = (int *)malloc(sizeof(int) * G);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            f[i * 6 + a] = s->p[i * 3 + a];
+            f[i * 6 + 3 + a] = 0.5 * ext * s->nrm[i * 3 + a];
+        }
+    for (int k = 0; k < G; ++k) memcpy(cen + k * 6, f + (size_t)((long)k * n / G) * 6, sizeof(double) * 6);
+    for (int i = 0; i < n; ++i) g->assign[i] = -1;
+    for (int it = 0; it < 50; ++it) {
+        int changed = 0;
+        for (int i = 0; i < n; ++i) {
+            int best = 0;
+            double bd = 1e300;
+            for (int k = 0; k < G; ++k) {
+                double dd = 0.0;
+                for (int a = 0; a < 6; ++a) dd += (f[i * 6 + a] - cen[k * 6 + a]) * (f[i * 6 + a] - cen[k * 6 + a]);
+                if (dd < bd) {
+                    bd = dd;
+                    best = k;
+                }
+            }
+            if (best != g->assign[i]) changed = 1;
+            g->assign[i] = best;
+        }
+        memset(acc, 0, sizeof(double) * G * 6);
+        memset(cnt, 0, sizeof(int) * G);
+        for (int i = 0; i < n; ++i) {
+            cnt[g->assign[i]]++;
+            for (int a = 0; a < 6; ++a) acc[g->assign[i] * 6 + a] += f[i * 6 + a];
+        }
+        for (int k = 0; k < G; ++k)
+            if (cnt[k])
+                for (int a = 0; a < 6; ++a) cen[k * 6 + a] = acc[k * 6 + a] / cnt[k];
+        if (!changed) break;
+    }
+    for (int k = 0; k < G; ++k) {
+        double gc[3] = {0, 0, 0}, gn[3] = {0, 0, 0};
+        int c = 0;
+        for (int i = 0; i < n; ++i)
+            if (g->assign[i] == k) {
+                ++c;
+                for (int a = 0; a < 3; ++a) {
+                    gc[a] += s->p[i * 3 + a];
+                    gn[a] += s->nrm[i * 3 + a];
+                }
+            }
+        const double ln = sqrt(dot3(gn, gn));
+        for (int a = 0; a < 3; ++a) {
+            g->gc[k * 3 + a] = c ? gc[a] / c : 0.0;
+            g->gn[k * 3 + a] = ln > 1e-12 ? gn[a] / ln : 0.0;
+        }
+    }
+    free(f);
+    free(cen);
+    free(acc);
+    free(cnt);
+}
+static void mc_groups_free(mc_groups *g) {
+    free(g->assign);
+    free(g->gc);
+    free(g->gn);
+}
+
+/* The next event of receiver a: flat (grp NULL), the pair drawn by reservoir sampling over
+ * all of a's pairs by their proxy weights w; grouped, first a group by its proxy
+ *   w_g = (|n_a.w_g| |n_g.w_g| / r_g^2 + 1e-12) (lum(|Y(-w_g)^T sum_{j in g} Bhat_j|) + floor)
+ * (w_g towards the group's mean centre, n_g its mean normal; 0 for a group holding none of
+ * a's sources), then a pair of a in that group by the proxy weights.  Returns the pair's
+ * index within a's pairs (-1 without pairs) and its probability p. */
+static long mc_choose(const or_scene *s, const double *Bhat, const double *Bsum, double fl, const mc_groups *grp, int a,
+                      uint64_t seed, int t, int q, double *w, double *p) {
+    const long np = s->pair_off[a + 1] - s->pair_off[a];
+    const double tot = mc_weights(s, Bhat, fl, a, w);
+    *p = 0.0;
+    if (!grp) {
+        const long pick = mc_reservoir(w, np, seed, t, q);
+        if (pick >= 0) *p = w[pick] / tot;
+        return pick;
+    }
+    const int G = grp->G, nc = s->nc, C = s->C, L = s->L;
+    double *wg = dup_arr(NULL, (size_t)G);
+    int *has = (int *)calloc((size_t)G, sizeof(int));
+    for (long k = 0; k < np; ++k) has[grp->assign[s->pair_j[s->pair_off[a] + k]]] = 1;
+    double Yo[1024], totg = 0.0;
+    for (int g = 0; g < G; ++g) {
+        wg[g] = 0.0;
+        if (!has[g]) continue;
+        double wv[3], md[3];
+        for (int c3 = 0; c3 < 3; ++c3) wv[c3] = grp->gc[g * 3 + c3] - s->p[a * 3 + c3];
+        const double r2 = dot3(wv, wv) + 1e-24, r = sqrt(r2);
+        for (int c3 = 0; c3 < 3; ++c3) {
+            wv[c3] /= r;
+            md[c3] = -wv[c3];
+        }
+        or_sh_eval(L, md, Yo);
+        double lum = 0.0;
+        for (int c = 0; c < C; ++c) {
+            double sv = 0.0;
+            for (int k = 0; k < nc; ++k) sv += Yo[k] * Bsum[((size_t)g * nc + k) * C + c];
+            lum += MC_LUM[c % 3] * fabs(sv);
+        }
+        const double geo = fabs(dot3(s->nrm + a * 3, wv)) * fabs(dot3(grp->gn + g * 3, wv)) / r2;
+        wg[g] = (geo + 1e-12) * (lum + fl);
+        totg += wg[g];
+    }
+    long pick = -1;
+    const long gsel = mc_reservoir(wg, G, seed, t, q + 0x40000000);
+    if (gsel >= 0) {
+        double *wk = dup_arr(NULL, (size_t)(np > 0 ? np : 1));
+        double totk = 0.0;
+        for (long k = 0; k < np; ++k) {
+            wk[k] = grp->assign[s->pair_j[s->pair_off[a] + k]] == gsel ? w[k] : 0.0;
+            totk += wk[k];
+        }
+        pick = mc_reservoir(wk, np, seed, t, q);
+        if (pick >= 0) *p = wg[gsel] / totg * wk[pick] / totk;
+        free(wk);
+    }
+    free(wg);
+    free(has);
+    return pick;
+}
+
+static void mc_group_sums(const or_scene *s, const mc_groups *grp, const double *Bhat, double *Bsum) {
+    const size_t R = (size_t)s->nc * s->C;
+    memset(Bsum, 0, sizeof(double) * grp->G * R);
+    for (int i = 0; i < s->n; ++i)
+        for (size_t k = 0; k < R; ++k) Bsum[grp->assign[i] * R + k] += Bhat[i * R + k];
+}
+
 /* The proposal of receiver a under the means Bhat, for tests: w [pairs of a] (unnormalised)
  * and the floor used.  Returns the number of pairs of a, or -1 without pairs. */
 long or_mc_weights(const or_scene *s, const double *Bhat, int a, double *w, double *floor_out) {
@@ -1991,30 +2146,57 @@ long or_mc_weights(const or_scene *s, const double *Bhat, int a, double *w, doub
     return s->pair_off[a + 1] - s->pair_off[a];
 }
 
-/* One estimate for tests: the pair (index within a's pairs) that weighted reservoir
- * sampling picks with the uniforms of (seed, t, q), its probability, and delta. */
-long or_mc_pick(const or_scene *s, const double *E, const double *Bhat, uint64_t seed, int t, int q, int a,
+/* One estimate for tests: the pair (index within a's pairs) that the next-event
+ * estimation picks with the uniforms of (seed, t, q) (flat for G = 0, else through G
+ * K-means groups), its probability, and delta. */
+long or_mc_pick(const or_scene *s, const double *E, const double *Bhat, uint64_t seed, int t, int q, int a, int G,
                 double *p_out, double *delta) {
     if (!s->pmode) return -1;
-    size_t M = (size_t)s->n * s->nc * s->C;
+    const size_t M = (size_t)s->n * s->nc * s->C;
     double *S = dup_arr(NULL, M);
     make_S(s, E, S);
     const long np = s->pair_off[a + 1] - s->pair_off[a];
     double *w = dup_arr(NULL, (size_t)(np > 0 ? np : 1));
-    const double tot = mc_weights(s, Bhat, mc_floor(s, Bhat), a, w);
-    const long pick = mc_reservoir(w, np, seed, t, q);
-    const double p = pick >= 0 ? w[pick] / tot : 0.0;
+    mc_groups grp = {0};
+    double *Bsum = NULL;
+    if (G > 0) {
+        mc_kmeans(s, G, &grp);
+        Bsum = dup_arr(NULL, (size_t)G * s->nc * s->C);
+        mc_group_sums(s, &grp, Bhat, Bsum);
+    }
+    double p;
+    const long pick = mc_choose(s, Bhat, Bsum, mc_floor(s, Bhat), G > 0 ? &grp : NULL, a, seed, t, q, w, &p);
     if (p_out) *p_out = p;
     if (delta) mc_estimate(s, S, Bhat, a, pick >= 0 ? s->pair_off[a] + pick : 0, p, delta);
+    if (G > 0) {
+        mc_groups_free(&grp);
+        free(Bsum);
+    }
     free(w);
     free(S);
     return pick;
 }
 
-/* Alg. 1: T steps, N estimates per step; B receives S^B / D, visits (optional) D. */
-int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, double *B, double *visits) {
+/* K-means group of every surfel (for tests). */
+int or_mc_groups(const or_scene *s, int G, int *assign) {
+    mc_groups grp = {0};
+    mc_kmeans(s, G, &grp);
+    memcpy(assign, grp.assign, sizeof(int) * s->n);
+    mc_groups_free(&grp);
+    return 0;
+}
+
+/* Alg. 1: T steps, N estimates per step (next events flat for G = 0, else through G
+ * K-means groups); B receives S^B / D, visits (optional) D. */
+int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, int G, double *B, double *visits) {
     if (!s->pmode) return -1;
     int n = s->n, nc = s->nc, C = s->C;
+    mc_groups grp = {0};
+    double *Bsum = NULL;
+    if (G > 0) {
+        mc_kmeans(s, G, &grp);
+        Bsum = dup_arr(NULL, (size_t)G * nc * C);
+    }
     size_t M = (size_t)n * nc * C, R = (size_t)nc * C;
     double *S = dup_arr(NULL, M), *SB = dup_arr(NULL, M), *SB2 = dup_arr(NULL, M), *Bhat = dup_arr(NULL, M);
     double *D = dup_arr(NULL, n), *var = dup_arr(NULL, n), *delta = dup_arr(NULL, (size_t)n * R);
@@ -2054,14 +2236,14 @@ int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, double
             }
         }
         const double fl = mc_floor(s, Bhat);
+        if (G > 0) mc_group_sums(s, &grp, Bhat, Bsum);
 #pragma omp parallel for schedule(dynamic, 4)
         for (int q = 0; q < n; ++q) {
             const int a = recv[q];
             const long np = s->pair_off[a + 1] - s->pair_off[a];
             double *w = (double *)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
-            const double tot = mc_weights(s, Bhat, fl, a, w);
-            const long pick = mc_reservoir(w, np, seed, t, q);
-            const double p = pick >= 0 ? w[pick] / tot : 0.0;
+            double p;
+            const long pick = mc_choose(s, Bhat, Bsum, fl, G > 0 ? &grp : NULL, a, seed, t, q, w, &p);
             mc_estimate(s, S, Bhat, a, pick >= 0 ? s->pair_off[a] + pick : 0, p, delta + (size_t)q * R);
             free(w);
         }
@@ -2079,6 +2261,10 @@ int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, double
     }
     memcpy(B, Bhat, sizeof(double) * M);
     if (visits) memcpy(visits, D, sizeof(double) * n);
+    if (G > 0) {
+        mc_groups_free(&grp);
+        free(Bsum);
+    }
     free(S);
     free(SB);
     free(SB2);

@@ -94,9 +94,11 @@ def lib():
             L.or_mc_weights.restype = ct.c_long
             L.or_mc_weights.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
             L.or_mc_pick.restype = ct.c_long
-            L.or_mc_pick.argtypes = [ct.c_void_p, _dp, _dp, ct.c_uint64, ct.c_int, ct.c_int, ct.c_int, _dp, _dp]
+            L.or_mc_pick.argtypes = [ct.c_void_p, _dp, _dp, ct.c_uint64, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _dp,
+                                     _dp]
             L.or_mc_solve.restype = ct.c_int
-            L.or_mc_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, ct.c_uint64, _dp, _dp]
+            L.or_mc_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, ct.c_uint64, ct.c_int, _dp, _dp]
+            L.or_mc_groups.argtypes = [ct.c_void_p, ct.c_int, _ip]
             L.or_render.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
             L.or_render_adjoint.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
             L.or_num_threads.restype = ct.c_int
@@ -318,15 +320,21 @@ class Oracle:
             raise RuntimeError("geometry gradients need a transport (transport() or pairs())")
         return dict(dp=dp, ds=ds, dtu=dtu, dtv=dtv)
 
-    def mc_solve(self, T, seed=0, E=None):
-        """Alg. 1 (Monte-Carlo TD(0) solver with next-event estimation) on the
-        center-to-center transport: (B [N][nc][C], visits [N])."""
+    def mc_solve(self, T, seed=0, E=None, groups=0):
+        """Alg. 1 (Monte-Carlo TD(0) solver with next-event estimation, flat or through
+        `groups` K-means groups) on the center-to-center transport: (B [N][nc][C], visits [N])."""
         if not getattr(self, "pmode", False):
             raise RuntimeError("the Monte-Carlo solver runs on the center-to-center transport (pairs())")
         B = np.zeros(self._shape())
         D = np.zeros(self.n)
-        lib().or_mc_solve(self.h, _ptr(_d(E)), int(T), ct.c_uint64(seed), _ptr(B), _ptr(D))
+        lib().or_mc_solve(self.h, _ptr(_d(E)), int(T), ct.c_uint64(seed), int(groups), _ptr(B), _ptr(D))
         return B, D
+
+    def mc_groups(self, G):
+        """The K-means group of every surfel."""
+        out = np.zeros(self.n, np.int32)
+        lib().or_mc_groups(self.h, int(G), out.ctypes.data_as(_ip))
+        return out
 
     def mc_weights(self, Bhat, a):
         """The proposal of receiver a under the means Bhat: (unnormalised weights over a's pairs, floor)."""
@@ -337,13 +345,13 @@ class Oracle:
         n = lib().or_mc_weights(self.h, _ptr(Bhat), int(a), _ptr(w), ct.byref(fl))
         return w[:n], fl.value
 
-    def mc_pick(self, Bhat, seed, t, q, a, E=None):
+    def mc_pick(self, Bhat, seed, t, q, a, E=None, groups=0):
         """One next-event estimate: (picked pair index within a's pairs, its probability, delta)."""
         Bhat = _d(Bhat).reshape(self._shape())
         p = ct.c_double(0.0)
         delta = np.zeros((self.nc, self.C))
-        k = lib().or_mc_pick(self.h, _ptr(_d(E)), _ptr(Bhat), ct.c_uint64(seed), int(t), int(q), int(a), ct.byref(p),
-                             _ptr(delta))
+        k = lib().or_mc_pick(self.h, _ptr(_d(E)), _ptr(Bhat), ct.c_uint64(seed), int(t), int(q), int(a), int(groups),
+                             ct.byref(p), _ptr(delta))
         return int(k), p.value, delta
 
     def render(self, B, cam, W, H, fov):

@@ -48,6 +48,32 @@ def test_estimator_is_unbiased_for_the_bounce(cluster):
         np.testing.assert_allclose(delta, S[a], rtol=1e-15)
 
 
+@pytest.mark.parametrize("groups", [3, 6])
+def test_grouped_proposal_is_unbiased(cluster, groups):
+    """Through K-means groups (App. "Monte-Carlo Solver Details"): p_b = p(group) p(b | group)
+    sums to 1 over the receiver's pairs and sum p_b delta_b = S_a + (K Bhat)_a exactly."""
+    sc, orc = cluster
+    assign = orc.mc_groups(groups)
+    assert set(assign) == set(range(groups))  # no empty group on this scene
+    Bhat = np.random.default_rng(2).normal(size=orc._shape())
+    S = orc.solve(E=sc["E"], nb=0)
+    KB = orc.apply_K(Bhat)[0]
+    off = orc.pair_list()["off"]
+    for a in [a for a in range(sc["n"]) if off[a + 1] - off[a] >= 3][:3]:
+        n_pairs = off[a + 1] - off[a]
+        seen = {}
+        for t in range(1, 40000):
+            k, pk, delta = orc.mc_pick(Bhat, 5, t, 1, a, E=sc["E"], groups=groups)
+            seen.setdefault(k, (pk, delta))
+            if len(seen) == n_pairs:
+                break
+        assert len(seen) == n_pairs
+        assert sum(pk for pk, _ in seen.values()) == pytest.approx(1.0, rel=1e-12)
+        expect = sum(pk * delta for pk, delta in seen.values())
+        ref = S[a] + KB[a]
+        assert np.linalg.norm(expect - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
 def test_reservoir_sampling_draws_from_the_proposal(cluster):
     sc, orc = cluster
     Bhat = np.random.default_rng(1).normal(size=orc._shape())
@@ -126,6 +152,21 @@ def test_solver_converges_to_the_neumann_solution(cluster):
         B, _ = orc.mc_solve(T, seed=3, E=sc["E"])
         err[T] = np.linalg.norm(B - ref) / np.linalg.norm(ref)
     assert err[4096] < 2e-3 and err[4096] < err[64] / 3
+
+
+def test_grouped_solver_converges(cluster):
+    """The grouped proposal is unbiased but, on this cloud of randomly oriented surfels,
+    a poorer match to the integrand (a group's mean normal and centre stand for all its
+    members), so it converges more slowly; the mean error over three seeds still falls
+    with T."""
+    sc, orc = cluster
+    ref = orc.solve(E=sc["E"], nb=300)
+
+    def mean_err(T):
+        return np.mean([np.linalg.norm(orc.mc_solve(T, seed=sd, E=sc["E"], groups=4)[0] - ref) / np.linalg.norm(ref)
+                        for sd in (3, 4, 5)])
+    e64, e16k = mean_err(64), mean_err(16384)
+    assert e16k < 3e-3 and e16k < e64 / 3
 
 
 def test_mc_needs_pairs():
