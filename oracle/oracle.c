@@ -2352,3 +2352,69 @@ void or_render(const or_scene *s, const double *B, const double *cam, int W, int
 void or_render_adjoint(const or_scene *s, const double *dimg, const double *cam, int W, int H, double fov, double *dB) {
     render_pass(s, NULL, dimg, cam, W, H, fov, NULL, dB);
 }
+
+/* Progressive refinement (Sec. 7, the shooting form of Eq. final-radiosity) on the
+ * center-to-center transport: Bhat = S and the unshot dB = S; each of M shots takes the
+ * kernel i whose unshot radiance is the largest (luminance of |dB_i|, summed over its
+ * coefficients and lights) and shoots it into every receiver j that has i as a source,
+ *   dB_j += K_ji dB_i,  Bhat_j += K_ji dB_i,  then dB_i = 0,
+ * with K_ji the pair's transport (as in the bounce).  The remaining problem
+ * B^r = dB + K B^r is again the full light transport, and B = Bhat + B^r - dB is exact for
+ * any number of shots (the paper's decomposition that lets the solvers be hybridised). */
+int or_prog_refine(const or_scene *s, const double *E, int M, double *Bhat, double *dB) {
+    if (!s->pmode) return -1;
+    const int n = s->n, nc = s->nc, C = s->C, L = s->L;
+    const size_t R = (size_t)nc * C, Mt = (size_t)n * R;
+    make_S(s, E, Bhat);
+    memcpy(dB, Bhat, sizeof(double) * Mt);
+    /* receivers of every source */
+    const long P = s->pair_off[n];
+    long *soff = (long *)calloc((size_t)n + 1, sizeof(long));
+    long *sent = (long *)malloc(sizeof(long) * (size_t)(P > 0 ? P : 1));
+    for (long e = 0; e < P; ++e) soff[s->pair_j[e] + 1]++;
+    for (int i = 0; i < n; ++i) soff[i + 1] += soff[i];
+    long *cur = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    memcpy(cur, soff, sizeof(long) * n);
+    for (int a = 0; a < n; ++a)
+        for (long e = s->pair_off[a]; e < s->pair_off[a + 1]; ++e) sent[cur[s->pair_j[e]]++] = e;
+    double Yo[1024], Yi[1024];
+    for (int m = 0; m < M; ++m) {
+        int best = -1;
+        double bl = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double l = 0.0;
+            for (size_t k = 0; k < R; ++k) l += MC_LUM[(k % C) % 3] * fabs(dB[i * R + k]);
+            if (l > bl) {
+                bl = l;
+                best = i;
+            }
+        }
+        if (best < 0) break; /* nothing left to shoot */
+        for (long q = soff[best]; q < soff[best + 1]; ++q) {
+            const long e = sent[q];
+            int a = 0; /* the receiver of pair e */
+            while (s->pair_off[a + 1] <= e) ++a;
+            double d[3], md[3], rd[3];
+            pair_dir(s, a, best, d);
+            for (int c3 = 0; c3 < 3; ++c3) md[c3] = -d[c3];
+            reflect(s->nrm + a * 3, d, rd);
+            or_sh_eval(L, md, Yo);
+            or_sh_eval(L, rd, Yi);
+            for (int c = 0; c < C; ++c) {
+                double sv = 0.0;
+                for (int k = 0; k < nc; ++k) sv += Yo[k] * dB[((size_t)best * nc + k) * C + c];
+                for (int k = 0; k < nc; ++k) {
+                    const double v = alpha_c(s, a) * s->c[((size_t)a * (L + 1) + band_of(k)) * 3 + c % 3] * Yi[k] *
+                                     s->pair_V[e] * sv;
+                    Bhat[((size_t)a * nc + k) * C + c] += v;
+                    dB[((size_t)a * nc + k) * C + c] += v;
+                }
+            }
+        }
+        memset(dB + (size_t)best * R, 0, sizeof(double) * R);
+    }
+    free(soff);
+    free(sent);
+    free(cur);
+    return 0;
+}

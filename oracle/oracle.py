@@ -101,6 +101,8 @@ def lib():
             L.or_mc_groups.argtypes = [ct.c_void_p, ct.c_int, _ip]
             L.or_render.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
             L.or_render_adjoint.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
+            L.or_prog_refine.restype = ct.c_int
+            L.or_prog_refine.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, _dp]
             L.or_num_threads.restype = ct.c_int
             _lib = L
     return _lib
@@ -329,6 +331,15 @@ class Oracle:
         D = np.zeros(self.n)
         lib().or_mc_solve(self.h, _ptr(_d(E)), int(T), ct.c_uint64(seed), int(groups), _ptr(B), _ptr(D))
         return B, D
+
+    def prog_refine(self, M, E=None):
+        """Progressive refinement (shooting) with M shots on the center-to-center transport:
+        (Bhat, unshot dB), both [N][nc][C]."""
+        if not getattr(self, "pmode", False):
+            raise RuntimeError("progressive refinement runs on the center-to-center transport (pairs())")
+        Bh, dB = np.zeros(self._shape()), np.zeros(self._shape())
+        lib().or_prog_refine(self.h, _ptr(_d(E)), int(M), _ptr(Bh), _ptr(dB))
+        return Bh, dB
 
     def mc_groups(self, G):
         """The K-means group of every surfel."""

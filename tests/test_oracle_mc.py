@@ -173,3 +173,35 @@ def test_mc_needs_pairs():
     sc = scenes.lone_plane()
     with pytest.raises(RuntimeError):
         O.Oracle(sc).transport().mc_solve(4)
+
+
+def _neumann(orc, x, nb=400):
+    out, cur = x.copy(), x.copy()
+    for _ in range(nb):
+        cur = orc.apply_K(cur)[0]
+        out += cur
+    return out
+
+
+@pytest.mark.parametrize("shots", [0, 1, 5, 24])
+def test_progressive_refinement_decomposition(cluster, shots):
+    """After any number of shots, B = Bhat + B^r - dB with B^r = dB + K B^r (the remaining
+    problem is again the full transport) equals the solution: Sec. 7's decomposition."""
+    sc, orc = cluster
+    ref = orc.solve(E=sc["E"], nb=400)
+    Bh, dB = orc.prog_refine(shots, E=sc["E"])
+    full = Bh + _neumann(orc, dB) - dB
+    assert np.linalg.norm(full - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_progressive_refinement_shoots_the_brightest_and_converges(cluster):
+    sc, orc = cluster
+    S = orc.solve(E=sc["E"], nb=0)
+    lum = np.array([0.2126, 0.7152, 0.0722])[np.arange(orc.C) % 3]
+    first = int(np.argmax((np.abs(S) * lum).sum(axis=(1, 2))))
+    Bh, dB = orc.prog_refine(1, E=sc["E"])
+    assert np.all(dB[first] == 0.0)
+    np.testing.assert_array_equal(Bh[first], S[first])  # nothing has reached it yet
+    ref = orc.solve(E=sc["E"], nb=400)
+    Bh, dB = orc.prog_refine(400, E=sc["E"])
+    assert np.linalg.norm(Bh - ref) <= 1e-12 * np.linalg.norm(ref)
