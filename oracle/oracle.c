@@ -2187,8 +2187,11 @@ int or_mc_groups(const or_scene *s, int G, int *assign) {
 }
 
 /* Alg. 1: T steps, N estimates per step (next events flat for G = 0, else through G
- * K-means groups); B receives S^B / D, visits (optional) D. */
-int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, int G, double *B, double *visits) {
+ * K-means groups); B receives S^B / D, visits (optional) D.  S_in (optional) replaces the
+ * source term S = E + D: the hybrid solver runs Alg. 1 on the remaining problem of
+ * progressive refinement, whose source is the unshot radiance. */
+int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, int G, const double *S_in, double *B,
+                double *visits) {
     if (!s->pmode) return -1;
     int n = s->n, nc = s->nc, C = s->C;
     mc_groups grp = {0};
@@ -2201,7 +2204,8 @@ int or_mc_solve(const or_scene *s, const double *E, int T, uint64_t seed, int G,
     double *S = dup_arr(NULL, M), *SB = dup_arr(NULL, M), *SB2 = dup_arr(NULL, M), *Bhat = dup_arr(NULL, M);
     double *D = dup_arr(NULL, n), *var = dup_arr(NULL, n), *delta = dup_arr(NULL, (size_t)n * R);
     int *recv = (int *)malloc(sizeof(int) * n);
-    make_S(s, E, S);
+    if (S_in) memcpy(S, S_in, sizeof(double) * M);
+    else make_S(s, E, S);
     memset(SB, 0, sizeof(double) * M);
     memset(SB2, 0, sizeof(double) * M);
     memset(Bhat, 0, sizeof(double) * M);

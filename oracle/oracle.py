@@ -97,7 +97,7 @@ def lib():
             L.or_mc_pick.argtypes = [ct.c_void_p, _dp, _dp, ct.c_uint64, ct.c_int, ct.c_int, ct.c_int, ct.c_int, _dp,
                                      _dp]
             L.or_mc_solve.restype = ct.c_int
-            L.or_mc_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, ct.c_uint64, ct.c_int, _dp, _dp]
+            L.or_mc_solve.argtypes = [ct.c_void_p, _dp, ct.c_int, ct.c_uint64, ct.c_int, _dp, _dp, _dp]
             L.or_mc_groups.argtypes = [ct.c_void_p, ct.c_int, _ip]
             L.or_render.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
             L.or_render_adjoint.argtypes = [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_int, ct.c_double, _dp]
@@ -322,14 +322,15 @@ class Oracle:
             raise RuntimeError("geometry gradients need a transport (transport() or pairs())")
         return dict(dp=dp, ds=ds, dtu=dtu, dtv=dtv)
 
-    def mc_solve(self, T, seed=0, E=None, groups=0):
+    def mc_solve(self, T, seed=0, E=None, groups=0, S=None):
         """Alg. 1 (Monte-Carlo TD(0) solver with next-event estimation, flat or through
         `groups` K-means groups) on the center-to-center transport: (B [N][nc][C], visits [N])."""
         if not getattr(self, "pmode", False):
             raise RuntimeError("the Monte-Carlo solver runs on the center-to-center transport (pairs())")
         B = np.zeros(self._shape())
         D = np.zeros(self.n)
-        lib().or_mc_solve(self.h, _ptr(_d(E)), int(T), ct.c_uint64(seed), int(groups), _ptr(B), _ptr(D))
+        S = None if S is None else _d(S).reshape(self._shape())
+        lib().or_mc_solve(self.h, _ptr(_d(E)), int(T), ct.c_uint64(seed), int(groups), _ptr(S), _ptr(B), _ptr(D))
         return B, D
 
     def prog_refine(self, M, E=None):
@@ -340,6 +341,13 @@ class Oracle:
         Bh, dB = np.zeros(self._shape()), np.zeros(self._shape())
         lib().or_prog_refine(self.h, _ptr(_d(E)), int(M), _ptr(Bh), _ptr(dB))
         return Bh, dB
+
+    def hybrid_solve(self, shots, T, seed=0, E=None, groups=0):
+        """Sec. 7's hybrid solver: progressive refinement for `shots` shots, then Alg. 1 on the
+        remaining problem (source = the unshot radiance dB): B = Bhat + B^r - dB."""
+        Bh, dB = self.prog_refine(shots, E=E)
+        Br, _ = self.mc_solve(T, seed=seed, groups=groups, S=dB)
+        return Bh + Br - dB
 
     def mc_groups(self, G):
         """The K-means group of every surfel."""

@@ -205,3 +205,20 @@ def test_progressive_refinement_shoots_the_brightest_and_converges(cluster):
     ref = orc.solve(E=sc["E"], nb=400)
     Bh, dB = orc.prog_refine(400, E=sc["E"])
     assert np.linalg.norm(Bh - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_hybrid_solver_lowers_the_variance(cluster):
+    """Sec. 7's hybrid solver: shooting first and running Alg. 1 on the remaining problem
+    (source = the unshot radiance) reaches the solution with far less noise than Alg. 1 on
+    the whole problem for the same number of steps."""
+    sc, orc = cluster
+    ref = orc.solve(E=sc["E"], nb=300)
+
+    def mean_err(shots):
+        return np.mean([np.linalg.norm(orc.hybrid_solve(shots, 1024, seed=sd, E=sc["E"]) - ref) / np.linalg.norm(ref)
+                        for sd in (1, 2, 3)])
+    pure, hybrid = mean_err(0), mean_err(24)
+    assert hybrid < 1e-4 and hybrid < pure / 5
+    # with nothing left unshot the hybrid returns the shooting result itself
+    Bh, dB = orc.prog_refine(400, E=sc["E"])
+    np.testing.assert_allclose(orc.hybrid_solve(400, 16, E=sc["E"]), Bh, rtol=1e-12, atol=1e-14)
