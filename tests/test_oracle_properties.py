@@ -1,0 +1,86 @@
+"""Property checks of the oracle over generated inputs (hypothesis): the adjoint identity
+and energy bounds on random clusters, the render transpose on random cameras, the
+geometry gradient along random directions against a central difference, and the SH
+gradient's tangential part (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+from oracle import oracle as O  # noqa: E402
+from paper_2509_18497_gb300 import scenes  # noqa: E402
+
+SEEDS = st.integers(min_value=0, max_value=10_000)
+
+
+@settings(max_examples=12, deadline=None)
+@given(seed=SEEDS, n=st.integers(min_value=8, max_value=40), pairs=st.booleans())
+def test_adjoint_identity_and_energy(seed, n, pairs):
+    sc = scenes.random_cluster(n=n, seed=seed, L=2, nd=32, nb=2, n_lights=1)
+    orc = O.Oracle(sc)
+    orc = orc.pairs() if pairs else orc.transport()
+    rng = np.random.default_rng(seed)
+    u, v = rng.normal(size=orc._shape()), rng.normal(size=orc._shape())
+    lhs = float(np.sum(orc.apply_KT(u) * v))
+    rhs = float(np.sum(u * orc.apply_K(v)[0]))
+    assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12)
+    if not pairs:  # every ray's compositing weights sum to at most 1
+        h = orc.hits()
+        cs = np.concatenate([[0.0], np.cumsum(h["a"])])
+        sums = cs[h["off"][1:]] - cs[h["off"][:-1]]
+        assert np.all(sums <= 1.0 + 1e-12) and np.all(np.asarray(h["a"]) >= 0.0)
+
+
+@settings(max_examples=10, deadline=None)
+@given(seed=SEEDS, yaw=st.floats(-math.pi, math.pi), pitch=st.floats(-1.2, 1.2))
+def test_render_transpose_on_random_cameras(seed, yaw, pitch):
+    sc = scenes.random_cluster(n=30, seed=seed, L=2, nd=32, nb=1, n_lights=1)
+    orc = O.Oracle(sc).transport()
+    f = np.array([math.cos(pitch) * math.sin(yaw), math.sin(pitch), -math.cos(pitch) * math.cos(yaw)])
+    o = np.array([0.5, 0.5, 0.5]) - 2.5 * f
+    cam = list(o) + list(f) + [0.0, 1.0, 0.0]
+    rng = np.random.default_rng(seed)
+    B = rng.normal(size=orc._shape())
+    W = rng.normal(size=(12, 16, orc.C))
+    lhs = float(np.sum(orc.render(B, cam, 16, 12, 0.9) * W))
+    rhs = float(np.sum(B * orc.render_adjoint(W, cam, 16, 12, 0.9)))
+    assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12)
+
+
+@settings(max_examples=6, deadline=None)
+@given(seed=SEEDS)
+def test_geometry_gradient_along_a_random_direction(seed):
+    """dL/dp . delta equals the central difference of L along delta (all centres moved)."""
+    sc = scenes.with_emission(scenes.random_cluster(n=20, seed=seed, L=2, nb=2, n_lights=1), seed=seed + 1)
+    orc = O.Oracle(sc).pairs()
+    rng = np.random.default_rng(seed)
+    W = rng.normal(size=orc._shape())
+    g = orc.geometry_grad(W, E=sc["E"], nb=sc["nb"])
+    delta = rng.normal(size=sc["p"].shape)
+
+    def loss(h):
+        s2 = dict(sc)
+        s2["p"] = sc["p"] + h * delta
+        return float(np.sum(W * O.Oracle(s2).pairs().solve(E=sc["E"], nb=sc["nb"])))
+    h = 1e-6
+    num = (loss(h) - loss(-h)) / (2 * h)
+    an = float(np.sum(g["dp"] * delta))
+    assert num == pytest.approx(an, rel=1e-5, abs=1e-7 * (1 + abs(loss(0))))
+
+
+@settings(max_examples=30, deadline=None)
+@given(x=st.floats(-1, 1), y=st.floats(-1, 1), z=st.floats(-1, 1), L=st.integers(1, 3))
+def test_sh_gradient_tangential_part(x, y, z, L):
+    w = np.array([x, y, z])
+    hypothesis.assume(np.linalg.norm(w) > 0.1)
+    w /= np.linalg.norm(w)
+    t = np.cross(w, [0.3, -0.5, 0.8])
+    hypothesis.assume(np.linalg.norm(t) > 0.1)
+    t /= np.linalg.norm(t)
+    _, dY = O.sh_grad(L, w)
+    h = 1e-5
+    num = (O.sh_eval(L, (w + h * t) / np.linalg.norm(w + h * t)) - O.sh_eval(L, (w - h * t) / np.linalg.norm(w - h * t))) / (2 * h)
+    np.testing.assert_allclose(dY.T @ t, num, atol=1e-8)
