@@ -66,9 +66,15 @@ def test_geometry_gradient_along_a_random_direction(seed):
         s2["p"] = sc["p"] + h * delta
         return float(np.sum(W * O.Oracle(s2).pairs().solve(E=sc["E"], nb=sc["nb"])))
     h = 1e-6
-    num = (loss(h) - loss(-h)) / (2 * h)
+    cd1 = (loss(h) - loss(-h)) / (2 * h)
+    cd2 = (loss(h / 2) - loss(-h / 2)) / h
+    tol = 1e-5 * abs(cd1) + 1e-7 * (1 + abs(loss(0)))
+    # moving every centre at once can cross a discrete event (a front test, the cutoff, an
+    # eps_plane rule) inside (-h, h): the differences then disagree and the case says
+    # nothing about the smooth piece the gradient describes
+    hypothesis.assume(abs(cd1 - cd2) <= tol)
     an = float(np.sum(g["dp"] * delta))
-    assert num == pytest.approx(an, rel=1e-5, abs=1e-7 * (1 + abs(loss(0))))
+    assert cd1 == pytest.approx(an, rel=1e-5, abs=1e-7 * (1 + abs(loss(0))))
 
 
 @settings(max_examples=30, deadline=None)
