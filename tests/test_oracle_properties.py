@@ -16,7 +16,7 @@ from paper_2509_18497_gb300 import scenes  # noqa: E402
 SEEDS = st.integers(min_value=0, max_value=10_000)
 
 
-@settings(max_examples=12, deadline=None)
+@settings(max_examples=12, deadline=None, derandomize=True)
 @given(seed=SEEDS, n=st.integers(min_value=8, max_value=40), pairs=st.booleans())
 def test_adjoint_identity_and_energy(seed, n, pairs):
     sc = scenes.random_cluster(n=n, seed=seed, L=2, nd=32, nb=2, n_lights=1)
@@ -34,7 +34,7 @@ def test_adjoint_identity_and_energy(seed, n, pairs):
         assert np.all(sums <= 1.0 + 1e-12) and np.all(np.asarray(h["a"]) >= 0.0)
 
 
-@settings(max_examples=10, deadline=None)
+@settings(max_examples=10, deadline=None, derandomize=True)
 @given(seed=SEEDS, yaw=st.floats(-math.pi, math.pi), pitch=st.floats(-1.2, 1.2))
 def test_render_transpose_on_random_cameras(seed, yaw, pitch):
     sc = scenes.random_cluster(n=30, seed=seed, L=2, nd=32, nb=1, n_lights=1)
@@ -50,7 +50,7 @@ def test_render_transpose_on_random_cameras(seed, yaw, pitch):
     assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12)
 
 
-@settings(max_examples=6, deadline=None)
+@settings(max_examples=6, deadline=None, derandomize=True)
 @given(seed=SEEDS)
 def test_geometry_gradient_along_a_random_direction(seed):
     """dL/dp . delta equals the central difference of L along delta (all centres moved)."""
@@ -77,7 +77,7 @@ def test_geometry_gradient_along_a_random_direction(seed):
     assert cd1 == pytest.approx(an, rel=1e-5, abs=1e-7 * (1 + abs(loss(0))))
 
 
-@settings(max_examples=30, deadline=None)
+@settings(max_examples=30, deadline=None, derandomize=True)
 @given(x=st.floats(-1, 1), y=st.floats(-1, 1), z=st.floats(-1, 1), L=st.integers(1, 3))
 def test_sh_gradient_tangential_part(x, y, z, L):
     w = np.array([x, y, z])
