@@ -1,6 +1,8 @@
 """Convenience layer over the C-ABI binding: upload a scene, run build -> trace -> solve
--> adjoint, and a torch.autograd.Function differentiable in emission, diffuse albedo and
-opacity.  Every numerical step is a librgs.so kernel; this module only moves tensors.
+-> adjoint, and torch.autograd.Functions differentiable in emission, diffuse albedo and
+opacity (radiosity) and also in the surfels' centres, scales and frames
+(radiosity_geometry).  Every numerical step is a librgs.so kernel; this module only moves
+tensors.
 """
 from __future__ import annotations
 
@@ -114,3 +116,34 @@ class RadiositySolve(torch.autograd.Function):
 
 def radiosity(E, ad, o, geom, nb, alpha_model=rgs.RGS_ALPHA_GAUSS):
     return RadiositySolve.apply(E, ad, o, geom, nb, alpha_model)
+
+
+class RadiositySolveGeometry(torch.autograd.Function):
+    """B = solve(E, a^d, o, p, s, tu, tv; the rest of the scene and the lights) with gradients
+    with respect to all seven (Eqs. final_dL_dE, final-dl-dbrdf, dl-dgeo-0/1).
+
+    forward rebuilds the scene from the given tensors, traces and runs n bounces (every
+    iterate kept: the hemisphere form's geometry gradients read them all); backward runs
+    rgs_adjoint_geometry."""
+
+    @staticmethod
+    def forward(ctx, E, ad, o, p, s, tu, tv, geom, nb, alpha_model=rgs.RGS_ALPHA_GAUSS, pairs=False):
+        d = dict(geom)
+        for key, v in (("ad", ad), ("o", o), ("p", p), ("s", s), ("tu", tu), ("tv", tv)):
+            d[key] = v.detach().contiguous()
+        pipe = Pipeline(alpha_model, pairs=pairs)
+        pipe.build(d)
+        pipe.trace(d)
+        B, _ = pipe.solve(E.detach().contiguous() if E is not None else None, int(nb))
+        ctx.pipe = pipe
+        return B
+
+    @staticmethod
+    def backward(ctx, gB):
+        dE, dad, do, dp, ds, dtu, dtv = ctx.pipe.adjoint_geometry(gB.contiguous())
+        return dE, dad, do, dp, ds, dtu, dtv, None, None, None, None
+
+
+def radiosity_geometry(E, ad, o, p, s, tu, tv, geom, nb, alpha_model=rgs.RGS_ALPHA_GAUSS, pairs=False):
+    """B differentiable in emission, albedo, opacity, centres, scales and frame inputs."""
+    return RadiositySolveGeometry.apply(E, ad, o, p, s, tu, tv, geom, nb, alpha_model, pairs)
