@@ -17,6 +17,10 @@
  *   Eq. before-final-radiosity / final-radiosity (Sec. 5.3), solid-angle form App. B
  *   Eq. final_dL_dE  adjoint (dual) transport (Sec. 6, App. C)
  *   Eq. final-dl-dbrdf closed-form BRDF gradient (limit n -> infinity)
+ *   Eqs. dl-dgeo-0/1 geometry gradients (centres, scales, frames) of both transports
+ *   Sec. 8           the center-to-center approximation (App. E: the GFSGS alpha, Ein)
+ *   Sec. 7, Alg. 1   progressive refinement, the Monte-Carlo TD(0) solver, their hybrid
+ *   Eq. L_I          image formation for a pinhole camera, and its transpose
  *
  * Readings taken where the paper is silent (each is listed in the design notes):
  *   - kappa_i is a Dirac at p_i, so alpha_i(p_i)/Lambda_i * int kappa = o_i, and the
