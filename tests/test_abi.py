@@ -56,6 +56,12 @@ def test_argument_validation_without_device_work():
     assert L.rgs_solve(None, None, 1, 0, None, None, None) == 1
     assert L.rgs_adjoint(None, None, None, None, None, None) == 1
     assert L.rgs_get_iterate(None, 0, None, None) == 1
+    # the center-to-center and geometry entry points on NULL handles
+    assert L.rgs_trace_pairs(None, None, None, None, ct.byref(h)) == 1
+    assert L.rgs_adjoint_pairs(None, None, None, None, None, None, None) == 1
+    assert L.rgs_adjoint_pairs_geometry(None, None, None, None, None, None, None, None, None, None, None) == 1
+    assert L.rgs_adjoint_geometry(None, None, None, None, None, None, None, None, None, None) == 1
+    assert b"NULL" in L.rgs_last_error()
     L.rgs_destroy_scene(None)
     L.rgs_destroy_transport(None)
 
