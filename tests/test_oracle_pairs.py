@@ -167,3 +167,38 @@ def test_gradients_match_finite_differences():
                 return loss(perturb(key, idx, hh), lam)
         num = fd(f)
         assert abs(num - an) <= 1e-6 * scale[key], (key, idx, num, an)
+
+
+def test_center_to_center_is_the_small_surfel_limit_of_the_hemisphere_transport():
+    """Sec. 8 replaces the area integral of Eq. before-final-radiosity by one segment
+    between centres, an approximation for surfels small against their distance.  A glossy
+    receiver and a tilted, off-axis Gaussian emitter of scale s at distance D: the two
+    transports' B^(1) must differ by a term of second order in s/D (the 1/r^2 and cosine
+    factors vary quadratically across the emitter), so (B_hemi / B_pairs - 1)(D/s)^2 stays
+    the same constant at every distance.  A constant relative error in either transport (a
+    lost factor of the alpha integral, a cosine, 1/pi) adds a term growing like (D/s)^2 and
+    breaks that.  2^20 stratified rays keep the hemisphere estimate's own error below a
+    tenth of the compared term."""
+    s, L, nc = 0.08, 2, 9
+    d = np.array([0.5, 0.2, 1.0]) / np.linalg.norm([0.5, 0.2, 1.0])
+    nrm = -d + np.array([0.3, -0.1, 0.0])
+    nrm /= np.linalg.norm(nrm)
+    tu = np.cross(nrm, [0.0, 1.0, 0.0])
+    tu /= np.linalg.norm(tu)
+    tv = np.cross(nrm, tu)
+    E = np.zeros((2, nc, 3))
+    E[1, 0], E[1, 2], E[1, 3] = (1.0, 2.0, 3.0), (0.4, 0.1, -0.2), (0.2, -0.3, 0.1)
+    c00, chigh = [], []
+    for D in (0.5, 0.7, 1.0, 1.4):
+        sc = make_scene([dict(p=(0, 0, 0), tu=(1, 0, 0), tv=(0, 1, 0), k=0.6, as_=(0.3, 0.3, 0.3), shin=3.0),
+                         dict(p=D * d, tu=tu, tv=tv, s=(s, 0.6 * s), o=0.9)], L=L, nd=1 << 20, E=E)
+        Bh = O.Oracle(sc).transport().solve(E=sc["E"], nb=1)[0]
+        Bp = O.Oracle(sc).pairs().solve(E=sc["E"], nb=1)[0]
+        k = (D / s) ** 2
+        c00.append((Bh[0] / Bp[0] - 1.0) * k)
+        q = np.argmax(np.abs(Bp[1:]))
+        chigh.append((Bh[1:] - Bp[1:]).ravel()[q] / np.abs(Bp[1:]).ravel()[q] * k)
+    c00, chigh = np.array(c00), np.array(chigh)
+    assert np.all(np.abs(c00) < 4.0) and np.all(np.abs(chigh) < 4.0)
+    np.testing.assert_allclose(c00, np.broadcast_to(c00.mean(axis=0), c00.shape), rtol=0.15)
+    np.testing.assert_allclose(chigh, chigh.mean(), rtol=0.15)
