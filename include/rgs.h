@@ -389,7 +389,8 @@ typedef struct rgs_kernel_time {
 void rgs_profile_enable(int32_t on);
 void rgs_profile_reset(void);
 /* Writes up to max entries to out (host); returns the number of kernel names seen, or -1
- * if an event could not be read (see rgs_last_error).  Synchronises on the events. */
+ * if out is NULL with max > 0 or an event could not be read (see rgs_last_error).
+ * Synchronises on the events. */
 int32_t rgs_profile_report(rgs_kernel_time *out, int32_t max);
 int64_t rgs_launch_count(void);
 

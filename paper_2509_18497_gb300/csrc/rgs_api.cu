@@ -187,6 +187,10 @@ void rgs_profile_reset(void) {
 }
 
 int32_t rgs_profile_report(rgs_kernel_time *out, int32_t max) {
+    if (!out && max > 0) {
+        rgs_set_error("rgs_profile_report: NULL output array with max = %d", max);
+        return -1;
+    }
     std::lock_guard<std::mutex> lk(g_prof_mu);
     std::vector<double> ms(g_names.size(), 0.0);
     std::vector<long long> cnt(g_names.size(), 0);

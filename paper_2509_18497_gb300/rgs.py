@@ -416,8 +416,11 @@ def rgs_residual_norm_noalloc(x, y, norm_out=None, stream=None):
 def rgs_solve_batched(transports, E_list, n_bounces, precision=RGS_FP32, use_graph=True, autotune=True,
                       spin_limit=0, B_outs=None, norms=False, stream=None):
     """rgs_solve_batched over a list of traced Transport objects; returns (list of B tensors, norms or None)."""
-    L = load()
     m = len(transports)
+    for name, seq in (("n_bounces", n_bounces), ("E_list", E_list), ("B_outs", B_outs)):
+        if seq is not None and len(seq) != m:
+            raise ValueError(f"{name}: {len(seq)} entries for {m} transports")
+    L = load()
     hs = (ct.c_void_p * m)(*[t.h.value for t in transports])
     Es = None
     if E_list is not None:

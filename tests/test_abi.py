@@ -66,6 +66,43 @@ def test_argument_validation_without_device_work():
     L.rgs_destroy_transport(None)
 
 
+def test_service_entry_points_reject_bad_arguments_without_device_work():
+    L = rgs.load()
+    one = (ct.c_int32 * 1)(1)
+    hs = (ct.c_void_p * 1)(None)
+    # empty, oversized and NULL batches; a NULL transport inside a batch
+    assert L.rgs_solve_batched(None, 1, None, one, None, None, None, None) == 1
+    assert L.rgs_solve_batched(hs, 0, None, one, None, None, None, None) == 1
+    assert L.rgs_solve_batched(hs, 4097, None, one, None, None, None, None) == 1
+    assert L.rgs_solve_batched(hs, 1, None, None, None, None, None, None) == 1
+    assert L.rgs_solve_batched(hs, 1, None, one, None, None, None, None) == 1
+    assert b"NULL" in L.rgs_last_error()
+    assert L.rgs_set_checkpointing(None, 2) == 1
+    assert L.rgs_set_memory_budget(None, 1 << 20) == 1
+    assert L.rgs_transport_info_get(None, None) == 1
+    # the no-allocation norm: NULL arrays, negative and oversized lengths
+    p = ct.c_void_p(16)
+    assert L.rgs_residual_norm_noalloc(None, p, 1, p, None) == 1
+    assert L.rgs_residual_norm_noalloc(p, p, -1, p, None) == 1
+    assert L.rgs_residual_norm_noalloc(p, p, 1 << 40, p, None) == 1
+    assert b"outside" in L.rgs_last_error()
+    # the profiler's report wants an array when asked for entries
+    assert L.rgs_profile_report(None, 4) == -1
+    assert L.rgs_profile_report(None, 0) >= 0
+
+
+def test_binding_checks_before_any_library_call():
+    torch = pytest.importorskip("torch")
+    cpu = torch.zeros(4, 3)
+    with pytest.raises(TypeError, match="CUDA"):
+        rgs.rgs_build_scene(cpu, cpu, cpu, torch.zeros(4, 2), torch.zeros(4), cpu, torch.zeros(4), cpu,
+                            torch.zeros(4), 2)
+    with pytest.raises(ValueError, match="n_bounces"):
+        rgs.rgs_solve_batched([object(), object()], None, [3])
+    with pytest.raises(ValueError, match="E_list"):
+        rgs.rgs_solve_batched([object()], [None, None], [3])
+
+
 def test_oracle_library_builds():
     from oracle import oracle as O
     assert os.path.exists(O.build())
