@@ -222,3 +222,23 @@ def test_hybrid_solver_lowers_the_variance(cluster):
     # with nothing left unshot the hybrid returns the shooting result itself
     Bh, dB = orc.prog_refine(400, E=sc["E"])
     np.testing.assert_allclose(orc.hybrid_solve(400, 16, E=sc["E"]), Bh, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,G", [(24, 3), (24, 6), (300, 8), (300, 20)])
+def test_kmeans_groups_equal_an_independent_lloyd(n, G):
+    """The grouping of the next-event proposal (App. "Monte-Carlo Solver Details": K-means
+    over the surfels) is Lloyd's algorithm on (centre, extent/2 * normal) features from
+    evenly spaced seeds.  scikit-learn's Lloyd iteration from the same seeds, run to a
+    fixed point, must give the same assignment."""
+    cluster_mod = pytest.importorskip("sklearn.cluster")
+    sc = scenes.random_cluster(n=n, seed=2, L=2, nb=3, n_lights=1)
+    got = O.Oracle(sc).mc_groups(G)
+    p = sc["p"].astype(float)
+    nrm = np.cross(sc["tu"].astype(float), sc["tv"].astype(float))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    ext = max(float((p.max(axis=0) - p.min(axis=0)).max()), 1e-12)
+    feats = np.hstack([p, 0.5 * ext * nrm])
+    seeds = feats[[k * n // G for k in range(G)]]
+    km = cluster_mod.KMeans(n_clusters=G, init=seeds, n_init=1, algorithm="lloyd", max_iter=50, tol=0.0).fit(feats)
+    assert len(set(got)) == G
+    np.testing.assert_array_equal(got, km.labels_)
