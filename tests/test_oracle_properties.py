@@ -1,7 +1,7 @@
 """Property checks of the oracle over generated inputs (hypothesis): the adjoint identity
 and energy bounds on random clusters, the render transpose on random cameras, the
 geometry gradient along random directions against a central difference, and the SH
-gradient's tangential part (no GPU)."""
+gradient's tangential part, and the shooting invariant of progressive refinement (no GPU)."""
 import math
 
 import numpy as np
@@ -90,3 +90,19 @@ def test_sh_gradient_tangential_part(x, y, z, L):
     h = 1e-5
     num = (O.sh_eval(L, (w + h * t) / np.linalg.norm(w + h * t)) - O.sh_eval(L, (w - h * t) / np.linalg.norm(w - h * t))) / (2 * h)
     np.testing.assert_allclose(dY.T @ t, num, atol=1e-8)
+
+
+@settings(max_examples=12, deadline=None, derandomize=True)
+@given(seed=SEEDS, n=st.integers(min_value=8, max_value=30), shots=st.integers(min_value=0, max_value=60))
+def test_shooting_invariant_on_random_clusters(seed, n, shots):
+    """Progressive refinement (Sec. 7) keeps Bhat = S + K (Bhat - dB) after every shot: what
+    each surfel has received is the source plus the transport of everything already shot.
+    Multiplying Sec. 7's decomposition B = Bhat + (I - K)^-1 dB - dB by (I - K) gives
+    exactly this, so it holds for any scene and shot count, checked here with the
+    gather-form K that the shooting code does not use."""
+    sc = scenes.with_emission(scenes.random_cluster(n=n, seed=seed, L=2, nd=32, nb=2, n_lights=1), seed=seed + 1)
+    orc = O.Oracle(sc).pairs()
+    S = orc.solve(E=sc["E"], nb=0)
+    Bh, dB = orc.prog_refine(shots, E=sc["E"])
+    rhs = S + orc.apply_K(Bh - dB)[0]
+    assert np.linalg.norm(Bh - rhs) <= 1e-12 * max(np.linalg.norm(S), 1e-300)
