@@ -1,6 +1,6 @@
 """Property checks of the oracle over generated inputs (hypothesis): the adjoint identity
 and energy bounds on random clusters, the render transpose on random cameras, the
-geometry gradient along random directions against a central difference, and the SH
+geometry gradient along random directions against a central difference, the SH
 gradient's tangential part, and the shooting invariant of progressive refinement (no GPU)."""
 import math
 
