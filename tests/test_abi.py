@@ -106,3 +106,26 @@ def test_binding_checks_before_any_library_call():
 def test_oracle_library_builds():
     from oracle import oracle as O
     assert os.path.exists(O.build())
+
+
+def test_plain_c_client_compiles_links_and_runs(tmp_path):
+    """include/rgs.h is a C header: a C99 client (tests/abi_c_client.c) compiles with
+    -pedantic -Werror, links against librgs.so and runs the device-free entry points; the
+    same header also compiles as C++."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.dirname(build.build())
+    exe = str(tmp_path / "abi_c_client")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "abi_c_client.c"), "-o", exe, "-L", lib_dir, "-lrgs",
+                    "-Wl,-rpath," + lib_dir], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    assert "ok" in out
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is not None:
+        subprocess.run([cxx, "-std=c++11", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", "c++",
+                        "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_c_client.c")], check=True)
