@@ -226,6 +226,10 @@ rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE,
  *   dL_dtu, dL_dtv : device [N][3] (dL/dtu_i, dL/dtv_i of the frame inputs) or NULL.
  *   the rest as rgs_adjoint_pairs (every output may be NULL).
  * Asynchronous.  Errors as rgs_adjoint_pairs. */
+rgs_status rgs_adjoint_pairs_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
+                                      float *dL_dopacity, float *dL_dlambda, float *dL_dp, float *dL_ds,
+                                      float *dL_dtu, float *dL_dtv, void *stream);
+
 /* rgs_adjoint with the geometry gradients as well (Sec. 6, Eqs. dl-dgeo-0/1, App. C),
  * for either transport (a center-to-center transport gives what rgs_adjoint_pairs_geometry
  * gives, without dL/dlambda).  For the hemisphere rays (rgs_trace_transport):
@@ -245,10 +249,6 @@ rgs_status rgs_adjoint_pairs(rgs_transport *t, const float *dL_dB, float *dL_dE,
 rgs_status rgs_adjoint_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
                                 float *dL_dopacity, float *dL_dp, float *dL_ds, float *dL_dtu, float *dL_dtv,
                                 void *stream);
-
-rgs_status rgs_adjoint_pairs_geometry(rgs_transport *t, const float *dL_dB, float *dL_dE, float *dL_dalbedo,
-                                      float *dL_dopacity, float *dL_dlambda, float *dL_dp, float *dL_ds,
-                                      float *dL_dtu, float *dL_dtv, void *stream);
 
 /* Runs B^(0) = S = E + D, B^(k) = S + K B^(k-1) for k = 1..n_bounces with
  * (K B)_i = o_i c_i (x) sum_r (pi/nd) Y(R_i d_r) sum_h a_rh Y(-d_r)^T B_{j_h}
