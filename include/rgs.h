@@ -185,8 +185,9 @@ rgs_status rgs_trace_transport(rgs_scene *scene, const rgs_lights *lights, const
  * over the sources j lying more than eps_plane in front of receiver i's plane.  T_ij is the
  * product of (1 - alpha_k) over the surfels k != i, j the open segment meets under the
  * hemisphere-ray hit rules whose plane lies more than eps_plane from p_j as well.
- * int alpha_j dx = 2 pi s^u s^v o (1 - e^{-9/2}) (Gaussian to 3 sigma) or pi s^u s^v o
- * (disc).  The direct term is that of rgs_trace_transport.  The result is a transport
+ * int alpha_j dx = 2 pi s^u s^v o (1 - e^{-9/2}) (Gaussian to 3 sigma), pi s^u s^v o
+ * (disc) or, for the GFSGS model, App. E's closed form (2 pi / 3.4) s^u s^v Ein(c) with
+ * c = 0.03279 o^3.4 and Ein(c) = int_0^c (1 - e^{-y}) / y dy.  The direct term is that of rgs_trace_transport.  The result is a transport
  * handle that rgs_solve, rgs_get_iterate and rgs_adjoint accept (every iterate is kept;
  * rgs_solve_batched does not take it).  Cost: N^2 front tests and one segment trace per
  * front pair; memory 8 bytes per pair.
