@@ -269,7 +269,8 @@ rgs_status rgs_solve(rgs_transport *t, const float *E, int32_t n_bounces, int32_
  * paper's Eq. final_dL_dE / final-dl-dbrdf are its n -> infinity limit):
  *   v^(0) = dL/dB, v^(a) = K^T v^(a-1), u = sum_a v^(a) = dL/dS
  *   dL/dE[i][k][ch]  = sum over lights of u                                 (device [N][nc][3])
- *   dL/da^d[i][ch]   = 4 k_i o_i sum_{light} ( sum_a v^(a) Q^(n-1-a) + u Dgeo )_00  (device [N][3])
+ *   dL/da^d[i][ch]   = 4 k_i alpha_i sum_{light} ( sum_a v^(a) Q^(n-1-a) + u Dgeo )_00  (device [N][3]),
+ *                      alpha_i = alpha_i(p_i): o_i, or 1 - exp(-0.03279 o_i^3.4) for GFSGS
  *   dL/do[i]         = receiver factor + backward through the compositing of every
  *                      hemisphere and shadow ray that hits surfel i           (device [N])
  * Each output may be NULL (not computed).  dL_dB: device [N][nc][C].
