@@ -37,11 +37,15 @@ def build(force=False):
 
 
 def lib():
+    """The loaded oracle library.  ORACLE_LIB names a prebuilt copy to load instead (the
+    mutation tests run the pins against deliberately broken builds of oracle.c)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ct.CDLL(_LIB)
+            path = os.environ.get("ORACLE_LIB")
+            if not path:
+                path = build()
+            L = ct.CDLL(path)
             L.or_scene_new.restype = ct.c_void_p
             L.or_scene_new.argtypes = [ct.c_int, ct.c_int] + [_dp] * 9 + [ct.c_int, ct.c_int]
             L.or_scene_free.argtypes = [ct.c_void_p]

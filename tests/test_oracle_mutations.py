@@ -1,0 +1,132 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Each entry below copies oracle.c with one plausible mistake (a dropped term, a wrong sign,
+factor or index, a missing rule of the hit test), compiles the copy on the CPU and runs the
+pin files that should catch it against that library (ORACLE_LIB).  Every mutant has to make
+at least one pin fail: a pin set that lets a mistake through is not pinning that part.  The
+unmutated oracle passes the same files in the rest of the suite (no GPU)."""
+import concurrent.futures
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+# (mistake, text in oracle.c, replacement, pin files that must catch it)
+MUTANTS = [
+    # hemisphere transport (Eq. L_I, Sec. 5.2)
+    ("compositing drops the (1 - alpha) of nearer hits",
+     "            s->hit_a[e] = per[r].h[q].alpha * T;\n            T *= (1.0 - per[r].h[q].alpha);",
+     "            s->hit_a[e] = per[r].h[q].alpha * T;\n            T *= 1.0;", ["transport"]),
+    ("shadow rays ignore occluders",
+     "for (int q = 0; q < hv->cnt; ++q) T *= (1.0 - hv->h[q].alpha);",
+     "for (int q = 0; q < hv->cnt; ++q) T *= 1.0;", ["transport"]),
+    ("direct term evaluates the lobe without the reflection R_i",
+     "            reflect(s->nrm + i * 3, w, rw);\n            or_sh_eval(L, rw, Y);\n            for (int kk = 0; kk < nc; ++kk)\n"
+     "                for (int ch = 0; ch < 3; ++ch)\n                    s->Dgeo",
+     "            memcpy(rw, w, sizeof rw);\n            or_sh_eval(L, rw, Y);\n            for (int kk = 0; kk < nc; ++kk)\n"
+     "                for (int ch = 0; ch < 3; ++ch)\n                    s->Dgeo", ["transport"]),
+    ("the gather reads the source's radiance along d instead of -d",
+     "            for (int q = 0; q < 3; ++q) md[q] = -d[q];\n            reflect(s->nrm + i * 3, d, rd);\n"
+     "            or_sh_eval(L, md, Yo);\n            or_sh_eval(L, rd, Yi);\n            long ray = (long)i * nd + r;\n"
+     "            for (int c = 0; c < C; ++c) x[c] = 0.0;",
+     "            for (int q = 0; q < 3; ++q) md[q] = d[q];\n            reflect(s->nrm + i * 3, d, rd);\n"
+     "            or_sh_eval(L, md, Yo);\n            or_sh_eval(L, rd, Yi);\n            long ray = (long)i * nd + r;\n"
+     "            for (int c = 0; c < C; ++c) x[c] = 0.0;", ["transport"]),
+    ("no eps_plane rule for planes through the ray origin",
+     "    if (fabs(h) <= s->eps_plane) return;", "    (void)h;", ["transport"]),
+    ("no tie runs for near-equal depths",
+     "            if (e > k) qsort(out->h + k, (size_t)(e - k + 1), sizeof(or_hit), cmp_hit_j);",
+     "            (void)cmp_hit_j;", ["transport"]),
+    ("Gaussian exp(-r^2) instead of exp(-r^2 / 2)",
+     "        G = exp(-0.5 * r2);\n    }\n    or_hit x", "        G = exp(-r2);\n    }\n    or_hit x",
+     ["transport", "pairs"]),
+    ("point light falls off as 1/r instead of 1/r^2",
+     "    return s->ldir ? cs : cs / (len * len);", "    return s->ldir ? cs : cs / len;", ["transport"]),
+    ("albedo gradient without the blend weight k",
+     "dad[i * 3 + ch] = 4.0 * s->k[i] * alpha_c(s, i) * P[", "dad[i * 3 + ch] = 4.0 * alpha_c(s, i) * P[",
+     ["transport"]),
+    ("albedo gradient pairs v^(a) with Q^(a) instead of Q^(n-1-a)",
+     "acc += v[(size_t)a * M + idx] * Q[(size_t)(nb - 1 - a) * M + idx];",
+     "acc += v[(size_t)a * M + idx] * Q[(size_t)a * M + idx];", ["transport"]),
+    # BRDF, SH, ray keys (Eq. brdf, App. A, App. B)
+    ("diffuse coefficient k a^d instead of 4 k a^d",
+     "4.0 * k * ad[ch] + (1.0 - k) * as[ch]", "k * ad[ch] + (1.0 - k) * as[ch]", ["math"]),
+    ("Phong factor of odd bands with a shifted denominator",
+     "for (int q = 2; q <= l + 1; q += 2) den *= (s + q);", "for (int q = 2; q <= l + 1; q += 2) den *= (s + q + 1);",
+     ["math"]),
+    ("SH without the Condon-Shortley phase",
+     "for (int q = 1; q <= m; ++q) pmm *= -(2.0 * q - 1.0); /* (-1)^m",
+     "for (int q = 1; q <= m; ++q) pmm *= (2.0 * q - 1.0); /* (-1)^m", ["math"]),
+    ("SplitMix64 with a wrong multiplier",
+     "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 27)) * 0x94D049BB133111EDULL;", ["math"]),
+    # center-to-center transport (Sec. 8, App. E)
+    ("pair transport without the source's cosine",
+     "double geo = fabs(dot3(s->nrm + i * 3, d)) * fabs(dot3(s->nrm + j * 3, d)) / r2;",
+     "double geo = fabs(dot3(s->nrm + i * 3, d)) / r2;", ["pairs"]),
+    ("pair segments ignore occluders",
+     "for (int q = 0; q < occ[e].cnt; ++q) T *= 1.0 - occ[e].h[q].alpha;",
+     "for (int q = 0; q < occ[e].cnt; ++q) T *= 1.0;", ["pairs"]),
+    ("Ein series without its alternating sign",
+     "            term *= -x / k;", "            term *= x / k;", ["gfsgs"]),
+    # geometry gradients (Eqs. dl-dgeo-0/1)
+    ("crossing point's normal derivative with the wrong sign",
+     "const double fn = -dot3(gx, d) / dot3(nk, d);", "const double fn = dot3(gx, d) / dot3(nk, d);", ["geometry"]),
+    ("decay term's distance derivative -geo/r instead of -2 geo/r",
+     "const double gr = ge * lam * A * T * (-2.0 * geo / r);", "const double gr = ge * lam * A * T * (-geo / r);",
+     ["geometry"]),
+    ("source scale gradient dropped",
+     "            ds[j * 2] += ge * lam * T * geo * A / s->su[j];", "            ds[j * 2] += 0.0 * ge;", ["geometry"]),
+    # Monte-Carlo solver, progressive refinement (Sec. 7, Alg. 1)
+    ("one-point estimate without the 1/p weight",
+     "                                s->pair_V[e] * sv / p;", "                                s->pair_V[e] * sv;",
+     ["mc"]),
+    ("reservoir keeps candidates with twice their probability",
+     "if (mc_u(seed, (uint64_t)t, (uint64_t)q, 1000 + (uint64_t)k) * W < w[k]) pick = k;",
+     "if (mc_u(seed, (uint64_t)t, (uint64_t)q, 1000 + (uint64_t)k) * W < 2.0 * w[k]) pick = k;", ["mc"]),
+    ("visit count advances by two",
+     "            D[a] += 1.0;", "            D[a] += 2.0;", ["mc"]),
+    ("shooting leaves the shot radiance unshot",
+     "        memset(dB + (size_t)best * R, 0, sizeof(double) * R);", "        (void)best;", ["mc"]),
+    # image formation (Eq. L_I for a camera)
+    ("camera rays ignore the transmittance of nearer surfels",
+     "                T *= 1.0 - hv.h[h].alpha;\n                const int j = hv.h[h].j;",
+     "                T *= 1.0;\n                const int j = hv.h[h].j;", ["render"]),
+]
+
+
+def _run_mutant(tmp, index, old, new, files):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutant {index}: the text to replace must occur exactly once"
+    c_path = os.path.join(tmp, f"mutant{index}.c")
+    so_path = os.path.join(tmp, f"mutant{index}.so")
+    with open(c_path, "w") as f:
+        f.write(src.replace(old, new, 1))
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", so_path, c_path, "-lm"],
+                   check=True, capture_output=True)
+    env = dict(os.environ, ORACLE_LIB=so_path, OMP_NUM_THREADS="2")
+    paths = [os.path.join(ROOT, "tests", f"test_oracle_{f}.py") for f in files]
+    proc = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *paths],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return proc.returncode, proc.stdout[-2000:]
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    workers = max(1, min(4, (os.cpu_count() or 2) // 2))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        futs = [ex.submit(_run_mutant, str(tmp_path), q, old, new, files)
+                for q, (_, old, new, files) in enumerate(MUTANTS)]
+        results = [f.result() for f in futs]
+    survived = []
+    for (name, _, _, files), (rc, out) in zip(MUTANTS, results):
+        # 1: a pin failed; a negative code: the mutant crashed the run.  0 means it went
+        # unnoticed; 2-5 mean pytest itself could not run the files.
+        if rc == 0 or rc in (2, 3, 4, 5):
+            survived.append(f"{name} (files {files}, exit {rc}):\n{out}")
+    assert not survived, "planted mistakes the pins did not catch:\n" + "\n".join(survived)
