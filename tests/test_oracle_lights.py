@@ -36,6 +36,24 @@ def test_lone_plane_directional_closed_form():
     np.testing.assert_allclose(D[0, 1:, :], 0.0, atol=1e-15)
 
 
+def test_directional_shadow_ray_reaches_any_distance():
+    """A directional light's shadow ray runs to infinity whatever the length of the given
+    direction: a Gaussian occluder 3 units above the receiver, crossed at (dx/s^u, 0) in its
+    own frame, multiplies D by 1 - o exp(-(dx/s^u)^2 / 2) although the direction vector is
+    only 0.1 long."""
+    dx, su, o = 0.02, 0.05, 0.6
+    w = np.array([0.0, 0.0, 0.1])
+    base = make_scene([dict(p=(0, 0, 0), tu=(1, 0, 0), tv=(0, 1, 0), k=1.0, o=0.8),
+                       dict(p=(dx, 0, 3.0), tu=(1, 0, 0), tv=(0, -1, 0), s=(su, 0.05), o=o)])
+    lit = _directional(base, [w], [[2.0, 3.0, 4.0]])
+    D = O.Oracle(lit).transport().direct()
+    free = _directional(make_scene([dict(p=(0, 0, 0), tu=(1, 0, 0), tv=(0, 1, 0), k=1.0, o=0.8)]), [w],
+                        [[2.0, 3.0, 4.0]])
+    D0 = O.Oracle(free).transport().direct()
+    T = 1.0 - o * math.exp(-0.5 * (dx / su) ** 2)
+    np.testing.assert_allclose(D[0], D0[0] * T, rtol=1e-12, atol=1e-15)
+
+
 def test_far_point_light_limit():
     """A point light at distance R along w with intensity I R^2 tends to the directional
     light of intensity I, with an O(size/R) error, in every band (glossy receivers)."""

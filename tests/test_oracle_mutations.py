@@ -50,6 +50,11 @@ MUTANTS = [
     ("albedo gradient without the blend weight k",
      "dad[i * 3 + ch] = 4.0 * s->k[i] * alpha_c(s, i) * P[", "dad[i * 3 + ch] = 4.0 * alpha_c(s, i) * P[",
      ["transport"]),
+    ("compositing backward without the later hits' share R",
+     "                    double dalpha = Th[h] * (gh[h] - R);", "                    double dalpha = Th[h] * gh[h];",
+     ["transport"]),
+    ("directional light's shadow ray stops at the direction vector's length",
+     "    *r = s->ldir ? INFINITY : len;", "    *r = len;", ["lights"]),
     ("albedo gradient pairs v^(a) with Q^(a) instead of Q^(n-1-a)",
      "acc += v[(size_t)a * M + idx] * Q[(size_t)(nb - 1 - a) * M + idx];",
      "acc += v[(size_t)a * M + idx] * Q[(size_t)a * M + idx];", ["transport"]),
@@ -71,6 +76,10 @@ MUTANTS = [
     ("pair segments ignore occluders",
      "for (int q = 0; q < occ[e].cnt; ++q) T *= 1.0 - occ[e].h[q].alpha;",
      "for (int q = 0; q < occ[e].cnt; ++q) T *= 1.0;", ["pairs"]),
+    ("lambda gradient without the alpha integral",
+     "if (dlam) dlam[j] += g * A * T * geo;", "if (dlam) dlam[j] += g * T * geo;", ["pairs"]),
+    ("GFSGS opacity derivative without the exponent 3.4",
+     "        return exp(-p) * 3.4 * p / o;", "        return exp(-p) * p / o;", ["gfsgs"]),
     ("Ein series without its alternating sign",
      "            term *= -x / k;", "            term *= x / k;", ["gfsgs"]),
     # geometry gradients (Eqs. dl-dgeo-0/1)
@@ -78,6 +87,9 @@ MUTANTS = [
      "const double fn = -dot3(gx, d) / dot3(nk, d);", "const double fn = dot3(gx, d) / dot3(nk, d);", ["geometry"]),
     ("decay term's distance derivative -geo/r instead of -2 geo/r",
      "const double gr = ge * lam * A * T * (-2.0 * geo / r);", "const double gr = ge * lam * A * T * (-geo / r);",
+     ["geometry"]),
+    ("occluder scale derivative with half its factor",
+     "        ds[k * 2] += coef * (-2.0 * u * u / s->su[k]);", "        ds[k * 2] += coef * (-u * u / s->su[k]);",
      ["geometry"]),
     ("source scale gradient dropped",
      "            ds[j * 2] += ge * lam * T * geo * A / s->su[j];", "            ds[j * 2] += 0.0 * ge;", ["geometry"]),
