@@ -45,6 +45,25 @@ MUTANTS = [
     ("Gaussian exp(-r^2) instead of exp(-r^2 / 2)",
      "        G = exp(-0.5 * r2);\n    }\n    or_hit x", "        G = exp(-r2);\n    }\n    or_hit x",
      ["transport", "pairs"]),
+    ("3-sigma cutoff at 2 sigma",
+     "        if (r2 > 9.0) return;\n        G = exp(-0.5 * r2);", "        if (r2 > 4.0) return;\n        G = exp(-0.5 * r2);",
+     ["transport", "pairs", "gfsgs", "lights"]),
+    ("disc model of radius 2",
+     "        if (r2 > 1.0) return;\n        G = 1.0;", "        if (r2 > 4.0) return;\n        G = 1.0;",
+     ["transport", "pairs"]),
+    ("BVH slab test keeps the far slab distance as the entry",
+     "        if (ta > t0) t0 = ta;", "        if (ta > t0) t0 = tb;", ["transport", "pairs"]),
+    ("Malley mapping with radius sqrt(1 - u)",
+     "    double rr = sqrt(u1), ph = 2.0 * OR_PI * u2;", "    double rr = sqrt(1.0 - u1), ph = 2.0 * OR_PI * u2;",
+     ["math", "transport"]),
+    ("strata indices swapped",
+     "    int a = r / nb, b = r % nb;", "    int a = r % na, b = r / na;", ["math"]),
+    ("rays in the world frame instead of the receiver's",
+     "    for (int q = 0; q < 3; ++q) d[q] = c[0] * s->tu[i * 3 + q] + c[1] * s->tv[i * 3 + q] + c[2] * s->nrm[i * 3 + q];",
+     "    for (int q = 0; q < 3; ++q) d[q] = c[q];", ["transport", "math"]),
+    ("lights behind the receiver contribute",
+     "    if (!(cs > 0.0)) return 0.0; /* only the front hemisphere Omega receives */", "    /* none */",
+     ["transport", "lights"]),
     ("point light falls off as 1/r instead of 1/r^2",
      "    return s->ldir ? cs : cs / (len * len);", "    return s->ldir ? cs : cs / len;", ["transport"]),
     ("albedo gradient without the blend weight k",
@@ -76,6 +95,14 @@ MUTANTS = [
     ("pair segments ignore occluders",
      "for (int q = 0; q < occ[e].cnt; ++q) T *= 1.0 - occ[e].h[q].alpha;",
      "for (int q = 0; q < occ[e].cnt; ++q) T *= 1.0;", ["pairs"]),
+    ("Gaussian alpha integral without the 3-sigma truncation",
+     "    return 2.0 * OR_PI * s->su[j] * s->sv[j] * (1.0 - exp(-4.5));", "    return 2.0 * OR_PI * s->su[j] * s->sv[j];",
+     ["pairs"]),
+    ("pair front test without eps_plane",
+     "            if (dot3(s->nrm + i * 3, d) > s->eps_plane) cnt[i]++;",
+     "            if (dot3(s->nrm + i * 3, d) > -1.0) cnt[i]++;", ["pairs"]),
+    ("occluders within eps_plane of the source's plane kept",
+     "        if (fabs(dot3(nk, e)) <= s->eps_plane) continue;", "        (void)e;", ["pairs"]),
     ("lambda gradient without the alpha integral",
      "if (dlam) dlam[j] += g * A * T * geo;", "if (dlam) dlam[j] += g * T * geo;", ["pairs"]),
     ("GFSGS opacity derivative without the exponent 3.4",
@@ -102,9 +129,20 @@ MUTANTS = [
      "if (mc_u(seed, (uint64_t)t, (uint64_t)q, 1000 + (uint64_t)k) * W < 2.0 * w[k]) pick = k;", ["mc"]),
     ("visit count advances by two",
      "            D[a] += 1.0;", "            D[a] += 2.0;", ["mc"]),
+    ("receiver selection by the second moment instead of the variance",
+     "                    v += SB2[i * R + k] / D[i] - m * m;", "                    v += SB2[i * R + k] / D[i];", ["mc"]),
+    ("shooting takes the dimmest unshot surfel",
+     "            if (l > bl) {\n                bl = l;\n                best = i;",
+     "            if (l > 0.0 && (best < 0 || l < bl)) {\n                bl = l;\n                best = i;", ["mc"]),
     ("shooting leaves the shot radiance unshot",
      "        memset(dB + (size_t)best * R, 0, sizeof(double) * R);", "        (void)best;", ["mc"]),
     # image formation (Eq. L_I for a camera)
+    ("pixel rays through pixel corners instead of centres",
+     "    const double sx = (2.0 * (x + 0.5) / W - 1.0) * th * (double)W / (double)H;",
+     "    const double sx = (2.0 * x / W - 1.0) * th * (double)W / (double)H;", ["render"]),
+    ("image rows not flipped (y up)",
+     "    const double sy = (1.0 - 2.0 * (y + 0.5) / H) * th;", "    const double sy = (2.0 * (y + 0.5) / H - 1.0) * th;",
+     ["render"]),
     ("camera rays ignore the transmittance of nearer surfels",
      "                T *= 1.0 - hv.h[h].alpha;\n                const int j = hv.h[h].j;",
      "                T *= 1.0;\n                const int j = hv.h[h].j;", ["render"]),

@@ -94,6 +94,18 @@ def test_coplanar_neighbours_of_the_source_do_not_occlude():
     orc = O.Oracle(sc).pairs()
     pl = orc.pair_list()
     assert np.all(pl["T"][pl["off"][0]:pl["off"][1]] == 1.0)
+    # the same neighbour moved 0.4 eps_plane towards the receiver: the segment now crosses its
+    # plane before reaching the source, and only the eps_plane rule keeps it from occluding
+    # (while one moved 3 eps_plane towards the receiver does occlude)
+    eps = O.Oracle(sc).eps_plane
+    for shift, occludes in ((0.4, False), (3.0, True)):
+        sc2 = make_scene([dict(p=(0, 0, 0), tu=(1, 0, 0), tv=(0, 1, 0)),
+                          dict(p=(0.1, 0, 1), tu=(0, 1, 0), tv=(1, 0, 0), s=(0.2, 0.2)),
+                          dict(p=(0.12, 0.01, 1 - shift * eps), tu=(0, 1, 0), tv=(1, 0, 0), s=(0.2, 0.2))])
+        pl = O.Oracle(sc2).pairs().pair_list()
+        j = list(pl["j"][pl["off"][0]:pl["off"][1]])
+        T = pl["T"][pl["off"][0] + j.index(1)]
+        assert (T < 1.0) == occludes
 
 
 def test_adjoint_identity_and_dense_solve():

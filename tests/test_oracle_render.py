@@ -47,6 +47,24 @@ def test_disc_coverage_and_value():
     np.testing.assert_array_equal(img[~inside], 0.0)
 
 
+def test_offset_disc_lands_where_the_pinhole_puts_it():
+    """A disc up and to the right of the optical axis covers exactly the pixels whose
+    rays (pixel (x, y) with x to the right and y down) meet it: the image is not mirrored
+    in either axis."""
+    s, cx, cy = 0.12, 0.25, 0.2
+    orc = _oracle([dict(p=(cx, cy, 0), tu=(1, 0, 0), tv=(0, 1, 0), s=(s, s), o=1.0)], alpha_model=O.ALPHA_DISC)
+    B = np.zeros((1, 4, 3))
+    B[0, 0] = (1.0, 1.0, 1.0)
+    W, H, fov = 40, 30, 0.6
+    img = orc.render(B, CAM, W, H, fov)
+    d = _pixel_dirs(W, H, fov)
+    t = 2.0 / -d[..., 2]
+    inside = (t * d[..., 0] - cx) ** 2 + (t * d[..., 1] - cy) ** 2 <= s * s
+    ys, xs = np.nonzero(inside)
+    assert inside.sum() > 10 and ys.max() < H // 2 and xs.min() >= W // 2  # upper right quadrant
+    np.testing.assert_array_equal(img[..., 0] > 0.0, inside)
+
+
 def test_gaussian_centre_and_stacked_composite():
     W = H = 21  # odd: the centre pixel's ray is the axis
     fov = 0.6
