@@ -5,7 +5,7 @@ import os
 
 import numpy as np
 import pytest
-from scipy import integrate, special
+from scipy import integrate, special, stats
 
 from oracle import oracle as O
 
@@ -128,6 +128,16 @@ def test_splitmix64_golden():
             continue
         k, val = line.split()
         assert O.splitmix64((int(k) * gamma) % 2 ** 64) == int(val, 16)
+
+
+def test_jitter_is_uniform_on_24_bit_grid():
+    """The stratum jitter is uniform on [0, 1) in steps of 2^-24 (App. B's stratified
+    sampling needs the full unit interval per stratum): a Kolmogorov-Smirnov test over
+    20,000 keys, and every value on the 24-bit grid."""
+    v = np.array([O.jitter(3, i, r, dim) for i in range(2500) for r in range(4) for dim in range(2)])
+    assert np.all((v >= 0.0) & (v < 1.0))
+    np.testing.assert_array_equal(v * 2.0 ** 24, np.floor(v * 2.0 ** 24))
+    assert stats.kstest(v, "uniform").pvalue > 1e-3
 
 
 @pytest.mark.parametrize("nd", [32, 64, 128, 192, 256, 512])

@@ -88,6 +88,30 @@ MUTANTS = [
      "for (int q = 1; q <= m; ++q) pmm *= (2.0 * q - 1.0); /* (-1)^m", ["math"]),
     ("SplitMix64 with a wrong multiplier",
      "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 27)) * 0x94D049BB133111EDULL;", ["math"]),
+    ("Phong factor of even bands with a shifted numerator",
+     "        for (int q = 0; q >= -(l - 2); q -= 2) num *= (s + q);",
+     "        for (int q = 0; q >= -(l - 2); q -= 2) num *= (s + q + 1);", ["math"]),
+    ("specular coefficients weighted by k instead of 1 - k",
+     "(1.0 - k) * as[ch] * or_phong_rho(l, shin)", "k * as[ch] * or_phong_rho(l, shin)", ["math", "transport"]),
+    ("jitter on [0, 1/2) (one bit short)",
+     "    return (double)(or_splitmix64(key) >> 40) * (1.0 / 16777216.0);",
+     "    return (double)(or_splitmix64(key) >> 41) * (1.0 / 16777216.0);", ["math"]),
+    ("eps_plane a hundred times too wide",
+     "    s->eps_plane = 1e-5 * sqrt(diag);", "    s->eps_plane = 1e-3 * sqrt(diag);", ["transport", "pairs"]),
+    ("tie runs a thousand times too wide",
+     "            while (e + 1 < out->cnt && out->h[e + 1].t - out->h[e].t <= 1e-6 * fmax(1.0, out->h[e].t)) ++e;",
+     "            while (e + 1 < out->cnt && out->h[e + 1].t - out->h[e].t <= 1e-3 * fmax(1.0, out->h[e].t)) ++e;",
+     ["transport"]),
+    ("hit opacity ignores the surfel's o",
+     "    or_hit x = {t, alpha_of(s, s->o[j], G), G, j};", "    or_hit x = {t, alpha_of(s, 1.0, G), G, j};",
+     ["transport", "pairs"]),
+    ("directional light without the receiver's cosine",
+     "    return s->ldir ? cs : cs / (len * len);", "    return s->ldir ? 1.0 : cs / (len * len);", ["lights"]),
+    ("opacity receiver term with alpha instead of d alpha / d o",
+     "            dop[i] = dalpha_c(s, i) * acc;", "            dop[i] = alpha_c(s, i) * acc;", ["gfsgs", "transport"]),
+    ("shadow-ray opacity backward with the wrong sign",
+     "                    dop[s->sh_j[e]] += -qv * others * dalpha_do(s, s->o[s->sh_j[e]], s->sh_G[e]);",
+     "                    dop[s->sh_j[e]] += qv * others * dalpha_do(s, s->o[s->sh_j[e]], s->sh_G[e]);", ["transport"]),
     # center-to-center transport (Sec. 8, App. E)
     ("pair transport without the source's cosine",
      "double geo = fabs(dot3(s->nrm + i * 3, d)) * fabs(dot3(s->nrm + j * 3, d)) / r2;",
@@ -107,9 +131,20 @@ MUTANTS = [
      "if (dlam) dlam[j] += g * A * T * geo;", "if (dlam) dlam[j] += g * T * geo;", ["pairs"]),
     ("GFSGS opacity derivative without the exponent 3.4",
      "        return exp(-p) * 3.4 * p / o;", "        return exp(-p) * p / o;", ["gfsgs"]),
+    ("lambda left out of the pair transport",
+     "            s->pair_V[e] = s->lam[j] * or_alpha_area(s, j) * T * geo;",
+     "            s->pair_V[e] = or_alpha_area(s, j) * T * geo;", ["pairs"]),
+    ("GFSGS receiver factor o instead of alpha_i(p_i)",
+     "static double alpha_c(const or_scene *s, int i) { return alpha_of(s, s->o[i], 1.0); }",
+     "static double alpha_c(const or_scene *s, int i) { return s->o[i]; }", ["gfsgs"]),
+    ("GFSGS exponent 3 instead of 3.4",
+     "        return -expm1(-0.03279 * pow(x, 3.4));", "        return -expm1(-0.03279 * pow(x, 3.0));", ["gfsgs"]),
     ("Ein series without its alternating sign",
      "            term *= -x / k;", "            term *= x / k;", ["gfsgs"]),
     # geometry gradients (Eqs. dl-dgeo-0/1)
+    ("lobe reflection's normal derivative without its factor 2",
+     "    for (int a = 0; a < 3; ++a) gn[a] += 2.0 * (ng * w[a] + nw * gR[a]);",
+     "    for (int a = 0; a < 3; ++a) gn[a] += (ng * w[a] + nw * gR[a]);", ["geometry"]),
     ("crossing point's normal derivative with the wrong sign",
      "const double fn = -dot3(gx, d) / dot3(nk, d);", "const double fn = dot3(gx, d) / dot3(nk, d);", ["geometry"]),
     ("decay term's distance derivative -geo/r instead of -2 geo/r",
@@ -127,6 +162,8 @@ MUTANTS = [
     ("reservoir keeps candidates with twice their probability",
      "if (mc_u(seed, (uint64_t)t, (uint64_t)q, 1000 + (uint64_t)k) * W < w[k]) pick = k;",
      "if (mc_u(seed, (uint64_t)t, (uint64_t)q, 1000 + (uint64_t)k) * W < 2.0 * w[k]) pick = k;", ["mc"]),
+    ("grouped proposal's probability without the group's share",
+     "        if (pick >= 0) *p = wg[gsel] / totg * wk[pick] / totk;", "        if (pick >= 0) *p = wk[pick] / totk;", ["mc"]),
     ("visit count advances by two",
      "            D[a] += 1.0;", "            D[a] += 2.0;", ["mc"]),
     ("receiver selection by the second moment instead of the variance",
@@ -143,6 +180,9 @@ MUTANTS = [
     ("image rows not flipped (y up)",
      "    const double sy = (1.0 - 2.0 * (y + 0.5) / H) * th;", "    const double sy = (2.0 * (y + 0.5) / H - 1.0) * th;",
      ["render"]),
+    ("image transpose drops the radiance direction's SH",
+     "                            dB[((size_t)j * nc + k) * C + c] += g * Yo[k];",
+     "                            dB[((size_t)j * nc + k) * C + c] += g;", ["render"]),
     ("camera rays ignore the transmittance of nearer surfels",
      "                T *= 1.0 - hv.h[h].alpha;\n                const int j = hv.h[h].j;",
      "                T *= 1.0;\n                const int j = hv.h[h].j;", ["render"]),

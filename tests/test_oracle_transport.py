@@ -187,6 +187,10 @@ def test_compositing_order_and_weights():
     orc = O.Oracle(make_scene([rec, twin_far, near]))
     j, t, a, G = orc.trace_ray(0, [0, 0, 0], [0, 0, 1.0])
     assert list(j) == [1, 2]
+    # depths 1e-4 apart are no tie: depth order even though the nearer has the larger index
+    gap_far = dict(p=(0, 0, 1 + 1e-4), tu=(0, 1, 0), tv=(1, 0, 0), s=(1, 1), o=0.4)
+    j, *_ = O.Oracle(make_scene([rec, gap_far, near])).trace_ray(0, [0, 0, 0], [0, 0, 1.0])
+    assert list(j) == [2, 1]
     # (nearly) coplanar with the ray origin: ignored (|n_j.(p_j - o)| <= eps_plane)
     for dz in (0.0, 1e-7):
         side = dict(p=(0.3, 0, dz), tu=(1, 0, 0), tv=(0, 1, 0), s=(1, 1), o=1.0)
