@@ -147,6 +147,14 @@ MUTANTS = [
      "    for (int a = 0; a < 3; ++a) gn[a] += (ng * w[a] + nw * gR[a]);", ["geometry"]),
     ("crossing point's normal derivative with the wrong sign",
      "const double fn = -dot3(gx, d) / dot3(nk, d);", "const double fn = dot3(gx, d) / dot3(nk, d);", ["geometry"]),
+    ("occluder crossing moves the ray origin with the wrong sign",
+     "        gpo[a] += coef * pw[a];\n        gd[a] += coef * t * pw[a];",
+     "        gpo[a] -= coef * pw[a];\n        gd[a] += coef * t * pw[a];", ["geometry"]),
+    ("crossing's direction derivative without the depth t",
+     "        gd[a] += coef * t * pw[a];\n        if (dp)", "        gd[a] += coef * pw[a];\n        if (dp)", ["geometry"]),
+    ("occluder's t^v derivative with u for v",
+     "            gF[k * 9 + 3 + a] += coef * 2.0 * v * xm[a] / s->sv[k];",
+     "            gF[k * 9 + 3 + a] += coef * 2.0 * u * xm[a] / s->sv[k];", ["geometry"]),
     ("decay term's distance derivative -geo/r instead of -2 geo/r",
      "const double gr = ge * lam * A * T * (-2.0 * geo / r);", "const double gr = ge * lam * A * T * (-geo / r);",
      ["geometry"]),
@@ -168,6 +176,11 @@ MUTANTS = [
      "            D[a] += 1.0;", "            D[a] += 2.0;", ["mc"]),
     ("receiver selection by the second moment instead of the variance",
      "                    v += SB2[i * R + k] / D[i] - m * m;", "                    v += SB2[i * R + k] / D[i];", ["mc"]),
+    ("TD(0) mean not divided by the visits",
+     "                for (size_t k = 0; k < R; ++k) Bhat[i * R + k] = SB[i * R + k] / D[i];",
+     "                for (size_t k = 0; k < R; ++k) Bhat[i * R + k] = SB[i * R + k];", ["mc"]),
+    ("proposal without its floor",
+     "    return 1e-9 * (1.0 + acc / (double)s->n);", "    return 0.0 * acc;", ["mc"]),
     ("shooting takes the dimmest unshot surfel",
      "            if (l > bl) {\n                bl = l;\n                best = i;",
      "            if (l > 0.0 && (best < 0 || l < bl)) {\n                bl = l;\n                best = i;", ["mc"]),
@@ -179,6 +192,9 @@ MUTANTS = [
      "    const double sx = (2.0 * x / W - 1.0) * th * (double)W / (double)H;", ["render"]),
     ("image rows not flipped (y up)",
      "    const double sy = (1.0 - 2.0 * (y + 0.5) / H) * th;", "    const double sy = (2.0 * (y + 0.5) / H - 1.0) * th;",
+     ["render"]),
+    ("camera up taken as given instead of right x forward",
+     "    cross3(r, fn, u);\n    const double th", "    for (int a = 0; a < 3; ++a) u[a] = u0[a];\n    const double th",
      ["render"]),
     ("image transpose drops the radiance direction's SH",
      "                            dB[((size_t)j * nc + k) * C + c] += g * Yo[k];",

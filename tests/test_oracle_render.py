@@ -65,6 +65,17 @@ def test_offset_disc_lands_where_the_pinhole_puts_it():
     np.testing.assert_array_equal(img[..., 0] > 0.0, inside)
 
 
+def test_camera_up_need_not_be_perpendicular():
+    """Only the plane of forward and up matters: the true up is right x forward, so an up
+    vector tilted towards the view direction renders the same image."""
+    orc = _oracle([dict(p=(0.2, 0.1, 0), tu=(1, 0, 0), tv=(0, 1, 0), s=(0.2, 0.1), o=0.9)])
+    B = np.zeros((1, 4, 3))
+    B[0, 0], B[0, 2] = (1.0, 2.0, 3.0), (0.3, 0.2, 0.1)
+    tilted = CAM[:6] + [0.0, 1.0, 0.7]
+    np.testing.assert_allclose(orc.render(B, tilted, 24, 18, 0.7), orc.render(B, CAM, 24, 18, 0.7),
+                               rtol=1e-12, atol=1e-14)
+
+
 def test_gaussian_centre_and_stacked_composite():
     W = H = 21  # odd: the centre pixel's ray is the axis
     fov = 0.6
