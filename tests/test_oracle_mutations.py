@@ -66,6 +66,16 @@ MUTANTS = [
      ["transport", "lights"]),
     ("point light falls off as 1/r instead of 1/r^2",
      "    return s->ldir ? cs : cs / (len * len);", "    return s->ldir ? cs : cs / len;", ["transport"]),
+    ("emission added to the first light's columns only",
+     "                for (int c = 0; c < C; ++c) S[((size_t)i * nc + kk) * C + c] += E[((size_t)i * nc + kk) * 3 + c % 3];",
+     "                for (int c = 0; c < 3; ++c) S[((size_t)i * nc + kk) * C + c] += E[((size_t)i * nc + kk) * 3 + c % 3];",
+     ["transport", "lights", "pairs"]),
+    ("dL/dE summed over the first light's columns only",
+     "                    for (int lt = 0; lt < C / 3; ++lt) acc += u[((size_t)i * nc + kk) * C + lt * 3 + ch];",
+     "                    for (int lt = 0; lt < 1; ++lt) acc += u[((size_t)i * nc + kk) * C + lt * 3 + ch];",
+     ["transport", "lights", "pairs"]),
+    ("albedo gradient without the direct term's share",
+     "                double acc = u[idx] * s->Dgeo[idx];", "                double acc = 0.0 * s->Dgeo[idx];", ["transport"]),
     ("albedo gradient without the blend weight k",
      "dad[i * 3 + ch] = 4.0 * s->k[i] * alpha_c(s, i) * P[", "dad[i * 3 + ch] = 4.0 * alpha_c(s, i) * P[",
      ["transport"]),
@@ -127,6 +137,8 @@ MUTANTS = [
      "            if (dot3(s->nrm + i * 3, d) > -1.0) cnt[i]++;", ["pairs"]),
     ("occluders within eps_plane of the source's plane kept",
      "        if (fabs(dot3(nk, e)) <= s->eps_plane) continue;", "        (void)e;", ["pairs"]),
+    ("pair opacity gradient without lambda",
+     "                dop[j] += g * s->lam[j] * dA * T * geo;", "                dop[j] += g * dA * T * geo;", ["pairs"]),
     ("lambda gradient without the alpha integral",
      "if (dlam) dlam[j] += g * A * T * geo;", "if (dlam) dlam[j] += g * T * geo;", ["pairs"]),
     ("GFSGS opacity derivative without the exponent 3.4",
