@@ -154,6 +154,12 @@ MUTANTS = [
     ("Ein series without its alternating sign",
      "            term *= -x / k;", "            term *= x / k;", ["gfsgs"]),
     # geometry gradients (Eqs. dl-dgeo-0/1)
+    ("hemisphere ray's t^u share of the direction gradient not passed to the frame",
+     "                        gF[i * 9 + a] += c3[0] * gd[a];", "                        gF[i * 9 + a] += 0.0 * gd[a];",
+     ["geometry"]),
+    ("hemisphere ray's normal share with t^v's coefficient",
+     "                        gF[i * 9 + 6 + a] += c3[2] * gd[a];", "                        gF[i * 9 + 6 + a] += c3[1] * gd[a];",
+     ["geometry"]),
     ("lobe reflection's normal derivative without its factor 2",
      "    for (int a = 0; a < 3; ++a) gn[a] += 2.0 * (ng * w[a] + nw * gR[a]);",
      "    for (int a = 0; a < 3; ++a) gn[a] += (ng * w[a] + nw * gR[a]);", ["geometry"]),
