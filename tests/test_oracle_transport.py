@@ -4,7 +4,6 @@ import math
 
 import numpy as np
 import pytest
-from scipy import special
 
 from oracle import oracle as O
 from paper_2509_18497_gb300 import scenes
