@@ -1,9 +1,10 @@
 #!/usr/bin/env python
 """Throughput of the surfel light-transport hot path on one or more GB300s.
 
-A step is one pass of the whole path on the 50,000-surfel fruit-bowl scene (SH degree
-3, 256 hemisphere rays per surfel, 4 bounces, one point light; `--workload` selects the
-200,000-surfel 100-light batch or the 32-scene uneven batch instead): scene build (frames,
+A step is one pass of the whole path on the 200,000-surfel fruit-bowl scene lit by 100
+point lights (300 right-hand sides; SH degree 3, 256 hemisphere rays per surfel, 4
+bounces; `--workload` selects the 50,000-surfel one-light bowl, the 32-scene uneven batch
+and the other workloads instead): scene build (frames,
 BRDF coefficients, Morton sort, BVH), hemisphere and shadow-ray tracing with alpha
 compositing, the bounce iteration, and the adjoint (transposed bounces, emission,
 albedo and opacity gradients).  Metric: surfel x light x bounces per second.
@@ -34,7 +35,7 @@ METRIC = "surfel·light·bounces/s, fwd+adjoint, batched vs plain FP32 on GB300 
 UNIT = "surfel·light·bounces/s"
 WORKLOAD = ("fruit bowl: 50,000 Gaussian surfels on 12 spheres in a hemispherical bowl on a ground plane, "
             "SH degree 3 (16 x RGB), 256 stratified hemisphere rays/surfel, 4 bounces, 1 point light, "
-            "FP32, forward + adjoint (emission, albedo, opacity gradients)")
+            "forward + adjoint (emission, albedo, opacity gradients)")
 MULTI_WORKLOAD = ("multi-light batch: 200,000 fruit-bowl surfels, 100 point lights on a Fibonacci sphere of radius 3 "
                   "(intensity U[5,20]) as 300 right-hand sides, SH degree 3, 256 rays/surfel, 4 bounces, "
                   "forward + adjoint")
@@ -51,6 +52,16 @@ ENV_WORKLOAD = ("environment map: fruit bowl, 50,000 surfels, SH degree 3, 256 r
                 "16 x 32 latitude-longitude map of directional lights (512 lights, 1,536 right-hand sides), "
                 "forward + adjoint")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+# the arithmetic of the batched form: bounces and the opacity gather take BF16 copies of the
+# iterates with FP32 accumulation; the last forward bounce (the residual correction) and the
+# transposed bounces of the adjoint run in FP32
+WORKLOADS = {"fruit_bowl": WORKLOAD, "multi_light": MULTI_WORKLOAD, "uneven": UNEVEN_WORKLOAD,
+             "large": LARGE_WORKLOAD, "pairs": PAIRS_WORKLOAD, "envmap": ENV_WORKLOAD}
+# oracle samples (surfels): about 10-30 s of host work for the CPU baseline, a few seconds
+# per step for the reference arm
+CPU_SAMPLE = {"fruit_bowl": 6000, "multi_light": 1200, "uneven": 2500, "large": 2000, "pairs": 6000, "envmap": 400}
+REF_SAMPLE = {"fruit_bowl": 1500, "multi_light": 300, "uneven": 600, "large": 500, "pairs": 1500, "envmap": 100}
+DTYPE_BATCHED = "bf16 operands, f32 accumulate; f32 correction bounce and adjoint"
 
 
 def max_over_ranks(x, dist, device):
@@ -193,25 +204,81 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def cpu_baseline(n_sample, threads=None):
+def _sample_scene(workload, n_sample):
+    """A bounded sample of the workload for the oracle: the same generator (SH degree, rays,
+    bounces, lights) at n_sample surfels; the many-scene and large workloads sample their
+    fruit-bowl generator with 8 and 16 lights."""
+    from paper_2509_18497_gb300 import scenes
+    if workload == "multi_light":
+        return scenes.multi_light(n=n_sample)
+    if workload == "uneven":
+        return scenes.fruit_bowl(n=n_sample, L=3, nd=192, nb=4, n_lights=8)
+    if workload == "large":
+        return scenes.large_scene(n=n_sample)
+    if workload == "envmap":
+        return scenes.with_env_map(scenes.fruit_bowl(n=n_sample))
+    return scenes.fruit_bowl(n=n_sample)
+
+
+def cpu_baseline(n_sample, workload="multi_light"):
     """The FP64 oracle as it stands, timed on the host cores: full pipeline (transport,
-    4 bounces, adjoint with all gradients) on an n_sample-surfel scene of the same
-    generator, 256 rays/surfel, SH degree 3, one light."""
+    bounces, adjoint with all gradients) on an n_sample-surfel scene of the workload's
+    generator (same SH degree, rays, bounces and lights)."""
     import numpy as np
 
     from oracle import oracle as O
-    from paper_2509_18497_gb300 import scenes
 
-    sc = scenes.fruit_bowl(n=n_sample)
-    W = np.random.default_rng(0).normal(size=(sc["n"], 16, 3))
+    sc = _sample_scene(workload, n_sample)
+    nl = max(1, sc["light_pos"].shape[0])
+    W = np.random.default_rng(0).normal(size=(sc["n"], (sc["L"] + 1) ** 2, 3 * nl))
     t0 = time.perf_counter()
     orc = O.Oracle(sc).transport()
     orc.adjoint(W, E=None, nb=sc["nb"])  # runs the solve (with iterates) and the adjoint
     dt = time.perf_counter() - t0
-    units = sc["n"] * 1 * sc["nb"]
+    units = sc["n"] * sc["light_pos"].shape[0] * sc["nb"]
     return {"value": units / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"fruit-bowl generator at {n_sample} surfels (same SH degree, rays, bounces, light), "
-                      f"full forward + adjoint in {dt:.1f} s"}, dt
+            "sample": f"{workload} generator at {n_sample} surfels (same SH degree, rays, bounces, "
+                      f"{sc['light_pos'].shape[0]} lights), full forward + adjoint in {dt:.1f} s"}, dt, units
+
+
+def pick_receivers(scs, form, rgs, torch):
+    """The batched form's B^(0) on 24 and B^(1) on 3 seeded receivers of (up to three of) the
+    workload's scenes, copied to the host for the oracle check of the CPU leg."""
+    import numpy as np
+    picks = []
+    idx = sorted(range(len(scs)), key=lambda q: scs[q]["n"])
+    for q in sorted({idx[0], idx[len(idx) // 2], idx[-1]}):
+        rng = np.random.default_rng(11 + q)
+        recv = rng.choice(scs[q]["n"], size=min(24, scs[q]["n"]), replace=False)
+        t = form.pipes[q].transport
+        it = [rgs.rgs_get_iterate(t, b) for b in (0, 1)]
+        picks.append((q, recv, it[0][torch.as_tensor(recv, device=it[0].device)].double().cpu().numpy(),
+                      it[1][torch.as_tensor(recv[:3], device=it[1].device)].double().cpu().numpy()))
+        del it
+    return picks
+
+
+def oracle_check(scs, picks):
+    """Relative L2 of the batched iterates against the FP64 oracle computed receiver by
+    receiver: B^(0) = S (the direct term, shadow rays) on 24 receivers and B^(1) (one
+    bounce over the seeded hemisphere rays) on 3, per sampled scene, with the oracle's time."""
+    import numpy as np
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    b0_num = b0_den = b1_num = b1_den = 0.0
+    for q, recv, g0, g1 in picks:
+        orc = O.Oracle(scs[q])
+        o0 = orc.sample_direct(recv)
+        if scs[q].get("E") is not None:  # B^(0) = S = E + D, E broadcast over the light groups
+            o0 = o0 + np.tile(np.asarray(scs[q]["E"], np.float64)[recv], (1, 1, o0.shape[2] // 3))
+        o1 = orc.sample_bounce1(recv[:3], E=scs[q].get("E"))
+        b0_num += float(np.sum((g0 - o0) ** 2))
+        b0_den += float(np.sum(o0 ** 2))
+        b1_num += float(np.sum((g1 - o1) ** 2))
+        b1_den += float(np.sum(o1 ** 2))
+    return {"B0_rel_l2": math.sqrt(b0_num / max(b0_den, 1e-300)), "B1_rel_l2": math.sqrt(b1_num / max(b1_den, 1e-300)),
+            "receivers_B0": sum(len(p[1]) for p in picks), "receivers_B1": sum(min(3, len(p[1])) for p in picks),
+            "scenes": [int(p[0]) for p in picks], "oracle_s": time.perf_counter() - t0}
 
 
 def run_reference(args):
@@ -220,19 +287,19 @@ def run_reference(args):
         return 0
     n_sample = args.ref_sample
     for _ in range(args.warmup):
-        cpu_baseline(n_sample)
+        cpu_baseline(n_sample, args.workload)
     total, units = 0.0, 0
     cb = None
     for _ in range(args.steps):
-        cb, dt = cpu_baseline(n_sample)
+        cb, dt, u = cpu_baseline(n_sample, args.workload)
         total += dt
-        units += n_sample * 1 * 4
+        units += u
     value = units / total
     cb = dict(cb, value=value)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_surfels": n_sample},
+            "config": {"workload": WORKLOADS[args.workload], "sample_surfels": n_sample},
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -281,19 +348,28 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=50000, help="surfel count (default: the 50,000-surfel workload)")
-    ap.add_argument("--workload", default="fruit_bowl", choices=["fruit_bowl", "multi_light", "uneven", "large", "pairs", "envmap"],
-                    help="fruit_bowl: 1 light (default); multi_light: 200,000 surfels and 100 lights; "
+    ap.add_argument("--n", type=int, default=None, help="surfel count (default: the workload's own)")
+    ap.add_argument("--workload", default="multi_light",
+                    choices=["fruit_bowl", "multi_light", "uneven", "large", "pairs", "envmap"],
+                    help="multi_light: 200,000 surfels and 100 lights (default); fruit_bowl: 50,000 surfels, 1 light; "
                          "uneven: 32 scenes of uneven size in one persistent launch; large: 1,000,000 surfels, "
                          "512 rays, 6 bounces, 16 lights, checkpointed iterates; pairs: the center-to-center "
                          "approximation on a 20,000-surfel bowl; envmap: the 50,000-surfel bowl under a 16 x 32 "
                          "environment map of directional lights (1,536 columns)")
+    ap.add_argument("--plain-steps", type=int, default=None,
+                    help="timed steps of the plain FP32 comparison form (default: all K for the light workloads, "
+                         "2 for the many-light and large ones, whose plain steps take 10-70 s)")
+    ap.add_argument("--e2e-steps", type=int, default=None, help="timed steps of the end-to-end leg (default min(K, 3))")
+    ap.add_argument("--no-oracle-sample", action="store_true",
+                    help="skip the FP64 oracle's receiver samples of the batched iterates")
     ap.add_argument("--scenes", type=int, default=32, help="uneven workload: number of scenes (profiling cases)")
     ap.add_argument("--scale", type=float, default=1.0, help="uneven workload: surfel-count factor (profiling cases)")
-    ap.add_argument("--cpu-sample", type=int, default=6000, help="surfels of the timed oracle sample")
-    ap.add_argument("--ref-sample", type=int, default=1500, help="surfels per reference-arm step")
+    ap.add_argument("--cpu-sample", type=int, default=None, help="surfels of the timed oracle sample")
+    ap.add_argument("--ref-sample", type=int, default=None, help="surfels per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.ref_sample is None:
+        args.ref_sample = REF_SAMPLE[args.workload]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -313,24 +389,26 @@ def main():
     build.build()
     rgs.load()
     if args.workload == "multi_light":
-        scs = [scenes.multi_light(n=200000 if args.n == 50000 else args.n)]
+        scs = [scenes.multi_light(n=args.n or 200000)]
         workload = MULTI_WORKLOAD
+        if args.n and args.n != 200000:
+            workload = f"reduced ({args.n} surfels) " + workload
     elif args.workload == "uneven":
         scs = scenes.uneven_batch(args.scenes, scale=args.scale)
         workload = UNEVEN_WORKLOAD
         if args.scenes != 32 or args.scale != 1.0:
             workload = f"reduced uneven batch ({args.scenes} scenes, counts x{args.scale}) of: " + workload
     elif args.workload == "pairs":
-        scs = [scenes.fruit_bowl(n=20000 if args.n == 50000 else args.n)]
+        scs = [scenes.fruit_bowl(n=args.n or 20000)]
         workload = PAIRS_WORKLOAD
     elif args.workload == "envmap":
-        scs = [scenes.with_env_map(scenes.fruit_bowl(n=args.n))]
+        scs = [scenes.with_env_map(scenes.fruit_bowl(n=args.n or 50000))]
         workload = ENV_WORKLOAD
     elif args.workload == "large":
-        scs = [scenes.large_scene(n=1000000 if args.n == 50000 else args.n)]
+        scs = [scenes.large_scene(n=args.n or 1000000)]
         workload = LARGE_WORKLOAD
     else:
-        scs = [scenes.fruit_bowl(n=args.n)]
+        scs = [scenes.fruit_bowl(n=args.n or 50000)]
         workload = WORKLOAD
     units_per_step = sum(sc["n"] * sc["light_pos"].shape[0] * sc["nb"] for sc in scs)
 
@@ -351,16 +429,20 @@ def main():
     ckpt = -1 if args.workload == "large" else 0
     specs = {"plain": (rgs.RGS_FP32, "per_scene"), "batched": (rgs.RGS_BF16_FP32ACC_RESCORR, batched_launch)}
 
-    def make_form(name):
+    heavy = args.workload in ("multi_light", "uneven", "large", "envmap")
+    plain_steps = args.plain_steps or (min(args.steps, 2) if heavy else args.steps)
+    e2e_steps = args.e2e_steps or min(args.steps, 3)
+
+    def make_form(name, warm):
         prec, launch = specs[name]
         f = Form(api, rgs, torch, datas, prec, launch, dev, checkpoint=ckpt, pairs=args.workload == "pairs")
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(warm):
             f.step(datas, gs)
         torch.cuda.synchronize()
         return f
 
-    def timed(f, profile):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    def timed(f, profile, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -369,7 +451,7 @@ def main():
             rgs.rgs_profile_enable(True)
         launches0 = rgs.rgs_launch_count()
         t_wall = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(steps):
             flush.zero_()  # evict L2 between steps (outside the step's events)
             ev[k][0].record(stream)
             f.step(datas, gs)
@@ -383,10 +465,11 @@ def main():
             prof = rgs.rgs_profile_report()
         step_ms = [a.elapsed_time(b) for a, b in ev]
         total_s = max_over_ranks(sum(step_ms) / 1e3, dist if world > 1 else None, dev)
-        return job_throughput(units_per_step, args.steps, world, total_s), step_ms, launches, prof, t_wall
+        return job_throughput(units_per_step, steps, world, total_s), step_ms, launches, prof, t_wall
 
     clocks = Clocks(local)
     res, outs = {}, {}
+    picked = None
     f = None
     for name in ("plain", "batched"):
         if f is not None and sequential:
@@ -394,10 +477,17 @@ def main():
             torch.cuda.synchronize()
             rgs.rgs_trim_workspace()
             torch.cuda.empty_cache()
-        f = make_form(name)
-        res[name] = timed(f, True)
+        # the plain FP32 form is the comparison leg: on the many-light workloads (10-70 s per
+        # step) it gets one warm-up step and a few timed ones; the batched form, the line's
+        # value, gets W >= 3 warm-ups and all K timed steps
+        warm = max(args.warmup, 3) if (name == "batched" or not heavy) else 1
+        steps = args.steps if name == "batched" else plain_steps
+        f = make_form(name, warm)
+        res[name] = timed(f, True, steps)
         keep = (lambda x: x.cpu()) if sequential else (lambda x: x.clone())
         outs[name] = ([keep(B) for B in f.Bs], [tuple(keep(x) for x in gr) for gr in f.grads])
+        if name == "batched" and rank == 0 and not args.no_oracle_sample and not args.no_cpu_baseline:
+            picked = pick_receivers(scs, f, rgs, torch)
         if name == "batched":
             infos = []
             for sc, p in zip(scs, f.pipes):
@@ -419,7 +509,7 @@ def main():
         del f
         torch.cuda.synchronize()
         rgs.rgs_trim_workspace()
-        f = make_form("plain")
+        f = make_form("plain", 1)
 
     # ---------------------------------------------------------- end to end (host buffers)
     keys = api.SURFEL_KEYS + ("light_pos", "light_I")
@@ -430,9 +520,9 @@ def main():
     d_e2e = [dict(d) for d in datas]
     h2d = sum(v.numel() * 4 for h in hosts for v in h.values()) + sum(g.numel() * 4 for g in g_hosts)
     d2h = sum(x.numel() * 4 for o in outs_host for x in o)
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(e2e_steps):
         flush.zero_()
         e2e_ev[k][0].record(stream)
         for de, h in zip(d_e2e, hosts):
@@ -446,7 +536,7 @@ def main():
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dist if world > 1 else None, dev)
-    e2e_value = job_throughput(units_per_step, args.steps, world, e2e_s)
+    e2e_value = job_throughput(units_per_step, e2e_steps, world, e2e_s)
 
     if rank != 0:
         if world > 1:
@@ -488,7 +578,9 @@ def main():
 
     cb = None
     if not args.no_cpu_baseline and world == 1:
-        cb, _ = cpu_baseline(args.cpu_sample)
+        cb, _, _ = cpu_baseline(args.cpu_sample or CPU_SAMPLE[args.workload], args.workload)
+        if picked is not None:
+            cb["batched_vs_oracle"] = oracle_check(scs, picked)
 
     if len(scs) == 1:
         sc = scs[0]
@@ -506,7 +598,7 @@ def main():
             "warmup": max(args.warmup, 3),
             "ms_per_step": sum(step_ms) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16-gather/f32-acc" if headline == "batched" else "f32", "data": "synthetic",
+            "dtype": DTYPE_BATCHED if headline == "batched" else "f32", "data": "synthetic",
             "config": config,
             "batched_vs_plain": {"batched": value_b, "plain": value_p, "speedup": value_b / value_p,
                                  "batched_rel_l2_vs_fp32": rel_err, "batched_grad_rel_l2_vs_fp32": grad_err,

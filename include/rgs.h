@@ -359,10 +359,14 @@ rgs_status rgs_trim_workspace(void);
  * Its scratch (one FP64 partial per 8192-element block, 8192 blocks = 64 KiB) is a static
  * device array inside librgs.so that every GPU loading the library keeps until exit.
  *   x, y     : device float arrays, n elements each (caller-owned, read only).
- *   n        : 0 <= n <= 8192 * 8192 = 67,108,864; larger n returns RGS_ERR_ARG.
+ *   n        : 0 <= n <= 8192 * 8192 = 67,108,864; larger n returns RGS_ERR_ARG; n = 0
+ *              writes 0.
  *   norm_out : device double (caller-owned), written on `stream`.
+ * x, y and norm_out must live on the current device; the kernels run there.
  * The first call on each device looks up the scratch's device address (with that device
- * current) and caches it; make that first call before any stream capture.  All calls share
+ * current) and caches it for the life of the process; make that first call before any
+ * stream capture, and do not use this entry point after a device reset (cudaDeviceReset
+ * reloads the library's device image and leaves the cached address stale).  All calls share
  * the one scratch array, which keeps the last call's contents (each call writes every slot
  * it reads, so nothing needs clearing); calls that overlap on the GPU -- on different
  * streams, or from different host threads -- race on it and must be serialised.

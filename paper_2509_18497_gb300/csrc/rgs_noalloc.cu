@@ -11,7 +11,9 @@
 //
 // Host code must not pass the array's name to a kernel: on the host it names a stand-in,
 // not a device address.  The device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and cached.
+// cudaGetSymbolAddress (with that device current) and cached for the life of the process;
+// a device reset (cudaDeviceReset) unloads the module and leaves that cached address stale,
+// so this entry point must not be used after one.
 #include <mutex>
 
 #include "rgs_internal.cuh"
@@ -107,14 +109,20 @@ extern "C" rgs_status rgs_residual_norm_noalloc(const float *x, const float *y, 
     if (r != RGS_OK) return r;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int blocks = (int)((n + RGS_NOALLOC_CHUNK - 1) / RGS_NOALLOC_CHUNK);
+    // an error left pending by earlier, unrelated work is not this call's: clear it first,
+    // then check each launch on its own
+    (void)cudaGetLastError();
     if (blocks > 0) {
-        ProfScope ps_("k_norm_partials", st);
-        k_norm_partials<<<blocks, RGS_NOALLOC_THREADS, 0, st>>>(x, y, (long long)n, partials);
+        {
+            ProfScope ps_("k_norm_partials", st);
+            k_norm_partials<<<blocks, RGS_NOALLOC_THREADS, 0, st>>>(x, y, (long long)n, partials);
+        }
+        RGS_LAUNCH("residual_norm_noalloc: k_norm_partials");
     }
     {
         ProfScope ps_("k_norm_final", st);
         k_norm_final<<<1, RGS_NOALLOC_THREADS, 0, st>>>(partials, blocks, norm_out);
     }
-    RGS_LAUNCH("residual_norm_noalloc");
+    RGS_LAUNCH("residual_norm_noalloc: k_norm_final");
     return RGS_OK;
 }

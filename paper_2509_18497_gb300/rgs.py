@@ -408,8 +408,13 @@ def rgs_residual_norm_noalloc(x, y, norm_out=None, stream=None):
         norm_out = torch.empty((), device=x.device, dtype=torch.float64)
     if not (norm_out.is_cuda and norm_out.dtype == torch.float64 and norm_out.numel() == 1):
         raise TypeError("norm_out: expected a float64 CUDA scalar")
-    _check(L.rgs_residual_norm_noalloc(_dev(x, tuple(x.shape), "x"), _dev(y, tuple(x.shape), "y"), int(n),
-                                       ct.c_void_p(norm_out.data_ptr()), _stream(stream)))
+    for name, t in (("y", y), ("norm_out", norm_out)):
+        if t.device != x.device:
+            raise ValueError(f"{name} is on {t.device}, x on {x.device}: all three must share one device")
+    # the C entry launches on the current device: make it x's
+    with torch.cuda.device(x.device):
+        _check(L.rgs_residual_norm_noalloc(_dev(x, tuple(x.shape), "x"), _dev(y, tuple(x.shape), "y"), int(n),
+                                           ct.c_void_p(norm_out.data_ptr()), _stream(stream)))
     return norm_out
 
 

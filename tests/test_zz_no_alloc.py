@@ -53,3 +53,29 @@ def test_noalloc_residual_norm_matches_solve_norms():
     st = L.rgs_residual_norm_noalloc(ct.c_void_p(iters[1].data_ptr()), ct.c_void_p(iters[0].data_ptr()),
                                      ct.c_int64(8192 * 8192 + 1), ct.c_void_p(out[0].data_ptr()), stream)
     assert st == 1 and b"outside" in L.rgs_last_error()
+
+
+def test_noalloc_residual_norm_empty_and_full_scratch():
+    """n = 0 launches no partial block and still writes 0; n at the limit fills all 8,192
+    scratch slots (x = y gives exactly 0; a one-element difference in the last slot's block
+    gives exactly its magnitude, so that slot was summed too)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_18497_gb300 import build, rgs
+
+    build.build()
+    L = rgs.load()
+    stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    x = torch.zeros(8192 * 8192, dtype=torch.float32, device="cuda")
+    y = x.clone()
+    y[-1] = 0.75
+    for call, (n, a, b) in enumerate(((0, x, y), (x.numel(), x, x), (x.numel(), x, y))):
+        st = L.rgs_residual_norm_noalloc(ct.c_void_p(a.data_ptr()), ct.c_void_p(b.data_ptr()), ct.c_int64(n),
+                                         ct.c_void_p(out[call].data_ptr()), stream)
+        assert st == 0, L.rgs_last_error()
+    torch.cuda.synchronize()
+    assert out.cpu().tolist() == [0.0, 0.0, 0.75]
+    # the binding checks devices and runs on x's device
+    got = rgs.rgs_residual_norm_noalloc(x[:1000], y[:1000])
+    assert float(got) == 0.0
