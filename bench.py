@@ -59,8 +59,8 @@ WORKLOADS = {"fruit_bowl": WORKLOAD, "multi_light": MULTI_WORKLOAD, "uneven": UN
              "large": LARGE_WORKLOAD, "pairs": PAIRS_WORKLOAD, "envmap": ENV_WORKLOAD}
 # oracle samples (surfels): about 10-30 s of host work for the CPU baseline, a few seconds
 # per step for the reference arm
-CPU_SAMPLE = {"fruit_bowl": 6000, "multi_light": 1200, "uneven": 2500, "large": 2000, "pairs": 6000, "envmap": 400}
-REF_SAMPLE = {"fruit_bowl": 1500, "multi_light": 300, "uneven": 600, "large": 500, "pairs": 1500, "envmap": 100}
+CPU_SAMPLE = {"fruit_bowl": 6000, "multi_light": 120, "uneven": 1500, "large": 1500, "pairs": 6000, "envmap": 40}
+REF_SAMPLE = {"fruit_bowl": 1500, "multi_light": 60, "uneven": 400, "large": 400, "pairs": 1500, "envmap": 20}
 DTYPE_BATCHED = "bf16 operands, f32 accumulate; f32 correction bounce and adjoint"
 
 
@@ -602,8 +602,9 @@ def main():
             "config": config,
             "batched_vs_plain": {"batched": value_b, "plain": value_p, "speedup": value_b / value_p,
                                  "batched_rel_l2_vs_fp32": rel_err, "batched_grad_rel_l2_vs_fp32": grad_err,
-                                 "plain_ms_per_step": sum(step_ms_p) / args.steps,
-                                 "batched_ms_per_step": sum(step_ms_b) / args.steps,
+                                 "plain_ms_per_step": sum(step_ms_p) / len(step_ms_p),
+                                 "batched_ms_per_step": sum(step_ms_b) / len(step_ms_b),
+                                 "plain_steps": len(step_ms_p), "plain_warmup": 1 if heavy else max(args.warmup, 3),
                                  "batched_launch": batched_launch},
             "roofline": roofline, "trace": trace, "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -341,6 +341,26 @@ rgs_status rgs_set_checkpointing(rgs_transport *t, int32_t stride);
  * allocated even above the budget.  Host-only.  Errors: RGS_ERR_ARG. */
 rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
 
+/* Which contraction the batched precision modes (RGS_BF16_FP32ACC, RGS_BF16_FP32ACC_RESCORR)
+ * of the following rgs_solve / rgs_adjoint calls on a hemisphere transport with SH degree 3
+ * use (Eq. final-radiosity; the many-light batching of Sec. 7):
+ *   mode = -1 : automatic (default) -- the tensor-core form when C >= 96 columns and its
+ *               buffers fit in free device memory, else the row-gather kernels;
+ *   mode =  0 : always the row-gather kernels;
+ *   mode =  1 : the tensor-core form whenever it applies (any C; still not for checkpointed
+ *               solves, SH degree < 3, more than 2^20 surfels or 512 rays per surfel).
+ * The tensor-core form regroups the hit records once per trace into tiles of 8 consecutive
+ * receivers, and per tile into the sources they see; per (tile, source) it forms the 8
+ * receivers' 16 x 16 transport blocks G_ij = sum_{r,h: j_h = j} a_rh Y(R_i d_r) Y(-d_r)^T as a
+ * 128 x 16 BF16 operand and multiplies it with the source's BF16 rows (copied into shared
+ * memory by the bulk-copy engine) on the tcgen05 tensor cores, FP32 accumulation in tensor
+ * memory.  RGS_BF16_FP32ACC_RESCORR's last bounce splits both operands into BF16 high and low
+ * parts (three products, FP32-level accuracy).  rgs_adjoint then runs the transposed bounces
+ * the same way over tiles of 8 sources (y = o c (x) v rounded to BF16), with FP32 outputs.
+ * Extra device memory: about 40 bytes per stored hit and three BF16 copies of an iterate.
+ * Host-only.  Errors: RGS_ERR_ARG (NULL transport, mode outside [-1, 1]). */
+rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode);
+
 /* Workspace pool: the per-call scratch of rgs_adjoint (the transposed hit index, 8 bytes per
  * hit; per-hit opacity sums, 4 bytes; v^(a) and u; per-ray adjoint values) and of
  * rgs_get_iterate comes from one stream-ordered memory pool per device, so transports used

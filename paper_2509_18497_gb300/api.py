@@ -35,8 +35,9 @@ class Pipeline:
     cudaMalloc inside the library."""
 
     def __init__(self, alpha_model=rgs.RGS_ALPHA_GAUSS, precision=rgs.RGS_FP32, checkpoint=0, mem_budget=0,
-                 pairs=False):
+                 pairs=False, tensor_cores=-1):
         self.pairs = pairs  # center-to-center transport (Sec. 8) instead of hemisphere rays
+        self.tensor_cores = tensor_cores  # contraction of the batched modes (rgs_set_tensor_cores)
         self.alpha_model = alpha_model
         self.precision = precision
         self.checkpoint = checkpoint  # iterate checkpoint stride (0 all kept, -1 automatic)
@@ -60,6 +61,7 @@ class Pipeline:
                                                      transport=self.transport, directional=d.get("light_dir", False))
         rgs.rgs_set_checkpointing(self.transport, self.checkpoint)
         rgs.rgs_set_memory_budget(self.transport, self.mem_budget)
+        rgs.rgs_set_tensor_cores(self.transport, self.tensor_cores)
         return self.transport
 
     def solve(self, E, nb, B_out=None, stats=False, stream=None, precision=None):

@@ -566,7 +566,7 @@ rgs_status opacity_group(rgs_transport *t, SceneDev sd, RaysDev rd, int na, cons
 template <int NC>
 rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, float *dopo,
                        const std::vector<int> &parts, const std::vector<long long> &part_base, cudaStream_t st,
-                       const RgsGeoAcc *geo) {
+                       const RgsGeoAcc *geo, bool tcp) {
     const int n = t->n, C = t->C, nb = t->nb_last, s = t->stride;
     const size_t A = t->arr();
     const size_t A16 = (size_t)n * C * bf16_stride<NC>();
@@ -589,6 +589,10 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     // every source unless memory asked for more), per column tile
     auto KT = [&](int a) -> rgs_status {
         rgs_status q;
+        if (tcp) { // tensor cores over source tiles: y^(a-1) = o c (x) v^(a-1) in BF16 row blocks
+            if (a == 1 && (q = rgs_tc_make_y(t, vp(0), 0, st)) != RGS_OK) return q;
+            return rgs_tc_adjoint_bounce(t, (a - 1) & 1, a & 1, vp(a), t->u, st);
+        }
         for (size_t p = 0; p + 1 < parts.size(); ++p) {
             const int j0 = parts[p], j1 = parts[p + 1];
             if (j1 <= j0) continue;
@@ -695,7 +699,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     }
     { ProfScope ps_("k_finalize", st); k_finalize<NC><<<gn, 128, 0, st>>>(sd, C, t->u, t->Pg, t->sc->kk, t->dop, dE, dad, dopo); }
     RGS_LAUNCH("finalize");
-    return RGS_OK;
+    return tcp ? rgs_tc_check(t, st) : RGS_OK;
 }
 
 } // namespace
@@ -798,6 +802,10 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
     } scratch{t, st, {}};
     const bool mc = wide_adjoint(t->C);
     const bool want_gh = (dop || want_geo) && nb >= 1;
+    // the last solve ran on the tensor cores: so do the transposed bounces (source tiles
+    // instead of the transposed hit index and the per-ray adjoint values)
+    const bool tcp = t->tc_used && t->kind == RGS_KIND_HEMISPHERE && t->stride == 0 && nb >= 1;
+    if (tcp && (r = rgs_tc_prepare_adjoint(t, st)) != RGS_OK) return r;
     if (want_geo) {
         RgsGeoAcc &geo = scratch.geo;
         if ((r = pool_alloc(&geo.dp, (size_t)n * 3, st)) != RGS_OK) return r;
@@ -811,7 +819,8 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
     const int n_v = t->stride ? t->stride + 1 : nb + 1;
     if ((r = pool_alloc(&t->v, A * n_v, st)) != RGS_OK) return r;
     if ((r = pool_alloc(&t->u, A, st)) != RGS_OK) return r;
-    if (mc) {
+    if (tcp) {
+    } else if (mc) {
         if ((r = pool_alloc(&t->dy_mc, (size_t)n_rays * 32, st)) != RGS_OK) return r;
     } else {
         if ((r = pool_alloc(&t->dy, (size_t)n_rays, st)) != RGS_OK) return r;
@@ -829,7 +838,7 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
         avail = std::min(avail, (double)t->mem_budget - (double)t->device_bytes - scratch - seg);
     }
     int P = 1;
-    while (P < 64 && tr_all / P > avail) P *= 2;
+    while (!tcp && P < 64 && tr_all / P > avail) P *= 2;
     std::vector<int> parts{0};
     std::vector<long long> base{0};
     if (P > 1) {
@@ -850,13 +859,15 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
         const long long e1 = p + 2 < parts.size() ? base[p + 1] : t->n_hits;
         biggest = std::max(biggest, e1 - base[p]);
     }
-    if ((r = pool_alloc(&t->tr, (size_t)std::max(biggest, 1ll), st)) != RGS_OK) return r;
-    if (parts.size() == 2 && (r = build_index(t, 0, n, 0, st)) != RGS_OK) return r;
+    if (!tcp) {
+        if ((r = pool_alloc(&t->tr, (size_t)std::max(biggest, 1ll), st)) != RGS_OK) return r;
+        if (parts.size() == 2 && (r = build_index(t, 0, n, 0, st)) != RGS_OK) return r;
+    }
     switch (t->nc) {
-    case 1: r = run_adjoint<1>(t, g, dE, dad, dop, parts, base, st, geop); break;
-    case 4: r = run_adjoint<4>(t, g, dE, dad, dop, parts, base, st, geop); break;
-    case 9: r = run_adjoint<9>(t, g, dE, dad, dop, parts, base, st, geop); break;
-    default: r = run_adjoint<16>(t, g, dE, dad, dop, parts, base, st, geop);
+    case 1: r = run_adjoint<1>(t, g, dE, dad, dop, parts, base, st, geop, false); break;
+    case 4: r = run_adjoint<4>(t, g, dE, dad, dop, parts, base, st, geop, false); break;
+    case 9: r = run_adjoint<9>(t, g, dE, dad, dop, parts, base, st, geop, false); break;
+    default: r = run_adjoint<16>(t, g, dE, dad, dop, parts, base, st, geop, tcp);
     }
     if (r != RGS_OK || !want_geo) return r;
     return rgs_geometry_out(t, scratch.geo, dp, ds, dtu, dtv, st);

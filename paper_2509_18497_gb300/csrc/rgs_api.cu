@@ -497,6 +497,15 @@ rgs_status rgs_set_checkpointing(rgs_transport *t, int32_t stride) {
     return RGS_OK;
 }
 
+rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode) {
+    if (!t || mode < -1 || mode > 1) {
+        rgs_set_error("rgs_set_tensor_cores: NULL transport or mode outside [-1, 1]");
+        return RGS_ERR_ARG;
+    }
+    t->tc_mode = mode;
+    return RGS_OK;
+}
+
 rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes) {
     if (!t || bytes < 0) {
         rgs_set_error("rgs_set_memory_budget: NULL transport or negative budget");
@@ -570,6 +579,7 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->lam);
     dev_free(t->aarea);
     dev_free(t->daarea);
+    rgs_tc_free(t);
     delete t;
 }
 

@@ -484,6 +484,7 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
     RGS_CUDA(cudaStreamSynchronize(st));
     for (int s = 0; s < count; ++s) {
         ts[s]->nb_last = err ? -1 : nbs[s];
+        ts[s]->tc_used = false;
         ts[s]->prec_last = precision;
     }
     if (err) {

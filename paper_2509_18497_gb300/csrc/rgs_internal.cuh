@@ -66,6 +66,7 @@ enum {
     FLAG_FULL_RAYS = 1, // rays whose full RGS_HMAX buffer ended above the transmittance cut
     FLAG_STACK = 2,     // traversal stack overflow (the ray then misses the rest of the tree)
     FLAG_NONFINITE = 3,
+    FLAG_TC_TIMEOUT = 4, // a bounded wait of the tensor-core contraction ran out
     FLAG_COUNT = 8
 };
 
@@ -605,6 +606,11 @@ struct rgs_scene {
 
 enum { RGS_KIND_NONE = 0, RGS_KIND_HEMISPHERE = 1, RGS_KIND_PAIRS = 2 };
 
+// tensor-core contraction state of a transport (rgs_tc.cu): pair tiles and BF16 row blocks
+struct rgs_tc_state;
+// the batched modes take the tensor-core contraction from this many columns on (automatic mode)
+#define RGS_TC_MIN_COLS 96
+
 struct rgs_transport {
     rgs_scene *sc = nullptr;
     int kind = RGS_KIND_NONE; // which trace built it: hemisphere rays or center-to-center pairs
@@ -687,6 +693,10 @@ struct rgs_transport {
     int pg_cap = 0;       // surfels allocated in Pg / dop
     float *gh = nullptr;  // per hit-record slot: dL/d(weight) accumulated over the bounces
     long long device_bytes = 0;
+    // tensor-core contraction (batched modes): -1 automatic (many columns), 0 off, 1 always
+    int tc_mode = -1;
+    bool tc_used = false; // the last solve ran on the tensor-core path
+    rgs_tc_state *tc = nullptr;
     RaysDev rays() const {
         RaysDev r;
         r.nd = nd;
@@ -802,6 +812,19 @@ template <class T, int NA> struct OpaSet {
 template <int NC>
 rgs_status mc_opacity(rgs_transport *t, SceneDev sd, RaysDev rd, int na, const float *const *v, const float *const *Bf,
                       const __nv_bfloat16 *const *Bh, bool first, cudaStream_t st);
+
+// tensor-core contraction (rgs_tc.cu)
+bool rgs_tc_eligible(const rgs_transport *t, int precision);
+rgs_status rgs_tc_prepare(rgs_transport *t, cudaStream_t st);
+rgs_status rgs_tc_prepare_adjoint(rgs_transport *t, cudaStream_t st);
+rgs_status rgs_tc_load_blk(rgs_transport *t, const float *x, int slot, bool lo, cudaStream_t st);
+rgs_status rgs_tc_bounce(rgs_transport *t, int in, int out, bool split, bool want_lo, const float *Bprev,
+                         const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16, double *norm2, cudaStream_t st);
+rgs_status rgs_tc_make_y(rgs_transport *t, const float *v, int slot, cudaStream_t st);
+rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout, float *u, cudaStream_t st);
+rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st); // RGS_ERR_TIMEOUT if a bounded wait ran out
+void rgs_tc_invalidate(rgs_transport *t);
+void rgs_tc_free(rgs_transport *t);
 
 // entry points implemented per translation unit
 rgs_status rgs_scene_build_impl(rgs_scene *s, const rgs_surfels *in, const rgs_build_opts *o, cudaStream_t st);

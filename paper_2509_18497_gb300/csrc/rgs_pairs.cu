@@ -536,6 +536,8 @@ __global__ void k_lam_out(int n, const int *__restrict__ uid, const float *__res
 rgs_status rgs_trace_pairs_impl(rgs_transport *t, const rgs_lights *L, const float *lambda, cudaStream_t st) {
     rgs_status r;
     t->kind = RGS_KIND_PAIRS;
+    rgs_tc_invalidate(t);
+    t->tc_used = false;
     t->nd = 0;
     if ((r = rgs_transport_common(t, L, st)) != RGS_OK) return r;
     const int n = t->n;

@@ -81,9 +81,34 @@ void launch_to_user(const rgs_transport *t, const float *X, float *Y, cudaStream
 
 } // namespace
 
+// the batched modes on the tensor cores (rgs_tc.cu): B^(0) = S, then per bounce the pair-tile
+// contraction reading the blocked BF16 copy of B^(b-1) (and its low part in the correction
+// bounce) and writing Q^(b-1), B^(b), its row-layout BF16 copy and the next blocked copy
+rgs_status run_solve_tc(rgs_transport *t, const float *E, int nb, int precision, cudaStream_t st) {
+    const size_t A = t->arr();
+    rgs_status r;
+    launch_make_S<16>(t, E, t->iters, t->iters16, st);
+    RGS_LAUNCH("make_S");
+    if ((r = rgs_tc_prepare(t, st)) != RGS_OK) return r;
+    const bool rescorr = precision == RGS_BF16_FP32ACC_RESCORR;
+    if ((r = rgs_tc_load_blk(t, t->iters, 0, rescorr && nb == 1, st)) != RGS_OK) return r;
+    for (int b = 1; b <= nb; ++b) {
+        const bool split = rescorr && b == nb;
+        const bool want_lo = rescorr && b == nb - 1;
+        if ((r = rgs_tc_bounce(t, (b - 1) & 1, b & 1, split, want_lo, t->iters + A * (b - 1), t->iters,
+                               t->Q + A * (b - 1), t->iters + A * b, t->iters16 + A * b, t->norm2 + b, st)) != RGS_OK)
+            return r;
+    }
+    t->tc_used = true;
+    return rgs_tc_check(t, st);
+}
+
 template <int NC>
 rgs_status run_solve(rgs_transport *t, const float *E, int nb, int precision, cudaStream_t st) {
     const size_t A = t->arr();
+    t->tc_used = false;
+    if constexpr (NC == 16)
+        if (nb >= 1 && rgs_tc_eligible(t, precision)) return run_solve_tc(t, E, nb, precision, st);
     const size_t A16 = (size_t)t->n * t->C * bf16_stride<NC>();
     const bool bf16 = precision != RGS_FP32;
     SceneDev sd = t->sc->dev();

@@ -1,0 +1,985 @@
+// Tensor-core bounce contraction (many right-hand sides, Eq. final-radiosity; Sec. 7):
+//   Q_i = sum_j G_ij B_j,   G_ij = sum_{r, h : j_h = j} a_rh Y(R_i d_r) Y(-d_r)^T   (16 x 16)
+// and its transpose for the adjoint (Eq. final_dL_dE):
+//   (K^T v)_j = sum_i G_ij^T y_i,   y_i = o_i c_i (x) v_i.
+//
+// The stored hit records are regrouped once per transport into "pair tiles": 8 consecutive
+// receivers (Morton order) and, for each source j any of them sees, the hits of that
+// (tile, source) group, sorted by receiver and ray.  Per group the CTA
+//   * bulk-copies the source's BF16 row block (C columns x 16 coefficients, stored in the
+//     core-matrix layout of rgs_tc.cuh) from global into shared memory (TMA engine),
+//   * forms the 8 receivers' 16 x 16 blocks G_ij as one 128 x 16 operand from the group's
+//     hits (FP32, rounded to BF16; rows of receivers that do not see j are zero),
+//   * issues D[128 x C] += A[128 x 16] * B_j^T with tcgen05 (accumulator in TMEM).
+// After the tile's last group D holds Q^T of its 8 receivers (rows = receiver x SH
+// coefficient), and the epilogue forms B = S + o c (x) (pi/nd) Q, its BF16 copies and the FP64
+// residual norm.  The adjoint is the same kernel over "source tiles" (8 consecutive
+// sources, groups = receivers seeing them) with the roles of Y(R_i d) and Y(-d) swapped.
+// The residual-correction bounce splits both operands into BF16 high and low parts and
+// accumulates the three products hi*hi + hi*lo + lo*hi (FP32-level accuracy).
+//
+// Roles (one persistent CTA per SM, tiles assigned round-robin):
+//   warp 0      producer: group list, bulk copies of source rows into a ring of stages
+//   warp 1      TMEM owner and MMA issuer (one elected lane)
+//   warps 2..9  operand builders (one group each, round-robin) and epilogue (TMEM -> HBM)
+// Every wait on an mbarrier is bounded; a wait that runs out sets an error flag and the
+// kernel returns (the host reports RGS_ERR_TIMEOUT), so a broken partner cannot hang the GPU.
+#include <algorithm>
+#include <vector>
+
+#include "rgs_internal.cuh"
+#include "rgs_tc.cuh"
+
+namespace {
+
+constexpr int TC_R = 8;           // receivers (or sources) per tile: 8 x 16 coefficients = M 128
+constexpr int TC_NB = 8;          // builder warps
+constexpr int TC_THREADS = (2 + TC_NB) * 32;
+constexpr int TC_MAX_STAGES = 8;
+constexpr int TC_CHUNK = 512;     // columns per pass (TMEM holds 512 FP32 columns)
+constexpr uint64_t TC_WAIT_NS = 4000000000ull; // 4 s per wait before giving up
+
+// ------------------------------------------------------------------ SH as monomials
+// Y_k(v) = sum_q TC_SH[k][q] m_q(v) with the 20 monomials of degree <= 3
+// (1, x, y, z, xy, yz, zz, xz, xx, yy, xxy, yyy, xyz, yzz, zzz, xzz, xxz, yyz, xxx, xyy):
+// the real orthonormal SH with the Condon-Shortley phase (the polynomials of sh_eval), so
+// that a lane can evaluate "its" coefficient k with the same instructions as every other.
+__device__ __constant__ float TC_SH[16][20] = {
+    {0.28209479177387814f},
+    {0, 0, -0.4886025119029199f},
+    {0, 0, 0, 0.4886025119029199f},
+    {0, -0.4886025119029199f},
+    {0, 0, 0, 0, 1.0925484305920792f},
+    {0, 0, 0, 0, 0, -1.0925484305920792f},
+    {-0.31539156525252005f, 0, 0, 0, 0, 0, 3.f * 0.31539156525252005f},
+    {0, 0, 0, 0, 0, 0, 0, -1.0925484305920792f},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0.5462742152960396f, -0.5462742152960396f},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, -3.f * 0.5900435899266435f, 0.5900435899266435f},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 2.890611442640554f},
+    {0, 0, 0.4570457994644658f, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, -5.f * 0.4570457994644658f},
+    {0, 0, 0, -3.f * 0.3731763325901154f, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 5.f * 0.3731763325901154f},
+    {0, 0.4570457994644658f, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, -5.f * 0.4570457994644658f},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1.445305721320277f, -1.445305721320277f},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, -0.5900435899266435f, 3.f * 0.5900435899266435f},
+};
+
+__device__ __forceinline__ float sh_mono(const float (&cf)[20], float3 v) {
+    const float x = v.x, y = v.y, z = v.z;
+    const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, yz = y * z, xz = x * z;
+    float s = cf[0];
+    s = fmaf(cf[1], x, s);
+    s = fmaf(cf[2], y, s);
+    s = fmaf(cf[3], z, s);
+    s = fmaf(cf[4], xy, s);
+    s = fmaf(cf[5], yz, s);
+    s = fmaf(cf[6], zz, s);
+    s = fmaf(cf[7], xz, s);
+    s = fmaf(cf[8], xx, s);
+    s = fmaf(cf[9], yy, s);
+    s = fmaf(cf[10], xx * y, s);
+    s = fmaf(cf[11], yy * y, s);
+    s = fmaf(cf[12], xy * z, s);
+    s = fmaf(cf[13], y * zz, s);
+    s = fmaf(cf[14], z * zz, s);
+    s = fmaf(cf[15], x * zz, s);
+    s = fmaf(cf[16], xx * z, s);
+    s = fmaf(cf[17], yy * z, s);
+    s = fmaf(cf[18], xx * x, s);
+    s = fmaf(cf[19], x * yy, s);
+    return s;
+}
+
+// ------------------------------------------------------------------ kernel arguments
+struct TcArgs {
+    int adjoint;   // 0: forward over receiver tiles, 1: transpose over source tiles
+    int split;     // 1: hi/lo operands, three MMAs per column piece
+    int n, C, Cp, nd, ntiles, nchunks, stages;
+    uint32_t stage_bytes, rows_bytes, a_bytes;
+    const long long *hoff; // [ntiles + 1] first hit of each tile
+    const long long *goff; // [ntiles + 1] first group of each tile
+    const int2 *grp;       // (other entity, hit count) per group
+    const float4 *hd;      // per hit: ray direction d, weight a
+    const uint32_t *hk;    // per hit: tile slot p << 9 | ray q (| h << 12)
+    const __nv_bfloat16 *rows_hi, *rows_lo; // [n][Cp x 16] blocked BF16 rows of the other entities
+    const float4 *N4, *P;
+    const float *cl;
+    int alpha_model;
+    float w; // pi / nd
+    // forward epilogue
+    const float *S, *Bprev;
+    float *Qout, *Bout;
+    __nv_bfloat16 *Bout16;           // row layout copy (stride 16 per column)
+    __nv_bfloat16 *Bblk, *Bblk_lo;   // blocked copies (lo: optional)
+    double *norm2;
+    // adjoint epilogue
+    float *vout, *u;
+    __nv_bfloat16 *yblk;
+    int *flags;
+};
+
+struct __align__(16) StageMeta {
+    int other, cnt;
+    long long h0;
+    float4 nrm;
+};
+
+__device__ __forceinline__ float alpha_at(int model, float o) {
+    if (model == RGS_ALPHA_GFSGS) return o > 0.f ? -expm1f(-0.03279f * powf(o, 3.4f)) : 0.f;
+    return o;
+}
+
+__device__ __forceinline__ bool aborted(const int *f) { return *(volatile const int *)f != 0; }
+
+__device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag) {
+    atomicExch(abort_flag, 1);
+    atomicAdd(&g.flags[FLAG_TC_TIMEOUT], 1);
+}
+
+// ------------------------------------------------------------------ the contraction kernel
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES], bar_afull[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_dfull, bar_dempty;
+    __shared__ StageMeta meta[TC_MAX_STAGES];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ float ybuf[TC_NB][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = g.stages;
+    const int items = g.ntiles * g.nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::bar_init(&bar_full[s], 1);
+            tc::bar_init(&bar_afull[s], 1);
+            tc::bar_init(&bar_empty[s], 1);
+        }
+        tc::bar_init(&bar_dfull, 1);
+        tc::bar_init(&bar_dempty, TC_NB);
+        abort_flag = 0;
+        tc::bar_init_fence();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        long long gcount = 0;
+        for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x) {
+            const int t = it / g.nchunks, ch = it - t * g.nchunks;
+            const int c0 = ch * TC_CHUNK;
+            const int cw = min(TC_CHUNK, g.Cp - c0);
+            const uint32_t bytes = (uint32_t)cw * 32u;
+            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            long long h = g.hoff[t];
+            for (long long gb = g0; gb < g1 && !aborted(&abort_flag); gb += 32) {
+                const int m = (int)min(32ll, g1 - gb);
+                int2 e = make_int2(0, 0);
+                float4 nrm = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (lane < m) {
+                    e = __ldg(&g.grp[gb + lane]);
+                    if (g.adjoint) nrm = __ldg(&g.N4[e.x]);
+                }
+                int incl = e.y; // inclusive scan of the counts: each group's first hit
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                const long long hs = h + (incl - e.y);
+                for (int q = 0; q < m; ++q) {
+                    const int other = __shfl_sync(0xffffffffu, e.x, q);
+                    const int cnt = __shfl_sync(0xffffffffu, e.y, q);
+                    const long long h0 = __shfl_sync(0xffffffffu, hs, q);
+                    float4 nq;
+                    nq.x = __shfl_sync(0xffffffffu, nrm.x, q);
+                    nq.y = __shfl_sync(0xffffffffu, nrm.y, q);
+                    nq.z = __shfl_sync(0xffffffffu, nrm.z, q);
+                    nq.w = 0.f;
+                    if (lane == 0) {
+                        const int s = (int)(gcount % S);
+                        const uint32_t ph = (uint32_t)((gcount / S) & 1);
+                        if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, TC_WAIT_NS)) {
+                            tc_fail(g, &abort_flag);
+                        } else {
+                            meta[s].other = other;
+                            meta[s].cnt = cnt;
+                            meta[s].h0 = h0;
+                            meta[s].nrm = nq;
+                            unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                            tc::bar_arrive_tx(&bar_full[s], bytes * (g.split ? 2u : 1u));
+                            const size_t rb = (size_t)other * (size_t)g.Cp * 16 + (size_t)c0 * 16;
+                            tc::bulk_g2s(st, g.rows_hi + rb, bytes, &bar_full[s]);
+                            if (g.split) tc::bulk_g2s(st + bytes, g.rows_lo + rb, bytes, &bar_full[s]);
+                        }
+                    }
+                    ++gcount;
+                    __syncwarp();
+                    if (aborted(&abort_flag)) break;
+                }
+                h += __shfl_sync(0xffffffffu, incl, m - 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        long long gcount = 0;
+        int tl = 0;
+        for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
+            const int t = it / g.nchunks, ch = it - t * g.nchunks;
+            const int c0 = ch * TC_CHUNK;
+            const int cw = min(TC_CHUNK, g.Cp - c0);
+            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            if (lane == 0) {
+                bool ok = true;
+                if (tl > 0) ok = tc::bar_wait(&bar_dempty, (uint32_t)((tl - 1) & 1), TC_WAIT_NS);
+                tc::fence_after();
+                if (!ok) tc_fail(g, &abort_flag);
+                for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gcount) {
+                    const int s = (int)(gcount % S);
+                    const uint32_t ph = (uint32_t)((gcount / S) & 1);
+                    if (!tc::bar_wait(&bar_afull[s], ph, TC_WAIT_NS) || !tc::bar_wait(&bar_full[s], ph, TC_WAIT_NS)) {
+                        tc_fail(g, &abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                    const uint32_t rows = tc::smem_addr(st);
+                    const uint32_t A = tc::smem_addr(st + g.rows_bytes);
+                    const uint32_t acc0 = (q == g0) ? 0u : 1u;
+                    for (int c = 0; c < cw; c += 256) {
+                        const int N = min(256, cw - c);
+                        const uint32_t id = tc::idesc_bf16(128, N);
+                        const uint32_t d = tmem + (uint32_t)c;
+                        const uint64_t da = tc::sdesc(A), db = tc::sdesc(rows + (uint32_t)c * 32u);
+                        tc::mma_bf16(d, da, db, id, acc0);
+                        if (g.split) {
+                            const uint32_t rbytes = (uint32_t)cw * 32u;
+                            const uint64_t da_lo = tc::sdesc(A + 4096u), db_lo = tc::sdesc(rows + rbytes + (uint32_t)c * 32u);
+                            tc::mma_bf16(d, da, db_lo, id, 1u);
+                            tc::mma_bf16(d, da_lo, db, id, 1u);
+                        }
+                    }
+                    tc::mma_commit(&bar_empty[s]);
+                }
+                tc::mma_commit(&bar_dfull); // after a failure the other roles give up on their own waits
+            }
+            __syncwarp();
+            gcount = __shfl_sync(0xffffffffu, gcount, 0);
+        }
+    } else {
+        // ---------------------------------------------------------- builders + epilogue
+        const int b = warp - 2;
+        const int k = lane & 15, mh = lane >> 4;
+        float cf[20];
+#pragma unroll
+        for (int q = 0; q < 20; ++q) cf[q] = TC_SH[k][q];
+        // forward: rows of the operand are receivers (X = Y(R_i d)), columns sources (Z = Y(-d));
+        // adjoint: rows are sources (X = Y(-d)), columns receivers (Z = Y(R_i d))
+        const int xoff = g.adjoint ? 0 : 16, zoff = g.adjoint ? 16 : 0;
+        long long gcount = 0;
+        int tl = 0;
+        for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
+            const int t = it / g.nchunks, ch = it - t * g.nchunks;
+            const int c0 = ch * TC_CHUNK;
+            const int cw = min(TC_CHUNK, g.Cp - c0);
+            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            for (long long q = g0; q < g1 && !aborted(&abort_flag); ++q, ++gcount) {
+                if ((int)(gcount % TC_NB) != b) continue;
+                const int s = (int)(gcount % S);
+                const uint32_t ph = (uint32_t)((gcount / S) & 1);
+                bool ok = true;
+                if (lane == 0) ok = tc::bar_wait(&bar_full[s], ph, TC_WAIT_NS);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp(); // lane 0's acquire of the stage covers the warp's reads of its meta
+                if (!ok) {
+                    if (lane == 0) tc_fail(g, &abort_flag);
+                    break;
+                }
+                const int cnt = meta[s].cnt;
+                const long long h0 = meta[s].h0;
+                const float3 ngrp = f3(meta[s].nrm);
+                unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                const uint32_t A = tc::smem_addr(st + g.rows_bytes);
+                float acc[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                int cur = -1;
+                unsigned written = 0;
+                auto flush = [&](int p) {
+                    const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
+                    uint4 hi, lo;
+                    float r[8];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) r[m] = __bfloat162float(__float2bfloat16_rn(acc[m]));
+                    hi.x = tc::pack_bf16(acc[0], acc[1]);
+                    hi.y = tc::pack_bf16(acc[2], acc[3]);
+                    hi.z = tc::pack_bf16(acc[4], acc[5]);
+                    hi.w = tc::pack_bf16(acc[6], acc[7]);
+                    tc::sts128(A + off, hi);
+                    if (g.split) {
+                        lo.x = tc::pack_bf16(acc[0] - r[0], acc[1] - r[1]);
+                        lo.y = tc::pack_bf16(acc[2] - r[2], acc[3] - r[3]);
+                        lo.z = tc::pack_bf16(acc[4] - r[4], acc[5] - r[5]);
+                        lo.w = tc::pack_bf16(acc[6] - r[6], acc[7] - r[7]);
+                        tc::sts128(A + 4096u + off, lo);
+                    }
+                    written |= 1u << p;
+                };
+                for (int base = 0; base < cnt; base += 32) {
+                    const int m_here = min(32, cnt - base);
+                    float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+                    uint32_t key = 0;
+                    if (lane < m_here) {
+                        rec = __ldg(&g.hd[h0 + base + lane]);
+                        key = __ldg(&g.hk[h0 + base + lane]);
+                    }
+                    for (int e = 0; e < m_here; ++e) {
+                        const float dx = __shfl_sync(0xffffffffu, rec.x, e);
+                        const float dy = __shfl_sync(0xffffffffu, rec.y, e);
+                        const float dz = __shfl_sync(0xffffffffu, rec.z, e);
+                        const float a = __shfl_sync(0xffffffffu, rec.w, e);
+                        const uint32_t kk = __shfl_sync(0xffffffffu, key, e);
+                        const int p = (int)((kk >> 9) & 7u);
+                        const float3 d = make_float3(dx, dy, dz);
+                        float3 nrm = ngrp;
+                        if (!g.adjoint) nrm = f3(__ldg(&g.N4[t * TC_R + p]));
+                        // lanes 0..15: Y_k(-d); lanes 16..31: Y_k(R d)
+                        const float3 v = (lane < 16) ? make_float3(-dx, -dy, -dz) : reflect_n(nrm, d);
+                        const float y = sh_mono(cf, v);
+                        ybuf[b][lane] = y;
+                        __syncwarp();
+                        const float X = ybuf[b][xoff + k];
+                        float Z[8];
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) Z[m] = ybuf[b][zoff + mh * 8 + m];
+                        __syncwarp();
+                        if (p != cur) {
+                            if (cur >= 0) flush(cur);
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                            cur = p;
+                        }
+                        const float ax = a * X;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) acc[m] = fmaf(ax, Z[m], acc[m]);
+                    }
+                }
+                if (cur >= 0) flush(cur);
+                const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+                for (int p = 0; p < TC_R; ++p) {
+                    if (written & (1u << p)) continue;
+                    const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
+                    tc::sts128(A + off, z4);
+                    if (g.split) tc::sts128(A + 4096u + off, z4);
+                }
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::bar_arrive(&bar_afull[s]);
+            }
+            if (aborted(&abort_flag)) break;
+            // ------------------------------------------------------ epilogue of the item
+            bool ok = true;
+            if (lane == 0) ok = tc::bar_wait(&bar_dfull, (uint32_t)(tl & 1), TC_WAIT_NS);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();
+            tc::fence_after();
+            if (!ok) {
+                if (lane == 0) tc_fail(g, &abort_flag);
+                break;
+            }
+            const bool empty = (g1 == g0);
+            const int quarter = warp & 3, half = b >> 2;
+            const int row = quarter * 32 + lane;
+            const int p = row >> 4, kr = row & 15;
+            const int e_ent = t * TC_R + p;
+            const bool live = e_ent < g.n;
+            const float oe = live ? alpha_at(g.alpha_model, __ldg(&g.P[e_ent].w)) : 0.f;
+            double dsq = 0.0;
+            for (int cb = half * 16; cb < cw; cb += 32) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb, v);
+                if (!live) continue;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = c0 + cb + q;
+                    if (c >= g.C) break;
+                    const float val = empty ? 0.f : v[q] * g.w;
+                    const size_t idx = ((size_t)e_ent * g.C + c) * 16 + kr;
+                    const float oc = oe * __ldg(&g.cl[(size_t)e_ent * 12 + band_of(kr) * 3 + (c % 3)]);
+                    const size_t bidx = (size_t)e_ent * g.Cp * 16 + tc::blk_off(c, kr) / 2;
+                    if (!g.adjoint) {
+                        g.Qout[idx] = val;
+                        const float bb = g.S[idx] + oc * val;
+                        g.Bout[idx] = bb;
+                        const __nv_bfloat16 bh = __float2bfloat16_rn(bb);
+                        if (g.Bout16) g.Bout16[idx] = bh;
+                        g.Bblk[bidx] = bh;
+                        if (g.Bblk_lo) g.Bblk_lo[bidx] = __float2bfloat16_rn(bb - __bfloat162float(bh));
+                        const double df = (double)bb - (double)g.Bprev[idx];
+                        dsq += df * df;
+                    } else {
+                        g.vout[idx] = val;
+                        g.u[idx] += val;
+                        g.yblk[bidx] = __float2bfloat16_rn(oc * val);
+                    }
+                }
+            }
+            if (!g.adjoint) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) dsq += __shfl_xor_sync(0xffffffffu, dsq, off);
+                if (lane == 0) atomicAdd(g.norm2, dsq);
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::bar_arrive(&bar_dempty);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------------ pair-tile construction
+// hits per receiver tile (forward): the sum of the counts of its rays
+__global__ void k_tc_tile_count_fwd(const int *__restrict__ cnt, int n, int nd, int ntiles, int *tcount) {
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    const long long r0 = (long long)t * TC_R * nd, r1 = (long long)min(n, (t + 1) * TC_R) * nd;
+    int s = 0;
+    for (long long r = r0 + lane; r < r1; r += 32) s += cnt[r];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) tcount[t] = s;
+}
+// hits per source tile (adjoint): from the per-source offsets of the trace
+__global__ void k_tc_tile_count_adj(const long long *__restrict__ src_off, int n, int ntiles, int *tcount) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    tcount[t] = (int)(src_off[min(n, (t + 1) * TC_R)] - src_off[t * TC_R]);
+}
+
+// forward: the tile's hits in ray order, key = j << 12 | rho << 9 | q, payload (a, h)
+__global__ void __launch_bounds__(256) k_tc_gather_fwd(RaysDev rays, int n, const long long *__restrict__ hoff,
+                                                       uint32_t *key, uint2 *pay) {
+    const int t = blockIdx.x;
+    const int nd = rays.nd;
+    const long long r0 = (long long)t * TC_R * nd, r1 = (long long)min(n, (t + 1) * TC_R) * nd;
+    __shared__ int wsum[8];
+    long long pos = hoff[t];
+    for (long long rb = r0; rb < r1; rb += 256) {
+        const long long r = rb + threadIdx.x;
+        const int c = (r < r1) ? rays.cnt[r] : 0;
+        // block exclusive scan of c
+        int incl = c;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int q = 0; q < 8; ++q) {
+            if (q < w) before += wsum[q];
+            total += wsum[q];
+        }
+        const long long out = pos + before + (incl - c);
+        if (c > 0) {
+            const long long base = rays.off[r];
+            const int rl = (int)(r - r0);
+            const uint32_t lo = (uint32_t)(((rl / nd) << 9) | (rl % nd));
+            for (int h = 0; h < c; ++h) {
+                const int2 ja = rays.rec_ja[base + h];
+                key[out + h] = ((uint32_t)ja.x << 12) | lo;
+                pay[out + h] = make_uint2((uint32_t)ja.y, (uint32_t)h);
+            }
+        }
+        pos += total;
+        __syncthreads();
+    }
+}
+
+// adjoint: every hit to its source tile (unordered), key = i << 12 | sigma << 9 | q
+__global__ void __launch_bounds__(256) k_tc_scatter_adj(RaysDev rays, long long n_rays, unsigned long long *cursor,
+                                                        uint32_t *key, uint2 *pay) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int c = rays.cnt[r];
+    const long long base = rays.off[r];
+    const int nd = rays.nd;
+    const int i = (int)(r / nd), q = (int)(r - (long long)i * nd);
+    for (int h = 0; h < c; ++h) {
+        const int2 ja = rays.rec_ja[base + h];
+        const unsigned long long at = atomicAdd(&cursor[ja.x / TC_R], 1ull);
+        key[at] = ((uint32_t)i << 12) | ((uint32_t)(ja.x % TC_R) << 9) | (uint32_t)q;
+        pay[at] = make_uint2((uint32_t)ja.y, (uint32_t)h);
+    }
+}
+
+__global__ void k_tc_cursor(const long long *__restrict__ hoff, int ntiles, unsigned long long *cursor) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) cursor[t] = (unsigned long long)hoff[t];
+}
+
+// one stable pass of a segmented LSD radix sort (one block per segment): elements of
+// segment t move by their digit (key >> shift) & 255, keeping their order within a digit
+constexpr int SORT_THREADS = 1024;
+__global__ void __launch_bounds__(SORT_THREADS) k_tc_sort_pass(const long long *__restrict__ seg, int shift,
+                                                                const uint32_t *__restrict__ kin,
+                                                                const uint2 *__restrict__ pin, uint32_t *kout,
+                                                                uint2 *pout) {
+    __shared__ int base[256];
+    __shared__ int tot[256];
+    __shared__ int wcnt[SORT_THREADS / 32][256];
+    const long long s0 = seg[blockIdx.x], s1 = seg[blockIdx.x + 1];
+    const int n = (int)(s1 - s0);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid < 256) base[tid] = 0;
+    __syncthreads();
+    for (int e = tid; e < n; e += SORT_THREADS) atomicAdd(&base[(kin[s0 + e] >> shift) & 255u], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int d = 0; d < 256; ++d) {
+            const int c = base[d];
+            base[d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += SORT_THREADS) {
+        for (int q = tid; q < (SORT_THREADS / 32) * 256; q += SORT_THREADS) (&wcnt[0][0])[q] = 0;
+        __syncthreads();
+        const int e = c0 + tid;
+        const bool valid = e < n;
+        uint32_t kv = 0;
+        uint2 pv = make_uint2(0u, 0u);
+        int d = 256; // sentinel for lanes past the end
+        if (valid) {
+            kv = kin[s0 + e];
+            pv = pin[s0 + e];
+            d = (int)((kv >> shift) & 255u);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        if (tid < 256) {
+            int run = 0;
+            for (int q = 0; q < SORT_THREADS / 32; ++q) {
+                const int c = wcnt[q][tid];
+                wcnt[q][tid] = run;
+                run += c;
+            }
+            tot[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const int at = base[d] + wcnt[w][d] + rank;
+            kout[s0 + at] = kv;
+            pout[s0 + at] = pv;
+        }
+        __syncthreads();
+        if (tid < 256) base[tid] += tot[tid];
+        __syncthreads();
+    }
+}
+
+// groups (runs of equal key >> 12) per segment
+__global__ void __launch_bounds__(256) k_tc_group_count(const long long *__restrict__ seg, const uint32_t *__restrict__ key,
+                                                        int *gcount) {
+    const long long s0 = seg[blockIdx.x], s1 = seg[blockIdx.x + 1];
+    int c = 0;
+    for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x)
+        c += (e == s0 || (key[e] >> 12) != (key[e - 1] >> 12)) ? 1 : 0;
+    __shared__ int red[8];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+        gcount[blockIdx.x] = s;
+    }
+}
+
+// group list (other entity, count) and the per-hit records (d, a) and keys (p, q, h)
+__global__ void __launch_bounds__(256) k_tc_finish(const long long *__restrict__ seg, const long long *__restrict__ goff,
+                                                   const uint32_t *__restrict__ key, const uint2 *__restrict__ pay,
+                                                   const float4 *__restrict__ dir, int nd, int adjoint, int ntile_ent,
+                                                   int2 *grp, float4 *hd, uint32_t *hk) {
+    const int t = blockIdx.x;
+    const long long s0 = seg[t], s1 = seg[t + 1];
+    // records: element-parallel
+    for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
+        const uint32_t kv = key[e];
+        const uint2 pv = pay[e];
+        const int other = (int)(kv >> 12), p = (int)((kv >> 9) & 7u), q = (int)(kv & 511u);
+        const int recv = adjoint ? other : t * ntile_ent + p;
+        const float4 d = dir[(long long)recv * nd + q];
+        hd[e] = make_float4(d.x, d.y, d.z, __uint_as_float(pv.x));
+        hk[e] = (uint32_t)((p << 9) | q) | (pv.y << 12);
+    }
+    // groups: one warp walks the segment in 32-element windows
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        long long gi = goff[t];
+        long long start = s0;
+        for (long long e0 = s0; e0 < s1; e0 += 32) {
+            const long long e = e0 + lane;
+            const bool in = e < s1;
+            const bool head = in && (e == s0 || (key[e] >> 12) != (key[e - 1] >> 12));
+            const unsigned heads = __ballot_sync(0xffffffffu, head);
+            // every head closes the previous group
+            unsigned hm = heads;
+            while (hm) {
+                const int l = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const long long he = e0 + l;
+                if (he != s0 && lane == 0) {
+                    grp[gi] = make_int2((int)(key[start] >> 12), (int)(he - start));
+                    ++gi;
+                }
+                start = he;
+            }
+        }
+        if (lane == 0 && s1 > s0) grp[gi] = make_int2((int)(key[start] >> 12), (int)(s1 - start));
+    }
+}
+
+// y = o c (x) v in the blocked BF16 layout (the adjoint's first right-hand side)
+__global__ void k_tc_make_y(int n, int C, int Cp, int alpha_model, const float4 *__restrict__ P,
+                            const float *__restrict__ cl, const float *__restrict__ v, __nv_bfloat16 *yblk) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * C * 16) return;
+    const int k = (int)(idx & 15);
+    const size_t ic = idx >> 4;
+    const int c = (int)(ic % C);
+    const int i = (int)(ic / C);
+    const float o = alpha_at(alpha_model, P[i].w);
+    const float y = o * cl[(size_t)i * 12 + band_of(k) * 3 + (c % 3)] * v[idx];
+    yblk[(size_t)i * Cp * 16 + tc::blk_off(c, k) / 2] = __float2bfloat16_rn(y);
+}
+// x in the blocked BF16 layout, hi and (optionally) lo parts
+__global__ void k_tc_to_blk(int n, int C, int Cp, const float *__restrict__ x, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * C * 16) return;
+    const int k = (int)(idx & 15);
+    const size_t ic = idx >> 4;
+    const int c = (int)(ic % C);
+    const int i = (int)(ic / C);
+    const float v = x[idx];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const size_t b = (size_t)i * Cp * 16 + tc::blk_off(c, k) / 2;
+    hi[b] = h;
+    if (lo) lo[b] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+} // namespace
+
+// ------------------------------------------------------------------ host side
+struct TcPairs {
+    int ntiles = 0;
+    long long n_hits = 0, n_groups = 0;
+    long long *hoff = nullptr, *goff = nullptr;
+    int2 *grp = nullptr;
+    float4 *hd = nullptr;
+    uint32_t *hk = nullptr;
+};
+
+struct rgs_tc_state {
+    TcPairs fwd, adj;
+    bool fwd_ok = false, adj_ok = false;
+    long long bytes = 0;
+    int Cp = 0;
+    __nv_bfloat16 *blk[3] = {nullptr, nullptr, nullptr}; // ping, pong, lo
+    long long blk_cap = 0;
+};
+
+namespace {
+
+void pairs_free(TcPairs &p) {
+    dev_free(p.hoff);
+    dev_free(p.goff);
+    dev_free(p.grp);
+    dev_free(p.hd);
+    dev_free(p.hk);
+    p = TcPairs{};
+}
+
+// builds one pair-tile structure (forward: receiver tiles; adjoint: source tiles)
+rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t st) {
+    rgs_status r;
+    const int n = t->n, nd = t->nd;
+    const int ntiles = (n + TC_R - 1) / TC_R;
+    const long long H = t->n_hits;
+    RaysDev rd = t->rays();
+    pairs_free(P);
+    P.ntiles = ntiles;
+    P.n_hits = H;
+    int *tcount = nullptr;
+    uint32_t *kA = nullptr, *kB = nullptr;
+    uint2 *pA = nullptr, *pB = nullptr;
+    unsigned long long *cur = nullptr;
+    long long *scan_tmp = nullptr;
+    struct Tmp {
+        cudaStream_t st;
+        int **tc;
+        uint32_t **ka, **kb;
+        uint2 **pa, **pb;
+        unsigned long long **cu;
+        long long **sc;
+        ~Tmp() {
+            pool_release(*tc, st);
+            pool_release(*ka, st);
+            pool_release(*kb, st);
+            pool_release(*pa, st);
+            pool_release(*pb, st);
+            pool_release(*cu, st);
+            pool_release(*sc, st);
+        }
+    } tmp{st, &tcount, &kA, &kB, &pA, &pB, &cur, &scan_tmp};
+    const int scan_cap = rgs_scan_tmp_size(ntiles);
+    if ((r = pool_alloc(&tcount, (size_t)ntiles + 1, st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&scan_tmp, (size_t)scan_cap, st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&kA, (size_t)std::max(H, 1ll), st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&kB, (size_t)std::max(H, 1ll), st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&pA, (size_t)std::max(H, 1ll), st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&pB, (size_t)std::max(H, 1ll), st)) != RGS_OK) return r;
+    if ((r = dev_alloc(&P.hoff, (size_t)ntiles + 1)) != RGS_OK) return r;
+    if ((r = dev_alloc(&P.goff, (size_t)ntiles + 1)) != RGS_OK) return r;
+    if ((r = dev_alloc(&P.hd, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
+    if ((r = dev_alloc(&P.hk, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
+    if (!adjoint) {
+        { ProfScope ps_("k_tc_tile_count", st); k_tc_tile_count_fwd<<<(ntiles + 7) / 8, 256, 0, st>>>(t->cnt, n, nd, ntiles, tcount); }
+    } else {
+        { ProfScope ps_("k_tc_tile_count", st); k_tc_tile_count_adj<<<(ntiles + 255) / 256, 256, 0, st>>>(t->src_off, n, ntiles, tcount); }
+    }
+    RGS_LAUNCH("tc tile count");
+    if ((r = rgs_scan_counts(tcount, P.hoff, ntiles, scan_tmp, scan_cap, st)) != RGS_OK) return r;
+    int passes_lo;
+    if (!adjoint) {
+        { ProfScope ps_("k_tc_gather", st); k_tc_gather_fwd<<<ntiles, 256, 0, st>>>(rd, n, P.hoff, kA, pA); }
+        passes_lo = 12; // ray order already sorts the low 12 bits (rho, q); sort j stably
+    } else {
+        if ((r = pool_alloc(&cur, (size_t)ntiles, st)) != RGS_OK) return r;
+        { ProfScope ps_("k_tc_cursor", st); k_tc_cursor<<<(ntiles + 255) / 256, 256, 0, st>>>(P.hoff, ntiles, cur); }
+        const long long n_rays = (long long)n * nd;
+        { ProfScope ps_("k_tc_scatter", st); k_tc_scatter_adj<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(rd, n_rays, cur, kA, pA); }
+        passes_lo = 0; // arbitrary order: sort all 32 bits
+    }
+    RGS_LAUNCH("tc gather");
+    // LSD passes of 8 bits from passes_lo up to bit 32 (keys: entity < 2^20 above bit 12)
+    uint32_t *kin = kA, *kout = kB;
+    uint2 *pin = pA, *pout = pB;
+    for (int shift = passes_lo; shift < 32; shift += 8) {
+        { ProfScope ps_("k_tc_sort_pass", st); k_tc_sort_pass<<<ntiles, SORT_THREADS, 0, st>>>(P.hoff, shift, kin, pin, kout, pout); }
+        std::swap(kin, kout);
+        std::swap(pin, pout);
+    }
+    RGS_LAUNCH("tc sort");
+    { ProfScope ps_("k_tc_group_count", st); k_tc_group_count<<<ntiles, 256, 0, st>>>(P.hoff, kin, tcount); }
+    RGS_LAUNCH("tc group count");
+    if ((r = rgs_scan_counts(tcount, P.goff, ntiles, scan_tmp, scan_cap, st)) != RGS_OK) return r;
+    long long ng = 0;
+    RGS_CUDA(cudaMemcpyAsync(&ng, P.goff + ntiles, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    RGS_CUDA(cudaStreamSynchronize(st));
+    P.n_groups = ng;
+    if ((r = dev_alloc(&P.grp, (size_t)std::max(ng, 1ll))) != RGS_OK) return r;
+    { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, nd, adjoint ? 1 : 0, TC_R, P.grp, P.hd, P.hk); }
+    RGS_LAUNCH("tc finish");
+    return RGS_OK;
+}
+
+int g_num_sms = 0;
+
+rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
+    if (!g_num_sms) {
+        int dev = 0;
+        RGS_CUDA(cudaGetDevice(&dev));
+        RGS_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int cw = std::min(TC_CHUNK, a.Cp);
+    a.nchunks = (a.Cp + TC_CHUNK - 1) / TC_CHUNK;
+    a.rows_bytes = (uint32_t)cw * 32u * (a.split ? 2u : 1u);
+    a.a_bytes = 4096u * (a.split ? 2u : 1u);
+    a.stage_bytes = (a.rows_bytes + a.a_bytes + 1023u) & ~1023u;
+    const uint32_t budget = 200u * 1024u;
+    a.stages = (int)std::min<uint32_t>(TC_MAX_STAGES, budget / a.stage_bytes);
+    if (a.stages < 2) {
+        rgs_set_error("tensor-core contraction: stage of %u bytes too large", a.stage_bytes);
+        return RGS_ERR_ARG;
+    }
+    // at least 120 KB, so that one CTA (and its 512 TMEM columns) holds an SM
+    const size_t smem = std::max<size_t>((size_t)a.stages * a.stage_bytes, 120u * 1024u);
+    RGS_CUDA(cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int items = a.ntiles * a.nchunks;
+    const int grid = std::max(1, std::min(items, g_num_sms));
+    {
+        ProfScope ps_(a.adjoint ? "k_tc_adjoint" : "k_tc_bounce", st);
+        k_tc_contract<<<grid, TC_THREADS, smem, st>>>(a);
+    }
+    RGS_LAUNCH("tensor-core contraction");
+    return RGS_OK;
+}
+
+} // namespace
+
+void rgs_tc_free(rgs_transport *t) {
+    if (!t->tc) return;
+    pairs_free(t->tc->fwd);
+    pairs_free(t->tc->adj);
+    for (auto &b : t->tc->blk) dev_free(b);
+    delete t->tc;
+    t->tc = nullptr;
+}
+
+rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st) {
+    int f = 0;
+    RGS_CUDA(cudaMemcpyAsync(&f, t->flags + FLAG_TC_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RGS_CUDA(cudaStreamSynchronize(st));
+    if (f) {
+        rgs_set_error("tensor-core contraction: %d bounded waits ran out (a pipeline role stopped)", f);
+        return RGS_ERR_TIMEOUT;
+    }
+    return RGS_OK;
+}
+
+void rgs_tc_invalidate(rgs_transport *t) {
+    if (!t->tc) return;
+    t->tc->fwd_ok = t->tc->adj_ok = false;
+}
+
+bool rgs_tc_eligible(const rgs_transport *t, int precision) {
+    if (t->tc_mode == 0) return false; // disabled by the caller
+    if (t->kind != RGS_KIND_HEMISPHERE || t->nc != 16 || precision == RGS_FP32) return false;
+    if (t->n > (1 << 20) || t->nd > 512 || t->n_hits <= 0) return false;
+    if (t->tc_mode < 0 && t->C < RGS_TC_MIN_COLS) return false; // automatic: many right-hand sides only
+    if (t->stride != 0) return false; // the adjoint reads every iterate of this path
+    // memory: two structures of 20 B per hit, three blocked BF16 arrays, sort scratch of 24 B per hit
+    const double need = 2.0 * 20.0 * t->n_hits + 24.0 * t->n_hits + 3.0 * 2.0 * t->n * (double)((t->C + 15) & ~15) * 16;
+    return need < 0.8 * (double)pool_available_bytes();
+}
+
+// the forward structure and the blocked BF16 buffers (built once per trace)
+rgs_status rgs_tc_prepare(rgs_transport *t, cudaStream_t st) {
+    rgs_status r;
+    if (!t->tc) t->tc = new rgs_tc_state();
+    rgs_tc_state &s = *t->tc;
+    const int Cp = (t->C + 15) & ~15; // MMA pieces of N = 16k columns
+    const long long need = (long long)t->n * Cp * 16;
+    if (need > s.blk_cap || s.Cp != Cp) {
+        for (auto &b : s.blk)
+            if ((r = dev_alloc(&b, (size_t)need, &t->device_bytes)) != RGS_OK) return r;
+        s.blk_cap = need;
+        s.Cp = Cp;
+        for (auto &b : s.blk) RGS_CUDA(cudaMemsetAsync(b, 0, sizeof(__nv_bfloat16) * need, st)); // padding columns stay 0
+    }
+    if (!s.fwd_ok) {
+        if ((r = build_pairs(t, false, s.fwd, st)) != RGS_OK) return r;
+        s.fwd_ok = true;
+    }
+    return RGS_OK;
+}
+
+rgs_status rgs_tc_prepare_adjoint(rgs_transport *t, cudaStream_t st) {
+    rgs_status r;
+    if ((r = rgs_tc_prepare(t, st)) != RGS_OK) return r;
+    if (!t->tc->adj_ok) {
+        if ((r = build_pairs(t, true, t->tc->adj, st)) != RGS_OK) return r;
+        t->tc->adj_ok = true;
+    }
+    return RGS_OK;
+}
+
+// B^(0) = S into the blocked buffer `slot` (hi) and, with lo, its low part
+rgs_status rgs_tc_load_blk(rgs_transport *t, const float *x, int slot, bool lo, cudaStream_t st) {
+    rgs_tc_state &s = *t->tc;
+    const size_t tot = t->arr();
+    { ProfScope ps_("k_tc_to_blk", st); k_tc_to_blk<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t->n, t->C, s.Cp, x, s.blk[slot], lo ? s.blk[2] : nullptr); }
+    RGS_LAUNCH("to blocked");
+    return RGS_OK;
+}
+
+// one forward bounce on the tensor cores: reads blk[in] (and blk[2] as lo when split),
+// writes Q, B (FP32), B16 (row layout, optional), blk[out] and, with want_lo, blk[2]
+rgs_status rgs_tc_bounce(rgs_transport *t, int in, int out, bool split, bool want_lo, const float *Bprev,
+                         const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16, double *norm2, cudaStream_t st) {
+    rgs_tc_state &s = *t->tc;
+    TcArgs a{};
+    a.adjoint = 0;
+    a.split = split ? 1 : 0;
+    a.n = t->n;
+    a.C = t->C;
+    a.Cp = s.Cp;
+    a.nd = t->nd;
+    a.ntiles = s.fwd.ntiles;
+    a.hoff = s.fwd.hoff;
+    a.goff = s.fwd.goff;
+    a.grp = s.fwd.grp;
+    a.hd = s.fwd.hd;
+    a.hk = s.fwd.hk;
+    a.rows_hi = s.blk[in];
+    a.rows_lo = split ? s.blk[2] : nullptr;
+    a.N4 = t->sc->N4;
+    a.P = t->sc->P;
+    a.cl = t->sc->cl;
+    a.alpha_model = t->sc->alpha_model;
+    a.w = 3.14159265358979f / (float)t->nd;
+    a.S = S;
+    a.Bprev = Bprev;
+    a.Qout = Q;
+    a.Bout = Bout;
+    a.Bout16 = Bout16;
+    a.Bblk = s.blk[out];
+    a.Bblk_lo = want_lo ? s.blk[2] : nullptr;
+    a.norm2 = norm2;
+    a.flags = t->flags;
+    return launch_contract(t, a, st);
+}
+
+// y^(0) = o c (x) v^(0) into blk[slot]
+rgs_status rgs_tc_make_y(rgs_transport *t, const float *v, int slot, cudaStream_t st) {
+    rgs_tc_state &s = *t->tc;
+    const size_t tot = t->arr();
+    { ProfScope ps_("k_tc_make_y", st); k_tc_make_y<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t->n, t->C, s.Cp, t->sc->alpha_model, t->sc->P, t->sc->cl, v, s.blk[slot]); }
+    RGS_LAUNCH("make y");
+    return RGS_OK;
+}
+
+// one transposed bounce: v_out = K^T v_in from y_in = blk[in]; u += v_out; y_out = blk[out]
+rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout, float *u, cudaStream_t st) {
+    rgs_tc_state &s = *t->tc;
+    TcArgs a{};
+    a.adjoint = 1;
+    a.split = 0;
+    a.n = t->n;
+    a.C = t->C;
+    a.Cp = s.Cp;
+    a.nd = t->nd;
+    a.ntiles = s.adj.ntiles;
+    a.hoff = s.adj.hoff;
+    a.goff = s.adj.goff;
+    a.grp = s.adj.grp;
+    a.hd = s.adj.hd;
+    a.hk = s.adj.hk;
+    a.rows_hi = s.blk[in];
+    a.N4 = t->sc->N4;
+    a.P = t->sc->P;
+    a.cl = t->sc->cl;
+    a.alpha_model = t->sc->alpha_model;
+    a.w = 3.14159265358979f / (float)t->nd;
+    a.vout = vout;
+    a.u = u;
+    a.yblk = s.blk[out];
+    a.flags = t->flags;
+    return launch_contract(t, a, st);
+}

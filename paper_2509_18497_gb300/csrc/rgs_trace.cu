@@ -250,6 +250,8 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
     const int n = sc->n;
     rgs_status r;
     t->kind = RGS_KIND_HEMISPHERE;
+    rgs_tc_invalidate(t);
+    t->tc_used = false;
     t->nd = o->nd;
     t->na = strata_a(o->nd);
     t->nbs = o->nd / t->na;

@@ -29,7 +29,8 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_transport_info_get", "rgs_destroy_transport", "rgs_destroy_scene", "rgs_profile_enable",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
-           "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_trace_pairs",
+           "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_set_tensor_cores",
+           "rgs_trace_pairs",
            "rgs_adjoint_pairs", "rgs_adjoint_pairs_geometry", "rgs_adjoint_geometry")
 
 
@@ -131,6 +132,8 @@ def load(path=LIB_PATH):
     L.rgs_adjoint_geometry.restype = ct.c_int
     L.rgs_set_memory_budget.argtypes = [vp, ct.c_int64]
     L.rgs_set_memory_budget.restype = ct.c_int
+    L.rgs_set_tensor_cores.argtypes = [vp, ct.c_int32]
+    L.rgs_set_tensor_cores.restype = ct.c_int
     L.rgs_trim_workspace.argtypes = []
     L.rgs_trim_workspace.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
@@ -359,6 +362,12 @@ def rgs_set_memory_budget(transport, nbytes):
     """Bytes the transport may hold with its pooled scratch (0: no budget); steers the
     automatic checkpoint stride and the number of transposed-index parts of the adjoint."""
     _check(load().rgs_set_memory_budget(transport.h, int(nbytes)))
+
+
+def rgs_set_tensor_cores(transport, mode):
+    """Contraction of the batched modes: -1 automatic (tensor cores from 96 columns), 0 the
+    row-gather kernels, 1 the tensor-core form wherever it applies."""
+    _check(load().rgs_set_tensor_cores(transport.h, int(mode)))
 
 
 def rgs_trim_workspace():

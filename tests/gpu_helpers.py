@@ -15,11 +15,13 @@ def rel_l2(a, b):
 
 
 def run_gpu(sc, W=None, alpha_model=rgs.RGS_ALPHA_GAUSS, iterates=False, stats=False, precision=rgs.RGS_FP32,
-            checkpoint=0, pairs=False, geometry=False):
+            checkpoint=0, pairs=False, geometry=False, tensor_cores=-1, mem_budget=0):
     """build -> trace -> solve (-> adjoint with dL/dB = W) on cuda:0; numpy float64 out.
-    pairs: the center-to-center transport (the adjoint then also returns dlam)."""
+    pairs: the center-to-center transport (the adjoint then also returns dlam);
+    tensor_cores: rgs_set_tensor_cores mode of the batched precisions."""
     d = api.upload(sc)
-    pipe = api.Pipeline(alpha_model, precision, checkpoint=checkpoint, pairs=pairs)
+    pipe = api.Pipeline(alpha_model, precision, checkpoint=checkpoint, pairs=pairs, tensor_cores=tensor_cores,
+                        mem_budget=mem_budget)
     pipe.build(d)
     pipe.trace(d)
     B, st = pipe.solve(d["E"], d["nb"], stats=stats)
