@@ -361,6 +361,15 @@ rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
  * Host-only.  Errors: RGS_ERR_ARG (NULL transport, mode outside [-1, 1]). */
 rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode);
 
+/* Limit, in nanoseconds, of every wait inside the tensor-core contraction's pipeline (a
+ * role waiting for a stage of source rows, an operand, a finished accumulator; 0 = default,
+ * 4 s).  A wait that runs out makes every role of the kernel stop, wait (for at most a
+ * second) for its own copies and MMAs in flight, free its tensor memory and return; the
+ * solve or adjoint then returns RGS_ERR_TIMEOUT (the results are invalid, the context stays
+ * usable).  The library's service watchdog for the contraction; its tests set a tiny limit.
+ * Host-only.  Errors: RGS_ERR_ARG (NULL transport, negative limit). */
+rgs_status rgs_set_wait_limit(rgs_transport *t, int64_t ns);
+
 /* Workspace pool: the per-call scratch of rgs_adjoint (the transposed hit index, 8 bytes per
  * hit; per-hit opacity sums, 4 bytes; v^(a) and u; per-ray adjoint values) and of
  * rgs_get_iterate comes from one stream-ordered memory pool per device, so transports used

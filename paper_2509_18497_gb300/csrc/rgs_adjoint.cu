@@ -805,7 +805,7 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
     // the last solve ran on the tensor cores: so do the transposed bounces (source tiles
     // instead of the transposed hit index and the per-ray adjoint values)
     const bool tcp = t->tc_used && t->kind == RGS_KIND_HEMISPHERE && t->stride == 0 && nb >= 1;
-    if (tcp && (r = rgs_tc_prepare_adjoint(t, st)) != RGS_OK) return r;
+    if (tcp && ((r = rgs_tc_prepare_adjoint(t, st)) != RGS_OK || (r = rgs_tc_reset_flags(t, st)) != RGS_OK)) return r;
     if (want_geo) {
         RgsGeoAcc &geo = scratch.geo;
         if ((r = pool_alloc(&geo.dp, (size_t)n * 3, st)) != RGS_OK) return r;

@@ -506,6 +506,15 @@ rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode) {
     return RGS_OK;
 }
 
+rgs_status rgs_set_wait_limit(rgs_transport *t, int64_t ns) {
+    if (!t || ns < 0) {
+        rgs_set_error("rgs_set_wait_limit: NULL transport or negative limit");
+        return RGS_ERR_ARG;
+    }
+    t->tc_wait_ns = ns ? (unsigned long long)ns : 4000000000ull;
+    return RGS_OK;
+}
+
 rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes) {
     if (!t || bytes < 0) {
         rgs_set_error("rgs_set_memory_budget: NULL transport or negative budget");

@@ -66,7 +66,7 @@ enum {
     FLAG_FULL_RAYS = 1, // rays whose full RGS_HMAX buffer ended above the transmittance cut
     FLAG_STACK = 2,     // traversal stack overflow (the ray then misses the rest of the tree)
     FLAG_NONFINITE = 3,
-    FLAG_TC_TIMEOUT = 4, // a bounded wait of the tensor-core contraction ran out
+    FLAG_TC_TIMEOUT = 4, // a bounded wait of the tensor-core contraction ran out (5, 6: where)
     FLAG_COUNT = 8
 };
 
@@ -695,6 +695,7 @@ struct rgs_transport {
     long long device_bytes = 0;
     // tensor-core contraction (batched modes): -1 automatic (many columns), 0 off, 1 always
     int tc_mode = -1;
+    unsigned long long tc_wait_ns = 4000000000ull; // limit of each pipeline wait (rgs_set_wait_limit)
     bool tc_used = false; // the last solve ran on the tensor-core path
     rgs_tc_state *tc = nullptr;
     RaysDev rays() const {
@@ -823,6 +824,7 @@ rgs_status rgs_tc_bounce(rgs_transport *t, int in, int out, bool split, bool wan
 rgs_status rgs_tc_make_y(rgs_transport *t, const float *v, int slot, cudaStream_t st);
 rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout, float *u, cudaStream_t st);
 rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st); // RGS_ERR_TIMEOUT if a bounded wait ran out
+rgs_status rgs_tc_reset_flags(rgs_transport *t, cudaStream_t st);
 void rgs_tc_invalidate(rgs_transport *t);
 void rgs_tc_free(rgs_transport *t);
 

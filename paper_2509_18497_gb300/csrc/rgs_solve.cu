@@ -90,6 +90,7 @@ rgs_status run_solve_tc(rgs_transport *t, const float *E, int nb, int precision,
     launch_make_S<16>(t, E, t->iters, t->iters16, st);
     RGS_LAUNCH("make_S");
     if ((r = rgs_tc_prepare(t, st)) != RGS_OK) return r;
+    if ((r = rgs_tc_reset_flags(t, st)) != RGS_OK) return r;
     const bool rescorr = precision == RGS_BF16_FP32ACC_RESCORR;
     if ((r = rgs_tc_load_blk(t, t->iters, 0, rescorr && nb == 1, st)) != RGS_OK) return r;
     for (int b = 1; b <= nb; ++b) {

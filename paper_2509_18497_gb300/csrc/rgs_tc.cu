@@ -37,7 +37,7 @@ constexpr int TC_NB = 8;          // builder warps
 constexpr int TC_THREADS = (2 + TC_NB) * 32;
 constexpr int TC_MAX_STAGES = 8;
 constexpr int TC_CHUNK = 512;     // columns per pass (TMEM holds 512 FP32 columns)
-constexpr uint64_t TC_WAIT_NS = 4000000000ull; // 4 s per wait before giving up
+constexpr uint64_t TC_DRAIN_NS = 1000000000ull; // wait for in-flight copies and MMAs at exit
 
 // ------------------------------------------------------------------ SH as monomials
 // Y_k(v) = sum_q TC_SH[k][q] m_q(v) with the 20 monomials of degree <= 3
@@ -115,6 +115,7 @@ struct TcArgs {
     float *vout, *u;
     __nv_bfloat16 *yblk;
     int *flags;
+    unsigned long long wait_ns; // limit of every pipeline wait
 };
 
 struct __align__(16) StageMeta {
@@ -130,16 +131,21 @@ __device__ __forceinline__ float alpha_at(int model, float o) {
 
 __device__ __forceinline__ bool aborted(const int *f) { return *(volatile const int *)f != 0; }
 
-__device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag) {
+// where = role * 16 + wait site (1 producer empty, 2 mma dempty, 3 mma afull/full, 4 builder
+// full, 5 builder dfull); the first failure's site and group count are kept for the message
+__device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int where, long long gcount) {
     atomicExch(abort_flag, 1);
-    atomicAdd(&g.flags[FLAG_TC_TIMEOUT], 1);
+    if (atomicAdd(&g.flags[FLAG_TC_TIMEOUT], 1) == 0) {
+        g.flags[FLAG_TC_TIMEOUT + 1] = where;
+        g.flags[FLAG_TC_TIMEOUT + 2] = (int)gcount;
+    }
 }
 
 // ------------------------------------------------------------------ the contraction kernel
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES], bar_afull[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
-    __shared__ __align__(8) uint64_t bar_dfull, bar_dempty;
+    __shared__ __align__(8) uint64_t bar_dfull, bar_dempty, bar_drain;
     __shared__ StageMeta meta[TC_MAX_STAGES];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
@@ -156,6 +162,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         }
         tc::bar_init(&bar_dfull, 1);
         tc::bar_init(&bar_dempty, TC_NB);
+        tc::bar_init(&bar_drain, 1);
         abort_flag = 0;
         tc::bar_init_fence();
     }
@@ -202,8 +209,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     if (lane == 0) {
                         const int s = (int)(gcount % S);
                         const uint32_t ph = (uint32_t)((gcount / S) & 1);
-                        if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, TC_WAIT_NS)) {
-                            tc_fail(g, &abort_flag);
+                        if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
+                            tc_fail(g, &abort_flag, 1, gcount);
                         } else {
                             meta[s].other = other;
                             meta[s].cnt = cnt;
@@ -223,6 +230,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 h += __shfl_sync(0xffffffffu, incl, m - 1);
             }
         }
+        // no bulk copy may still be writing into this CTA's shared memory when it exits: wait
+        // (bounded) for the last fill of every stage
+        if (lane == 0)
+            for (long long q = gcount - 1; q >= 0 && q >= gcount - S; --q)
+                tc::bar_wait(&bar_full[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
+        __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         long long gcount = 0;
@@ -234,14 +247,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
             if (lane == 0) {
                 bool ok = true;
-                if (tl > 0) ok = tc::bar_wait(&bar_dempty, (uint32_t)((tl - 1) & 1), TC_WAIT_NS);
+                if (tl > 0) ok = tc::bar_wait(&bar_dempty, (uint32_t)((tl - 1) & 1), g.wait_ns);
                 tc::fence_after();
-                if (!ok) tc_fail(g, &abort_flag);
+                if (!ok) tc_fail(g, &abort_flag, 2, gcount);
                 for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gcount) {
                     const int s = (int)(gcount % S);
                     const uint32_t ph = (uint32_t)((gcount / S) & 1);
-                    if (!tc::bar_wait(&bar_afull[s], ph, TC_WAIT_NS) || !tc::bar_wait(&bar_full[s], ph, TC_WAIT_NS)) {
-                        tc_fail(g, &abort_flag);
+                    if (!tc::bar_wait(&bar_afull[s], ph, g.wait_ns) || !tc::bar_wait(&bar_full[s], ph, g.wait_ns)) {
+                        tc_fail(g, &abort_flag, 3, gcount);
                         ok = false;
                         break;
                     }
@@ -270,6 +283,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             __syncwarp();
             gcount = __shfl_sync(0xffffffffu, gcount, 0);
         }
+        // every MMA this thread issued has completed before the TMEM is freed
+        if (lane == 0) {
+            tc::mma_commit(&bar_drain);
+            tc::bar_wait(&bar_drain, 0u, TC_DRAIN_NS);
+        }
+        __syncwarp();
     } else {
         // ---------------------------------------------------------- builders + epilogue
         const int b = warp - 2;
@@ -288,15 +307,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             const int cw = min(TC_CHUNK, g.Cp - c0);
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
             for (long long q = g0; q < g1 && !aborted(&abort_flag); ++q, ++gcount) {
-                if ((int)(gcount % TC_NB) != b) continue;
+                // builder b owns stage b: every use of a stage is then awaited by the warp that
+                // awaited its previous use, so a parity wait cannot see a phase two uses old
                 const int s = (int)(gcount % S);
+                if (s != b) continue;
                 const uint32_t ph = (uint32_t)((gcount / S) & 1);
                 bool ok = true;
-                if (lane == 0) ok = tc::bar_wait(&bar_full[s], ph, TC_WAIT_NS);
+                if (lane == 0) ok = tc::bar_wait(&bar_full[s], ph, g.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 __syncwarp(); // lane 0's acquire of the stage covers the warp's reads of its meta
                 if (!ok) {
-                    if (lane == 0) tc_fail(g, &abort_flag);
+                    if (lane == 0) tc_fail(g, &abort_flag, 16 * (2 + b) + 4, gcount);
                     break;
                 }
                 const int cnt = meta[s].cnt;
@@ -383,12 +404,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             if (aborted(&abort_flag)) break;
             // ------------------------------------------------------ epilogue of the item
             bool ok = true;
-            if (lane == 0) ok = tc::bar_wait(&bar_dfull, (uint32_t)(tl & 1), TC_WAIT_NS);
+            if (lane == 0) ok = tc::bar_wait(&bar_dfull, (uint32_t)(tl & 1), g.wait_ns);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             __syncwarp();
             tc::fence_after();
             if (!ok) {
-                if (lane == 0) tc_fail(g, &abort_flag);
+                if (lane == 0) tc_fail(g, &abort_flag, 16 * (2 + b) + 5, gcount);
                 break;
             }
             const bool empty = (g1 == g0);
@@ -812,8 +833,9 @@ rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
     a.rows_bytes = (uint32_t)cw * 32u * (a.split ? 2u : 1u);
     a.a_bytes = 4096u * (a.split ? 2u : 1u);
     a.stage_bytes = (a.rows_bytes + a.a_bytes + 1023u) & ~1023u;
-    const uint32_t budget = 200u * 1024u;
-    a.stages = (int)std::min<uint32_t>(TC_MAX_STAGES, budget / a.stage_bytes);
+    const uint32_t budget = 220u * 1024u;
+    // at most one stage per builder warp (a builder owns its stage)
+    a.stages = (int)std::min<uint32_t>(std::min(TC_MAX_STAGES, TC_NB), budget / a.stage_bytes);
     if (a.stages < 2) {
         rgs_set_error("tensor-core contraction: stage of %u bytes too large", a.stage_bytes);
         return RGS_ERR_ARG;
@@ -842,12 +864,19 @@ void rgs_tc_free(rgs_transport *t) {
     t->tc = nullptr;
 }
 
+// clears the contraction's failure record before a solve or an adjoint on the tensor cores
+rgs_status rgs_tc_reset_flags(rgs_transport *t, cudaStream_t st) {
+    RGS_CUDA(cudaMemsetAsync(t->flags + FLAG_TC_TIMEOUT, 0, 3 * sizeof(int), st));
+    return RGS_OK;
+}
+
 rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st) {
-    int f = 0;
-    RGS_CUDA(cudaMemcpyAsync(&f, t->flags + FLAG_TC_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int f[3] = {0, 0, 0};
+    RGS_CUDA(cudaMemcpyAsync(f, t->flags + FLAG_TC_TIMEOUT, sizeof f, cudaMemcpyDeviceToHost, st));
     RGS_CUDA(cudaStreamSynchronize(st));
-    if (f) {
-        rgs_set_error("tensor-core contraction: %d bounded waits ran out (a pipeline role stopped)", f);
+    if (f[0]) {
+        rgs_set_error("tensor-core contraction: %d bounded waits ran out (first: role %d, site %d, group %d)", f[0],
+                      f[1] / 16, f[1] % 16, f[2]);
         return RGS_ERR_TIMEOUT;
     }
     return RGS_OK;
@@ -943,6 +972,7 @@ rgs_status rgs_tc_bounce(rgs_transport *t, int in, int out, bool split, bool wan
     a.Bblk_lo = want_lo ? s.blk[2] : nullptr;
     a.norm2 = norm2;
     a.flags = t->flags;
+    a.wait_ns = t->tc_wait_ns;
     return launch_contract(t, a, st);
 }
 
@@ -981,5 +1011,6 @@ rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout,
     a.u = u;
     a.yblk = s.blk[out];
     a.flags = t->flags;
+    a.wait_ns = t->tc_wait_ns;
     return launch_contract(t, a, st);
 }

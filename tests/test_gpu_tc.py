@@ -78,6 +78,27 @@ def test_tensor_cores_match_row_gathers():
         assert rel_l2(a[key], b[key]) <= TOL_BF16, key
 
 
+def test_tensor_core_wait_limit_reports_timeout():
+    """Failure detection without a GPU fault: with a 1 ns limit the pipeline's waits run out,
+    every role stops (after draining its own copies and MMAs) and the solve returns
+    RGS_ERR_TIMEOUT; with the default limit the same transport solves again, correctly."""
+    from paper_2509_18497_gb300 import api
+    sc = scenes.fruit_bowl(n=1200, L=3, nd=64, nb=2, n_lights=8)
+    d = api.upload(sc)
+    pipe = api.Pipeline(precision=rgs.RGS_BF16_FP32ACC, tensor_cores=TC)
+    pipe.build(d)
+    pipe.trace(d)
+    rgs.rgs_set_wait_limit(pipe.transport, 1)
+    with pytest.raises(rgs.RgsError) as err:
+        pipe.solve(d["E"], d["nb"])
+    assert err.value.status == 6  # RGS_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    rgs.rgs_set_wait_limit(pipe.transport, 0)
+    B, _ = pipe.solve(d["E"], d["nb"])
+    ref = run_gpu(sc, precision=rgs.RGS_BF16_FP32ACC, tensor_cores=0)
+    assert rel_l2(B.double().cpu().numpy(), ref["B"]) <= TOL_BF16
+
+
 @pytest.fixture(scope="module")
 def hundred():
     """100 lights (C = 300) on a 2,000-surfel bowl with 64 rays and 3 bounces: small enough for
