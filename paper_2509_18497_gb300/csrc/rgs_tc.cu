@@ -34,8 +34,9 @@ namespace {
 
 constexpr int TC_R = 8;           // receivers (or sources) per tile: 8 x 16 coefficients = M 128
 constexpr int TC_NB = 8;          // builder warps
-constexpr int TC_THREADS = (2 + TC_NB) * 32;
-constexpr int TC_MAX_STAGES = 8;
+constexpr int TC_THREADS = (1 + TC_NB) * 32;
+constexpr int TC_MAX_STAGES = 16;  // up to two per builder
+constexpr int TC_HCAP = 32;        // hit records per group (longer (tile, source) runs are split)
 constexpr int TC_CHUNK = 512;     // columns per pass (TMEM holds 512 FP32 columns)
 constexpr uint64_t TC_DRAIN_NS = 1000000000ull; // wait for in-flight copies and MMAs at exit
 
@@ -93,13 +94,12 @@ __device__ __forceinline__ float sh_mono(const float (&cf)[20], float3 v) {
 struct TcArgs {
     int adjoint;   // 0: forward over receiver tiles, 1: transpose over source tiles
     int split;     // 1: hi/lo operands, three MMAs per column piece
-    int n, C, Cp, nd, ntiles, nchunks, stages;
+    int n, C, Cp, nd, ntiles, nchunks, stages, spb;
     uint32_t stage_bytes, rows_bytes, a_bytes;
     const long long *hoff; // [ntiles + 1] first hit of each tile
     const long long *goff; // [ntiles + 1] first group of each tile
-    const int2 *grp;       // (other entity, hit count) per group
-    const float4 *hd;      // per hit: ray direction d, weight a
-    const uint32_t *hk;    // per hit: tile slot p << 9 | ray q (| h << 12)
+    const int2 *grp;       // per group: (other entity, first hit relative to its tile)
+    const float4 *hd;      // per hit: ray direction d, weight a (tile slot p in a's 3 low bits)
     const __nv_bfloat16 *rows_hi, *rows_lo; // [n][Cp x 16] blocked BF16 rows of the other entities
     const float4 *N4, *P;
     const float *cl;
@@ -118,12 +118,6 @@ struct TcArgs {
     unsigned long long wait_ns; // limit of every pipeline wait
 };
 
-struct __align__(16) StageMeta {
-    int other, cnt;
-    long long h0;
-    float4 nrm;
-};
-
 __device__ __forceinline__ float alpha_at(int model, float o) {
     if (model == RGS_ALPHA_GFSGS) return o > 0.f ? -expm1f(-0.03279f * powf(o, 3.4f)) : 0.f;
     return o;
@@ -131,7 +125,7 @@ __device__ __forceinline__ float alpha_at(int model, float o) {
 
 __device__ __forceinline__ bool aborted(const int *f) { return *(volatile const int *)f != 0; }
 
-// where = role * 16 + wait site (1 producer empty, 2 mma dempty, 3 mma afull/full, 4 builder
+// where = role * 16 + wait site (2 mma dempty, 3 mma afull/full, 1 builder empty, 4 builder
 // full, 5 builder dfull); the first failure's site and group count are kept for the message
 __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int where, long long gcount) {
     atomicExch(abort_flag, 1);
@@ -141,17 +135,39 @@ __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int wh
     }
 }
 
+// metadata of group q of tile t: its other entity, first hit (absolute) and hit count
+struct GroupMeta {
+    int other, cnt;
+    long long h0;
+};
+__device__ __forceinline__ GroupMeta group_meta(const TcArgs &g, int t, long long q, long long g1) {
+    const int2 e = __ldg(&g.grp[q]);
+    const long long hb = g.hoff[t];
+    const int end = (q + 1 < g1) ? __ldg(&g.grp[q + 1]).y : (int)(g.hoff[t + 1] - hb);
+    GroupMeta m;
+    m.other = e.x;
+    m.cnt = end - e.y;
+    m.h0 = hb + e.y;
+    return m;
+}
+
 // ------------------------------------------------------------------ the contraction kernel
+// Roles: warp 0 owns the TMEM and issues the MMAs (one lane); warps 1..TC_NB are builders.
+// Builder b takes the CTA's groups b, b + TC_NB, b + 2 TC_NB, ... and owns `spb` stages
+// (every use of a stage is awaited by the warp that awaited its previous use, so a parity
+// wait can never see a phase two uses old).  For each of its groups it waits until the
+// stage is free, bulk-copies the source rows and the group's hit records into it, and --
+// one group later, so that the copy overlaps the previous group's work -- forms the 128 x 16
+// operand from the records in shared memory.  After the item's last group the builders
+// drain the accumulator from TMEM (each TMEM lane quarter is read by two builder warps).
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES], bar_afull[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
     __shared__ __align__(8) uint64_t bar_dfull, bar_dempty, bar_drain;
-    __shared__ StageMeta meta[TC_MAX_STAGES];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ float ybuf[TC_NB][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = g.stages;
+    const int S = g.stages, SPB = g.spb;
     const int items = g.ntiles * g.nchunks;
 
     if (threadIdx.x == 0) {
@@ -166,95 +182,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         abort_flag = 0;
         tc::bar_init_fence();
     }
-    if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        // ---------------------------------------------------------- producer
-        long long gcount = 0;
-        for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x) {
-            const int t = it / g.nchunks, ch = it - t * g.nchunks;
-            const int c0 = ch * TC_CHUNK;
-            const int cw = min(TC_CHUNK, g.Cp - c0);
-            const uint32_t bytes = (uint32_t)cw * 32u;
-            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
-            long long h = g.hoff[t];
-            for (long long gb = g0; gb < g1 && !aborted(&abort_flag); gb += 32) {
-                const int m = (int)min(32ll, g1 - gb);
-                int2 e = make_int2(0, 0);
-                float4 nrm = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (lane < m) {
-                    e = __ldg(&g.grp[gb + lane]);
-                    if (g.adjoint) nrm = __ldg(&g.N4[e.x]);
-                }
-                int incl = e.y; // inclusive scan of the counts: each group's first hit
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (lane >= off) incl += v;
-                }
-                const long long hs = h + (incl - e.y);
-                for (int q = 0; q < m; ++q) {
-                    const int other = __shfl_sync(0xffffffffu, e.x, q);
-                    const int cnt = __shfl_sync(0xffffffffu, e.y, q);
-                    const long long h0 = __shfl_sync(0xffffffffu, hs, q);
-                    float4 nq;
-                    nq.x = __shfl_sync(0xffffffffu, nrm.x, q);
-                    nq.y = __shfl_sync(0xffffffffu, nrm.y, q);
-                    nq.z = __shfl_sync(0xffffffffu, nrm.z, q);
-                    nq.w = 0.f;
-                    if (lane == 0) {
-                        const int s = (int)(gcount % S);
-                        const uint32_t ph = (uint32_t)((gcount / S) & 1);
-                        if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
-                            tc_fail(g, &abort_flag, 1, gcount);
-                        } else {
-                            meta[s].other = other;
-                            meta[s].cnt = cnt;
-                            meta[s].h0 = h0;
-                            meta[s].nrm = nq;
-                            unsigned char *st = smem + (size_t)s * g.stage_bytes;
-                            tc::bar_arrive_tx(&bar_full[s], bytes * (g.split ? 2u : 1u));
-                            const size_t rb = (size_t)other * (size_t)g.Cp * 16 + (size_t)c0 * 16;
-                            tc::bulk_g2s(st, g.rows_hi + rb, bytes, &bar_full[s]);
-                            if (g.split) tc::bulk_g2s(st + bytes, g.rows_lo + rb, bytes, &bar_full[s]);
-                        }
-                    }
-                    ++gcount;
-                    __syncwarp();
-                    if (aborted(&abort_flag)) break;
-                }
-                h += __shfl_sync(0xffffffffu, incl, m - 1);
-            }
-        }
-        // no bulk copy may still be writing into this CTA's shared memory when it exits: wait
-        // (bounded) for the last fill of every stage
-        if (lane == 0)
-            for (long long q = gcount - 1; q >= 0 && q >= gcount - S; --q)
-                tc::bar_wait(&bar_full[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
-        __syncwarp();
-    } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
-        long long gcount = 0;
+        long long gc = 0; // CTA-wide group counter (the builders count the same way)
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
-            const int c0 = ch * TC_CHUNK;
-            const int cw = min(TC_CHUNK, g.Cp - c0);
+            const int cw = min(TC_CHUNK, g.Cp - ch * TC_CHUNK);
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
             if (lane == 0) {
                 bool ok = true;
-                if (tl > 0) ok = tc::bar_wait(&bar_dempty, (uint32_t)((tl - 1) & 1), g.wait_ns);
+                if (tl > 0 && !tc::bar_wait(&bar_dempty, (uint32_t)((tl - 1) & 1), g.wait_ns)) {
+                    tc_fail(g, &abort_flag, 2, gc);
+                    ok = false;
+                }
                 tc::fence_after();
-                if (!ok) tc_fail(g, &abort_flag, 2, gcount);
-                for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gcount) {
-                    const int s = (int)(gcount % S);
-                    const uint32_t ph = (uint32_t)((gcount / S) & 1);
+                for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gc) {
+                    const int b = (int)(gc % TC_NB);
+                    const long long k = gc / TC_NB;
+                    const int s = b * SPB + (int)(k % SPB);
+                    const uint32_t ph = (uint32_t)((k / SPB) & 1);
                     if (!tc::bar_wait(&bar_afull[s], ph, g.wait_ns) || !tc::bar_wait(&bar_full[s], ph, g.wait_ns)) {
-                        tc_fail(g, &abort_flag, 3, gcount);
+                        tc_fail(g, &abort_flag, 3, gc);
                         ok = false;
                         break;
                     }
@@ -263,6 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     const uint32_t rows = tc::smem_addr(st);
                     const uint32_t A = tc::smem_addr(st + g.rows_bytes);
                     const uint32_t acc0 = (q == g0) ? 0u : 1u;
+                    const uint32_t rbytes = (uint32_t)cw * 32u;
                     for (int c = 0; c < cw; c += 256) {
                         const int N = min(256, cw - c);
                         const uint32_t id = tc::idesc_bf16(128, N);
@@ -270,10 +226,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                         const uint64_t da = tc::sdesc(A), db = tc::sdesc(rows + (uint32_t)c * 32u);
                         tc::mma_bf16(d, da, db, id, acc0);
                         if (g.split) {
-                            const uint32_t rbytes = (uint32_t)cw * 32u;
-                            const uint64_t da_lo = tc::sdesc(A + 4096u), db_lo = tc::sdesc(rows + rbytes + (uint32_t)c * 32u);
-                            tc::mma_bf16(d, da, db_lo, id, 1u);
-                            tc::mma_bf16(d, da_lo, db, id, 1u);
+                            tc::mma_bf16(d, da, tc::sdesc(rows + rbytes + (uint32_t)c * 32u), id, 1u);
+                            tc::mma_bf16(d, tc::sdesc(A + 4096u), db, id, 1u);
                         }
                     }
                     tc::mma_commit(&bar_empty[s]);
@@ -281,7 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 tc::mma_commit(&bar_dfull); // after a failure the other roles give up on their own waits
             }
             __syncwarp();
-            gcount = __shfl_sync(0xffffffffu, gcount, 0);
+            gc = __shfl_sync(0xffffffffu, gc, 0);
         }
         // every MMA this thread issued has completed before the TMEM is freed
         if (lane == 0) {
@@ -291,7 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         __syncwarp();
     } else {
         // ---------------------------------------------------------- builders + epilogue
-        const int b = warp - 2;
+        const int b = warp - 1;
         const int k = lane & 15, mh = lane >> 4;
         float cf[20];
 #pragma unroll
@@ -299,32 +253,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         // forward: rows of the operand are receivers (X = Y(R_i d)), columns sources (Z = Y(-d));
         // adjoint: rows are sources (X = Y(-d)), columns receivers (Z = Y(R_i d))
         const int xoff = g.adjoint ? 0 : 16, zoff = g.adjoint ? 16 : 0;
-        long long gcount = 0;
+        __shared__ float ybuf_all[TC_NB][32];
+        float *ybuf = ybuf_all[b];
+        long long gc = 0;  // CTA-wide group counter
+        long long kb = 0;  // this builder's groups so far (stage ring position)
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
             const int c0 = ch * TC_CHUNK;
             const int cw = min(TC_CHUNK, g.Cp - c0);
+            const uint32_t rbytes = (uint32_t)cw * 32u;
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
-            for (long long q = g0; q < g1 && !aborted(&abort_flag); ++q, ++gcount) {
-                // builder b owns stage b: every use of a stage is then awaited by the warp that
-                // awaited its previous use, so a parity wait cannot see a phase two uses old
-                const int s = (int)(gcount % S);
-                if (s != b) continue;
-                const uint32_t ph = (uint32_t)((gcount / S) & 1);
+            // this builder's groups of the item: q = qfirst, qfirst + TC_NB, ...
+            const long long qfirst = g0 + (long long)((b - (int)(gc % TC_NB) + TC_NB) % TC_NB);
+            // issue(q): wait for the stage, then bulk-copy the rows and the hit records into it
+            auto issue = [&](long long q, long long kk, GroupMeta m) -> bool {
+                const int s = b * SPB + (int)(kk % SPB);
+                const uint32_t ph = (uint32_t)((kk / SPB) & 1);
+                bool ok = true;
+                if (lane == 0) {
+                    if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
+                        tc_fail(g, &abort_flag, 16 * (1 + b) + 1, q);
+                        ok = false;
+                    } else {
+                        unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                        const uint32_t hbytes = (uint32_t)m.cnt * 16u;
+                        tc::bar_arrive_tx(&bar_full[s], rbytes * (g.split ? 2u : 1u) + hbytes);
+                        const size_t rb = (size_t)m.other * (size_t)g.Cp * 16 + (size_t)c0 * 16;
+                        tc::bulk_g2s(st, g.rows_hi + rb, rbytes, &bar_full[s]);
+                        if (g.split) tc::bulk_g2s(st + rbytes, g.rows_lo + rb, rbytes, &bar_full[s]);
+                        tc::bulk_g2s(st + g.rows_bytes + g.a_bytes, g.hd + m.h0, hbytes, &bar_full[s]);
+                    }
+                }
+                return __shfl_sync(0xffffffffu, ok, 0);
+            };
+            GroupMeta mcur{}, mnext{};
+            bool alive = true;
+            if (qfirst < g1) {
+                mcur = group_meta(g, t, qfirst, g1);
+                alive = issue(qfirst, kb, mcur);
+            }
+            for (long long q = qfirst; q < g1 && alive && !aborted(&abort_flag); q += TC_NB, ++kb) {
+                // with two stages per builder the copies of its next group fly while this one is
+                // built; with one, the next group's copies wait for this group's MMA (below)
+                const long long qn = q + TC_NB;
+                if (qn < g1) mnext = group_meta(g, t, qn, g1);
+                if (SPB > 1 && qn < g1 && !issue(qn, kb + 1, mnext)) break;
+                const int s = b * SPB + (int)(kb % SPB);
+                const uint32_t ph = (uint32_t)((kb / SPB) & 1);
                 bool ok = true;
                 if (lane == 0) ok = tc::bar_wait(&bar_full[s], ph, g.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
-                __syncwarp(); // lane 0's acquire of the stage covers the warp's reads of its meta
+                __syncwarp();
                 if (!ok) {
-                    if (lane == 0) tc_fail(g, &abort_flag, 16 * (2 + b) + 4, gcount);
+                    if (lane == 0) tc_fail(g, &abort_flag, 16 * (1 + b) + 4, q);
                     break;
                 }
-                const int cnt = meta[s].cnt;
-                const long long h0 = meta[s].h0;
-                const float3 ngrp = f3(meta[s].nrm);
                 unsigned char *st = smem + (size_t)s * g.stage_bytes;
                 const uint32_t A = tc::smem_addr(st + g.rows_bytes);
+                const float4 *hits = reinterpret_cast<const float4 *>(st + g.rows_bytes + g.a_bytes);
+                float3 ngrp = make_float3(0.f, 0.f, 1.f);
+                if (g.adjoint) ngrp = f3(__ldg(&g.N4[mcur.other]));
                 float acc[8];
 #pragma unroll
                 for (int m = 0; m < 8; ++m) acc[m] = 0.f;
@@ -332,62 +321,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 unsigned written = 0;
                 auto flush = [&](int p) {
                     const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
-                    uint4 hi, lo;
-                    float r[8];
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) r[m] = __bfloat162float(__float2bfloat16_rn(acc[m]));
+                    uint4 hi;
                     hi.x = tc::pack_bf16(acc[0], acc[1]);
                     hi.y = tc::pack_bf16(acc[2], acc[3]);
                     hi.z = tc::pack_bf16(acc[4], acc[5]);
                     hi.w = tc::pack_bf16(acc[6], acc[7]);
                     tc::sts128(A + off, hi);
                     if (g.split) {
-                        lo.x = tc::pack_bf16(acc[0] - r[0], acc[1] - r[1]);
-                        lo.y = tc::pack_bf16(acc[2] - r[2], acc[3] - r[3]);
-                        lo.z = tc::pack_bf16(acc[4] - r[4], acc[5] - r[5]);
-                        lo.w = tc::pack_bf16(acc[6] - r[6], acc[7] - r[7]);
+                        float r[8];
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) r[m] = acc[m] - __bfloat162float(__float2bfloat16_rn(acc[m]));
+                        uint4 lo;
+                        lo.x = tc::pack_bf16(r[0], r[1]);
+                        lo.y = tc::pack_bf16(r[2], r[3]);
+                        lo.z = tc::pack_bf16(r[4], r[5]);
+                        lo.w = tc::pack_bf16(r[6], r[7]);
                         tc::sts128(A + 4096u + off, lo);
                     }
                     written |= 1u << p;
                 };
-                for (int base = 0; base < cnt; base += 32) {
-                    const int m_here = min(32, cnt - base);
-                    float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
-                    uint32_t key = 0;
-                    if (lane < m_here) {
-                        rec = __ldg(&g.hd[h0 + base + lane]);
-                        key = __ldg(&g.hk[h0 + base + lane]);
+                for (int e = 0; e < mcur.cnt; ++e) {
+                    const float4 rec = hits[e]; // broadcast read
+                    const uint32_t abits = __float_as_uint(rec.w);
+                    const int p = (int)(abits & 7u);
+                    const float a = __uint_as_float(abits & ~7u);
+                    const float3 d = make_float3(rec.x, rec.y, rec.z);
+                    const float3 nrm = g.adjoint ? ngrp : f3(__ldg(&g.N4[t * TC_R + p]));
+                    // lanes 0..15: Y_k(-d); lanes 16..31: Y_k(R d)
+                    const float3 v = (lane < 16) ? make_float3(-d.x, -d.y, -d.z) : reflect_n(nrm, d);
+                    ybuf[lane] = sh_mono(cf, v);
+                    __syncwarp();
+                    const float X = ybuf[xoff + k];
+                    float Z[8];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) Z[m] = ybuf[zoff + mh * 8 + m];
+                    __syncwarp();
+                    if (p != cur) {
+                        if (cur >= 0) flush(cur);
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                        cur = p;
                     }
-                    for (int e = 0; e < m_here; ++e) {
-                        const float dx = __shfl_sync(0xffffffffu, rec.x, e);
-                        const float dy = __shfl_sync(0xffffffffu, rec.y, e);
-                        const float dz = __shfl_sync(0xffffffffu, rec.z, e);
-                        const float a = __shfl_sync(0xffffffffu, rec.w, e);
-                        const uint32_t kk = __shfl_sync(0xffffffffu, key, e);
-                        const int p = (int)((kk >> 9) & 7u);
-                        const float3 d = make_float3(dx, dy, dz);
-                        float3 nrm = ngrp;
-                        if (!g.adjoint) nrm = f3(__ldg(&g.N4[t * TC_R + p]));
-                        // lanes 0..15: Y_k(-d); lanes 16..31: Y_k(R d)
-                        const float3 v = (lane < 16) ? make_float3(-dx, -dy, -dz) : reflect_n(nrm, d);
-                        const float y = sh_mono(cf, v);
-                        ybuf[b][lane] = y;
-                        __syncwarp();
-                        const float X = ybuf[b][xoff + k];
-                        float Z[8];
+                    const float ax = a * X;
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) Z[m] = ybuf[b][zoff + mh * 8 + m];
-                        __syncwarp();
-                        if (p != cur) {
-                            if (cur >= 0) flush(cur);
-#pragma unroll
-                            for (int m = 0; m < 8; ++m) acc[m] = 0.f;
-                            cur = p;
-                        }
-                        const float ax = a * X;
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) acc[m] = fmaf(ax, Z[m], acc[m]);
-                    }
+                    for (int m = 0; m < 8; ++m) acc[m] = fmaf(ax, Z[m], acc[m]);
                 }
                 if (cur >= 0) flush(cur);
                 const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
@@ -400,7 +377,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::bar_arrive(&bar_afull[s]);
+                if (SPB == 1 && qn < g1 && !issue(qn, kb + 1, mnext)) break;
+                mcur = mnext;
             }
+            gc += g1 - g0;
+            kb = (gc + TC_NB - 1 - b) / TC_NB; // groups of this builder in all items so far
             if (aborted(&abort_flag)) break;
             // ------------------------------------------------------ epilogue of the item
             bool ok = true;
@@ -409,7 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             __syncwarp();
             tc::fence_after();
             if (!ok) {
-                if (lane == 0) tc_fail(g, &abort_flag, 16 * (2 + b) + 5, gcount);
+                if (lane == 0) tc_fail(g, &abort_flag, 16 * (1 + b) + 5, gc);
                 break;
             }
             const bool empty = (g1 == g0);
@@ -458,11 +439,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             __syncwarp();
             if (lane == 0) tc::bar_arrive(&bar_dempty);
         }
+        // no bulk copy may still be writing into this CTA's shared memory when it exits: wait
+        // (bounded) for the last fill of each of this builder's stages
+        if (lane == 0)
+            for (long long kk = kb - 1; kk >= 0 && kk >= kb - SPB; --kk)
+                tc::bar_wait(&bar_full[b * SPB + (int)(kk % SPB)], (uint32_t)((kk / SPB) & 1), TC_DRAIN_NS);
+        __syncwarp();
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------------ pair-tile construction
@@ -613,13 +600,18 @@ __global__ void __launch_bounds__(SORT_THREADS) k_tc_sort_pass(const long long *
     }
 }
 
-// groups (runs of equal key >> 12) per segment
+// groups per segment: each run of equal key >> 12 (one source, or one receiver) in pieces of
+// at most TC_HCAP hits
 __global__ void __launch_bounds__(256) k_tc_group_count(const long long *__restrict__ seg, const uint32_t *__restrict__ key,
                                                         int *gcount) {
     const long long s0 = seg[blockIdx.x], s1 = seg[blockIdx.x + 1];
     int c = 0;
-    for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x)
-        c += (e == s0 || (key[e] >> 12) != (key[e - 1] >> 12)) ? 1 : 0;
+    for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
+        if (e != s0 && (key[e] >> 12) == (key[e - 1] >> 12)) continue;
+        long long f = e + 1;
+        while (f < s1 && (key[f] >> 12) == (key[e] >> 12)) ++f;
+        c += (int)((f - e + TC_HCAP - 1) / TC_HCAP);
+    }
     __shared__ int red[8];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
@@ -632,47 +624,46 @@ __global__ void __launch_bounds__(256) k_tc_group_count(const long long *__restr
     }
 }
 
-// group list (other entity, count) and the per-hit records (d, a) and keys (p, q, h)
+// the group list (other entity, first hit relative to the tile) and the per-hit records:
+// direction d and weight a, with the hit's tile slot p in the 3 low mantissa bits of a
+// (a relative change below 1e-6)
 __global__ void __launch_bounds__(256) k_tc_finish(const long long *__restrict__ seg, const long long *__restrict__ goff,
                                                    const uint32_t *__restrict__ key, const uint2 *__restrict__ pay,
-                                                   const float4 *__restrict__ dir, int nd, int adjoint, int ntile_ent,
-                                                   int2 *grp, float4 *hd, uint32_t *hk) {
+                                                   const float4 *__restrict__ dir, int nd, int adjoint, int2 *grp,
+                                                   float4 *hd) {
     const int t = blockIdx.x;
     const long long s0 = seg[t], s1 = seg[t + 1];
-    // records: element-parallel
     for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
         const uint32_t kv = key[e];
         const uint2 pv = pay[e];
         const int other = (int)(kv >> 12), p = (int)((kv >> 9) & 7u), q = (int)(kv & 511u);
-        const int recv = adjoint ? other : t * ntile_ent + p;
+        const int recv = adjoint ? other : t * TC_R + p;
         const float4 d = dir[(long long)recv * nd + q];
-        hd[e] = make_float4(d.x, d.y, d.z, __uint_as_float(pv.x));
-        hk[e] = (uint32_t)((p << 9) | q) | (pv.y << 12);
+        hd[e] = make_float4(d.x, d.y, d.z, __uint_as_float((pv.x & ~7u) | (uint32_t)p));
     }
-    // groups: one warp walks the segment in 32-element windows
+    // groups: one warp walks the runs in 32-element windows
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         long long gi = goff[t];
         long long start = s0;
+        auto emit = [&](long long a, long long b) { // the run [a, b) in pieces of TC_HCAP
+            for (long long x = a; x < b; x += TC_HCAP) {
+                if (lane == 0) grp[gi] = make_int2((int)(key[a] >> 12), (int)(x - s0));
+                ++gi;
+            }
+        };
         for (long long e0 = s0; e0 < s1; e0 += 32) {
             const long long e = e0 + lane;
-            const bool in = e < s1;
-            const bool head = in && (e == s0 || (key[e] >> 12) != (key[e - 1] >> 12));
-            const unsigned heads = __ballot_sync(0xffffffffu, head);
-            // every head closes the previous group
-            unsigned hm = heads;
+            const bool head = e < s1 && e != s0 && (key[e] >> 12) != (key[e - 1] >> 12);
+            unsigned hm = __ballot_sync(0xffffffffu, head);
             while (hm) {
                 const int l = __ffs(hm) - 1;
                 hm &= hm - 1;
-                const long long he = e0 + l;
-                if (he != s0 && lane == 0) {
-                    grp[gi] = make_int2((int)(key[start] >> 12), (int)(he - start));
-                    ++gi;
-                }
-                start = he;
+                emit(start, e0 + l);
+                start = e0 + l;
             }
         }
-        if (lane == 0 && s1 > s0) grp[gi] = make_int2((int)(key[start] >> 12), (int)(s1 - start));
+        if (s1 > s0) emit(start, s1);
     }
 }
 
@@ -713,7 +704,6 @@ struct TcPairs {
     long long *hoff = nullptr, *goff = nullptr;
     int2 *grp = nullptr;
     float4 *hd = nullptr;
-    uint32_t *hk = nullptr;
 };
 
 struct rgs_tc_state {
@@ -732,7 +722,6 @@ void pairs_free(TcPairs &p) {
     dev_free(p.goff);
     dev_free(p.grp);
     dev_free(p.hd);
-    dev_free(p.hk);
     p = TcPairs{};
 }
 
@@ -778,7 +767,6 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
     if ((r = dev_alloc(&P.hoff, (size_t)ntiles + 1)) != RGS_OK) return r;
     if ((r = dev_alloc(&P.goff, (size_t)ntiles + 1)) != RGS_OK) return r;
     if ((r = dev_alloc(&P.hd, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
-    if ((r = dev_alloc(&P.hk, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
     if (!adjoint) {
         { ProfScope ps_("k_tc_tile_count", st); k_tc_tile_count_fwd<<<(ntiles + 7) / 8, 256, 0, st>>>(t->cnt, n, nd, ntiles, tcount); }
     } else {
@@ -815,7 +803,7 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
     RGS_CUDA(cudaStreamSynchronize(st));
     P.n_groups = ng;
     if ((r = dev_alloc(&P.grp, (size_t)std::max(ng, 1ll))) != RGS_OK) return r;
-    { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, nd, adjoint ? 1 : 0, TC_R, P.grp, P.hd, P.hk); }
+    { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, nd, adjoint ? 1 : 0, P.grp, P.hd); }
     RGS_LAUNCH("tc finish");
     return RGS_OK;
 }
@@ -832,15 +820,14 @@ rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
     a.nchunks = (a.Cp + TC_CHUNK - 1) / TC_CHUNK;
     a.rows_bytes = (uint32_t)cw * 32u * (a.split ? 2u : 1u);
     a.a_bytes = 4096u * (a.split ? 2u : 1u);
-    a.stage_bytes = (a.rows_bytes + a.a_bytes + 1023u) & ~1023u;
-    const uint32_t budget = 220u * 1024u;
-    // at most one stage per builder warp (a builder owns its stage)
-    a.stages = (int)std::min<uint32_t>(std::min(TC_MAX_STAGES, TC_NB), budget / a.stage_bytes);
-    if (a.stages < 2) {
-        rgs_set_error("tensor-core contraction: stage of %u bytes too large", a.stage_bytes);
+    a.stage_bytes = (a.rows_bytes + a.a_bytes + TC_HCAP * 16u + 127u) & ~127u;
+    const uint32_t budget = 224u * 1024u; // of the 227 KB a CTA may hold, with the static barriers
+    a.spb = (2u * TC_NB * a.stage_bytes <= budget) ? 2 : 1;
+    a.stages = TC_NB * a.spb;
+    if ((uint32_t)a.stages * a.stage_bytes > budget) {
+        rgs_set_error("tensor-core contraction: %d stages of %u bytes exceed shared memory", a.stages, a.stage_bytes);
         return RGS_ERR_ARG;
     }
-    // at least 120 KB, so that one CTA (and its 512 TMEM columns) holds an SM
     const size_t smem = std::max<size_t>((size_t)a.stages * a.stage_bytes, 120u * 1024u);
     RGS_CUDA(cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int items = a.ntiles * a.nchunks;
@@ -955,7 +942,6 @@ rgs_status rgs_tc_bounce(rgs_transport *t, int in, int out, bool split, bool wan
     a.goff = s.fwd.goff;
     a.grp = s.fwd.grp;
     a.hd = s.fwd.hd;
-    a.hk = s.fwd.hk;
     a.rows_hi = s.blk[in];
     a.rows_lo = split ? s.blk[2] : nullptr;
     a.N4 = t->sc->N4;
@@ -1000,7 +986,6 @@ rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout,
     a.goff = s.adj.goff;
     a.grp = s.adj.grp;
     a.hd = s.adj.hd;
-    a.hk = s.adj.hk;
     a.rows_hi = s.blk[in];
     a.N4 = t->sc->N4;
     a.P = t->sc->P;

@@ -95,6 +95,17 @@ __device__ __forceinline__ bool bar_test(uint64_t *bar, uint32_t parity) {
                  : "memory");
     return ok != 0;
 }
+// the same with a suspend-time hint: the thread sleeps (up to hint_ns) until the phase
+// completes instead of spinning, so waiting roles leave the issue slots to working warps
+__device__ __forceinline__ bool bar_test_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ uint64_t now_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -106,7 +117,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, uint64_
     if (bar_test(bar, parity)) return true;
     const uint64_t t0 = now_ns();
     while (true) {
-        if (bar_test(bar, parity)) return true;
+        if (bar_test_sleep(bar, parity, 20000u)) return true;
         if (now_ns() - t0 > limit_ns) return false;
     }
 }
