@@ -34,9 +34,9 @@ namespace {
 
 constexpr int TC_R = 8;           // receivers (or sources) per tile: 8 x 16 coefficients = M 128
 constexpr int TC_NB = 8;          // builder warps
-constexpr int TC_THREADS = (1 + TC_NB) * 32;
+constexpr int TC_THREADS = (3 + TC_NB) * 32; // two producers, the MMA warp, the builders
 constexpr int TC_MAX_STAGES = 16;  // up to two per builder
-constexpr int TC_HCAP = 32;        // hit records per group (longer (tile, source) runs are split)
+constexpr int TC_HCAP = 24;        // hit records per group (longer (tile, source) runs are split)
 constexpr int TC_CHUNK = 512;     // columns per pass (TMEM holds 512 FP32 columns)
 constexpr uint64_t TC_DRAIN_NS = 1000000000ull; // wait for in-flight copies and MMAs at exit
 
@@ -94,7 +94,7 @@ __device__ __forceinline__ float sh_mono(const float (&cf)[20], float3 v) {
 struct TcArgs {
     int adjoint;   // 0: forward over receiver tiles, 1: transpose over source tiles
     int split;     // 1: hi/lo operands, three MMAs per column piece
-    int n, C, Cp, nd, ntiles, nchunks, stages, spb;
+    int n, C, Cp, nd, ntiles, nchunks, stages;
     uint32_t stage_bytes, rows_bytes, a_bytes;
     const long long *hoff; // [ntiles + 1] first hit of each tile
     const long long *goff; // [ntiles + 1] first group of each tile
@@ -118,6 +118,11 @@ struct TcArgs {
     unsigned long long wait_ns; // limit of every pipeline wait
 };
 
+struct __align__(16) StageMeta {
+    float4 nrm; // adjoint: the group's receiver normal
+    int other, cnt;
+};
+
 __device__ __forceinline__ float alpha_at(int model, float o) {
     if (model == RGS_ALPHA_GFSGS) return o > 0.f ? -expm1f(-0.03279f * powf(o, 3.4f)) : 0.f;
     return o;
@@ -125,8 +130,8 @@ __device__ __forceinline__ float alpha_at(int model, float o) {
 
 __device__ __forceinline__ bool aborted(const int *f) { return *(volatile const int *)f != 0; }
 
-// where = role * 16 + wait site (2 mma dempty, 3 mma afull/full, 1 builder empty, 4 builder
-// full, 5 builder dfull); the first failure's site and group count are kept for the message
+// where = role * 16 + wait site (1 producer empty, 2 mma dempty, 3 mma afull/rows, 4 builder
+// hits, 5 builder dfull); the first failure's site and group count are kept for the message
 __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int where, long long gcount) {
     atomicExch(abort_flag, 1);
     if (atomicAdd(&g.flags[FLAG_TC_TIMEOUT], 1) == 0) {
@@ -135,44 +140,35 @@ __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int wh
     }
 }
 
-// metadata of group q of tile t: its other entity, first hit (absolute) and hit count
-struct GroupMeta {
-    int other, cnt;
-    long long h0;
-};
-__device__ __forceinline__ GroupMeta group_meta(const TcArgs &g, int t, long long q, long long g1) {
-    const int2 e = __ldg(&g.grp[q]);
-    const long long hb = g.hoff[t];
-    const int end = (q + 1 < g1) ? __ldg(&g.grp[q + 1]).y : (int)(g.hoff[t + 1] - hb);
-    GroupMeta m;
-    m.other = e.x;
-    m.cnt = end - e.y;
-    m.h0 = hb + e.y;
-    return m;
-}
-
 // ------------------------------------------------------------------ the contraction kernel
-// Roles: warp 0 owns the TMEM and issues the MMAs (one lane); warps 1..TC_NB are builders.
-// Builder b takes the CTA's groups b, b + TC_NB, b + 2 TC_NB, ... and owns `spb` stages
-// (every use of a stage is awaited by the warp that awaited its previous use, so a parity
-// wait can never see a phase two uses old).  For each of its groups it waits until the
-// stage is free, bulk-copies the source rows and the group's hit records into it, and --
-// one group later, so that the copy overlaps the previous group's work -- forms the 128 x 16
-// operand from the records in shared memory.  After the item's last group the builders
-// drain the accumulator from TMEM (each TMEM lane quarter is read by two builder warps).
+// Roles: warps 0 and 1 produce (even and odd groups: a stage's empty barrier is always
+// awaited by the same warp), warp 2 owns the TMEM and issues the MMAs (one lane), warps
+// 3 .. 3 + TC_NB - 1 build operands and drain the accumulator.  Group g of the CTA uses stage
+// g % S; builder b takes the groups g = b (mod TC_NB), i.e. the stages b, b + TC_NB, ...,
+// so every use of a stage is awaited by the warp that awaited its previous use and a parity
+// wait can never see a phase two uses old.  Per stage: `hits` (the group's hit records and
+// metadata), `rows` (the source rows; awaited by the MMA only, so the S - 1 groups ahead of
+// it hide the copy's latency), `afull` (operand built), `empty` (MMAs done).
+constexpr int TC_PROD = 2;
+constexpr int TC_MMA_WARP = TC_PROD;
+constexpr int TC_B0 = TC_PROD + 1; // first builder warp
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES], bar_afull[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_hits[TC_MAX_STAGES], bar_rows[TC_MAX_STAGES], bar_afull[TC_MAX_STAGES],
+        bar_empty[TC_MAX_STAGES];
     __shared__ __align__(8) uint64_t bar_dfull, bar_dempty, bar_drain;
+    __shared__ StageMeta meta[TC_MAX_STAGES];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    __shared__ float ybuf_all[TC_NB][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = g.stages, SPB = g.spb;
+    const int S = g.stages;
     const int items = g.ntiles * g.nchunks;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            tc::bar_init(&bar_full[s], 1);
+            tc::bar_init(&bar_hits[s], 1);
+            tc::bar_init(&bar_rows[s], 1);
             tc::bar_init(&bar_afull[s], 1);
             tc::bar_init(&bar_empty[s], 1);
         }
@@ -182,15 +178,86 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         abort_flag = 0;
         tc::bar_init_fence();
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (warp == TC_MMA_WARP) tc::tmem_alloc(&tmem_slot, 512);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0) {
+    if (warp < TC_PROD) {
+        // ---------------------------------------------------------- producers
+        long long gc = 0, issued = 0;
+        for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x) {
+            const int t = it / g.nchunks, ch = it - t * g.nchunks;
+            const int c0 = ch * TC_CHUNK;
+            const int cw = min(TC_CHUNK, g.Cp - c0);
+            const uint32_t rbytes = (uint32_t)cw * 32u;
+            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            const long long hb = g.hoff[t];
+            const int tile_hits = (int)(g.hoff[t + 1] - hb);
+            for (long long gb = g0; gb < g1 && !aborted(&abort_flag); gb += 32) {
+                const int m = (int)min(32ll, g1 - gb);
+                int2 e = make_int2(0, 0);
+                int next = tile_hits;
+                float4 nrm = make_float4(0.f, 0.f, 1.f, 0.f);
+                if (lane < m) {
+                    e = __ldg(&g.grp[gb + lane]);
+                    if (gb + lane + 1 < g1) next = __ldg(&g.grp[gb + lane + 1]).y;
+                    if (g.adjoint) nrm = __ldg(&g.N4[e.x]);
+                }
+                for (int q = 0; q < m; ++q) {
+                    const long long gq = gc + (gb - g0) + q; // CTA-wide group index
+                    if ((int)(gq % TC_PROD) != warp) continue;
+                    const int other = __shfl_sync(0xffffffffu, e.x, q);
+                    const int first = __shfl_sync(0xffffffffu, e.y, q);
+                    const int cnt = __shfl_sync(0xffffffffu, next, q) - first;
+                    float4 nq;
+                    nq.x = __shfl_sync(0xffffffffu, nrm.x, q);
+                    nq.y = __shfl_sync(0xffffffffu, nrm.y, q);
+                    nq.z = __shfl_sync(0xffffffffu, nrm.z, q);
+                    nq.w = 0.f;
+                    if (lane == 0) {
+                        const int s = (int)(gq % S);
+                        const uint32_t ph = (uint32_t)((gq / S) & 1);
+                        if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
+                            tc_fail(g, &abort_flag, 16 * warp + 1, gq);
+                        } else {
+                            meta[s].nrm = nq;
+                            meta[s].other = other;
+                            meta[s].cnt = cnt;
+                            unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                            const uint32_t hbytes = (uint32_t)cnt * 16u;
+                            tc::bar_arrive_tx(&bar_hits[s], hbytes);
+                            tc::bulk_g2s(st + g.rows_bytes + g.a_bytes, g.hd + hb + first, hbytes, &bar_hits[s]);
+                            tc::bar_arrive_tx(&bar_rows[s], rbytes * (g.split ? 2u : 1u));
+                            const size_t rb = (size_t)other * (size_t)g.Cp * 16 + (size_t)c0 * 16;
+                            tc::bulk_g2s(st, g.rows_hi + rb, rbytes, &bar_rows[s]);
+                            if (g.split) tc::bulk_g2s(st + rbytes, g.rows_lo + rb, rbytes, &bar_rows[s]);
+                            ++issued;
+                        }
+                    }
+                    __syncwarp();
+                    if (aborted(&abort_flag)) break;
+                }
+            }
+            gc += g1 - g0;
+        }
+        // no bulk copy may still be writing into this CTA's shared memory when it exits: wait
+        // (bounded) for the last fills this warp issued
+        if (lane == 0) {
+            long long seen = 0;
+            for (long long q = gc - 1; q >= 0 && seen < S / TC_PROD; --q) {
+                if ((int)(q % TC_PROD) != warp) continue;
+                ++seen;
+                tc::bar_wait(&bar_rows[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
+                tc::bar_wait(&bar_hits[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
+            }
+        }
+        __syncwarp();
+        (void)issued;
+    } else if (warp == TC_MMA_WARP) {
         // ---------------------------------------------------------- MMA issuer
-        long long gc = 0; // CTA-wide group counter (the builders count the same way)
+        long long gc = 0;
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
@@ -199,17 +266,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             if (lane == 0) {
                 bool ok = true;
                 if (tl > 0 && !tc::bar_wait(&bar_dempty, (uint32_t)((tl - 1) & 1), g.wait_ns)) {
-                    tc_fail(g, &abort_flag, 2, gc);
+                    tc_fail(g, &abort_flag, 16 * warp + 2, gc);
                     ok = false;
                 }
                 tc::fence_after();
+                const uint32_t rbytes = (uint32_t)cw * 32u;
                 for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gc) {
-                    const int b = (int)(gc % TC_NB);
-                    const long long k = gc / TC_NB;
-                    const int s = b * SPB + (int)(k % SPB);
-                    const uint32_t ph = (uint32_t)((k / SPB) & 1);
-                    if (!tc::bar_wait(&bar_afull[s], ph, g.wait_ns) || !tc::bar_wait(&bar_full[s], ph, g.wait_ns)) {
-                        tc_fail(g, &abort_flag, 3, gc);
+                    const int s = (int)(gc % S);
+                    const uint32_t ph = (uint32_t)((gc / S) & 1);
+                    if (!tc::bar_wait(&bar_afull[s], ph, g.wait_ns) || !tc::bar_wait(&bar_rows[s], ph, g.wait_ns)) {
+                        tc_fail(g, &abort_flag, 16 * warp + 3, gc);
                         ok = false;
                         break;
                     }
@@ -218,7 +284,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     const uint32_t rows = tc::smem_addr(st);
                     const uint32_t A = tc::smem_addr(st + g.rows_bytes);
                     const uint32_t acc0 = (q == g0) ? 0u : 1u;
-                    const uint32_t rbytes = (uint32_t)cw * 32u;
                     for (int c = 0; c < cw; c += 256) {
                         const int N = min(256, cw - c);
                         const uint32_t id = tc::idesc_bf16(128, N);
@@ -245,7 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         __syncwarp();
     } else {
         // ---------------------------------------------------------- builders + epilogue
-        const int b = warp - 1;
+        const int b = warp - TC_B0;
         const int k = lane & 15, mh = lane >> 4;
         float cf[20];
 #pragma unroll
@@ -253,67 +318,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         // forward: rows of the operand are receivers (X = Y(R_i d)), columns sources (Z = Y(-d));
         // adjoint: rows are sources (X = Y(-d)), columns receivers (Z = Y(R_i d))
         const int xoff = g.adjoint ? 0 : 16, zoff = g.adjoint ? 16 : 0;
-        __shared__ float ybuf_all[TC_NB][32];
         float *ybuf = ybuf_all[b];
-        long long gc = 0;  // CTA-wide group counter
-        long long kb = 0;  // this builder's groups so far (stage ring position)
+        long long gc = 0; // CTA-wide group counter
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
             const int c0 = ch * TC_CHUNK;
             const int cw = min(TC_CHUNK, g.Cp - c0);
-            const uint32_t rbytes = (uint32_t)cw * 32u;
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
-            // this builder's groups of the item: q = qfirst, qfirst + TC_NB, ...
             const long long qfirst = g0 + (long long)((b - (int)(gc % TC_NB) + TC_NB) % TC_NB);
-            // issue(q): wait for the stage, then bulk-copy the rows and the hit records into it
-            auto issue = [&](long long q, long long kk, GroupMeta m) -> bool {
-                const int s = b * SPB + (int)(kk % SPB);
-                const uint32_t ph = (uint32_t)((kk / SPB) & 1);
+            for (long long q = qfirst; q < g1 && !aborted(&abort_flag); q += TC_NB) {
+                const long long gq = gc + (q - g0);
+                const int s = (int)(gq % S);
+                const uint32_t ph = (uint32_t)((gq / S) & 1);
                 bool ok = true;
-                if (lane == 0) {
-                    if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
-                        tc_fail(g, &abort_flag, 16 * (1 + b) + 1, q);
-                        ok = false;
-                    } else {
-                        unsigned char *st = smem + (size_t)s * g.stage_bytes;
-                        const uint32_t hbytes = (uint32_t)m.cnt * 16u;
-                        tc::bar_arrive_tx(&bar_full[s], rbytes * (g.split ? 2u : 1u) + hbytes);
-                        const size_t rb = (size_t)m.other * (size_t)g.Cp * 16 + (size_t)c0 * 16;
-                        tc::bulk_g2s(st, g.rows_hi + rb, rbytes, &bar_full[s]);
-                        if (g.split) tc::bulk_g2s(st + rbytes, g.rows_lo + rb, rbytes, &bar_full[s]);
-                        tc::bulk_g2s(st + g.rows_bytes + g.a_bytes, g.hd + m.h0, hbytes, &bar_full[s]);
-                    }
-                }
-                return __shfl_sync(0xffffffffu, ok, 0);
-            };
-            GroupMeta mcur{}, mnext{};
-            bool alive = true;
-            if (qfirst < g1) {
-                mcur = group_meta(g, t, qfirst, g1);
-                alive = issue(qfirst, kb, mcur);
-            }
-            for (long long q = qfirst; q < g1 && alive && !aborted(&abort_flag); q += TC_NB, ++kb) {
-                // with two stages per builder the copies of its next group fly while this one is
-                // built; with one, the next group's copies wait for this group's MMA (below)
-                const long long qn = q + TC_NB;
-                if (qn < g1) mnext = group_meta(g, t, qn, g1);
-                if (SPB > 1 && qn < g1 && !issue(qn, kb + 1, mnext)) break;
-                const int s = b * SPB + (int)(kb % SPB);
-                const uint32_t ph = (uint32_t)((kb / SPB) & 1);
-                bool ok = true;
-                if (lane == 0) ok = tc::bar_wait(&bar_full[s], ph, g.wait_ns);
+                if (lane == 0) ok = tc::bar_wait(&bar_hits[s], ph, g.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
-                __syncwarp();
+                __syncwarp(); // lane 0's acquire of the stage covers the warp's reads of it
                 if (!ok) {
-                    if (lane == 0) tc_fail(g, &abort_flag, 16 * (1 + b) + 4, q);
+                    if (lane == 0) tc_fail(g, &abort_flag, 16 * warp + 4, gq);
                     break;
                 }
+                const int cnt = meta[s].cnt;
+                const float3 ngrp = f3(meta[s].nrm);
                 unsigned char *st = smem + (size_t)s * g.stage_bytes;
                 const uint32_t A = tc::smem_addr(st + g.rows_bytes);
                 const float4 *hits = reinterpret_cast<const float4 *>(st + g.rows_bytes + g.a_bytes);
-                float3 ngrp = make_float3(0.f, 0.f, 1.f);
-                if (g.adjoint) ngrp = f3(__ldg(&g.N4[mcur.other]));
                 float acc[8];
 #pragma unroll
                 for (int m = 0; m < 8; ++m) acc[m] = 0.f;
@@ -340,7 +370,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     }
                     written |= 1u << p;
                 };
-                for (int e = 0; e < mcur.cnt; ++e) {
+                for (int e = 0; e < cnt; ++e) {
                     const float4 rec = hits[e]; // broadcast read
                     const uint32_t abits = __float_as_uint(rec.w);
                     const int p = (int)(abits & 7u);
@@ -377,11 +407,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::bar_arrive(&bar_afull[s]);
-                if (SPB == 1 && qn < g1 && !issue(qn, kb + 1, mnext)) break;
-                mcur = mnext;
             }
             gc += g1 - g0;
-            kb = (gc + TC_NB - 1 - b) / TC_NB; // groups of this builder in all items so far
             if (aborted(&abort_flag)) break;
             // ------------------------------------------------------ epilogue of the item
             bool ok = true;
@@ -390,7 +417,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             __syncwarp();
             tc::fence_after();
             if (!ok) {
-                if (lane == 0) tc_fail(g, &abort_flag, 16 * (1 + b) + 5, gc);
+                if (lane == 0) tc_fail(g, &abort_flag, 16 * warp + 5, gc);
                 break;
             }
             const bool empty = (g1 == g0);
@@ -439,17 +466,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             __syncwarp();
             if (lane == 0) tc::bar_arrive(&bar_dempty);
         }
-        // no bulk copy may still be writing into this CTA's shared memory when it exits: wait
-        // (bounded) for the last fill of each of this builder's stages
-        if (lane == 0)
-            for (long long kk = kb - 1; kk >= 0 && kk >= kb - SPB; --kk)
-                tc::bar_wait(&bar_full[b * SPB + (int)(kk % SPB)], (uint32_t)((kk / SPB) & 1), TC_DRAIN_NS);
-        __syncwarp();
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == TC_MMA_WARP) tc::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------------ pair-tile construction
@@ -809,6 +830,7 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
 }
 
 int g_num_sms = 0;
+uint32_t g_smem_budget = 0;
 
 rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
     if (!g_num_sms) {
@@ -821,9 +843,18 @@ rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
     a.rows_bytes = (uint32_t)cw * 32u * (a.split ? 2u : 1u);
     a.a_bytes = 4096u * (a.split ? 2u : 1u);
     a.stage_bytes = (a.rows_bytes + a.a_bytes + TC_HCAP * 16u + 127u) & ~127u;
-    const uint32_t budget = 224u * 1024u; // of the 227 KB a CTA may hold, with the static barriers
-    a.spb = (2u * TC_NB * a.stage_bytes <= budget) ? 2 : 1;
-    a.stages = TC_NB * a.spb;
+    // the dynamic shared memory a CTA may opt into, less the kernel's static barriers and buffers
+    if (!g_smem_budget) {
+        int dev = 0, optin = 0;
+        RGS_CUDA(cudaGetDevice(&dev));
+        RGS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa{};
+        RGS_CUDA(cudaFuncGetAttributes(&fa, k_tc_contract));
+        g_smem_budget = (uint32_t)(optin - (int)fa.sharedSizeBytes - 1024);
+    }
+    const uint32_t budget = g_smem_budget;
+    // a multiple of the builder count (a builder owns the stages = b mod TC_NB), up to 16
+    a.stages = (2u * TC_NB * a.stage_bytes <= budget) ? 2 * TC_NB : TC_NB;
     if ((uint32_t)a.stages * a.stage_bytes > budget) {
         rgs_set_error("tensor-core contraction: %d stages of %u bytes exceed shared memory", a.stages, a.stage_bytes);
         return RGS_ERR_ARG;
