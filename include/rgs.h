@@ -361,6 +361,15 @@ rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
  * Host-only.  Errors: RGS_ERR_ARG (NULL transport, mode outside [-1, 1]). */
 rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode);
 
+/* Sizes of the tensor-core contraction's pair tiles for t (built by the first solve or
+ * adjoint that used the tensor-core form after the trace), written to out[0..5] (host):
+ * receiver tiles, their (tile, source) groups, distinct (receiver, source) pairs, stored hits,
+ * source tiles, their (tile, receiver) groups; zeros where a structure is not built.  One
+ * 16 x 16 transport block per pair is the algorithmic work of a bounce (2 * 256 * C flops
+ * per pair); every group costs one 128 x C x 16 MMA.  Host-only.  Errors: RGS_ERR_ARG
+ * (NULL t or out, n < 6). */
+rgs_status rgs_contraction_info(const rgs_transport *t, int64_t *out, int32_t n);
+
 /* Limit, in nanoseconds, of every wait inside the tensor-core contraction's pipeline (a
  * role waiting for a stage of source rows, an operand, a finished accumulator; 0 = default,
  * 4 s).  A wait that runs out makes every role of the kernel stop, wait (for at most a

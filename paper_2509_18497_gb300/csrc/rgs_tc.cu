@@ -624,10 +624,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_tc_sort_pass(const long long *
 // groups per segment: each run of equal key >> 12 (one source, or one receiver) in pieces of
 // at most TC_HCAP hits
 __global__ void __launch_bounds__(256) k_tc_group_count(const long long *__restrict__ seg, const uint32_t *__restrict__ key,
-                                                        int *gcount) {
+                                                        int *gcount, unsigned long long *pairs) {
     const long long s0 = seg[blockIdx.x], s1 = seg[blockIdx.x + 1];
-    int c = 0;
+    int c = 0, pc = 0;
     for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
+        // distinct (other entity, tile slot) pairs: runs of equal key >> 9
+        pc += (e == s0 || (key[e] >> 9) != (key[e - 1] >> 9)) ? 1 : 0;
         if (e != s0 && (key[e] >> 12) == (key[e - 1] >> 12)) continue;
         long long f = e + 1;
         while (f < s1 && (key[f] >> 12) == (key[e] >> 12)) ++f;
@@ -637,6 +639,9 @@ __global__ void __launch_bounds__(256) k_tc_group_count(const long long *__restr
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, off);
+    if ((threadIdx.x & 31) == 0 && pc) atomicAdd(pairs, (unsigned long long)pc);
     __syncthreads();
     if (threadIdx.x == 0) {
         int s = 0;
@@ -721,7 +726,7 @@ __global__ void k_tc_to_blk(int n, int C, int Cp, const float *__restrict__ x, _
 // ------------------------------------------------------------------ host side
 struct TcPairs {
     int ntiles = 0;
-    long long n_hits = 0, n_groups = 0;
+    long long n_hits = 0, n_groups = 0, n_pairs = 0;
     long long *hoff = nullptr, *goff = nullptr;
     int2 *grp = nullptr;
     float4 *hd = nullptr;
@@ -780,6 +785,13 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
     } tmp{st, &tcount, &kA, &kB, &pA, &pB, &cur, &scan_tmp};
     const int scan_cap = rgs_scan_tmp_size(ntiles);
     if ((r = pool_alloc(&tcount, (size_t)ntiles + 1, st)) != RGS_OK) return r;
+    unsigned long long *cur_pairs = nullptr;
+    struct PairsTmp {
+        cudaStream_t st;
+        unsigned long long **p;
+        ~PairsTmp() { pool_release(*p, st); }
+    } ptmp{st, &cur_pairs};
+    if ((r = pool_alloc(&cur_pairs, 1, st)) != RGS_OK) return r;
     if ((r = pool_alloc(&scan_tmp, (size_t)scan_cap, st)) != RGS_OK) return r;
     if ((r = pool_alloc(&kA, (size_t)std::max(H, 1ll), st)) != RGS_OK) return r;
     if ((r = pool_alloc(&kB, (size_t)std::max(H, 1ll), st)) != RGS_OK) return r;
@@ -816,13 +828,17 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
         std::swap(pin, pout);
     }
     RGS_LAUNCH("tc sort");
-    { ProfScope ps_("k_tc_group_count", st); k_tc_group_count<<<ntiles, 256, 0, st>>>(P.hoff, kin, tcount); }
+    RGS_CUDA(cudaMemsetAsync(cur_pairs, 0, sizeof(unsigned long long), st));
+    { ProfScope ps_("k_tc_group_count", st); k_tc_group_count<<<ntiles, 256, 0, st>>>(P.hoff, kin, tcount, cur_pairs); }
     RGS_LAUNCH("tc group count");
     if ((r = rgs_scan_counts(tcount, P.goff, ntiles, scan_tmp, scan_cap, st)) != RGS_OK) return r;
     long long ng = 0;
+    unsigned long long np = 0;
     RGS_CUDA(cudaMemcpyAsync(&ng, P.goff + ntiles, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    RGS_CUDA(cudaMemcpyAsync(&np, cur_pairs, sizeof(np), cudaMemcpyDeviceToHost, st));
     RGS_CUDA(cudaStreamSynchronize(st));
     P.n_groups = ng;
+    P.n_pairs = (long long)np;
     if ((r = dev_alloc(&P.grp, (size_t)std::max(ng, 1ll))) != RGS_OK) return r;
     { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, nd, adjoint ? 1 : 0, P.grp, P.hd); }
     RGS_LAUNCH("tc finish");
@@ -1029,4 +1045,28 @@ rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout,
     a.flags = t->flags;
     a.wait_ns = t->tc_wait_ns;
     return launch_contract(t, a, st);
+}
+
+// counts of the pair tiles (for throughput reports): receiver tiles, their groups and
+// distinct (receiver, source) pairs, stored hits, source tiles and their groups; zeros for
+// a structure not built yet
+extern "C" rgs_status rgs_contraction_info(const rgs_transport *t, int64_t *out, int32_t n) {
+    if (!t || !out || n < 6) {
+        rgs_set_error("rgs_contraction_info: NULL argument or fewer than 6 entries");
+        return RGS_ERR_ARG;
+    }
+    for (int q = 0; q < n; ++q) out[q] = 0;
+    if (!t->tc) return RGS_OK;
+    const rgs_tc_state &s = *t->tc;
+    if (s.fwd_ok) {
+        out[0] = s.fwd.ntiles;
+        out[1] = s.fwd.n_groups;
+        out[2] = s.fwd.n_pairs;
+        out[3] = s.fwd.n_hits;
+    }
+    if (s.adj_ok) {
+        out[4] = s.adj.ntiles;
+        out[5] = s.adj.n_groups;
+    }
+    return RGS_OK;
 }

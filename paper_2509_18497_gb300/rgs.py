@@ -30,7 +30,7 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
            "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_set_tensor_cores",
-           "rgs_set_wait_limit",
+           "rgs_set_wait_limit", "rgs_contraction_info",
            "rgs_trace_pairs",
            "rgs_adjoint_pairs", "rgs_adjoint_pairs_geometry", "rgs_adjoint_geometry")
 
@@ -137,6 +137,8 @@ def load(path=LIB_PATH):
     L.rgs_set_tensor_cores.restype = ct.c_int
     L.rgs_set_wait_limit.argtypes = [vp, ct.c_int64]
     L.rgs_set_wait_limit.restype = ct.c_int
+    L.rgs_contraction_info.argtypes = [vp, ct.POINTER(ct.c_int64), ct.c_int32]
+    L.rgs_contraction_info.restype = ct.c_int
     L.rgs_trim_workspace.argtypes = []
     L.rgs_trim_workspace.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
@@ -376,6 +378,15 @@ def rgs_set_tensor_cores(transport, mode):
 def rgs_set_wait_limit(transport, ns):
     """Limit (ns) of every wait in the tensor-core contraction's pipeline (0: default 4 s)."""
     _check(load().rgs_set_wait_limit(transport.h, int(ns)))
+
+
+def rgs_contraction_info(transport):
+    """Pair-tile sizes of the tensor-core contraction: dict of receiver tiles, groups, pairs,
+    hits, source tiles and source-tile groups (zeros before the structures are built)."""
+    out = (ct.c_int64 * 6)()
+    _check(load().rgs_contraction_info(transport.h, out, 6))
+    keys = ("tiles", "groups", "pairs", "hits", "src_tiles", "src_groups")
+    return {k: int(v) for k, v in zip(keys, out)}
 
 
 def rgs_trim_workspace():

@@ -81,6 +81,7 @@ def test_service_entry_points_reject_bad_arguments_without_device_work():
     assert L.rgs_set_memory_budget(None, 1 << 20) == 1
     assert L.rgs_set_tensor_cores(None, 1) == 1
     assert L.rgs_set_wait_limit(None, 1000) == 1
+    assert L.rgs_contraction_info(None, None, 6) == 1
     assert L.rgs_transport_info_get(None, None) == 1
     # the no-allocation norm: NULL arrays, negative and oversized lengths
     p = ct.c_void_p(16)
