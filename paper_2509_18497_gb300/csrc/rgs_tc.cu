@@ -33,10 +33,10 @@
 namespace {
 
 constexpr int TC_R = 8;           // receivers (or sources) per tile: 8 x 16 coefficients = M 128
-constexpr int TC_NB = 8;          // builder warps
+constexpr int TC_NB = 16;         // builder warps (as many as stages take part)
 constexpr int TC_THREADS = (3 + TC_NB) * 32; // two producers, the MMA warp, the builders
-constexpr int TC_MAX_STAGES = 16;  // up to two per builder
-constexpr int TC_HCAP = 24;        // hit records per group (longer (tile, source) runs are split)
+constexpr int TC_MAX_STAGES = 16;  // one per builder
+constexpr int TC_HCAP = 20;        // hit records per group (longer (tile, source) runs are split)
 constexpr int TC_CHUNK = 512;     // columns per pass (TMEM holds 512 FP32 columns)
 constexpr uint64_t TC_DRAIN_NS = 1000000000ull; // wait for in-flight copies and MMAs at exit
 
@@ -144,8 +144,8 @@ __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int wh
 // Roles: warps 0 and 1 produce (even and odd groups: a stage's empty barrier is always
 // awaited by the same warp), warp 2 owns the TMEM and issues the MMAs (one lane), warps
 // 3 .. 3 + TC_NB - 1 build operands and drain the accumulator.  Group g of the CTA uses stage
-// g % S; builder b takes the groups g = b (mod TC_NB), i.e. the stages b, b + TC_NB, ...,
-// so every use of a stage is awaited by the warp that awaited its previous use and a parity
+// g % S; builder b < S takes the groups g = b (mod S), i.e. every use of stage b, so every
+// use of a stage is awaited by the warp that awaited its previous use and a parity
 // wait can never see a phase two uses old.  Per stage: `hits` (the group's hit records and
 // metadata), `rows` (the source rows; awaited by the MMA only, so the S - 1 groups ahead of
 // it hide the copy's latency), `afull` (operand built), `empty` (MMAs done).
@@ -153,6 +153,8 @@ constexpr int TC_PROD = 2;
 constexpr int TC_MMA_WARP = TC_PROD;
 constexpr int TC_B0 = TC_PROD + 1; // first builder warp
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
+    // builder b takes the CTA's groups g = b (mod S), i.e. stage b: S = 16, or 8 when the
+    // stages are large (then builders 8..15 only drain the accumulator)
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_hits[TC_MAX_STAGES], bar_rows[TC_MAX_STAGES], bar_afull[TC_MAX_STAGES],
         bar_empty[TC_MAX_STAGES];
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     __shared__ StageMeta meta[TC_MAX_STAGES];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ float ybuf_all[TC_NB][32];
+    __shared__ __align__(16) float ybuf_all[TC_NB][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = g.stages;
     const int items = g.ntiles * g.nchunks;
@@ -326,8 +328,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             const int c0 = ch * TC_CHUNK;
             const int cw = min(TC_CHUNK, g.Cp - c0);
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
-            const long long qfirst = g0 + (long long)((b - (int)(gc % TC_NB) + TC_NB) % TC_NB);
-            for (long long q = qfirst; q < g1 && !aborted(&abort_flag); q += TC_NB) {
+            // forward: lane p < 8 holds the item's receiver p's normal
+            float4 tn = make_float4(0.f, 0.f, 1.f, 0.f);
+            if (!g.adjoint && lane < TC_R && t * TC_R + lane < g.n) tn = __ldg(&g.N4[t * TC_R + lane]);
+            const long long qfirst = b < S ? g0 + (long long)((b - (int)(gc % S) + S) % S) : g1;
+            for (long long q = qfirst; q < g1 && !aborted(&abort_flag); q += S) {
                 const long long gq = gc + (q - g0);
                 const int s = (int)(gq % S);
                 const uint32_t ph = (uint32_t)((gq / S) & 1);
@@ -376,15 +381,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     const int p = (int)(abits & 7u);
                     const float a = __uint_as_float(abits & ~7u);
                     const float3 d = make_float3(rec.x, rec.y, rec.z);
-                    const float3 nrm = g.adjoint ? ngrp : f3(__ldg(&g.N4[t * TC_R + p]));
+                    float3 nrm = ngrp;
+                    if (!g.adjoint)
+                        nrm = make_float3(__shfl_sync(0xffffffffu, tn.x, p), __shfl_sync(0xffffffffu, tn.y, p),
+                                          __shfl_sync(0xffffffffu, tn.z, p));
                     // lanes 0..15: Y_k(-d); lanes 16..31: Y_k(R d)
                     const float3 v = (lane < 16) ? make_float3(-d.x, -d.y, -d.z) : reflect_n(nrm, d);
                     ybuf[lane] = sh_mono(cf, v);
                     __syncwarp();
                     const float X = ybuf[xoff + k];
-                    float Z[8];
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) Z[m] = ybuf[zoff + mh * 8 + m];
+                    const float4 z0 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8);
+                    const float4 z1 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8 + 4);
+                    const float Z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
                     __syncwarp();
                     if (p != cur) {
                         if (cur >= 0) flush(cur);
@@ -421,14 +429,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 break;
             }
             const bool empty = (g1 == g0);
-            const int quarter = warp & 3, half = b >> 2;
+            const int quarter = warp & 3, part = b >> 2; // TC_NB / 4 warps share a TMEM lane quarter
             const int row = quarter * 32 + lane;
             const int p = row >> 4, kr = row & 15;
             const int e_ent = t * TC_R + p;
             const bool live = e_ent < g.n;
             const float oe = live ? alpha_at(g.alpha_model, __ldg(&g.P[e_ent].w)) : 0.f;
             double dsq = 0.0;
-            for (int cb = half * 16; cb < cw; cb += 32) {
+            for (int cb = part * 16; cb < cw; cb += 16 * (TC_NB / 4)) {
                 float v[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb, v);
                 if (!live) continue;
@@ -866,11 +874,11 @@ rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
         RGS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         cudaFuncAttributes fa{};
         RGS_CUDA(cudaFuncGetAttributes(&fa, k_tc_contract));
-        g_smem_budget = (uint32_t)(optin - (int)fa.sharedSizeBytes - 1024);
+        g_smem_budget = (uint32_t)(optin - (int)fa.sharedSizeBytes - 256);
     }
     const uint32_t budget = g_smem_budget;
-    // a multiple of the builder count (a builder owns the stages = b mod TC_NB), up to 16
-    a.stages = (2u * TC_NB * a.stage_bytes <= budget) ? 2 * TC_NB : TC_NB;
+    // one stage per active builder: 16, or 8 when 16 do not fit
+    a.stages = (16u * a.stage_bytes <= budget) ? 16 : 8;
     if ((uint32_t)a.stages * a.stage_bytes > budget) {
         rgs_set_error("tensor-core contraction: %d stages of %u bytes exceed shared memory", a.stages, a.stage_bytes);
         return RGS_ERR_ARG;

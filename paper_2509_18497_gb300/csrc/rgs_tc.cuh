@@ -117,7 +117,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, uint64_
     if (bar_test(bar, parity)) return true;
     const uint64_t t0 = now_ns();
     while (true) {
-        if (bar_test_sleep(bar, parity, 20000u)) return true;
+        if (bar_test_sleep(bar, parity, 1000000u)) return true;
         if (now_ns() - t0 > limit_ns) return false;
     }
 }
