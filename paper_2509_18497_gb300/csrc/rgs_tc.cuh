@@ -46,6 +46,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
                  "l"(a), "l"(b), "r"(idesc), "r"(accum)
                  : "memory");
 }
+// the same with A in tensor memory: a_tmem addresses the 128 x 16 BF16 slice (8 columns, two
+// consecutive K elements per 32-bit column, the lower K in the low half)
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accum) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(
+                     d_tmem),
+                 "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+                 : "memory");
+}
+// descriptor of the same blocked layout read as an MN-major operand (the N index contiguous
+// within a core matrix): 256 bytes between K-adjacent and 128 between N-adjacent core matrices
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(256 >> 4) << 16;
+    d |= (uint64_t)(128 >> 4) << 32;
+    d |= 1ull << 46;
+    return d;
+}
 // the mbarrier receives one arrival once every MMA this thread issued before has completed
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
@@ -75,6 +93,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
+
+// 32 lanes x 8 consecutive 32-bit TMEM columns from registers (warp-collective)
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------------ mbarriers
 __device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count) {
