@@ -663,8 +663,8 @@ __global__ void __launch_bounds__(256) k_tc_group_count(const long long *__restr
 // (a relative change below 1e-6)
 __global__ void __launch_bounds__(256) k_tc_finish(const long long *__restrict__ seg, const long long *__restrict__ goff,
                                                    const uint32_t *__restrict__ key, const uint2 *__restrict__ pay,
-                                                   const float4 *__restrict__ dir, int nd, int adjoint, int2 *grp,
-                                                   float4 *hd) {
+                                                   const float4 *__restrict__ dir, const long long *__restrict__ off,
+                                                   int nd, int adjoint, int2 *grp, float4 *hd, uint32_t *hslot) {
     const int t = blockIdx.x;
     const long long s0 = seg[t], s1 = seg[t + 1];
     for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
@@ -672,8 +672,10 @@ __global__ void __launch_bounds__(256) k_tc_finish(const long long *__restrict__
         const uint2 pv = pay[e];
         const int other = (int)(kv >> 12), p = (int)((kv >> 9) & 7u), q = (int)(kv & 511u);
         const int recv = adjoint ? other : t * TC_R + p;
-        const float4 d = dir[(long long)recv * nd + q];
+        const long long r = (long long)recv * nd + q;
+        const float4 d = dir[r];
         hd[e] = make_float4(d.x, d.y, d.z, __uint_as_float((pv.x & ~7u) | (uint32_t)p));
+        if (hslot) hslot[e] = (uint32_t)(off[r] + pv.y); // the record slot of the hit (its ray's h-th)
     }
     // groups: one warp walks the runs in 32-element windows
     if (threadIdx.x < 32) {
@@ -738,6 +740,7 @@ struct TcPairs {
     long long *hoff = nullptr, *goff = nullptr;
     int2 *grp = nullptr;
     float4 *hd = nullptr;
+    uint32_t *hslot = nullptr; // source tiles: each hit's record slot (the opacity gather writes g_h there)
 };
 
 struct rgs_tc_state {
@@ -756,6 +759,7 @@ void pairs_free(TcPairs &p) {
     dev_free(p.goff);
     dev_free(p.grp);
     dev_free(p.hd);
+    dev_free(p.hslot);
     p = TcPairs{};
 }
 
@@ -808,6 +812,7 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
     if ((r = dev_alloc(&P.hoff, (size_t)ntiles + 1)) != RGS_OK) return r;
     if ((r = dev_alloc(&P.goff, (size_t)ntiles + 1)) != RGS_OK) return r;
     if ((r = dev_alloc(&P.hd, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
+    if (adjoint && (r = dev_alloc(&P.hslot, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
     if (!adjoint) {
         { ProfScope ps_("k_tc_tile_count", st); k_tc_tile_count_fwd<<<(ntiles + 7) / 8, 256, 0, st>>>(t->cnt, n, nd, ntiles, tcount); }
     } else {
@@ -848,7 +853,7 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
     P.n_groups = ng;
     P.n_pairs = (long long)np;
     if ((r = dev_alloc(&P.grp, (size_t)std::max(ng, 1ll))) != RGS_OK) return r;
-    { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, nd, adjoint ? 1 : 0, P.grp, P.hd); }
+    { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, t->off, nd, adjoint ? 1 : 0, P.grp, P.hd, P.hslot); }
     RGS_LAUNCH("tc finish");
     return RGS_OK;
 }
@@ -932,10 +937,10 @@ void rgs_tc_invalidate(rgs_transport *t) {
 bool rgs_tc_eligible(const rgs_transport *t, int precision) {
     if (t->tc_mode == 0) return false; // disabled by the caller
     if (t->kind != RGS_KIND_HEMISPHERE || t->nc != 16 || precision == RGS_FP32) return false;
-    if (t->n > (1 << 20) || t->nd > 512 || t->n_hits <= 0) return false;
+    if (t->n > (1 << 20) || t->nd > 512 || t->n_hits <= 0 || t->n_slots >= (1ll << 32)) return false;
     if (t->tc_mode < 0 && t->C < RGS_TC_MIN_COLS) return false; // automatic: many right-hand sides only
     if (t->stride != 0) return false; // the adjoint reads every iterate of this path
-    // memory: two structures of 20 B per hit, three blocked BF16 arrays, sort scratch of 24 B per hit
+    // memory: two structures of 16-20 B per hit, three blocked BF16 arrays, sort scratch of 24 B per hit
     const double need = 2.0 * 20.0 * t->n_hits + 24.0 * t->n_hits + 3.0 * 2.0 * t->n * (double)((t->C + 15) & ~15) * 16;
     return need < 0.8 * (double)pool_available_bytes();
 }
