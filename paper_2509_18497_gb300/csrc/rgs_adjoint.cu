@@ -590,8 +590,16 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     auto KT = [&](int a) -> rgs_status {
         rgs_status q;
         if (tcp) { // tensor cores over source tiles: y^(a-1) = o c (x) v^(a-1) in BF16 row blocks
-            if (a == 1 && (q = rgs_tc_make_y(t, vp(0), 0, st)) != RGS_OK) return q;
-            return rgs_tc_adjoint_bounce(t, (a - 1) & 1, a & 1, vp(a), t->u, st);
+            // the opacity gather pairs y^(a) with B^(n-1-a) while y^(a) is at hand
+            const bool gh = (dopo || geo) && nb >= 1;
+            if (a == 1) {
+                if ((q = rgs_tc_make_y(t, vp(0), 0, st)) != RGS_OK) return q;
+                if (gh && (q = rgs_tc_opacity(t, 0, t->iters + A * (nb - 1), true, st)) != RGS_OK) return q;
+            }
+            if ((q = rgs_tc_adjoint_bounce(t, (a - 1) & 1, a & 1, vp(a), t->u, st)) != RGS_OK) return q;
+            if (gh && a <= nb - 1 && (q = rgs_tc_opacity(t, a & 1, t->iters + A * (nb - 1 - a), false, st)) != RGS_OK)
+                return q;
+            return RGS_OK;
         }
         for (size_t p = 0; p + 1 < parts.size(); ++p) {
             const int j0 = parts[p], j1 = parts[p + 1];
@@ -665,7 +673,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
             { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, vp(a), Qb[b - lo], t->Pg); }
             RGS_LAUNCH("pair accum");
         }
-        if (dopo || geo) { // g_h over this segment's iterates, four per launch
+        if ((dopo || geo) && !tcp) { // g_h over this segment's iterates, four per launch
             for (int b0 = hi; b0 >= lo; b0 -= 4) {
                 const int na = min(4, b0 - lo + 1);
                 const float *vv[4], *bb[4];

@@ -823,6 +823,7 @@ rgs_status rgs_tc_bounce(rgs_transport *t, int in, int out, bool split, bool wan
                          const float *S, float *Q, float *Bout, __nv_bfloat16 *Bout16, double *norm2, cudaStream_t st);
 rgs_status rgs_tc_make_y(rgs_transport *t, const float *v, int slot, cudaStream_t st);
 rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout, float *u, cudaStream_t st);
+rgs_status rgs_tc_opacity(rgs_transport *t, int slot, const float *Bsrc, bool first, cudaStream_t st);
 rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st); // RGS_ERR_TIMEOUT if a bounded wait ran out
 rgs_status rgs_tc_reset_flags(rgs_transport *t, cudaStream_t st);
 void rgs_tc_invalidate(rgs_transport *t);

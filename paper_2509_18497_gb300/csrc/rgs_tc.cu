@@ -481,6 +481,294 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     if (warp == TC_MMA_WARP) tc::tmem_dealloc(tmem, 512);
 }
 
+// ------------------------------------------------------------------ opacity gather (adjoint)
+// The per-hit sums of the opacity backward, g_h += sum over columns of y_r^(a) . s_h^(b) with
+// y_r = (pi/nd) Y(R_i d)^T y_i^(a) and s_h = Y(-d)^T B_j^(b) (y = o c (x) v), regrouped per
+// (receiver i, source j) pair:  g_h = (pi/nd) Y(R_i d)^T P_ij Y(-d),  P_ij[k][m] =
+// sum_c y_i[c][k] B_j[c][m].  Over the adjoint's source tiles: the tile's 8 sources' rows
+// B^(b) sit in TMEM as a 128 x C BF16 operand (rows = source x coefficient m); per group
+// (receiver i) the receiver's BF16 y^(a) rows are bulk-copied into shared memory and read as
+// an MN-major C x 16 operand, so C/16 MMAs leave D2[(sigma, m)][k] = P_{i sigma}[k][m] in TMEM;
+// then the warps of one quad (one per TMEM lane quarter: sources 2q, 2q + 1) read their
+// quarter and finish g_h for the group's hits on those sources.
+struct TcOpaArgs {
+    int n, C, Cp, nd, ntiles, stages;
+    uint32_t stage_bytes, rows_bytes, tmem_cols;
+    const long long *hoff, *goff;
+    const int2 *grp;
+    const float4 *hd;
+    const uint32_t *hslot;          // per hit: its record slot (the compositing order of its ray)
+    const __nv_bfloat16 *yblk;      // y^(a) of every receiver, blocked BF16 rows
+    const float *Bsrc;              // B^(b), FP32 [N][C][16]
+    const float4 *N4;
+    float w;
+    float *gh;
+    int first;                      // write g_h instead of adding to it
+    int *flags;
+    unsigned long long wait_ns;
+};
+
+constexpr int TO_PROD = 2, TO_MMA = 2, TO_C0 = 3, TO_NC = 16, TO_QUADS = TO_NC / 4;
+constexpr int TO_THREADS = (TO_C0 + TO_NC) * 32;
+
+__device__ __forceinline__ void to_fail(const TcOpaArgs &g, int *abort_flag, int where, long long gcount) {
+    atomicExch(abort_flag, 1);
+    if (atomicAdd(&g.flags[FLAG_TC_TIMEOUT], 1) == 0) {
+        g.flags[FLAG_TC_TIMEOUT + 1] = where;
+        g.flags[FLAG_TC_TIMEOUT + 2] = (int)gcount;
+    }
+}
+
+__global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_hits[TC_MAX_STAGES], bar_rows[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_d2full[TO_QUADS], bar_d2empty[TO_QUADS], bar_a2full, bar_a2empty, bar_drain;
+    __shared__ StageMeta meta[TC_MAX_STAGES];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ __align__(16) float ybuf_all[TO_NC][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = g.stages;
+    const int a2cols = g.Cp / 2;                 // BF16 pairs per TMEM column
+    const int d2col0 = (a2cols + 15) & ~15;      // D2 slots after the A2 operand
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::bar_init(&bar_hits[s], 1);
+            tc::bar_init(&bar_rows[s], 1);
+            tc::bar_init(&bar_empty[s], 1 + 4); // the MMAs (rows free) and the quad's 4 warps (hits read)
+        }
+        for (int q = 0; q < TO_QUADS; ++q) {
+            tc::bar_init(&bar_d2full[q], 1);
+            tc::bar_init(&bar_d2empty[q], 4);
+        }
+        tc::bar_init(&bar_a2full, TO_NC);
+        tc::bar_init(&bar_a2empty, 1);
+        tc::bar_init(&bar_drain, 1);
+        abort_flag = 0;
+        tc::bar_init_fence();
+    }
+    if (warp == TO_MMA) tc::tmem_alloc(&tmem_slot, g.tmem_cols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int items = g.ntiles;
+
+    if (warp < TO_PROD) {
+        // ---------------------------------------------------------- producers
+        long long gc = 0;
+        const uint32_t rbytes = (uint32_t)g.Cp * 32u;
+        for (int t = blockIdx.x; t < items && !aborted(&abort_flag); t += gridDim.x) {
+            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            const long long hb = g.hoff[t];
+            const int tile_hits = (int)(g.hoff[t + 1] - hb);
+            for (long long gb = g0; gb < g1 && !aborted(&abort_flag); gb += 32) {
+                const int m = (int)min(32ll, g1 - gb);
+                int2 e = make_int2(0, 0);
+                int next = tile_hits;
+                float4 nrm = make_float4(0.f, 0.f, 1.f, 0.f);
+                if (lane < m) {
+                    e = __ldg(&g.grp[gb + lane]);
+                    if (gb + lane + 1 < g1) next = __ldg(&g.grp[gb + lane + 1]).y;
+                    nrm = __ldg(&g.N4[e.x]);
+                }
+                for (int q = 0; q < m; ++q) {
+                    const long long gq = gc + (gb - g0) + q;
+                    if ((int)(gq % TO_PROD) != warp) continue;
+                    const int other = __shfl_sync(0xffffffffu, e.x, q);
+                    const int first = __shfl_sync(0xffffffffu, e.y, q);
+                    const int cnt = __shfl_sync(0xffffffffu, next, q) - first;
+                    float4 nq;
+                    nq.x = __shfl_sync(0xffffffffu, nrm.x, q);
+                    nq.y = __shfl_sync(0xffffffffu, nrm.y, q);
+                    nq.z = __shfl_sync(0xffffffffu, nrm.z, q);
+                    nq.w = __int_as_float(first); // the group's first hit, relative to the tile
+                    if (lane == 0) {
+                        const int s = (int)(gq % S);
+                        const uint32_t ph = (uint32_t)((gq / S) & 1);
+                        if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
+                            to_fail(g, &abort_flag, 16 * warp + 1, gq);
+                        } else {
+                            meta[s].nrm = nq;
+                            meta[s].other = other;
+                            meta[s].cnt = cnt;
+                            unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                            const uint32_t hbytes = (uint32_t)cnt * 16u;
+                            tc::bar_arrive_tx(&bar_hits[s], hbytes);
+                            tc::bulk_g2s(st + g.rows_bytes, g.hd + hb + first, hbytes, &bar_hits[s]);
+                            tc::bar_arrive_tx(&bar_rows[s], rbytes);
+                            tc::bulk_g2s(st, g.yblk + (size_t)other * (size_t)g.Cp * 16, rbytes, &bar_rows[s]);
+                        }
+                    }
+                    __syncwarp();
+                    if (aborted(&abort_flag)) break;
+                }
+            }
+            gc += g1 - g0;
+        }
+        if (lane == 0) {
+            long long seen = 0;
+            for (long long q = gc - 1; q >= 0 && seen < S / TO_PROD; --q) {
+                if ((int)(q % TO_PROD) != warp) continue;
+                ++seen;
+                tc::bar_wait(&bar_rows[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
+                tc::bar_wait(&bar_hits[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
+            }
+        }
+        __syncwarp();
+    } else if (warp == TO_MMA) {
+        // ---------------------------------------------------------- MMA issuer
+        long long gc = 0;
+        long long quse[TO_QUADS] = {0, 0, 0, 0};
+        int tl = 0;
+        for (int t = blockIdx.x; t < items && !aborted(&abort_flag); t += gridDim.x, ++tl) {
+            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            if (lane == 0) {
+                bool ok = tc::bar_wait(&bar_a2full, (uint32_t)(tl & 1), g.wait_ns);
+                if (!ok) to_fail(g, &abort_flag, 16 * warp + 2, gc);
+                tc::fence_after();
+                for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gc) {
+                    const int s = (int)(gc % S);
+                    const uint32_t ph = (uint32_t)((gc / S) & 1);
+                    const int Q = (int)(gc % TO_QUADS);
+                    if (!tc::bar_wait(&bar_rows[s], ph, g.wait_ns) ||
+                        (quse[Q] > 0 && !tc::bar_wait(&bar_d2empty[Q], (uint32_t)((quse[Q] - 1) & 1), g.wait_ns))) {
+                        to_fail(g, &abort_flag, 16 * warp + 3, gc);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint32_t rows = tc::smem_addr(smem + (size_t)s * g.stage_bytes);
+                    const uint32_t d = tmem + (uint32_t)(d2col0 + 16 * Q);
+                    const uint32_t id = tc::idesc_bf16(128, 16) | (1u << 16); // B MN-major
+                    for (int kk = 0; kk < g.Cp / 16; ++kk)
+                        tc::mma_bf16_ta(d, tmem + (uint32_t)(kk * 8), tc::sdesc_mn(rows + (uint32_t)kk * 512u), id,
+                                        kk > 0 ? 1u : 0u);
+                    tc::mma_commit(&bar_empty[s]);
+                    tc::mma_commit(&bar_d2full[Q]);
+                    ++quse[Q];
+                }
+                tc::mma_commit(&bar_a2empty);
+            }
+            __syncwarp();
+            gc = __shfl_sync(0xffffffffu, gc, 0);
+            for (int Q = 0; Q < TO_QUADS; ++Q) quse[Q] = __shfl_sync(0xffffffffu, quse[Q], 0);
+        }
+        if (lane == 0) {
+            tc::mma_commit(&bar_drain);
+            tc::bar_wait(&bar_drain, 0u, TC_DRAIN_NS);
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- A2 loaders + consumers
+        const int cwp = warp - TO_C0;            // 0..15
+        const int Q = cwp >> 2;                  // quad
+        const int quarter = warp & 3;            // TMEM lane quarter: sources 2 quarter, 2 quarter + 1
+        const int part = cwp >> 2;               // column share of the A2 load within the quarter
+        const int k = lane & 15;
+        float cf[20];
+#pragma unroll
+        for (int q = 0; q < 20; ++q) cf[q] = TC_SH[k][q];
+        float *ybuf = ybuf_all[cwp];
+        long long gc = 0, use = 0;
+        int tl = 0;
+        for (int t = blockIdx.x; t < items && !aborted(&abort_flag); t += gridDim.x, ++tl) {
+            const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            // A2: lane (sigma, m) of this quarter holds B^(b)[sigma][c][m] for every c, BF16 pairs
+            if (tl > 0) {
+                bool ok = true;
+                if (lane == 0) ok = tc::bar_wait(&bar_a2empty, (uint32_t)((tl - 1) & 1), g.wait_ns);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp();
+                tc::fence_after();
+                if (!ok) {
+                    if (lane == 0) to_fail(g, &abort_flag, 16 * warp + 6, gc);
+                    break;
+                }
+            }
+            {
+                const int row = quarter * 32 + lane;
+                const int src = t * TC_R + (row >> 4), m = row & 15;
+                const bool live = src < g.n;
+                for (int j0 = part * 8; j0 < a2cols; j0 += 8 * 4) {
+                    uint32_t r[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int c = 2 * (j0 + q);
+                        float x0 = 0.f, x1 = 0.f;
+                        if (live && c < g.C) x0 = __ldg(&g.Bsrc[((size_t)src * g.C + c) * 16 + m]);
+                        if (live && c + 1 < g.C) x1 = __ldg(&g.Bsrc[((size_t)src * g.C + c + 1) * 16 + m]);
+                        r[q] = tc::pack_bf16(x0, x1);
+                    }
+                    tc::tmem_st8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j0, r);
+                }
+                tc::tmem_st_wait();
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::bar_arrive(&bar_a2full);
+            }
+            // this quad's groups of the item: CTA-wide index gq = Q (mod 4)
+            const long long qfirst = g0 + (long long)((Q - (int)(gc % TO_QUADS) + TO_QUADS) % TO_QUADS);
+            for (long long q = qfirst; q < g1 && !aborted(&abort_flag); q += TO_QUADS, ++use) {
+                const long long gq = gc + (q - g0);
+                const int s = (int)(gq % S);
+                const uint32_t ph = (uint32_t)((gq / S) & 1);
+                bool ok = true;
+                if (lane == 0)
+                    ok = tc::bar_wait(&bar_hits[s], ph, g.wait_ns) && tc::bar_wait(&bar_d2full[Q], (uint32_t)(use & 1), g.wait_ns);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp();
+                tc::fence_after();
+                if (!ok) {
+                    if (lane == 0) to_fail(g, &abort_flag, 16 * warp + 4, gq);
+                    break;
+                }
+                float P[16]; // P[k] of this lane's (sigma, m) row
+                tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d2col0 + 16 * Q), P);
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::bar_arrive(&bar_d2empty[Q]);
+                const int cnt = meta[s].cnt;
+                const float3 nrm = f3(meta[s].nrm);
+                const long long h0 = g.hoff[t] + __float_as_int(meta[s].nrm.w);
+                const float4 *hits = reinterpret_cast<const float4 *>(smem + (size_t)s * g.stage_bytes + g.rows_bytes);
+                const int mysig = 2 * quarter + (lane >> 4);
+                for (int e = 0; e < cnt; ++e) {
+                    const float4 rec = hits[e];
+                    const uint32_t abits = __float_as_uint(rec.w);
+                    const int sig = (int)(abits & 7u);
+                    if ((sig >> 1) != quarter) continue; // another quarter's source
+                    const float3 d = make_float3(rec.x, rec.y, rec.z);
+                    // lanes 0..15: Y_k(R_i d); lanes 16..31: Y_k(-d)
+                    const float3 v = (lane < 16) ? reflect_n(nrm, d) : make_float3(-d.x, -d.y, -d.z);
+                    ybuf[lane] = sh_mono(cf, v);
+                    __syncwarp();
+                    float tsum = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < 16; ++kk) tsum = fmaf(ybuf[kk], P[kk], tsum);
+                    float val = (sig == mysig) ? tsum * ybuf[16 + (lane & 15)] : 0.f;
+#pragma unroll
+                    for (int off = 8; off > 0; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
+                    __syncwarp();
+                    if (lane == (sig & 1) * 16) {
+                        const uint32_t slot = __ldg(&g.hslot[h0 + e]);
+                        const float add = g.w * val;
+                        g.gh[slot] = g.first ? add : g.gh[slot] + add;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) tc::bar_arrive(&bar_empty[s]);
+            }
+            gc += g1 - g0;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == TO_MMA) tc::tmem_dealloc(tmem, g.tmem_cols);
+}
+
 // ------------------------------------------------------------------ pair-tile construction
 // hits per receiver tile (forward): the sum of the counts of its rays
 __global__ void k_tc_tile_count_fwd(const int *__restrict__ cnt, int n, int nd, int ntiles, int *tcount) {
@@ -1081,5 +1369,63 @@ extern "C" rgs_status rgs_contraction_info(const rgs_transport *t, int64_t *out,
         out[4] = s.adj.ntiles;
         out[5] = s.adj.n_groups;
     }
+    return RGS_OK;
+}
+
+// the opacity gather of one adjoint pairing: g_h (+)= the sums of y^(a) (blk[slot]) against B^(b)
+// (FP32 Bsrc) over the source tiles; first: write instead of add
+rgs_status rgs_tc_opacity(rgs_transport *t, int slot, const float *Bsrc, bool first, cudaStream_t st) {
+    rgs_tc_state &s = *t->tc;
+    if (!g_num_sms) {
+        int dev = 0;
+        RGS_CUDA(cudaGetDevice(&dev));
+        RGS_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    TcOpaArgs a{};
+    a.n = t->n;
+    a.C = t->C;
+    a.Cp = s.Cp;
+    a.nd = t->nd;
+    a.ntiles = s.adj.ntiles;
+    a.hoff = s.adj.hoff;
+    a.goff = s.adj.goff;
+    a.grp = s.adj.grp;
+    a.hd = s.adj.hd;
+    a.hslot = s.adj.hslot;
+    a.yblk = s.blk[slot];
+    a.Bsrc = Bsrc;
+    a.N4 = t->sc->N4;
+    a.w = 3.14159265358979f / (float)t->nd;
+    a.gh = t->gh;
+    a.first = first ? 1 : 0;
+    a.flags = t->flags;
+    a.wait_ns = t->tc_wait_ns;
+    a.rows_bytes = (uint32_t)s.Cp * 32u;
+    a.stage_bytes = (a.rows_bytes + TC_HCAP * 16u + 127u) & ~127u;
+    const uint32_t need_cols = (uint32_t)(((s.Cp / 2 + 15) & ~15) + 16 * TO_QUADS);
+    a.tmem_cols = need_cols <= 256 ? 256u : 512u;
+    if (need_cols > 512) {
+        rgs_set_error("tensor-core opacity gather: %d columns do not fit tensor memory", t->C);
+        return RGS_ERR_ARG;
+    }
+    int optin = 0, dev = 0;
+    RGS_CUDA(cudaGetDevice(&dev));
+    RGS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    RGS_CUDA(cudaFuncGetAttributes(&fa, k_tc_opacity));
+    const uint32_t budget = (uint32_t)(optin - (int)fa.sharedSizeBytes - 256);
+    a.stages = (16u * a.stage_bytes <= budget) ? 16 : 8;
+    if ((uint32_t)a.stages * a.stage_bytes > budget) {
+        rgs_set_error("tensor-core opacity gather: stages of %u bytes exceed shared memory", a.stage_bytes);
+        return RGS_ERR_ARG;
+    }
+    const size_t smem = std::max<size_t>((size_t)a.stages * a.stage_bytes, 120u * 1024u);
+    RGS_CUDA(cudaFuncSetAttribute(k_tc_opacity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = std::max(1, std::min(a.ntiles, g_num_sms));
+    {
+        ProfScope ps_("k_tc_opacity", st);
+        k_tc_opacity<<<grid, TO_THREADS, smem, st>>>(a);
+    }
+    RGS_LAUNCH("tensor-core opacity gather");
     return RGS_OK;
 }
