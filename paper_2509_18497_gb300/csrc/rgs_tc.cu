@@ -45,7 +45,7 @@ constexpr uint64_t TC_DRAIN_NS = 1000000000ull; // wait for in-flight copies and
 // (1, x, y, z, xy, yz, zz, xz, xx, yy, xxy, yyy, xyz, yzz, zzz, xzz, xxz, yyz, xxx, xyy):
 // the real orthonormal SH with the Condon-Shortley phase (the polynomials of sh_eval), so
 // that a lane can evaluate "its" coefficient k with the same instructions as every other.
-__device__ __constant__ float TC_SH[16][20] = {
+__device__ const float TC_SH[16][20] = {
     {0.28209479177387814f},
     {0, 0, -0.4886025119029199f},
     {0, 0, 0, 0.4886025119029199f},
@@ -163,9 +163,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ __align__(16) float ybuf_all[TC_NB][32];
+    __shared__ float sh_tab[16][20];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = g.stages;
     const int items = g.ntiles * g.nchunks;
+    for (int q = threadIdx.x; q < 16 * 20; q += blockDim.x) (&sh_tab[0][0])[q] = (&TC_SH[0][0])[q];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -281,7 +283,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                         ok = false;
                         break;
                     }
-                    tc::fence_after();
                     unsigned char *st = smem + (size_t)s * g.stage_bytes;
                     const uint32_t rows = tc::smem_addr(st);
                     const uint32_t A = tc::smem_addr(st + g.rows_bytes);
@@ -314,9 +315,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         // ---------------------------------------------------------- builders + epilogue
         const int b = warp - TC_B0;
         const int k = lane & 15, mh = lane >> 4;
+        // this lane's SH coefficients from the CTA's shared copy of the table (a divergent
+        // read of constant memory would serialise the lanes every time it is re-read)
         float cf[20];
 #pragma unroll
-        for (int q = 0; q < 20; ++q) cf[q] = TC_SH[k][q];
+        for (int q = 0; q < 20; ++q) cf[q] = sh_tab[k][q];
         // forward: rows of the operand are receivers (X = Y(R_i d)), columns sources (Z = Y(-d));
         // adjoint: rows are sources (X = Y(-d)), columns receivers (Z = Y(R_i d))
         const int xoff = g.adjoint ? 0 : 16, zoff = g.adjoint ? 16 : 0;
@@ -527,8 +530,10 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ __align__(16) float ybuf_all[TO_NC][32];
+    __shared__ float sh_tab[16][20];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = g.stages;
+    for (int q = threadIdx.x; q < 16 * 20; q += blockDim.x) (&sh_tab[0][0])[q] = (&TC_SH[0][0])[q];
     const int a2cols = g.Cp / 2;                 // BF16 pairs per TMEM column
     const int d2col0 = (a2cols + 15) & ~15;      // D2 slots after the A2 operand
 
@@ -667,9 +672,11 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
         const int quarter = warp & 3;            // TMEM lane quarter: sources 2 quarter, 2 quarter + 1
         const int part = cwp >> 2;               // column share of the A2 load within the quarter
         const int k = lane & 15;
+        // this lane's SH coefficients from the CTA's shared copy of the table (a divergent
+        // read of constant memory would serialise the lanes every time it is re-read)
         float cf[20];
 #pragma unroll
-        for (int q = 0; q < 20; ++q) cf[q] = TC_SH[k][q];
+        for (int q = 0; q < 20; ++q) cf[q] = sh_tab[k][q];
         float *ybuf = ybuf_all[cwp];
         long long gc = 0, use = 0;
         int tl = 0;
