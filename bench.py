@@ -62,6 +62,10 @@ WORKLOADS = {"fruit_bowl": WORKLOAD, "multi_light": MULTI_WORKLOAD, "uneven": UN
 CPU_SAMPLE = {"fruit_bowl": 6000, "multi_light": 120, "uneven": 1500, "large": 1500, "pairs": 6000, "envmap": 40}
 REF_SAMPLE = {"fruit_bowl": 1500, "multi_light": 60, "uneven": 400, "large": 400, "pairs": 1500, "envmap": 20}
 DTYPE_BATCHED = "bf16 operands, f32 accumulate; f32 correction bounce and adjoint"
+# the same form on the tensor cores (the many-column default): every contraction takes BF16
+# operands with FP32 accumulation in tensor memory; the correction bounce multiplies BF16 high
+# and low parts (three products)
+DTYPE_BATCHED_TC = "bf16 x bf16 -> f32 (tcgen05); correction bounce bf16 hi/lo x3"
 
 
 def max_over_ranks(x, dist, device):
@@ -89,6 +93,15 @@ def _peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _tensor_peak():
+    """Measured sustained dense BF16 TFLOP/s (a kernel timed inside a long step)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
 
 
 def _src_sha(name):
@@ -135,6 +148,13 @@ def _launch_bytes(kernel, sc):
         "k_adj_src_pairs": (H * 8 + 3 * A, nb),
         "k_pair_g": (H * (8 + 4) + 2 * nb * A, 1),
         "k_pair_grad": (n * 64 + (n - 1) * 64 + H * 4 + n * 8, 1),
+        # tensor-core contraction: per (tile, source) group one BF16 source row block (Cp x 32 B)
+        # and its hit records (16 B each) into shared memory; the epilogue's arrays once
+        # (bounce: S, B^(k-1) in, Q, B^(k) FP32 and two BF16 copies out; adjoint: v out, u read
+        # and written, y BF16 out; opacity: the sources' iterate in, g per hit read and written)
+        "k_tc_bounce": (sc.get("tc_groups", 0) * sc.get("Cp", 0) * 32 + H * 16 + 4 * A + 2 * A16, nb),
+        "k_tc_adjoint": (sc.get("tc_src_groups", 0) * sc.get("Cp", 0) * 32 + H * 16 + 3 * A + A16, nb),
+        "k_tc_opacity": (sc.get("tc_src_groups", 0) * sc.get("Cp", 0) * 32 + H * (16 + 4 + 8) + A, nb),
         # per 32-column tile: records, counts, offsets, directions; the iterate rows once
         "k_bounce_mc": (tiles * (H * 8 + rays * (4 + 8 + 16)) + A16 + 4 * A + A16, nb),
         # one tile and up to four iterates: records + ray data; v (FP32) and B (BF16) tiles; g per hit
@@ -492,8 +512,11 @@ def main():
             infos = []
             for sc, p in zip(scs, f.pipes):
                 info = rgs.rgs_transport_info_get(p.transport)
+                tcinfo = rgs.rgs_contraction_info(p.transport)
                 infos.append(dict(n=sc["n"], nd=sc["nd"], nb=sc["nb"], C=info["n_cols"], nc=info["nc"],
-                                  n_hits=info["n_hits"], device_bytes=info["device_bytes"]))
+                                  n_hits=info["n_hits"], device_bytes=info["device_bytes"],
+                                  Cp=(info["n_cols"] + 15) // 16 * 16, tc_groups=tcinfo["groups"],
+                                  tc_pairs=tcinfo["pairs"], tc_src_groups=tcinfo["src_groups"]))
     clk = clocks.stop()
     # accuracy of the batched form against the FP32 form (which the tests hold to 1e-4 of the oracle)
     rel_err = _rel(outs["batched"][0], outs["plain"][0], torch)
@@ -558,7 +581,8 @@ def main():
                 "k_bounce_mc": "rgs_manycol.cu", "k_opacity_g_mc": "rgs_manycol.cu", "k_adj_src_mc": "rgs_manycol.cu",
                 "k_opacity_g": "rgs_adjoint.cu", "k_opacity_rec": "rgs_adjoint.cu",
                 "k_bounce_persistent": "rgs_batch.cu", "k_trace_hemi": "rgs_trace.cu",
-                "k_pair_fill": "rgs_pairs.cu", "k_bounce_pairs": "rgs_pairs.cu", "k_pair_grad": "rgs_pairs.cu"}.get(dom)
+                "k_pair_fill": "rgs_pairs.cu", "k_bounce_pairs": "rgs_pairs.cu", "k_pair_grad": "rgs_pairs.cu",
+                "k_tc_bounce": "rgs_tc.cu", "k_tc_adjoint": "rgs_tc.cu", "k_tc_opacity": "rgs_tc.cu"}.get(dom)
     traffic = None
     if len(scs) == 1 and dom in NCU_TRAFFIC and src_file and NCU_TRAFFIC[dom]["src_sha"] == _src_sha(src_file):
         traffic = NCU_TRAFFIC[dom]["bytes_per_launch"] * (scs[0]["n"] / NCU_TRAFFIC[dom]["n"])
@@ -566,6 +590,25 @@ def main():
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "algorithmic_bytes": alg_step / launches_dom if alg_step else None,
                 "avg_launch_ms": ms_dom_step / launches_dom, "peak_source": peak_kind}
+    if dom in ("k_tc_bounce", "k_tc_adjoint", "k_tc_opacity"):
+        # a contraction on the tensor cores: algorithmic work = one 16 x 16 block per distinct
+        # (receiver, source) pair times the C columns (2 * 256 * C flops per pair), against the
+        # measured sustained BF16 peak (the kernel runs inside a multi-second step); the issued
+        # MMA work (a 128 x Cp x 16 product per group, zero blocks included) beside it
+        tf_peak, tf_kind = _tensor_peak()
+        pairs = sum(x["tc_pairs"] for x in infos)
+        groups = sum(x["tc_groups"] if dom == "k_tc_bounce" else x["tc_src_groups"] for x in infos)
+        C = infos[0]["C"]
+        Cp = infos[0]["Cp"]
+        t_launch = ms_dom_step / launches_dom * 1e-3
+        alg_flops = pairs * 2.0 * 256 * C
+        mma_flops = groups * 2.0 * 128 * Cp * 16
+        roofline = {"kernel": dom, "bound": "tensor", "achieved": alg_flops / t_launch / 1e12, "peak": tf_peak,
+                    "unit": "TFLOP/s", "frac": alg_flops / t_launch / 1e12 / tf_peak, "traffic": None,
+                    "algorithmic_flops": alg_flops, "issued_mma_tflops": mma_flops / t_launch / 1e12,
+                    "hbm_achieved_gbs": (alg_step / launches_dom / t_launch / 1e9) if alg_step else None,
+                    "hbm_frac": (alg_step / launches_dom / t_launch / 1e9 / peak) if alg_step else None,
+                    "avg_launch_ms": ms_dom_step / launches_dom, "peak_source": tf_kind}
 
     # the hemisphere trace on its own (rays per second of the live trace launches), and the
     # fraction of the step it takes
@@ -598,7 +641,8 @@ def main():
             "warmup": max(args.warmup, 3),
             "ms_per_step": sum(step_ms) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE_BATCHED if headline == "batched" else "f32", "data": "synthetic",
+            "dtype": (DTYPE_BATCHED_TC if "k_tc_bounce" in prof else DTYPE_BATCHED) if headline == "batched" else "f32",
+            "data": "synthetic",
             "config": config,
             "batched_vs_plain": {"batched": value_b, "plain": value_p, "speedup": value_b / value_p,
                                  "batched_rel_l2_vs_fp32": rel_err, "batched_grad_rel_l2_vs_fp32": grad_err,
