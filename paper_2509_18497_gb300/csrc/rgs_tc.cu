@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     __shared__ __align__(16) float ybuf_all[TC_NB][32];
     __shared__ float sh_tab[16][20];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = g.stages;
+    const int S = g.stages, SS = (S == 16) ? 4 : 3; // 16 or 8 stages
     const int items = g.ntiles * g.nchunks;
     for (int q = threadIdx.x; q < 16 * 20; q += blockDim.x) (&sh_tab[0][0])[q] = (&TC_SH[0][0])[q];
 
@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     nq.z = __shfl_sync(0xffffffffu, nrm.z, q);
                     nq.w = 0.f;
                     if (lane == 0) {
-                        const int s = (int)(gq % S);
-                        const uint32_t ph = (uint32_t)((gq / S) & 1);
+                        const int s = (int)(gq & (S - 1));
+                        const uint32_t ph = (uint32_t)((gq >> SS) & 1);
                         if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
                             tc_fail(g, &abort_flag, 16 * warp + 1, gq);
                         } else {
@@ -253,8 +253,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             for (long long q = gc - 1; q >= 0 && seen < S / TC_PROD; --q) {
                 if ((int)(q % TC_PROD) != warp) continue;
                 ++seen;
-                tc::bar_wait(&bar_rows[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
-                tc::bar_wait(&bar_hits[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
+                tc::bar_wait(&bar_rows[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
+                tc::bar_wait(&bar_hits[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
             }
         }
         __syncwarp();
@@ -275,9 +275,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 }
                 tc::fence_after();
                 const uint32_t rbytes = (uint32_t)cw * 32u;
-                for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gc) {
-                    const int s = (int)(gc % S);
-                    const uint32_t ph = (uint32_t)((gc / S) & 1);
+                for (long long q = g0; q < g1 && ok; ++q, ++gc) {
+                    const int s = (int)(gc & (S - 1));
+                    const uint32_t ph = (uint32_t)((gc >> SS) & 1);
                     if (!tc::bar_wait(&bar_afull[s], ph, g.wait_ns) || !tc::bar_wait(&bar_rows[s], ph, g.wait_ns)) {
                         tc_fail(g, &abort_flag, 16 * warp + 3, gc);
                         ok = false;
@@ -334,11 +334,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             // forward: lane p < 8 holds the item's receiver p's normal
             float4 tn = make_float4(0.f, 0.f, 1.f, 0.f);
             if (!g.adjoint && lane < TC_R && t * TC_R + lane < g.n) tn = __ldg(&g.N4[t * TC_R + lane]);
-            const long long qfirst = b < S ? g0 + (long long)((b - (int)(gc % S) + S) % S) : g1;
+            const long long qfirst = b < S ? g0 + (long long)((b - (int)(gc & (S - 1)) + S) & (S - 1)) : g1;
             for (long long q = qfirst; q < g1 && !aborted(&abort_flag); q += S) {
                 const long long gq = gc + (q - g0);
-                const int s = (int)(gq % S);
-                const uint32_t ph = (uint32_t)((gq / S) & 1);
+                const int s = (int)(gq & (S - 1));
+                const uint32_t ph = (uint32_t)((gq >> SS) & 1);
                 bool ok = true;
                 if (lane == 0) ok = tc::bar_wait(&bar_hits[s], ph, g.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
     __shared__ __align__(16) float ybuf_all[TO_NC][32];
     __shared__ float sh_tab[16][20];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = g.stages;
+    const int S = g.stages, SS = (S == 16) ? 4 : 3; // 16 or 8 stages
     for (int q = threadIdx.x; q < 16 * 20; q += blockDim.x) (&sh_tab[0][0])[q] = (&TC_SH[0][0])[q];
     const int a2cols = g.Cp / 2;                 // BF16 pairs per TMEM column
     const int d2col0 = (a2cols + 15) & ~15;      // D2 slots after the A2 operand
@@ -590,8 +590,8 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
                     nq.z = __shfl_sync(0xffffffffu, nrm.z, q);
                     nq.w = __int_as_float(first); // the group's first hit, relative to the tile
                     if (lane == 0) {
-                        const int s = (int)(gq % S);
-                        const uint32_t ph = (uint32_t)((gq / S) & 1);
+                        const int s = (int)(gq & (S - 1));
+                        const uint32_t ph = (uint32_t)((gq >> SS) & 1);
                         if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
                             to_fail(g, &abort_flag, 16 * warp + 1, gq);
                         } else {
@@ -617,8 +617,8 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
             for (long long q = gc - 1; q >= 0 && seen < S / TO_PROD; --q) {
                 if ((int)(q % TO_PROD) != warp) continue;
                 ++seen;
-                tc::bar_wait(&bar_rows[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
-                tc::bar_wait(&bar_hits[q % S], (uint32_t)((q / S) & 1), TC_DRAIN_NS);
+                tc::bar_wait(&bar_rows[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
+                tc::bar_wait(&bar_hits[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
             }
         }
         __syncwarp();
@@ -634,8 +634,8 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
                 if (!ok) to_fail(g, &abort_flag, 16 * warp + 2, gc);
                 tc::fence_after();
                 for (long long q = g0; q < g1 && ok && !aborted(&abort_flag); ++q, ++gc) {
-                    const int s = (int)(gc % S);
-                    const uint32_t ph = (uint32_t)((gc / S) & 1);
+                    const int s = (int)(gc & (S - 1));
+                    const uint32_t ph = (uint32_t)((gc >> SS) & 1);
                     const int Q = (int)(gc % TO_QUADS);
                     if (!tc::bar_wait(&bar_rows[s], ph, g.wait_ns) ||
                         (quse[Q] > 0 && !tc::bar_wait(&bar_d2empty[Q], (uint32_t)((quse[Q] - 1) & 1), g.wait_ns))) {
@@ -719,8 +719,8 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_tc_opacity(TcOpaArgs g) {
             const long long qfirst = g0 + (long long)((Q - (int)(gc % TO_QUADS) + TO_QUADS) % TO_QUADS);
             for (long long q = qfirst; q < g1 && !aborted(&abort_flag); q += TO_QUADS, ++use) {
                 const long long gq = gc + (q - g0);
-                const int s = (int)(gq % S);
-                const uint32_t ph = (uint32_t)((gq / S) & 1);
+                const int s = (int)(gq & (S - 1));
+                const uint32_t ph = (uint32_t)((gq >> SS) & 1);
                 bool ok = true;
                 if (lane == 0)
                     ok = tc::bar_wait(&bar_hits[s], ph, g.wait_ns) && tc::bar_wait(&bar_d2full[Q], (uint32_t)(use & 1), g.wait_ns);
