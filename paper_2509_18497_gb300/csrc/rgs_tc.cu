@@ -34,7 +34,9 @@ namespace {
 
 constexpr int TC_R = 8;           // receivers (or sources) per tile: 8 x 16 coefficients = M 128
 constexpr int TC_NB = 16;         // builder warps (as many as stages take part)
-constexpr int TC_THREADS = (3 + TC_NB) * 32; // two producers, the MMA warp, the builders
+constexpr int TC_THREADS = (2 + TC_NB) * 32; // the producer, the MMA warp, the builders
+constexpr int TC_GPS_MAX = 4;      // groups per pipeline stage
+constexpr int TC_CT_STAGES = 4;    // pipeline stages of the contraction
 constexpr int TC_MAX_STAGES = 16;  // one per builder
 constexpr int TC_HCAP = 20;        // hit records per group (longer (tile, source) runs are split)
 constexpr int TC_CHUNK = 512;     // columns per pass (TMEM holds 512 FP32 columns)
@@ -94,8 +96,8 @@ __device__ __forceinline__ float sh_mono(const float (&cf)[20], float3 v) {
 struct TcArgs {
     int adjoint;   // 0: forward over receiver tiles, 1: transpose over source tiles
     int split;     // 1: hi/lo operands, three MMAs per column piece
-    int n, C, Cp, nd, ntiles, nchunks, stages;
-    uint32_t stage_bytes, rows_bytes, a_bytes;
+    int n, C, Cp, nd, ntiles, nchunks, stages, stage_shift, gps;
+    uint32_t stage_bytes, rows_bytes, a_bytes; // a stage; the rows and the operand of one of its groups
     const long long *hoff; // [ntiles + 1] first hit of each tile
     const long long *goff; // [ntiles + 1] first group of each tile
     const int2 *grp;       // per group: (other entity, first hit relative to its tile)
@@ -130,6 +132,9 @@ __device__ __forceinline__ float alpha_at(int model, float o) {
 
 __device__ __forceinline__ bool aborted(const int *f) { return *(volatile const int *)f != 0; }
 
+// pipeline stages an item's groups [g0, g1) fill, gps groups each
+__device__ __forceinline__ long long stage_uses(long long g0, long long g1, int gps) { return (g1 - g0 + gps - 1) / gps; }
+
 // where = role * 16 + wait site (1 producer empty, 2 mma dempty, 3 mma afull/rows, 4 builder
 // hits, 5 builder dfull); the first failure's site and group count are kept for the message
 __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int where, long long gcount) {
@@ -141,31 +146,33 @@ __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int wh
 }
 
 // ------------------------------------------------------------------ the contraction kernel
-// Roles: warps 0 and 1 produce (even and odd groups: a stage's empty barrier is always
-// awaited by the same warp), warp 2 owns the TMEM and issues the MMAs (one lane), warps
-// 3 .. 3 + TC_NB - 1 build operands and drain the accumulator.  Group g of the CTA uses stage
-// g % S; builder b < S takes the groups g = b (mod S), i.e. every use of stage b, so every
-// use of a stage is awaited by the warp that awaited its previous use and a parity
-// wait can never see a phase two uses old.  Per stage: `hits` (the group's hit records and
-// metadata), `rows` (the source rows; awaited by the MMA only, so the S - 1 groups ahead of
-// it hide the copy's latency), `afull` (operand built), `empty` (MMAs done).
-constexpr int TC_PROD = 2;
-constexpr int TC_MMA_WARP = TC_PROD;
-constexpr int TC_B0 = TC_PROD + 1; // first builder warp
+// A stage holds GPS consecutive groups of one item (their source rows, their operands and
+// their hit records, copied with one bulk copy), so that every barrier handshake, bulk
+// hit copy and MMA commit is shared by GPS groups: the single issuing thread's per-group
+// cost, not the tensor work, bounds a pipeline of 16-column-deep (K = 16) products.
+// Roles: warp 0 produces (all bulk copies), warp 1 owns the TMEM and issues the MMAs (one
+// lane), warps 2 .. 2 + TC_NB - 1 build operands (builder b = s * GPS + j builds slot j of
+// every use of stage s, so every use of a stage is awaited by the same warps and a parity
+// wait can never see a phase two uses old) and drain the accumulator.  Per stage: `hits`
+// (records and metadata), `rows` (awaited by the MMA only), `afull` (GPS builders done),
+// `empty` (MMAs done).
+constexpr int TC_B0 = 2; // first builder warp
+struct __align__(16) SlotMeta {
+    float4 nrm; // adjoint: the group's receiver normal
+    int other, cnt, hoff, pad;
+};
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
-    // builder b takes the CTA's groups g = b (mod S), i.e. stage b: S = 16, or 8 when the
-    // stages are large (then builders 8..15 only drain the accumulator)
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_hits[TC_MAX_STAGES], bar_rows[TC_MAX_STAGES], bar_afull[TC_MAX_STAGES],
-        bar_empty[TC_MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_hits[TC_CT_STAGES], bar_rows[TC_CT_STAGES], bar_afull[TC_CT_STAGES],
+        bar_empty[TC_CT_STAGES];
     __shared__ __align__(8) uint64_t bar_dfull, bar_dempty, bar_drain;
-    __shared__ StageMeta meta[TC_MAX_STAGES];
+    __shared__ SlotMeta meta[TC_CT_STAGES][TC_GPS_MAX];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ __align__(16) float ybuf_all[TC_NB][32];
     __shared__ float sh_tab[16][20];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = g.stages, SS = (S == 16) ? 4 : 3; // 16 or 8 stages
+    const int S = g.stages, SS = g.stage_shift, GPS = g.gps;
     const int items = g.ntiles * g.nchunks;
     for (int q = threadIdx.x; q < 16 * 20; q += blockDim.x) (&sh_tab[0][0])[q] = (&TC_SH[0][0])[q];
 
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         for (int s = 0; s < S; ++s) {
             tc::bar_init(&bar_hits[s], 1);
             tc::bar_init(&bar_rows[s], 1);
-            tc::bar_init(&bar_afull[s], 1);
+            tc::bar_init(&bar_afull[s], GPS);
             tc::bar_init(&bar_empty[s], 1);
         }
         tc::bar_init(&bar_dfull, 1);
@@ -182,15 +189,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         abort_flag = 0;
         tc::bar_init_fence();
     }
-    if (warp == TC_MMA_WARP) tc::tmem_alloc(&tmem_slot, 512);
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
+    const uint32_t slot_rows = g.rows_bytes, slot_a = g.a_bytes; // per group of a stage
+    const uint32_t a_off = (uint32_t)GPS * slot_rows;            // the operands after the rows
+    const uint32_t h_off = a_off + (uint32_t)GPS * slot_a;       // then the hit records
 
-    if (warp < TC_PROD) {
-        // ---------------------------------------------------------- producers
-        long long gc = 0, issued = 0;
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        long long su = 0; // stage uses so far (stage su mod S, its use su >> SS)
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
             const int c0 = ch * TC_CHUNK;
@@ -209,101 +219,119 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     if (gb + lane + 1 < g1) next = __ldg(&g.grp[gb + lane + 1]).y;
                     if (g.adjoint) nrm = __ldg(&g.N4[e.x]);
                 }
-                for (int q = 0; q < m; ++q) {
-                    const long long gq = gc + (gb - g0) + q; // CTA-wide group index
-                    if ((int)(gq % TC_PROD) != warp) continue;
-                    const int other = __shfl_sync(0xffffffffu, e.x, q);
-                    const int first = __shfl_sync(0xffffffffu, e.y, q);
-                    const int cnt = __shfl_sync(0xffffffffu, next, q) - first;
-                    float4 nq;
-                    nq.x = __shfl_sync(0xffffffffu, nrm.x, q);
-                    nq.y = __shfl_sync(0xffffffffu, nrm.y, q);
-                    nq.z = __shfl_sync(0xffffffffu, nrm.z, q);
-                    nq.w = 0.f;
-                    if (lane == 0) {
-                        const int s = (int)(gq & (S - 1));
-                        const uint32_t ph = (uint32_t)((gq >> SS) & 1);
-                        if (!tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
-                            tc_fail(g, &abort_flag, 16 * warp + 1, gq);
-                        } else {
-                            meta[s].nrm = nq;
-                            meta[s].other = other;
-                            meta[s].cnt = cnt;
-                            unsigned char *st = smem + (size_t)s * g.stage_bytes;
-                            const uint32_t hbytes = (uint32_t)cnt * 16u;
-                            tc::bar_arrive_tx(&bar_hits[s], hbytes);
-                            tc::bulk_g2s(st + g.rows_bytes + g.a_bytes, g.hd + hb + first, hbytes, &bar_hits[s]);
-                            tc::bar_arrive_tx(&bar_rows[s], rbytes * (g.split ? 2u : 1u));
-                            const size_t rb = (size_t)other * (size_t)g.Cp * 16 + (size_t)c0 * 16;
-                            tc::bulk_g2s(st, g.rows_hi + rb, rbytes, &bar_rows[s]);
-                            if (g.split) tc::bulk_g2s(st + rbytes, g.rows_lo + rb, rbytes, &bar_rows[s]);
-                            ++issued;
-                        }
+                // the batch in stage-sized chunks (a chunk never leaves its item)
+                for (int q0 = 0; q0 < m; q0 += GPS, ++su) {
+                    const int s = (int)(su & (S - 1));
+                    const uint32_t ph = (uint32_t)((su >> SS) & 1);
+                    bool ok = true;
+                    if (lane == 0 && !tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
+                        tc_fail(g, &abort_flag, 16 * warp + 1, su);
+                        ok = false;
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) break;
+                    // lanes j < GPS describe slot j; lane 0 issues the copies
+                    const int nin = min(GPS, m - q0);
+                    const int first0 = __shfl_sync(0xffffffffu, e.y, q0);
+                    int jo = 0, jc = -1, jf = 0;
+                    float4 jn = make_float4(0.f, 0.f, 1.f, 0.f);
+                    {
+                        const int src = min(q0 + (lane < GPS ? lane : 0), 31);
+                        jo = __shfl_sync(0xffffffffu, e.x, src);
+                        jf = __shfl_sync(0xffffffffu, e.y, src);
+                        const int jn_ = __shfl_sync(0xffffffffu, next, src);
+                        jn.x = __shfl_sync(0xffffffffu, nrm.x, src);
+                        jn.y = __shfl_sync(0xffffffffu, nrm.y, src);
+                        jn.z = __shfl_sync(0xffffffffu, nrm.z, src);
+                        jc = jn_ - jf;
+                    }
+                    const int last = __shfl_sync(0xffffffffu, next, q0 + nin - 1);
+                    unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                    if (lane < GPS) {
+                        SlotMeta sm;
+                        sm.nrm = jn;
+                        sm.other = jo;
+                        sm.cnt = lane < nin ? jc : -1;
+                        sm.hoff = jf - first0;
+                        sm.pad = 0;
+                        meta[s][lane] = sm;
                     }
                     __syncwarp();
-                    if (aborted(&abort_flag)) break;
+                    if (lane == 0) {
+                        const uint32_t hbytes = (uint32_t)(last - first0) * 16u;
+                        tc::bar_arrive_tx(&bar_hits[s], hbytes);
+                        tc::bulk_g2s(st + h_off, g.hd + hb + first0, hbytes, &bar_hits[s]);
+                        tc::bar_arrive_tx(&bar_rows[s], (uint32_t)nin * rbytes * (g.split ? 2u : 1u));
+                    }
+                    if (lane < nin) { // one lane per group of the chunk issues its row copies
+                        const size_t rb = (size_t)jo * (size_t)g.Cp * 16 + (size_t)c0 * 16;
+                        unsigned char *dst = st + (size_t)lane * slot_rows;
+                        tc::bulk_g2s(dst, g.rows_hi + rb, rbytes, &bar_rows[s]);
+                        if (g.split) tc::bulk_g2s(dst + rbytes, g.rows_lo + rb, rbytes, &bar_rows[s]);
+                    }
+                    __syncwarp();
                 }
+                if (aborted(&abort_flag)) break;
             }
-            gc += g1 - g0;
         }
         // no bulk copy may still be writing into this CTA's shared memory when it exits: wait
-        // (bounded) for the last fills this warp issued
-        if (lane == 0) {
-            long long seen = 0;
-            for (long long q = gc - 1; q >= 0 && seen < S / TC_PROD; --q) {
-                if ((int)(q % TC_PROD) != warp) continue;
-                ++seen;
+        // (bounded) for the last fill of every stage
+        if (lane == 0)
+            for (long long q = su - 1; q >= 0 && q >= su - S; --q) {
                 tc::bar_wait(&bar_rows[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
                 tc::bar_wait(&bar_hits[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
             }
-        }
         __syncwarp();
-        (void)issued;
-    } else if (warp == TC_MMA_WARP) {
+    } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
-        long long gc = 0;
+        long long su = 0;
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
             const int cw = min(TC_CHUNK, g.Cp - ch * TC_CHUNK);
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            const long long nst = stage_uses(g0, g1, GPS);
             if (lane == 0) {
                 bool ok = true;
                 if (tl > 0 && !tc::bar_wait(&bar_dempty, (uint32_t)((tl - 1) & 1), g.wait_ns)) {
-                    tc_fail(g, &abort_flag, 16 * warp + 2, gc);
+                    tc_fail(g, &abort_flag, 16 * warp + 2, su);
                     ok = false;
                 }
                 tc::fence_after();
                 const uint32_t rbytes = (uint32_t)cw * 32u;
-                for (long long q = g0; q < g1 && ok; ++q, ++gc) {
-                    const int s = (int)(gc & (S - 1));
-                    const uint32_t ph = (uint32_t)((gc >> SS) & 1);
+                uint32_t acc0 = 0u;
+                for (long long k = 0; k < nst && ok; ++k, ++su) {
+                    const int s = (int)(su & (S - 1));
+                    const uint32_t ph = (uint32_t)((su >> SS) & 1);
                     if (!tc::bar_wait(&bar_afull[s], ph, g.wait_ns) || !tc::bar_wait(&bar_rows[s], ph, g.wait_ns)) {
-                        tc_fail(g, &abort_flag, 16 * warp + 3, gc);
+                        tc_fail(g, &abort_flag, 16 * warp + 3, su);
                         ok = false;
                         break;
                     }
-                    unsigned char *st = smem + (size_t)s * g.stage_bytes;
-                    const uint32_t rows = tc::smem_addr(st);
-                    const uint32_t A = tc::smem_addr(st + g.rows_bytes);
-                    const uint32_t acc0 = (q == g0) ? 0u : 1u;
-                    for (int c = 0; c < cw; c += 256) {
-                        const int N = min(256, cw - c);
-                        const uint32_t id = tc::idesc_bf16(128, N);
-                        const uint32_t d = tmem + (uint32_t)c;
-                        const uint64_t da = tc::sdesc(A), db = tc::sdesc(rows + (uint32_t)c * 32u);
-                        tc::mma_bf16(d, da, db, id, acc0);
-                        if (g.split) {
-                            tc::mma_bf16(d, da, tc::sdesc(rows + rbytes + (uint32_t)c * 32u), id, 1u);
-                            tc::mma_bf16(d, tc::sdesc(A + 4096u), db, id, 1u);
+                    const uint32_t st = tc::smem_addr(smem + (size_t)s * g.stage_bytes);
+                    const int nin = (int)min((long long)GPS, (g1 - g0) - k * GPS);
+                    for (int j = 0; j < nin; ++j) {
+                        const uint32_t rows = st + (uint32_t)j * slot_rows;
+                        const uint32_t A = st + a_off + (uint32_t)j * slot_a;
+                        for (int c = 0; c < cw; c += 256) {
+                            const int N = min(256, cw - c);
+                            const uint32_t id = tc::idesc_bf16(128, N);
+                            const uint32_t d = tmem + (uint32_t)c;
+                            const uint64_t da = tc::sdesc(A), db = tc::sdesc(rows + (uint32_t)c * 32u);
+                            tc::mma_bf16(d, da, db, id, acc0);
+                            if (g.split) {
+                                tc::mma_bf16(d, da, tc::sdesc(rows + rbytes + (uint32_t)c * 32u), id, 1u);
+                                tc::mma_bf16(d, tc::sdesc(A + 4096u), db, id, 1u);
+                            }
                         }
+                        acc0 = 1u;
                     }
                     tc::mma_commit(&bar_empty[s]);
                 }
                 tc::mma_commit(&bar_dfull); // after a failure the other roles give up on their own waits
             }
             __syncwarp();
-            gc = __shfl_sync(0xffffffffu, gc, 0);
+            su = __shfl_sync(0xffffffffu, su, 0);
         }
         // every MMA this thread issued has completed before the TMEM is freed
         if (lane == 0) {
@@ -314,6 +342,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     } else {
         // ---------------------------------------------------------- builders + epilogue
         const int b = warp - TC_B0;
+        const int bs = b / GPS, bj = b - bs * GPS; // the stage and slot this warp builds
         const int k = lane & 15, mh = lane >> 4;
         // this lane's SH coefficients from the CTA's shared copy of the table (a divergent
         // read of constant memory would serialise the lanes every time it is re-read)
@@ -324,102 +353,106 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         // adjoint: rows are sources (X = Y(-d)), columns receivers (Z = Y(R_i d))
         const int xoff = g.adjoint ? 0 : 16, zoff = g.adjoint ? 16 : 0;
         float *ybuf = ybuf_all[b];
-        long long gc = 0; // CTA-wide group counter
+        long long su = 0;
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
             const int c0 = ch * TC_CHUNK;
             const int cw = min(TC_CHUNK, g.Cp - c0);
             const long long g0 = g.goff[t], g1 = g.goff[t + 1];
+            const long long nst = stage_uses(g0, g1, GPS);
             // forward: lane p < 8 holds the item's receiver p's normal
             float4 tn = make_float4(0.f, 0.f, 1.f, 0.f);
             if (!g.adjoint && lane < TC_R && t * TC_R + lane < g.n) tn = __ldg(&g.N4[t * TC_R + lane]);
-            const long long qfirst = b < S ? g0 + (long long)((b - (int)(gc & (S - 1)) + S) & (S - 1)) : g1;
-            for (long long q = qfirst; q < g1 && !aborted(&abort_flag); q += S) {
-                const long long gq = gc + (q - g0);
-                const int s = (int)(gq & (S - 1));
-                const uint32_t ph = (uint32_t)((gq >> SS) & 1);
+            // this warp's uses: those of stage bs among the item's stage uses su .. su + nst - 1
+            const long long k0 = (long long)((bs - (int)(su & (S - 1)) + S) & (S - 1));
+            for (long long kk = k0; bs < S && kk < nst && !aborted(&abort_flag); kk += S) {
+                const long long u = su + kk;
+                const int s = bs;
+                const uint32_t ph = (uint32_t)((u >> SS) & 1);
                 bool ok = true;
                 if (lane == 0) ok = tc::bar_wait(&bar_hits[s], ph, g.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 __syncwarp(); // lane 0's acquire of the stage covers the warp's reads of it
                 if (!ok) {
-                    if (lane == 0) tc_fail(g, &abort_flag, 16 * warp + 4, gq);
+                    if (lane == 0) tc_fail(g, &abort_flag, 16 * warp + 4, u);
                     break;
                 }
-                const int cnt = meta[s].cnt;
-                const float3 ngrp = f3(meta[s].nrm);
-                unsigned char *st = smem + (size_t)s * g.stage_bytes;
-                const uint32_t A = tc::smem_addr(st + g.rows_bytes);
-                const float4 *hits = reinterpret_cast<const float4 *>(st + g.rows_bytes + g.a_bytes);
-                float acc[8];
+                const SlotMeta mt = meta[s][bj];
+                if (mt.cnt >= 0) {
+                    unsigned char *st = smem + (size_t)s * g.stage_bytes;
+                    const uint32_t A = tc::smem_addr(st + a_off + (size_t)bj * slot_a);
+                    const float4 *hits = reinterpret_cast<const float4 *>(st + h_off) + mt.hoff;
+                    const float3 ngrp = f3(mt.nrm);
+                    float acc[8];
 #pragma unroll
-                for (int m = 0; m < 8; ++m) acc[m] = 0.f;
-                int cur = -1;
-                unsigned written = 0;
-                auto flush = [&](int p) {
-                    const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
-                    uint4 hi;
-                    hi.x = tc::pack_bf16(acc[0], acc[1]);
-                    hi.y = tc::pack_bf16(acc[2], acc[3]);
-                    hi.z = tc::pack_bf16(acc[4], acc[5]);
-                    hi.w = tc::pack_bf16(acc[6], acc[7]);
-                    tc::sts128(A + off, hi);
-                    if (g.split) {
-                        float r[8];
+                    for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                    int cur = -1;
+                    unsigned written = 0;
+                    auto flush = [&](int p) {
+                        const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
+                        uint4 hi;
+                        hi.x = tc::pack_bf16(acc[0], acc[1]);
+                        hi.y = tc::pack_bf16(acc[2], acc[3]);
+                        hi.z = tc::pack_bf16(acc[4], acc[5]);
+                        hi.w = tc::pack_bf16(acc[6], acc[7]);
+                        tc::sts128(A + off, hi);
+                        if (g.split) {
+                            float r[8];
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) r[m] = acc[m] - __bfloat162float(__float2bfloat16_rn(acc[m]));
-                        uint4 lo;
-                        lo.x = tc::pack_bf16(r[0], r[1]);
-                        lo.y = tc::pack_bf16(r[2], r[3]);
-                        lo.z = tc::pack_bf16(r[4], r[5]);
-                        lo.w = tc::pack_bf16(r[6], r[7]);
-                        tc::sts128(A + 4096u + off, lo);
+                            for (int m = 0; m < 8; ++m) r[m] = acc[m] - __bfloat162float(__float2bfloat16_rn(acc[m]));
+                            uint4 lo;
+                            lo.x = tc::pack_bf16(r[0], r[1]);
+                            lo.y = tc::pack_bf16(r[2], r[3]);
+                            lo.z = tc::pack_bf16(r[4], r[5]);
+                            lo.w = tc::pack_bf16(r[6], r[7]);
+                            tc::sts128(A + 4096u + off, lo);
+                        }
+                        written |= 1u << p;
+                    };
+                    for (int e = 0; e < mt.cnt; ++e) {
+                        const float4 rec = hits[e]; // broadcast read
+                        const uint32_t abits = __float_as_uint(rec.w);
+                        const int p = (int)(abits & 7u);
+                        const float a = __uint_as_float(abits & ~7u);
+                        const float3 d = make_float3(rec.x, rec.y, rec.z);
+                        float3 nrm = ngrp;
+                        if (!g.adjoint)
+                            nrm = make_float3(__shfl_sync(0xffffffffu, tn.x, p), __shfl_sync(0xffffffffu, tn.y, p),
+                                              __shfl_sync(0xffffffffu, tn.z, p));
+                        // lanes 0..15: Y_k(-d); lanes 16..31: Y_k(R d)
+                        const float3 v = (lane < 16) ? make_float3(-d.x, -d.y, -d.z) : reflect_n(nrm, d);
+                        ybuf[lane] = sh_mono(cf, v);
+                        __syncwarp();
+                        const float X = ybuf[xoff + k];
+                        const float4 z0 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8);
+                        const float4 z1 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8 + 4);
+                        const float Z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+                        __syncwarp();
+                        if (p != cur) {
+                            if (cur >= 0) flush(cur);
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                            cur = p;
+                        }
+                        const float ax = a * X;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) acc[m] = fmaf(ax, Z[m], acc[m]);
                     }
-                    written |= 1u << p;
-                };
-                for (int e = 0; e < cnt; ++e) {
-                    const float4 rec = hits[e]; // broadcast read
-                    const uint32_t abits = __float_as_uint(rec.w);
-                    const int p = (int)(abits & 7u);
-                    const float a = __uint_as_float(abits & ~7u);
-                    const float3 d = make_float3(rec.x, rec.y, rec.z);
-                    float3 nrm = ngrp;
-                    if (!g.adjoint)
-                        nrm = make_float3(__shfl_sync(0xffffffffu, tn.x, p), __shfl_sync(0xffffffffu, tn.y, p),
-                                          __shfl_sync(0xffffffffu, tn.z, p));
-                    // lanes 0..15: Y_k(-d); lanes 16..31: Y_k(R d)
-                    const float3 v = (lane < 16) ? make_float3(-d.x, -d.y, -d.z) : reflect_n(nrm, d);
-                    ybuf[lane] = sh_mono(cf, v);
-                    __syncwarp();
-                    const float X = ybuf[xoff + k];
-                    const float4 z0 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8);
-                    const float4 z1 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8 + 4);
-                    const float Z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-                    __syncwarp();
-                    if (p != cur) {
-                        if (cur >= 0) flush(cur);
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) acc[m] = 0.f;
-                        cur = p;
+                    if (cur >= 0) flush(cur);
+                    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+                    for (int p = 0; p < TC_R; ++p) {
+                        if (written & (1u << p)) continue;
+                        const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
+                        tc::sts128(A + off, z4);
+                        if (g.split) tc::sts128(A + 4096u + off, z4);
                     }
-                    const float ax = a * X;
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) acc[m] = fmaf(ax, Z[m], acc[m]);
+                    tc::fence_async_smem();
                 }
-                if (cur >= 0) flush(cur);
-                const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-                for (int p = 0; p < TC_R; ++p) {
-                    if (written & (1u << p)) continue;
-                    const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
-                    tc::sts128(A + off, z4);
-                    if (g.split) tc::sts128(A + 4096u + off, z4);
-                }
-                tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::bar_arrive(&bar_afull[s]);
             }
-            gc += g1 - g0;
+            su += nst;
             if (aborted(&abort_flag)) break;
             // ------------------------------------------------------ epilogue of the item
             bool ok = true;
@@ -428,7 +461,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
             __syncwarp();
             tc::fence_after();
             if (!ok) {
-                if (lane == 0) tc_fail(g, &abort_flag, 16 * warp + 5, gc);
+                if (lane == 0) tc_fail(g, &abort_flag, 16 * warp + 5, su);
                 break;
             }
             const bool empty = (g1 == g0);
@@ -481,7 +514,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == TC_MMA_WARP) tc::tmem_dealloc(tmem, 512);
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------------ opacity gather (adjoint)
@@ -1166,7 +1199,6 @@ rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
     a.nchunks = (a.Cp + TC_CHUNK - 1) / TC_CHUNK;
     a.rows_bytes = (uint32_t)cw * 32u * (a.split ? 2u : 1u);
     a.a_bytes = 4096u * (a.split ? 2u : 1u);
-    a.stage_bytes = (a.rows_bytes + a.a_bytes + TC_HCAP * 16u + 127u) & ~127u;
     // the dynamic shared memory a CTA may opt into, less the kernel's static barriers and buffers
     if (!g_smem_budget) {
         int dev = 0, optin = 0;
@@ -1177,10 +1209,19 @@ rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
         g_smem_budget = (uint32_t)(optin - (int)fa.sharedSizeBytes - 256);
     }
     const uint32_t budget = g_smem_budget;
-    // one stage per active builder: 16, or 8 when 16 do not fit
-    a.stages = (16u * a.stage_bytes <= budget) ? 16 : 8;
-    if ((uint32_t)a.stages * a.stage_bytes > budget) {
-        rgs_set_error("tensor-core contraction: %d stages of %u bytes exceed shared memory", a.stages, a.stage_bytes);
+    // four stages of as many groups as fit (up to four: the builder warps are stages x groups)
+    a.stages = TC_CT_STAGES;
+    a.stage_shift = 2;
+    a.gps = 0;
+    for (int gps = TC_GPS_MAX; gps >= 1 && !a.gps; gps /= 2) {
+        const uint32_t sb = ((uint32_t)gps * (a.rows_bytes + a.a_bytes + TC_HCAP * 16u) + 127u) & ~127u;
+        if ((uint32_t)a.stages * sb <= budget) {
+            a.gps = gps;
+            a.stage_bytes = sb;
+        }
+    }
+    if (!a.gps) {
+        rgs_set_error("tensor-core contraction: a stage of %u-byte rows exceeds shared memory", a.rows_bytes);
         return RGS_ERR_ARG;
     }
     const size_t smem = std::max<size_t>((size_t)a.stages * a.stage_bytes, 120u * 1024u);
