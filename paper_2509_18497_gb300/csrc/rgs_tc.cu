@@ -384,68 +384,94 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                     const uint32_t A = tc::smem_addr(st + a_off + (size_t)bj * slot_a);
                     const float4 *hits = reinterpret_cast<const float4 *>(st + h_off) + mt.hoff;
                     const float3 ngrp = f3(mt.nrm);
-                    float acc[8];
+                    // half-warp hf takes the group's hits whose tile slot p has parity hf, so the
+                    // halves never share a row; lane k of a half forms row (p, k): sum over its hits
+                    // of a X_k Z^T, X = Y(R d) (forward) or Y(-d) (adjoint), Z the other one
+                    const int hf = lane >> 4;
+                    float acc[16];
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                    for (int m = 0; m < 16; ++m) acc[m] = 0.f;
                     int cur = -1;
                     unsigned written = 0;
                     auto flush = [&](int p) {
-                        const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
-                        uint4 hi;
-                        hi.x = tc::pack_bf16(acc[0], acc[1]);
-                        hi.y = tc::pack_bf16(acc[2], acc[3]);
-                        hi.z = tc::pack_bf16(acc[4], acc[5]);
-                        hi.w = tc::pack_bf16(acc[6], acc[7]);
-                        tc::sts128(A + off, hi);
+                        uint4 h0, h1;
+                        h0.x = tc::pack_bf16(acc[0], acc[1]);
+                        h0.y = tc::pack_bf16(acc[2], acc[3]);
+                        h0.z = tc::pack_bf16(acc[4], acc[5]);
+                        h0.w = tc::pack_bf16(acc[6], acc[7]);
+                        h1.x = tc::pack_bf16(acc[8], acc[9]);
+                        h1.y = tc::pack_bf16(acc[10], acc[11]);
+                        h1.z = tc::pack_bf16(acc[12], acc[13]);
+                        h1.w = tc::pack_bf16(acc[14], acc[15]);
+                        const uint32_t off = tc::blk_off(p * 16 + k, 0);
+                        tc::sts128(A + off, h0);
+                        tc::sts128(A + off + 128u, h1);
                         if (g.split) {
-                            float r[8];
+                            float r[16];
 #pragma unroll
-                            for (int m = 0; m < 8; ++m) r[m] = acc[m] - __bfloat162float(__float2bfloat16_rn(acc[m]));
-                            uint4 lo;
-                            lo.x = tc::pack_bf16(r[0], r[1]);
-                            lo.y = tc::pack_bf16(r[2], r[3]);
-                            lo.z = tc::pack_bf16(r[4], r[5]);
-                            lo.w = tc::pack_bf16(r[6], r[7]);
-                            tc::sts128(A + 4096u + off, lo);
+                            for (int m = 0; m < 16; ++m) r[m] = acc[m] - __bfloat162float(__float2bfloat16_rn(acc[m]));
+                            uint4 l0, l1;
+                            l0.x = tc::pack_bf16(r[0], r[1]);
+                            l0.y = tc::pack_bf16(r[2], r[3]);
+                            l0.z = tc::pack_bf16(r[4], r[5]);
+                            l0.w = tc::pack_bf16(r[6], r[7]);
+                            l1.x = tc::pack_bf16(r[8], r[9]);
+                            l1.y = tc::pack_bf16(r[10], r[11]);
+                            l1.z = tc::pack_bf16(r[12], r[13]);
+                            l1.w = tc::pack_bf16(r[14], r[15]);
+                            tc::sts128(A + 4096u + off, l0);
+                            tc::sts128(A + 4096u + off + 128u, l1);
                         }
                         written |= 1u << p;
                     };
-                    for (int e = 0; e < mt.cnt; ++e) {
-                        const float4 rec = hits[e]; // broadcast read
-                        const uint32_t abits = __float_as_uint(rec.w);
-                        const int p = (int)(abits & 7u);
-                        const float a = __uint_as_float(abits & ~7u);
-                        const float3 d = make_float3(rec.x, rec.y, rec.z);
-                        float3 nrm = ngrp;
-                        if (!g.adjoint)
-                            nrm = make_float3(__shfl_sync(0xffffffffu, tn.x, p), __shfl_sync(0xffffffffu, tn.y, p),
-                                              __shfl_sync(0xffffffffu, tn.z, p));
-                        // lanes 0..15: Y_k(-d); lanes 16..31: Y_k(R d)
-                        const float3 v = (lane < 16) ? make_float3(-d.x, -d.y, -d.z) : reflect_n(nrm, d);
-                        ybuf[lane] = sh_mono(cf, v);
-                        __syncwarp();
-                        const float X = ybuf[xoff + k];
-                        const float4 z0 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8);
-                        const float4 z1 = *reinterpret_cast<const float4 *>(ybuf + zoff + mh * 8 + 4);
-                        const float Z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-                        __syncwarp();
-                        if (p != cur) {
-                            if (cur >= 0) flush(cur);
+                    // the slots' parities, 32 hits at a time: lane e holds hit e's parity bit
+                    for (int base = 0; base < mt.cnt; base += 32) {
+                        const int m_here = min(32, mt.cnt - base);
+                        const bool odd = lane < m_here && (__float_as_uint(hits[base + lane].w) & 1u);
+                        const unsigned odd_m = __ballot_sync(0xffffffffu, odd);
+                        const unsigned all_m = m_here == 32 ? 0xffffffffu : ((1u << m_here) - 1u);
+                        unsigned mine = hf ? odd_m : (all_m & ~odd_m); // this half's hits in the window
+                        const int n_mine = __popc(mine);
+                        const int n_iter = max(__popc(odd_m), __popc(all_m & ~odd_m));
+                        for (int it2 = 0; it2 < n_iter; ++it2) {
+                            const bool have = it2 < n_mine;
+                            const int e = have ? __ffs(mine) - 1 : 0;
+                            if (have) mine &= mine - 1;
+                            const float4 rec = hits[base + e];
+                            const uint32_t abits = __float_as_uint(rec.w);
+                            const int p = (int)(abits & 7u);
+                            const float a = have ? __uint_as_float(abits & ~7u) : 0.f;
+                            const float3 d = make_float3(rec.x, rec.y, rec.z);
+                            float3 nrm = ngrp;
+                            if (!g.adjoint)
+                                nrm = make_float3(__shfl_sync(0xffffffffu, tn.x, p), __shfl_sync(0xffffffffu, tn.y, p),
+                                                  __shfl_sync(0xffffffffu, tn.z, p));
+                            const float3 rd = reflect_n(nrm, d), md = make_float3(-d.x, -d.y, -d.z);
+                            const float X = sh_mono(cf, g.adjoint ? md : rd);
+                            float Z[16];
+                            sh_eval<16>(g.adjoint ? rd : md, Z);
+                            if (have && p != cur) {
+                                if (cur >= 0) flush(cur);
 #pragma unroll
-                            for (int m = 0; m < 8; ++m) acc[m] = 0.f;
-                            cur = p;
+                                for (int m = 0; m < 16; ++m) acc[m] = 0.f;
+                                cur = p;
+                            }
+                            const float ax = a * X;
+#pragma unroll
+                            for (int m = 0; m < 16; ++m) acc[m] = fmaf(ax, Z[m], acc[m]);
                         }
-                        const float ax = a * X;
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) acc[m] = fmaf(ax, Z[m], acc[m]);
                     }
                     if (cur >= 0) flush(cur);
                     const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-                    for (int p = 0; p < TC_R; ++p) {
+                    for (int p = hf; p < TC_R; p += 2) { // this half's unwritten rows
                         if (written & (1u << p)) continue;
-                        const uint32_t off = tc::blk_off(p * 16 + k, mh * 8);
+                        const uint32_t off = tc::blk_off(p * 16 + k, 0);
                         tc::sts128(A + off, z4);
-                        if (g.split) tc::sts128(A + 4096u + off, z4);
+                        tc::sts128(A + off + 128u, z4);
+                        if (g.split) {
+                            tc::sts128(A + 4096u + off, z4);
+                            tc::sts128(A + 4096u + off + 128u, z4);
+                        }
                     }
                     tc::fence_async_smem();
                 }
