@@ -169,7 +169,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     __shared__ SlotMeta meta[TC_CT_STAGES][TC_GPS_MAX];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ __align__(16) float ybuf_all[TC_NB][32];
     __shared__ float sh_tab[16][20];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = g.stages, SS = g.stage_shift, GPS = g.gps;
@@ -343,16 +342,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         // ---------------------------------------------------------- builders + epilogue
         const int b = warp - TC_B0;
         const int bs = b / GPS, bj = b - bs * GPS; // the stage and slot this warp builds
-        const int k = lane & 15, mh = lane >> 4;
+        const int k = lane & 15;
         // this lane's SH coefficients from the CTA's shared copy of the table (a divergent
         // read of constant memory would serialise the lanes every time it is re-read)
         float cf[20];
 #pragma unroll
         for (int q = 0; q < 20; ++q) cf[q] = sh_tab[k][q];
-        // forward: rows of the operand are receivers (X = Y(R_i d)), columns sources (Z = Y(-d));
-        // adjoint: rows are sources (X = Y(-d)), columns receivers (Z = Y(R_i d))
-        const int xoff = g.adjoint ? 0 : 16, zoff = g.adjoint ? 16 : 0;
-        float *ybuf = ybuf_all[b];
         long long su = 0;
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
