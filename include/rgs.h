@@ -348,7 +348,11 @@ rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
  *               buffers fit in free device memory, else the row-gather kernels;
  *   mode =  0 : always the row-gather kernels;
  *   mode =  1 : the tensor-core form whenever it applies (any C; still not for checkpointed
- *               solves, SH degree < 3, more than 2^20 surfels or 512 rays per surfel).
+ *               solves, SH degree < 3, more than 2^20 surfels or 512 rays per surfel);
+ *   mode =  2 : as 1, and the adjoint's opacity gather on the tensor cores too (per (source
+ *               tile, receiver) group C / 16 products of 128 x 16 x 16 against the tile's
+ *               sources' rows held in tensor memory; C <= 768).  It is correct but measured
+ *               slower than the row-gather opacity kernels, which modes -1 and 1 keep.
  * The tensor-core form regroups the hit records once per trace into tiles of 8 consecutive
  * receivers, and per tile into the sources they see; per (tile, source) it forms the 8
  * receivers' 16 x 16 transport blocks G_ij = sum_{r,h: j_h = j} a_rh Y(R_i d_r) Y(-d_r)^T as a
@@ -358,7 +362,7 @@ rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
  * parts (three products, FP32-level accuracy).  rgs_adjoint then runs the transposed bounces
  * the same way over tiles of 8 sources (y = o c (x) v rounded to BF16), with FP32 outputs.
  * Extra device memory: about 40 bytes per stored hit and three BF16 copies of an iterate.
- * Host-only.  Errors: RGS_ERR_ARG (NULL transport, mode outside [-1, 1]). */
+ * Host-only.  Errors: RGS_ERR_ARG (NULL transport, mode outside [-1, 2]). */
 rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode);
 
 /* Sizes of the tensor-core contraction's pair tiles for t (built by the first solve or

@@ -591,7 +591,9 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
         rgs_status q;
         if (tcp) { // tensor cores over source tiles: y^(a-1) = o c (x) v^(a-1) in BF16 row blocks
             // the opacity gather pairs y^(a) with B^(n-1-a) while y^(a) is at hand
-            const bool gh = (dopo || geo) && nb >= 1;
+            // (on the tensor cores only in mode 2: at 16 columns per MMA and C / 16 products per
+            // (tile, receiver) group it measured slower than the row gathers below)
+            const bool gh = (dopo || geo) && nb >= 1 && t->tc_mode == 2;
             if (a == 1) {
                 if ((q = rgs_tc_make_y(t, vp(0), 0, st)) != RGS_OK) return q;
                 if (gh && (q = rgs_tc_opacity(t, 0, t->iters + A * (nb - 1), true, st)) != RGS_OK) return q;
@@ -673,7 +675,7 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
             { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, vp(a), Qb[b - lo], t->Pg); }
             RGS_LAUNCH("pair accum");
         }
-        if ((dopo || geo) && !tcp) { // g_h over this segment's iterates, four per launch
+        if ((dopo || geo) && !(tcp && t->tc_mode == 2)) { // g_h over this segment's iterates, four per launch
             for (int b0 = hi; b0 >= lo; b0 -= 4) {
                 const int na = min(4, b0 - lo + 1);
                 const float *vv[4], *bb[4];

@@ -34,7 +34,8 @@ namespace {
 
 constexpr int TC_R = 8;           // receivers (or sources) per tile: 8 x 16 coefficients = M 128
 constexpr int TC_NB = 16;         // builder warps (as many as stages take part)
-constexpr int TC_THREADS = (2 + TC_NB) * 32; // the producer, the MMA warp, the builders
+constexpr int TC_NP = 2;           // producer warps (each owns every TC_NP-th stage)
+constexpr int TC_THREADS = (TC_NP + 1 + TC_NB) * 32; // producers, the MMA warp, the builders
 constexpr int TC_GPS_MAX = 4;      // groups per pipeline stage
 constexpr int TC_CT_STAGES = 4;    // pipeline stages of the contraction
 constexpr int TC_MAX_STAGES = 16;  // one per builder
@@ -150,13 +151,15 @@ __device__ __forceinline__ void tc_fail(const TcArgs &g, int *abort_flag, int wh
 // their hit records, copied with one bulk copy), so that every barrier handshake, bulk
 // hit copy and MMA commit is shared by GPS groups: the single issuing thread's per-group
 // cost, not the tensor work, bounds a pipeline of 16-column-deep (K = 16) products.
-// Roles: warp 0 produces (all bulk copies), warp 1 owns the TMEM and issues the MMAs (one
-// lane), warps 2 .. 2 + TC_NB - 1 build operands (builder b = s * GPS + j builds slot j of
+// Roles: warps 0 .. TC_NP - 1 produce (all bulk copies; stage s belongs to warp s mod TC_NP:
+// a copy's issue costs its thread a few hundred cycles), warp TC_NP owns the TMEM and issues
+// the MMAs (one lane), the next TC_NB warps build operands (builder b = s * GPS + j builds slot j of
 // every use of stage s, so every use of a stage is awaited by the same warps and a parity
 // wait can never see a phase two uses old) and drain the accumulator.  Per stage: `hits`
 // (records and metadata), `rows` (awaited by the MMA only), `afull` (GPS builders done),
 // `empty` (MMAs done).
-constexpr int TC_B0 = 2; // first builder warp
+constexpr int TC_MW = TC_NP;     // the MMA warp
+constexpr int TC_B0 = TC_NP + 1; // first builder warp
 struct __align__(16) SlotMeta {
     float4 nrm; // adjoint: the group's receiver normal
     int other, cnt, hoff, pad;
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         abort_flag = 0;
         tc::bar_init_fence();
     }
-    if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
+    if (warp == TC_MW) tc::tmem_alloc(&tmem_slot, 512);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -197,8 +200,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     const uint32_t a_off = (uint32_t)GPS * slot_rows;            // the operands after the rows
     const uint32_t h_off = a_off + (uint32_t)GPS * slot_a;       // then the hit records
 
-    if (warp == 0) {
-        // ---------------------------------------------------------- producer
+    if (warp < TC_NP) {
+        // ---------------------------------------------------------- producers (stage s: warp s mod TC_NP)
         long long su = 0; // stage uses so far (stage su mod S, its use su >> SS)
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x) {
             const int t = it / g.nchunks, ch = it - t * g.nchunks;
@@ -221,6 +224,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                 // the batch in stage-sized chunks (a chunk never leaves its item)
                 for (int q0 = 0; q0 < m; q0 += GPS, ++su) {
                     const int s = (int)(su & (S - 1));
+                    if (s % TC_NP != warp) continue; // another producer's stage
                     const uint32_t ph = (uint32_t)((su >> SS) & 1);
                     bool ok = true;
                     if (lane == 0 && !tc::bar_wait(&bar_empty[s], ph ^ 1u, g.wait_ns)) {
@@ -277,11 +281,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         // (bounded) for the last fill of every stage
         if (lane == 0)
             for (long long q = su - 1; q >= 0 && q >= su - S; --q) {
+                if ((int)(q & (S - 1)) % TC_NP != warp) continue;
                 tc::bar_wait(&bar_rows[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
                 tc::bar_wait(&bar_hits[q & (S - 1)], (uint32_t)((q >> SS) & 1), TC_DRAIN_NS);
             }
         __syncwarp();
-    } else if (warp == 1) {
+    } else if (warp == TC_MW) {
         // ---------------------------------------------------------- MMA issuer
         long long su = 0;
         int tl = 0;
@@ -535,7 +540,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+    if (warp == TC_MW) tc::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------------ opacity gather (adjoint)
@@ -1296,6 +1301,7 @@ bool rgs_tc_eligible(const rgs_transport *t, int precision) {
     if (t->kind != RGS_KIND_HEMISPHERE || t->nc != 16 || precision == RGS_FP32) return false;
     if (t->n > (1 << 20) || t->nd > 512 || t->n_hits <= 0 || t->n_slots >= (1ll << 32)) return false;
     if (t->tc_mode < 0 && t->C < RGS_TC_MIN_COLS) return false; // automatic: many right-hand sides only
+    if (2 * ((t->C + 15) / 16) * 8 + 64 > 512 && t->tc_mode == 2) return false; // opacity operand in TMEM
     if (t->stride != 0) return false; // the adjoint reads every iterate of this path
     // memory: two structures of 16-20 B per hit, three blocked BF16 arrays, sort scratch of 24 B per hit
     const double need = 2.0 * 20.0 * t->n_hits + 24.0 * t->n_hits + 3.0 * 2.0 * t->n * (double)((t->C + 15) & ~15) * 16;

@@ -371,7 +371,8 @@ def rgs_set_memory_budget(transport, nbytes):
 
 def rgs_set_tensor_cores(transport, mode):
     """Contraction of the batched modes: -1 automatic (tensor cores from 96 columns), 0 the
-    row-gather kernels, 1 the tensor-core form wherever it applies."""
+    row-gather kernels, 1 the tensor-core form wherever it applies, 2 as 1 with the adjoint's
+    opacity gather on the tensor cores too."""
     _check(load().rgs_set_tensor_cores(transport.h, int(mode)))
 
 

@@ -35,10 +35,10 @@ def _lib():
     build.build()
 
 
-def _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GAUSS):
+def _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GAUSS, mode=TC):
     errs = {}
     for prec, tol in ((rgs.RGS_BF16_FP32ACC, TOL_BF16), (rgs.RGS_BF16_FP32ACC_RESCORR, TOL_RESCORR)):
-        g = run_gpu(sc, W=W, precision=prec, tensor_cores=TC, stats=True, alpha_model=alpha_model)
+        g = run_gpu(sc, W=W, precision=prec, tensor_cores=mode, stats=True, alpha_model=alpha_model)
         errs[prec] = rel_l2(g["B"], o["B"])
         assert errs[prec] <= tol, (prec, errs[prec])
         for key in ("dE", "dad", "dop"):
@@ -52,18 +52,21 @@ def _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GAUSS):
 
 @pytest.mark.parametrize("n_lights", [1, 20])
 def test_tensor_cores_against_oracle(n_lights):
+    """Mode 1 (bounces and transposed bounces on the tensor cores) and mode 2 (the opacity
+    gather too)."""
     sc = scenes.with_emission(scenes.fruit_bowl(n=2997, L=3, nd=64, nb=3, n_lights=n_lights), seed=4)
     C = 3 * n_lights
     W = np.random.default_rng(9).normal(size=(sc["n"], 16, C))
     o = run_oracle(sc, W=W)
-    _check(sc, W, o)
+    _check(sc, W, o, mode=1)
+    _check(sc, W, o, mode=2)
 
 
 def test_tensor_cores_gfsgs():
     sc = scenes.with_emission(scenes.fruit_bowl(n=1501, L=3, nd=64, nb=2, n_lights=3), seed=6)
     W = np.random.default_rng(2).normal(size=(sc["n"], 16, 9))
     o = run_oracle(sc, W=W, alpha_model=O.ALPHA_GFSGS)
-    _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GFSGS)
+    _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GFSGS, mode=2)
 
 
 def test_tensor_cores_match_row_gathers():
@@ -110,7 +113,8 @@ def hundred():
 
 def test_hundred_lights_tensor_cores_full_oracle(hundred):
     sc, W, o = hundred
-    _check(sc, W, o)
+    _check(sc, W, o, mode=1)
+    _check(sc, W, o, mode=2)
 
 
 def test_hundred_lights_fp32_and_row_gathers_full_oracle(hundred):
