@@ -383,6 +383,34 @@ rgs_status rgs_contraction_info(const rgs_transport *t, int64_t *out, int32_t n)
  * Host-only.  Errors: RGS_ERR_ARG (NULL transport, negative limit). */
 rgs_status rgs_set_wait_limit(rgs_transport *t, int64_t ns);
 
+/* Image formation, Eq. L_I for the rays of a pinhole camera (what the paper draws with its
+ * tile rasterizer from the surfels' outgoing radiance, Sec. 5.3): each pixel's ray
+ * o + t d meets the surfels of t's scene in depth order under the transport's hit rules
+ * (the eps_plane plane test, the Gaussian's cutoff, runs of near-equal depth ordered by caller
+ * index; no surfel excluded), composited with a_h = alpha_h prod_{k<h} (1 - alpha_k) until the
+ * transmittance falls below 1e-6 (at most 96 nearest hits), and
+ *     img[y][x][c] = sum_h a_h Y(-d)^T B_{j_h}[:, c].
+ * cam: HOST float[9] = {o[3], forward[3], up[3]}; right = forward x up (normalised), the true
+ * up = right x forward; fov is the vertical field of view in radians (0, pi); pixel (x, y),
+ * y pointing down, is sampled at its centre.  B: device float [N][nc][C] in caller order (the
+ * layout rgs_solve writes); img: device float [H][W][C], fully written.  Device buffers are
+ * the caller's; pooled scratch (about 800 bytes per pixel) is returned before the call ends.
+ * Synchronises `stream` once (the traversal's overflow check).  Errors: RGS_ERR_ARG (NULL
+ * pointer, W or H <= 0, W*H > 2^26, fov outside (0, pi)), RGS_ERR_NONFINITE (camera),
+ * RGS_ERR_STATE (t not traced), RGS_ERR_CAPACITY (traversal stack), RGS_ERR_OOM,
+ * RGS_ERR_CUDA. */
+rgs_status rgs_render(rgs_transport *t, const float *B, const float *cam, int32_t W, int32_t H, float fov,
+                      float *img, void *stream);
+
+/* The transpose of rgs_render: dL_dB[j][k][c] = sum over pixels and their hits h on surfel j of
+ * a_h Y_k(-d) dL_dimg[y][x][c] -- the dL/dB that a loss on the image hands to rgs_adjoint.
+ * dL_dimg: device float [H][W][C]; dL_dB: device float [N][nc][C] in caller order, fully
+ * written (overwritten, not accumulated).  Sums are formed with atomic adds, so the last bits
+ * may differ from run to run.  Same camera, scratch, synchronisation and errors as
+ * rgs_render. */
+rgs_status rgs_render_adjoint(rgs_transport *t, const float *dL_dimg, const float *cam, int32_t W, int32_t H,
+                              float fov, float *dL_dB, void *stream);
+
 /* Workspace pool: the per-call scratch of rgs_adjoint (the transposed hit index, 8 bytes per
  * hit; per-hit opacity sums, 4 bytes; v^(a) and u; per-ray adjoint values) and of
  * rgs_get_iterate comes from one stream-ordered memory pool per device, so transports used

@@ -1,0 +1,315 @@
+// Image formation (rgs_render / rgs_render_adjoint): Eq. L_I for the rays of a pinhole camera
+// over a solved radiance B -- what the paper's tile rasterizer draws from the surfels'
+// outgoing SH radiance (Sec. 5.3, end) -- and its transpose, the dL/dB a loss on the image
+// hands to rgs_adjoint (Sec. 6, opening).
+//
+//  k_render_trace : one thread per pixel.  The pixel ray o + t d meets the surfels in depth
+//                   order under the transport's hit rules (eps_plane, the cutoff, tie runs;
+//                   no surfel excluded), composited a_h = alpha_h prod_{k<h} (1 - alpha_k)
+//                   until the transmittance is below RGS_T_EPS; records (j, a_h) per pixel.
+//  k_render_shade : a warp per pixel, a lane per column: I[c] = sum_h a_h Y(-d)^T B_j[c].
+//  k_render_adj   : a warp per pixel, a lane per column: dB_j[c][k] += a_h Y_k(-d) dI[c].
+#include "rgs_internal.cuh"
+
+namespace {
+
+constexpr int RN_THREADS = 128;
+
+// pixel (x, y) (y down) of a W x H pinhole camera cam = {o, forward, up} with vertical field
+// of view fov: right = forward x up, the true up = right x forward, the pixel's centre
+__device__ __forceinline__ float3 pixel_dir(const float *cam, int W, int H, float fov, int x, int y) {
+    const float3 f = make_float3(cam[3], cam[4], cam[5]), u0 = make_float3(cam[6], cam[7], cam[8]);
+    const float lf = sqrtf(dot3(f, f));
+    const float3 fn = (1.f / lf) * f;
+    float3 r = make_float3(fn.y * u0.z - fn.z * u0.y, fn.z * u0.x - fn.x * u0.z, fn.x * u0.y - fn.y * u0.x);
+    r = (1.f / sqrtf(dot3(r, r))) * r;
+    const float3 u = make_float3(r.y * fn.z - r.z * fn.y, r.z * fn.x - r.x * fn.z, r.x * fn.y - r.y * fn.x);
+    const float th = tanf(0.5f * fov);
+    const float sx = (2.f * (x + 0.5f) / (float)W - 1.f) * th * (float)W / (float)H;
+    const float sy = (1.f - 2.f * (y + 0.5f) / (float)H) * th;
+    float3 d = fn + sx * r + sy * u;
+    return (1.f / sqrtf(dot3(d, d))) * d;
+}
+
+struct Cam {
+    float v[9];
+};
+
+__global__ void __launch_bounds__(RN_THREADS) k_render_trace(SceneDev sc, Cam cam, int W, int H, float fov,
+                                                            int2 *rec, int *cnt, float4 *pdir, int *flags) {
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= W * H) return;
+    const int x = pix % W, y = pix / W;
+    const float3 o = make_float3(cam.v[0], cam.v[1], cam.v[2]);
+    const float3 d = pixel_dir(cam.v, W, H, fov, x, y);
+    pdir[pix] = make_float4(d.x, d.y, d.z, 0.f);
+    const float eps = *sc.eps_plane;
+    unsigned long long key[RGS_HMAX];
+    int nh = 0;
+    auto visit = [&](int j) {
+        float t, r2;
+        if (!hit_surfel_t(sc, j, -1, o, d, INFINITY, eps, t, r2)) return;
+        const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)j;
+        if (nh < RGS_HMAX) {
+            key[nh++] = k;
+            return;
+        }
+        int far = 0; // keep the RGS_HMAX nearest
+        for (int m = 1; m < RGS_HMAX; ++m)
+            if (key[m] > key[far]) far = m;
+        if (k < key[far]) key[far] = k;
+    };
+    if (!bvh_traverse_ordered(sc, o, d, visit)) atomicAdd(&flags[FLAG_STACK], 1);
+    for (int a = 1; a < nh; ++a) { // depth order
+        const unsigned long long k = key[a];
+        int b = a - 1;
+        while (b >= 0 && key[b] > k) {
+            key[b + 1] = key[b];
+            --b;
+        }
+        key[b + 1] = k;
+    }
+    for (int k0 = 0; k0 < nh;) { // runs of near-equal depth by caller index
+        int e = k0;
+        float te = __uint_as_float((unsigned)(key[e] >> 32));
+        while (e + 1 < nh) {
+            const float tn = __uint_as_float((unsigned)(key[e + 1] >> 32));
+            if (tn - te > 1e-6f * fmaxf(1.f, te)) break;
+            ++e;
+            te = tn;
+        }
+        for (int a = k0 + 1; a <= e; ++a) {
+            const unsigned long long k = key[a];
+            const int uk = sc.uid[(int)(unsigned)k];
+            int b = a - 1;
+            while (b >= k0 && sc.uid[(int)(unsigned)key[b]] > uk) {
+                key[b + 1] = key[b];
+                --b;
+            }
+            key[b + 1] = k;
+        }
+        k0 = e + 1;
+    }
+    float T = 1.f;
+    int kept = 0;
+    for (; kept < nh && T >= RGS_T_EPS; ++kept) {
+        const int j = (int)(unsigned)key[kept];
+        const float G = surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[kept] >> 32))));
+        const float alpha = alpha_of(sc, __ldg(&sc.P[j].w), G);
+        rec[(size_t)pix * RGS_HMAX + kept] = make_int2(j, __float_as_int(alpha * T));
+        T *= 1.f - alpha;
+    }
+    cnt[pix] = kept;
+}
+
+// internal [N][C][NC] <- user [N][nc][C]
+template <int NC>
+__global__ void k_render_from_user(int n, int C, const int *__restrict__ uid, const float *__restrict__ X, float *Y) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * C * NC) return;
+    const int k = (int)(idx % NC);
+    const size_t ic = idx / NC;
+    const int c = (int)(ic % C);
+    const int i = (int)(ic / C);
+    Y[idx] = X[((size_t)uid[i] * NC + k) * C + c];
+}
+// user [N][nc][C] <- internal [N][C][NC]
+template <int NC>
+__global__ void k_render_to_user(int n, int C, const int *__restrict__ uid, const float *__restrict__ X, float *Y) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * C * NC) return;
+    const int k = (int)(idx % NC);
+    const size_t ic = idx / NC;
+    const int c = (int)(ic % C);
+    const int i = (int)(ic / C);
+    Y[((size_t)uid[i] * NC + k) * C + c] = X[idx];
+}
+
+template <int NC>
+__global__ void __launch_bounds__(RN_THREADS) k_render_shade(int npix, int C, const int2 *__restrict__ rec,
+                                                            const int *__restrict__ cnt, const float4 *__restrict__ pdir,
+                                                            const float *__restrict__ B, float *img) {
+    const int pix = (int)(((size_t)blockIdx.x * RN_THREADS + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (pix >= npix) return;
+    const float4 d4 = pdir[pix];
+    float Yo[NC];
+    sh_eval<NC>(make_float3(-d4.x, -d4.y, -d4.z), Yo);
+    const int nh = cnt[pix];
+    for (int c = lane; c < C; c += 32) {
+        float acc = 0.f;
+        for (int h = 0; h < nh; ++h) {
+            const int2 ja = __ldg(&rec[(size_t)pix * RGS_HMAX + h]);
+            const float *row = B + ((size_t)ja.x * C + c) * NC;
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) s += Yo[k] * __ldg(row + k);
+            acc += __int_as_float(ja.y) * s;
+        }
+        img[(size_t)pix * C + c] = acc;
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(RN_THREADS) k_render_adj(int npix, int C, const int2 *__restrict__ rec,
+                                                          const int *__restrict__ cnt, const float4 *__restrict__ pdir,
+                                                          const float *__restrict__ dimg, float *dB) {
+    const int pix = (int)(((size_t)blockIdx.x * RN_THREADS + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (pix >= npix) return;
+    const float4 d4 = pdir[pix];
+    float Yo[NC];
+    sh_eval<NC>(make_float3(-d4.x, -d4.y, -d4.z), Yo);
+    const int nh = cnt[pix];
+    for (int c = lane; c < C; c += 32) {
+        const float g = dimg[(size_t)pix * C + c];
+        if (g == 0.f) continue;
+        for (int h = 0; h < nh; ++h) {
+            const int2 ja = __ldg(&rec[(size_t)pix * RGS_HMAX + h]);
+            const float ga = __int_as_float(ja.y) * g;
+            float *row = dB + ((size_t)ja.x * C + c) * NC;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) atomicAdd(row + k, ga * Yo[k]);
+        }
+    }
+}
+
+struct RenderScratch {
+    cudaStream_t st;
+    int2 *rec = nullptr;
+    int *cnt = nullptr;
+    float4 *pdir = nullptr;
+    float *X = nullptr;
+    int *flag = nullptr;
+    ~RenderScratch() {
+        pool_release(flag, st);
+        pool_release(rec, st);
+        pool_release(cnt, st);
+        pool_release(pdir, st);
+        pool_release(X, st);
+    }
+};
+
+rgs_status check_args(const rgs_transport *t, const float *in, const float *cam, int W, int H, float fov,
+                      const float *out, const char *what) {
+    if (!t || !in || !cam || !out) {
+        rgs_set_error("%s: NULL argument", what);
+        return RGS_ERR_ARG;
+    }
+    if (t->kind == RGS_KIND_NONE) {
+        rgs_set_error("%s: the transport has not been traced", what);
+        return RGS_ERR_STATE;
+    }
+    if (W <= 0 || H <= 0 || (long long)W * H > (1ll << 26) || !(fov > 0.f && fov < 3.14159f)) {
+        rgs_set_error("%s: image %d x %d or field of view %g out of range", what, W, H, (double)fov);
+        return RGS_ERR_ARG;
+    }
+    for (int q = 0; q < 9; ++q)
+        if (!isfinite(cam[q])) {
+            rgs_set_error("%s: non-finite camera", what);
+            return RGS_ERR_NONFINITE;
+        }
+    return RGS_OK;
+}
+
+// traces every pixel into pooled scratch (records, counts, directions)
+rgs_status render_trace(rgs_transport *t, const float *cam, int W, int H, float fov, RenderScratch &s) {
+    rgs_status r;
+    const int npix = W * H;
+    if ((r = pool_alloc(&s.rec, (size_t)npix * RGS_HMAX, s.st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&s.cnt, (size_t)npix, s.st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&s.pdir, (size_t)npix, s.st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&s.flag, (size_t)FLAG_COUNT, s.st)) != RGS_OK) return r;
+    RGS_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int) * FLAG_COUNT, s.st));
+    Cam c;
+    for (int q = 0; q < 9; ++q) c.v[q] = cam[q];
+    {
+        ProfScope ps_("k_render_trace", s.st);
+        k_render_trace<<<(npix + RN_THREADS - 1) / RN_THREADS, RN_THREADS, 0, s.st>>>(t->sc->dev(), c, W, H, fov, s.rec,
+                                                                                      s.cnt, s.pdir, s.flag);
+    }
+    RGS_LAUNCH("render trace");
+    int stack_overflows = 0;
+    RGS_CUDA(cudaMemcpyAsync(&stack_overflows, s.flag + FLAG_STACK, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+    RGS_CUDA(cudaStreamSynchronize(s.st));
+    if (stack_overflows) {
+        rgs_set_error("render: BVH traversal stack overflow on %d pixel rays", stack_overflows);
+        return RGS_ERR_CAPACITY;
+    }
+    return RGS_OK;
+}
+
+template <int NC>
+rgs_status render_nc(rgs_transport *t, const float *B, const float *cam, int W, int H, float fov, float *img,
+                     cudaStream_t st) {
+    rgs_status r;
+    RenderScratch s{st};
+    const size_t A = (size_t)t->n * t->C * NC;
+    if ((r = pool_alloc(&s.X, A, st)) != RGS_OK) return r;
+    {
+        ProfScope ps_("k_render_from_user", st);
+        k_render_from_user<NC><<<(unsigned)((A + 255) / 256), 256, 0, st>>>(t->n, t->C, t->sc->uid, B, s.X);
+    }
+    RGS_LAUNCH("render from user");
+    if ((r = render_trace(t, cam, W, H, fov, s)) != RGS_OK) return r;
+    const int npix = W * H;
+    {
+        ProfScope ps_("k_render_shade", st);
+        k_render_shade<NC><<<(unsigned)(((size_t)npix * 32 + RN_THREADS - 1) / RN_THREADS), RN_THREADS, 0, st>>>(
+            npix, t->C, s.rec, s.cnt, s.pdir, s.X, img);
+    }
+    RGS_LAUNCH("render shade");
+    return RGS_OK;
+}
+
+template <int NC>
+rgs_status render_adjoint_nc(rgs_transport *t, const float *dimg, const float *cam, int W, int H, float fov,
+                             float *dB, cudaStream_t st) {
+    rgs_status r;
+    RenderScratch s{st};
+    const size_t A = (size_t)t->n * t->C * NC;
+    if ((r = pool_alloc(&s.X, A, st)) != RGS_OK) return r;
+    RGS_CUDA(cudaMemsetAsync(s.X, 0, sizeof(float) * A, st));
+    if ((r = render_trace(t, cam, W, H, fov, s)) != RGS_OK) return r;
+    const int npix = W * H;
+    {
+        ProfScope ps_("k_render_adj", st);
+        k_render_adj<NC><<<(unsigned)(((size_t)npix * 32 + RN_THREADS - 1) / RN_THREADS), RN_THREADS, 0, st>>>(
+            npix, t->C, s.rec, s.cnt, s.pdir, dimg, s.X);
+    }
+    RGS_LAUNCH("render adjoint");
+    {
+        ProfScope ps_("k_render_to_user", st);
+        k_render_to_user<NC><<<(unsigned)((A + 255) / 256), 256, 0, st>>>(t->n, t->C, t->sc->uid, s.X, dB);
+    }
+    RGS_LAUNCH("render to user");
+    return RGS_OK;
+}
+
+} // namespace
+
+extern "C" rgs_status rgs_render(rgs_transport *t, const float *B, const float *cam, int32_t W, int32_t H, float fov,
+                                 float *img, void *stream) {
+    rgs_status r = check_args(t, B, cam, W, H, fov, img, "rgs_render");
+    if (r != RGS_OK) return r;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (t->nc) {
+    case 1: return render_nc<1>(t, B, cam, W, H, fov, img, st);
+    case 4: return render_nc<4>(t, B, cam, W, H, fov, img, st);
+    case 9: return render_nc<9>(t, B, cam, W, H, fov, img, st);
+    default: return render_nc<16>(t, B, cam, W, H, fov, img, st);
+    }
+}
+
+extern "C" rgs_status rgs_render_adjoint(rgs_transport *t, const float *dL_dimg, const float *cam, int32_t W,
+                                         int32_t H, float fov, float *dL_dB, void *stream) {
+    rgs_status r = check_args(t, dL_dimg, cam, W, H, fov, dL_dB, "rgs_render_adjoint");
+    if (r != RGS_OK) return r;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (t->nc) {
+    case 1: return render_adjoint_nc<1>(t, dL_dimg, cam, W, H, fov, dL_dB, st);
+    case 4: return render_adjoint_nc<4>(t, dL_dimg, cam, W, H, fov, dL_dB, st);
+    case 9: return render_adjoint_nc<9>(t, dL_dimg, cam, W, H, fov, dL_dB, st);
+    default: return render_adjoint_nc<16>(t, dL_dimg, cam, W, H, fov, dL_dB, st);
+    }
+}

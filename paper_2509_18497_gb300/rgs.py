@@ -30,7 +30,7 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_profile_reset", "rgs_profile_report", "rgs_launch_count", "rgs_status_string",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
            "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_set_tensor_cores",
-           "rgs_set_wait_limit", "rgs_contraction_info",
+           "rgs_set_wait_limit", "rgs_contraction_info", "rgs_render", "rgs_render_adjoint",
            "rgs_trace_pairs",
            "rgs_adjoint_pairs", "rgs_adjoint_pairs_geometry", "rgs_adjoint_geometry")
 
@@ -139,6 +139,10 @@ def load(path=LIB_PATH):
     L.rgs_set_wait_limit.restype = ct.c_int
     L.rgs_contraction_info.argtypes = [vp, ct.POINTER(ct.c_int64), ct.c_int32]
     L.rgs_contraction_info.restype = ct.c_int
+    L.rgs_render.argtypes = [vp, vp, ct.POINTER(ct.c_float), ct.c_int32, ct.c_int32, ct.c_float, vp, vp]
+    L.rgs_render.restype = ct.c_int
+    L.rgs_render_adjoint.argtypes = [vp, vp, ct.POINTER(ct.c_float), ct.c_int32, ct.c_int32, ct.c_float, vp, vp]
+    L.rgs_render_adjoint.restype = ct.c_int
     L.rgs_trim_workspace.argtypes = []
     L.rgs_trim_workspace.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
@@ -388,6 +392,37 @@ def rgs_contraction_info(transport):
     _check(load().rgs_contraction_info(transport.h, out, 6))
     keys = ("tiles", "groups", "pairs", "hits", "src_tiles", "src_groups")
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def _cam9(cam):
+    c = [float(v) for v in torch.as_tensor(cam, dtype=torch.float64).reshape(-1).tolist()]
+    if len(c) != 9:
+        raise ValueError("cam must hold 9 numbers: origin, forward, up")
+    return (ct.c_float * 9)(*c)
+
+
+def rgs_render(transport, B, cam, W, H, fov, img_out=None, stream=None):
+    """Image [H][W][C] of the radiance B [N][nc][C] (device float32) seen by a pinhole camera
+    cam = (origin, forward, up) with vertical field of view fov (Eq. L_I per pixel ray)."""
+    n, nc, C = transport.n, transport.nc, transport.C
+    pB = _dev(B, (n, nc, C), "B")
+    img = torch.empty((H, W, C), dtype=torch.float32, device=B.device) if img_out is None else img_out
+    pimg = _dev(img, (H, W, C), "img_out")
+    with torch.cuda.device(B.device):
+        _check(load().rgs_render(transport.h, pB, _cam9(cam), int(W), int(H), float(fov), pimg, _stream(stream)))
+    return img
+
+
+def rgs_render_adjoint(transport, dimg, cam, W, H, fov, dB_out=None, stream=None):
+    """The transpose of rgs_render: dL/dB [N][nc][C] from dL/dimg [H][W][C] (device float32)."""
+    n, nc, C = transport.n, transport.nc, transport.C
+    pd = _dev(dimg, (H, W, C), "dimg")
+    dB = torch.empty((n, nc, C), dtype=torch.float32, device=dimg.device) if dB_out is None else dB_out
+    pdB = _dev(dB, (n, nc, C), "dB_out")
+    with torch.cuda.device(dimg.device):
+        _check(load().rgs_render_adjoint(transport.h, pd, _cam9(cam), int(W), int(H), float(fov), pdB,
+                                         _stream(stream)))
+    return dB
 
 
 def rgs_trim_workspace():

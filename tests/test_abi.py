@@ -83,6 +83,10 @@ def test_service_entry_points_reject_bad_arguments_without_device_work():
     assert L.rgs_set_wait_limit(None, 1000) == 1
     assert L.rgs_contraction_info(None, None, 6) == 1
     assert L.rgs_transport_info_get(None, None) == 1
+    cam = (ct.c_float * 9)(0, 0, 2, 0, 0, -1, 0, 1, 0)
+    assert L.rgs_render(None, p16 := ct.c_void_p(16), cam, 4, 4, 0.5, p16, None) == 1
+    assert L.rgs_render_adjoint(None, p16, cam, 4, 4, 0.5, p16, None) == 1
+    assert L.rgs_render(None, p16, None, 4, 4, 0.5, p16, None) == 1
     # the no-allocation norm: NULL arrays, negative and oversized lengths
     p = ct.c_void_p(16)
     assert L.rgs_residual_norm_noalloc(None, p, 1, p, None) == 1
