@@ -388,14 +388,15 @@ rgs_status rgs_set_wait_limit(rgs_transport *t, int64_t ns);
  * o + t d meets the surfels of t's scene in depth order under the transport's hit rules
  * (the eps_plane plane test, the Gaussian's cutoff, runs of near-equal depth ordered by caller
  * index; no surfel excluded), composited with a_h = alpha_h prod_{k<h} (1 - alpha_k) until the
- * transmittance falls below 1e-6 (at most 96 nearest hits), and
+ * transmittance falls below 1e-6 (any number of hits), and
  *     img[y][x][c] = sum_h a_h Y(-d)^T B_{j_h}[:, c].
  * cam: HOST float[9] = {o[3], forward[3], up[3]}; right = forward x up (normalised), the true
  * up = right x forward; fov is the vertical field of view in radians (0, pi); pixel (x, y),
  * y pointing down, is sampled at its centre.  B: device float [N][nc][C] in caller order (the
  * layout rgs_solve writes); img: device float [H][W][C], fully written.  Device buffers are
- * the caller's; pooled scratch (about 800 bytes per pixel) is returned before the call ends.
- * Synchronises `stream` once (the traversal's overflow check).  Errors: RGS_ERR_ARG (NULL
+ * the caller's; pooled scratch (40 bytes per pixel and 8 per composited hit) is returned
+ * before the call ends.  Every pixel ray is traced twice (count, then fill).  Synchronises
+ * `stream` once (the record count and the traversal's overflow check).  Errors: RGS_ERR_ARG (NULL
  * pointer, W or H <= 0, W*H > 2^26, fov outside (0, pi)), RGS_ERR_NONFINITE (camera),
  * RGS_ERR_STATE (t not traced), RGS_ERR_CAPACITY (traversal stack), RGS_ERR_OOM,
  * RGS_ERR_CUDA. */
@@ -410,6 +411,70 @@ rgs_status rgs_render(rgs_transport *t, const float *B, const float *cam, int32_
  * rgs_render. */
 rgs_status rgs_render_adjoint(rgs_transport *t, const float *dL_dimg, const float *cam, int32_t W, int32_t H,
                               float fov, float *dL_dB, void *stream);
+
+/* The Monte-Carlo TD(0) solver of Sec. 7 (Alg. 1) on a center-to-center transport (traced
+ * by rgs_trace_pairs), with next-event estimation by weighted reservoir sampling and the
+ * variance-driven receiver selection of App. "Monte-Carlo Solver Details":
+ *   step t = 1..steps draws N estimates; draw q's receiver is a = q for t <= 8, afterwards a
+ *   draw with replacement with probability proportional to the receivers' tracked variances
+ *   (sum over coefficients of S2/D - (S/D)^2, plus 1e-30); its next event is one pair
+ *   (a <- b) picked with probability p_b proportional to the proxy
+ *     w_b = geo_ab (sum_c lum(c) |Y(-d)^T Bhat_b[:, c]| + floor),
+ *   geo = |n_a.d||n_b.d|/r^2, lum the Rec. 709 weights (0.2126, 0.7152, 0.0722) of each
+ *   column's colour channel, floor = 1e-9 (1 + sum of lum |Bhat| / N); with groups > 0 the
+ *   surfels are first grouped by K-means on centre and normal and the pick is a group by
+ *   its proxy, then a pair of a inside it (p_b the product).  The estimate
+ *   delta = S_a + (1/p_b) K_ab Bhat_b enters a's FP64 sums (S += delta, S2 += delta^2,
+ *   D += 1); Bhat = S / D after every step, and every draw reads the previous step's means.
+ * Random numbers: u = (SplitMix64(k) >> 11) * 2^-53 with
+ * k = SplitMix64(SplitMix64(SplitMix64(seed) + t) + q) + stream, stream 0 for the receiver
+ * selection and 1000 + k for the k-th candidate of a reservoir (the group stage uses draw
+ * q + 2^30); a's candidates are its pairs in increasing caller index of the source (the
+ * order rgs_trace_pairs stores them in) or the groups in index order.
+ * E: device [N][nc][3] or NULL (no emission); S_in: device [N][nc][C] or NULL -- when given
+ * it replaces S = E + D (the direct term), e.g. the unshot radiance of a shooting solver.
+ * B_out: device [N][nc][C], the means after `steps` steps (zero for a receiver never
+ * visited); visits: device float [N] or NULL, each receiver's estimate count.  Scratch:
+ * about 24 bytes per entry of B from the workspace pool.  Synchronises `stream` per K-means
+ * iteration the first time a group count is used on t.  Errors: RGS_ERR_ARG (NULL t or
+ * B_out, a hemisphere transport, steps < 0, groups outside [0, min(1024, N)]),
+ * RGS_ERR_STATE (t not traced), RGS_ERR_OOM, RGS_ERR_CUDA. */
+rgs_status rgs_mc_solve(rgs_transport *t, const float *E, const float *S_in, int32_t steps, uint64_t seed,
+                        int32_t groups, float *B_out, float *visits, void *stream);
+
+/* One step's next-event estimates for given means, the building block of rgs_mc_solve:
+ * draw q (0 <= q < n_draws) uses the keys (seed, step, q), receiver recv[q] (device int32
+ * [n_draws], caller indices; NULL: receiver q, then n_draws <= N) and the means Bhat
+ * (device [N][nc][C]).  Writes pick[q] (device int64: the picked pair's index among the
+ * receiver's pairs in increasing caller index of the source, -1 if the receiver has none),
+ * p[q] (device double: its probability, 0 without a pick) and delta (device float
+ * [n_draws][nc][C], S_a + K_ab Bhat_b / p_b with S = E + D).  Synchronises `stream` (the
+ * check of recv).  Errors: RGS_ERR_ARG (NULL pointers, step < 1, n_draws < 0, n_draws > N
+ * without recv, a receiver outside [0, N), groups outside [0, min(1024, N)]), RGS_ERR_STATE,
+ * RGS_ERR_OOM, RGS_ERR_CUDA. */
+rgs_status rgs_mc_estimate(rgs_transport *t, const float *E, const float *Bhat, uint64_t seed, int32_t step,
+                           int32_t groups, int32_t n_draws, const int32_t *recv, int64_t *pick, double *p,
+                           float *delta, void *stream);
+
+/* The K-means groups the solver's grouped proposal uses (App. "Monte-Carlo Solver
+ * Details"): Lloyd's iterations in FP64 on the features (p, (extent / 2) n), extent the
+ * scene's largest side, from the surfels with caller indices floor(k N / groups), until no
+ * assignment changes (at most 50).  assign: device int32 [N], caller order.  The result is
+ * cached on t until its next trace.  Errors: as rgs_mc_solve, groups in [1, min(1024, N)]. */
+rgs_status rgs_mc_groups(rgs_transport *t, int32_t groups, int32_t *assign, void *stream);
+
+/* Progressive refinement (the shooting solver of Sec. 7) on a center-to-center transport:
+ * Bhat = dB = S = E + D, then `shots` times the surfel whose unshot radiance has the largest
+ * luminance (sum over its coefficients and columns of lum(c) |dB|, the Rec. 709 weights of
+ * each column's channel; ties to the lower caller index) sends it to every receiver a that
+ * has it as a source, dB_a += K_a,b dB_b and Bhat_a += K_a,b dB_b, and its dB is cleared;
+ * once no unshot radiance is left the remaining shots do nothing.  The remaining problem
+ * B^r = dB + K B^r is again the full transport, so B = Bhat + B^r - dB exactly: running
+ * rgs_mc_solve with S_in = dB and combining gives the paper's hybrid solver.  Bhat_out,
+ * dB_out: device [N][nc][C].  Three launches per shot.  Errors: RGS_ERR_ARG (NULL t or
+ * output, shots < 0, a hemisphere transport), RGS_ERR_STATE, RGS_ERR_OOM, RGS_ERR_CUDA. */
+rgs_status rgs_prog_refine(rgs_transport *t, const float *E, int32_t shots, float *Bhat_out, float *dB_out,
+                           void *stream);
 
 /* Workspace pool: the per-call scratch of rgs_adjoint (the transposed hit index, 8 bytes per
  * hit; per-hit opacity sums, 4 bytes; v^(a) and u; per-ray adjoint values) and of

@@ -356,28 +356,23 @@ __global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const flo
     }
 }
 
-// Geometry gradients of the hemisphere-ray transport (Eqs. dl-dgeo-0/1), one thread per ray,
-// from every iterate B^(b), every v^(a) and the per-record g_h of the opacity backward:
-//  - compositing: each hit's alpha moves with q_h = u^2 + v^2 at the hit point on its
-//    source's plane, with dL/dalpha_h = T_h (g_h - R_h) (back to front, as k_opacity_rec);
-//    q_h moves with p_i, the ray direction and the source's centre, scales and frame;
-//  - directional effects: Y(R_i d) through X^(a)[c] = sum_h a_h Y(-d).B_{j_h}^(b)[c] and
-//    Y(-d) through every hit's source row;
-//  - the ray leaves p_i along d = c_x t^u_i + c_y t^v_i + c_z n_i with fixed c, so dL/dd
-//    goes to the receiver's frame, and R_i to its normal.
+// Geometry gradients of the hemisphere-ray transport (Eqs. dl-dgeo-0/1), part 1 (compositing),
+// one thread per ray from the per-record g_h of the opacity backward: each hit's alpha moves
+// with q_h = u^2 + v^2 at the hit point on its source's plane, with dL/dalpha_h =
+// T_h (g_h - R_h) (back to front, as k_opacity_rec); q_h moves with p_i, the ray direction
+// and the source's centre, scales and frame.  The ray leaves p_i along
+// d = c_x t^u_i + c_y t^v_i + c_z n_i with fixed c, so dL/dd goes to the receiver's frame.
 // The receiver's terms are summed over the warp (nd is a multiple of 32, so a warp's rays
-// share their receiver) and added once per warp.
-template <int NC>
-__global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int C, int nb, size_t A,
-                                                 const float *__restrict__ V, const float *__restrict__ Bit,
-                                                 const float *__restrict__ gh, float *dp, float *ds, float *gF) {
+// share their receiver) and added once per warp.  Part 2 is k_hemi_geo_dir.
+__global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int nb, const float *__restrict__ gh,
+                                                 float *dp, float *ds, float *gF) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     const int n_rays = sc.n * rays.nd;
     if (r - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps (n_rays % 32 == 0)
     const int i = r / rays.nd;
     const int cnt = rays.cnt[r];
     const float3 o = f3(sc.P[i]), n = f3(sc.N4[i]), d = f3(rays.dir[r]);
-    float3 gpi = make_float3(0.f, 0.f, 0.f), gd = make_float3(0.f, 0.f, 0.f), t1 = make_float3(0.f, 0.f, 0.f);
+    float3 gpi = make_float3(0.f, 0.f, 0.f), gd = make_float3(0.f, 0.f, 0.f);
     if (cnt > 0 && nb > 0) {
         const long long base = rays.off[r];
         float Th[RGS_HMAX];
@@ -412,49 +407,10 @@ __global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int
             }
             R = al * g + (1.f - al) * R;
         }
-        float Yo[NC], Yi[NC], wi[NC], wo[NC];
-        const float3 rd = reflect_n(n, d);
-        sh_eval<NC>(neg3(d), Yo);
-        sh_eval<NC>(rd, Yi);
-#pragma unroll
-        for (int k = 0; k < NC; ++k) wi[k] = wo[k] = 0.f;
-        const float wa = alpha_center(sc, i) * (3.14159265358979f / (float)rays.nd);
-        for (int a = 0; a < nb; ++a) {
-            const float *va = V + A * a + (size_t)i * C * NC;
-            const float *Bb = Bit + A * (nb - 1 - a);
-            for (int c = 0; c < C; ++c) {
-                const int ch = c % 3;
-                float cv[NC], y = 0.f;
-#pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    cv[k] = wa * __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + ch]) * __ldg(&va[c * NC + k]);
-                    y += cv[k] * Yi[k];
-                }
-                float X = 0.f;
-                for (int h = 0; h < cnt; ++h) {
-                    const int2 ja = __ldg(&rays.rec_ja[base + h]);
-                    const float ah = __int_as_float(ja.y);
-                    const float *row = Bb + ((size_t)ja.x * C + c) * NC;
-                    float s = 0.f;
-#pragma unroll
-                    for (int k = 0; k < NC; ++k) {
-                        const float b = __ldg(&row[k]);
-                        s += Yo[k] * b;
-                        wo[k] += ah * y * b;
-                    }
-                    X += ah * s;
-                }
-#pragma unroll
-                for (int k = 0; k < NC; ++k) wi[k] += X * cv[k];
-            }
-        }
-        t1 = sh_grad_dot<NC>(rd, wi);
-        const float3 t3 = reflect_n(n, t1), t2 = sh_grad_dot<NC>(neg3(d), wo);
-        gd = gd + (t3 - t2);
     }
     const float3 tu = f3(sc.FU[i]), tv = f3(sc.FV[i]);
     const float cx = dot3(d, tu), cy = dot3(d, tv), cz = dot3(d, n);
-    const float3 gn = reflect_grad_n(n, d, t1) + cz * gd;
+    const float3 gn = cz * gd;
     float red[12] = {gpi.x, gpi.y, gpi.z, cx * gd.x, cx * gd.y, cx * gd.z, cy * gd.x, cy * gd.y, cy * gd.z,
                      gn.x, gn.y, gn.z};
 #pragma unroll
@@ -468,6 +424,132 @@ __global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int
 #pragma unroll
         for (int q = 0; q < 9; ++q)
             if (red[3 + q] != 0.f) atomicAdd(&gF[9 * (size_t)i + q], red[3 + q]);
+    }
+}
+
+constexpr int GEO_DIR_THREADS = 256;
+
+// Part 2 (directional effects), a CTA per receiver and G lanes per ray, each lane a slice of
+// the SH coefficients (the layout of the bounce gather): Y(R_i d) through
+// X^(a)[c] = Y(-d).P^(a)[c] and Y(-d) through the composited source rows
+// P^(a)[c] = sum_h a_h B_{j_h}^(nb-1-a)[c] (gathered once per 3-column tile and iterate);
+// with cv = (pi/nd) o_i c_i (x) v_i^(a)[c], w_i = sum X cv and w_o = sum (cv.Y(R_i d)) P,
+// dL/dd = R_i grad Y(R_i d).w_i - grad Y(-d).w_o, dL/dn_i from R_i, summed over the
+// receiver's rays into its frame gradient.
+template <int NC>
+__global__ void __launch_bounds__(GEO_DIR_THREADS) k_hemi_geo_dir(SceneDev sc, RaysDev rays, int C, int nb, size_t A,
+                                                                const float *__restrict__ V,
+                                                                const float *__restrict__ Bit, float *gF) {
+    using SL = Slice<NC>;
+    constexpr int G = SL::G, KPL = SL::KPL, GROUPS = GEO_DIR_THREADS / G, CT = 3;
+    __shared__ float red[GEO_DIR_THREADS / 32][9];
+    const int i = blockIdx.x;
+    const int grp = threadIdx.x / G, g = threadIdx.x % G, lane = threadIdx.x & 31;
+    const int nd = rays.nd;
+    const float3 n = f3(sc.N4[i]), tu = f3(sc.FU[i]), tv = f3(sc.FV[i]);
+    const float wa = alpha_center(sc, i) * (3.14159265358979f / (float)nd);
+    float acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = 0.f;
+    for (int qb = 0; qb < nd; qb += GROUPS) { // every lane makes the same trips (group shuffles)
+        const int q = qb + grp;
+        const bool live = q < nd;
+        const long long r = (long long)i * nd + (live ? q : 0);
+        const float3 d = f3(rays.dir[r]);
+        const int cnt = live ? rays.cnt[r] : 0;
+        const long long base = rays.off[r];
+        const float3 rd = reflect_n(n, d);
+        float yo[KPL], yi[KPL];
+        {
+            float Y[NC];
+            sh_eval<NC>(neg3(d), Y);
+            SL::pick(Y, g, yo);
+            sh_eval<NC>(rd, Y);
+            SL::pick(Y, g, yi);
+        }
+        float wi[KPL], wo[KPL];
+#pragma unroll
+        for (int m = 0; m < KPL; ++m) wi[m] = wo[m] = 0.f;
+        for (int a = 0; a < nb; ++a) {
+            const float *va = V + A * a + (size_t)i * C * NC;
+            const float *Bb = Bit + A * (nb - 1 - a);
+            for (int c0 = 0; c0 < C; c0 += CT) {
+                float P[CT][KPL];
+#pragma unroll
+                for (int c = 0; c < CT; ++c)
+#pragma unroll
+                    for (int m = 0; m < KPL; ++m) P[c][m] = 0.f;
+#pragma unroll 2
+                for (int h = 0; h < cnt; ++h) {
+                    const int2 ja = __ldg(&rays.rec_ja[base + h]);
+                    const float ah = __int_as_float(ja.y);
+                    const float *Bj = Bb + ((size_t)ja.x * C + c0) * NC;
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        float v[KPL];
+                        SL::load(Bj + c * NC, g, v);
+#pragma unroll
+                        for (int m = 0; m < KPL; ++m) P[c][m] += ah * v[m];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < CT; ++c) {
+                    const int col = c0 + c;
+                    float vv[KPL], cv[KPL];
+                    SL::load(va + (size_t)col * NC, g, vv);
+                    float xs = 0.f, ys = 0.f;
+#pragma unroll
+                    for (int m = 0; m < KPL; ++m) {
+                        const int k = SL::k(g, m);
+                        cv[m] = k < NC ? wa * __ldg(&sc.cl[(size_t)i * 12 + band_of(k) * 3 + (col % 3)]) * vv[m] : 0.f;
+                        xs += yo[m] * P[c][m];
+                        ys += cv[m] * yi[m];
+                    }
+                    const float X = SL::group_sum(xs), y = SL::group_sum(ys);
+#pragma unroll
+                    for (int m = 0; m < KPL; ++m) {
+                        wi[m] += X * cv[m];
+                        wo[m] += y * P[c][m];
+                    }
+                }
+            }
+        }
+        // the whole w_i, w_o from the group's lanes
+        float WI[NC], WO[NC];
+#pragma unroll
+        for (int g2 = 0; g2 < G; ++g2)
+#pragma unroll
+            for (int m = 0; m < KPL; ++m) {
+                const float xi = __shfl_sync(0xffffffffu, wi[m], (lane & ~(G - 1)) + g2);
+                const float xo = __shfl_sync(0xffffffffu, wo[m], (lane & ~(G - 1)) + g2);
+                const int k = SL::k(g2, m);
+                if (k < NC) {
+                    WI[k] = xi;
+                    WO[k] = xo;
+                }
+            }
+        if (live && g == 0 && cnt > 0) {
+            const float3 t1 = sh_grad_dot<NC>(rd, WI);
+            const float3 gd = reflect_n(n, t1) - sh_grad_dot<NC>(neg3(d), WO);
+            const float cx = dot3(d, tu), cy = dot3(d, tv), cz = dot3(d, n);
+            const float3 gn = reflect_grad_n(n, d, t1) + cz * gd;
+            acc[0] += cx * gd.x, acc[1] += cx * gd.y, acc[2] += cx * gd.z;
+            acc[3] += cy * gd.x, acc[4] += cy * gd.y, acc[5] += cy * gd.z;
+            acc[6] += gn.x, acc[7] += gn.y, acc[8] += gn.z;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        float v = acc[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[threadIdx.x >> 5][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        float v = 0.f;
+        for (int w = 0; w < GEO_DIR_THREADS / 32; ++w) v += red[w][threadIdx.x];
+        if (v != 0.f) atomicAdd(&gF[9 * (size_t)i + threadIdx.x], v);
     }
 }
 
@@ -704,8 +786,10 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     }
     if (nb >= 1 && geo) { // every iterate is kept (the caller checked the stride)
         const long long n_rays = (long long)n * t->nd;
-        { ProfScope ps_("k_hemi_geo", st); k_hemi_geo<NC><<<(unsigned)((n_rays + 127) / 128), 128, 0, st>>>(sd, rd, C, nb, A, t->v, t->iters, t->gh, geo->dp, geo->ds, geo->gF); }
+        { ProfScope ps_("k_hemi_geo", st); k_hemi_geo<<<(unsigned)((n_rays + 127) / 128), 128, 0, st>>>(sd, rd, nb, t->gh, geo->dp, geo->ds, geo->gF); }
         RGS_LAUNCH("hemisphere geometry backward");
+        { ProfScope ps_("k_hemi_geo_dir", st); k_hemi_geo_dir<NC><<<n, GEO_DIR_THREADS, 0, st>>>(sd, rd, C, nb, A, t->v, t->iters, geo->gF); }
+        RGS_LAUNCH("hemisphere geometry backward (directional)");
     }
     { ProfScope ps_("k_finalize", st); k_finalize<NC><<<gn, 128, 0, st>>>(sd, C, t->u, t->Pg, t->sc->kk, t->dop, dE, dad, dopo); }
     RGS_LAUNCH("finalize");

@@ -589,6 +589,7 @@ void rgs_destroy_transport(rgs_transport *t) {
     dev_free(t->aarea);
     dev_free(t->daarea);
     rgs_tc_free(t);
+    rgs_mc_free(t);
     delete t;
 }
 

@@ -85,7 +85,8 @@ struct SceneDev {
     float cutoff2;
     const float4 *P, *N4, *FU, *FV;
     const float *cl; // [n][4][3]
-    const int *uid;
+    const int *uid; // caller index of internal surfel i
+    const int *inv; // internal index of caller surfel k
     const BvhNode *nodes;
     const float *eps_plane; // device scalar
 };
@@ -598,6 +599,7 @@ struct rgs_scene {
         s.FV = FV;
         s.cl = cl;
         s.uid = uid;
+        s.inv = inv;
         s.nodes = nodes;
         s.eps_plane = eps_plane;
         return s;
@@ -608,6 +610,8 @@ enum { RGS_KIND_NONE = 0, RGS_KIND_HEMISPHERE = 1, RGS_KIND_PAIRS = 2 };
 
 // tensor-core contraction state of a transport (rgs_tc.cu): pair tiles and BF16 row blocks
 struct rgs_tc_state;
+// Monte-Carlo solver state of a transport (rgs_mc.cu): the cached K-means groups
+struct rgs_mc_cache;
 // the batched modes take the tensor-core contraction from this many columns on (automatic mode)
 #define RGS_TC_MIN_COLS 96
 
@@ -698,6 +702,7 @@ struct rgs_transport {
     unsigned long long tc_wait_ns = 4000000000ull; // limit of each pipeline wait (rgs_set_wait_limit)
     bool tc_used = false; // the last solve ran on the tensor-core path
     rgs_tc_state *tc = nullptr;
+    rgs_mc_cache *mc = nullptr;
     RaysDev rays() const {
         RaysDev r;
         r.nd = nd;
@@ -826,6 +831,8 @@ rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout,
 rgs_status rgs_tc_opacity(rgs_transport *t, int slot, const float *Bsrc, bool first, cudaStream_t st);
 rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st); // RGS_ERR_TIMEOUT if a bounded wait ran out
 rgs_status rgs_tc_reset_flags(rgs_transport *t, cudaStream_t st);
+// drops the Monte-Carlo solver's cached K-means groups (rgs_mc.cu)
+void rgs_mc_free(rgs_transport *t);
 void rgs_tc_invalidate(rgs_transport *t);
 void rgs_tc_free(rgs_transport *t);
 
@@ -875,4 +882,6 @@ rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float 
                                float *gF = nullptr);
 rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st);
 void rgs_copy_offsets(const long long *off, unsigned long long *cursor, int n, cudaStream_t st);
+// center-to-center transport: fills the transposed pair index tr [n_pairs] (rgs_pairs.cu)
+rgs_status rgs_pairs_transpose(rgs_transport *t, int2 *tr, cudaStream_t st);
 int rgs_scan_tmp_size(int n);

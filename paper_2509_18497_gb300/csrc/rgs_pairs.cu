@@ -11,7 +11,7 @@
 // must lie more than eps_plane from the source's end too; int alpha_j is closed-form.
 //
 // Storage: the pairs of receiver i are contiguous (pair_off[i] .. pair_off[i+1]), each one
-// record (j, bits of V_ji), sources in increasing internal index.  A count pass sizes
+// record (j, bits of V_ji), sources in increasing caller index.  A count pass sizes
 // every (receiver, 256-source chunk) block exactly; the fill pass traces each front pair's
 // segment and writes its record at the chunk's offset plus its rank in the block.
 #include <algorithm>
@@ -24,20 +24,26 @@ namespace {
 constexpr int PCH = 256;      // sources per block of the count / fill passes
 constexpr int PAIR_THREADS = 128;
 
-// Ein(x) = int_0^x (1 - e^{-y}) / y dy in double: its power series sum (-1)^{k+1} x^k / (k k!)
-// up to x = 20 (the largest term is ~2e6 there, so the sum keeps ~1e-10 relative), and
-// ln x + gamma beyond, where the remainder E1(x) < e^{-x}/x < 1e-10.
-__device__ double ein_d(double x) {
-    if (!(x > 0.0)) return 0.0;
-    if (x > 20.0) return log(x) + 0.5772156649015329;
-    double term = x, sum = x;
-    for (int k = 2; k < 120; ++k) {
-        term *= -x / k;
-        const double add = term / k;
-        sum += add;
-        if (fabs(add) < 1e-17 * fabs(sum)) break;
+// Ein(x) = int_0^x (1 - e^{-y}) / y dy in FP32: for x <= 2 its power series
+// sum (-1)^{k+1} x^k / (k k!) (terms below 2^-24 of the sum after k = 14); beyond,
+// ln x + gamma + E1(x) with E1 from the continued fraction of Abramowitz & Stegun 5.1.22,
+// E1(x) = e^{-x} / (x + 1/(1 + 1/(x + 2/(1 + 2/(x + ...))))), evaluated from depth 12 upwards
+// (the truncation is below 1.2e-7 relative from x = 2 on).  Within 2.3e-7 of the exact value.
+__device__ float ein_f(float x) {
+    if (!(x > 0.f)) return 0.f;
+    if (x <= 2.f) {
+        float term = x, sum = x;
+#pragma unroll
+        for (int k = 2; k <= 16; ++k) {
+            term *= -x / (float)k;
+            sum += term / (float)k;
+        }
+        return sum;
     }
-    return sum;
+    float tail = 0.f;
+#pragma unroll
+    for (int m = 12; m >= 1; --m) tail = (float)m / (1.f + (float)m / (x + tail));
+    return logf(x) + 0.5772157f + expf(-x) / (x + tail);
 }
 
 // int alpha_j dx over the tangent plane and its derivative in o_j, per surfel: the
@@ -47,20 +53,21 @@ __device__ double ein_d(double x) {
 __global__ void k_alpha_area(SceneDev sc, float *aarea, float *daarea) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= sc.n) return;
-    const double su = 1.0 / (double)sc.FU[j].w, sv = 1.0 / (double)sc.FV[j].w, o = sc.P[j].w;
-    const double two_pi = 6.283185307179586;
-    double A, dA;
+    const float su = 1.f / sc.FU[j].w, sv = 1.f / sc.FV[j].w, o = sc.P[j].w;
+    const float two_pi = 6.2831853f;
+    float A, dA;
     if (sc.alpha_model == RGS_ALPHA_GFSGS) {
-        A = two_pi / 3.4 * su * sv * ein_d(0.03279 * pow(o, 3.4));
-        dA = o > 0.0 ? two_pi * su * sv * (-expm1(-0.03279 * pow(o, 3.4))) / o : 0.0;
+        const float x = o > 0.f ? 0.03279f * powf(o, 3.4f) : 0.f;
+        A = two_pi / 3.4f * su * sv * ein_f(x);
+        dA = o > 0.f ? two_pi * su * sv * (-expm1f(-x)) / o : 0.f;
     } else {
-        const double unit = (sc.alpha_model == RGS_ALPHA_DISC) ? 0.5 * two_pi * su * sv
-                                                                : two_pi * su * sv * (1.0 - exp(-4.5));
+        const float unit = (sc.alpha_model == RGS_ALPHA_DISC) ? 0.5f * two_pi * su * sv
+                                                              : two_pi * su * sv * (1.f - expf(-4.5f));
         A = o * unit;
         dA = unit;
     }
-    aarea[j] = (float)A;
-    daarea[j] = (float)dA;
+    aarea[j] = A;
+    daarea[j] = dA;
 }
 
 // source j in front of receiver i: n_i.(p_j - p_i) > eps (explicitly rounded, so the count
@@ -71,6 +78,12 @@ __device__ __forceinline__ bool pair_front(const SceneDev &sc, float3 pi, float3
     const float h = __fmaf_rn(ni.z, dv.z, __fmaf_rn(ni.y, dv.y, __fmul_rn(ni.x, dv.x)));
     return h > eps;
 }
+
+// The sources of a receiver are enumerated in caller order (chunk c holds the surfels with
+// caller indices c * 256 .. c * 256 + 255), so every receiver's pair list runs by increasing
+// caller index of the source: the order in which the Monte-Carlo solver's reservoir streams
+// a receiver's candidates.  Returns the internal index (n past the end).
+__device__ __forceinline__ int pair_source(const SceneDev &sc, int n, int jc) { return jc < n ? __ldg(&sc.inv[jc]) : n; }
 
 __device__ __forceinline__ float3 unit_dir(float3 dv, float &r) {
     r = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
@@ -93,7 +106,7 @@ __device__ __forceinline__ bool pair_occluder(const SceneDev &sc, int k, int i, 
 __global__ void __launch_bounds__(PCH) k_pair_count(SceneDev sc, int n, int chunks, int *chunk_cnt, int *src_cnt) {
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
-    const int j = c * PCH + threadIdx.x;
+    const int j = pair_source(sc, n, c * PCH + threadIdx.x);
     const float eps = *sc.eps_plane;
     const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
     float3 dv;
@@ -109,7 +122,7 @@ __global__ void __launch_bounds__(PCH) k_pair_fill(SceneDev sc, int n, int chunk
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
-    const int j = c * PCH + threadIdx.x;
+    const int j = pair_source(sc, n, c * PCH + threadIdx.x);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float eps = *sc.eps_plane;
     const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
-    const int j = c * PCH + threadIdx.x;
+    const int j = pair_source(sc, n, c * PCH + threadIdx.x);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float eps = *sc.eps_plane;
     const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
@@ -537,6 +550,7 @@ rgs_status rgs_trace_pairs_impl(rgs_transport *t, const rgs_lights *L, const flo
     rgs_status r;
     t->kind = RGS_KIND_PAIRS;
     rgs_tc_invalidate(t);
+    rgs_mc_free(t);
     t->tc_used = false;
     t->nd = 0;
     if ((r = rgs_transport_common(t, L, st)) != RGS_OK) return r;
@@ -622,6 +636,16 @@ template rgs_status pairs_bounce<9>(const rgs_transport *, bool, const float *, 
                                     float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
 template rgs_status pairs_bounce<16>(const rgs_transport *, bool, const float *, const __nv_bfloat16 *, const float *,
                                      float *, float *, __nv_bfloat16 *, double *, cudaStream_t);
+
+// the transposed pair index: for every source j its entries (receiver i, bits of V_ji) at
+// src_off[j] .. src_off[j+1] of tr (entry order within a source unspecified)
+rgs_status rgs_pairs_transpose(rgs_transport *t, int2 *tr, cudaStream_t st) {
+    const int n = t->n;
+    { ProfScope ps_("k_copy_off", st); rgs_copy_offsets(t->src_off, t->cursor, n, st); }
+    { ProfScope ps_("k_pair_src_fill", st); k_pair_src_fill<<<n, 256, 0, st>>>(n, t->pair_off, t->pair_rec, t->cursor, tr); }
+    RGS_LAUNCH("pair transposed index");
+    return RGS_OK;
+}
 
 namespace {
 struct GeoAcc : RgsGeoAcc { // with the pairs' directional derivatives (all or none)
@@ -712,9 +736,7 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
         RGS_CUDA(cudaMemsetAsync(geo.ds, 0, sizeof(float) * n * 2, st));
         RGS_CUDA(cudaMemsetAsync(geo.gF, 0, sizeof(float) * n * 9, st));
     }
-    { ProfScope ps_("k_copy_off", st); rgs_copy_offsets(t->src_off, t->cursor, n, st); }
-    { ProfScope ps_("k_pair_src_fill", st); k_pair_src_fill<<<n, 256, 0, st>>>(n, t->pair_off, t->pair_rec, t->cursor, t->tr); }
-    RGS_LAUNCH("pair transposed index");
+    if ((r = rgs_pairs_transpose(t, t->tr, st)) != RGS_OK) return r;
     RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));
     switch (t->nc) {
     case 1: r = run_adjoint_pairs<1>(t, g, dE, dad, dop, dlam_acc, geo, st); break;

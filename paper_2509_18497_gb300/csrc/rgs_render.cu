@@ -35,71 +35,113 @@ struct Cam {
     float v[9];
 };
 
-__global__ void __launch_bounds__(RN_THREADS) k_render_trace(SceneDev sc, Cam cam, int W, int H, float fov,
-                                                            int2 *rec, int *cnt, float4 *pdir, int *flags) {
-    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= W * H) return;
-    const int x = pix % W, y = pix / W;
-    const float3 o = make_float3(cam.v[0], cam.v[1], cam.v[2]);
-    const float3 d = pixel_dir(cam.v, W, H, fov, x, y);
-    pdir[pix] = make_float4(d.x, d.y, d.z, 0.f);
-    const float eps = *sc.eps_plane;
+// The composited hits of one pixel ray, nearest first: emit(h, j, a_h) for h = 0, 1, ...
+// until the transmittance falls below RGS_T_EPS.  Hits are gathered RGS_HMAX at a time: each
+// pass keeps the RGS_HMAX nearest hits beyond the previous pass's last composited one, so a
+// ray composites any number of hits.  A full buffer's last run of near-equal depths may
+// continue past the buffer, so it is left to the next pass (a run is never split, unless one
+// run alone fills the buffer).  Returns false if the traversal stack overflowed.
+template <class F>
+__device__ bool render_ray(const SceneDev &sc, float3 o, float3 d, float eps, F &&emit) {
     unsigned long long key[RGS_HMAX];
-    int nh = 0;
-    auto visit = [&](int j) {
-        float t, r2;
-        if (!hit_surfel_t(sc, j, -1, o, d, INFINITY, eps, t, r2)) return;
-        const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)j;
-        if (nh < RGS_HMAX) {
-            key[nh++] = k;
-            return;
-        }
-        int far = 0; // keep the RGS_HMAX nearest
-        for (int m = 1; m < RGS_HMAX; ++m)
-            if (key[m] > key[far]) far = m;
-        if (k < key[far]) key[far] = k;
-    };
-    if (!bvh_traverse_ordered(sc, o, d, visit)) atomicAdd(&flags[FLAG_STACK], 1);
-    for (int a = 1; a < nh; ++a) { // depth order
-        const unsigned long long k = key[a];
-        int b = a - 1;
-        while (b >= 0 && key[b] > k) {
-            key[b + 1] = key[b];
-            --b;
-        }
-        key[b + 1] = k;
-    }
-    for (int k0 = 0; k0 < nh;) { // runs of near-equal depth by caller index
-        int e = k0;
-        float te = __uint_as_float((unsigned)(key[e] >> 32));
-        while (e + 1 < nh) {
-            const float tn = __uint_as_float((unsigned)(key[e + 1] >> 32));
-            if (tn - te > 1e-6f * fmaxf(1.f, te)) break;
-            ++e;
-            te = tn;
-        }
-        for (int a = k0 + 1; a <= e; ++a) {
+    unsigned long long lower = 0ull;
+    bool have_lower = false, ok = true;
+    float T = 1.f;
+    int out = 0;
+    while (true) {
+        int nh = 0;
+        auto visit = [&](int j) {
+            float t, r2;
+            if (!hit_surfel_t(sc, j, -1, o, d, INFINITY, eps, t, r2)) return;
+            const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)j;
+            if (have_lower && k <= lower) return;
+            if (nh < RGS_HMAX) {
+                key[nh++] = k;
+                return;
+            }
+            int far = 0; // keep the RGS_HMAX nearest
+            for (int m = 1; m < RGS_HMAX; ++m)
+                if (key[m] > key[far]) far = m;
+            if (k < key[far]) key[far] = k;
+        };
+        ok = bvh_traverse_ordered(sc, o, d, visit) && ok;
+        for (int a = 1; a < nh; ++a) { // depth order
             const unsigned long long k = key[a];
-            const int uk = sc.uid[(int)(unsigned)k];
             int b = a - 1;
-            while (b >= k0 && sc.uid[(int)(unsigned)key[b]] > uk) {
+            while (b >= 0 && key[b] > k) {
                 key[b + 1] = key[b];
                 --b;
             }
             key[b + 1] = k;
         }
-        k0 = e + 1;
+        auto tkey = [&](int m) { return __uint_as_float((unsigned)(key[m] >> 32)); };
+        auto same_run = [&](int m) { // hit m + 1 continues the run of hit m
+            const float tm = tkey(m);
+            return tkey(m + 1) - tm <= 1e-6f * fmaxf(1.f, tm);
+        };
+        const bool full = nh == RGS_HMAX;
+        int limit = nh;
+        if (full) {
+            int s0 = nh - 1;
+            while (s0 > 0 && same_run(s0 - 1)) --s0;
+            if (s0 > 0) limit = s0;
+        }
+        for (int k0 = 0; k0 < limit;) { // runs of near-equal depth by caller index
+            int e = k0;
+            while (e + 1 < limit && same_run(e)) ++e;
+            for (int a = k0 + 1; a <= e; ++a) {
+                const unsigned long long k = key[a];
+                const int uk = sc.uid[(int)(unsigned)k];
+                int b = a - 1;
+                while (b >= k0 && sc.uid[(int)(unsigned)key[b]] > uk) {
+                    key[b + 1] = key[b];
+                    --b;
+                }
+                key[b + 1] = k;
+            }
+            k0 = e + 1;
+        }
+        unsigned long long last = 0ull;
+        for (int h = 0; h < limit && T >= RGS_T_EPS; ++h) {
+            const int j = (int)(unsigned)key[h];
+            const float G = surfel_G(sc, surfel_r2(sc, j, o, d, tkey(h)));
+            const float alpha = alpha_of(sc, __ldg(&sc.P[j].w), G);
+            emit(out++, j, alpha * T);
+            T *= 1.f - alpha;
+            last = max(last, key[h]);
+        }
+        if (!full || T < RGS_T_EPS) break;
+        lower = last; // every key up to the composited ones (the run order may differ from key order)
+        have_lower = true;
     }
-    float T = 1.f;
-    int kept = 0;
-    for (; kept < nh && T >= RGS_T_EPS; ++kept) {
-        const int j = (int)(unsigned)key[kept];
-        const float G = surfel_G(sc, surfel_r2(sc, j, o, d, __uint_as_float((unsigned)(key[kept] >> 32))));
-        const float alpha = alpha_of(sc, __ldg(&sc.P[j].w), G);
-        rec[(size_t)pix * RGS_HMAX + kept] = make_int2(j, __float_as_int(alpha * T));
-        T *= 1.f - alpha;
+    return ok;
+}
+
+// pass 0 counts every pixel's composited hits; pass 1 writes them (j, a_h) at the pixel's offset
+template <bool FILL>
+__global__ void __launch_bounds__(RN_THREADS) k_render_trace(SceneDev sc, Cam cam, int W, int H, float fov,
+                                                            int *cnt, const long long *__restrict__ off, int2 *rec,
+                                                            float4 *pdir, int *flags) {
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= W * H) return;
+    const int x = pix % W, y = pix / W;
+    const float3 o = make_float3(cam.v[0], cam.v[1], cam.v[2]);
+    const float3 d = pixel_dir(cam.v, W, H, fov, x, y);
+    const float eps = *sc.eps_plane;
+    int n = 0;
+    bool ok;
+    if (FILL) {
+        int2 *r = rec + off[pix];
+        ok = render_ray(sc, o, d, eps, [&](int h, int j, float a) {
+            r[h] = make_int2(j, __float_as_int(a));
+            n = h + 1;
+        });
+    } else {
+        ok = render_ray(sc, o, d, eps, [&](int h, int, float) { n = h + 1; });
+        pdir[pix] = make_float4(d.x, d.y, d.z, 0.f);
+        cnt[pix] = n;
     }
-    cnt[pix] = kept;
+    if (!ok && !FILL) atomicAdd(&flags[FLAG_STACK], 1);
 }
 
 // internal [N][C][NC] <- user [N][nc][C]
@@ -127,7 +169,7 @@ __global__ void k_render_to_user(int n, int C, const int *__restrict__ uid, cons
 
 template <int NC>
 __global__ void __launch_bounds__(RN_THREADS) k_render_shade(int npix, int C, const int2 *__restrict__ rec,
-                                                            const int *__restrict__ cnt, const float4 *__restrict__ pdir,
+                                                            const long long *__restrict__ off, const float4 *__restrict__ pdir,
                                                             const float *__restrict__ B, float *img) {
     const int pix = (int)(((size_t)blockIdx.x * RN_THREADS + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -135,11 +177,11 @@ __global__ void __launch_bounds__(RN_THREADS) k_render_shade(int npix, int C, co
     const float4 d4 = pdir[pix];
     float Yo[NC];
     sh_eval<NC>(make_float3(-d4.x, -d4.y, -d4.z), Yo);
-    const int nh = cnt[pix];
+    const long long h0 = off[pix], h1 = off[pix + 1];
     for (int c = lane; c < C; c += 32) {
         float acc = 0.f;
-        for (int h = 0; h < nh; ++h) {
-            const int2 ja = __ldg(&rec[(size_t)pix * RGS_HMAX + h]);
+        for (long long h = h0; h < h1; ++h) {
+            const int2 ja = __ldg(&rec[h]);
             const float *row = B + ((size_t)ja.x * C + c) * NC;
             float s = 0.f;
 #pragma unroll
@@ -152,7 +194,7 @@ __global__ void __launch_bounds__(RN_THREADS) k_render_shade(int npix, int C, co
 
 template <int NC>
 __global__ void __launch_bounds__(RN_THREADS) k_render_adj(int npix, int C, const int2 *__restrict__ rec,
-                                                          const int *__restrict__ cnt, const float4 *__restrict__ pdir,
+                                                          const long long *__restrict__ off, const float4 *__restrict__ pdir,
                                                           const float *__restrict__ dimg, float *dB) {
     const int pix = (int)(((size_t)blockIdx.x * RN_THREADS + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -160,12 +202,12 @@ __global__ void __launch_bounds__(RN_THREADS) k_render_adj(int npix, int C, cons
     const float4 d4 = pdir[pix];
     float Yo[NC];
     sh_eval<NC>(make_float3(-d4.x, -d4.y, -d4.z), Yo);
-    const int nh = cnt[pix];
+    const long long h0 = off[pix], h1 = off[pix + 1];
     for (int c = lane; c < C; c += 32) {
         const float g = dimg[(size_t)pix * C + c];
         if (g == 0.f) continue;
-        for (int h = 0; h < nh; ++h) {
-            const int2 ja = __ldg(&rec[(size_t)pix * RGS_HMAX + h]);
+        for (long long h = h0; h < h1; ++h) {
+            const int2 ja = __ldg(&rec[h]);
             const float ga = __int_as_float(ja.y) * g;
             float *row = dB + ((size_t)ja.x * C + c) * NC;
 #pragma unroll
@@ -178,6 +220,7 @@ struct RenderScratch {
     cudaStream_t st;
     int2 *rec = nullptr;
     int *cnt = nullptr;
+    long long *off = nullptr, *scan_tmp = nullptr;
     float4 *pdir = nullptr;
     float *X = nullptr;
     int *flag = nullptr;
@@ -185,6 +228,8 @@ struct RenderScratch {
         pool_release(flag, st);
         pool_release(rec, st);
         pool_release(cnt, st);
+        pool_release(off, st);
+        pool_release(scan_tmp, st);
         pool_release(pdir, st);
         pool_release(X, st);
     }
@@ -212,30 +257,43 @@ rgs_status check_args(const rgs_transport *t, const float *in, const float *cam,
     return RGS_OK;
 }
 
-// traces every pixel into pooled scratch (records, counts, directions)
+// traces every pixel twice into pooled scratch: the counts (and directions), their offsets,
+// then the exactly sized records
 rgs_status render_trace(rgs_transport *t, const float *cam, int W, int H, float fov, RenderScratch &s) {
     rgs_status r;
     const int npix = W * H;
-    if ((r = pool_alloc(&s.rec, (size_t)npix * RGS_HMAX, s.st)) != RGS_OK) return r;
+    const int tmp_cap = rgs_scan_tmp_size(npix);
     if ((r = pool_alloc(&s.cnt, (size_t)npix, s.st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&s.off, (size_t)npix + 1, s.st)) != RGS_OK) return r;
+    if ((r = pool_alloc(&s.scan_tmp, (size_t)tmp_cap, s.st)) != RGS_OK) return r;
     if ((r = pool_alloc(&s.pdir, (size_t)npix, s.st)) != RGS_OK) return r;
     if ((r = pool_alloc(&s.flag, (size_t)FLAG_COUNT, s.st)) != RGS_OK) return r;
     RGS_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int) * FLAG_COUNT, s.st));
     Cam c;
     for (int q = 0; q < 9; ++q) c.v[q] = cam[q];
+    const SceneDev sd = t->sc->dev();
+    const unsigned blocks = (npix + RN_THREADS - 1) / RN_THREADS;
     {
         ProfScope ps_("k_render_trace", s.st);
-        k_render_trace<<<(npix + RN_THREADS - 1) / RN_THREADS, RN_THREADS, 0, s.st>>>(t->sc->dev(), c, W, H, fov, s.rec,
-                                                                                      s.cnt, s.pdir, s.flag);
+        k_render_trace<false><<<blocks, RN_THREADS, 0, s.st>>>(sd, c, W, H, fov, s.cnt, nullptr, nullptr, s.pdir, s.flag);
     }
-    RGS_LAUNCH("render trace");
+    RGS_LAUNCH("render trace (count)");
+    if ((r = rgs_scan_counts(s.cnt, s.off, npix, s.scan_tmp, tmp_cap, s.st)) != RGS_OK) return r;
+    long long total = 0;
     int stack_overflows = 0;
+    RGS_CUDA(cudaMemcpyAsync(&total, s.off + npix, sizeof total, cudaMemcpyDeviceToHost, s.st));
     RGS_CUDA(cudaMemcpyAsync(&stack_overflows, s.flag + FLAG_STACK, sizeof(int), cudaMemcpyDeviceToHost, s.st));
     RGS_CUDA(cudaStreamSynchronize(s.st));
     if (stack_overflows) {
         rgs_set_error("render: BVH traversal stack overflow on %d pixel rays", stack_overflows);
         return RGS_ERR_CAPACITY;
     }
+    if ((r = pool_alloc(&s.rec, (size_t)total, s.st)) != RGS_OK) return r;
+    if (total > 0) {
+        ProfScope ps_("k_render_trace", s.st);
+        k_render_trace<true><<<blocks, RN_THREADS, 0, s.st>>>(sd, c, W, H, fov, nullptr, s.off, s.rec, nullptr, s.flag);
+    }
+    RGS_LAUNCH("render trace (fill)");
     return RGS_OK;
 }
 
@@ -256,7 +314,7 @@ rgs_status render_nc(rgs_transport *t, const float *B, const float *cam, int W, 
     {
         ProfScope ps_("k_render_shade", st);
         k_render_shade<NC><<<(unsigned)(((size_t)npix * 32 + RN_THREADS - 1) / RN_THREADS), RN_THREADS, 0, st>>>(
-            npix, t->C, s.rec, s.cnt, s.pdir, s.X, img);
+            npix, t->C, s.rec, s.off, s.pdir, s.X, img);
     }
     RGS_LAUNCH("render shade");
     return RGS_OK;
@@ -275,7 +333,7 @@ rgs_status render_adjoint_nc(rgs_transport *t, const float *dimg, const float *c
     {
         ProfScope ps_("k_render_adj", st);
         k_render_adj<NC><<<(unsigned)(((size_t)npix * 32 + RN_THREADS - 1) / RN_THREADS), RN_THREADS, 0, st>>>(
-            npix, t->C, s.rec, s.cnt, s.pdir, dimg, s.X);
+            npix, t->C, s.rec, s.off, s.pdir, dimg, s.X);
     }
     RGS_LAUNCH("render adjoint");
     {

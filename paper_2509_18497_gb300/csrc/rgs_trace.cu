@@ -251,6 +251,7 @@ rgs_status rgs_trace_impl(rgs_transport *t, const rgs_lights *L, const rgs_trace
     rgs_status r;
     t->kind = RGS_KIND_HEMISPHERE;
     rgs_tc_invalidate(t);
+    rgs_mc_free(t);
     t->tc_used = false;
     t->nd = o->nd;
     t->na = strata_a(o->nd);

@@ -23,6 +23,8 @@ RGS_FP32, RGS_BF16_FP32ACC, RGS_BF16_FP32ACC_RESCORR = 0, 1, 2
 
 STATUS = {0: "RGS_OK", 1: "RGS_ERR_ARG", 2: "RGS_ERR_CUDA", 3: "RGS_ERR_OOM", 4: "RGS_ERR_CAPACITY",
           5: "RGS_ERR_NONFINITE", 6: "RGS_ERR_TIMEOUT", 7: "RGS_ERR_STATE"}
+(RGS_OK, RGS_ERR_ARG, RGS_ERR_CUDA, RGS_ERR_OOM, RGS_ERR_CAPACITY, RGS_ERR_NONFINITE, RGS_ERR_TIMEOUT,
+ RGS_ERR_STATE) = range(8)
 
 # names exported by librgs.so, as declared in include/rgs.h
 EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
@@ -31,6 +33,7 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
            "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_set_tensor_cores",
            "rgs_set_wait_limit", "rgs_contraction_info", "rgs_render", "rgs_render_adjoint",
+           "rgs_mc_solve", "rgs_mc_estimate", "rgs_mc_groups", "rgs_prog_refine",
            "rgs_trace_pairs",
            "rgs_adjoint_pairs", "rgs_adjoint_pairs_geometry", "rgs_adjoint_geometry")
 
@@ -143,6 +146,14 @@ def load(path=LIB_PATH):
     L.rgs_render.restype = ct.c_int
     L.rgs_render_adjoint.argtypes = [vp, vp, ct.POINTER(ct.c_float), ct.c_int32, ct.c_int32, ct.c_float, vp, vp]
     L.rgs_render_adjoint.restype = ct.c_int
+    L.rgs_mc_solve.argtypes = [vp, vp, vp, ct.c_int32, ct.c_uint64, ct.c_int32, vp, vp, vp]
+    L.rgs_mc_solve.restype = ct.c_int
+    L.rgs_mc_estimate.argtypes = [vp, vp, vp, ct.c_uint64, ct.c_int32, ct.c_int32, ct.c_int32, vp, vp, vp, vp, vp]
+    L.rgs_mc_estimate.restype = ct.c_int
+    L.rgs_prog_refine.argtypes = [vp, vp, ct.c_int32, vp, vp, vp]
+    L.rgs_prog_refine.restype = ct.c_int
+    L.rgs_mc_groups.argtypes = [vp, ct.c_int32, vp, vp]
+    L.rgs_mc_groups.restype = ct.c_int
     L.rgs_trim_workspace.argtypes = []
     L.rgs_trim_workspace.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
@@ -423,6 +434,68 @@ def rgs_render_adjoint(transport, dimg, cam, W, H, fov, dB_out=None, stream=None
         _check(load().rgs_render_adjoint(transport.h, pd, _cam9(cam), int(W), int(H), float(fov), pdB,
                                          _stream(stream)))
     return dB
+
+
+def _opt_dev(t, shape, name):
+    return ct.c_void_p(None) if t is None else _dev(t, shape, name)
+
+
+def rgs_mc_solve(transport, steps, seed=0, E=None, S=None, groups=0, B_out=None, visits=True, stream=None):
+    """Alg. 1's Monte-Carlo TD(0) solver on a center-to-center transport: (B [N][nc][C],
+    visits [N] or None), both device float32."""
+    n, nc, C = transport.n, transport.nc, transport.C
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = torch.empty((n, nc, C), dtype=torch.float32, device=dev) if B_out is None else B_out
+    pB = _dev(B, (n, nc, C), "B_out")
+    V = torch.empty(n, dtype=torch.float32, device=B.device) if visits else None
+    with torch.cuda.device(B.device):
+        _check(load().rgs_mc_solve(transport.h, _opt_dev(E, (n, nc, 3), "E"), _opt_dev(S, (n, nc, C), "S"),
+                                   int(steps), ct.c_uint64(seed), int(groups), pB,
+                                   _opt_dev(V, (n,), "visits"), _stream(stream)))
+    return B, V
+
+
+def rgs_mc_estimate(transport, Bhat, seed, step, recv=None, n_draws=None, E=None, groups=0, stream=None):
+    """One step's next-event estimates for the means Bhat: (pick int64 [q], p float64 [q],
+    delta float32 [q][nc][C]); receivers recv (int32 device, caller indices) or 0..n_draws-1."""
+    n, nc, C = transport.n, transport.nc, transport.C
+    pBh = _dev(Bhat, (n, nc, C), "Bhat")
+    dev = Bhat.device
+    if recv is not None:
+        if not (isinstance(recv, torch.Tensor) and recv.is_cuda and recv.dtype == torch.int32 and recv.is_contiguous()):
+            raise TypeError("recv: expected a contiguous int32 CUDA tensor")
+        q = recv.numel()
+    else:
+        q = n if n_draws is None else int(n_draws)
+    pick = torch.empty(q, dtype=torch.int64, device=dev)
+    p = torch.empty(q, dtype=torch.float64, device=dev)
+    delta = torch.empty((q, nc, C), dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(load().rgs_mc_estimate(transport.h, _opt_dev(E, (n, nc, 3), "E"), pBh, ct.c_uint64(seed), int(step),
+                                      int(groups), int(q),
+                                      ct.c_void_p(recv.data_ptr()) if recv is not None else ct.c_void_p(None),
+                                      ct.c_void_p(pick.data_ptr()), ct.c_void_p(p.data_ptr()),
+                                      ct.c_void_p(delta.data_ptr()), _stream(stream)))
+    return pick, p, delta
+
+
+def rgs_prog_refine(transport, shots, E=None, stream=None):
+    """Progressive refinement with `shots` shots: (Bhat, unshot dB), device float32 [N][nc][C]."""
+    n, nc, C = transport.n, transport.nc, transport.C
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Bh = torch.empty((n, nc, C), dtype=torch.float32, device=dev)
+    dB = torch.empty((n, nc, C), dtype=torch.float32, device=dev)
+    _check(load().rgs_prog_refine(transport.h, _opt_dev(E, (n, nc, 3), "E"), int(shots), _dev(Bh, (n, nc, C), "Bhat"),
+                                  _dev(dB, (n, nc, C), "dB"), _stream(stream)))
+    return Bh, dB
+
+
+def rgs_mc_groups(transport, groups, stream=None):
+    """The K-means group (int32, caller order) of every surfel, as the grouped proposal uses them."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty(transport.n, dtype=torch.int32, device=dev)
+    _check(load().rgs_mc_groups(transport.h, int(groups), ct.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
 
 
 def rgs_trim_workspace():

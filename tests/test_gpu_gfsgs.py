@@ -24,15 +24,17 @@ def _lib():
     build.build()
 
 
-def _gfsgs(sc, seed):
+def _gfsgs(sc, seed, lo=1.0, hi=5.0):
     out = dict(sc)
-    out["o"] = np.random.default_rng(seed).uniform(1.0, 5.0, sc["n"]).astype(np.float32).astype(np.float64)
+    out["o"] = np.random.default_rng(seed).uniform(lo, hi, sc["n"]).astype(np.float32).astype(np.float64)
     return out
 
 
-@pytest.mark.parametrize("pairs", [False, True])
-def test_gfsgs_matches_oracle(pairs):
-    sc = _gfsgs(scenes.with_emission(scenes.fruit_bowl(n=1500, L=2, nd=64, nb=3, n_lights=2), seed=3), 4)
+# g in [1, 5] puts Ein's argument 0.03279 g^3.4 in [0.033, 7.8]; [0.4, 9] in [0.0014, 58]:
+# both branches of the GPU's FP32 Ein (its power series up to 2, ln x + gamma + E1(x) beyond)
+@pytest.mark.parametrize("pairs,g_range", [(False, (1.0, 5.0)), (True, (1.0, 5.0)), (True, (0.4, 9.0))])
+def test_gfsgs_matches_oracle(pairs, g_range):
+    sc = _gfsgs(scenes.with_emission(scenes.fruit_bowl(n=1500, L=2, nd=64, nb=3, n_lights=2), seed=3), 4, *g_range)
     if pairs:
         sc["lam"] = np.random.default_rng(6).uniform(0.5, 1.5, sc["n"]).astype(np.float32).astype(np.float64)
     W = np.random.default_rng(5).normal(size=(sc["n"], 9, 6))

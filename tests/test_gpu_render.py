@@ -99,7 +99,7 @@ def test_render_of_a_hundred_light_radiance():
 def test_render_degenerate_images():
     """One pixel; a camera looking away from the scene (every pixel 0, dL/dB 0); a rejected
     field of view and a non-finite camera leave the outputs untouched."""
-    sc = scenes.fruit_bowl(n=997, L=1, nd=16, nb=1, n_lights=1)
+    sc = scenes.fruit_bowl(n=997, L=1, nd=32, nb=1, n_lights=1)
     pipe, orc = _pair(sc, rgs.RGS_ALPHA_GAUSS, O.ALPHA_GAUSS)
     rng = np.random.default_rng(7)
     B = rng.normal(size=(sc["n"], 4, orc.C))
