@@ -375,21 +375,18 @@ __global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int
     float3 gpi = make_float3(0.f, 0.f, 0.f), gd = make_float3(0.f, 0.f, 0.f);
     if (cnt > 0 && nb > 0) {
         const long long base = rays.off[r];
-        float Th[RGS_HMAX];
-        float T = 1.f;
-        for (int h = 0; h < cnt; ++h) {
-            const int j = __ldg(&rays.rec_ja[base + h]).x;
-            Th[h] = T;
-            T *= 1.f - alpha_of(sc, __ldg(&sc.P[j].w), stored_hit_G(sc, j, o, d));
-        }
         float R = 0.f;
         for (int h = cnt - 1; h >= 0; --h) {
-            const int j = __ldg(&rays.rec_ja[base + h]).x;
+            const int2 ja = __ldg(&rays.rec_ja[base + h]);
+            const int j = ja.x;
             const float G = stored_hit_G(sc, j, o, d);
             const float oj = __ldg(&sc.P[j].w);
             const float al = alpha_of(sc, oj, G);
             const float g = gh[base + h];
-            const float coef = Th[h] * (g - R) * dalpha_dq(sc, oj, G);
+            // the transmittance in front of the hit from its stored weight a_h = alpha_h T_h
+            // (alpha_h = 0 makes dalpha/dq vanish too)
+            const float Th = al > 0.f ? __int_as_float(ja.y) / al : 0.f;
+            const float coef = Th * (g - R) * dalpha_dq(sc, oj, G);
             if (coef != 0.f) {
                 const float4 Nj = __ldg(&sc.N4[j]), Pj = __ldg(&sc.P[j]);
                 const float t = (Nj.x * (Pj.x - o.x) + Nj.y * (Pj.y - o.y) + Nj.z * (Pj.z - o.z)) /
