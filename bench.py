@@ -649,7 +649,8 @@ def main():
                                  "plain_ms_per_step": sum(step_ms_p) / len(step_ms_p),
                                  "batched_ms_per_step": sum(step_ms_b) / len(step_ms_b),
                                  "plain_steps": len(step_ms_p), "plain_warmup": 1 if heavy else max(args.warmup, 3),
-                                 "batched_launch": batched_launch},
+                                 "batched_launch": batched_launch,
+                                 "batch_plan": rgs.rgs_batch_last_plan() if batched_launch == "batched" else None},
             "roofline": roofline, "trace": trace, "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clk, "wall_s_timed": t_wall, "kernels": kernels}

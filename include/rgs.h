@@ -314,6 +314,18 @@ rgs_status rgs_solve_batched(rgs_transport *const *ts, int32_t count, const floa
                              const int32_t *n_bounces, const rgs_batch_opts *opts, float *const *B_out,
                              double *residual_norms, void *stream);
 
+/* The plan of the last rgs_solve_batched call (host-only, no device work): writes up to n
+ * values to out and returns how many there are (-1 if no batched solve ran yet, or out is
+ * NULL with n > 0).  Layout: [0] persistent blocks, [1] the kernel instance (2 or 3 resident
+ * blocks per SM), [2] 1 if the plan was autotuned, [3] the number of buckets K (scenes with
+ * equal nc, C and rays per surfel), then per bucket seven values: nc, C, rays per surfel,
+ * the item-shape policy of its BF16-row and of its FP32-row levels (0 = 3-column items,
+ * 1 = the measured crossover, 2 = 32-column items from 6 columns) and the item widths they
+ * give (3 or 32 columns).  The autotuner times bounce level 1 for one policy shared by every
+ * bucket with either kernel instance, then each bucket's policy in turn with the others
+ * held, and in the corrected mode the same for the FP32-row level. */
+int32_t rgs_batch_last_plan(int32_t *out, int32_t n);
+
 /* Copies iterate B^(b) (0 <= b <= last n_bounces) of the last rgs_solve to the device
  * array out [N][nc][C].  An iterate that a checkpointed solve did not keep is recomputed
  * from the checkpoint below it (bit-identical to the solve's value) in pooled scratch.

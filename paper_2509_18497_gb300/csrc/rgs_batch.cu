@@ -10,6 +10,7 @@
 // kernel instead of hanging.  The launches of a batch are captured once into a CUDA graph
 // and replayed on later calls with the same arguments; the number of resident blocks per
 // SM is chosen by timing the candidates on the first call (autotuning).
+#include <array>
 #include <map>
 #include <memory>
 #include <type_traits>
@@ -149,9 +150,13 @@ struct Plan {
     int maxnb = 0, count = 0;
     int blocks = 0;         // persistent grid size (autotuned)
     int minb = 3;           // kernel instance: registers for 2 or 3 resident blocks per SM (autotuned)
-    int pol16 = 1, pol32 = 1; // item-shape policy of the BF16-row and FP32-row levels (autotuned):
-                              // 0 = 3-column items, 1 = wide_bounce's choice, 2 = 32-column items
-                              // wherever C >= kWideMinCols
+    // item-shape policy of the BF16-row and FP32-row levels per bucket of scenes with equal
+    // (nc, C, rays per surfel) (autotuned): 0 = 3-column items, 1 = wide_bounce's choice,
+    // 2 = 32-column items wherever C >= kWideMinCols
+    std::vector<int> bucket;            // per scene
+    std::vector<std::array<int, 3>> bkey; // per bucket: nc, C, rays per surfel
+    std::vector<int> pol16, pol32;      // per bucket
+    bool tuned = false;
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
     ~Plan() {
@@ -166,6 +171,26 @@ struct Plan {
 
 std::mutex g_plan_mu;
 std::map<std::vector<const void *>, Plan *> g_plans;
+bool policy_wide(int pol, int C, bool rows16);
+std::vector<int32_t> g_last_plan; // the plan of the last rgs_solve_batched call (rgs_batch_last_plan)
+
+void note_plan(const Plan &P) {
+    g_last_plan.clear();
+    g_last_plan.push_back(P.blocks);
+    g_last_plan.push_back(P.minb);
+    g_last_plan.push_back(P.tuned ? 1 : 0);
+    g_last_plan.push_back((int32_t)P.bkey.size());
+    for (size_t k = 0; k < P.bkey.size(); ++k) {
+        const int C = P.bkey[k][1];
+        g_last_plan.push_back(P.bkey[k][0]);
+        g_last_plan.push_back(C);
+        g_last_plan.push_back(P.bkey[k][2]);
+        g_last_plan.push_back(P.pol16[k]);
+        g_last_plan.push_back(P.pol32[k]);
+        g_last_plan.push_back(policy_wide(P.pol16[k], C, true) ? 32 : 3);
+        g_last_plan.push_back(policy_wide(P.pol32[k], C, false) ? 32 : 3);
+    }
+}
 
 template <int NC>
 void enqueue_make_S(rgs_transport *t, const float *E, cudaStream_t st, bool bf16);
@@ -181,9 +206,10 @@ bool policy_wide(int pol, int C, bool rows16) {
 // their upload
 rgs_status upload_shape(Plan &P, cudaStream_t st, bool force32 = false) {
     const int count = P.count;
-    for (auto &b : P.host) {
-        b.wide16 = policy_wide(P.pol16, b.C, true) ? 1 : 0;
-        b.wide32 = policy_wide(P.pol32, b.C, false) ? 1 : 0;
+    for (int s = 0; s < count; ++s) {
+        BatchSceneDev &b = P.host[s];
+        b.wide16 = policy_wide(P.pol16[P.bucket[s]], b.C, true) ? 1 : 0;
+        b.wide32 = policy_wide(P.pol32[P.bucket[s]], b.C, false) ? 1 : 0;
         b.tiles16 = b.wide16 ? (b.C + 31) / 32 : b.C / 3;
         b.tiles32 = b.wide32 ? (b.C + 31) / 32 : b.C / 3;
     }
@@ -366,7 +392,15 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
             b.A16 = (long long)t->n * t->C * (t->nc >= 9 ? 16 : t->nc);
             b.norm2 = t->norm2;
             P->host.push_back(b);
+            const std::array<int, 3> bk = {t->nc, t->C, t->nd};
+            int k = 0;
+            while (k < (int)P->bkey.size() && P->bkey[k] != bk) ++k;
+            if (k == (int)P->bkey.size()) P->bkey.push_back(bk);
+            P->bucket.push_back(k);
         }
+        const int nbk = (int)P->bkey.size();
+        P->pol16.assign(nbk, 1);
+        P->pol32.assign(nbk, 1);
         if ((r = dev_alloc(&P->d_scenes, (size_t)count)) != RGS_OK) return r;
         if ((r = dev_alloc(&P->d_level_off, (size_t)(P->maxnb + 1) * (count + 1))) != RGS_OK) return r;
         if ((r = dev_alloc(&P->d_counters, (size_t)P->maxnb + 1)) != RGS_OK) return r;
@@ -381,14 +415,16 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
             rgs_set_error("rgs_solve_batched: the persistent kernel cannot be resident");
             return RGS_ERR_CUDA;
         }
-        auto configure = [&](int pol16, int pol32, int minb, bool force32) -> rgs_status {
+        auto configure = [&](const std::vector<int> &pol16, const std::vector<int> &pol32, int minb,
+                             bool force32) -> rgs_status {
             P->pol16 = pol16;
             P->pol32 = pol32;
             P->minb = minb;
             P->blocks = sms * (minb == 2 ? occ2 : occ3);
             return upload_shape(*P, st, force32);
         };
-        if ((r = configure(1, 1, 3, false)) != RGS_OK) return r; // default: the measured crossovers, 3 blocks/SM
+        const std::vector<int> ones(nbk, 1);
+        if ((r = configure(ones, ones, 3, false)) != RGS_OK) return r; // default: the measured crossovers, 3 blocks/SM
         if (autotune && P->maxnb > 0) {
             // Time bounce level 1 per candidate and keep the fastest: first the item-shape policy
             // of the rows level 1 gathers (BF16 in the batched modes) with the kernel occupancy,
@@ -398,7 +434,8 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
             cudaEvent_t e0, e1;
             RGS_CUDA(cudaEventCreate(&e0));
             RGS_CUDA(cudaEventCreate(&e1));
-            auto time_level1 = [&](int pol16, int pol32, int minb, bool force32, float *ms) -> rgs_status {
+            auto time_level1 = [&](const std::vector<int> &pol16, const std::vector<int> &pol32, int minb,
+                                   bool force32, float *ms) -> rgs_status {
                 rgs_status q;
                 if ((q = configure(pol16, pol32, minb, force32)) != RGS_OK) return q;
                 RGS_CUDA(cudaEventRecord(e0, st));
@@ -408,38 +445,67 @@ rgs_status rgs_solve_batched_impl(rgs_transport *const *tsp, int count, const fl
                 RGS_CUDA(cudaEventElapsedTime(ms, e0, e1));
                 return RGS_OK;
             };
+            // 1. one policy for every bucket, with the kernel occupancy; 2. each bucket's policy
+            // in turn with the others held (coordinate descent, when scenes differ in nc, C or
+            // rays per surfel); the level being tuned gathers BF16 rows in the batched modes
             const bool bf16 = precision != RGS_FP32;
+            std::vector<int> p16 = ones, p32 = ones;
+            std::vector<int> &tuned = bf16 ? p16 : p32;
             float best = 1e30f;
             int best_pol = 1, best_minb = 3;
             for (int pol = 0; pol <= 2 && r == RGS_OK; ++pol)
                 for (int minb = 2; minb <= 3 && r == RGS_OK; ++minb) {
                     float ms = 0.f;
-                    r = time_level1(bf16 ? pol : 1, bf16 ? 1 : pol, minb, false, &ms);
+                    std::fill(tuned.begin(), tuned.end(), pol);
+                    r = time_level1(p16, p32, minb, false, &ms);
                     if (r == RGS_OK && ms < best) {
                         best = ms;
                         best_pol = pol;
                         best_minb = minb;
                     }
                 }
-            int pol16 = bf16 ? best_pol : 1, pol32 = bf16 ? 1 : best_pol;
-            if (r == RGS_OK && precision == RGS_BF16_FP32ACC_RESCORR) {
-                float best32 = 1e30f;
-                for (int pol = 0; pol <= 2 && r == RGS_OK; ++pol) {
-                    float ms = 0.f;
-                    r = time_level1(pol16, pol, best_minb, true, &ms);
-                    if (r == RGS_OK && ms < best32) {
-                        best32 = ms;
-                        pol32 = pol;
+            std::fill(tuned.begin(), tuned.end(), best_pol);
+            auto refine = [&](std::vector<int> &pols, bool force32, float &cur) {
+                if (nbk < 2) return;
+                for (int k = 0; k < nbk && r == RGS_OK; ++k) {
+                    const int keep = pols[k];
+                    for (int pol = 0; pol <= 2 && r == RGS_OK; ++pol) {
+                        if (pol == keep) continue;
+                        const int prev = pols[k];
+                        pols[k] = pol;
+                        float ms = 0.f;
+                        r = time_level1(p16, p32, best_minb, force32, &ms);
+                        if (r == RGS_OK && ms < cur) cur = ms;
+                        else pols[k] = prev;
                     }
                 }
+            };
+            refine(tuned, false, best);
+            if (r == RGS_OK && precision == RGS_BF16_FP32ACC_RESCORR) {
+                // the FP32-row level (the corrected bounce), timed as level 1 gathering FP32 rows
+                float best32 = 1e30f;
+                int bp32 = 1;
+                for (int pol = 0; pol <= 2 && r == RGS_OK; ++pol) {
+                    float ms = 0.f;
+                    std::fill(p32.begin(), p32.end(), pol);
+                    r = time_level1(p16, p32, best_minb, true, &ms);
+                    if (r == RGS_OK && ms < best32) {
+                        best32 = ms;
+                        bp32 = pol;
+                    }
+                }
+                std::fill(p32.begin(), p32.end(), bp32);
+                refine(p32, true, best32);
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             if (r != RGS_OK) return r;
-            if ((r = configure(pol16, pol32, best_minb, false)) != RGS_OK) return r;
+            if ((r = configure(p16, p32, best_minb, false)) != RGS_OK) return r;
+            P->tuned = true;
         }
         g_plans[key] = owner.release();
     }
+    note_plan(*P);
     bool launched = false;
     if (use_graph && !P->graph_failed) {
         if (!P->exec) { // capture the core once, on the library's own stream
@@ -515,4 +581,12 @@ void rgs_batch_forget(const rgs_transport *t) {
             ++it;
         }
     }
+}
+
+extern "C" int32_t rgs_batch_last_plan(int32_t *out, int32_t n) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (g_last_plan.empty()) return -1;
+    if (n > 0 && !out) return -1;
+    for (int32_t q = 0; q < n && q < (int32_t)g_last_plan.size(); ++q) out[q] = g_last_plan[q];
+    return (int32_t)g_last_plan.size();
 }

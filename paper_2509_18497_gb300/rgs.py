@@ -33,7 +33,7 @@ EXPORTS = ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint",
            "rgs_last_error", "rgs_abi_version", "rgs_residual_norm_noalloc", "rgs_solve_batched",
            "rgs_set_checkpointing", "rgs_trim_workspace", "rgs_set_memory_budget", "rgs_set_tensor_cores",
            "rgs_set_wait_limit", "rgs_contraction_info", "rgs_render", "rgs_render_adjoint",
-           "rgs_mc_solve", "rgs_mc_estimate", "rgs_mc_groups", "rgs_prog_refine",
+           "rgs_mc_solve", "rgs_mc_estimate", "rgs_mc_groups", "rgs_prog_refine", "rgs_batch_last_plan",
            "rgs_trace_pairs",
            "rgs_adjoint_pairs", "rgs_adjoint_pairs_geometry", "rgs_adjoint_geometry")
 
@@ -154,6 +154,8 @@ def load(path=LIB_PATH):
     L.rgs_prog_refine.restype = ct.c_int
     L.rgs_mc_groups.argtypes = [vp, ct.c_int32, vp, vp]
     L.rgs_mc_groups.restype = ct.c_int
+    L.rgs_batch_last_plan.argtypes = [ct.POINTER(ct.c_int32), ct.c_int32]
+    L.rgs_batch_last_plan.restype = ct.c_int32
     L.rgs_trim_workspace.argtypes = []
     L.rgs_trim_workspace.restype = ct.c_int
     for fn in ("rgs_build_scene", "rgs_trace_transport", "rgs_solve", "rgs_adjoint", "rgs_get_iterate",
@@ -496,6 +498,21 @@ def rgs_mc_groups(transport, groups, stream=None):
     out = torch.empty(transport.n, dtype=torch.int32, device=dev)
     _check(load().rgs_mc_groups(transport.h, int(groups), ct.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+def rgs_batch_last_plan():
+    """The plan of the last rgs_solve_batched call: dict(blocks, blocks_per_sm, autotuned,
+    buckets=[dict(nc, C, rays, policy_bf16, policy_fp32, items_bf16, items_fp32)]), or None."""
+    L = load()
+    m = L.rgs_batch_last_plan(None, 0)
+    if m < 0:
+        return None
+    buf = (ct.c_int32 * m)()
+    L.rgs_batch_last_plan(buf, m)
+    v = list(buf)
+    keys = ("nc", "C", "rays", "policy_bf16", "policy_fp32", "items_bf16", "items_fp32")
+    buckets = [dict(zip(keys, v[4 + 7 * k: 11 + 7 * k])) for k in range(v[3])]
+    return dict(blocks=v[0], blocks_per_sm=v[1], autotuned=bool(v[2]), buckets=buckets)
 
 
 def rgs_trim_workspace():
