@@ -199,6 +199,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
     const uint32_t slot_rows = g.rows_bytes, slot_a = g.a_bytes; // per group of a stage
     const uint32_t a_off = (uint32_t)GPS * slot_rows;            // the operands after the rows
     const uint32_t h_off = a_off + (uint32_t)GPS * slot_a;       // then the hit records
+    // the operands start as zeros: a builder then only clears the rows it wrote last time
+    for (uint32_t q = threadIdx.x; q < (uint32_t)S * (GPS * slot_a / 16u); q += blockDim.x) {
+        const uint32_t s = q / (GPS * slot_a / 16u), w = q - s * (GPS * slot_a / 16u);
+        reinterpret_cast<uint4 *>(smem + (size_t)s * g.stage_bytes + a_off)[w] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    tc::fence_async_smem();
+    __syncthreads();
 
     if (warp < TC_NP) {
         // ---------------------------------------------------------- producers (stage s: warp s mod TC_NP)
@@ -353,6 +360,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
         float cf[20];
 #pragma unroll
         for (int q = 0; q < 20; ++q) cf[q] = sh_tab[k][q];
+        unsigned prev_written = 0u; // rows (tile slots) of this half written by the buffer's last use
         long long su = 0;
         int tl = 0;
         for (int it = blockIdx.x; it < items && !aborted(&abort_flag); it += gridDim.x, ++tl) {
@@ -462,9 +470,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_contract(TcArgs g) {
                         }
                     }
                     if (cur >= 0) flush(cur);
+                    // rows this half wrote in the buffer's last use and not now go back to zero
                     const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-                    for (int p = hf; p < TC_R; p += 2) { // this half's unwritten rows
-                        if (written & (1u << p)) continue;
+                    unsigned stale = prev_written & ~written;
+                    prev_written = written;
+                    while (stale) {
+                        const int p = __ffs(stale) - 1;
+                        stale &= stale - 1;
                         const uint32_t off = tc::blk_off(p * 16 + k, 0);
                         tc::sts128(A + off, z4);
                         tc::sts128(A + off + 128u, z4);
