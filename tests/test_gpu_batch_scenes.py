@@ -53,6 +53,24 @@ def test_batched_scenes_match_oracle_and_single_solves(batch, precision, tol):
         np.testing.assert_allclose(nrm, st["residual_norm"], rtol=1e-4)
 
 
+def test_batch_plan_has_one_bucket_per_scene_shape(batch):
+    """The autotuned plan (rgs_batch_last_plan): one bucket per distinct (nc, C, rays per
+    surfel) of the batch, each with a policy per row precision and the item width it gives."""
+    scs, pipes, ds = batch
+    ts = [p.transport for p in pipes]
+    rgs.rgs_solve_batched(ts, [d["E"] for d in ds], [sc["nb"] for sc in scs],
+                          precision=rgs.RGS_BF16_FP32ACC_RESCORR)
+    plan = rgs.rgs_batch_last_plan()
+    assert plan is not None and plan["autotuned"] and plan["blocks_per_sm"] in (2, 3) and plan["blocks"] > 0
+    shapes = {((L + 1) ** 2, 9, nd) for n, L, nd, nb, seed in SPECS}
+    assert {(b["nc"], b["C"], b["rays"]) for b in plan["buckets"]} == shapes
+    for b in plan["buckets"]:
+        assert b["policy_bf16"] in (0, 1, 2) and b["policy_fp32"] in (0, 1, 2)
+        assert b["items_bf16"] in (3, 32) and b["items_fp32"] in (3, 32)
+        if b["policy_bf16"] == 0:
+            assert b["items_bf16"] == 3
+
+
 def test_adjoint_after_batched_solve(batch):
     scs, pipes, ds = batch
     ts = [p.transport for p in pipes]
