@@ -316,8 +316,9 @@ __global__ void RGS_OPA_LB k_opacity_g(SceneDev sc, RaysDev rays, int C, int col
 }
 
 // Hemisphere rays, part 2: back to front, R_{h-1} = alpha_h g_h + (1 - alpha_h) R_h and
-// dL/do_{j_h} += T_h (g_h - R_h) dalpha_h/do, with T_h the transmittance in front of hit h.
-// G_h is recomputed from the stored direction (bit-identical to the trace's value).
+// dL/do_{j_h} += T_h (g_h - R_h) dalpha_h/do, with T_h the transmittance in front of hit h,
+// T_h = a_h / alpha_h from the stored weight.  G_h is recomputed from the stored direction
+// (bit-identical to the trace's value).
 __global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const float *__restrict__ gh,
                                                      float *dop) {
     // Blocks take the rays in a scattered order (block b -> b * 2654435761 mod gridDim, a
@@ -333,24 +334,20 @@ __global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const flo
     const int i = r / rays.nd;
     const float3 o = f3(sc.P[i]);
     const float3 d = f3(rays.dir[r]);
-    float Th[RGS_HMAX], Gh[RGS_HMAX];
-    float T = 1.f;
-    for (int h = 0; h < cnt; ++h) {
-        const int j = __ldg(&rays.rec_ja[base + h]).x;
-        const float G = stored_hit_G(sc, j, o, d);
-        Th[h] = T;
-        Gh[h] = G;
-        T *= 1.f - alpha_of(sc, __ldg(&sc.P[j].w), G);
-    }
     float R = 0.f;
     for (int h = cnt - 1; h >= 0; --h) {
         const long long slot = base + h;
-        const int j = __ldg(&rays.rec_ja[slot]).x;
-        const float G = Gh[h];
+        const int2 ja = __ldg(&rays.rec_ja[slot]);
+        const int j = ja.x;
+        const float G = stored_hit_G(sc, j, o, d);
         const float oj = __ldg(&sc.P[j].w);
         const float alpha = alpha_of(sc, oj, G);
         const float g = gh[slot];
-        const float da = Th[h] * (g - R);
+        // the transmittance in front of the hit from its stored weight a_h = alpha_h T_h
+        // (alpha_h = 0 makes dalpha/do vanish for the disc and Gaussian models; GFSGS: alpha = 0
+        // only where x = o G = 0, where dalpha/do is 0 too)
+        const float Th = alpha > 0.f ? __int_as_float(ja.y) / alpha : 0.f;
+        const float da = Th * (g - R);
         if (da != 0.f) atomicAdd(&dop[j], da * dalpha_do(sc, oj, G));
         R = alpha * g + (1.f - alpha) * R;
     }
