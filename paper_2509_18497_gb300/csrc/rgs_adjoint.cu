@@ -363,7 +363,10 @@ __global__ void RGS_OPAREC_LB k_opacity_rec(SceneDev sc, RaysDev rays, const flo
 // share their receiver) and added once per warp.  Part 2 is k_hemi_geo_dir.
 __global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int nb, const float *__restrict__ gh,
                                                  float *dp, float *ds, float *gF) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    // scattered block order (as k_opacity_rec): resident blocks hold receivers spread over the
+    // scene, so their per-hit atomics land on sources all over it
+    const unsigned bs = (unsigned)(((unsigned long long)blockIdx.x * 2654435761ull) % gridDim.x);
+    const int r = (int)bs * blockDim.x + threadIdx.x;
     const int n_rays = sc.n * rays.nd;
     if (r - (int)(threadIdx.x & 31) >= n_rays) return; // whole warps (n_rays % 32 == 0)
     const int i = r / rays.nd;

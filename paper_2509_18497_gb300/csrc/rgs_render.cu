@@ -9,7 +9,7 @@
 //                   until the transmittance is below RGS_T_EPS; records (j, a_h) per pixel.
 //  k_render_shade : a warp per pixel, a lane per column: I[c] = sum_h a_h Y(-d)^T B_j[c].
 //  k_render_adj   : a warp per pixel, a lane per column: dB_j[c][k] += a_h Y_k(-d) dI[c].
-#include "rgs_internal.cuh"
+#include "rgs_bounce_body.cuh"
 
 namespace {
 
@@ -178,17 +178,34 @@ __global__ void __launch_bounds__(RN_THREADS) k_render_shade(int npix, int C, co
     float Yo[NC];
     sh_eval<NC>(make_float3(-d4.x, -d4.y, -d4.z), Yo);
     const long long h0 = off[pix], h1 = off[pix + 1];
-    for (int c = lane; c < C; c += 32) {
-        float acc = 0.f;
-        for (long long h = h0; h < h1; ++h) {
-            const int2 ja = __ldg(&rec[h]);
-            const float *row = B + ((size_t)ja.x * C + c) * NC;
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) s += Yo[k] * __ldg(row + k);
-            acc += __int_as_float(ja.y) * s;
+    if constexpr (NC == 16) {
+        // 32-column tiles of each source row read as four contiguous 512-B warp requests, every
+        // lane ending with the dot product of one tile column (TileDot)
+        float ys[4];
+        TileDot<float, 16>::pick(Yo, lane, ys);
+        const int own = TileDot<float, 16>::own(lane);
+        for (int c0 = 0; c0 < C; c0 += 32) {
+            const int ncols = min(32, C - c0);
+            float acc = 0.f;
+            for (long long h = h0; h < h1; ++h) {
+                const int2 ja = __ldg(&rec[h]);
+                acc += __int_as_float(ja.y) * TileDot<float, 16>::dot(B + ((size_t)ja.x * C + c0) * 16, ncols, lane, ys);
+            }
+            if (own < ncols) img[(size_t)pix * C + c0 + own] = acc;
         }
-        img[(size_t)pix * C + c] = acc;
+    } else {
+        for (int c = lane; c < C; c += 32) {
+            float acc = 0.f;
+            for (long long h = h0; h < h1; ++h) {
+                const int2 ja = __ldg(&rec[h]);
+                const float *row = B + ((size_t)ja.x * C + c) * NC;
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) s += Yo[k] * __ldg(row + k);
+                acc += __int_as_float(ja.y) * s;
+            }
+            img[(size_t)pix * C + c] = acc;
+        }
     }
 }
 
