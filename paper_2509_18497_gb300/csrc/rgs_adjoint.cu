@@ -193,9 +193,7 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
         const float f = fall * T;
         gw = make_float3(f * (cs * t3.x + H * n.x), f * (cs * t3.y + H * n.y), f * (cs * t3.z + H * n.z));
         const float3 gn = reflect_grad_n(n, w, (f * cs) * t1) + (H * f) * w; // R_i w and cos = n_i.w
-        atomicAdd(&gF[9 * (size_t)i + 6], gn.x);
-        atomicAdd(&gF[9 * (size_t)i + 7], gn.y);
-        atomicAdd(&gF[9 * (size_t)i + 8], gn.z);
+        geo_add3(gF + GEO_GF * (size_t)i + GEO_N, gn);
     }
     if (qv != 0.f && nzero <= 1) {
         auto pass2 = [&](int j) {
@@ -215,11 +213,9 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
                 const float3 pw = crossing_pw(sc, j, o, w, t, uu, vv);
                 gpi = gpi + coef * pw;
                 gw = gw + (coef * t) * pw;
-                atomicAdd(&dp[3 * j], -coef * pw.x);
-                atomicAdd(&dp[3 * j + 1], -coef * pw.y);
-                atomicAdd(&dp[3 * j + 2], -coef * pw.z);
-                atomicAdd(&ds[2 * j], coef * (-2.f * uu * uu * __ldg(&sc.FU[j].w)));
-                atomicAdd(&ds[2 * j + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[j].w)));
+                geo_add3(dp + GEO_DP * (size_t)j, (-coef) * pw);
+                geo_add2(ds + 2 * (size_t)j, coef * (-2.f * uu * uu * __ldg(&sc.FU[j].w)),
+                         coef * (-2.f * vv * vv * __ldg(&sc.FV[j].w)));
                 occluder_frame_grad(sc, j, o, w, t, uu, vv, coef, gF);
             }
         };
@@ -233,9 +229,7 @@ __global__ void k_shadow_bwd(SceneDev sc, int nl, int ldir, const float *__restr
             gp.y += -(gw.y - w.y * ww) / r - w.y * gr;
             gp.z += -(gw.z - w.z * ww) / r - w.z * gr;
         }
-        atomicAdd(&dp[3 * i], gp.x);
-        atomicAdd(&dp[3 * i + 1], gp.y);
-        atomicAdd(&dp[3 * i + 2], gp.z);
+        geo_add3(dp + GEO_DP * (size_t)i, gp);
     }
 }
 
@@ -395,11 +389,9 @@ __global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int
                 const float3 pw = crossing_pw(sc, j, o, d, t, uu, vv);
                 gpi = gpi + coef * pw;
                 gd = gd + (coef * t) * pw;
-                atomicAdd(&dp[3 * j], -coef * pw.x);
-                atomicAdd(&dp[3 * j + 1], -coef * pw.y);
-                atomicAdd(&dp[3 * j + 2], -coef * pw.z);
-                atomicAdd(&ds[2 * j], coef * (-2.f * uu * uu * __ldg(&sc.FU[j].w)));
-                atomicAdd(&ds[2 * j + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[j].w)));
+                geo_add3(dp + GEO_DP * (size_t)j, (-coef) * pw);
+                geo_add2(ds + 2 * (size_t)j, coef * (-2.f * uu * uu * __ldg(&sc.FU[j].w)),
+                         coef * (-2.f * vv * vv * __ldg(&sc.FV[j].w)));
                 occluder_frame_grad(sc, j, o, d, t, uu, vv, coef, gF);
             }
             R = al * g + (1.f - al) * R;
@@ -417,10 +409,10 @@ __global__ void __launch_bounds__(128) k_hemi_geo(SceneDev sc, RaysDev rays, int
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            if (red[q] != 0.f) atomicAdd(&dp[3 * i + q], red[q]);
+            if (red[q] != 0.f) atomicAdd(&dp[GEO_DP * (size_t)i + q], red[q]);
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-            if (red[3 + q] != 0.f) atomicAdd(&gF[9 * (size_t)i + q], red[3 + q]);
+            if (red[3 + q] != 0.f) atomicAdd(&gF[GEO_GF * (size_t)i + 4 * (q / 3) + q % 3], red[3 + q]);
     }
 }
 
@@ -546,7 +538,7 @@ __global__ void __launch_bounds__(GEO_DIR_THREADS) k_hemi_geo_dir(SceneDev sc, R
     if (threadIdx.x < 9) {
         float v = 0.f;
         for (int w = 0; w < GEO_DIR_THREADS / 32; ++w) v += red[w][threadIdx.x];
-        if (v != 0.f) atomicAdd(&gF[9 * (size_t)i + threadIdx.x], v);
+        if (v != 0.f) atomicAdd(&gF[GEO_GF * (size_t)i + 4 * (threadIdx.x / 3) + threadIdx.x % 3], v);
     }
 }
 
@@ -899,12 +891,12 @@ rgs_status rgs_adjoint_impl(rgs_transport *t, const float *g, float *dE, float *
     if (tcp && ((r = rgs_tc_prepare_adjoint(t, st)) != RGS_OK || (r = rgs_tc_reset_flags(t, st)) != RGS_OK)) return r;
     if (want_geo) {
         RgsGeoAcc &geo = scratch.geo;
-        if ((r = pool_alloc(&geo.dp, (size_t)n * 3, st)) != RGS_OK) return r;
+        if ((r = pool_alloc(&geo.dp, (size_t)n * GEO_DP, st)) != RGS_OK) return r;
         if ((r = pool_alloc(&geo.ds, (size_t)n * 2, st)) != RGS_OK) return r;
-        if ((r = pool_alloc(&geo.gF, (size_t)n * 9, st)) != RGS_OK) return r;
-        RGS_CUDA(cudaMemsetAsync(geo.dp, 0, sizeof(float) * n * 3, st));
+        if ((r = pool_alloc(&geo.gF, (size_t)n * GEO_GF, st)) != RGS_OK) return r;
+        RGS_CUDA(cudaMemsetAsync(geo.dp, 0, sizeof(float) * n * GEO_DP, st));
         RGS_CUDA(cudaMemsetAsync(geo.ds, 0, sizeof(float) * n * 2, st));
-        RGS_CUDA(cudaMemsetAsync(geo.gF, 0, sizeof(float) * n * 9, st));
+        RGS_CUDA(cudaMemsetAsync(geo.gF, 0, sizeof(float) * n * GEO_GF, st));
     }
     const RgsGeoAcc *geop = want_geo ? &scratch.geo : nullptr;
     const int n_v = t->stride ? t->stride + 1 : nb + 1;

@@ -373,6 +373,17 @@ __device__ __forceinline__ float3 crossing_pw(const SceneDev &sc, int k, float3 
     g.z -= Nk.z * s;
     return g;
 }
+// Geometry-gradient accumulators (scratch of the geometry adjoints, in internal order): dp
+// [n][GEO_DP] (x, y, z, unused), ds [n][2] and gF [n][GEO_GF] (dL/dt^u at GEO_TU, dL/dt^v at
+// GEO_TV, dL/dn at GEO_N, three floats each), so that each 3-vector is one 16-byte (and each
+// scale pair one 8-byte) vector atomic.
+constexpr int GEO_DP = 4, GEO_GF = 12, GEO_TU = 0, GEO_TV = 4, GEO_N = 8;
+__device__ __forceinline__ void geo_add3(float *base, float3 v) {
+    atomicAdd(reinterpret_cast<float4 *>(base), make_float4(v.x, v.y, v.z, 0.f));
+}
+__device__ __forceinline__ void geo_add2(float *base, float x, float y) {
+    atomicAdd(reinterpret_cast<float2 *>(base), make_float2(x, y));
+}
 // Frame gradients of an occluder k crossed at o + t d (u, v from crossing_pw), scaled by
 // coef = dL/dq, added to gF[k] = (dL/dt^u, dL/dt^v, dL/dn): q = u^2 + v^2 with
 // u = (x - p_k).t^u_k / s^u_k moves with t^u_k by 2 u (x - p_k) / s^u_k, and with n_k through
@@ -380,17 +391,14 @@ __device__ __forceinline__ float3 crossing_pw(const SceneDev &sc, int k, float3 
 __device__ __forceinline__ void occluder_frame_grad(const SceneDev &sc, int k, float3 o, float3 d, float t, float u,
                                                     float v, float coef, float *gF) {
     const float4 Pk = __ldg(&sc.P[k]), Nk = __ldg(&sc.N4[k]), U = __ldg(&sc.FU[k]), V = __ldg(&sc.FV[k]);
-    const float xm[3] = {o.x + t * d.x - Pk.x, o.y + t * d.y - Pk.y, o.z + t * d.z - Pk.z};
+    const float3 xm = make_float3(o.x + t * d.x - Pk.x, o.y + t * d.y - Pk.y, o.z + t * d.z - Pk.z);
     const float a = 2.f * u * U.w, b = 2.f * v * V.w;
     const float gxd = a * (U.x * d.x + U.y * d.y + U.z * d.z) + b * (V.x * d.x + V.y * d.y + V.z * d.z);
     const float fn = -gxd / (Nk.x * d.x + Nk.y * d.y + Nk.z * d.z);
-    float *g = gF + 9 * (size_t)k;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        atomicAdd(&g[q], coef * a * xm[q]);
-        atomicAdd(&g[3 + q], coef * b * xm[q]);
-        atomicAdd(&g[6 + q], coef * fn * xm[q]);
-    }
+    float *g = gF + GEO_GF * (size_t)k;
+    geo_add3(g + GEO_TU, (coef * a) * xm);
+    geo_add3(g + GEO_TV, (coef * b) * xm);
+    geo_add3(g + GEO_N, (coef * fn) * xm);
 }
 // dL/dn of a term gR . Y(R w) with R w = 2 (n.w) n - w: 2 ((n.gR) w + (n.w) gR)
 __device__ __forceinline__ float3 reflect_grad_n(float3 n, float3 w, float3 gR) {
@@ -882,6 +890,11 @@ rgs_status rgs_shadow_backward(rgs_transport *t, int nc, cudaStream_t st, float 
                                float *gF = nullptr);
 rgs_status rgs_adjoint_finalize(rgs_transport *t, int nc, float *dE, float *dad, float *dop, cudaStream_t st);
 void rgs_copy_offsets(const long long *off, unsigned long long *cursor, int n, cudaStream_t st);
+// stable sort of every segment [seg[s], seg[s+1]) of (key, value) by the low 8 * passes bits of
+// the key (one 8-bit pass each, one block per segment; rgs_tc.cu); the result lands in (k1, v1)
+// for an odd pass count, in (k0, v0) for an even one
+rgs_status rgs_seg_sort(const long long *seg, int nseg, int passes, uint32_t *k0, uint2 *v0, uint32_t *k1, uint2 *v1,
+                        cudaStream_t st);
 // center-to-center transport: fills the transposed pair index tr [n_pairs] (rgs_pairs.cu)
 rgs_status rgs_pairs_transpose(rgs_transport *t, int2 *tr, cudaStream_t st);
 int rgs_scan_tmp_size(int n);

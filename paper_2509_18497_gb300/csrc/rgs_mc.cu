@@ -7,7 +7,9 @@
 // draw with replacement with probability proportional to each receiver's tracked variance
 // (an FP64 scan of the variances in caller order and a binary search of the draw's uniform).
 // Its next event is one of a's pairs, picked by a single-item weighted reservoir (Chao's
-// scheme) streamed over a's pairs in caller order of the source, with proxy weights
+// scheme) streamed over a's pairs in caller order of the source (the transport stores them in
+// internal order; a per-receiver sorted copy, cached with the transport, gives the caller
+// order), with proxy weights
 //     w_b = geo_ab (sum_c lum(c) |Y(-d)^T Bhat_b[c]| + floor),  floor = 1e-9 (1 + mean lum),
 // or, with K-means groups, first a group by its proxy (mean centre, mean normal, the sum of
 // its members' means; zero for a group holding none of a's sources), then a pair inside it.
@@ -32,6 +34,8 @@ struct rgs_mc_cache {
     int *assign = nullptr; // [n] internal order
     double *gc = nullptr, *gn = nullptr; // [G][3]
     long long bytes = 0;
+    int2 *rec = nullptr; // [n_pairs] the transport's pair records, each receiver's by caller index of the source
+    long long rec_bytes = 0;
 };
 
 namespace {
@@ -136,6 +140,17 @@ struct McArgs {
     float *delta_out; // [n_draws][nc][C] caller layout
     int *bad;         // count of draws whose receiver index is out of range
 };
+
+// sort keys of the pair records: the caller index of the source
+__global__ void k_mc_rec_keys(long long n_pairs, const int2 *__restrict__ rec, const int *__restrict__ uid,
+                              uint32_t *key, uint2 *val) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_pairs;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int2 r = rec[e];
+        key[e] = (uint32_t)__ldg(&uid[r.x]);
+        val[e] = make_uint2((uint32_t)r.x, (uint32_t)r.y);
+    }
+}
 
 template <int NC>
 __device__ __forceinline__ float row_lum(const float *Y, const float *X, int C) {
@@ -623,7 +638,7 @@ rgs_status ensure_groups(rgs_transport *t, int G, cudaStream_t st) {
     m->G = 0;
     rgs_status r;
     const int n = t->n;
-    long long acct = 0;
+    long long acct = m->bytes; // a reallocation takes the old blocks' sizes off
     if ((r = dev_alloc(&m->assign, (size_t)n, &acct)) != RGS_OK) return r;
     if ((r = dev_alloc(&m->gc, (size_t)3 * G, &acct)) != RGS_OK) return r;
     if ((r = dev_alloc(&m->gn, (size_t)3 * G, &acct)) != RGS_OK) return r;
@@ -665,6 +680,34 @@ rgs_status ensure_groups(rgs_transport *t, int G, cudaStream_t st) {
     return RGS_OK;
 }
 
+// the caller-ordered copy of t's pair records (cached)
+rgs_status ensure_caller_rec(rgs_transport *t, cudaStream_t st) {
+    if (!t->mc) t->mc = new rgs_mc_cache();
+    rgs_mc_cache *m = t->mc;
+    const long long np = t->n_pairs;
+    if (m->rec || np == 0) return RGS_OK;
+    rgs_status r;
+    long long acct = 0;
+    if ((r = dev_alloc(&m->rec, (size_t)np, &acct)) != RGS_OK) return r;
+    t->device_bytes += acct;
+    m->rec_bytes = acct;
+    Scratch s{st};
+    uint32_t *k0, *k1;
+    uint2 *v0;
+    if ((r = s.get(&k0, (size_t)np)) != RGS_OK || (r = s.get(&k1, (size_t)np)) != RGS_OK ||
+        (r = s.get(&v0, (size_t)np)) != RGS_OK)
+        return r;
+    const SceneDev sd = t->sc->dev();
+    { ProfScope ps_("k_mc_rec_keys", st); k_mc_rec_keys<<<std::min<long long>((np + 255) / 256, 4096), 256, 0, st>>>(np, t->pair_rec, sd.uid, k0, v0); }
+    RGS_LAUNCH("mc pair keys");
+    // caller indices below 2^24 take three passes (the result in the odd buffers), else four
+    uint2 *v1 = reinterpret_cast<uint2 *>(m->rec);
+    if (t->n <= (1 << 24)) return rgs_seg_sort(t->pair_off, t->n, 3, k0, v0, k1, v1, st);
+    if ((r = rgs_seg_sort(t->pair_off, t->n, 4, k0, v0, k1, v1, st)) != RGS_OK) return r;
+    RGS_CUDA(cudaMemcpyAsync(v1, v0, sizeof(uint2) * np, cudaMemcpyDeviceToDevice, st));
+    return RGS_OK;
+}
+
 // per-step inputs shared by the solve and the estimate: the floor's sum and the group sums
 template <int NC>
 rgs_status step_inputs(rgs_transport *t, const float *Bhat, double *lum_acc, double *Bsum, int G, cudaStream_t st) {
@@ -687,7 +730,7 @@ McArgs base_args(rgs_transport *t, int G, const float *S, const float *Bhat, con
     A.n = t->n;
     A.C = t->C;
     A.pair_off = t->pair_off;
-    A.rec = t->pair_rec;
+    A.rec = t->mc && t->mc->rec ? t->mc->rec : t->pair_rec; // the caller-ordered copy (none: no pairs)
     A.S = S;
     A.Bhat = Bhat;
     A.lum_acc = lum_acc;
@@ -706,7 +749,7 @@ rgs_status mc_solve_nc(rgs_transport *t, const float *E, const float *S_in, int 
     rgs_status r;
     const int n = t->n, C = t->C, R = C * NC;
     const size_t M = t->arr();
-    if ((r = ensure_groups(t, G, st)) != RGS_OK) return r;
+    if ((r = ensure_groups(t, G, st)) != RGS_OK || (r = ensure_caller_rec(t, st)) != RGS_OK) return r;
     Scratch s{st};
     float *S, *Bhat;
     double *SB, *SB2, *D, *var, *cum, *lum_acc, *Bsum = nullptr;
@@ -766,7 +809,7 @@ rgs_status mc_estimate_nc(rgs_transport *t, const float *E, const float *Bhat_us
     rgs_status r;
     const int n = t->n, C = t->C, R = C * NC;
     const size_t M = t->arr();
-    if ((r = ensure_groups(t, G, st)) != RGS_OK) return r;
+    if ((r = ensure_groups(t, G, st)) != RGS_OK || (r = ensure_caller_rec(t, st)) != RGS_OK) return r;
     Scratch s{st};
     float *S, *Bhat;
     double *lum_acc, *Bsum = nullptr;
@@ -844,7 +887,8 @@ void rgs_mc_free(rgs_transport *t) {
     dev_free(t->mc->assign);
     dev_free(t->mc->gc);
     dev_free(t->mc->gn);
-    t->device_bytes -= t->mc->bytes;
+    dev_free(t->mc->rec);
+    t->device_bytes -= t->mc->bytes + t->mc->rec_bytes;
     delete t->mc;
     t->mc = nullptr;
 }

@@ -11,7 +11,8 @@
 // must lie more than eps_plane from the source's end too; int alpha_j is closed-form.
 //
 // Storage: the pairs of receiver i are contiguous (pair_off[i] .. pair_off[i+1]), each one
-// record (j, bits of V_ji), sources in increasing caller index.  A count pass sizes
+// record (j, bits of V_ji), sources in increasing internal (Morton) index, so that a warp's 32
+// segments leave one centre towards neighbouring sources.  A count pass sizes
 // every (receiver, 256-source chunk) block exactly; the fill pass traces each front pair's
 // segment and writes its record at the chunk's offset plus its rank in the block.
 #include <algorithm>
@@ -79,12 +80,6 @@ __device__ __forceinline__ bool pair_front(const SceneDev &sc, float3 pi, float3
     return h > eps;
 }
 
-// The sources of a receiver are enumerated in caller order (chunk c holds the surfels with
-// caller indices c * 256 .. c * 256 + 255), so every receiver's pair list runs by increasing
-// caller index of the source: the order in which the Monte-Carlo solver's reservoir streams
-// a receiver's candidates.  Returns the internal index (n past the end).
-__device__ __forceinline__ int pair_source(const SceneDev &sc, int n, int jc) { return jc < n ? __ldg(&sc.inv[jc]) : n; }
-
 __device__ __forceinline__ float3 unit_dir(float3 dv, float &r) {
     r = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
     const float inv = 1.f / r;
@@ -106,7 +101,7 @@ __device__ __forceinline__ bool pair_occluder(const SceneDev &sc, int k, int i, 
 __global__ void __launch_bounds__(PCH) k_pair_count(SceneDev sc, int n, int chunks, int *chunk_cnt, int *src_cnt) {
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
-    const int j = pair_source(sc, n, c * PCH + threadIdx.x);
+    const int j = c * PCH + threadIdx.x;
     const float eps = *sc.eps_plane;
     const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
     float3 dv;
@@ -122,7 +117,7 @@ __global__ void __launch_bounds__(PCH) k_pair_fill(SceneDev sc, int n, int chunk
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
-    const int j = pair_source(sc, n, c * PCH + threadIdx.x);
+    const int j = c * PCH + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float eps = *sc.eps_plane;
     const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
@@ -363,7 +358,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_g(SceneDev sc, int C, int
         for (int q = 0; q < 3; ++q) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) red[q] += __shfl_xor_sync(0xffffffffu, red[q], off);
-            if ((threadIdx.x & 31) == 0 && red[q] != 0.f) atomicAdd(&gF[9 * (size_t)i + 6 + q], red[q]);
+            if ((threadIdx.x & 31) == 0 && red[q] != 0.f) atomicAdd(&gF[GEO_GF * (size_t)i + GEO_N + q], red[q]);
         }
     }
 }
@@ -387,7 +382,7 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     __shared__ int warp_base[PCH / 32];
     const int blk = blockIdx.x;
     const int i = blk / chunks, c = blk - i * chunks;
-    const int j = pair_source(sc, n, c * PCH + threadIdx.x);
+    const int j = c * PCH + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float eps = *sc.eps_plane;
     const float3 pi = f3(sc.P[i]), ni = f3(sc.N4[i]);
@@ -433,14 +428,11 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
             gd = gd + f * (fabsf(njd) * ni + (fabsf(nid) * sj) * nj);
             gr = g * lj * Aj * T * (-2.f * geo / r);
             const float fs = g * lj * T * geo * Aj;
-            atomicAdd(&ds[2 * j], fs * __ldg(&sc.FU[j].w));
-            atomicAdd(&ds[2 * j + 1], fs * __ldg(&sc.FV[j].w));
+            geo_add2(ds + 2 * (size_t)j, fs * __ldg(&sc.FU[j].w), fs * __ldg(&sc.FV[j].w));
             // normals through geo: d geo/d n_i = |n_j.d| d / r^2, d geo/d n_j = (n_i.d) sgn(n_j.d) d / r^2
             const float fi = f * fabsf(njd), fj = f * fabsf(nid) * sj;
             gni = gni + fi * d;
-            atomicAdd(&gF[9 * (size_t)j + 6], fj * d.x);
-            atomicAdd(&gF[9 * (size_t)j + 7], fj * d.y);
-            atomicAdd(&gF[9 * (size_t)j + 8], fj * d.z);
+            geo_add3(gF + GEO_GF * (size_t)j + GEO_N, fj * d);
         }
         if ((dop || GEO) && nzero <= 1 && g != 0.f) {
             const float q = -g * lj * Aj * geo;
@@ -461,11 +453,9 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
                     const float3 pw = crossing_pw(sc, k, pi, d, tk, uu, vv);
                     gpi = gpi + coef * pw;
                     gd = gd + (coef * tk) * pw;
-                    atomicAdd(&dp[3 * k], -coef * pw.x);
-                    atomicAdd(&dp[3 * k + 1], -coef * pw.y);
-                    atomicAdd(&dp[3 * k + 2], -coef * pw.z);
-                    atomicAdd(&ds[2 * k], coef * (-2.f * uu * uu * __ldg(&sc.FU[k].w)));
-                    atomicAdd(&ds[2 * k + 1], coef * (-2.f * vv * vv * __ldg(&sc.FV[k].w)));
+                    geo_add3(dp + GEO_DP * (size_t)k, (-coef) * pw);
+                    geo_add2(ds + 2 * (size_t)k, coef * (-2.f * uu * uu * __ldg(&sc.FU[k].w)),
+                             coef * (-2.f * vv * vv * __ldg(&sc.FV[k].w)));
                     occluder_frame_grad(sc, k, pi, d, tk, uu, vv, coef, gF);
                 }
             };
@@ -475,9 +465,7 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
             const float dd = dot3(d, gd);
             const float3 gp = make_float3((gd.x - d.x * dd) / r + d.x * gr, (gd.y - d.y * dd) / r + d.y * gr,
                                           (gd.z - d.z * dd) / r + d.z * gr);
-            atomicAdd(&dp[3 * j], gp.x);
-            atomicAdd(&dp[3 * j + 1], gp.y);
-            atomicAdd(&dp[3 * j + 2], gp.z);
+            geo_add3(dp + GEO_DP * (size_t)j, gp);
             dpi = gpi - gp;
         }
     };
@@ -491,8 +479,8 @@ __global__ void __launch_bounds__(PCH) k_pair_grad(SceneDev sc, int n, int chunk
     if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            if (red[q] != 0.f) atomicAdd(&dp[3 * i + q], red[q]);
-            if (red[3 + q] != 0.f) atomicAdd(&gF[9 * (size_t)i + 6 + q], red[3 + q]);
+            if (red[q] != 0.f) atomicAdd(&dp[GEO_DP * (size_t)i + q], red[q]);
+            if (red[3 + q] != 0.f) atomicAdd(&gF[GEO_GF * (size_t)i + GEO_N + q], red[3 + q]);
         }
     }
 }
@@ -507,18 +495,18 @@ __global__ void k_geo_out(SceneDev sc, const float4 *__restrict__ GS, int n, con
     if (i >= n) return;
     const int o = uid[i];
     if (dp)
-        for (int a = 0; a < 3; ++a) dp[3 * o + a] = dp_acc[3 * i + a];
+        for (int a = 0; a < 3; ++a) dp[3 * o + a] = dp_acc[GEO_DP * (size_t)i + a];
     if (ds)
         for (int a = 0; a < 2; ++a) ds[2 * o + a] = ds_acc[2 * i + a];
     if (!dtu && !dtv) return;
     const float3 tu = f3(sc.FU[i]), tv = f3(sc.FV[i]);
     const float4 gs = GS[i];
-    const float *g = gF + 9 * (size_t)i;
-    const float3 Gn = make_float3(g[6], g[7], g[8]);
+    const float *g = gF + GEO_GF * (size_t)i;
+    const float3 Gn = make_float3(g[GEO_N], g[GEO_N + 1], g[GEO_N + 2]);
     const float3 cu = make_float3(tv.y * Gn.z - tv.z * Gn.y, tv.z * Gn.x - tv.x * Gn.z, tv.x * Gn.y - tv.y * Gn.x);
     const float3 cv = make_float3(Gn.y * tu.z - Gn.z * tu.y, Gn.z * tu.x - Gn.x * tu.z, Gn.x * tu.y - Gn.y * tu.x);
-    float3 Gu = make_float3(g[0] + cu.x, g[1] + cu.y, g[2] + cu.z);
-    const float3 Gv = make_float3(g[3] + cv.x, g[4] + cv.y, g[5] + cv.z);
+    float3 Gu = make_float3(g[GEO_TU] + cu.x, g[GEO_TU + 1] + cu.y, g[GEO_TU + 2] + cu.z);
+    const float3 Gv = make_float3(g[GEO_TV] + cv.x, g[GEO_TV + 1] + cv.y, g[GEO_TV + 2] + cv.z);
     const float vg = dot3(tv, Gv);
     const float3 gb = (1.f / gs.y) * (Gv - vg * tv);
     const float3 b = gs.y * tv + gs.z * tu;
@@ -728,13 +716,13 @@ rgs_status rgs_adjoint_pairs_impl(rgs_transport *t, const float *g, float *dE, f
         RGS_CUDA(cudaMemsetAsync(dlam_acc, 0, sizeof(float) * n, st));
     }
     if (want_geo) {
-        if ((r = pool_alloc(&geo.dp, (size_t)n * 3, st)) != RGS_OK) return r;
+        if ((r = pool_alloc(&geo.dp, (size_t)n * GEO_DP, st)) != RGS_OK) return r;
         if ((r = pool_alloc(&geo.ds, (size_t)n * 2, st)) != RGS_OK) return r;
         if ((r = pool_alloc(&geo.gq, (size_t)std::max(t->n_pairs, 1ll), st)) != RGS_OK) return r;
-        if ((r = pool_alloc(&geo.gF, (size_t)n * 9, st)) != RGS_OK) return r;
-        RGS_CUDA(cudaMemsetAsync(geo.dp, 0, sizeof(float) * n * 3, st));
+        if ((r = pool_alloc(&geo.gF, (size_t)n * GEO_GF, st)) != RGS_OK) return r;
+        RGS_CUDA(cudaMemsetAsync(geo.dp, 0, sizeof(float) * n * GEO_DP, st));
         RGS_CUDA(cudaMemsetAsync(geo.ds, 0, sizeof(float) * n * 2, st));
-        RGS_CUDA(cudaMemsetAsync(geo.gF, 0, sizeof(float) * n * 9, st));
+        RGS_CUDA(cudaMemsetAsync(geo.gF, 0, sizeof(float) * n * GEO_GF, st));
     }
     if ((r = rgs_pairs_transpose(t, t->tr, st)) != RGS_OK) return r;
     RGS_CUDA(cudaMemsetAsync(t->flags, 0, sizeof(int) * FLAG_COUNT, st));

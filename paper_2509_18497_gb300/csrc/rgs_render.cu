@@ -227,8 +227,15 @@ __global__ void __launch_bounds__(RN_THREADS) k_render_adj(int npix, int C, cons
             const int2 ja = __ldg(&rec[h]);
             const float ga = __int_as_float(ja.y) * g;
             float *row = dB + ((size_t)ja.x * C + c) * NC;
+            if constexpr (NC % 4 == 0) { // rows of NC floats start on 16-byte boundaries
 #pragma unroll
-            for (int k = 0; k < NC; ++k) atomicAdd(row + k, ga * Yo[k]);
+                for (int q = 0; q < NC / 4; ++q)
+                    atomicAdd(reinterpret_cast<float4 *>(row) + q,
+                              make_float4(ga * Yo[4 * q], ga * Yo[4 * q + 1], ga * Yo[4 * q + 2], ga * Yo[4 * q + 3]));
+            } else {
+#pragma unroll
+                for (int k = 0; k < NC; ++k) atomicAdd(row + k, ga * Yo[k]);
+            }
         }
     }
 }

@@ -1276,6 +1276,18 @@ rgs_status launch_contract(const rgs_transport *t, TcArgs a, cudaStream_t st) {
 
 } // namespace
 
+rgs_status rgs_seg_sort(const long long *seg, int nseg, int passes, uint32_t *k0, uint2 *v0, uint32_t *k1, uint2 *v1,
+                        cudaStream_t st) {
+    if (nseg <= 0) return RGS_OK;
+    for (int p = 0; p < passes; ++p) {
+        ProfScope ps_("k_tc_sort_pass", st);
+        if (p % 2 == 0) k_tc_sort_pass<<<nseg, SORT_THREADS, 0, st>>>(seg, 8 * p, k0, v0, k1, v1);
+        else k_tc_sort_pass<<<nseg, SORT_THREADS, 0, st>>>(seg, 8 * p, k1, v1, k0, v0);
+    }
+    RGS_LAUNCH("segmented sort");
+    return RGS_OK;
+}
+
 void rgs_tc_free(rgs_transport *t) {
     if (!t->tc) return;
     pairs_free(t->tc->fwd);
