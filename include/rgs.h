@@ -361,10 +361,17 @@ rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
  *   mode =  0 : always the row-gather kernels;
  *   mode =  1 : the tensor-core form whenever it applies (any C; still not for checkpointed
  *               solves, SH degree < 3, more than 2^20 surfels or 512 rays per surfel);
- *   mode =  2 : as 1, and the adjoint's opacity gather on the tensor cores too (per (source
- *               tile, receiver) group C / 16 products of 128 x 16 x 16 against the tile's
- *               sources' rows held in tensor memory; C <= 768).  It is correct but measured
- *               slower than the row-gather opacity kernels, which modes -1 and 1 keep.
+ *   mode =  2 : as 1, with the adjoint's opacity gather as per (source tile, receiver) group
+ *               products (C / 16 products of 128 x 16 x 16 against the tile's sources' rows
+ *               held in tensor memory; C <= 768): correct, but slower than mode 1's form;
+ *   mode =  3 : as 1, with the adjoint's opacity gather as row gathers on the CUDA cores.
+ * Modes -1 and 1 run the adjoint's opacity gather (g_h = sum_c y_r[c] (Y(-d)^T B_j[c]) per
+ * stored hit, y_r = (pi/nd) o_i c_i (x) Y(R_i d_r)^T v_i per ray) as sampled products on the
+ * tensor cores: the rays' y rows are formed once (BF16, at most 320 columns per pass; the
+ * buffer takes 2 bytes per ray and column of a pass, sized to free device memory), and per
+ * tile of 8 sources and block of 128 of its hits a 128 x 128 product of the hits' gathered
+ * y rows with the 8 sources' BF16 rows keeps each hit's own 16 entries.  Where no pass fits
+ * in memory they fall back to mode 3's row gathers.
  * The tensor-core form regroups the hit records once per trace into tiles of 8 consecutive
  * receivers, and per tile into the sources they see; per (tile, source) it forms the 8
  * receivers' 16 x 16 transport blocks G_ij = sum_{r,h: j_h = j} a_rh Y(R_i d_r) Y(-d_r)^T as a
@@ -373,8 +380,8 @@ rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
  * memory.  RGS_BF16_FP32ACC_RESCORR's last bounce splits both operands into BF16 high and low
  * parts (three products, FP32-level accuracy).  rgs_adjoint then runs the transposed bounces
  * the same way over tiles of 8 sources (y = o c (x) v rounded to BF16), with FP32 outputs.
- * Extra device memory: about 40 bytes per stored hit and three BF16 copies of an iterate.
- * Host-only.  Errors: RGS_ERR_ARG (NULL transport, mode outside [-1, 2]). */
+ * Extra device memory: about 48 bytes per stored hit and three BF16 copies of an iterate.
+ * Host-only.  Errors: RGS_ERR_ARG (NULL transport, mode outside [-1, 3]). */
 rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode);
 
 /* Sizes of the tensor-core contraction's pair tiles for t (built by the first solve or

@@ -661,9 +661,9 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
     auto KT = [&](int a) -> rgs_status {
         rgs_status q;
         if (tcp) { // tensor cores over source tiles: y^(a-1) = o c (x) v^(a-1) in BF16 row blocks
-            // the opacity gather pairs y^(a) with B^(n-1-a) while y^(a) is at hand
-            // (on the tensor cores only in mode 2: at 16 columns per MMA and C / 16 products per
-            // (tile, receiver) group it measured slower than the row gathers below)
+            // mode 2: the opacity gather pairs y^(a) with B^(n-1-a) while y^(a) is at hand, per
+            // (tile, receiver) group (at 16 columns per MMA it measured slower than the row
+            // gathers and than the sampled products that modes -1 and 1 run after the bounces)
             const bool gh = (dopo || geo) && nb >= 1 && t->tc_mode == 2;
             if (a == 1) {
                 if ((q = rgs_tc_make_y(t, vp(0), 0, st)) != RGS_OK) return q;
@@ -720,6 +720,9 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
         if ((r = pool_alloc(&seg.nrm, RGS_MAX_BOUNCES + 1, st)) != RGS_OK) return r;
     }
     bool first_g = true;
+    // the opacity gather's form, fixed for the whole adjoint (the sampled products sum in
+    // the source tiles' hit order and hand the record slots their sums after the last pairing)
+    const bool sddmm = tcp && (t->tc_mode == -1 || t->tc_mode == 1) && rgs_tc_opa_pass_cols(t) > 0;
     for (int hi = nb - 1; hi >= 0;) {
         const int lo = s ? (hi / s) * s : 0;
         // iterates B^(b) (FP32, BF16) and Q^(b) of this segment, indexed by b - lo
@@ -746,7 +749,12 @@ rgs_status run_adjoint(rgs_transport *t, const float *g, float *dE, float *dad, 
             { ProfScope ps_("k_pair_accum", st); k_pair_accum<NC><<<gn, 128, 0, st>>>(n, C, vp(a), Qb[b - lo], t->Pg); }
             RGS_LAUNCH("pair accum");
         }
-        if ((dopo || geo) && !(tcp && t->tc_mode == 2)) { // g_h over this segment's iterates, four per launch
+        if ((dopo || geo) && sddmm) { // g_h as sampled products on the tensor cores
+            for (int b = hi; b >= lo; --b) {
+                if ((r = rgs_tc_opacity_sddmm(t, vp(nb - 1 - b), Bf[b - lo], first_g, b == 0, st)) != RGS_OK) return r;
+                first_g = false;
+            }
+        } else if ((dopo || geo) && !(tcp && t->tc_mode == 2)) { // g_h over this segment's iterates, four per launch
             for (int b0 = hi; b0 >= lo; b0 -= 4) {
                 const int na = min(4, b0 - lo + 1);
                 const float *vv[4], *bb[4];

@@ -498,8 +498,8 @@ rgs_status rgs_set_checkpointing(rgs_transport *t, int32_t stride) {
 }
 
 rgs_status rgs_set_tensor_cores(rgs_transport *t, int32_t mode) {
-    if (!t || mode < -1 || mode > 2) {
-        rgs_set_error("rgs_set_tensor_cores: NULL transport or mode outside [-1, 2]");
+    if (!t || mode < -1 || mode > 3) {
+        rgs_set_error("rgs_set_tensor_cores: NULL transport or mode outside [-1, 3]");
         return RGS_ERR_ARG;
     }
     t->tc_mode = mode;

@@ -837,6 +837,23 @@ rgs_status rgs_tc_bounce(rgs_transport *t, int in, int out, bool split, bool wan
 rgs_status rgs_tc_make_y(rgs_transport *t, const float *v, int slot, cudaStream_t st);
 rgs_status rgs_tc_adjoint_bounce(rgs_transport *t, int in, int out, float *vout, float *u, cudaStream_t st);
 rgs_status rgs_tc_opacity(rgs_transport *t, int slot, const float *Bsrc, bool first, cudaStream_t st);
+// the adjoint's source tiles' hits (built by rgs_tc_prepare_adjoint): per tile [hoff[t], hoff[t+1]),
+// per hit its direction (source slot in the weight's 3 low bits), record slot and ray
+// per hit its direction (source slot in the weight's 3 low bits), record slot and ray, and a
+// per-hit float buffer in the same order
+struct RgsTcAdjHits {
+    int ntiles;
+    long long n_hits;
+    const long long *hoff;
+    const float4 *hd;
+    const uint32_t *hslot, *hray;
+    float *gt;
+};
+bool rgs_tc_adj_hits(const rgs_transport *t, RgsTcAdjHits *out);
+// the opacity gather of one adjoint pairing as a sampled product on the tensor cores (rgs_tc_opa.cu)
+rgs_status rgs_tc_opacity_sddmm(rgs_transport *t, const float *v, const float *B, bool first, bool last,
+                                cudaStream_t st);
+int rgs_tc_opa_pass_cols(const rgs_transport *t);
 rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st); // RGS_ERR_TIMEOUT if a bounded wait ran out
 rgs_status rgs_tc_reset_flags(rgs_transport *t, cudaStream_t st);
 // drops the Monte-Carlo solver's cached K-means groups (rgs_mc.cu)

@@ -1030,7 +1030,8 @@ __global__ void __launch_bounds__(256) k_tc_group_count(const long long *__restr
 __global__ void __launch_bounds__(256) k_tc_finish(const long long *__restrict__ seg, const long long *__restrict__ goff,
                                                    const uint32_t *__restrict__ key, const uint2 *__restrict__ pay,
                                                    const float4 *__restrict__ dir, const long long *__restrict__ off,
-                                                   int nd, int adjoint, int2 *grp, float4 *hd, uint32_t *hslot) {
+                                                   int nd, int adjoint, int2 *grp, float4 *hd, uint32_t *hslot,
+                                                   uint32_t *hray) {
     const int t = blockIdx.x;
     const long long s0 = seg[t], s1 = seg[t + 1];
     for (long long e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
@@ -1042,6 +1043,7 @@ __global__ void __launch_bounds__(256) k_tc_finish(const long long *__restrict__
         const float4 d = dir[r];
         hd[e] = make_float4(d.x, d.y, d.z, __uint_as_float((pv.x & ~7u) | (uint32_t)p));
         if (hslot) hslot[e] = (uint32_t)(off[r] + pv.y); // the record slot of the hit (its ray's h-th)
+        if (hray) hray[e] = (uint32_t)r;
     }
     // groups: one warp walks the runs in 32-element windows
     if (threadIdx.x < 32) {
@@ -1107,6 +1109,8 @@ struct TcPairs {
     int2 *grp = nullptr;
     float4 *hd = nullptr;
     uint32_t *hslot = nullptr; // source tiles: each hit's record slot (the opacity gather writes g_h there)
+    uint32_t *hray = nullptr;  // source tiles: each hit's ray (the opacity gather reads its y row)
+    float *gt = nullptr;       // source tiles: the opacity gather's per-hit sums in this order
 };
 
 struct rgs_tc_state {
@@ -1126,6 +1130,8 @@ void pairs_free(TcPairs &p) {
     dev_free(p.grp);
     dev_free(p.hd);
     dev_free(p.hslot);
+    dev_free(p.hray);
+    dev_free(p.gt);
     p = TcPairs{};
 }
 
@@ -1179,6 +1185,8 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
     if ((r = dev_alloc(&P.goff, (size_t)ntiles + 1)) != RGS_OK) return r;
     if ((r = dev_alloc(&P.hd, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
     if (adjoint && (r = dev_alloc(&P.hslot, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
+    if (adjoint && (r = dev_alloc(&P.hray, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
+    if (adjoint && (r = dev_alloc(&P.gt, (size_t)std::max(H, 1ll))) != RGS_OK) return r;
     if (!adjoint) {
         { ProfScope ps_("k_tc_tile_count", st); k_tc_tile_count_fwd<<<(ntiles + 7) / 8, 256, 0, st>>>(t->cnt, n, nd, ntiles, tcount); }
     } else {
@@ -1219,7 +1227,7 @@ rgs_status build_pairs(rgs_transport *t, bool adjoint, TcPairs &P, cudaStream_t 
     P.n_groups = ng;
     P.n_pairs = (long long)np;
     if ((r = dev_alloc(&P.grp, (size_t)std::max(ng, 1ll))) != RGS_OK) return r;
-    { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, t->off, nd, adjoint ? 1 : 0, P.grp, P.hd, P.hslot); }
+    { ProfScope ps_("k_tc_finish", st); k_tc_finish<<<ntiles, 256, 0, st>>>(P.hoff, P.goff, kin, pin, t->dir, t->off, nd, adjoint ? 1 : 0, P.grp, P.hd, P.hslot, P.hray); }
     RGS_LAUNCH("tc finish");
     return RGS_OK;
 }
@@ -1315,6 +1323,13 @@ rgs_status rgs_tc_check(rgs_transport *t, cudaStream_t st) {
     return RGS_OK;
 }
 
+bool rgs_tc_adj_hits(const rgs_transport *t, RgsTcAdjHits *out) {
+    if (!t->tc || !t->tc->adj_ok) return false;
+    const TcPairs &P = t->tc->adj;
+    *out = RgsTcAdjHits{P.ntiles, P.n_hits, P.hoff, P.hd, P.hslot, P.hray, P.gt};
+    return true;
+}
+
 void rgs_tc_invalidate(rgs_transport *t) {
     if (!t->tc) return;
     t->tc->fwd_ok = t->tc->adj_ok = false;
@@ -1327,8 +1342,8 @@ bool rgs_tc_eligible(const rgs_transport *t, int precision) {
     if (t->tc_mode < 0 && t->C < RGS_TC_MIN_COLS) return false; // automatic: many right-hand sides only
     if (2 * ((t->C + 15) / 16) * 8 + 64 > 512 && t->tc_mode == 2) return false; // opacity operand in TMEM
     if (t->stride != 0) return false; // the adjoint reads every iterate of this path
-    // memory: two structures of 16-20 B per hit, three blocked BF16 arrays, sort scratch of 24 B per hit
-    const double need = 2.0 * 20.0 * t->n_hits + 24.0 * t->n_hits + 3.0 * 2.0 * t->n * (double)((t->C + 15) & ~15) * 16;
+    // memory: two structures of 16-28 B per hit, three blocked BF16 arrays, sort scratch of 24 B per hit
+    const double need = 48.0 * t->n_hits + 24.0 * t->n_hits + 3.0 * 2.0 * t->n * (double)((t->C + 15) & ~15) * 16;
     return need < 0.8 * (double)pool_available_bytes();
 }
 

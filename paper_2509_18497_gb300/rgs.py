@@ -388,8 +388,9 @@ def rgs_set_memory_budget(transport, nbytes):
 
 def rgs_set_tensor_cores(transport, mode):
     """Contraction of the batched modes: -1 automatic (tensor cores from 96 columns), 0 the
-    row-gather kernels, 1 the tensor-core form wherever it applies, 2 as 1 with the adjoint's
-    opacity gather on the tensor cores too."""
+    row-gather kernels, 1 the tensor-core form wherever it applies (the adjoint's opacity
+    gather as sampled products on the tensor cores in both), 2 as 1 with the opacity gather
+    as per-(tile, receiver) products, 3 as 1 with the opacity gather as row gathers."""
     _check(load().rgs_set_tensor_cores(transport.h, int(mode)))
 
 

@@ -52,14 +52,16 @@ def _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GAUSS, mode=TC):
 
 @pytest.mark.parametrize("n_lights", [1, 20])
 def test_tensor_cores_against_oracle(n_lights):
-    """Mode 1 (bounces and transposed bounces on the tensor cores) and mode 2 (the opacity
-    gather too)."""
+    """Mode 1 (bounces, transposed bounces and the opacity gather's sampled products on the
+    tensor cores), mode 2 (the opacity gather as per-(tile, receiver) products instead) and
+    mode 3 (the opacity gather as row gathers)."""
     sc = scenes.with_emission(scenes.fruit_bowl(n=2997, L=3, nd=64, nb=3, n_lights=n_lights), seed=4)
     C = 3 * n_lights
     W = np.random.default_rng(9).normal(size=(sc["n"], 16, C))
     o = run_oracle(sc, W=W)
     _check(sc, W, o, mode=1)
     _check(sc, W, o, mode=2)
+    _check(sc, W, o, mode=3)
 
 
 def test_tensor_cores_gfsgs():
@@ -67,6 +69,7 @@ def test_tensor_cores_gfsgs():
     W = np.random.default_rng(2).normal(size=(sc["n"], 16, 9))
     o = run_oracle(sc, W=W, alpha_model=O.ALPHA_GFSGS)
     _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GFSGS, mode=2)
+    _check(sc, W, o, alpha_model=rgs.RGS_ALPHA_GFSGS, mode=3)
 
 
 def test_tensor_cores_match_row_gathers():
@@ -100,6 +103,18 @@ def test_tensor_core_wait_limit_reports_timeout():
     B, _ = pipe.solve(d["E"], d["nb"])
     ref = run_gpu(sc, precision=rgs.RGS_BF16_FP32ACC, tensor_cores=0)
     assert rel_l2(B.double().cpu().numpy(), ref["B"]) <= TOL_BF16
+    # the adjoint (transposed bounces and the sampled-product opacity gather): their waits
+    # run out as well
+    g = torch.ones((sc["n"], 16, 24), device="cuda")
+    rgs.rgs_set_wait_limit(pipe.transport, 1)
+    with pytest.raises(rgs.RgsError) as err:
+        pipe.adjoint(g)
+    assert err.value.status == 6
+    torch.cuda.synchronize()
+    rgs.rgs_set_wait_limit(pipe.transport, 0)
+    dE, dad, dop = pipe.adjoint(g)
+    ref = run_gpu(sc, W=np.ones((sc["n"], 16, 24)), precision=rgs.RGS_BF16_FP32ACC, tensor_cores=0)
+    assert rel_l2(dop.double().cpu().numpy(), ref["dop"]) <= TOL_BF16
 
 
 @pytest.fixture(scope="module")
@@ -115,6 +130,23 @@ def test_hundred_lights_tensor_cores_full_oracle(hundred):
     sc, W, o = hundred
     _check(sc, W, o, mode=1)
     _check(sc, W, o, mode=2)
+    _check(sc, W, o, mode=3)
+
+
+def test_opacity_products_in_two_column_passes():
+    """120 lights (C = 360): the sampled-product opacity gather (mode 1) forms the rays' y rows
+    in passes of at most 320 columns, so this case takes two (320 + 40 columns, the second
+    padded with zeros to 64).  Against the oracle on every gradient entry, and against the
+    row-gather opacity kernels (mode 3) on the same bounces: equal up to the BF16 rounding
+    of y and of the source rows."""
+    sc = scenes.with_emission(scenes.multi_light(n=603, nd=32, nb=2, n_lights=120), seed=8)
+    W = np.random.default_rng(12).normal(size=(sc["n"], 16, 360))
+    o = run_oracle(sc, W=W)
+    _check(sc, W, o, mode=1)
+    a = run_gpu(sc, W=W, precision=rgs.RGS_BF16_FP32ACC, tensor_cores=1)
+    b = run_gpu(sc, W=W, precision=rgs.RGS_BF16_FP32ACC, tensor_cores=3)
+    assert rel_l2(a["dE"], b["dE"]) <= 1e-6  # the same transposed bounces
+    assert rel_l2(a["dop"], b["dop"]) <= TOL_BF16
 
 
 def test_hundred_lights_fp32_and_row_gathers_full_oracle(hundred):
