@@ -890,7 +890,8 @@ static void pair_apply_K(const or_scene *s, const double *Bin, double *Bout, dou
     int n = s->n, nc = s->nc, C = s->C, L = s->L;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < n; ++i) {
-        double Yo[1024], Yi[1024], acc[16384];
+        double Yo[1024], Yi[1024];
+        double *acc = dup_arr(NULL, (size_t)nc * C);
         memset(acc, 0, sizeof(double) * nc * C);
         for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
             double d[3], md[3], rd[3];
@@ -912,6 +913,7 @@ static void pair_apply_K(const or_scene *s, const double *Bin, double *Bout, dou
                 if (Q) Q[idx] = acc[kk * C + c];
                 if (Bout) Bout[idx] = alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
             }
+        free(acc);
     }
 }
 
@@ -919,7 +921,8 @@ static void pair_apply_K(const or_scene *s, const double *Bin, double *Bout, dou
 static void pair_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
     int n = s->n, nc = s->nc, C = s->C, L = s->L;
     memset(Vout, 0, sizeof(double) * (size_t)n * nc * C);
-    double Yo[1024], Yi[1024], y[4096];
+    double Yo[1024], Yi[1024];
+    double *y = dup_arr(NULL, (size_t)C);
     for (int i = 0; i < n; ++i)
         for (long e = s->pair_off[i]; e < s->pair_off[i + 1]; ++e) {
             double d[3], md[3], rd[3];
@@ -938,6 +941,7 @@ static void pair_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
             for (int kk = 0; kk < nc; ++kk)
                 for (int c = 0; c < C; ++c) Vj[kk * C + c] += s->pair_V[e] * Yo[kk] * y[c];
         }
+    free(y);
 }
 
 /* Source-side gradients of the pairs: with g_e = dL/dV_ji (summed over the bounces),
@@ -1000,7 +1004,8 @@ void or_apply_K(const or_scene *s, const double *Bin, double *Bout, double *Q) {
     double w = OR_PI / nd;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < n; ++i) {
-        double Yo[1024], Yi[1024], x[4096], acc[16384];
+        double Yo[1024], Yi[1024];
+        double *x = dup_arr(NULL, (size_t)C), *acc = dup_arr(NULL, (size_t)nc * C);
         memset(acc, 0, sizeof(double) * nc * C);
         for (int r = 0; r < nd; ++r) {
             double d[3], md[3], rd[3];
@@ -1028,6 +1033,8 @@ void or_apply_K(const or_scene *s, const double *Bin, double *Bout, double *Q) {
                 if (Q) Q[idx] = acc[kk * C + c];
                 if (Bout) Bout[idx] = alpha_c(s, i) * s->c[((size_t)i * (L + 1) + band_of(kk)) * 3 + c % 3] * acc[kk * C + c];
             }
+        free(x);
+        free(acc);
     }
 }
 
@@ -1043,7 +1050,8 @@ void or_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
     int n = s->n, nc = s->nc, C = s->C, nd = s->nd, L = s->L;
     double w = OR_PI / nd;
     memset(Vout, 0, sizeof(double) * (size_t)n * nc * C);
-    double Yo[1024], Yi[1024], y[4096];
+    double Yo[1024], Yi[1024];
+    double *y = dup_arr(NULL, (size_t)C);
     for (int i = 0; i < n; ++i) {
         for (int r = 0; r < nd; ++r) {
             double d[3], md[3], rd[3];
@@ -1066,6 +1074,7 @@ void or_apply_KT(const or_scene *s, const double *Vin, double *Vout) {
             }
         }
     }
+    free(y);
 }
 
 /* S = E (broadcast over lights) + D */
@@ -1371,7 +1380,8 @@ void or_sample_bounce1(const or_scene *s, int nd, uint64_t seed, int nl, const d
         double *Q = dup_arr(NULL, (size_t)nc * C);
         memset(Q, 0, sizeof(double) * nc * C);
         double *Sj = dup_arr(NULL, (size_t)nc * C);
-        double Yo[1024], Yi[1024], x[4096];
+        double Yo[1024], Yi[1024];
+        double *x = dup_arr(NULL, (size_t)C);
         hitvec hv = {0};
         for (int r = 0; r < nd; ++r) {
             double d[3], md[3], rd[3];
@@ -1406,6 +1416,7 @@ void or_sample_bounce1(const or_scene *s, int nd, uint64_t seed, int nl, const d
         free(hv.h);
         free(Q);
         free(Sj);
+        free(x);
     }
 }
 

@@ -133,3 +133,31 @@ def test_gradients_with_directional_lights():
         assert abs(fd("ad", (i, ch)) - g["dad"][i, ch]) <= 1e-6 * scale["ad"]
         i, kk, ch = rng.integers(sc["n"]), rng.integers(9), rng.integers(3)
         assert abs(fd("E", (i, kk, ch)) - g["dE"][i, kk, ch]) <= 1e-6 * scale["E"]
+
+
+def test_wide_batches_split_by_light():
+    """Columns of different lights never mix (Sec. 7's batching of lights as right-hand
+    sides): 400 point lights (1,200 columns, more than a 1,024-column row) give, column for
+    column, what 2-light subsets of them give on their own; and dL/dB nonzero on those
+    columns only gives the subset's gradients."""
+    sc = scenes.multi_light(n=40, nd=8, nb=2, n_lights=400)
+    orc = O.Oracle(sc).transport()
+    C = orc.C
+    assert C == 1200
+    rng = np.random.default_rng(21)
+    B = orc.solve(E=None, nb=sc["nb"])
+    for sel in ([0, 1], [398, 399]):
+        sub = dict(sc)
+        sub["light_pos"] = sc["light_pos"][sel]
+        sub["light_I"] = sc["light_I"][sel]
+        cols = [3 * k + ch for k in sel for ch in range(3)]
+        o2 = O.Oracle(sub).transport()
+        B2 = o2.solve(E=None, nb=sc["nb"])
+        np.testing.assert_allclose(B[..., cols], B2, rtol=1e-12, atol=1e-300)
+        W = np.zeros((sc["n"], 16, C))
+        W[..., cols] = rng.normal(size=(sc["n"], 16, 6))
+        g_full = orc.adjoint(W)
+        g_sub = o2.adjoint(W[..., cols])
+        for key in ("dE", "dad", "dop"):
+            assert np.abs(g_sub[key]).max() > 0.0, key
+            np.testing.assert_allclose(g_full[key], g_sub[key], rtol=1e-10, atol=1e-14 * np.abs(g_sub[key]).max())
