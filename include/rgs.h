@@ -368,7 +368,8 @@ rgs_status rgs_set_memory_budget(rgs_transport *t, int64_t bytes);
  * Modes -1 and 1 run the adjoint's opacity gather (g_h = sum_c y_r[c] (Y(-d)^T B_j[c]) per
  * stored hit, y_r = (pi/nd) o_i c_i (x) Y(R_i d_r)^T v_i per ray) as sampled products on the
  * tensor cores: the rays' y rows are formed once (BF16, at most 320 columns per pass; the
- * buffer takes 2 bytes per ray and column of a pass, sized to free device memory), and per
+ * buffer takes 2 bytes per ray and column of a pass, sized to free device memory and to
+ * half of what rgs_set_memory_budget leaves beside the transport's buffers), and per
  * tile of 8 sources and block of 128 of its hits a 128 x 128 product of the hits' gathered
  * y rows with the 8 sources' BF16 rows keeps each hit's own 16 entries.  Where no pass fits
  * in memory they fall back to mode 3's row gathers.

@@ -402,11 +402,14 @@ __global__ void k_tc_opa_scatter(long long H, const uint32_t *__restrict__ hslot
 
 } // namespace
 
-// columns per pass that the y buffer may take (a multiple of 64, at most 320; 0: none fits)
+// columns per pass that the y buffer may take (a multiple of 64, at most 320; 0: none fits):
+// at most 30 % of the free device memory (48 GB at most) and, under a memory budget, half
+// of what the budget leaves beside the transport's own buffers
 int rgs_tc_opa_pass_cols(const rgs_transport *t) {
     const long long n_rays = (long long)t->n * t->nd;
     const int full = std::min(OP_KW_MAX, (t->C + OP_SC - 1) / OP_SC * OP_SC);
-    const double budget = std::min(0.3 * (double)pool_available_bytes(), 48e9);
+    double budget = std::min(0.3 * (double)pool_available_bytes(), 48e9);
+    if (t->mem_budget > 0) budget = std::min(budget, 0.5 * (double)(t->mem_budget - t->device_bytes));
     int kw = (int)(budget / (2.0 * (double)std::max(n_rays, 1ll)) / OP_SC) * OP_SC;
     return t->nd > YR_MAX_RAYS ? 0 : std::min(full, kw);
 }

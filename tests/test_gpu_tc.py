@@ -84,6 +84,36 @@ def test_tensor_cores_match_row_gathers():
         assert rel_l2(a[key], b[key]) <= TOL_BF16, key
 
 
+def test_opacity_products_respect_the_memory_budget():
+    """A memory budget that leaves no room beside the transport for a 64-column pass of y
+    rows: the adjoint's opacity gather takes the row gathers instead (mode 3's form, the
+    same results), and the gradients still meet the BF16 bar against the oracle."""
+    from paper_2509_18497_gb300 import api
+    sc = scenes.with_emission(scenes.fruit_bowl(n=2001, L=3, nd=64, nb=2, n_lights=40), seed=3)
+    W = np.random.default_rng(6).normal(size=(sc["n"], 16, 120))
+    o = run_oracle(sc, W=W)
+    g = torch.as_tensor(np.ascontiguousarray(W, np.float32), device="cuda")
+    out = {}
+    for mode, budget in ((3, False), (1, True)):
+        d = api.upload(sc)
+        pipe = api.Pipeline(precision=rgs.RGS_BF16_FP32ACC, tensor_cores=mode)
+        pipe.build(d)
+        pipe.trace(d)
+        pipe.solve(d["E"], d["nb"])
+        if budget:
+            rgs.rgs_set_memory_budget(pipe.transport, rgs.rgs_transport_info_get(pipe.transport)["device_bytes"])
+        rgs.rgs_profile_reset()
+        rgs.rgs_profile_enable(True)
+        dE, dad, dop = pipe.adjoint(g)
+        torch.cuda.synchronize()
+        rgs.rgs_profile_enable(False)
+        rep = rgs.rgs_profile_report()
+        assert rep.get("k_tc_opa", (0, 0.0))[0] == 0 and rep.get("k_opacity_g_mc", (0, 0.0))[0] > 0, (mode, rep)
+        out[mode] = dop.double().cpu().numpy()
+        assert rel_l2(out[mode], o["dop"]) <= TOL_BF16
+    assert rel_l2(out[1], out[3]) <= 1e-6
+
+
 def test_tensor_core_wait_limit_reports_timeout():
     """Failure detection without a GPU fault: with a 1 ns limit the pipeline's waits run out,
     every role stops (after draining its own copies and MMAs) and the solve returns
