@@ -16,13 +16,15 @@
 // the 16 entries of each hit's own source and finishes g_h = Y(-d)^T D[h][(sigma_h, .)].
 // The tensor work per hit is 8x the kept part (all 8 sources of the tile are formed), but
 // at 128 x 128 x 16 per instruction it stays below the cost of gathering the y rows, 2 bytes
-// per hit and column, which bounds the kernel.
+// per hit and column, which bounds the kernel (the SM's L1/TEX data pipe).  The sums stay in
+// the tiles' hit order (coalesced) and reach the record slots after the last pairing.
 //
 // Roles (one persistent CTA per SM, source tiles round-robin):
 //   warps 0..3   epilogue (TMEM lane quarters 0..3: one hit row per thread)
 //   warp  4      TMEM owner and MMA issuer (one lane)
-//   warps 5..12  producers: the y rows of the block (warp p: rows 16p .. 16p + 15) through a
-//                ring of 64-column stages, and the tile's source rows
+//   warps 5..12  producers in 4 groups of 2 warps: group q copies the block's 128 y rows of
+//                every stage s = q (mod 4) of a ring of 64-column stages; all 8 load the
+//                tile's source rows
 // Every mbarrier wait is bounded; a wait that runs out sets the transport's error flag and
 // every role leaves its loop (the host then reports RGS_ERR_TIMEOUT).
 #include <algorithm>
@@ -35,7 +37,7 @@ namespace {
 constexpr int OP_EPI = 4;                   // epilogue warps
 constexpr int OP_MW = 4;                    // the MMA warp
 constexpr int OP_P0 = 5;                    // first producer warp
-constexpr int OP_NP = 8;                    // producer warps (16 rows each)
+constexpr int OP_NP = 8;                    // producer warps
 constexpr int OP_THREADS = (OP_P0 + OP_NP) * 32;
 constexpr int OP_ROWS = 128;                // hits per block (the MMA's M)
 constexpr int OP_SC = 64;                   // columns per stage (pass widths are multiples of it)
