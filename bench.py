@@ -155,6 +155,12 @@ def _launch_bytes(kernel, sc):
         "k_tc_bounce": (sc.get("tc_groups", 0) * sc.get("Cp", 0) * 32 + H * 16 + 4 * A + 2 * A16, nb),
         "k_tc_adjoint": (sc.get("tc_src_groups", 0) * sc.get("Cp", 0) * 32 + H * 16 + 3 * A + A16, nb),
         "k_tc_opacity": (sc.get("tc_src_groups", 0) * sc.get("Cp", 0) * 32 + H * (16 + 4 + 8) + A, nb),
+        # opacity products, one pass of kw <= 320 columns per launch (kw = C rounded up to 64):
+        # the hits' y rows (2 B per column), direction + weight, ray and running sum (in tile
+        # order, read and written after the first pass) per hit, the 8-source tiles' rows once;
+        # their y rows: one BF16 row per ray written, the adjoint iterate read once
+        "k_tc_opa": (H * (2 * min(C, 320) + 16 + 4 + 8) + n * min(C, 320) * nc * 4, nb * -(-C // 320)),
+        "k_tc_opa_y": (rays * 2 * min(-(-C // 64) * 64, 320) + n * min(C, 320) * nc * 4, nb * -(-C // 320)),
         # per 32-column tile: records, counts, offsets, directions; the iterate rows once
         "k_bounce_mc": (tiles * (H * 8 + rays * (4 + 8 + 16)) + A16 + 4 * A + A16, nb),
         # one tile and up to four iterates: records + ray data; v (FP32) and B (BF16) tiles; g per hit
@@ -571,6 +577,11 @@ def main():
     tot_ms = max(1e-9, sum(v[1] for v in prof.values()))
     kernels = {k: {"launches_per_step": c / args.steps, "ms_per_step": ms / args.steps, "share": ms / tot_ms}
                for k, (c, ms) in prof.items()}
+    for k, v in kernels.items():  # algorithmic HBM bytes against the copy peak, where the table knows them
+        b = step_algorithmic_bytes(k, infos)
+        if b and v["ms_per_step"] > 0:
+            v["hbm_gbs"] = b / (v["ms_per_step"] * 1e-3) / 1e9
+            v["hbm_frac"] = v["hbm_gbs"] / peak
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
     c_dom, ms_dom = prof[dom]
     alg_step = step_algorithmic_bytes(dom, infos)
@@ -582,7 +593,8 @@ def main():
                 "k_opacity_g": "rgs_adjoint.cu", "k_opacity_rec": "rgs_adjoint.cu",
                 "k_bounce_persistent": "rgs_batch.cu", "k_trace_hemi": "rgs_trace.cu",
                 "k_pair_fill": "rgs_pairs.cu", "k_bounce_pairs": "rgs_pairs.cu", "k_pair_grad": "rgs_pairs.cu",
-                "k_tc_bounce": "rgs_tc.cu", "k_tc_adjoint": "rgs_tc.cu", "k_tc_opacity": "rgs_tc.cu"}.get(dom)
+                "k_tc_bounce": "rgs_tc.cu", "k_tc_adjoint": "rgs_tc.cu", "k_tc_opacity": "rgs_tc.cu",
+                "k_tc_opa": "rgs_tc_opa.cu"}.get(dom)
     traffic = None
     if len(scs) == 1 and dom in NCU_TRAFFIC and src_file and NCU_TRAFFIC[dom]["src_sha"] == _src_sha(src_file):
         traffic = NCU_TRAFFIC[dom]["bytes_per_launch"] * (scs[0]["n"] / NCU_TRAFFIC[dom]["n"])
