@@ -30,6 +30,12 @@ def test_algorithmic_bytes_cover_the_step_kernels():
     import bench
     sc = dict(n=1000, nd=64, nb=3, C=6, nc=16, n_hits=200000)
     for k in ("k_trace_hemi", "k_bounce", "k_bounce_mc", "k_adj_src", "k_adj_ray", "k_opacity_g", "k_opacity_rec",
-              "k_src_fill", "k_pair_fill", "k_bounce_pairs", "k_pair_grad", "k_pair_g"):
+              "k_src_fill", "k_pair_fill", "k_bounce_pairs", "k_pair_grad", "k_pair_g", "k_tc_opa", "k_tc_opa_y"):
         b, launches = bench._launch_bytes(k, sc)
         assert b is not None and b > 0 and launches > 0, k
+    # the opacity products take one pass of at most 320 columns per pairing: 1,536 columns
+    # (the environment map) in five passes, each reading 2 B per hit and pass column
+    wide = dict(sc, C=1536)
+    b, launches = bench._launch_bytes("k_tc_opa", wide)
+    assert launches == 5 * wide["nb"]
+    assert b >= wide["n_hits"] * 2 * 320
