@@ -144,9 +144,10 @@ __global__ void __launch_bounds__(OP_THREADS, 1) k_tc_opa(OpaArgs g) {
     if (warp >= OP_P0) {
         // ------------------------------------------------------------ producers
         // groups of OP_WPG warps own every OP_NG-th stage: a group copies its stage's rows, waits
-        // for its own copies, makes them visible to the tensor core (the proxy fence also
-        // waits for the thread's copies in flight, so one thread never has two stages in
-        // flight) and signals; the other groups' stages are in flight meanwhile
+        // for its own copies, makes them visible to the tensor core and signals, while the
+        // other groups' stages are in flight (with one group whose threads kept several stages
+        // in flight, the proxy fence before each signal took 46 % of the producers' time, as
+        // if it waited for the later stages' copies too)
         const int p = warp - OP_P0, grp = p / OP_WPG, wig = p % OP_WPG;
         const int hl = lane & 15, half = lane >> 4;
         const uint32_t sbase = tc::smem_addr(smem);
